@@ -1,0 +1,227 @@
+/*
+ * ndhss.h -- C ABI of a GB300 (sm_103a) nested-dissection preconditioner
+ * with dense and HSS-compressed fronts (Bonev & Hesthaven, "A hierarchical
+ * preconditioner for wave problems in quasilinear complexity").
+ *
+ * The library solves A x = b for a sparse Galerkin matrix A (Sec. 1,
+ * Eq. 1.1) with GMRES on P^{-1} A x = P^{-1} b (Eq. 1.2), where
+ * P = L D R (Eq. 3.1) is built front by front over a box nested dissection.
+ *
+ * Conventions that hold for every entry point:
+ *  - All functions return an ndhss_status; on failure ndhss_last_error()
+ *    returns a thread-local message (with node / level where known).  No
+ *    function aborts, throws across the ABI or traps the GPU.
+ *  - "host" pointers are ordinary CPU memory, "device" pointers are CUDA
+ *    device memory of the current device.  The caller owns every buffer it
+ *    passes; the library never keeps a caller pointer after returning.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default).
+ *    Device work is ordered on it.  Functions that return host-side results
+ *    (ndhss_factor, ndhss_gmres, ndhss_factor_get_block) synchronise it.
+ *  - Matrices are CSR with int32 row pointers and column indices in the
+ *    ORIGINAL numbering, values float64 (NDHSS_R64) or interleaved
+ *    complex128 (NDHSS_C128).  A must be structurally symmetric.
+ *  - Dense blocks are column-major.  Complex numbers are interleaved
+ *    (re, im) pairs.
+ *  - Opaque handles are owned by the library and released with the
+ *    matching _destroy function.
+ */
+#ifndef NDHSS_H
+#define NDHSS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    NDHSS_OK = 0,
+    NDHSS_ERR_INVALID_ARG = 1,   /* bad size, NULL pointer, inconsistent input        */
+    NDHSS_ERR_OOM = 2,           /* device or host allocation failed                    */
+    NDHSS_ERR_SINGULAR = 3,      /* exact zero pivot in some A_ii (node in message)     */
+    NDHSS_ERR_RANK_CAP = 4,      /* HSS compression hit rank_cap before eps_hss         */
+    NDHSS_ERR_NOT_CONVERGED = 5, /* GMRES stopped at maxit above tolerance (x is valid) */
+    NDHSS_ERR_TIMEOUT = 6,       /* a bounded device wait gave up                       */
+    NDHSS_ERR_CUDA = 7,          /* a CUDA runtime call failed (message has the code)   */
+    NDHSS_ERR_INTERNAL = 8
+} ndhss_status;
+
+typedef enum { NDHSS_R64 = 0, NDHSS_C128 = 1 } ndhss_vtype;
+
+/* Factor storage / arithmetic.  GMRES vectors, the sparse product and the
+ * true residual are always float64 (complex128). */
+typedef enum {
+    NDHSS_FP64 = 0,      /* fronts in float64 / complex128, FP64 arithmetic           */
+    NDHSS_FP32 = 1,      /* fronts in float32 / complex64, FP32 arithmetic            */
+    NDHSS_FP32_TF32 = 2  /* as FP32, front updates on TF32 tensor cores, FP32 accum.  */
+} ndhss_prec;
+
+typedef struct ndhss_tree ndhss_tree;
+typedef struct ndhss_factorization ndhss_factorization;
+
+typedef struct {
+    int32_t prec;               /* ndhss_prec                                          */
+    int32_t hss_levels;         /* compress fronts on levels <= depth - hss_levels
+                                   (4 = "4 levels above the lowest", Sec. 4);
+                                   < 0 disables compression (exact factorization)     */
+    double eps_hss;             /* relative HSS tolerance (Eq. 2.7), e.g. 1e-6        */
+    int32_t beta;               /* HSS leaf block size (Eq. 2.1), e.g. 64              */
+    int32_t k0;                 /* initial rank guess of Alg. A.1, e.g. 32             */
+    int32_t r;                  /* rank step / estimator samples of Alg. A.1, e.g. 16  */
+    int32_t rank_cap;           /* largest HSS rank allowed, e.g. 512                  */
+    int32_t panel;              /* pivot block width of the front kernels, 0 = auto    */
+    uint64_t seed;              /* random sampling seed                                */
+} ndhss_factor_opts;
+
+typedef struct {
+    int32_t restart;            /* Krylov basis length per cycle, e.g. 30              */
+    int32_t maxit;              /* total Arnoldi steps allowed, e.g. 300               */
+    double tol;                 /* relative residual target, e.g. 1e-8                 */
+} ndhss_gmres_opts;
+
+typedef struct {
+    int32_t iters;              /* Arnoldi steps (products with P^{-1} A)              */
+    int32_t cycles;             /* restart cycles                                      */
+    int32_t converged;          /* 1 when ||b - A x|| / ||b|| <= tol                   */
+    int32_t pad;
+    double true_relres;         /* final float64 ||b - A x|| / ||b||                   */
+    double precond_relres;      /* last ||P^{-1}(b - A x)|| / ||P^{-1} b|| estimate    */
+} ndhss_gmres_stats;
+
+typedef struct {
+    int64_t n;
+    int32_t nnodes, depth;
+    int64_t front_elems;        /* sum over nodes of m^2 (dense front storage)        */
+    int64_t apply_bytes;        /* bytes of factor data one apply reads                */
+    int64_t factor_bytes;       /* device bytes held by the factor                     */
+    double factor_ms;           /* device time of the last ndhss_factor (CUDA events)  */
+    int32_t kmax;               /* largest rank of any compressed block (0 if none)    */
+    int32_t prec;
+} ndhss_factor_stats;
+
+/* Library version string (static storage). */
+const char* ndhss_version(void);
+
+/* Message of the last failed call on this thread (static per-thread storage). */
+const char* ndhss_last_error(void);
+
+/*
+ * ndhss_build_tree -- box nested dissection and elimination tree
+ * (Def. 3.1; boxes of Fig. 3; Sec. 3.1 for I^sigma and B^sigma; Sec. 3.3 and
+ * Fig. 4 for the numbering inside the fronts).  Host only, integer only,
+ * deterministic.
+ *   n          number of DOFs (>= 1)
+ *   coords     host int32 [n][2], integer lattice coordinate of every DOF
+ *              (DOFs of one DG element share one coordinate)
+ *   rowptr,col host int32 CSR pattern of A (n+1, nnz); explicit zeros count
+ *   leaf_size  a box with at most leaf_size DOFs is a leaf (e.g. 64)
+ *   out        receives a new tree handle
+ * Inputs are copied.  Returns INVALID_ARG for bad sizes or indices.
+ */
+ndhss_status ndhss_build_tree(int32_t n, const int32_t* coords, const int32_t* rowptr,
+                              const int32_t* col, int32_t leaf_size, ndhss_tree** out);
+
+/* Sizes of the arrays ndhss_tree_export fills (any pointer may be NULL). */
+ndhss_status ndhss_tree_sizes(const ndhss_tree* t, int32_t* nnodes, int32_t* depth,
+                              int64_t* nnz, int64_t* sum_mb);
+
+/*
+ * ndhss_tree_export -- copy the tree into caller-owned host arrays, for
+ * inspection and bit-exact comparison (any pointer may be NULL to skip):
+ *   perm      int32 [n]           new -> old numbering (I^sigma in post-order)
+ *   node_info int32 [nnodes][14]  level, parent, child0, child1, i_off, m_i,
+ *                                 b_off, m_b, x0, x1, y0, y1, axis, cut
+ *   blist     int32 [sum_mb]      B^sigma in new numbering, node after node
+ *   emap      int32 [sum_mb]      position of each B^kappa row in the parent front
+ *   e_off     int32 [nnodes+1]    entry ranges per node
+ *   e_row, e_col, e_idx int32 [nnz]  front-local row/column and CSR position of
+ *                                 every entry of A, grouped by the node whose
+ *                                 front receives it (Eq. 3.2 / Eq. 3.4)
+ */
+ndhss_status ndhss_tree_export(const ndhss_tree* t, int32_t* perm, int32_t* node_info,
+                               int32_t* blist, int32_t* emap, int32_t* e_off, int32_t* e_row,
+                               int32_t* e_col, int32_t* e_idx);
+
+void ndhss_tree_destroy(ndhss_tree* t);
+
+/*
+ * ndhss_factor -- approximate factorization P = L D R (Alg. 3.4): fronts
+ * assembled bottom-up level by level (Eq. 3.2, Eq. 3.4), interior blocks
+ * eliminated with partial pivoting restricted to I^sigma, giving
+ * (A_ii)^{-1}, R = -(A_ii)^{-1} A_ib (Eq. 3.3b), L = -A_bi (A_ii)^{-1}
+ * (Eq. 3.3a) and the Schur complement S (Eq. 3.5) passed to the parent.
+ *   t          tree from ndhss_build_tree (not modified, must outlive nothing)
+ *   vtype      value type of A
+ *   d_rowptr, d_col, d_vals  device CSR of A in the original numbering; only
+ *              read during the call
+ *   opts       factor options (NULL = FP64, no compression)
+ *   stream     stream for all device work; synchronised before returning
+ *   out        receives a new factor handle holding device memory
+ * Errors: SINGULAR (node reported), OOM, CUDA, INVALID_ARG.
+ */
+ndhss_status ndhss_factor(const ndhss_tree* t, int32_t vtype, const int32_t* d_rowptr,
+                          const int32_t* d_col, const void* d_vals, const ndhss_factor_opts* opts,
+                          void* stream, ndhss_factorization** out);
+
+ndhss_status ndhss_factor_stats_get(const ndhss_factorization* f, ndhss_factor_stats* st);
+
+/*
+ * ndhss_factor_get_block -- copy one factor block of node `node` to host
+ * memory as float64/complex128 column-major with leading dimension ld:
+ *   which 0: (A_ii)^{-1}   m_i x m_i        which 1: R   m_i x m_b (Eq. 3.3b)
+ *   which 2: L   m_b x m_i (Eq. 3.3a)       which 3: S   m_b x m_b (Eq. 3.5)
+ * Synchronises the factor's stream.  INVALID_ARG for a bad node, block or ld.
+ */
+ndhss_status ndhss_factor_get_block(const ndhss_factorization* f, int32_t node, int32_t which,
+                                    void* host_out, int64_t ld);
+
+void ndhss_factor_destroy(ndhss_factorization* f);
+
+/*
+ * ndhss_apply -- y = P^{-1} x by Algorithm 3.1: bottom-up b(B) += L b(I),
+ * the block-diagonal solve b(I) <- (A_ii)^{-1} b(I) at all nodes at once,
+ * top-down b(I) += R b(B).
+ *   nrhs      number of right-hand sides (columns)
+ *   x, y      float64/complex128 (per the factor's vtype) n x nrhs,
+ *             column-major with leading dimensions ldx, ldy >= n, ORIGINAL
+ *             numbering; device or host pointers (host buffers are staged
+ *             through device memory inside the call).  x and y may alias.
+ * Stream-ordered; synchronises only when x or y is host memory.
+ */
+ndhss_status ndhss_apply(const ndhss_factorization* f, int32_t nrhs, const void* x, int64_t ldx,
+                         void* y, int64_t ldy, void* stream);
+
+/*
+ * ndhss_spmv -- y = A x for a CSR matrix in float64 / complex128 (the
+ * matrix-vector product x -> A x of Sec. 2.3 and of every Krylov step).
+ * All pointers are device pointers; n rows; stream-ordered.
+ */
+ndhss_status ndhss_spmv(int32_t n, int32_t vtype, const int32_t* d_rowptr, const int32_t* d_col,
+                        const void* d_vals, const void* d_x, void* d_y, void* stream);
+
+/*
+ * ndhss_gmres -- solve A x = b with restarted GMRES on P^{-1} A x = P^{-1} b
+ * (Eq. 1.2, Sec. 4): x0 = 0, Arnoldi by classical Gram-Schmidt applied
+ * twice in float64, complex Givens rotations, a cycle ends when
+ * ||P^{-1} r|| <= tol ||P^{-1} b|| or after `restart` steps; a solve is
+ * converged only when the float64 true residual ||b - A x|| / ||b|| <= tol,
+ * checked after every cycle (restarts act as iterative refinement).
+ *   f         factor (the preconditioner)
+ *   d_rowptr, d_col, d_vals  device CSR of A (original numbering, vtype of f)
+ *   nrhs      right-hand sides, solved one after another
+ *   b, x      n x nrhs column-major (ldb, ldx >= n), device or host pointers
+ *   opts      NULL = restart 30, maxit 300, tol 1e-8
+ *   stats     host array of nrhs entries (may be NULL)
+ * Returns NOT_CONVERGED if any right-hand side missed tol (x still written).
+ * Synchronises the stream once per Arnoldi step (to read the residual).
+ */
+ndhss_status ndhss_gmres(const ndhss_factorization* f, const int32_t* d_rowptr, const int32_t* d_col,
+                         const void* d_vals, int32_t nrhs, const void* b, int64_t ldb, void* x,
+                         int64_t ldx, const ndhss_gmres_opts* opts, ndhss_gmres_stats* stats,
+                         void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* NDHSS_H */

@@ -1,0 +1,84 @@
+// C ABI glue: version, error reporting and the tree handle.
+#include <cstdarg>
+#include <cstring>
+#include <new>
+
+#include "internal.h"
+
+namespace ndhss {
+
+static thread_local char g_err[1024] = "";
+
+ndhss_status set_error(ndhss_status code, const char* fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    std::vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+    return code;
+}
+
+void clear_error() { g_err[0] = '\0'; }
+
+}  // namespace ndhss
+
+extern "C" {
+
+const char* ndhss_version(void) { return "ndhss 0.1 (sm_103a)"; }
+
+const char* ndhss_last_error(void) { return ndhss::g_err; }
+
+ndhss_status ndhss_build_tree(int32_t n, const int32_t* coords, const int32_t* rowptr, const int32_t* col,
+                              int32_t leaf_size, ndhss_tree** out) {
+    ndhss::clear_error();
+    if (!out) return ndhss::set_error(NDHSS_ERR_INVALID_ARG, "ndhss_build_tree: out is NULL");
+    *out = nullptr;
+    auto* t = new (std::nothrow) ndhss_tree();
+    if (!t) return ndhss::set_error(NDHSS_ERR_OOM, "ndhss_build_tree: host allocation failed");
+    ndhss_status rc;
+    try {
+        rc = ndhss::build_tree_impl(n, coords, rowptr, col, leaf_size, &t->t);
+    } catch (const std::bad_alloc&) {
+        rc = ndhss::set_error(NDHSS_ERR_OOM, "ndhss_build_tree: host allocation failed");
+    } catch (...) {
+        rc = ndhss::set_error(NDHSS_ERR_INTERNAL, "ndhss_build_tree: unexpected exception");
+    }
+    if (rc != NDHSS_OK) {
+        delete t;
+        return rc;
+    }
+    *out = t;
+    return NDHSS_OK;
+}
+
+ndhss_status ndhss_tree_sizes(const ndhss_tree* t, int32_t* nnodes, int32_t* depth, int64_t* nnz, int64_t* sum_mb) {
+    ndhss::clear_error();
+    if (!t) return ndhss::set_error(NDHSS_ERR_INVALID_ARG, "ndhss_tree_sizes: NULL tree");
+    if (nnodes) *nnodes = t->t.nnodes;
+    if (depth) *depth = t->t.depth;
+    if (nnz) *nnz = t->t.nnz;
+    if (sum_mb) *sum_mb = (int64_t)t->t.blist.size();
+    return NDHSS_OK;
+}
+
+ndhss_status ndhss_tree_export(const ndhss_tree* th, int32_t* perm, int32_t* node_info, int32_t* blist, int32_t* emap,
+                               int32_t* e_off, int32_t* e_row, int32_t* e_col, int32_t* e_idx) {
+    ndhss::clear_error();
+    if (!th) return ndhss::set_error(NDHSS_ERR_INVALID_ARG, "ndhss_tree_export: NULL tree");
+    const auto& t = th->t;
+    auto cp = [](int32_t* dst, const std::vector<int32_t>& v) {
+        if (dst && !v.empty()) std::memcpy(dst, v.data(), v.size() * sizeof(int32_t));
+    };
+    cp(perm, t.perm);
+    cp(node_info, t.node_info);
+    cp(blist, t.blist);
+    cp(emap, t.emap);
+    cp(e_off, t.e_off);
+    cp(e_row, t.e_row);
+    cp(e_col, t.e_col);
+    cp(e_idx, t.e_idx);
+    return NDHSS_OK;
+}
+
+void ndhss_tree_destroy(ndhss_tree* t) { delete t; }
+
+}  // extern "C"

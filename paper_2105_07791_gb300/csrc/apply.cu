@@ -1,0 +1,224 @@
+// y = P^{-1} x by Algorithm 3.1 on the device.
+//
+//   gather/cast   y = x(perm) converted to the factor precision
+//   up-sweep      levels bottom-up:  y(B^s) += L^s y(I^s)          (L = -BL P)
+//   diagonal      all nodes at once: z(I^s) = A_ii^{-1} y(I^s)     ("fully in parallel")
+//   down-sweep    levels top-down:   z(I^s) += R^s z(B^s)
+//   scatter/cast  out(perm) = z converted back to float64
+//
+// Work is split into tasks of APPLY_ROWS output rows of one node; the tasks
+// of a level (or of the diagonal step) form one launch.  Inside a task the
+// 256 threads hold 64 rows x 4 column slices, so each column of a stored
+// block is read as a contiguous, coalesced segment; the partial sums of the
+// four slices are added in shared memory.  The whole factor is streamed
+// once per apply (the diagonal blocks once, the off-diagonal blocks twice).
+#include "factor.cuh"
+
+namespace ndhss {
+namespace {
+
+constexpr int AT = 256;
+constexpr int SLICES = AT / APPLY_ROWS;
+
+__device__ __forceinline__ int nf(const int32_t* node, int s, int f) { return node[s * NODE_NF + f]; }
+
+template <typename T, typename V>
+__global__ void gather_cast_kernel(int n, const int32_t* __restrict__ perm, const V* __restrict__ x, T* __restrict__ y) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) y[i] = from_val<T>(x[perm[i]]);
+}
+
+template <typename T, typename V>
+__global__ void scatter_cast_kernel(int n, const int32_t* __restrict__ perm, const T* __restrict__ z, V* __restrict__ out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[perm[i]] = to_val(z[i]);
+}
+
+template <typename T>
+__device__ __forceinline__ T slice_sum(T acc, T (*red)[APPLY_ROWS], int rl, int sl) {
+    red[sl][rl] = acc;
+    __syncthreads();
+    T sum = zero<T>();
+    if (sl == 0)
+        for (int q = 0; q < SLICES; ++q) sum += red[q][rl];
+    return sum;
+}
+
+// y(B^s) -= BL y(I^s)(sigma)   (= L^s y(I^s), Eq. 3.3a)
+template <typename T>
+__global__ void __launch_bounds__(AT)
+upsweep_kernel(const int32_t* __restrict__ tasks, const int32_t* __restrict__ node, const int64_t* __restrict__ foff,
+               const int32_t* __restrict__ blist, const int32_t* __restrict__ sigma, const T* __restrict__ front,
+               T* __restrict__ y) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ T red[SLICES][APPLY_ROWS];
+    T* ys = reinterpret_cast<T*>(smem_raw);
+    const int s = tasks[2 * blockIdx.x], j0 = tasks[2 * blockIdx.x + 1];
+    const int m_i = nf(node, s, 5), m_b = nf(node, s, 7), i_off = nf(node, s, 4), b_off = nf(node, s, 6);
+    const int64_t m = (int64_t)m_i + m_b;
+    for (int c = threadIdx.x; c < m_i; c += AT) ys[c] = y[i_off + sigma[i_off + c]];
+    __syncthreads();
+    const int rl = threadIdx.x % APPLY_ROWS, sl = threadIdx.x / APPLY_ROWS;
+    const int j = j0 + rl;
+    const T* F = front + foff[s] + m_i;
+    T acc = zero<T>();
+    if (j < m_b)
+        for (int c = sl; c < m_i; c += SLICES) acc = fmac(F[c * m + j], ys[c], acc);
+    const T sum = slice_sum(acc, red, rl, sl);
+    if (sl == 0 && j < m_b) {
+        const int g = blist[b_off + j];
+        y[g] = y[g] - sum;
+    }
+}
+
+// z(I^s) = X y(I^s)(sigma)   (= A_ii^{-1} y(I^s))
+template <typename T>
+__global__ void __launch_bounds__(AT)
+diag_kernel(const int32_t* __restrict__ tasks, const int32_t* __restrict__ node, const int64_t* __restrict__ foff,
+            const int32_t* __restrict__ sigma, const T* __restrict__ front, const T* __restrict__ y, T* __restrict__ z) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ T red[SLICES][APPLY_ROWS];
+    T* ys = reinterpret_cast<T*>(smem_raw);
+    const int s = tasks[2 * blockIdx.x], i0 = tasks[2 * blockIdx.x + 1];
+    const int m_i = nf(node, s, 5), i_off = nf(node, s, 4);
+    const int64_t m = (int64_t)m_i + nf(node, s, 7);
+    for (int c = threadIdx.x; c < m_i; c += AT) ys[c] = y[i_off + sigma[i_off + c]];
+    __syncthreads();
+    const int rl = threadIdx.x % APPLY_ROWS, sl = threadIdx.x / APPLY_ROWS;
+    const int i = i0 + rl;
+    const T* F = front + foff[s];
+    T acc = zero<T>();
+    if (i < m_i)
+        for (int c = sl; c < m_i; c += SLICES) acc = fmac(F[c * m + i], ys[c], acc);
+    const T sum = slice_sum(acc, red, rl, sl);
+    if (sl == 0 && i < m_i) z[i_off + i] = sum;
+}
+
+// z(I^s) += R z(B^s)   (Eq. 3.3b)
+template <typename T>
+__global__ void __launch_bounds__(AT)
+downsweep_kernel(const int32_t* __restrict__ tasks, const int32_t* __restrict__ node, const int64_t* __restrict__ foff,
+                 const int32_t* __restrict__ blist, const T* __restrict__ front, T* __restrict__ z) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ T red[SLICES][APPLY_ROWS];
+    T* zb = reinterpret_cast<T*>(smem_raw);
+    const int s = tasks[2 * blockIdx.x], i0 = tasks[2 * blockIdx.x + 1];
+    const int m_i = nf(node, s, 5), m_b = nf(node, s, 7), i_off = nf(node, s, 4), b_off = nf(node, s, 6);
+    const int64_t m = (int64_t)m_i + m_b;
+    for (int j = threadIdx.x; j < m_b; j += AT) zb[j] = z[blist[b_off + j]];
+    __syncthreads();
+    const int rl = threadIdx.x % APPLY_ROWS, sl = threadIdx.x / APPLY_ROWS;
+    const int i = i0 + rl;
+    const T* F = front + foff[s] + (int64_t)m_i * m;
+    T acc = zero<T>();
+    if (i < m_i)
+        for (int j = sl; j < m_b; j += SLICES) acc = fmac(F[j * m + i], zb[j], acc);
+    const T sum = slice_sum(acc, red, rl, sl);
+    if (sl == 0 && i < m_i) z[i_off + i] = z[i_off + i] + sum;
+}
+
+template <typename T, typename V>
+ndhss_status apply_run(const FactorData& F, int32_t nrhs, const V* x, int64_t ldx, V* y, int64_t ldy, T* w0, T* w1,
+                       cudaStream_t st) {
+    const T* front = static_cast<const T*>(F.d_front);
+    const int nb = (F.n + 255) / 256;
+    const size_t smem_i = (size_t)std::max(F.max_mi, 1) * sizeof(T);
+    const size_t smem_b = (size_t)std::max(F.max_mb, 1) * sizeof(T);
+    if (smem_i > 48 * 1024) {
+        NDHSS_CUDA_TRY(cudaFuncSetAttribute(upsweep_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_i));
+        NDHSS_CUDA_TRY(cudaFuncSetAttribute(diag_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_i));
+    }
+    if (smem_b > 48 * 1024)
+        NDHSS_CUDA_TRY(cudaFuncSetAttribute(downsweep_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_b));
+    for (int r = 0; r < nrhs; ++r) {
+        gather_cast_kernel<T, V><<<nb, 256, 0, st>>>(F.n, F.d_perm, x + r * ldx, w0);
+        NDHSS_LAUNCH_CHECK("gather_cast_kernel");
+        for (int l = F.depth; l >= 0; --l) {
+            if (F.up_cnt[l] == 0) continue;
+            upsweep_kernel<T><<<(unsigned)F.up_cnt[l], AT, smem_i, st>>>(F.d_tasks + 2 * F.up_off[l], F.d_node, F.d_foff,
+                                                                         F.d_blist, F.d_sigma, front, w0);
+            NDHSS_LAUNCH_CHECK("upsweep_kernel");
+        }
+        if (F.diag_cnt > 0) {
+            diag_kernel<T><<<(unsigned)F.diag_cnt, AT, smem_i, st>>>(F.d_tasks + 2 * F.diag_off, F.d_node, F.d_foff,
+                                                                     F.d_sigma, front, w0, w1);
+            NDHSS_LAUNCH_CHECK("diag_kernel");
+        }
+        for (int l = 0; l <= F.depth; ++l) {
+            if (F.dn_cnt[l] == 0) continue;
+            downsweep_kernel<T><<<(unsigned)F.dn_cnt[l], AT, smem_b, st>>>(F.d_tasks + 2 * F.dn_off[l], F.d_node, F.d_foff,
+                                                                           F.d_blist, front, w1);
+            NDHSS_LAUNCH_CHECK("downsweep_kernel");
+        }
+        scatter_cast_kernel<T, V><<<nb, 256, 0, st>>>(F.n, F.d_perm, w1, y + r * ldy);
+        NDHSS_LAUNCH_CHECK("scatter_cast_kernel");
+    }
+    return NDHSS_OK;
+}
+
+}  // namespace
+
+size_t apply_work_bytes(const FactorData& F) { return 2 * (size_t)F.n * F.esize + 256; }
+
+ndhss_status apply_device(const FactorData& F, int32_t nrhs, const void* d_x, int64_t ldx, void* d_y, int64_t ldy,
+                          void* d_work, cudaStream_t st) {
+    const bool cplx = F.vtype == NDHSS_C128;
+    unsigned char* w = static_cast<unsigned char*>(d_work);
+    const size_t half = ((size_t)F.n * F.esize + 255) / 256 * 256;
+    if (!cplx && F.prec == NDHSS_FP64)
+        return apply_run<double, double>(F, nrhs, (const double*)d_x, ldx, (double*)d_y, ldy, (double*)w, (double*)(w + half), st);
+    if (!cplx)
+        return apply_run<float, double>(F, nrhs, (const double*)d_x, ldx, (double*)d_y, ldy, (float*)w, (float*)(w + half), st);
+    if (F.prec == NDHSS_FP64)
+        return apply_run<c128, c128>(F, nrhs, (const c128*)d_x, ldx, (c128*)d_y, ldy, (c128*)w, (c128*)(w + half), st);
+    return apply_run<c64, c128>(F, nrhs, (const c128*)d_x, ldx, (c128*)d_y, ldy, (c64*)w, (c64*)(w + half), st);
+}
+
+}  // namespace ndhss
+
+extern "C" ndhss_status ndhss_apply(const ndhss_factorization* fh, int32_t nrhs, const void* x, int64_t ldx, void* y,
+                                    int64_t ldy, void* stream) {
+    using namespace ndhss;
+    clear_error();
+    if (!fh || !x || !y || nrhs < 0) return set_error(NDHSS_ERR_INVALID_ARG, "ndhss_apply: bad argument");
+    const FactorData& F = fh->f;
+    if (ldx < F.n || ldy < F.n) return set_error(NDHSS_ERR_INVALID_ARG, "ndhss_apply: leading dimension < n");
+    if (nrhs == 0) return NDHSS_OK;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const size_t vsz = F.vtype == NDHSS_C128 ? 16 : 8;
+    const bool xdev = is_device_ptr(x), ydev = is_device_ptr(y);
+    const size_t wb = apply_work_bytes(F) + (xdev ? 0 : (size_t)F.n * nrhs * vsz + 256) + (ydev ? 0 : (size_t)F.n * nrhs * vsz + 256);
+    void* work = nullptr;
+    NDHSS_CUDA_TRY(cudaMallocAsync(&work, wb, st));
+    unsigned char* p = static_cast<unsigned char*>(work) + (apply_work_bytes(F) + 255) / 256 * 256;
+    const void* dx = x;
+    void* dy = y;
+    int64_t lx = ldx, ly = ldy;
+    ndhss_status rc = NDHSS_OK;
+    if (!xdev) {
+        dx = p;
+        lx = F.n;
+        p += ((size_t)F.n * nrhs * vsz + 255) / 256 * 256;
+        for (int r = 0; r < nrhs && rc == NDHSS_OK; ++r)
+            if (cudaMemcpyAsync((unsigned char*)dx + (size_t)r * F.n * vsz, (const unsigned char*)x + (size_t)r * ldx * vsz,
+                                (size_t)F.n * vsz, cudaMemcpyHostToDevice, st) != cudaSuccess)
+                rc = set_error(NDHSS_ERR_CUDA, "ndhss_apply: host-to-device copy failed");
+    }
+    if (!ydev) {
+        dy = p;
+        ly = F.n;
+    }
+    if (rc == NDHSS_OK) rc = apply_device(F, nrhs, dx, lx, dy, ly, work, st);
+    if (rc == NDHSS_OK && !ydev) {
+        for (int r = 0; r < nrhs && rc == NDHSS_OK; ++r)
+            if (cudaMemcpyAsync((unsigned char*)y + (size_t)r * ldy * vsz, (const unsigned char*)dy + (size_t)r * F.n * vsz,
+                                (size_t)F.n * vsz, cudaMemcpyDeviceToHost, st) != cudaSuccess)
+                rc = set_error(NDHSS_ERR_CUDA, "ndhss_apply: device-to-host copy failed");
+    }
+    cudaFreeAsync(work, st);
+    if (!xdev || !ydev) {
+        if (cudaStreamSynchronize(st) != cudaSuccess && rc == NDHSS_OK)
+            rc = set_error(NDHSS_ERR_CUDA, "ndhss_apply: stream synchronisation failed");
+    }
+    return rc;
+}

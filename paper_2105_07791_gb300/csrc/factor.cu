@@ -1,0 +1,768 @@
+// Front factorization (Sec. 3.1, Eq. 3.2 - 3.5; Alg. 3.4 below the
+// switching level), level by level from the leaves up.
+//
+// Every level is one batch: all its fronts are assembled by the extend-add
+// of the children's Schur complements plus the sparse cross blocks of A
+// (Eq. 3.4), then their first m_i unknowns are eliminated by a blocked,
+// in-place Gauss-Jordan sweep with partial pivoting inside A_ii.  After the
+// sweep a front holds A_ii^{-1} (column-permuted), R = -A_ii^{-1} A_ib,
+// -L (column-permuted) and S = A_bb - A_bi A_ii^{-1} A_ib, which is what the
+// apply (Alg. 3.1) and the parent's assembly read.
+//
+// One pivot block of width kb costs three launches per level:
+//   panel_factor  one CTA per front: LU with partial pivoting of the
+//                 candidate rows [k0, m_i) of the kb panel columns, held in
+//                 shared memory; emits the row interchanges and
+//                 Ainv = (A_PP)^{-1}                       (kb x kb)
+//   panel_prep    applies the interchanges to every column, packs the
+//                 column panel C (pivot rows replaced by identity rows) and
+//                 Z = [Ainv | -Ainv * M(P, others)]
+//   gemm_update   M = beta .* M + C * Z, beta = 0 on pivot rows / columns,
+//                 i.e. the rank-kb Gauss-Jordan update of the whole front.
+#include <algorithm>
+#include <climits>
+#include <cmath>
+
+#include "factor.cuh"
+
+namespace ndhss {
+namespace {
+
+constexpr int KBMAX = 32;
+constexpr int PANEL_THREADS = 512;
+constexpr int PREP_WARPS = 8;
+constexpr int GT = 64;          // gemm tile
+constexpr int GK = 16;          // gemm k chunk
+constexpr size_t PANEL_SMEM_BUDGET = 200 * 1024;
+
+__device__ __forceinline__ int nf(const int32_t* node, int s, int f) { return node[s * NODE_NF + f]; }
+
+template <typename T> __device__ __forceinline__ T shfl_idx(T v, int src);
+template <> __device__ __forceinline__ double shfl_idx<double>(double v, int src) { return __shfl_sync(0xffffffffu, v, src); }
+template <> __device__ __forceinline__ float shfl_idx<float>(float v, int src) { return __shfl_sync(0xffffffffu, v, src); }
+template <> __device__ __forceinline__ c128 shfl_idx<c128>(c128 v, int src) {
+    return {__shfl_sync(0xffffffffu, v.x, src), __shfl_sync(0xffffffffu, v.y, src)};
+}
+template <> __device__ __forceinline__ c64 shfl_idx<c64>(c64 v, int src) {
+    return {__shfl_sync(0xffffffffu, v.x, src), __shfl_sync(0xffffffffu, v.y, src)};
+}
+
+// ---------------------------------------------------------------- assembly
+// F = blockdiag(S^mu, S^nu) scattered to the parent order of Eq. 3.4 (zero
+// where the row and column come from different children).  fsrc[pos] =
+// (child << 30) | row of that child's S.
+template <typename T>
+__global__ void assemble_kernel(const int32_t* __restrict__ lev, const int32_t* __restrict__ node,
+                                const int64_t* __restrict__ foff, const int32_t* __restrict__ fsrc,
+                                const int64_t* __restrict__ poff, T* __restrict__ front) {
+    const int s = lev[blockIdx.y];
+    const int64_t m = nf(node, s, 5) + nf(node, s, 7);
+    T* F = front + foff[s];
+    const int c0 = nf(node, s, 2);
+    if (c0 < 0) {
+        for (int64_t c = blockIdx.x; c < m; c += gridDim.x)
+            for (int64_t r = threadIdx.x; r < m; r += blockDim.x) F[c * m + r] = zero<T>();
+        return;
+    }
+    const int ch[2] = {c0, nf(node, s, 3)};
+    const T* CF[2];
+    int64_t cm[2], cmi[2];
+    for (int w = 0; w < 2; ++w) {
+        cmi[w] = nf(node, ch[w], 5);
+        cm[w] = cmi[w] + nf(node, ch[w], 7);
+        CF[w] = front + foff[ch[w]];
+    }
+    const int32_t* src = fsrc + poff[s];
+    for (int64_t c = blockIdx.x; c < m; c += gridDim.x) {
+        const int sc = src[c];
+        const int wc = sc >> 30;
+        const int64_t lc = sc & 0x3fffffff;
+        const T* colS = CF[wc] + (cmi[wc] + lc) * cm[wc] + cmi[wc];
+        for (int64_t r = threadIdx.x; r < m; r += blockDim.x) {
+            const int sr = src[r];
+            T v = zero<T>();
+            if ((sr >> 30) == wc) v = colS[sr & 0x3fffffff];
+            F[c * m + r] = v;
+        }
+    }
+}
+
+// Sparse entries of A that enter this front (Eq. 3.2 for leaves, the A~
+// blocks of Eq. 3.4 otherwise); each front position receives at most one.
+template <typename T, typename V>
+__global__ void scatter_entries_kernel(const int32_t* __restrict__ lev, const int32_t* __restrict__ node,
+                                       const int64_t* __restrict__ foff, const int32_t* __restrict__ e_off,
+                                       const int32_t* __restrict__ e_row, const int32_t* __restrict__ e_col,
+                                       const int32_t* __restrict__ e_idx, const V* __restrict__ vals,
+                                       T* __restrict__ front) {
+    const int s = lev[blockIdx.x];
+    const int64_t m = nf(node, s, 5) + nf(node, s, 7);
+    T* F = front + foff[s];
+    for (int e = e_off[s] + threadIdx.x; e < e_off[s + 1]; e += blockDim.x)
+        F[(int64_t)e_col[e] * m + e_row[e]] += from_val<T>(vals[e_idx[e]]);
+}
+
+// ---------------------------------------------------------------- panel
+template <typename T>
+__global__ void __launch_bounds__(PANEL_THREADS)
+panel_factor_kernel(const int32_t* __restrict__ lev, const int32_t* __restrict__ node,
+                    const int64_t* __restrict__ foff, const T* __restrict__ front, int32_t* __restrict__ ipiv,
+                    T* __restrict__ ainv_buf, int k0, int kb, DevStatus* status) {
+    using real = typename Tr<T>::real;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ int s_piv[KBMAX];
+    __shared__ real s_val[32];
+    __shared__ int s_idx[32];
+    const int s = lev[blockIdx.x];
+    const int m_i = nf(node, s, 5);
+    if (k0 >= m_i) return;
+    const int64_t m = m_i + nf(node, s, 7);
+    const int kbp = min(kb, m_i - k0);
+    const int mc = m_i - k0;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
+    T* P = reinterpret_cast<T*>(smem_raw);       // mc x kbp, ld mc
+    const T* F = front + foff[s];
+    for (int idx = tid; idx < mc * kbp; idx += blockDim.x) {
+        const int r = idx % mc, c = idx / mc;
+        P[idx] = F[(int64_t)(k0 + c) * m + k0 + r];
+    }
+    __syncthreads();
+    for (int c = 0; c < kbp; ++c) {
+        real best = real(-1);
+        int bi = INT_MAX;
+        for (int r = c + tid; r < mc; r += blockDim.x) {
+            const real v = abs1(P[c * mc + r]);
+            if (v > best) { best = v; bi = r; }
+        }
+        for (int off = 16; off; off >>= 1) {
+            const real ov = __shfl_down_sync(0xffffffffu, best, off);
+            const int oi = __shfl_down_sync(0xffffffffu, bi, off);
+            if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
+        }
+        if (lane == 0) { s_val[warp] = best; s_idx[warp] = bi; }
+        __syncthreads();
+        if (warp == 0) {
+            best = lane < nwarps ? s_val[lane] : real(-1);
+            bi = lane < nwarps ? s_idx[lane] : INT_MAX;
+            for (int off = 16; off; off >>= 1) {
+                const real ov = __shfl_down_sync(0xffffffffu, best, off);
+                const int oi = __shfl_down_sync(0xffffffffu, bi, off);
+                if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
+            }
+            if (lane == 0) s_piv[c] = (bi == INT_MAX) ? c : bi;   // all-NaN column: keep the diagonal
+        }
+        __syncthreads();
+        const int p = s_piv[c];
+        if (p != c) {
+            for (int cc = tid; cc < kbp; cc += blockDim.x) {
+                const T t = P[cc * mc + c];
+                P[cc * mc + c] = P[cc * mc + p];
+                P[cc * mc + p] = t;
+            }
+        }
+        __syncthreads();
+        T piv = P[c * mc + c];
+        if (!(abs1(piv) > real(0))) {     // exact zero (or NaN) pivot
+            piv = one<T>();
+            if (tid == 0) {
+                P[c * mc + c] = piv;
+                if (atomicCAS(&status->code, 0, (int)NDHSS_ERR_SINGULAR) == 0) status->node = s;
+            }
+        }
+        const T pinv = recip(piv);
+        for (int r = c + 1 + tid; r < mc; r += blockDim.x) {
+            const T l = P[c * mc + r] * pinv;
+            P[c * mc + r] = l;
+            for (int cc = c + 1; cc < kbp; ++cc) P[cc * mc + r] = fmac(-l, P[cc * mc + c], P[cc * mc + r]);
+        }
+        __syncthreads();
+    }
+    const int i_off = nf(node, s, 4);
+    if (tid < kbp) ipiv[i_off + k0 + tid] = k0 + s_piv[tid];
+    // Ainv = (L U)^{-1} of the kbp x kbp pivot block: column j by thread j
+    T* Ai = ainv_buf + (size_t)blockIdx.x * KBMAX * KBMAX;
+    if (tid < kbp) {
+        const int j = tid;
+        T y[KBMAX];
+#pragma unroll
+        for (int i = 0; i < KBMAX; ++i) {
+            if (i < kbp) {
+                T acc = (i == j) ? one<T>() : zero<T>();
+                for (int l = 0; l < i; ++l) acc = fmac(-P[l * mc + i], y[l], acc);
+                y[i] = acc;
+            }
+        }
+#pragma unroll
+        for (int i = KBMAX - 1; i >= 0; --i) {
+            if (i < kbp) {
+                T acc = y[i];
+                for (int l = i + 1; l < kbp; ++l) acc = fmac(-P[l * mc + i], y[l], acc);
+                y[i] = acc * recip(P[i * mc + i]);
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < KBMAX; ++i)
+            if (i < kbp) Ai[j * KBMAX + i] = y[i];
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(PREP_WARPS * 32)
+panel_prep_kernel(const int32_t* __restrict__ lev, const int32_t* __restrict__ node,
+                  const int64_t* __restrict__ foff, T* __restrict__ front, const int32_t* __restrict__ ipiv,
+                  const T* __restrict__ ainv_buf, T* __restrict__ cbuf, T* __restrict__ zbuf,
+                  const int64_t* __restrict__ woff, int k0, int kb) {
+    __shared__ T s_ai[KBMAX * KBMAX];
+    __shared__ int s_rows[2 * KBMAX], s_org[2 * KBMAX];
+    __shared__ int s_na;
+    const int li = blockIdx.y;
+    const int s = lev[li];
+    const int m_i = nf(node, s, 5);
+    if (k0 >= m_i) return;
+    const int64_t m = m_i + nf(node, s, 7);
+    const int kbp = min(kb, m_i - k0);
+    const int i_off = nf(node, s, 4);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const T* Ai = ainv_buf + (size_t)li * KBMAX * KBMAX;
+    for (int idx = tid; idx < KBMAX * KBMAX; idx += blockDim.x) s_ai[idx] = Ai[idx];
+    if (tid == 0) {
+        // net effect of the interchange sequence on the (at most 2 kb) rows it touches
+        int na = 0;
+        for (int c = 0; c < kbp; ++c) {
+            const int rr[2] = {k0 + c, ipiv[i_off + k0 + c]};
+            for (int q = 0; q < 2; ++q) {
+                int a = 0;
+                while (a < na && s_rows[a] != rr[q]) ++a;
+                if (a == na) { s_rows[na] = rr[q]; s_org[na] = rr[q]; ++na; }
+            }
+        }
+        for (int c = 0; c < kbp; ++c) {
+            const int r1 = k0 + c, r2 = ipiv[i_off + k0 + c];
+            int a1 = 0, a2 = 0;
+            while (s_rows[a1] != r1) ++a1;
+            while (s_rows[a2] != r2) ++a2;
+            const int t = s_org[a1];
+            s_org[a1] = s_org[a2];
+            s_org[a2] = t;
+        }
+        s_na = na;
+    }
+    __syncthreads();
+    const int na = s_na;
+    T* F = front + foff[s];
+    T* C = cbuf + woff[li] * KBMAX;     // m x kbp, ld m
+    T* Z = zbuf + woff[li] * KBMAX;     // kbp x m, ld KBMAX
+    for (int64_t j = (int64_t)blockIdx.x * PREP_WARPS + warp; j < m; j += (int64_t)gridDim.x * PREP_WARPS) {
+        T* Fj = F + j * m;
+        T v0 = zero<T>(), v1 = zero<T>();
+        if (lane < na) v0 = Fj[s_org[lane]];
+        if (lane + 32 < na) v1 = Fj[s_org[lane + 32]];
+        __syncwarp();
+        if (lane < na) Fj[s_rows[lane]] = v0;
+        if (lane + 32 < na) Fj[s_rows[lane + 32]] = v1;
+        __syncwarp();
+        if (j >= k0 && j < k0 + kbp) {
+            const int cidx = (int)(j - k0);
+            for (int64_t i = lane; i < m; i += 32) {
+                T v = Fj[i];
+                if (i >= k0 && i < k0 + kbp) v = (i - k0 == cidx) ? one<T>() : zero<T>();
+                C[(int64_t)cidx * m + i] = v;
+            }
+            if (lane < kbp) Z[j * KBMAX + lane] = s_ai[cidx * KBMAX + lane];
+        } else {
+            const T w = lane < kbp ? Fj[k0 + lane] : zero<T>();
+            T acc = zero<T>();
+            for (int l = 0; l < kbp; ++l) acc = fmac(s_ai[l * KBMAX + (lane < kbp ? lane : 0)], shfl_idx(w, l), acc);
+            if (lane < kbp) Z[j * KBMAX + lane] = -acc;
+        }
+    }
+}
+
+// M = beta .* M + C * Z over one 64 x 64 tile (beta = 0 on pivot rows or columns).
+template <typename T>
+__global__ void __launch_bounds__(256)
+gemm_update_kernel(const int32_t* __restrict__ lev, const int32_t* __restrict__ node,
+                   const int64_t* __restrict__ foff, T* __restrict__ front, const T* __restrict__ cbuf,
+                   const T* __restrict__ zbuf, const int64_t* __restrict__ woff, int k0, int kb) {
+    __shared__ T sC[GK][GT];
+    __shared__ T sZ[GK][GT];
+    const int li = blockIdx.z;
+    const int s = lev[li];
+    const int m_i = nf(node, s, 5);
+    if (k0 >= m_i) return;
+    const int64_t m = m_i + nf(node, s, 7);
+    const int64_t i0 = (int64_t)blockIdx.x * GT, j0 = (int64_t)blockIdx.y * GT;
+    if (i0 >= m || j0 >= m) return;
+    const int kbp = min(kb, m_i - k0);
+    const T* C = cbuf + woff[li] * KBMAX;
+    const T* Z = zbuf + woff[li] * KBMAX;
+    T* F = front + foff[s];
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    T acc[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b] = zero<T>();
+    for (int kc = 0; kc < kbp; kc += GK) {
+        for (int idx = tid; idx < GK * GT; idx += 256) {
+            const int ii = idx % GT, l = idx / GT;
+            const int64_t i = i0 + ii;
+            sC[l][ii] = (kc + l < kbp && i < m) ? C[(int64_t)(kc + l) * m + i] : zero<T>();
+        }
+        for (int idx = tid; idx < GK * GT; idx += 256) {
+            const int l = idx % GK, jj = idx / GK;
+            const int64_t j = j0 + jj;
+            sZ[l][jj] = (kc + l < kbp && j < m) ? Z[j * KBMAX + kc + l] : zero<T>();
+        }
+        __syncthreads();
+#pragma unroll
+        for (int l = 0; l < GK; ++l) {
+            T av[4], bv[4];
+#pragma unroll
+            for (int a = 0; a < 4; ++a) av[a] = sC[l][tx + 16 * a];
+#pragma unroll
+            for (int b = 0; b < 4; ++b) bv[b] = sZ[l][ty + 16 * b];
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int b = 0; b < 4; ++b) acc[a][b] = fmac(av[a], bv[b], acc[a][b]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+        const int64_t j = j0 + ty + 16 * b;
+        if (j >= m) continue;
+        const bool pj = (j >= k0 && j < k0 + kbp);
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+            const int64_t i = i0 + tx + 16 * a;
+            if (i >= m) continue;
+            const bool pi = (i >= k0 && i < k0 + kbp);
+            T* dst = F + j * m + i;
+            *dst = (pi || pj) ? acc[a][b] : (*dst + acc[a][b]);
+        }
+    }
+}
+
+// sigma(j) = original row of A_ii now at row j, from the interchange record
+__global__ void finalize_sigma_kernel(const int32_t* __restrict__ lev, const int32_t* __restrict__ node,
+                                      const int32_t* __restrict__ ipiv, int32_t* __restrict__ sigma) {
+    extern __shared__ int s_a[];
+    const int s = lev[blockIdx.x];
+    const int m_i = nf(node, s, 5), i_off = nf(node, s, 4);
+    int* a = s_a;
+    int* pv = s_a + m_i;
+    for (int j = threadIdx.x; j < m_i; j += blockDim.x) { a[j] = j; pv[j] = ipiv[i_off + j]; }
+    __syncthreads();
+    if (threadIdx.x == 0)
+        for (int k = 0; k < m_i; ++k) {
+            const int p = pv[k];
+            const int t = a[k]; a[k] = a[p]; a[p] = t;
+        }
+    __syncthreads();
+    for (int j = threadIdx.x; j < m_i; j += blockDim.x) sigma[i_off + j] = a[j];
+}
+
+int choose_kb(int64_t mc, size_t esize, int panel_opt) {
+    int kb = KBMAX;
+    while (kb > 1 && (size_t)mc * kb * esize > PANEL_SMEM_BUDGET) kb >>= 1;
+    if (panel_opt > 0) kb = std::min(kb, panel_opt);
+    return kb;
+}
+
+template <typename T>
+ndhss_status set_smem_attrs() {
+    NDHSS_CUDA_TRY(cudaFuncSetAttribute(panel_factor_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)(PANEL_SMEM_BUDGET + 1024)));
+    return NDHSS_OK;
+}
+
+struct DevBuf {
+    void* p = nullptr;
+    ~DevBuf() { if (p) cudaFree(p); }
+};
+
+template <typename U>
+ndhss_status upload(U** dst, const U* src, size_t count, int64_t* acc) {
+    *dst = nullptr;
+    size_t bytes = std::max<size_t>(count, 1) * sizeof(U);
+    if (cudaMalloc((void**)dst, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return set_error(NDHSS_ERR_OOM, "device allocation of %zu bytes failed", bytes);
+    }
+    *acc += (int64_t)bytes;
+    if (count) NDHSS_CUDA_TRY(cudaMemcpy(*dst, src, count * sizeof(U), cudaMemcpyHostToDevice));
+    return NDHSS_OK;
+}
+
+template <typename T, typename V>
+ndhss_status factor_run(FactorData& F, const Tree& t, const V* d_vals, const int32_t* d_eoff,
+                        const int32_t* d_erow, const int32_t* d_ecol, const int32_t* d_eidx,
+                        const int32_t* d_fsrc, const int64_t* d_poff, const int32_t* d_lev,
+                        const std::vector<int64_t>& lev_off, const int64_t* d_woff, T* d_cbuf, T* d_zbuf,
+                        T* d_ainv, DevStatus* d_status, int panel_opt, cudaStream_t st) {
+    ndhss_status rc = set_smem_attrs<T>();
+    if (rc != NDHSS_OK) return rc;
+    T* front = static_cast<T*>(F.d_front);
+    for (int l = F.depth; l >= 0; --l) {
+        const auto& nodes = F.levels[l];
+        const int L = (int)nodes.size();
+        if (L == 0) continue;
+        const int32_t* lev = d_lev + lev_off[l];
+        const int64_t* woff = d_woff + lev_off[l];
+        int64_t mmax = 0, mimax = 0;
+        for (int s : nodes) {
+            mmax = std::max<int64_t>(mmax, F.m_i(s) + F.m_b(s));
+            mimax = std::max<int64_t>(mimax, F.m_i(s));
+        }
+        if (mmax == 0) continue;
+        const int agx = (int)std::min<int64_t>(mmax, 256);
+        assemble_kernel<T><<<dim3(agx, L), 256, 0, st>>>(lev, F.d_node, F.d_foff, d_fsrc, d_poff, front);
+        NDHSS_LAUNCH_CHECK("assemble_kernel");
+        scatter_entries_kernel<T, V><<<L, 256, 0, st>>>(lev, F.d_node, F.d_foff, d_eoff, d_erow, d_ecol, d_eidx,
+                                                        d_vals, front);
+        NDHSS_LAUNCH_CHECK("scatter_entries_kernel");
+        const int gt = (int)((mmax + GT - 1) / GT);
+        const int pgx = (int)std::min<int64_t>((mmax + PREP_WARPS - 1) / PREP_WARPS, 1024);
+        for (int64_t k0 = 0; k0 < mimax;) {
+            const int kb = choose_kb(mimax - k0, sizeof(T), panel_opt);
+            const size_t smem = (size_t)(mimax - k0) * kb * sizeof(T);
+            if (smem > PANEL_SMEM_BUDGET)
+                return set_error(NDHSS_ERR_INVALID_ARG, "front with %lld interior unknowns exceeds the panel kernel's shared memory",
+                                 (long long)(mimax - k0));
+            panel_factor_kernel<T><<<L, PANEL_THREADS, smem, st>>>(lev, F.d_node, F.d_foff, front, F.d_ipiv, d_ainv,
+                                                                   (int)k0, kb, d_status);
+            NDHSS_LAUNCH_CHECK("panel_factor_kernel");
+            panel_prep_kernel<T><<<dim3(pgx, L), PREP_WARPS * 32, 0, st>>>(lev, F.d_node, F.d_foff, front, F.d_ipiv,
+                                                                          d_ainv, d_cbuf, d_zbuf, woff, (int)k0, kb);
+            NDHSS_LAUNCH_CHECK("panel_prep_kernel");
+            gemm_update_kernel<T><<<dim3(gt, gt, L), 256, 0, st>>>(lev, F.d_node, F.d_foff, front, d_cbuf, d_zbuf, woff,
+                                                                 (int)k0, kb);
+            NDHSS_LAUNCH_CHECK("gemm_update_kernel");
+            k0 += kb;
+        }
+        if (mimax > 0) {
+            finalize_sigma_kernel<<<L, 256, (size_t)mimax * 2 * sizeof(int), st>>>(lev, F.d_node, F.d_ipiv, F.d_sigma);
+            NDHSS_LAUNCH_CHECK("finalize_sigma_kernel");
+        }
+    }
+    return NDHSS_OK;
+}
+
+}  // namespace
+
+// --------------------------------------------------------------------------
+// public entry points
+// --------------------------------------------------------------------------
+
+static ndhss_status factor_impl(const ndhss_tree* th, int32_t vtype, const int32_t* d_rowptr, const int32_t* d_col,
+                                const void* d_vals, const ndhss_factor_opts* opts, void* stream, ndhss_factorization** out) {
+    (void)d_rowptr;
+    (void)d_col;
+    if (!th || !d_vals || !out) return set_error(NDHSS_ERR_INVALID_ARG, "ndhss_factor: NULL argument");
+    if (vtype != NDHSS_R64 && vtype != NDHSS_C128) return set_error(NDHSS_ERR_INVALID_ARG, "ndhss_factor: bad vtype %d", vtype);
+    const Tree& t = th->t;
+    ndhss_factor_opts o{};
+    o.prec = NDHSS_FP64;
+    o.hss_levels = -1;
+    if (opts) o = *opts;
+    if (o.prec != NDHSS_FP64 && o.prec != NDHSS_FP32 && o.prec != NDHSS_FP32_TF32)
+        return set_error(NDHSS_ERR_INVALID_ARG, "ndhss_factor: bad precision %d", o.prec);
+    if (o.hss_levels >= 0)
+        return set_error(NDHSS_ERR_INVALID_ARG, "ndhss_factor: HSS compression is not available in this build");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const bool cplx = vtype == NDHSS_C128;
+    const bool fp64 = o.prec == NDHSS_FP64;
+    const size_t esize = cplx ? (fp64 ? 16 : 8) : (fp64 ? 8 : 4);
+
+    auto* h = new ndhss_factorization();
+    FactorData& F = h->f;
+    F.vtype = vtype;
+    F.prec = o.prec;
+    F.n = t.n;
+    F.nnodes = t.nnodes;
+    F.depth = t.depth;
+    F.esize = esize;
+    F.node_info = t.node_info;
+    F.levels.assign(t.depth + 1, {});
+    for (int s = 0; s < t.nnodes; ++s) F.levels[t.level(s)].push_back(s);
+    F.foff.resize(t.nnodes);
+    int64_t acc = 0, posacc = 0;
+    std::vector<int64_t> poff(t.nnodes);
+    for (int s = 0; s < t.nnodes; ++s) {
+        const int64_t m = (int64_t)t.m_i(s) + t.m_b(s);
+        F.foff[s] = acc;
+        acc += m * m;
+        poff[s] = posacc;
+        posacc += m;
+        F.max_mi = std::max(F.max_mi, t.m_i(s));
+        F.max_mb = std::max(F.max_mb, t.m_b(s));
+    }
+    F.front_elems = acc;
+    // inverse extend-add map per front position
+    std::vector<int32_t> fsrc(std::max<int64_t>(posacc, 1), 0);
+    for (int s = 0; s < t.nnodes; ++s) {
+        for (int w = 0; w < 2; ++w) {
+            const int k = t.child(s, w);
+            if (k < 0) continue;
+            for (int r = 0; r < t.m_b(k); ++r) fsrc[poff[s] + t.emap[t.b_off(k) + r]] = (w << 30) | r;
+        }
+    }
+    // level lists and per-level workspace offsets
+    std::vector<int32_t> lev_flat;
+    std::vector<int64_t> lev_off(t.depth + 2, 0), woff_flat;
+    int64_t wmax = 0, lmax = 0;
+    for (int l = 0; l <= t.depth; ++l) {
+        lev_off[l] = (int64_t)lev_flat.size();
+        int64_t w = 0;
+        for (int s : F.levels[l]) {
+            lev_flat.push_back(s);
+            woff_flat.push_back(w);
+            w += (int64_t)t.m_i(s) + t.m_b(s);
+        }
+        wmax = std::max(wmax, w);
+        lmax = std::max<int64_t>(lmax, (int64_t)F.levels[l].size());
+    }
+    lev_off[t.depth + 1] = (int64_t)lev_flat.size();
+    // apply task lists
+    std::vector<int32_t> tasks;
+    F.up_off.assign(t.depth + 1, 0);
+    F.up_cnt.assign(t.depth + 1, 0);
+    F.dn_off.assign(t.depth + 1, 0);
+    F.dn_cnt.assign(t.depth + 1, 0);
+    for (int l = 0; l <= t.depth; ++l) {
+        F.up_off[l] = (int64_t)tasks.size() / 2;
+        for (int s : F.levels[l])
+            if (t.m_i(s) > 0)
+                for (int j0 = 0; j0 < t.m_b(s); j0 += APPLY_ROWS) { tasks.push_back(s); tasks.push_back(j0); }
+        F.up_cnt[l] = (int64_t)tasks.size() / 2 - F.up_off[l];
+    }
+    F.diag_off = (int64_t)tasks.size() / 2;
+    for (int s = 0; s < t.nnodes; ++s)
+        for (int i0 = 0; i0 < t.m_i(s); i0 += APPLY_ROWS) { tasks.push_back(s); tasks.push_back(i0); }
+    F.diag_cnt = (int64_t)tasks.size() / 2 - F.diag_off;
+    for (int l = 0; l <= t.depth; ++l) {
+        F.dn_off[l] = (int64_t)tasks.size() / 2;
+        for (int s : F.levels[l])
+            if (t.m_b(s) > 0)
+                for (int i0 = 0; i0 < t.m_i(s); i0 += APPLY_ROWS) { tasks.push_back(s); tasks.push_back(i0); }
+        F.dn_cnt[l] = (int64_t)tasks.size() / 2 - F.dn_off[l];
+    }
+    int64_t apply_elems = 0;
+    for (int s = 0; s < t.nnodes; ++s)
+        apply_elems += (int64_t)t.m_i(s) * t.m_i(s) + 2 * (int64_t)t.m_i(s) * t.m_b(s);
+    F.apply_bytes = apply_elems * (int64_t)esize;
+
+    ndhss_status rc = NDHSS_OK;
+    int32_t *d_eoff = nullptr, *d_erow = nullptr, *d_ecol = nullptr, *d_eidx = nullptr, *d_fsrc = nullptr, *d_lev = nullptr;
+    int64_t *d_poff = nullptr, *d_woff = nullptr;
+    void *d_cbuf = nullptr, *d_zbuf = nullptr, *d_ainv = nullptr;
+    DevStatus* d_status = nullptr;
+    int64_t tmp_bytes = 0;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    auto cleanup = [&]() {
+        cudaFree(d_eoff); cudaFree(d_erow); cudaFree(d_ecol); cudaFree(d_eidx); cudaFree(d_fsrc); cudaFree(d_lev);
+        cudaFree(d_poff); cudaFree(d_woff); cudaFree(d_cbuf); cudaFree(d_zbuf); cudaFree(d_ainv); cudaFree(d_status);
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+    };
+#define UP(dst, vec) do { rc = upload(&dst, (vec).data(), (vec).size(), &F.dev_bytes); if (rc) { cleanup(); ndhss_factor_destroy(h); return rc; } } while (0)
+#define UPT(dst, vec) do { rc = upload(&dst, (vec).data(), (vec).size(), &tmp_bytes); if (rc) { cleanup(); ndhss_factor_destroy(h); return rc; } } while (0)
+    UP(F.d_node, t.node_info);
+    UP(F.d_foff, F.foff);
+    UP(F.d_blist, t.blist);
+    UP(F.d_perm, t.perm);
+    UP(F.d_tasks, tasks);
+    UPT(d_eoff, t.e_off);
+    UPT(d_erow, t.e_row);
+    UPT(d_ecol, t.e_col);
+    UPT(d_eidx, t.e_idx);
+    UPT(d_fsrc, fsrc);
+    UPT(d_poff, poff);
+    UPT(d_lev, lev_flat);
+    UPT(d_woff, woff_flat);
+#undef UP
+#undef UPT
+    auto dalloc = [&](void** p, size_t bytes, int64_t* accb) -> bool {
+        if (cudaMalloc(p, std::max<size_t>(bytes, 16)) != cudaSuccess) {
+            cudaGetLastError();
+            *p = nullptr;
+            return false;
+        }
+        *accb += (int64_t)bytes;
+        return true;
+    };
+    if (!dalloc((void**)&F.d_sigma, (size_t)t.n * 4, &F.dev_bytes) ||
+        !dalloc((void**)&F.d_ipiv, (size_t)t.n * 4, &F.dev_bytes) ||
+        !dalloc(&F.d_front, (size_t)F.front_elems * esize, &F.dev_bytes) ||
+        !dalloc(&d_cbuf, (size_t)wmax * KBMAX * esize, &tmp_bytes) ||
+        !dalloc(&d_zbuf, (size_t)wmax * KBMAX * esize, &tmp_bytes) ||
+        !dalloc(&d_ainv, (size_t)lmax * KBMAX * KBMAX * esize, &tmp_bytes) ||
+        !dalloc((void**)&d_status, sizeof(DevStatus), &tmp_bytes)) {
+        cleanup();
+        ndhss_factor_destroy(h);
+        return set_error(NDHSS_ERR_OOM, "ndhss_factor: device allocation failed (front arena %lld elements)",
+                         (long long)F.front_elems);
+    }
+    NDHSS_CUDA_TRY(cudaMemsetAsync(d_status, 0, sizeof(DevStatus), st));
+    NDHSS_CUDA_TRY(cudaEventCreate(&e0));
+    NDHSS_CUDA_TRY(cudaEventCreate(&e1));
+    NDHSS_CUDA_TRY(cudaEventRecord(e0, st));
+    if (!cplx && fp64)
+        rc = factor_run<double, double>(F, t, (const double*)d_vals, d_eoff, d_erow, d_ecol, d_eidx, d_fsrc, d_poff, d_lev,
+                                        lev_off, d_woff, (double*)d_cbuf, (double*)d_zbuf, (double*)d_ainv, d_status,
+                                        o.panel, st);
+    else if (!cplx)
+        rc = factor_run<float, double>(F, t, (const double*)d_vals, d_eoff, d_erow, d_ecol, d_eidx, d_fsrc, d_poff, d_lev,
+                                       lev_off, d_woff, (float*)d_cbuf, (float*)d_zbuf, (float*)d_ainv, d_status,
+                                       o.panel, st);
+    else if (fp64)
+        rc = factor_run<c128, c128>(F, t, (const c128*)d_vals, d_eoff, d_erow, d_ecol, d_eidx, d_fsrc, d_poff, d_lev,
+                                    lev_off, d_woff, (c128*)d_cbuf, (c128*)d_zbuf, (c128*)d_ainv, d_status, o.panel, st);
+    else
+        rc = factor_run<c64, c128>(F, t, (const c128*)d_vals, d_eoff, d_erow, d_ecol, d_eidx, d_fsrc, d_poff, d_lev,
+                                   lev_off, d_woff, (c64*)d_cbuf, (c64*)d_zbuf, (c64*)d_ainv, d_status, o.panel, st);
+    if (rc == NDHSS_OK) {
+        cudaEventRecord(e1, st);
+        DevStatus hs{};
+        cudaError_t e = cudaMemcpyAsync(&hs, d_status, sizeof(hs), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) {
+            rc = set_error(NDHSS_ERR_CUDA, "ndhss_factor: %s", cudaGetErrorString(e));
+        } else if (hs.code != 0) {
+            rc = set_error((ndhss_status)hs.code, "ndhss_factor: zero pivot in A_ii of node %d (level %d)", hs.node,
+                           t.level(hs.node));
+        } else {
+            float ms = 0;
+            cudaEventElapsedTime(&ms, e0, e1);
+            F.factor_ms = ms;
+        }
+    }
+    cleanup();
+    if (rc != NDHSS_OK) {
+        cudaStreamSynchronize(st);
+        ndhss_factor_destroy(h);
+        return rc;
+    }
+    *out = h;
+    return NDHSS_OK;
+}
+
+template <typename T, typename V>
+static void convert_block(const T* src, V* dst, int64_t rows, int64_t cols, int64_t ldsrc, int64_t lddst,
+                          const int32_t* colperm, double sign);
+
+template <>
+void convert_block<double, double>(const double* src, double* dst, int64_t rows, int64_t cols, int64_t ls, int64_t ld,
+                                   const int32_t* cp, double sign) {
+    for (int64_t j = 0; j < cols; ++j)
+        for (int64_t i = 0; i < rows; ++i) dst[(cp ? cp[j] : j) * ld + i] = sign * src[j * ls + i];
+}
+template <>
+void convert_block<float, double>(const float* src, double* dst, int64_t rows, int64_t cols, int64_t ls, int64_t ld,
+                                  const int32_t* cp, double sign) {
+    for (int64_t j = 0; j < cols; ++j)
+        for (int64_t i = 0; i < rows; ++i) dst[(cp ? cp[j] : j) * ld + i] = sign * (double)src[j * ls + i];
+}
+template <>
+void convert_block<c128, c128>(const c128* src, c128* dst, int64_t rows, int64_t cols, int64_t ls, int64_t ld,
+                               const int32_t* cp, double sign) {
+    for (int64_t j = 0; j < cols; ++j)
+        for (int64_t i = 0; i < rows; ++i) {
+            const c128 v = src[j * ls + i];
+            dst[(cp ? cp[j] : j) * ld + i] = {sign * v.x, sign * v.y};
+        }
+}
+template <>
+void convert_block<c64, c128>(const c64* src, c128* dst, int64_t rows, int64_t cols, int64_t ls, int64_t ld,
+                              const int32_t* cp, double sign) {
+    for (int64_t j = 0; j < cols; ++j)
+        for (int64_t i = 0; i < rows; ++i) {
+            const c64 v = src[j * ls + i];
+            dst[(cp ? cp[j] : j) * ld + i] = {sign * (double)v.x, sign * (double)v.y};
+        }
+}
+
+static ndhss_status get_block_impl(const ndhss_factorization* fh, int32_t node, int32_t which, void* host_out, int64_t ld) {
+    if (!fh || !host_out) return set_error(NDHSS_ERR_INVALID_ARG, "ndhss_factor_get_block: NULL argument");
+    const FactorData& F = fh->f;
+    if (node < 0 || node >= F.nnodes || which < 0 || which > 3)
+        return set_error(NDHSS_ERR_INVALID_ARG, "ndhss_factor_get_block: bad node %d or block %d", node, which);
+    const int64_t mi = F.m_i(node), mb = F.m_b(node), m = mi + mb;
+    const int64_t rows = (which == 0 || which == 1) ? mi : mb;
+    const int64_t cols = (which == 0 || which == 2) ? mi : mb;
+    if (ld < std::max<int64_t>(rows, 1)) return set_error(NDHSS_ERR_INVALID_ARG, "ndhss_factor_get_block: ld too small");
+    if (rows == 0 || cols == 0) return NDHSS_OK;
+    std::vector<unsigned char> buf((size_t)(m * m) * F.esize);
+    NDHSS_CUDA_TRY(cudaDeviceSynchronize());
+    NDHSS_CUDA_TRY(cudaMemcpy(buf.data(), (const unsigned char*)F.d_front + (size_t)F.foff[node] * F.esize, buf.size(),
+                              cudaMemcpyDeviceToHost));
+    std::vector<int32_t> sig;
+    if (which == 0 || which == 2) {
+        sig.resize(mi);
+        NDHSS_CUDA_TRY(cudaMemcpy(sig.data(), F.d_sigma + F.info(node, 4), mi * 4, cudaMemcpyDeviceToHost));
+    }
+    const int64_t r0 = (which == 0 || which == 1) ? 0 : mi;
+    const int64_t c0 = (which == 0 || which == 2) ? 0 : mi;
+    const int32_t* cp = sig.empty() ? nullptr : sig.data();
+    const double sign = (which == 2) ? -1.0 : 1.0;
+    const bool cplx = F.vtype == NDHSS_C128;
+    const size_t off = (size_t)(c0 * m + r0);
+    if (!cplx && F.prec == NDHSS_FP64)
+        convert_block<double, double>((const double*)buf.data() + off, (double*)host_out, rows, cols, m, ld, cp, sign);
+    else if (!cplx)
+        convert_block<float, double>((const float*)buf.data() + off, (double*)host_out, rows, cols, m, ld, cp, sign);
+    else if (F.prec == NDHSS_FP64)
+        convert_block<c128, c128>((const c128*)buf.data() + off, (c128*)host_out, rows, cols, m, ld, cp, sign);
+    else
+        convert_block<c64, c128>((const c64*)buf.data() + off, (c128*)host_out, rows, cols, m, ld, cp, sign);
+    return NDHSS_OK;
+}
+
+}  // namespace ndhss
+
+extern "C" {
+
+ndhss_status ndhss_factor(const ndhss_tree* t, int32_t vtype, const int32_t* d_rowptr, const int32_t* d_col,
+                          const void* d_vals, const ndhss_factor_opts* opts, void* stream, ndhss_factorization** out) {
+    ndhss::clear_error();
+    return ndhss::factor_impl(t, vtype, d_rowptr, d_col, d_vals, opts, stream, out);
+}
+
+ndhss_status ndhss_factor_get_block(const ndhss_factorization* f, int32_t node, int32_t which, void* host_out, int64_t ld) {
+    ndhss::clear_error();
+    return ndhss::get_block_impl(f, node, which, host_out, ld);
+}
+
+ndhss_status ndhss_factor_stats_get(const ndhss_factorization* fh, ndhss_factor_stats* st) {
+    ndhss::clear_error();
+    if (!fh || !st) return ndhss::set_error(NDHSS_ERR_INVALID_ARG, "ndhss_factor_stats_get: NULL argument");
+    const auto& F = fh->f;
+    st->n = F.n;
+    st->nnodes = F.nnodes;
+    st->depth = F.depth;
+    st->front_elems = F.front_elems;
+    st->apply_bytes = F.apply_bytes;
+    st->factor_bytes = F.dev_bytes;
+    st->factor_ms = F.factor_ms;
+    st->kmax = 0;
+    st->prec = F.prec;
+    return NDHSS_OK;
+}
+
+void ndhss_factor_destroy(ndhss_factorization* fh) {
+    if (!fh) return;
+    auto& F = fh->f;
+    cudaFree(F.d_node);
+    cudaFree(F.d_foff);
+    cudaFree(F.d_blist);
+    cudaFree(F.d_perm);
+    cudaFree(F.d_sigma);
+    cudaFree(F.d_ipiv);
+    cudaFree(F.d_front);
+    cudaFree(F.d_tasks);
+    delete fh;
+}
+
+}  // extern "C"

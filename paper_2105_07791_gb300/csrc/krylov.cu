@@ -1,0 +1,454 @@
+// Sparse product and restarted, left-preconditioned GMRES (Eq. 1.2, Sec. 4)
+// in float64 / complex128 on the device.
+//
+// Per Arnoldi step j:  t = A v_j (CSR SpMV);  w = P^{-1} t (Algorithm 3.1);
+// classical Gram-Schmidt twice: h = V^H w, w -= V h (x2); ||w||; a one-thread
+// kernel stores the Hessenberg column, applies the previous complex Givens
+// rotations G = [[c, s], [-conj(s), c]], forms the new one and updates the
+// least-squares residual |g_{j+1}|; v_{j+1} = w / h_{j+1,j}.  The host reads
+// that residual once per step to decide whether the cycle ends.  After each
+// cycle x += V y with H y = g solved on the device, and the float64 true
+// residual ||b - A x|| / ||b|| decides convergence (restarts refine).
+//
+// Reductions are deterministic: each block writes its partial sums and the
+// last block to finish (ticket counter) adds them in block order.
+#include <algorithm>
+#include <cmath>
+
+#include "factor.cuh"
+
+namespace ndhss {
+namespace {
+
+constexpr int KMAX = 32;          // restart + 1 <= KMAX
+constexpr int RT = 256;           // reduction block size
+constexpr int RB = 2 * 152;       // reduction grid (two blocks per SM)
+
+__device__ __forceinline__ double ldcg(const double* p) { return __ldcg(p); }
+__device__ __forceinline__ c128 ldcg(const c128* p) {
+    const double2 v = __ldcg(reinterpret_cast<const double2*>(p));
+    return {v.x, v.y};
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ __forceinline__ c128 warp_sum(c128 v) {
+    for (int o = 16; o; o >>= 1) {
+        v.x += __shfl_xor_sync(0xffffffffu, v.x, o);
+        v.y += __shfl_xor_sync(0xffffffffu, v.y, o);
+    }
+    return v;
+}
+__device__ __forceinline__ double absv(double a) { return fabs(a); }
+__device__ __forceinline__ double absv(c128 a) { return hypot(a.x, a.y); }
+__device__ __forceinline__ c128 cdiv(c128 a, c128 b) { return a * recip(b); }
+__device__ __forceinline__ double cdiv(double a, double b) { return a / b; }
+
+// ----------------------------------------------------------------- SpMV
+template <typename V, int TPR>
+__global__ void spmv_kernel(int n, const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+                            const V* __restrict__ vals, const V* __restrict__ x, V* __restrict__ y) {
+    const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t row = gt / TPR;
+    const int lane = (int)(gt % TPR);
+    if (row >= n) return;               // whole TPR groups leave together
+    V acc = zero<V>();
+    for (int k = rowptr[row] + lane; k < rowptr[row + 1]; k += TPR) acc = fmac(vals[k], x[col[k]], acc);
+    if constexpr (sizeof(V) == 8) {
+        for (int o = TPR / 2; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o, TPR);
+    } else {
+        for (int o = TPR / 2; o; o >>= 1) {
+            acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o, TPR);
+            acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o, TPR);
+        }
+    }
+    if (lane == 0) y[row] = acc;
+}
+
+template <typename V>
+ndhss_status spmv_launch(int n, int64_t nnz, const int32_t* rowptr, const int32_t* col, const V* vals, const V* x, V* y,
+                         cudaStream_t st) {
+    const int tpr = (nnz > 8LL * n) ? 8 : 4;
+    const int64_t threads = (int64_t)n * tpr;
+    const unsigned blocks = (unsigned)((threads + 255) / 256);
+    if (tpr == 8) spmv_kernel<V, 8><<<blocks, 256, 0, st>>>(n, rowptr, col, vals, x, y);
+    else spmv_kernel<V, 4><<<blocks, 256, 0, st>>>(n, rowptr, col, vals, x, y);
+    NDHSS_LAUNCH_CHECK("spmv_kernel");
+    return NDHSS_OK;
+}
+
+// ---------------------------------------------------------- reductions
+// out[i] = sum_rows conj(Vb(row, i)) * w(row), i < k
+template <typename V>
+__global__ void __launch_bounds__(RT)
+mdot_kernel(int n, const V* __restrict__ Vb, int64_t ldv, int k, const V* __restrict__ w, V* __restrict__ partial,
+            V* __restrict__ out, unsigned* __restrict__ counter) {
+    __shared__ V sred[KMAX][RT / 32];
+    __shared__ bool s_last;
+    V acc[KMAX];
+#pragma unroll
+    for (int i = 0; i < KMAX; ++i) acc[i] = zero<V>();
+    for (int64_t row = (int64_t)blockIdx.x * RT + threadIdx.x; row < n; row += (int64_t)gridDim.x * RT) {
+        const V wv = w[row];
+#pragma unroll
+        for (int i = 0; i < KMAX; ++i)
+            if (i < k) acc[i] = fmac(conjv(Vb[row + i * ldv]), wv, acc[i]);
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int i = 0; i < KMAX; ++i) {
+        if (i < k) {
+            const V v = warp_sum(acc[i]);
+            if (lane == 0) sred[i][warp] = v;
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x < k) {
+        V sum = zero<V>();
+        for (int q = 0; q < RT / 32; ++q) sum += sred[threadIdx.x][q];
+        partial[blockIdx.x * KMAX + threadIdx.x] = sum;
+    }
+    __threadfence();
+    if (threadIdx.x == 0) s_last = (atomicAdd(counter, 1u) == gridDim.x - 1);
+    __syncthreads();
+    if (s_last) {
+        if (threadIdx.x < k) {
+            V sum = zero<V>();
+            for (unsigned b = 0; b < gridDim.x; ++b) sum += ldcg(partial + b * KMAX + threadIdx.x);
+            out[threadIdx.x] = sum;
+        }
+        if (threadIdx.x == 0) *counter = 0;
+    }
+}
+
+// out = sum |w|^2
+template <typename V>
+__global__ void __launch_bounds__(RT)
+nrm2_kernel(int n, const V* __restrict__ w, double* __restrict__ partial, double* __restrict__ out,
+            unsigned* __restrict__ counter) {
+    __shared__ double sred[RT / 32];
+    __shared__ bool s_last;
+    double acc = 0.0;
+    for (int64_t row = (int64_t)blockIdx.x * RT + threadIdx.x; row < n; row += (int64_t)gridDim.x * RT) acc += norm2(w[row]);
+    acc = warp_sum(acc);
+    if ((threadIdx.x & 31) == 0) sred[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int q = 0; q < RT / 32; ++q) s += sred[q];
+        partial[blockIdx.x] = s;
+    }
+    __threadfence();
+    if (threadIdx.x == 0) s_last = (atomicAdd(counter, 1u) == gridDim.x - 1);
+    __syncthreads();
+    if (s_last && threadIdx.x == 0) {
+        double s = 0.0;
+        for (unsigned b = 0; b < gridDim.x; ++b) s += __ldcg(partial + b);
+        *out = s;
+        *counter = 0;
+    }
+}
+
+// w += sgn * Vb(:, 0:k) h
+template <typename V>
+__global__ void maxpy_kernel(int n, V* __restrict__ w, const V* __restrict__ Vb, int64_t ldv, int k,
+                             const V* __restrict__ h, double sgn) {
+    __shared__ V sh[KMAX];
+    if (threadIdx.x < k) sh[threadIdx.x] = scale(h[threadIdx.x], sgn);
+    __syncthreads();
+    for (int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; row < n; row += (int64_t)gridDim.x * blockDim.x) {
+        V acc = w[row];
+        for (int i = 0; i < k; ++i) acc = fmac(Vb[row + i * ldv], sh[i], acc);
+        w[row] = acc;
+    }
+}
+
+template <typename V>
+__global__ void scale_kernel(int n, const V* __restrict__ src, V* __restrict__ dst, const double* __restrict__ s) {
+    const double f = *s;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        dst[i] = scale(src[i], f);
+}
+
+template <typename V>
+__global__ void residual_kernel(int n, const V* __restrict__ b, const V* __restrict__ ax, V* __restrict__ r) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        r[i] = b[i] - ax[i];
+}
+
+// scalars: [0] scale for the next basis vector, [1] |g_{j+1}|, [2] h_{j+1,j}, [3] beta
+struct GmState {
+    double scal[4];
+};
+
+// start of a cycle: beta = ||z||, g = beta e_1
+template <typename V>
+__global__ void cycle_init_kernel(const double* __restrict__ nrm2z, V* __restrict__ g, int restart, GmState* stt) {
+    const double beta = sqrt(*nrm2z);
+    for (int i = 0; i <= restart; ++i) g[i] = zero<V>();
+    V b0 = zero<V>();
+    if constexpr (sizeof(V) == 8) b0 = beta; else b0.x = beta;
+    g[0] = b0;
+    stt->scal[0] = beta > 0 ? 1.0 / beta : 0.0;
+    stt->scal[3] = beta;
+    stt->scal[1] = beta;
+}
+
+// Hessenberg column j, Givens rotations, residual estimate
+template <typename V>
+__global__ void arnoldi_step_kernel(int j, V* __restrict__ H, int ldh, const V* __restrict__ h1, const V* __restrict__ h2,
+                                    const double* __restrict__ nrm2w, V* __restrict__ g, double* __restrict__ cs,
+                                    V* __restrict__ sn, GmState* stt) {
+    V* Hj = H + (int64_t)j * ldh;
+    for (int i = 0; i <= j; ++i) Hj[i] = h1[i] + h2[i];
+    const double hn = sqrt(*nrm2w);
+    V hv = zero<V>();
+    if constexpr (sizeof(V) == 8) hv = hn; else hv.x = hn;
+    Hj[j + 1] = hv;
+    for (int i = 0; i < j; ++i) {
+        const V t0 = scale(Hj[i], cs[i]) + sn[i] * Hj[i + 1];
+        const V t1 = scale(Hj[i + 1], cs[i]) - conjv(sn[i]) * Hj[i];
+        Hj[i] = t0;
+        Hj[i + 1] = t1;
+    }
+    const V a = Hj[j], b = Hj[j + 1];
+    double c;
+    V s;
+    const double aa = absv(a), ab = absv(b);
+    if (ab == 0.0) {
+        c = 1.0;
+        s = zero<V>();
+    } else if (aa == 0.0) {
+        c = 0.0;
+        s = scale(conjv(b), 1.0 / ab);
+    } else {
+        const double t = hypot(aa, ab);
+        c = aa / t;
+        s = scale(a, 1.0 / aa) * scale(conjv(b), 1.0 / t);
+    }
+    cs[j] = c;
+    sn[j] = s;
+    Hj[j] = scale(a, c) + s * b;
+    Hj[j + 1] = zero<V>();
+    const V gj = g[j];
+    g[j + 1] = -(conjv(s) * gj);
+    g[j] = scale(gj, c);
+    stt->scal[0] = hn > 0 ? 1.0 / hn : 0.0;
+    stt->scal[1] = absv(g[j + 1]);
+    stt->scal[2] = hn;
+}
+
+// y = H(0:k, 0:k)^{-1} g(0:k) (upper triangular)
+template <typename V>
+__global__ void hsolve_kernel(int k, const V* __restrict__ H, int ldh, const V* __restrict__ g, V* __restrict__ y) {
+    for (int i = k - 1; i >= 0; --i) {
+        V acc = g[i];
+        for (int l = i + 1; l < k; ++l) acc = acc - H[(int64_t)l * ldh + i] * y[l];
+        y[i] = cdiv(acc, H[(int64_t)i * ldh + i]);
+    }
+}
+
+template <typename V>
+ndhss_status gmres_one(const FactorData& F, const int32_t* rowptr, const int32_t* col, const V* vals, int64_t nnz,
+                       const V* b, V* x, const ndhss_gmres_opts& o, ndhss_gmres_stats* stats, unsigned char* ws,
+                       cudaStream_t st) {
+    const int n = F.n;
+    const int R = o.restart;
+    const int64_t ldv = ((int64_t)n + 31) / 32 * 32;
+    auto carve = [&](size_t bytes) {
+        unsigned char* p = ws;
+        ws += (bytes + 255) / 256 * 256;
+        return p;
+    };
+    V* Vb = (V*)carve(sizeof(V) * ldv * (R + 1));
+    V* w = (V*)carve(sizeof(V) * n);
+    V* t = (V*)carve(sizeof(V) * n);
+    V* r = (V*)carve(sizeof(V) * n);
+    V* H = (V*)carve(sizeof(V) * (R + 1) * R);
+    V* g = (V*)carve(sizeof(V) * (R + 1));
+    double* cs = (double*)carve(sizeof(double) * R);
+    V* sn = (V*)carve(sizeof(V) * R);
+    V* h1 = (V*)carve(sizeof(V) * KMAX);
+    V* h2 = (V*)carve(sizeof(V) * KMAX);
+    V* yv = (V*)carve(sizeof(V) * KMAX);
+    V* part = (V*)carve(sizeof(V) * RB * KMAX);
+    double* dpart = (double*)carve(sizeof(double) * RB);
+    double* nrm = (double*)carve(sizeof(double) * 4);
+    unsigned* counter = (unsigned*)carve(sizeof(unsigned) * 4);
+    GmState* stt = (GmState*)carve(sizeof(GmState));
+    void* awork = carve(apply_work_bytes(F));
+    NDHSS_CUDA_TRY(cudaMemsetAsync(counter, 0, sizeof(unsigned) * 4, st));
+    NDHSS_CUDA_TRY(cudaMemsetAsync(x, 0, sizeof(V) * n, st));
+    const int eb = std::min((n + 255) / 256, 4 * 152);
+    ndhss_status rc;
+    double hb[4];
+
+    auto read_scalars = [&](const void* src, size_t bytes, void* dst) -> ndhss_status {
+        NDHSS_CUDA_TRY(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, st));
+        NDHSS_CUDA_TRY(cudaStreamSynchronize(st));
+        return NDHSS_OK;
+    };
+
+    nrm2_kernel<V><<<RB, RT, 0, st>>>(n, b, dpart, nrm, counter);
+    NDHSS_LAUNCH_CHECK("nrm2_kernel");
+    if ((rc = read_scalars(nrm, sizeof(double), hb))) return rc;
+    const double bnorm = sqrt(hb[0]);
+    ndhss_gmres_stats S{};
+    if (bnorm == 0.0) {
+        S.converged = 1;
+        if (stats) *stats = S;
+        return NDHSS_OK;
+    }
+    double zbnorm = -1.0;
+    int its = 0, cycles = 0;
+    double last_res = 1.0;
+    while (true) {
+        if ((rc = spmv_launch<V>(n, nnz, rowptr, col, vals, x, t, st))) return rc;
+        residual_kernel<V><<<eb, 256, 0, st>>>(n, b, t, r);
+        nrm2_kernel<V><<<RB, RT, 0, st>>>(n, r, dpart, nrm, counter);
+        NDHSS_LAUNCH_CHECK("residual/nrm2");
+        if ((rc = read_scalars(nrm, sizeof(double), hb))) return rc;
+        const double rel = sqrt(hb[0]) / bnorm;
+        S.true_relres = rel;
+        if (rel <= o.tol) { S.converged = 1; break; }
+        if (its >= o.maxit) break;
+        ++cycles;
+        if ((rc = apply_device(F, 1, r, n, w, n, awork, st))) return rc;
+        nrm2_kernel<V><<<RB, RT, 0, st>>>(n, w, dpart, nrm, counter);
+        cycle_init_kernel<V><<<1, 1, 0, st>>>(nrm, g, R, stt);
+        scale_kernel<V><<<eb, 256, 0, st>>>(n, w, Vb, &stt->scal[0]);
+        NDHSS_LAUNCH_CHECK("cycle start");
+        if (zbnorm < 0) {
+            if ((rc = read_scalars(stt, sizeof(GmState), hb))) return rc;
+            zbnorm = hb[3];
+            if (zbnorm == 0.0) return set_error(NDHSS_ERR_INTERNAL, "ndhss_gmres: P^{-1} b vanished");
+        }
+        int jend = 0;
+        for (int j = 0; j < R; ++j) {
+            V* vj = Vb + (int64_t)j * ldv;
+            if ((rc = spmv_launch<V>(n, nnz, rowptr, col, vals, vj, t, st))) return rc;
+            if ((rc = apply_device(F, 1, t, n, w, n, awork, st))) return rc;
+            ++its;
+            mdot_kernel<V><<<RB, RT, 0, st>>>(n, Vb, ldv, j + 1, w, part, h1, counter);
+            maxpy_kernel<V><<<eb, 256, 0, st>>>(n, w, Vb, ldv, j + 1, h1, -1.0);
+            mdot_kernel<V><<<RB, RT, 0, st>>>(n, Vb, ldv, j + 1, w, part, h2, counter);
+            maxpy_kernel<V><<<eb, 256, 0, st>>>(n, w, Vb, ldv, j + 1, h2, -1.0);
+            nrm2_kernel<V><<<RB, RT, 0, st>>>(n, w, dpart, nrm, counter);
+            arnoldi_step_kernel<V><<<1, 1, 0, st>>>(j, H, R + 1, h1, h2, nrm, g, cs, sn, stt);
+            scale_kernel<V><<<eb, 256, 0, st>>>(n, w, Vb + (int64_t)(j + 1) * ldv, &stt->scal[0]);
+            NDHSS_LAUNCH_CHECK("arnoldi step");
+            if ((rc = read_scalars(stt, sizeof(GmState), hb))) return rc;
+            jend = j + 1;
+            last_res = hb[1] / zbnorm;
+            if (last_res <= o.tol || hb[2] == 0.0 || its >= o.maxit) break;
+        }
+        hsolve_kernel<V><<<1, 1, 0, st>>>(jend, H, R + 1, g, yv);
+        maxpy_kernel<V><<<eb, 256, 0, st>>>(n, x, Vb, ldv, jend, yv, 1.0);
+        NDHSS_LAUNCH_CHECK("cycle end");
+    }
+    S.iters = its;
+    S.cycles = cycles;
+    S.precond_relres = last_res;
+    if (stats) *stats = S;
+    return NDHSS_OK;
+}
+
+size_t gmres_work_bytes(const FactorData& F, int R, size_t vsz) {
+    const int64_t ldv = ((int64_t)F.n + 31) / 32 * 32;
+    size_t b = 0;
+    auto add = [&](size_t x) { b += (x + 255) / 256 * 256; };
+    add(vsz * ldv * (R + 1));
+    add(vsz * F.n); add(vsz * F.n); add(vsz * F.n);
+    add(vsz * (R + 1) * R); add(vsz * (R + 1)); add(8 * R); add(vsz * R);
+    add(vsz * KMAX); add(vsz * KMAX); add(vsz * KMAX);
+    add(vsz * RB * KMAX); add(8 * RB); add(32); add(16); add(sizeof(GmState));
+    add(apply_work_bytes(F));
+    return b;
+}
+
+}  // namespace
+}  // namespace ndhss
+
+extern "C" {
+
+ndhss_status ndhss_spmv(int32_t n, int32_t vtype, const int32_t* d_rowptr, const int32_t* d_col, const void* d_vals,
+                        const void* d_x, void* d_y, void* stream) {
+    using namespace ndhss;
+    clear_error();
+    if (n < 0 || !d_rowptr || !d_col || !d_vals || !d_x || !d_y) return set_error(NDHSS_ERR_INVALID_ARG, "ndhss_spmv: bad argument");
+    if (n == 0) return NDHSS_OK;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    int32_t nnz = 0;
+    NDHSS_CUDA_TRY(cudaMemcpy(&nnz, d_rowptr + n, sizeof(int32_t), cudaMemcpyDeviceToHost));
+    if (vtype == NDHSS_R64)
+        return spmv_launch<double>(n, nnz, d_rowptr, d_col, (const double*)d_vals, (const double*)d_x, (double*)d_y, st);
+    if (vtype == NDHSS_C128)
+        return spmv_launch<c128>(n, nnz, d_rowptr, d_col, (const c128*)d_vals, (const c128*)d_x, (c128*)d_y, st);
+    return set_error(NDHSS_ERR_INVALID_ARG, "ndhss_spmv: bad vtype %d", vtype);
+}
+
+ndhss_status ndhss_gmres(const ndhss_factorization* fh, const int32_t* d_rowptr, const int32_t* d_col, const void* d_vals,
+                         int32_t nrhs, const void* b, int64_t ldb, void* x, int64_t ldx, const ndhss_gmres_opts* opts,
+                         ndhss_gmres_stats* stats, void* stream) {
+    using namespace ndhss;
+    clear_error();
+    if (!fh || !d_rowptr || !d_col || !d_vals || !b || !x || nrhs < 0)
+        return set_error(NDHSS_ERR_INVALID_ARG, "ndhss_gmres: bad argument");
+    const FactorData& F = fh->f;
+    if (ldb < F.n || ldx < F.n) return set_error(NDHSS_ERR_INVALID_ARG, "ndhss_gmres: leading dimension < n");
+    ndhss_gmres_opts o{30, 300, 1e-8};
+    if (opts) o = *opts;
+    if (o.restart < 1 || o.restart > KMAX - 1 || o.maxit < 0 || !(o.tol >= 0))
+        return set_error(NDHSS_ERR_INVALID_ARG, "ndhss_gmres: need 1 <= restart <= %d, maxit >= 0, tol >= 0", KMAX - 1);
+    if (nrhs == 0) return NDHSS_OK;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const size_t vsz = F.vtype == NDHSS_C128 ? 16 : 8;
+    int32_t nnz = 0;
+    NDHSS_CUDA_TRY(cudaMemcpy(&nnz, d_rowptr + F.n, sizeof(int32_t), cudaMemcpyDeviceToHost));
+    const bool bdev = is_device_ptr(b), xdev = is_device_ptr(x);
+    const size_t vec = ((size_t)F.n * vsz + 255) / 256 * 256;
+    const size_t wb = gmres_work_bytes(F, o.restart, vsz) + (bdev ? 0 : vec) + (xdev ? 0 : vec);
+    void* work = nullptr;
+    NDHSS_CUDA_TRY(cudaMallocAsync(&work, wb, st));
+    unsigned char* ws = static_cast<unsigned char*>(work);
+    unsigned char* extra = ws + gmres_work_bytes(F, o.restart, vsz);
+    void* db = bdev ? nullptr : extra;
+    void* dx = xdev ? nullptr : extra + (bdev ? 0 : vec);
+    ndhss_status rc = NDHSS_OK;
+    bool any_fail = false;
+    for (int rhs = 0; rhs < nrhs && rc == NDHSS_OK; ++rhs) {
+        const unsigned char* bsrc = (const unsigned char*)b + (size_t)rhs * ldb * vsz;
+        unsigned char* xdst = (unsigned char*)x + (size_t)rhs * ldx * vsz;
+        const void* bb = bsrc;
+        void* xx = xdst;
+        if (!bdev) {
+            if (cudaMemcpyAsync(db, bsrc, (size_t)F.n * vsz, cudaMemcpyHostToDevice, st) != cudaSuccess) {
+                rc = set_error(NDHSS_ERR_CUDA, "ndhss_gmres: host-to-device copy failed");
+                break;
+            }
+            bb = db;
+        }
+        if (!xdev) xx = dx;
+        ndhss_gmres_stats S{};
+        if (F.vtype == NDHSS_R64)
+            rc = gmres_one<double>(F, d_rowptr, d_col, (const double*)d_vals, nnz, (const double*)bb, (double*)xx, o, &S, ws, st);
+        else
+            rc = gmres_one<c128>(F, d_rowptr, d_col, (const c128*)d_vals, nnz, (const c128*)bb, (c128*)xx, o, &S, ws, st);
+        if (rc == NDHSS_OK && !xdev) {
+            if (cudaMemcpyAsync(xdst, dx, (size_t)F.n * vsz, cudaMemcpyDeviceToHost, st) != cudaSuccess)
+                rc = set_error(NDHSS_ERR_CUDA, "ndhss_gmres: device-to-host copy failed");
+        }
+        if (stats) stats[rhs] = S;
+        if (!S.converged) any_fail = true;
+    }
+    cudaFreeAsync(work, st);
+    if (cudaStreamSynchronize(st) != cudaSuccess && rc == NDHSS_OK)
+        rc = set_error(NDHSS_ERR_CUDA, "ndhss_gmres: stream synchronisation failed");
+    if (rc == NDHSS_OK && any_fail)
+        rc = set_error(NDHSS_ERR_NOT_CONVERGED, "ndhss_gmres: tolerance not reached within maxit");
+    return rc;
+}
+
+}  // extern "C"

@@ -1,0 +1,92 @@
+"""Host-side checks of the C-ABI library (no GPU needed): it builds, loads,
+exports every declared symbol, and its tree builder matches the oracle bit for bit."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+from ndhss_inputs import helmholtz_impedance, poisson_dirichlet
+from oracle.tree import build_tree
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def nd():
+    from paper_2105_07791_gb300 import build, ndhss
+    build.build()
+    ndhss.load()
+    return ndhss
+
+
+def test_exports_every_declared_symbol(nd):
+    hdr = open(os.path.join(ROOT, "include", "ndhss.h")).read()
+    declared = set(re.findall(r"^\s*(?:const\s+)?[\w\s\*]*?\b(ndhss_\w+)\s*\(", hdr, flags=re.M))
+    assert len(declared) >= 12
+    lib = nd.load()
+    for name in declared:
+        assert hasattr(lib, name), name
+    assert declared == set(nd.EXPORTED)
+    assert nd.ndhss_version().startswith("ndhss")
+
+
+TREE_KEYS = ("perm", "node_info", "blist", "emap", "e_off", "e_row", "e_col", "e_idx")
+
+
+@pytest.mark.parametrize("case", ["c1", "p1_odd", "p2_small", "helm_p1", "leaf16", "tiny", "single_leaf"])
+def test_tree_bit_exact_vs_oracle(nd, case):
+    leaf = 64
+    if case == "c1":
+        P = poisson_dirichlet(64)
+    elif case == "p1_odd":
+        P = poisson_dirichlet(37, seed=3)
+    elif case == "p2_small":
+        P = helmholtz_impedance(24, 2, 12.0)
+    elif case == "helm_p1":
+        P = helmholtz_impedance(45, 1, 9.0)
+    elif case == "leaf16":
+        P, leaf = helmholtz_impedance(20, 1, 4.0), 16
+    elif case == "tiny":
+        P, leaf = poisson_dirichlet(4), 2
+    else:
+        P = poisson_dirichlet(6)
+    T = build_tree(P.coords, P.A.indptr, P.A.indices, leaf)
+    e = nd.ndhss_tree_export(nd.ndhss_build_tree(P.coords, P.A.indptr, P.A.indices, leaf))
+    for k in TREE_KEYS:
+        assert np.array_equal(e[k], getattr(T, k)), k
+
+
+def test_tree_bit_exact_full_c2(nd):
+    """The benchmark workload (P2, 256 x 256 cells, n = 263169): identical tree."""
+    P = helmholtz_impedance(256, 2, 40.0)
+    T = build_tree(P.coords, P.A.indptr, P.A.indices, 64)
+    e = nd.ndhss_tree_export(nd.ndhss_build_tree(P.coords, P.A.indptr, P.A.indices, 64))
+    assert T.nnodes == 8445 and T.depth == 13 and T.node_info[-1, 5] == 1539
+    for k in TREE_KEYS:
+        assert np.array_equal(e[k], getattr(T, k)), k
+
+
+def test_tree_with_gaps_and_empty_boxes(nd):
+    """DOFs on a lattice with holes: empty boxes become size-0 leaves in both builders."""
+    P = poisson_dirichlet(32)
+    keep = np.nonzero((P.coords[:, 0] < 10) | (P.coords[:, 0] > 20) | (P.coords[:, 1] < 12))[0]
+    A = P.A[keep][:, keep].tocsr()
+    A.sort_indices()
+    coords = P.coords[keep]
+    T = build_tree(coords, A.indptr, A.indices, 20)
+    e = nd.ndhss_tree_export(nd.ndhss_build_tree(coords, A.indptr, A.indices, 20))
+    for k in TREE_KEYS:
+        assert np.array_equal(e[k], getattr(T, k)), k
+    assert np.any(T.f("m_i") + T.f("m_b") == 0)
+
+
+def test_invalid_arguments_return_error_codes(nd):
+    P = poisson_dirichlet(8)
+    bad = P.A.indices.copy()
+    bad[3] = 10 ** 6
+    with pytest.raises(nd.NdhssError) as ei:
+        nd.ndhss_build_tree(P.coords, P.A.indptr, bad, 16)
+    assert ei.value.code == 1 and "out of range" in str(ei.value)
+    with pytest.raises(nd.NdhssError):
+        nd.ndhss_build_tree(P.coords, P.A.indptr, P.A.indices, 0)
