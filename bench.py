@@ -1,0 +1,385 @@
+#!/usr/bin/env python
+"""Benchmark: solves/s and factor time at relative residual 1e-8, mixed
+(complex64 fronts, FP32 arithmetic) vs FP64 (complex128 fronts) GPU path.
+
+Workload: 2D Helmholtz -lap u - k^2 u = f on [0,1]^2, P2 continuous Galerkin
+on a 256 x 256 cell grid (n = 263169, nnz = 3018753), k = 40, first-order
+impedance condition (complex symmetric A), Gaussian point source of width
+0.02 at a seeded position; box nested dissection with leaf size 64.
+
+One step = one factorization P = L D R (all fronts, Sec. 3.1 / Alg. 3.4) plus
+one GMRES solve of A x = b to a float64 true relative residual of 1e-8 with
+P^{-1} applied by Algorithm 3.1.  ``value`` is solves per second of the solve
+phase (the factorization is reused across solves in practice and is reported
+separately as ``factor_ms``, as the metric defines); ``ms_per_step`` includes
+both.  Inputs stay resident in HBM; the factor (>= 0.7 GB) exceeds the 129 MB
+L2, so every apply streams it from HBM.
+
+``--impl reference`` times the FP64 CPU oracle (the only other place this
+script runs ``oracle/``) on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "solves/s and factor time at rel. residual 1e-8: mixed vs FP64 GPU path"
+WORKLOAD = dict(N=256, p=2, k=40.0, seed=0, leaf=64, tol=1e-8)
+
+# ncu DRAM traffic of the dominant kernel class, per launch, keyed by the
+# sha256 of the source file it was measured on (null once the source changes)
+NCU_TRAFFIC = {}
+
+
+def _args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ndhss", choices=["ndhss", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--only", choices=["mixed", "fp64"], help="time one precision only (profiling runs)")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer measurement (profiling runs)")
+    ap.add_argument("--N", type=int, default=WORKLOAD["N"], help="cells per side (default: the benchmark workload)")
+    return ap.parse_args()
+
+
+def _workload(N, seed):
+    from ndhss_inputs import helmholtz_impedance
+    k = WORKLOAD["k"] * N / 256.0
+    return helmholtz_impedance(N, WORKLOAD["p"], k, seed=seed)
+
+
+def _workload_name(P):
+    return (f"helmholtz_p2_cg_{P.meta['N']}x{P.meta['N']}_k{P.meta['k']:g}_impedance "
+            f"(n={P.n}, nnz={P.A.nnz}, leaf {WORKLOAD['leaf']})")
+
+
+class Clocks:
+    """nvidia-smi samples (every 200 ms) while the timed region runs."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.lines = []
+        self.p = None
+
+    def __enter__(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                       "-lms", "200", "-i", str(self.idx)], stdout=subprocess.PIPE,
+                                      stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.p = None
+        return self
+
+    def _read(self):
+        for line in self.p.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.p is not None:
+            self.p.terminate()
+            try:
+                self.p.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.p.kill()
+
+    def summary(self):
+        sm, smax, reasons = [], None, set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            pk = json.load(f)
+        return pk, "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def _src_sha(name):
+    with open(os.path.join(ROOT, "paper_2105_07791_gb300", "csrc", name), "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+def _dist():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+# ------------------------------------------------------------------ GPU arm
+def run_gpu(a):
+    import numpy as np
+    import torch
+
+    from paper_2105_07791_gb300 import build, ndhss
+
+    world, rank, local = _dist()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    build.build()
+    ndhss.load()
+    P = _workload(a.N, WORKLOAD["seed"] + rank)          # replicas: an independent instance per rank
+    tree = ndhss.ndhss_build_tree(P.coords, P.A.indptr, P.A.indices, WORKLOAD["leaf"])
+    M = ndhss.DeviceCSR(P.A)
+    b = torch.from_numpy(np.ascontiguousarray(P.b)).cuda()
+    x = torch.zeros_like(b)
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    def one_step(prec, timing):
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        e0.record(stream)
+        f = ndhss.ndhss_factor(tree, M.vtype, M.rowptr, M.col, M.vals,
+                               ndhss.make_factor_opts(prec=prec, timing=timing), stream=stream)
+        e1.record(stream)
+        st = ndhss.ndhss_gmres(f, M.rowptr, M.col, M.vals, b, x, tol=WORKLOAD["tol"], stream=stream, timing=timing)
+        e2.record(stream)
+        torch.cuda.synchronize()
+        return f, st, e0.elapsed_time(e1), e1.elapsed_time(e2)
+
+    results = {}
+    modes = [("mixed", ndhss.NDHSS_FP32), ("fp64", ndhss.NDHSS_FP64)]
+    if a.only:
+        modes = [m for m in modes if m[0] == a.only]
+    for name, prec in modes:
+        for _ in range(a.warmup):
+            f, st, _, _ = one_step(prec, False)
+            del f
+        barrier()
+        l0 = ndhss.ndhss_kernel_launches()
+        fms, sms, its, res, applies = [], [], [], [], []
+        fstats = None
+        with Clocks(local) as clk:
+            tw = time.time()
+            for k in range(a.steps):
+                f, st, tf, ts = one_step(prec, True)
+                fms.append(tf)
+                sms.append(ts)
+                its.append(st["iters"])
+                res.append(st["true_relres"])
+                applies.append((st["apply_ms"], st["napply"], st["spmv_ms"], st["nspmv"]))
+                fstats = ndhss.ndhss_factor_stats_get(f)
+                del f
+            barrier()
+            wall = time.time() - tw
+        launches = ndhss.ndhss_kernel_launches() - l0
+        tot_f, tot_s = sum(fms), sum(sms)
+        if world > 1:
+            t = torch.tensor([tot_f, tot_s], device="cuda", dtype=torch.float64)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            tot_f, tot_s = float(t[0]), float(t[1])
+        results[name] = dict(factor_ms=tot_f / a.steps, solve_ms=tot_s / a.steps,
+                             solves_per_s=world * a.steps / (tot_s / 1e3), iters=int(statistics.median(its)),
+                             iters_all=its, true_relres=max(res), launches=launches, clocks=clk.summary(),
+                             fstats=fstats, applies=applies, wall_s=wall)
+
+    if a.only or a.no_e2e:
+        for name, r in results.items():
+            if rank == 0:
+                print(json.dumps({"profiling_run": name, "factor_ms": r["factor_ms"], "solve_ms": r["solve_ms"],
+                                  "iters": r["iters"], "launches": r["launches"], "fstats": r["fstats"]}), flush=True)
+        return
+    # end-to-end: the same solve through the C ABI with pinned host buffers
+    f = ndhss.ndhss_factor(tree, M.vtype, M.rowptr, M.col, M.vals, ndhss.make_factor_opts(prec=ndhss.NDHSS_FP32),
+                           stream=stream)
+    bh = torch.from_numpy(np.ascontiguousarray(P.b)).pin_memory()
+    xh = torch.zeros_like(bh).pin_memory()
+    bn, xn = bh.numpy(), xh.numpy()
+    for _ in range(a.warmup):
+        ndhss.ndhss_gmres(f, M.rowptr, M.col, M.vals, bn, xn, tol=WORKLOAD["tol"], stream=stream)
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(a.steps):
+        ndhss.ndhss_gmres(f, M.rowptr, M.col, M.vals, bn, xn, tol=WORKLOAD["tol"], stream=stream)
+    barrier()
+    e2e_s = time.perf_counter() - t0
+    if world > 1:
+        t = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_s = float(t[0])
+    relres_e2e = float(np.linalg.norm(P.b - P.A @ xn) / np.linalg.norm(P.b))
+    del f
+
+    if rank != 0:
+        if world > 1:
+            torch.distributed.destroy_process_group()
+        return
+    mx, fp = results["mixed"], results["fp64"]
+    pk, pk_kind = _peaks()
+    # roofline of the dominant kernel class of a mixed step (live CUDA events)
+    fs = mx["fstats"]
+    cls_ms = fs["class_ms"]
+    ap_ms = sum(v[0] for v in mx["applies"]) / a.steps
+    ap_n = sum(v[1] for v in mx["applies"]) / a.steps
+    cands = dict(cls_ms)
+    cands["apply"] = ap_ms
+    dominant = max(cands, key=cands.get)
+    if dominant == "apply":
+        per = fs["apply_bytes"]
+        dur_ms = ap_ms / max(ap_n, 1)
+        ach = per / (dur_ms / 1e3) / 1e9
+        roof = {"kernel": "Alg. 3.1 apply (up-sweep, diagonal, down-sweep launches)", "bound": "hbm",
+                "achieved": ach, "peak": pk["hbm_gbs"], "unit": "GB/s", "frac": ach / pk["hbm_gbs"],
+                "traffic": NCU_TRAFFIC.get(("apply", _src_sha("apply.cu"))), "peak_kind": f"hbm_gbs of {pk_kind}",
+                "algorithmic_bytes_per_launch": per, "avg_launch_ms": dur_ms}
+    else:
+        nl = max(fs["class_launches"][dominant], 1)
+        dur_ms = cls_ms[dominant] / nl
+        if dominant == "update":
+            # FP32 SIMT FMA peak: 152 SMs x 128 lanes x 2 flop x max SM clock
+            peak = 152 * 128 * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+            ach = fs["update_flops"] / nl / (dur_ms / 1e3) / 1e12
+            roof = {"kernel": "gemm_update_kernel (Gauss-Jordan front update, FP32 complex)", "bound": "alu",
+                    "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+                    "traffic": NCU_TRAFFIC.get(("update", _src_sha("factor.cu"))),
+                    "peak_kind": "derived: 152 SM x 128 FP32 lanes x 2 x max SM clock",
+                    "algorithmic_flops_per_launch": fs["update_flops"] / nl, "avg_launch_ms": dur_ms}
+        else:
+            roof = {"kernel": dominant, "bound": "latency", "achieved": None, "peak": None, "unit": None,
+                    "frac": None, "traffic": None, "avg_launch_ms": dur_ms}
+    line = {
+        "metric": METRIC,
+        "value": mx["solves_per_s"],
+        "unit": "solves/s",
+        "n_gpus": world,
+        "steps": a.steps,
+        "warmup": a.warmup,
+        "ms_per_step": mx["factor_ms"] + mx["solve_ms"],
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "c64 fronts (fp32) / c128 Krylov (fp64)",
+        "data": "synthetic",
+        "config": {"workload": _workload_name(P), "rhs_per_step": 1, "tol": WORKLOAD["tol"],
+                   "compression": "off (exact dense fronts)", "l2": "inputs exceed L2 (factor streamed from HBM)",
+                   "parallelism": f"replicas x{world}"},
+        "factor_ms": mx["factor_ms"],
+        "solve_ms": mx["solve_ms"],
+        "iters": mx["iters"],
+        "true_relres": mx["true_relres"],
+        "fp64": {"solves_per_s": fp["solves_per_s"], "factor_ms": fp["factor_ms"], "solve_ms": fp["solve_ms"],
+                 "iters": fp["iters"], "true_relres": fp["true_relres"]},
+        "mixed_over_fp64": {"solves_per_s": mx["solves_per_s"] / fp["solves_per_s"],
+                            "factor_speedup": fp["factor_ms"] / mx["factor_ms"]},
+        "apply_gbs": fs["apply_bytes"] / (ap_ms / max(ap_n, 1) / 1e3) / 1e9,
+        "e2e": {"value": world * a.steps / e2e_s, "unit": "solves/s", "h2d_bytes_per_step": int(P.b.nbytes),
+                "d2h_bytes_per_step": int(xn.nbytes), "true_relres": relres_e2e},
+        "gpu_launches": mx["launches"],
+        "roofline": roof,
+        "factor_kernel_ms": {k: round(v, 3) for k, v in cls_ms.items()},
+        "clocks": mx["clocks"],
+    }
+    if not a.no_cpu_baseline and world == 1:
+        line["cpu_baseline"] = cpu_baseline(P)
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+# ------------------------------------------------------------- CPU oracle
+def _oracle_setup(P):
+    from oracle.frontal import apply_inverse, factor_dense
+    from oracle.tree import build_tree
+    t0 = time.perf_counter()
+    T = build_tree(P.coords, P.A.indptr, P.A.indices, WORKLOAD["leaf"])
+    t1 = time.perf_counter()
+    fac = factor_dense(T, P.A)
+    t2 = time.perf_counter()
+    return fac, apply_inverse, t1 - t0, t2 - t1
+
+
+def cpu_baseline(P):
+    """The FP64 oracle as it stands, on the host cores: factor once, then one solve."""
+    from oracle.gmres import gmres
+    fac, apply_inverse, t_tree, t_fac = _oracle_setup(P)
+    t0 = time.perf_counter()
+    r = gmres(P.A, P.b, lambda v: apply_inverse(fac, v), tol=WORKLOAD["tol"])
+    ts = time.perf_counter() - t0
+    return {"value": 1.0 / ts, "unit": "solves/s", "cores": os.cpu_count(), "kind": "oracle",
+            "sample": (f"one GMRES solve (tol 1e-8, {r.iters} it) on the full workload with the oracle's "
+                       f"dense FP64 factor; factor built once beforehand in {t_fac:.1f} s (tree {t_tree:.1f} s), "
+                       "not counted, like the GPU value"),
+            "factor_s": t_fac, "iters": r.iters}
+
+
+def run_reference(a):
+    world, rank, _ = _dist()
+    if rank != 0:
+        return
+    P = _workload(a.N, WORKLOAD["seed"])
+    from oracle.gmres import gmres
+    fac, apply_inverse, t_tree, t_fac = _oracle_setup(P)
+    for _ in range(a.warmup):
+        gmres(P.A, P.b, lambda v: apply_inverse(fac, v), tol=WORKLOAD["tol"])
+    t0 = time.perf_counter()
+    its = []
+    for _ in range(a.steps):
+        r = gmres(P.A, P.b, lambda v: apply_inverse(fac, v), tol=WORKLOAD["tol"])
+        its.append(r.iters)
+    ts = time.perf_counter() - t0
+    val = a.steps / ts
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "solves/s", "n_gpus": world,
+            "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1e3 * ts / a.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64/c128", "data": "synthetic",
+            "config": {"workload": _workload_name(P), "rhs_per_step": 1, "tol": WORKLOAD["tol"]},
+            "factor_ms": 1e3 * t_fac, "iters": int(statistics.median(its)),
+            "cpu_baseline": {"value": val, "unit": "solves/s", "cores": os.cpu_count(), "kind": "oracle",
+                             "sample": ("each step one GMRES solve on the full workload with the oracle's dense "
+                                        f"FP64 factor, built once beforehand in {t_fac:.1f} s")},
+            "e2e": {"value": val, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    a = _args()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_gpu(a)
+
+
+if __name__ == "__main__":
+    main()

@@ -72,12 +72,16 @@ typedef struct {
     int32_t rank_cap;           /* largest HSS rank allowed, e.g. 512                  */
     int32_t panel;              /* pivot block width of the front kernels, 0 = auto    */
     uint64_t seed;              /* random sampling seed                                */
+    int32_t timing;             /* 1: time every kernel class with CUDA events         */
+    int32_t pad;
 } ndhss_factor_opts;
 
 typedef struct {
     int32_t restart;            /* Krylov basis length per cycle, e.g. 30              */
     int32_t maxit;              /* total Arnoldi steps allowed, e.g. 300               */
     double tol;                 /* relative residual target, e.g. 1e-8                 */
+    int32_t timing;             /* 1: time every apply / SpMV with CUDA events         */
+    int32_t pad;
 } ndhss_gmres_opts;
 
 typedef struct {
@@ -87,6 +91,8 @@ typedef struct {
     int32_t pad;
     double true_relres;         /* final float64 ||b - A x|| / ||b||                   */
     double precond_relres;      /* last ||P^{-1}(b - A x)|| / ||P^{-1} b|| estimate    */
+    int32_t napply, nspmv;      /* preconditioner applies / sparse products issued     */
+    double apply_ms, spmv_ms;   /* their summed device time (only when timing = 1)     */
 } ndhss_gmres_stats;
 
 typedef struct {
@@ -98,6 +104,12 @@ typedef struct {
     double factor_ms;           /* device time of the last ndhss_factor (CUDA events)  */
     int32_t kmax;               /* largest rank of any compressed block (0 if none)    */
     int32_t prec;
+    int64_t launches;           /* kernels launched by the last ndhss_factor           */
+    /* per kernel class (only when opts.timing = 1): summed device ms and launches;
+       classes 0 assemble, 1 scatter, 2 panel, 3 prep, 4 update, 5 finalize            */
+    double class_ms[8];
+    int64_t class_launches[8];
+    double update_flops;        /* algorithmic real flops of the front updates         */
 } ndhss_factor_stats;
 
 /* Library version string (static storage). */
@@ -105,6 +117,10 @@ const char* ndhss_version(void);
 
 /* Message of the last failed call on this thread (static per-thread storage). */
 const char* ndhss_last_error(void);
+
+/* Number of CUDA kernels the library has launched in this process so far
+ * (monotonic; for accounting of device work, e.g. per timed region). */
+int64_t ndhss_kernel_launches(void);
 
 /*
  * ndhss_build_tree -- box nested dissection and elimination tree

@@ -1,4 +1,5 @@
 // C ABI glue: version, error reporting and the tree handle.
+#include <atomic>
 #include <cstdarg>
 #include <cstring>
 #include <new>
@@ -19,6 +20,10 @@ ndhss_status set_error(ndhss_status code, const char* fmt, ...) {
 
 void clear_error() { g_err[0] = '\0'; }
 
+static std::atomic<int64_t> g_launches{0};
+
+void note_launches(int64_t k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+
 }  // namespace ndhss
 
 extern "C" {
@@ -26,6 +31,8 @@ extern "C" {
 const char* ndhss_version(void) { return "ndhss 0.1 (sm_103a)"; }
 
 const char* ndhss_last_error(void) { return ndhss::g_err; }
+
+int64_t ndhss_kernel_launches(void) { return ndhss::g_launches.load(); }
 
 ndhss_status ndhss_build_tree(int32_t n, const int32_t* coords, const int32_t* rowptr, const int32_t* col,
                               int32_t leaf_size, ndhss_tree** out) {

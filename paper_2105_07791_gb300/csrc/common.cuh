@@ -113,8 +113,10 @@ struct DevStatus {
                                       cudaGetErrorString(e_), __FILE__, __LINE__);             \
     } while (0)
 
+
 #define NDHSS_LAUNCH_CHECK(what)                                                               \
     do {                                                                                       \
+        ::ndhss::note_launches(1);                                                             \
         cudaError_t e_ = cudaGetLastError();                                                   \
         if (e_ != cudaSuccess)                                                                 \
             return ::ndhss::set_error(NDHSS_ERR_CUDA, "launch of %s failed: %s", what,         \

@@ -396,15 +396,46 @@ ndhss_status upload(U** dst, const U* src, size_t count, int64_t* acc) {
     return NDHSS_OK;
 }
 
+// Optional per-launch CUDA-event timing, summed per kernel class.
+struct LaunchTimer {
+    bool on = false;
+    cudaStream_t st = nullptr;
+    std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev;
+    cudaEvent_t pending = nullptr;
+    void begin() {
+        if (!on) return;
+        cudaEventCreate(&pending);
+        cudaEventRecord(pending, st);
+    }
+    void end(int cls) {
+        if (!on) return;
+        cudaEvent_t e;
+        cudaEventCreate(&e);
+        cudaEventRecord(e, st);
+        ev.push_back({cls, {pending, e}});
+    }
+    void collect(FactorData& F) {
+        for (auto& x : ev) {
+            float ms = 0;
+            if (cudaEventElapsedTime(&ms, x.second.first, x.second.second) == cudaSuccess) F.class_ms[x.first] += ms;
+            F.class_launches[x.first]++;
+            cudaEventDestroy(x.second.first);
+            cudaEventDestroy(x.second.second);
+        }
+        ev.clear();
+    }
+};
+
 template <typename T, typename V>
 ndhss_status factor_run(FactorData& F, const Tree& t, const V* d_vals, const int32_t* d_eoff,
                         const int32_t* d_erow, const int32_t* d_ecol, const int32_t* d_eidx,
                         const int32_t* d_fsrc, const int64_t* d_poff, const int32_t* d_lev,
                         const std::vector<int64_t>& lev_off, const int64_t* d_woff, T* d_cbuf, T* d_zbuf,
-                        T* d_ainv, DevStatus* d_status, int panel_opt, cudaStream_t st) {
+                        T* d_ainv, DevStatus* d_status, int panel_opt, LaunchTimer& tm, cudaStream_t st) {
     ndhss_status rc = set_smem_attrs<T>();
     if (rc != NDHSS_OK) return rc;
     T* front = static_cast<T*>(F.d_front);
+    const double flops_per_mac = Tr<T>::cplx ? 8.0 : 2.0;
     for (int l = F.depth; l >= 0; --l) {
         const auto& nodes = F.levels[l];
         const int L = (int)nodes.size();
@@ -418,11 +449,16 @@ ndhss_status factor_run(FactorData& F, const Tree& t, const V* d_vals, const int
         }
         if (mmax == 0) continue;
         const int agx = (int)std::min<int64_t>(mmax, 256);
+        tm.begin();
         assemble_kernel<T><<<dim3(agx, L), 256, 0, st>>>(lev, F.d_node, F.d_foff, d_fsrc, d_poff, front);
         NDHSS_LAUNCH_CHECK("assemble_kernel");
+        tm.end(0);
+        tm.begin();
         scatter_entries_kernel<T, V><<<L, 256, 0, st>>>(lev, F.d_node, F.d_foff, d_eoff, d_erow, d_ecol, d_eidx,
                                                         d_vals, front);
         NDHSS_LAUNCH_CHECK("scatter_entries_kernel");
+        tm.end(1);
+        F.launches += 2;
         const int gt = (int)((mmax + GT - 1) / GT);
         const int pgx = (int)std::min<int64_t>((mmax + PREP_WARPS - 1) / PREP_WARPS, 1024);
         for (int64_t k0 = 0; k0 < mimax;) {
@@ -431,20 +467,34 @@ ndhss_status factor_run(FactorData& F, const Tree& t, const V* d_vals, const int
             if (smem > PANEL_SMEM_BUDGET)
                 return set_error(NDHSS_ERR_INVALID_ARG, "front with %lld interior unknowns exceeds the panel kernel's shared memory",
                                  (long long)(mimax - k0));
+            tm.begin();
             panel_factor_kernel<T><<<L, PANEL_THREADS, smem, st>>>(lev, F.d_node, F.d_foff, front, F.d_ipiv, d_ainv,
                                                                    (int)k0, kb, d_status);
             NDHSS_LAUNCH_CHECK("panel_factor_kernel");
+            tm.end(2);
+            tm.begin();
             panel_prep_kernel<T><<<dim3(pgx, L), PREP_WARPS * 32, 0, st>>>(lev, F.d_node, F.d_foff, front, F.d_ipiv,
                                                                           d_ainv, d_cbuf, d_zbuf, woff, (int)k0, kb);
             NDHSS_LAUNCH_CHECK("panel_prep_kernel");
+            tm.end(3);
+            tm.begin();
             gemm_update_kernel<T><<<dim3(gt, gt, L), 256, 0, st>>>(lev, F.d_node, F.d_foff, front, d_cbuf, d_zbuf, woff,
                                                                  (int)k0, kb);
             NDHSS_LAUNCH_CHECK("gemm_update_kernel");
+            tm.end(4);
+            F.launches += 3;
+            for (int s2 : nodes) {
+                const int64_t mi = F.m_i(s2), m2 = mi + F.m_b(s2);
+                if (mi > k0) F.update_flops += flops_per_mac * (double)m2 * (double)m2 * (double)std::min<int64_t>(kb, mi - k0);
+            }
             k0 += kb;
         }
         if (mimax > 0) {
+            tm.begin();
             finalize_sigma_kernel<<<L, 256, (size_t)mimax * 2 * sizeof(int), st>>>(lev, F.d_node, F.d_ipiv, F.d_sigma);
             NDHSS_LAUNCH_CHECK("finalize_sigma_kernel");
+            tm.end(5);
+            F.launches += 1;
         }
     }
     return NDHSS_OK;
@@ -608,21 +658,24 @@ static ndhss_status factor_impl(const ndhss_tree* th, int32_t vtype, const int32
     NDHSS_CUDA_TRY(cudaMemsetAsync(d_status, 0, sizeof(DevStatus), st));
     NDHSS_CUDA_TRY(cudaEventCreate(&e0));
     NDHSS_CUDA_TRY(cudaEventCreate(&e1));
+    LaunchTimer tm;
+    tm.on = o.timing != 0;
+    tm.st = st;
     NDHSS_CUDA_TRY(cudaEventRecord(e0, st));
     if (!cplx && fp64)
         rc = factor_run<double, double>(F, t, (const double*)d_vals, d_eoff, d_erow, d_ecol, d_eidx, d_fsrc, d_poff, d_lev,
                                         lev_off, d_woff, (double*)d_cbuf, (double*)d_zbuf, (double*)d_ainv, d_status,
-                                        o.panel, st);
+                                        o.panel, tm, st);
     else if (!cplx)
         rc = factor_run<float, double>(F, t, (const double*)d_vals, d_eoff, d_erow, d_ecol, d_eidx, d_fsrc, d_poff, d_lev,
                                        lev_off, d_woff, (float*)d_cbuf, (float*)d_zbuf, (float*)d_ainv, d_status,
-                                       o.panel, st);
+                                       o.panel, tm, st);
     else if (fp64)
         rc = factor_run<c128, c128>(F, t, (const c128*)d_vals, d_eoff, d_erow, d_ecol, d_eidx, d_fsrc, d_poff, d_lev,
-                                    lev_off, d_woff, (c128*)d_cbuf, (c128*)d_zbuf, (c128*)d_ainv, d_status, o.panel, st);
+                                    lev_off, d_woff, (c128*)d_cbuf, (c128*)d_zbuf, (c128*)d_ainv, d_status, o.panel, tm, st);
     else
         rc = factor_run<c64, c128>(F, t, (const c128*)d_vals, d_eoff, d_erow, d_ecol, d_eidx, d_fsrc, d_poff, d_lev,
-                                   lev_off, d_woff, (c64*)d_cbuf, (c64*)d_zbuf, (c64*)d_ainv, d_status, o.panel, st);
+                                   lev_off, d_woff, (c64*)d_cbuf, (c64*)d_zbuf, (c64*)d_ainv, d_status, o.panel, tm, st);
     if (rc == NDHSS_OK) {
         cudaEventRecord(e1, st);
         DevStatus hs{};
@@ -637,6 +690,7 @@ static ndhss_status factor_impl(const ndhss_tree* th, int32_t vtype, const int32
             float ms = 0;
             cudaEventElapsedTime(&ms, e0, e1);
             F.factor_ms = ms;
+            tm.collect(F);
         }
     }
     cleanup();
@@ -748,6 +802,12 @@ ndhss_status ndhss_factor_stats_get(const ndhss_factorization* fh, ndhss_factor_
     st->factor_ms = F.factor_ms;
     st->kmax = 0;
     st->prec = F.prec;
+    st->launches = F.launches;
+    for (int k = 0; k < 8; ++k) {
+        st->class_ms[k] = F.class_ms[k];
+        st->class_launches[k] = F.class_launches[k];
+    }
+    st->update_flops = F.update_flops;
     return NDHSS_OK;
 }
 

@@ -43,6 +43,10 @@ struct FactorData {
     int32_t max_mi = 0, max_mb = 0;
 
     double factor_ms = 0.0;
+    int64_t launches = 0;
+    double class_ms[8] = {0};
+    int64_t class_launches[8] = {0};
+    double update_flops = 0.0;
     int64_t apply_bytes = 0;
     int64_t dev_bytes = 0;
 

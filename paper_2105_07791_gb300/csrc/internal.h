@@ -31,6 +31,7 @@ struct Tree {
 // Records a formatted message for ndhss_last_error() and returns `code`.
 ndhss_status set_error(ndhss_status code, const char* fmt, ...);
 void clear_error();
+void note_launches(int64_t k);
 
 ndhss_status build_tree_impl(int32_t n, const int32_t* coords, const int32_t* rowptr,
                              const int32_t* col, int32_t leaf_size, Tree* T);

@@ -14,6 +14,7 @@
 // last block to finish (ticket counter) adds them in block order.
 #include <algorithm>
 #include <cmath>
+#include <vector>
 
 #include "factor.cuh"
 
@@ -291,11 +292,56 @@ ndhss_status gmres_one(const FactorData& F, const int32_t* rowptr, const int32_t
         return NDHSS_OK;
     };
 
+    ndhss_gmres_stats S{};
+    // optional CUDA-event timing of every apply and sparse product
+    std::vector<cudaEvent_t> ev_apply, ev_spmv;
+    auto event_pair = [&](std::vector<cudaEvent_t>& v) -> ndhss_status {
+        cudaEvent_t a, b2;
+        NDHSS_CUDA_TRY(cudaEventCreate(&a));
+        NDHSS_CUDA_TRY(cudaEventCreate(&b2));
+        v.push_back(a);
+        v.push_back(b2);
+        return NDHSS_OK;
+    };
+    auto timed_apply = [&](const V* in, V* outv) -> ndhss_status {
+        ndhss_status r2;
+        if (o.timing) {
+            if ((r2 = event_pair(ev_apply))) return r2;
+            cudaEventRecord(ev_apply[ev_apply.size() - 2], st);
+        }
+        if ((r2 = apply_device(F, 1, in, n, outv, n, awork, st))) return r2;
+        if (o.timing) cudaEventRecord(ev_apply.back(), st);
+        S.napply++;
+        return NDHSS_OK;
+    };
+    auto timed_spmv = [&](const V* in, V* outv) -> ndhss_status {
+        ndhss_status r2;
+        if (o.timing) {
+            if ((r2 = event_pair(ev_spmv))) return r2;
+            cudaEventRecord(ev_spmv[ev_spmv.size() - 2], st);
+        }
+        if ((r2 = spmv_launch<V>(n, nnz, rowptr, col, vals, in, outv, st))) return r2;
+        if (o.timing) cudaEventRecord(ev_spmv.back(), st);
+        S.nspmv++;
+        return NDHSS_OK;
+    };
+    auto collect = [&]() {
+        if (!o.timing) return;
+        cudaStreamSynchronize(st);
+        float ms;
+        for (size_t i = 0; i + 1 < ev_apply.size(); i += 2)
+            if (cudaEventElapsedTime(&ms, ev_apply[i], ev_apply[i + 1]) == cudaSuccess) S.apply_ms += ms;
+        for (size_t i = 0; i + 1 < ev_spmv.size(); i += 2)
+            if (cudaEventElapsedTime(&ms, ev_spmv[i], ev_spmv[i + 1]) == cudaSuccess) S.spmv_ms += ms;
+        for (auto e : ev_apply) cudaEventDestroy(e);
+        for (auto e : ev_spmv) cudaEventDestroy(e);
+        ev_apply.clear();
+        ev_spmv.clear();
+    };
     nrm2_kernel<V><<<RB, RT, 0, st>>>(n, b, dpart, nrm, counter);
     NDHSS_LAUNCH_CHECK("nrm2_kernel");
     if ((rc = read_scalars(nrm, sizeof(double), hb))) return rc;
     const double bnorm = sqrt(hb[0]);
-    ndhss_gmres_stats S{};
     if (bnorm == 0.0) {
         S.converged = 1;
         if (stats) *stats = S;
@@ -305,21 +351,24 @@ ndhss_status gmres_one(const FactorData& F, const int32_t* rowptr, const int32_t
     int its = 0, cycles = 0;
     double last_res = 1.0;
     while (true) {
-        if ((rc = spmv_launch<V>(n, nnz, rowptr, col, vals, x, t, st))) return rc;
+        if ((rc = timed_spmv(x, t))) return rc;
         residual_kernel<V><<<eb, 256, 0, st>>>(n, b, t, r);
+        NDHSS_LAUNCH_CHECK("residual_kernel");
         nrm2_kernel<V><<<RB, RT, 0, st>>>(n, r, dpart, nrm, counter);
-        NDHSS_LAUNCH_CHECK("residual/nrm2");
+        NDHSS_LAUNCH_CHECK("nrm2_kernel");
         if ((rc = read_scalars(nrm, sizeof(double), hb))) return rc;
         const double rel = sqrt(hb[0]) / bnorm;
         S.true_relres = rel;
         if (rel <= o.tol) { S.converged = 1; break; }
         if (its >= o.maxit) break;
         ++cycles;
-        if ((rc = apply_device(F, 1, r, n, w, n, awork, st))) return rc;
+        if ((rc = timed_apply(r, w))) return rc;
         nrm2_kernel<V><<<RB, RT, 0, st>>>(n, w, dpart, nrm, counter);
+        NDHSS_LAUNCH_CHECK("nrm2_kernel");
         cycle_init_kernel<V><<<1, 1, 0, st>>>(nrm, g, R, stt);
+        NDHSS_LAUNCH_CHECK("cycle_init_kernel");
         scale_kernel<V><<<eb, 256, 0, st>>>(n, w, Vb, &stt->scal[0]);
-        NDHSS_LAUNCH_CHECK("cycle start");
+        NDHSS_LAUNCH_CHECK("scale_kernel");
         if (zbnorm < 0) {
             if ((rc = read_scalars(stt, sizeof(GmState), hb))) return rc;
             zbnorm = hb[3];
@@ -328,26 +377,34 @@ ndhss_status gmres_one(const FactorData& F, const int32_t* rowptr, const int32_t
         int jend = 0;
         for (int j = 0; j < R; ++j) {
             V* vj = Vb + (int64_t)j * ldv;
-            if ((rc = spmv_launch<V>(n, nnz, rowptr, col, vals, vj, t, st))) return rc;
-            if ((rc = apply_device(F, 1, t, n, w, n, awork, st))) return rc;
+            if ((rc = timed_spmv(vj, t))) return rc;
+            if ((rc = timed_apply(t, w))) return rc;
             ++its;
             mdot_kernel<V><<<RB, RT, 0, st>>>(n, Vb, ldv, j + 1, w, part, h1, counter);
+            NDHSS_LAUNCH_CHECK("mdot_kernel");
             maxpy_kernel<V><<<eb, 256, 0, st>>>(n, w, Vb, ldv, j + 1, h1, -1.0);
+            NDHSS_LAUNCH_CHECK("maxpy_kernel");
             mdot_kernel<V><<<RB, RT, 0, st>>>(n, Vb, ldv, j + 1, w, part, h2, counter);
+            NDHSS_LAUNCH_CHECK("mdot_kernel");
             maxpy_kernel<V><<<eb, 256, 0, st>>>(n, w, Vb, ldv, j + 1, h2, -1.0);
+            NDHSS_LAUNCH_CHECK("maxpy_kernel");
             nrm2_kernel<V><<<RB, RT, 0, st>>>(n, w, dpart, nrm, counter);
+            NDHSS_LAUNCH_CHECK("nrm2_kernel");
             arnoldi_step_kernel<V><<<1, 1, 0, st>>>(j, H, R + 1, h1, h2, nrm, g, cs, sn, stt);
+            NDHSS_LAUNCH_CHECK("arnoldi_step_kernel");
             scale_kernel<V><<<eb, 256, 0, st>>>(n, w, Vb + (int64_t)(j + 1) * ldv, &stt->scal[0]);
-            NDHSS_LAUNCH_CHECK("arnoldi step");
+            NDHSS_LAUNCH_CHECK("scale_kernel");
             if ((rc = read_scalars(stt, sizeof(GmState), hb))) return rc;
             jend = j + 1;
             last_res = hb[1] / zbnorm;
             if (last_res <= o.tol || hb[2] == 0.0 || its >= o.maxit) break;
         }
         hsolve_kernel<V><<<1, 1, 0, st>>>(jend, H, R + 1, g, yv);
+        NDHSS_LAUNCH_CHECK("hsolve_kernel");
         maxpy_kernel<V><<<eb, 256, 0, st>>>(n, x, Vb, ldv, jend, yv, 1.0);
-        NDHSS_LAUNCH_CHECK("cycle end");
+        NDHSS_LAUNCH_CHECK("maxpy_kernel");
     }
+    collect();
     S.iters = its;
     S.cycles = cycles;
     S.precond_relres = last_res;
@@ -398,7 +455,7 @@ ndhss_status ndhss_gmres(const ndhss_factorization* fh, const int32_t* d_rowptr,
         return set_error(NDHSS_ERR_INVALID_ARG, "ndhss_gmres: bad argument");
     const FactorData& F = fh->f;
     if (ldb < F.n || ldx < F.n) return set_error(NDHSS_ERR_INVALID_ARG, "ndhss_gmres: leading dimension < n");
-    ndhss_gmres_opts o{30, 300, 1e-8};
+    ndhss_gmres_opts o{30, 300, 1e-8, 0, 0};
     if (opts) o = *opts;
     if (o.restart < 1 || o.restart > KMAX - 1 || o.maxit < 0 || !(o.tol >= 0))
         return set_error(NDHSS_ERR_INVALID_ARG, "ndhss_gmres: need 1 <= restart <= %d, maxit >= 0, tol >= 0", KMAX - 1);

@@ -22,7 +22,7 @@ NODE_FIELDS = ("level", "parent", "child0", "child1", "i_off", "m_i", "b_off", "
 STATUS = {0: "OK", 1: "INVALID_ARG", 2: "OOM", 3: "SINGULAR", 4: "RANK_CAP", 5: "NOT_CONVERGED",
           6: "TIMEOUT", 7: "CUDA", 8: "INTERNAL"}
 
-EXPORTED = ("ndhss_version", "ndhss_last_error", "ndhss_build_tree", "ndhss_tree_sizes", "ndhss_tree_export",
+EXPORTED = ("ndhss_version", "ndhss_last_error", "ndhss_kernel_launches", "ndhss_build_tree", "ndhss_tree_sizes", "ndhss_tree_export",
             "ndhss_tree_destroy", "ndhss_factor", "ndhss_factor_stats_get", "ndhss_factor_get_block",
             "ndhss_factor_destroy", "ndhss_apply", "ndhss_spmv", "ndhss_gmres")
 
@@ -36,29 +36,38 @@ class NdhssError(RuntimeError):
 class FactorOpts(C.Structure):
     _fields_ = [("prec", C.c_int32), ("hss_levels", C.c_int32), ("eps_hss", C.c_double), ("beta", C.c_int32),
                 ("k0", C.c_int32), ("r", C.c_int32), ("rank_cap", C.c_int32), ("panel", C.c_int32),
-                ("seed", C.c_uint64)]
+                ("seed", C.c_uint64), ("timing", C.c_int32), ("pad", C.c_int32)]
 
 
 class GmresOpts(C.Structure):
-    _fields_ = [("restart", C.c_int32), ("maxit", C.c_int32), ("tol", C.c_double)]
+    _fields_ = [("restart", C.c_int32), ("maxit", C.c_int32), ("tol", C.c_double), ("timing", C.c_int32),
+                ("pad", C.c_int32)]
 
 
 class GmresStats(C.Structure):
     _fields_ = [("iters", C.c_int32), ("cycles", C.c_int32), ("converged", C.c_int32), ("pad", C.c_int32),
-                ("true_relres", C.c_double), ("precond_relres", C.c_double)]
+                ("true_relres", C.c_double), ("precond_relres", C.c_double), ("napply", C.c_int32),
+                ("nspmv", C.c_int32), ("apply_ms", C.c_double), ("spmv_ms", C.c_double)]
 
     def as_dict(self):
         return dict(iters=self.iters, cycles=self.cycles, converged=bool(self.converged),
-                    true_relres=self.true_relres, precond_relres=self.precond_relres)
+                    true_relres=self.true_relres, precond_relres=self.precond_relres, napply=self.napply,
+                    nspmv=self.nspmv, apply_ms=self.apply_ms, spmv_ms=self.spmv_ms)
 
 
 class FactorStats(C.Structure):
     _fields_ = [("n", C.c_int64), ("nnodes", C.c_int32), ("depth", C.c_int32), ("front_elems", C.c_int64),
                 ("apply_bytes", C.c_int64), ("factor_bytes", C.c_int64), ("factor_ms", C.c_double),
-                ("kmax", C.c_int32), ("prec", C.c_int32)]
+                ("kmax", C.c_int32), ("prec", C.c_int32), ("launches", C.c_int64),
+                ("class_ms", C.c_double * 8), ("class_launches", C.c_int64 * 8), ("update_flops", C.c_double)]
+
+    CLASSES = ("assemble", "scatter", "panel", "prep", "update", "finalize")
 
     def as_dict(self):
-        return {k: getattr(self, k) for k, _ in self._fields_}
+        d = {k: getattr(self, k) for k, _ in self._fields_ if k not in ("class_ms", "class_launches")}
+        d["class_ms"] = {c: self.class_ms[i] for i, c in enumerate(self.CLASSES)}
+        d["class_launches"] = {c: self.class_launches[i] for i, c in enumerate(self.CLASSES)}
+        return d
 
 
 _lib = None
@@ -77,6 +86,7 @@ def load(path: str | None = None):
     sig = {
         "ndhss_version": (C.c_char_p, []),
         "ndhss_last_error": (C.c_char_p, []),
+        "ndhss_kernel_launches": (C.c_int64, []),
         "ndhss_build_tree": (I32, [I32, P, P, P, I32, C.POINTER(C.c_void_p)]),
         "ndhss_tree_sizes": (I32, [P, C.POINTER(I32), C.POINTER(I32), C.POINTER(I64), C.POINTER(I64)]),
         "ndhss_tree_export": (I32, [P] + [P] * 8),
@@ -182,8 +192,8 @@ class Factor:
 
 
 def make_factor_opts(prec=NDHSS_FP64, hss_levels=-1, eps_hss=1e-6, beta=64, k0=32, r=16, rank_cap=512,
-                     panel=0, seed=0) -> FactorOpts:
-    return FactorOpts(prec, hss_levels, eps_hss, beta, k0, r, rank_cap, panel, seed)
+                     panel=0, seed=0, timing=False) -> FactorOpts:
+    return FactorOpts(prec, hss_levels, eps_hss, beta, k0, r, rank_cap, panel, seed, int(bool(timing)), 0)
 
 
 def ndhss_factor(tree: Tree, vtype: int, d_rowptr, d_col, d_vals, opts: FactorOpts | None = None,
@@ -226,12 +236,16 @@ def ndhss_spmv(n: int, vtype: int, d_rowptr, d_col, d_vals, d_x, d_y, stream=Non
     return d_y
 
 
+def ndhss_kernel_launches() -> int:
+    return int(load().ndhss_kernel_launches())
+
+
 def ndhss_gmres(f: Factor, d_rowptr, d_col, d_vals, b, x, restart=30, maxit=300, tol=1e-8, stream=None,
-                raise_on_nonconvergence=False):
+                raise_on_nonconvergence=False, timing=False):
     """Solve A x = b; b, x are (n,) torch CUDA tensors or numpy arrays.  Returns the stats dict."""
     n = f.n
     st = GmresStats()
-    o = GmresOpts(int(restart), int(maxit), float(tol))
+    o = GmresOpts(int(restart), int(maxit), float(tol), int(bool(timing)), 0)
     code = load().ndhss_gmres(f.handle, _ptr(d_rowptr), _ptr(d_col), _ptr(d_vals), 1, _ptr(b), n, _ptr(x), n,
                               C.byref(o), C.byref(st), _stream(stream))
     if code == 5 and not raise_on_nonconvergence:
