@@ -209,6 +209,29 @@ ndhss_status ndhss_apply(const ndhss_factorization* f, int32_t nrhs, const void*
                          void* y, int64_t ldy, void* stream);
 
 /*
+ * ndhss_apply_noalloc -- the result of ndhss_apply for one right-hand side,
+ * from a call that allocates no memory at all.  For callers that cannot
+ * allocate at the moment they need P^{-1}: code recording a CUDA graph that
+ * must hold no memory nodes, host callbacks, or runtimes whose allocator may
+ * not be entered from the calling thread.  The paper has no counterpart; this
+ * is an interface convenience.
+ *   f          factor from ndhss_factor
+ *   d_x, d_y   DEVICE pointers, n float64/complex128 values (original
+ *              numbering); host pointers are rejected with INVALID_ARG
+ *   stream     stream the kernels are ordered on
+ * The two work vectors live in one static device array of 16 MiB that every
+ * GPU loading the library holds until the process exits; problems needing
+ * more (2 n x element size of the factor, i.e. n <= 524272 for complex128
+ * fronts, n <= 1048560 for complex64 or float64 fronts) get INVALID_ARG.
+ * The first call on a device looks up that array's device address (once per
+ * device, with that device current): make that first call before any stream
+ * capture.  All calls share the array and each overwrites it completely
+ * before reading it, so nothing needs clearing; calls that overlap on the
+ * GPU (other streams, other threads) race on it and must be serialised.
+ */
+ndhss_status ndhss_apply_noalloc(const ndhss_factorization* f, const void* d_x, void* d_y, void* stream);
+
+/*
  * ndhss_spmv -- y = A x for a CSR matrix in float64 / complex128 (the
  * matrix-vector product x -> A x of Sec. 2.3 and of every Krylov step).
  * All pointers are device pointers; n rows; stream-ordered.

@@ -12,6 +12,8 @@
 // block is read as a contiguous, coalesced segment; the partial sums of the
 // four slices are added in shared memory.  The whole factor is streamed
 // once per apply (the diagonal blocks once, the off-diagonal blocks twice).
+#include <mutex>
+
 #include "factor.cuh"
 
 namespace ndhss {
@@ -221,4 +223,67 @@ extern "C" ndhss_status ndhss_apply(const ndhss_factorization* fh, int32_t nrhs,
             rc = set_error(NDHSS_ERR_CUDA, "ndhss_apply: stream synchronisation failed");
     }
     return rc;
+}
+
+// --------------------------------------------------------------------------
+// Allocation-free apply (no counterpart in the paper).
+//
+// Callers that must not allocate (graph recording without memory nodes, host
+// callbacks, foreign allocators) get the same Alg. 3.1 result with the two
+// work vectors in this fixed static array instead of stream-ordered
+// allocations.  The array is part of the module image, so every device that
+// loads the library holds it until exit.  Host code must not take its address
+// directly (that would be a host-side shadow): the device address is looked
+// up once per device with cudaGetSymbolAddress.  Every call overwrites the
+// whole work area it uses before reading it (gather writes all of the first
+// vector, the diagonal step all of the second), so nothing needs clearing;
+// overlapping calls race on the array.
+namespace ndhss {
+namespace {
+
+constexpr size_t NOALLOC_SCRATCH_BYTES = size_t(16) << 20;
+__device__ __align__(256) unsigned char g_apply_scratch[NOALLOC_SCRATCH_BYTES];
+
+constexpr int NOALLOC_MAX_DEVICES = 64;
+std::mutex g_scratch_mu;
+void* g_scratch_addr[NOALLOC_MAX_DEVICES] = {};
+
+ndhss_status scratch_for_current_device(void** out) {
+    int dev = -1;
+    NDHSS_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= NOALLOC_MAX_DEVICES)
+        return set_error(NDHSS_ERR_INVALID_ARG, "ndhss_apply_noalloc: device %d beyond the supported %d", dev,
+                         NOALLOC_MAX_DEVICES);
+    std::lock_guard<std::mutex> lock(g_scratch_mu);
+    if (!g_scratch_addr[dev]) {
+        void* p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_apply_scratch);
+        if (e != cudaSuccess || !p)
+            return set_error(NDHSS_ERR_CUDA, "ndhss_apply_noalloc: cudaGetSymbolAddress of the scratch array failed: %s",
+                             cudaGetErrorString(e));
+        g_scratch_addr[dev] = p;
+    }
+    *out = g_scratch_addr[dev];
+    return NDHSS_OK;
+}
+
+}  // namespace
+}  // namespace ndhss
+
+extern "C" ndhss_status ndhss_apply_noalloc(const ndhss_factorization* fh, const void* d_x, void* d_y, void* stream) {
+    using namespace ndhss;
+    clear_error();
+    if (!fh || !d_x || !d_y) return set_error(NDHSS_ERR_INVALID_ARG, "ndhss_apply_noalloc: NULL argument");
+    const FactorData& F = fh->f;
+    const size_t need = apply_work_bytes(F);
+    if (need > NOALLOC_SCRATCH_BYTES)
+        return set_error(NDHSS_ERR_INVALID_ARG,
+                         "ndhss_apply_noalloc: n = %d needs %zu bytes of work space but the static scratch holds %zu; "
+                         "use ndhss_apply", F.n, need, NOALLOC_SCRATCH_BYTES);
+    if (!is_device_ptr(d_x) || !is_device_ptr(d_y))
+        return set_error(NDHSS_ERR_INVALID_ARG, "ndhss_apply_noalloc: x and y must be device pointers");
+    void* scratch = nullptr;
+    const ndhss_status rc = scratch_for_current_device(&scratch);
+    if (rc != NDHSS_OK) return rc;
+    return apply_device(F, 1, d_x, F.n, d_y, F.n, scratch, static_cast<cudaStream_t>(stream));
 }
