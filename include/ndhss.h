@@ -82,6 +82,12 @@ typedef struct {
     double tol;                 /* relative residual target, e.g. 1e-8                 */
     int32_t timing;             /* 1: time every apply / SpMV with CUDA events         */
     int32_t pad;
+    double inner;               /* a cycle ends at ||P^{-1} r|| <= inner tol ||P^{-1} b||;
+                                   0.1 = one decade below tol, as Sec. 4 stops at 1e-9 */
+    double cycle_rtol;          /* a cycle also ends once its residual estimate fell by
+                                   this factor (what one reduced-precision apply can
+                                   resolve); < 0 = automatic: 1e-4 for FP32 fronts,
+                                   0 (off) for FP64 fronts                            */
 } ndhss_gmres_opts;
 
 typedef struct {
@@ -243,14 +249,14 @@ ndhss_status ndhss_spmv(int32_t n, int32_t vtype, const int32_t* d_rowptr, const
  * ndhss_gmres -- solve A x = b with restarted GMRES on P^{-1} A x = P^{-1} b
  * (Eq. 1.2, Sec. 4): x0 = 0, Arnoldi by classical Gram-Schmidt applied
  * twice in float64, complex Givens rotations, a cycle ends when
- * ||P^{-1} r|| <= tol ||P^{-1} b|| or after `restart` steps; a solve is
+ * ||P^{-1} r|| <= inner tol ||P^{-1} b|| or after `restart` steps; a solve is
  * converged only when the float64 true residual ||b - A x|| / ||b|| <= tol,
  * checked after every cycle (restarts act as iterative refinement).
  *   f         factor (the preconditioner)
  *   d_rowptr, d_col, d_vals  device CSR of A (original numbering, vtype of f)
  *   nrhs      right-hand sides, solved one after another
  *   b, x      n x nrhs column-major (ldb, ldx >= n), device or host pointers
- *   opts      NULL = restart 30, maxit 300, tol 1e-8
+ *   opts      NULL = restart 30, maxit 300, tol 1e-8, inner 0.1, cycle_rtol auto
  *   stats     host array of nrhs entries (may be NULL)
  * Returns NOT_CONVERGED if any right-hand side missed tol (x still written).
  * Synchronises the stream once per Arnoldi step (to read the residual).

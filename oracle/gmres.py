@@ -9,8 +9,16 @@ not fixed by the paper for these workloads):
 
 * x0 = 0; Arnoldi with classical Gram-Schmidt applied twice (CGS2);
   complex Givens rotations G = [[c, s], [-conj(s), c]] with real c.
-* A cycle ends when |g_{j+1}| <= tol * ||P^{-1} b|| (inner test), after
-  ``restart`` steps, on breakdown, or at ``maxit`` total steps.
+* A cycle ends when |g_{j+1}| <= inner * tol * ||P^{-1} b|| (inner test),
+  after ``restart`` steps, on breakdown, or at ``maxit`` total steps.  The
+  default inner = 0.1 follows Sec. 4, which stops on a preconditioned
+  residual one decade below the accuracy it reports (1e-9); it keeps a
+  preconditioner applied in reduced precision from ending cycles on an
+  estimate that the float64 residual does not yet meet.
+* Optionally (cycle_rtol > 0) a cycle also ends once |g_{j+1}| <= cycle_rtol *
+  beta_cycle: with a preconditioner applied in reduced precision the Krylov
+  estimate is not trustworthy beyond what one application resolves, and the
+  float64 restart performs the refinement instead.
 * After each cycle the float64 true residual ||b - A x|| / ||b|| is checked;
   the solve is converged only when it is <= tol.  Otherwise the method
   restarts from the current x (so the outer loop acts as iterative
@@ -45,7 +53,8 @@ def givens(a, b):
     return abs(a) / t, (a / abs(a)) * np.conj(b) / t
 
 
-def gmres(A, b, prec, tol: float = 1e-8, restart: int = 30, maxit: int = 300) -> GmresResult:
+def gmres(A, b, prec, tol: float = 1e-8, restart: int = 30, maxit: int = 300, inner: float = 0.1,
+          cycle_rtol: float = 0.0) -> GmresResult:
     """Solve A x = b; ``prec(v)`` applies P^{-1}; ``A`` supports ``A @ v``."""
     dtype = np.result_type(A.dtype, b.dtype, np.float64)
     n = b.shape[0]
@@ -101,7 +110,7 @@ def gmres(A, b, prec, tol: float = 1e-8, restart: int = 30, maxit: int = 300) ->
             res = abs(g[j + 1]) / zbnorm
             hist.append(float(res))
             j_end = j + 1
-            if res <= tol or hn == 0 or its >= maxit:
+            if res <= inner * tol or abs(g[j + 1]) <= cycle_rtol * beta or hn == 0 or its >= maxit:
                 break
         y = sla.solve_triangular(H[:j_end, :j_end], g[:j_end], lower=False)
         x = x + V[:, :j_end] @ y

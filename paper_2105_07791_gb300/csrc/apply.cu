@@ -7,11 +7,8 @@
 //   scatter/cast  out(perm) = z converted back to float64
 //
 // Work is split into tasks of APPLY_ROWS output rows of one node; the tasks
-// of a level (or of the diagonal step) form one launch.  Inside a task the
-// 256 threads hold 64 rows x 4 column slices, so each column of a stored
-// block is read as a contiguous, coalesced segment; the partial sums of the
-// four slices are added in shared memory.  The whole factor is streamed
-// once per apply (the diagonal blocks once, the off-diagonal blocks twice).
+// of a level (or of the diagonal step) form one launch.  The whole factor is
+// streamed once per apply: A_ii^{-1}, L and R of every node once each.
 #include <mutex>
 
 #include "factor.cuh"
@@ -20,7 +17,6 @@ namespace ndhss {
 namespace {
 
 constexpr int AT = 256;
-constexpr int SLICES = AT / APPLY_ROWS;
 
 __device__ __forceinline__ int nf(const int32_t* node, int s, int f) { return node[s * NODE_NF + f]; }
 
@@ -36,13 +32,50 @@ __global__ void scatter_cast_kernel(int n, const int32_t* __restrict__ perm, con
     if (i < n) out[perm[i]] = to_val(z[i]);
 }
 
+// Rows [r0, r0 + 64) of (block A, column-major, leading dimension lda) times
+// the vector xs (shared memory): 8 warps take every 8th column, each lane
+// owns rows r0 + lane and r0 + lane + 32, and four columns are in flight per
+// step, so a thread keeps eight independent loads outstanding and a warp
+// reads each column segment as one contiguous 64-row access.  The eight warp
+// partial sums are added in shared memory; lanes of warp 0 and 1 return the
+// results for rows r0 + tid (tid < 64).
+constexpr int AW = AT / 32;
+
 template <typename T>
-__device__ __forceinline__ T slice_sum(T acc, T (*red)[APPLY_ROWS], int rl, int sl) {
-    red[sl][rl] = acc;
+__device__ __forceinline__ T gemv_rows64(const T* __restrict__ A, int64_t lda, int rows, int cols, int r0,
+                                         const T* __restrict__ xs, T (*red)[APPLY_ROWS]) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int ra = r0 + lane, rb = r0 + lane + 32;
+    const bool va = ra < rows, vb = rb < rows;
+    T acc0 = zero<T>(), acc1 = zero<T>();
+    int c = warp;
+    for (; c + 3 * AW < cols; c += 4 * AW) {
+        T a[4], b[4], x[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const T* col = A + (int64_t)(c + u * AW) * lda;
+            a[u] = va ? col[ra] : zero<T>();
+            b[u] = vb ? col[rb] : zero<T>();
+            x[u] = xs[c + u * AW];
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            acc0 = fmac(a[u], x[u], acc0);
+            acc1 = fmac(b[u], x[u], acc1);
+        }
+    }
+    for (; c < cols; c += AW) {
+        const T* col = A + (int64_t)c * lda;
+        const T xv = xs[c];
+        if (va) acc0 = fmac(col[ra], xv, acc0);
+        if (vb) acc1 = fmac(col[rb], xv, acc1);
+    }
+    red[warp][lane] = acc0;
+    red[warp][lane + 32] = acc1;
     __syncthreads();
     T sum = zero<T>();
-    if (sl == 0)
-        for (int q = 0; q < SLICES; ++q) sum += red[q][rl];
+    if (threadIdx.x < APPLY_ROWS)
+        for (int w = 0; w < AW; ++w) sum += red[w][threadIdx.x];
     return sum;
 }
 
@@ -53,21 +86,16 @@ upsweep_kernel(const int32_t* __restrict__ tasks, const int32_t* __restrict__ no
                const int32_t* __restrict__ blist, const int32_t* __restrict__ sigma, const T* __restrict__ front,
                T* __restrict__ y) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ T red[SLICES][APPLY_ROWS];
+    __shared__ T red[AW][APPLY_ROWS];
     T* ys = reinterpret_cast<T*>(smem_raw);
     const int s = tasks[2 * blockIdx.x], j0 = tasks[2 * blockIdx.x + 1];
     const int m_i = nf(node, s, 5), m_b = nf(node, s, 7), i_off = nf(node, s, 4), b_off = nf(node, s, 6);
     const int64_t m = (int64_t)m_i + m_b;
     for (int c = threadIdx.x; c < m_i; c += AT) ys[c] = y[i_off + sigma[i_off + c]];
     __syncthreads();
-    const int rl = threadIdx.x % APPLY_ROWS, sl = threadIdx.x / APPLY_ROWS;
-    const int j = j0 + rl;
-    const T* F = front + foff[s] + m_i;
-    T acc = zero<T>();
-    if (j < m_b)
-        for (int c = sl; c < m_i; c += SLICES) acc = fmac(F[c * m + j], ys[c], acc);
-    const T sum = slice_sum(acc, red, rl, sl);
-    if (sl == 0 && j < m_b) {
+    const T sum = gemv_rows64(front + foff[s] + m_i, m, m_b, m_i, j0, ys, red);
+    const int j = j0 + threadIdx.x;
+    if (threadIdx.x < APPLY_ROWS && j < m_b) {
         const int g = blist[b_off + j];
         y[g] = y[g] - sum;
     }
@@ -79,21 +107,16 @@ __global__ void __launch_bounds__(AT)
 diag_kernel(const int32_t* __restrict__ tasks, const int32_t* __restrict__ node, const int64_t* __restrict__ foff,
             const int32_t* __restrict__ sigma, const T* __restrict__ front, const T* __restrict__ y, T* __restrict__ z) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ T red[SLICES][APPLY_ROWS];
+    __shared__ T red[AW][APPLY_ROWS];
     T* ys = reinterpret_cast<T*>(smem_raw);
     const int s = tasks[2 * blockIdx.x], i0 = tasks[2 * blockIdx.x + 1];
     const int m_i = nf(node, s, 5), i_off = nf(node, s, 4);
     const int64_t m = (int64_t)m_i + nf(node, s, 7);
     for (int c = threadIdx.x; c < m_i; c += AT) ys[c] = y[i_off + sigma[i_off + c]];
     __syncthreads();
-    const int rl = threadIdx.x % APPLY_ROWS, sl = threadIdx.x / APPLY_ROWS;
-    const int i = i0 + rl;
-    const T* F = front + foff[s];
-    T acc = zero<T>();
-    if (i < m_i)
-        for (int c = sl; c < m_i; c += SLICES) acc = fmac(F[c * m + i], ys[c], acc);
-    const T sum = slice_sum(acc, red, rl, sl);
-    if (sl == 0 && i < m_i) z[i_off + i] = sum;
+    const T sum = gemv_rows64(front + foff[s], m, m_i, m_i, i0, ys, red);
+    const int i = i0 + threadIdx.x;
+    if (threadIdx.x < APPLY_ROWS && i < m_i) z[i_off + i] = sum;
 }
 
 // z(I^s) += R z(B^s)   (Eq. 3.3b)
@@ -102,21 +125,16 @@ __global__ void __launch_bounds__(AT)
 downsweep_kernel(const int32_t* __restrict__ tasks, const int32_t* __restrict__ node, const int64_t* __restrict__ foff,
                  const int32_t* __restrict__ blist, const T* __restrict__ front, T* __restrict__ z) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ T red[SLICES][APPLY_ROWS];
+    __shared__ T red[AW][APPLY_ROWS];
     T* zb = reinterpret_cast<T*>(smem_raw);
     const int s = tasks[2 * blockIdx.x], i0 = tasks[2 * blockIdx.x + 1];
     const int m_i = nf(node, s, 5), m_b = nf(node, s, 7), i_off = nf(node, s, 4), b_off = nf(node, s, 6);
     const int64_t m = (int64_t)m_i + m_b;
     for (int j = threadIdx.x; j < m_b; j += AT) zb[j] = z[blist[b_off + j]];
     __syncthreads();
-    const int rl = threadIdx.x % APPLY_ROWS, sl = threadIdx.x / APPLY_ROWS;
-    const int i = i0 + rl;
-    const T* F = front + foff[s] + (int64_t)m_i * m;
-    T acc = zero<T>();
-    if (i < m_i)
-        for (int j = sl; j < m_b; j += SLICES) acc = fmac(F[j * m + i], zb[j], acc);
-    const T sum = slice_sum(acc, red, rl, sl);
-    if (sl == 0 && i < m_i) z[i_off + i] = z[i_off + i] + sum;
+    const T sum = gemv_rows64(front + foff[s] + (int64_t)m_i * m, m, m_i, m_b, i0, zb, red);
+    const int i = i0 + threadIdx.x;
+    if (threadIdx.x < APPLY_ROWS && i < m_i) z[i_off + i] = z[i_off + i] + sum;
 }
 
 template <typename T, typename V>

@@ -33,7 +33,7 @@ constexpr int PANEL_THREADS = 512;
 constexpr int PREP_WARPS = 8;
 constexpr int GT = 64;          // gemm tile
 constexpr int GK = 16;          // gemm k chunk
-constexpr size_t PANEL_SMEM_BUDGET = 200 * 1024;
+constexpr size_t PANEL_SMEM_MAX = 220 * 1024;      // panel values + one int per candidate row
 
 __device__ __forceinline__ int nf(const int32_t* node, int s, int f) { return node[s * NODE_NF + f]; }
 
@@ -103,16 +103,26 @@ __global__ void scatter_entries_kernel(const int32_t* __restrict__ lev, const in
 }
 
 // ---------------------------------------------------------------- panel
+// One CTA per front.  The candidate rows [k0, m_i) of the kb panel columns
+// are swept in shared memory with the in-place Gauss-Jordan exchange step
+// and partial pivoting; below each pivot this is exactly the LU elimination,
+// so the interchanges are those of row-pivoted LU, and afterwards the top
+// kb x kb block holds (A_PP)^{-1} of the interchanged pivot block.  The pivot
+// search of the next column rides on the update of the current one, so a
+// pivot costs two barriers.  Outputs per front: the interchanges (ipiv), the
+// net row map they induce (<= 2 kb rows) and Ainv.
 template <typename T>
 __global__ void __launch_bounds__(PANEL_THREADS)
 panel_factor_kernel(const int32_t* __restrict__ lev, const int32_t* __restrict__ node,
                     const int64_t* __restrict__ foff, const T* __restrict__ front, int32_t* __restrict__ ipiv,
-                    T* __restrict__ ainv_buf, int k0, int kb, DevStatus* status) {
+                    T* __restrict__ ainv_buf, int32_t* __restrict__ swapmap, int k0, int kb, DevStatus* status) {
     using real = typename Tr<T>::real;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ int s_piv[KBMAX];
     __shared__ real s_val[32];
     __shared__ int s_idx[32];
+    __shared__ T s_prow[KBMAX];
+    __shared__ int s_na;
     const int s = lev[blockIdx.x];
     const int m_i = nf(node, s, 5);
     if (k0 >= m_i) return;
@@ -120,18 +130,22 @@ panel_factor_kernel(const int32_t* __restrict__ lev, const int32_t* __restrict__
     const int kbp = min(kb, m_i - k0);
     const int mc = m_i - k0;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
-    T* P = reinterpret_cast<T*>(smem_raw);       // mc x kbp, ld mc
+    T* P = reinterpret_cast<T*>(smem_raw);                       // mc x kbp, ld mc
+    int* idx = reinterpret_cast<int*>(P + (size_t)mc * kbp);     // row arrangement, mc
     const T* F = front + foff[s];
-    for (int idx = tid; idx < mc * kbp; idx += blockDim.x) {
-        const int r = idx % mc, c = idx / mc;
-        P[idx] = F[(int64_t)(k0 + c) * m + k0 + r];
+    for (int q = tid; q < mc * kbp; q += blockDim.x) {
+        const int r = q % mc, c = q / mc;
+        P[q] = F[(int64_t)(k0 + c) * m + k0 + r];
     }
+    for (int r = tid; r < mc; r += blockDim.x) idx[r] = r;
+    if (tid == 0) s_na = 0;
     __syncthreads();
-    for (int c = 0; c < kbp; ++c) {
+    // pivot search of column 0
+    {
         real best = real(-1);
         int bi = INT_MAX;
-        for (int r = c + tid; r < mc; r += blockDim.x) {
-            const real v = abs1(P[c * mc + r]);
+        for (int r = tid; r < mc; r += blockDim.x) {
+            const real v = abs1(P[r]);
             if (v > best) { best = v; bi = r; }
         }
         for (int off = 16; off; off >>= 1) {
@@ -140,115 +154,114 @@ panel_factor_kernel(const int32_t* __restrict__ lev, const int32_t* __restrict__
             if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
         }
         if (lane == 0) { s_val[warp] = best; s_idx[warp] = bi; }
-        __syncthreads();
+    }
+    __syncthreads();
+    for (int c = 0; c < kbp; ++c) {
         if (warp == 0) {
-            best = lane < nwarps ? s_val[lane] : real(-1);
-            bi = lane < nwarps ? s_idx[lane] : INT_MAX;
+            // finish the search, interchange rows c and p, form the new pivot row
+            real best = lane < nwarps ? s_val[lane] : real(-1);
+            int bi = lane < nwarps ? s_idx[lane] : INT_MAX;
             for (int off = 16; off; off >>= 1) {
                 const real ov = __shfl_down_sync(0xffffffffu, best, off);
                 const int oi = __shfl_down_sync(0xffffffffu, bi, off);
                 if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
             }
-            if (lane == 0) s_piv[c] = (bi == INT_MAX) ? c : bi;   // all-NaN column: keep the diagonal
-        }
-        __syncthreads();
-        const int p = s_piv[c];
-        if (p != c) {
-            for (int cc = tid; cc < kbp; cc += blockDim.x) {
-                const T t = P[cc * mc + c];
-                P[cc * mc + c] = P[cc * mc + p];
-                P[cc * mc + p] = t;
+            int p = __shfl_sync(0xffffffffu, bi, 0);
+            if (p == INT_MAX) p = c;                              // all-NaN column: keep the diagonal
+            T piv = P[c * mc + p];
+            if (!(abs1(piv) > real(0))) {                         // exact zero (or NaN) pivot
+                piv = one<T>();
+                if (lane == 0 && atomicCAS(&status->code, 0, (int)NDHSS_ERR_SINGULAR) == 0) status->node = s;
+            }
+            const T pinv = recip(piv);
+            __syncwarp();
+            if (lane < kbp) {
+                const T a = P[lane * mc + c];
+                const T b = P[lane * mc + p];
+                P[lane * mc + c] = b;
+                if (p != c) P[lane * mc + p] = a;
+                s_prow[lane] = (lane == c) ? pinv : -(b * pinv);
+            }
+            if (lane == 0) {
+                s_piv[c] = p;
+                const int t = idx[c];
+                idx[c] = idx[p];
+                idx[p] = t;
             }
         }
         __syncthreads();
-        T piv = P[c * mc + c];
-        if (!(abs1(piv) > real(0))) {     // exact zero (or NaN) pivot
-            piv = one<T>();
-            if (tid == 0) {
-                P[c * mc + c] = piv;
-                if (atomicCAS(&status->code, 0, (int)NDHSS_ERR_SINGULAR) == 0) status->node = s;
+        // exchange step on every candidate row; search of column c + 1 on the fly
+        real best = real(-1);
+        int bi = INT_MAX;
+        const bool next = c + 1 < kbp;
+        for (int r = tid; r < mc; r += blockDim.x) {
+            if (r == c) {
+                for (int j = 0; j < kbp; ++j) P[j * mc + r] = s_prow[j];
+                continue;
+            }
+            const T a = P[c * mc + r];
+            for (int j = 0; j < kbp; ++j)
+                if (j != c) P[j * mc + r] = fmac(a, s_prow[j], P[j * mc + r]);
+            P[c * mc + r] = a * s_prow[c];
+            if (next && r > c) {
+                const real v = abs1(P[(c + 1) * mc + r]);
+                if (v > best) { best = v; bi = r; }
             }
         }
-        const T pinv = recip(piv);
-        for (int r = c + 1 + tid; r < mc; r += blockDim.x) {
-            const T l = P[c * mc + r] * pinv;
-            P[c * mc + r] = l;
-            for (int cc = c + 1; cc < kbp; ++cc) P[cc * mc + r] = fmac(-l, P[cc * mc + c], P[cc * mc + r]);
+        if (next) {
+            for (int off = 16; off; off >>= 1) {
+                const real ov = __shfl_down_sync(0xffffffffu, best, off);
+                const int oi = __shfl_down_sync(0xffffffffu, bi, off);
+                if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
+            }
+            if (lane == 0) { s_val[warp] = best; s_idx[warp] = bi; }
         }
         __syncthreads();
     }
     const int i_off = nf(node, s, 4);
     if (tid < kbp) ipiv[i_off + k0 + tid] = k0 + s_piv[tid];
-    // Ainv = (L U)^{-1} of the kbp x kbp pivot block: column j by thread j
     T* Ai = ainv_buf + (size_t)blockIdx.x * KBMAX * KBMAX;
-    if (tid < kbp) {
-        const int j = tid;
-        T y[KBMAX];
-#pragma unroll
-        for (int i = 0; i < KBMAX; ++i) {
-            if (i < kbp) {
-                T acc = (i == j) ? one<T>() : zero<T>();
-                for (int l = 0; l < i; ++l) acc = fmac(-P[l * mc + i], y[l], acc);
-                y[i] = acc;
-            }
-        }
-#pragma unroll
-        for (int i = KBMAX - 1; i >= 0; --i) {
-            if (i < kbp) {
-                T acc = y[i];
-                for (int l = i + 1; l < kbp; ++l) acc = fmac(-P[l * mc + i], y[l], acc);
-                y[i] = acc * recip(P[i * mc + i]);
-            }
-        }
-#pragma unroll
-        for (int i = 0; i < KBMAX; ++i)
-            if (i < kbp) Ai[j * KBMAX + i] = y[i];
+    for (int q = tid; q < kbp * kbp; q += blockDim.x) {
+        const int i = q % kbp, j = q / kbp;
+        Ai[j * KBMAX + i] = P[j * mc + i];
     }
+    // net row map of the interchanges: row k0 + r receives the old row k0 + idx[r]
+    int32_t* sm = swapmap + (size_t)blockIdx.x * (4 * KBMAX + 1);
+    for (int r = tid; r < mc; r += blockDim.x) {
+        if (idx[r] != r) {
+            const int a = atomicAdd(&s_na, 1);
+            sm[1 + a] = k0 + r;
+            sm[1 + 2 * KBMAX + a] = k0 + idx[r];
+        }
+    }
+    __syncthreads();
+    if (tid == 0) sm[0] = s_na;
 }
 
 template <typename T>
 __global__ void __launch_bounds__(PREP_WARPS * 32)
 panel_prep_kernel(const int32_t* __restrict__ lev, const int32_t* __restrict__ node,
-                  const int64_t* __restrict__ foff, T* __restrict__ front, const int32_t* __restrict__ ipiv,
+                  const int64_t* __restrict__ foff, T* __restrict__ front, const int32_t* __restrict__ swapmap,
                   const T* __restrict__ ainv_buf, T* __restrict__ cbuf, T* __restrict__ zbuf,
                   const int64_t* __restrict__ woff, int k0, int kb) {
     __shared__ T s_ai[KBMAX * KBMAX];
     __shared__ int s_rows[2 * KBMAX], s_org[2 * KBMAX];
-    __shared__ int s_na;
     const int li = blockIdx.y;
     const int s = lev[li];
     const int m_i = nf(node, s, 5);
     if (k0 >= m_i) return;
     const int64_t m = m_i + nf(node, s, 7);
     const int kbp = min(kb, m_i - k0);
-    const int i_off = nf(node, s, 4);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const T* Ai = ainv_buf + (size_t)li * KBMAX * KBMAX;
-    for (int idx = tid; idx < KBMAX * KBMAX; idx += blockDim.x) s_ai[idx] = Ai[idx];
-    if (tid == 0) {
-        // net effect of the interchange sequence on the (at most 2 kb) rows it touches
-        int na = 0;
-        for (int c = 0; c < kbp; ++c) {
-            const int rr[2] = {k0 + c, ipiv[i_off + k0 + c]};
-            for (int q = 0; q < 2; ++q) {
-                int a = 0;
-                while (a < na && s_rows[a] != rr[q]) ++a;
-                if (a == na) { s_rows[na] = rr[q]; s_org[na] = rr[q]; ++na; }
-            }
-        }
-        for (int c = 0; c < kbp; ++c) {
-            const int r1 = k0 + c, r2 = ipiv[i_off + k0 + c];
-            int a1 = 0, a2 = 0;
-            while (s_rows[a1] != r1) ++a1;
-            while (s_rows[a2] != r2) ++a2;
-            const int t = s_org[a1];
-            s_org[a1] = s_org[a2];
-            s_org[a2] = t;
-        }
-        s_na = na;
+    for (int q = tid; q < KBMAX * KBMAX; q += blockDim.x) s_ai[q] = Ai[q];
+    const int32_t* sm = swapmap + (size_t)li * (4 * KBMAX + 1);
+    const int na = sm[0];
+    for (int a = tid; a < na; a += blockDim.x) {
+        s_rows[a] = sm[1 + a];
+        s_org[a] = sm[1 + 2 * KBMAX + a];
     }
     __syncthreads();
-    const int na = s_na;
     T* F = front + foff[s];
     T* C = cbuf + woff[li] * KBMAX;     // m x kbp, ld m
     T* Z = zbuf + woff[li] * KBMAX;     // kbp x m, ld KBMAX
@@ -366,7 +379,7 @@ __global__ void finalize_sigma_kernel(const int32_t* __restrict__ lev, const int
 
 int choose_kb(int64_t mc, size_t esize, int panel_opt) {
     int kb = KBMAX;
-    while (kb > 1 && (size_t)mc * kb * esize > PANEL_SMEM_BUDGET) kb >>= 1;
+    while (kb > 1 && (size_t)mc * (kb * esize + sizeof(int)) > PANEL_SMEM_MAX) kb >>= 1;
     if (panel_opt > 0) kb = std::min(kb, panel_opt);
     return kb;
 }
@@ -374,7 +387,7 @@ int choose_kb(int64_t mc, size_t esize, int panel_opt) {
 template <typename T>
 ndhss_status set_smem_attrs() {
     NDHSS_CUDA_TRY(cudaFuncSetAttribute(panel_factor_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        (int)(PANEL_SMEM_BUDGET + 1024)));
+                                        (int)PANEL_SMEM_MAX));
     return NDHSS_OK;
 }
 
@@ -431,7 +444,8 @@ ndhss_status factor_run(FactorData& F, const Tree& t, const V* d_vals, const int
                         const int32_t* d_erow, const int32_t* d_ecol, const int32_t* d_eidx,
                         const int32_t* d_fsrc, const int64_t* d_poff, const int32_t* d_lev,
                         const std::vector<int64_t>& lev_off, const int64_t* d_woff, T* d_cbuf, T* d_zbuf,
-                        T* d_ainv, DevStatus* d_status, int panel_opt, LaunchTimer& tm, cudaStream_t st) {
+                        T* d_ainv, int32_t* d_swapmap, DevStatus* d_status, int panel_opt, LaunchTimer& tm,
+                        cudaStream_t st) {
     ndhss_status rc = set_smem_attrs<T>();
     if (rc != NDHSS_OK) return rc;
     T* front = static_cast<T*>(F.d_front);
@@ -463,17 +477,20 @@ ndhss_status factor_run(FactorData& F, const Tree& t, const V* d_vals, const int
         const int pgx = (int)std::min<int64_t>((mmax + PREP_WARPS - 1) / PREP_WARPS, 1024);
         for (int64_t k0 = 0; k0 < mimax;) {
             const int kb = choose_kb(mimax - k0, sizeof(T), panel_opt);
-            const size_t smem = (size_t)(mimax - k0) * kb * sizeof(T);
-            if (smem > PANEL_SMEM_BUDGET)
+            const size_t smem = (size_t)(mimax - k0) * kb * sizeof(T) + (size_t)(mimax - k0) * sizeof(int);
+            if (smem > PANEL_SMEM_MAX)
                 return set_error(NDHSS_ERR_INVALID_ARG, "front with %lld interior unknowns exceeds the panel kernel's shared memory",
                                  (long long)(mimax - k0));
             tm.begin();
-            panel_factor_kernel<T><<<L, PANEL_THREADS, smem, st>>>(lev, F.d_node, F.d_foff, front, F.d_ipiv, d_ainv,
-                                                                   (int)k0, kb, d_status);
+            // one thread per candidate row up to 512: small fronts get small CTAs, so a level of
+            // thousands of leaves runs in one wave instead of repeating its pivot chain per wave
+            const int pthreads = (int)std::min<int64_t>(PANEL_THREADS, std::max<int64_t>(64, (mimax - k0 + 31) / 32 * 32));
+            panel_factor_kernel<T><<<L, pthreads, smem, st>>>(lev, F.d_node, F.d_foff, front, F.d_ipiv, d_ainv,
+                                                              d_swapmap, (int)k0, kb, d_status);
             NDHSS_LAUNCH_CHECK("panel_factor_kernel");
             tm.end(2);
             tm.begin();
-            panel_prep_kernel<T><<<dim3(pgx, L), PREP_WARPS * 32, 0, st>>>(lev, F.d_node, F.d_foff, front, F.d_ipiv,
+            panel_prep_kernel<T><<<dim3(pgx, L), PREP_WARPS * 32, 0, st>>>(lev, F.d_node, F.d_foff, front, d_swapmap,
                                                                           d_ainv, d_cbuf, d_zbuf, woff, (int)k0, kb);
             NDHSS_LAUNCH_CHECK("panel_prep_kernel");
             tm.end(3);
@@ -608,12 +625,13 @@ static ndhss_status factor_impl(const ndhss_tree* th, int32_t vtype, const int32
     int32_t *d_eoff = nullptr, *d_erow = nullptr, *d_ecol = nullptr, *d_eidx = nullptr, *d_fsrc = nullptr, *d_lev = nullptr;
     int64_t *d_poff = nullptr, *d_woff = nullptr;
     void *d_cbuf = nullptr, *d_zbuf = nullptr, *d_ainv = nullptr;
+    int32_t* d_swapmap = nullptr;
     DevStatus* d_status = nullptr;
     int64_t tmp_bytes = 0;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     auto cleanup = [&]() {
         cudaFree(d_eoff); cudaFree(d_erow); cudaFree(d_ecol); cudaFree(d_eidx); cudaFree(d_fsrc); cudaFree(d_lev);
-        cudaFree(d_poff); cudaFree(d_woff); cudaFree(d_cbuf); cudaFree(d_zbuf); cudaFree(d_ainv); cudaFree(d_status);
+        cudaFree(d_poff); cudaFree(d_woff); cudaFree(d_cbuf); cudaFree(d_zbuf); cudaFree(d_ainv); cudaFree(d_swapmap); cudaFree(d_status);
         if (e0) cudaEventDestroy(e0);
         if (e1) cudaEventDestroy(e1);
     };
@@ -649,6 +667,7 @@ static ndhss_status factor_impl(const ndhss_tree* th, int32_t vtype, const int32
         !dalloc(&d_cbuf, (size_t)wmax * KBMAX * esize, &tmp_bytes) ||
         !dalloc(&d_zbuf, (size_t)wmax * KBMAX * esize, &tmp_bytes) ||
         !dalloc(&d_ainv, (size_t)lmax * KBMAX * KBMAX * esize, &tmp_bytes) ||
+        !dalloc((void**)&d_swapmap, (size_t)lmax * (4 * KBMAX + 1) * sizeof(int32_t), &tmp_bytes) ||
         !dalloc((void**)&d_status, sizeof(DevStatus), &tmp_bytes)) {
         cleanup();
         ndhss_factor_destroy(h);
@@ -664,18 +683,18 @@ static ndhss_status factor_impl(const ndhss_tree* th, int32_t vtype, const int32
     NDHSS_CUDA_TRY(cudaEventRecord(e0, st));
     if (!cplx && fp64)
         rc = factor_run<double, double>(F, t, (const double*)d_vals, d_eoff, d_erow, d_ecol, d_eidx, d_fsrc, d_poff, d_lev,
-                                        lev_off, d_woff, (double*)d_cbuf, (double*)d_zbuf, (double*)d_ainv, d_status,
+                                        lev_off, d_woff, (double*)d_cbuf, (double*)d_zbuf, (double*)d_ainv, d_swapmap, d_status,
                                         o.panel, tm, st);
     else if (!cplx)
         rc = factor_run<float, double>(F, t, (const double*)d_vals, d_eoff, d_erow, d_ecol, d_eidx, d_fsrc, d_poff, d_lev,
-                                       lev_off, d_woff, (float*)d_cbuf, (float*)d_zbuf, (float*)d_ainv, d_status,
+                                       lev_off, d_woff, (float*)d_cbuf, (float*)d_zbuf, (float*)d_ainv, d_swapmap, d_status,
                                        o.panel, tm, st);
     else if (fp64)
         rc = factor_run<c128, c128>(F, t, (const c128*)d_vals, d_eoff, d_erow, d_ecol, d_eidx, d_fsrc, d_poff, d_lev,
-                                    lev_off, d_woff, (c128*)d_cbuf, (c128*)d_zbuf, (c128*)d_ainv, d_status, o.panel, tm, st);
+                                    lev_off, d_woff, (c128*)d_cbuf, (c128*)d_zbuf, (c128*)d_ainv, d_swapmap, d_status, o.panel, tm, st);
     else
         rc = factor_run<c64, c128>(F, t, (const c128*)d_vals, d_eoff, d_erow, d_ecol, d_eidx, d_fsrc, d_poff, d_lev,
-                                   lev_off, d_woff, (c64*)d_cbuf, (c64*)d_zbuf, (c64*)d_ainv, d_status, o.panel, tm, st);
+                                   lev_off, d_woff, (c64*)d_cbuf, (c64*)d_zbuf, (c64*)d_ainv, d_swapmap, d_status, o.panel, tm, st);
     if (rc == NDHSS_OK) {
         cudaEventRecord(e1, st);
         DevStatus hs{};
