@@ -111,7 +111,7 @@ __global__ void scatter_entries_kernel(const int32_t* __restrict__ lev, const in
 // search of the next column rides on the update of the current one, so a
 // pivot costs two barriers.  Outputs per front: the interchanges (ipiv), the
 // net row map they induce (<= 2 kb rows) and Ainv.
-template <typename T>
+template <typename T, int KB>
 __global__ void __launch_bounds__(PANEL_THREADS)
 panel_factor_kernel(const int32_t* __restrict__ lev, const int32_t* __restrict__ node,
                     const int64_t* __restrict__ foff, const T* __restrict__ front, int32_t* __restrict__ ipiv,
@@ -123,6 +123,7 @@ panel_factor_kernel(const int32_t* __restrict__ lev, const int32_t* __restrict__
     __shared__ int s_idx[32];
     __shared__ T s_prow[KBMAX];
     __shared__ int s_na;
+    for (int j = threadIdx.x; j < KBMAX; j += blockDim.x) s_prow[j] = zero<T>();
     const int s = lev[blockIdx.x];
     const int m_i = nf(node, s, 5);
     if (k0 >= m_i) return;
@@ -190,23 +191,34 @@ panel_factor_kernel(const int32_t* __restrict__ lev, const int32_t* __restrict__
             }
         }
         __syncthreads();
-        // exchange step on every candidate row; search of column c + 1 on the fly
+        // exchange step on every candidate row (one panel row in registers per
+        // step, all loads issued before the independent updates); search of
+        // column c + 1 on the fly
         real best = real(-1);
         int bi = INT_MAX;
         const bool next = c + 1 < kbp;
+        const T* pr = s_prow;            // pivot row, read as a shared-memory broadcast
         for (int r = tid; r < mc; r += blockDim.x) {
             if (r == c) {
-                for (int j = 0; j < kbp; ++j) P[j * mc + r] = s_prow[j];
+#pragma unroll
+                for (int j = 0; j < KB; ++j)
+                    if (j < kbp) P[j * mc + r] = pr[j];
                 continue;
             }
+            T v[KB];
+#pragma unroll
+            for (int j = 0; j < KB; ++j) v[j] = (j < kbp) ? P[j * mc + r] : zero<T>();
             const T a = P[c * mc + r];
-            for (int j = 0; j < kbp; ++j)
-                if (j != c) P[j * mc + r] = fmac(a, s_prow[j], P[j * mc + r]);
-            P[c * mc + r] = a * s_prow[c];
-            if (next && r > c) {
-                const real v = abs1(P[(c + 1) * mc + r]);
-                if (v > best) { best = v; bi = r; }
+            real nv = real(-1);
+#pragma unroll
+            for (int j = 0; j < KB; ++j) {
+                v[j] = (j == c) ? a * pr[j] : fmac(a, pr[j], v[j]);
+                if (j == c + 1) nv = abs1(v[j]);
             }
+#pragma unroll
+            for (int j = 0; j < KB; ++j)
+                if (j < kbp) P[j * mc + r] = v[j];
+            if (next && r > c && nv > best) { best = nv; bi = r; }
         }
         if (next) {
             for (int off = 16; off; off >>= 1) {
@@ -380,14 +392,18 @@ __global__ void finalize_sigma_kernel(const int32_t* __restrict__ lev, const int
 int choose_kb(int64_t mc, size_t esize, int panel_opt) {
     int kb = KBMAX;
     while (kb > 1 && (size_t)mc * (kb * esize + sizeof(int)) > PANEL_SMEM_MAX) kb >>= 1;
-    if (panel_opt > 0) kb = std::min(kb, panel_opt);
+    if (panel_opt > 0)
+        while (kb > panel_opt) kb >>= 1;     // powers of two only (the panel kernel is templated on it)
     return kb;
 }
 
 template <typename T>
 ndhss_status set_smem_attrs() {
-    NDHSS_CUDA_TRY(cudaFuncSetAttribute(panel_factor_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        (int)PANEL_SMEM_MAX));
+    void (*kernels[])(const int32_t*, const int32_t*, const int64_t*, const T*, int32_t*, T*, int32_t*, int, int,
+                      DevStatus*) = {panel_factor_kernel<T, 1>, panel_factor_kernel<T, 2>, panel_factor_kernel<T, 4>,
+                                     panel_factor_kernel<T, 8>, panel_factor_kernel<T, 16>, panel_factor_kernel<T, 32>};
+    for (auto k : kernels)
+        NDHSS_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PANEL_SMEM_MAX));
     return NDHSS_OK;
 }
 
@@ -485,8 +501,16 @@ ndhss_status factor_run(FactorData& F, const Tree& t, const V* d_vals, const int
             // one thread per candidate row up to 512: small fronts get small CTAs, so a level of
             // thousands of leaves runs in one wave instead of repeating its pivot chain per wave
             const int pthreads = (int)std::min<int64_t>(PANEL_THREADS, std::max<int64_t>(64, (mimax - k0 + 31) / 32 * 32));
-            panel_factor_kernel<T><<<L, pthreads, smem, st>>>(lev, F.d_node, F.d_foff, front, F.d_ipiv, d_ainv,
-                                                              d_swapmap, (int)k0, kb, d_status);
+            switch (kb) {
+#define NDHSS_PANEL(KBV)                                                                                          \
+    case KBV:                                                                                                   \
+        panel_factor_kernel<T, KBV><<<L, pthreads, smem, st>>>(lev, F.d_node, F.d_foff, front, F.d_ipiv, d_ainv, \
+                                                               d_swapmap, (int)k0, kb, d_status);             \
+        break;
+                NDHSS_PANEL(1) NDHSS_PANEL(2) NDHSS_PANEL(4) NDHSS_PANEL(8) NDHSS_PANEL(16) NDHSS_PANEL(32)
+#undef NDHSS_PANEL
+                default: return set_error(NDHSS_ERR_INTERNAL, "panel width %d is not a power of two <= 32", kb);
+            }
             NDHSS_LAUNCH_CHECK("panel_factor_kernel");
             tm.end(2);
             tm.begin();
