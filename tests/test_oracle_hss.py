@@ -1,0 +1,143 @@
+"""Pins of the oracle's HSS machinery (Sec. 2.1-2.3, App. A) and of the
+compressed factorization (Alg. 3.4)."""
+import os
+
+import numpy as np
+import pytest
+
+from ndhss_inputs import helmholtz_impedance, poisson_dirichlet
+from oracle.frontal import apply_inverse, factor_dense
+from oracle.gmres import gmres
+from oracle.hss import (HSS, apply_compressed, cluster_tree, factor_compressed, gaussian, hss_compress,
+                        hss_dense, hss_matvec, lowrank_rows, philox4x32_10, row_id)
+from oracle.tree import build_tree
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def test_philox_known_answers():
+    for line in open(os.path.join(GOLDEN, "philox4x32_10_kat.txt")):
+        if line.startswith("#") or not line.strip():
+            continue
+        v = [int(t, 16) for t in line.split()]
+        out = philox4x32_10(np.array([v[:4]], dtype=np.uint32), (v[4], v[5]))[0]
+        assert [int(x) for x in out] == v[6:]
+
+
+def test_gaussian_moments_and_determinism():
+    G = gaussian(400, 50, seed=7, stream=3)
+    assert abs(G.mean()) < 0.02 and abs(G.std() - 1.0) < 0.02
+    assert np.array_equal(G, gaussian(400, 50, seed=7, stream=3))
+    assert not np.array_equal(G, gaussian(400, 50, seed=7, stream=4))
+    # column-major element order: a taller matrix extends, it does not reshuffle, the first column
+    assert np.array_equal(gaussian(400, 1, 7, 3)[:, 0], G[:, 0])
+
+
+def test_cluster_tree_fig4_split_and_leaf_size():
+    T = cluster_tree(300, 130, 40)
+    assert (T[0].lo, T[0].hi) == (0, 300)
+    c1, c2 = T[0].children
+    assert (T[c1].lo, T[c1].hi, T[c2].lo, T[c2].hi) == (0, 130, 130, 300)
+    for c in T:
+        if c.children:
+            a, b = T[c.children[0]], T[c.children[1]]
+            assert a.lo == c.lo and a.hi == b.lo and b.hi == c.hi
+        else:
+            assert c.size <= 40
+
+
+def _random_hss(n, top, beta, k, seed, cplx=True):
+    rng = np.random.default_rng(seed)
+    T = cluster_tree(n, top, beta)
+    H = HSS(n=n, tree=T, dtype=np.complex128 if cplx else np.float64)
+    z = (lambda *s: rng.standard_normal(s) + 1j * rng.standard_normal(s)) if cplx else (lambda *s: rng.standard_normal(s))
+    for i, c in enumerate(T):
+        if i == 0:
+            continue
+        if not c.children:
+            H.U[i] = z(c.size, k)
+            D = z(c.size, c.size)
+            H.D[i] = D + D.T
+        else:
+            H.U[i] = z(2 * k, k)
+    for i, c in enumerate(T):
+        if c.children:
+            B = z(k, k)
+            H.B12[i], H.B21[i] = B, B.T
+    return H
+
+
+@pytest.mark.parametrize("cplx", [False, True])
+def test_exact_hss_recovery(cplx):
+    """A matrix with exact HSS rank k (Def. 2.3) is recovered to round-off by Alg. A.1."""
+    H = _random_hss(300, 130, 40, 6, seed=1, cplx=cplx)
+    A = hss_dense(H)
+    assert np.abs(A - A.T).max() <= 1e-10 * np.abs(A).max()
+    Hc = hss_compress(A, H.tree, 1e-10, k0=8, r=8, seed=3)
+    assert np.linalg.norm(hss_dense(Hc) - A) <= 1e-12 * np.linalg.norm(A)
+    assert Hc.kmax() <= 6
+
+
+def test_hss_matvec_is_linear_and_matches_dense():
+    H = _random_hss(200, 90, 30, 5, seed=2)
+    A = hss_dense(H)
+    rng = np.random.default_rng(0)
+    x = rng.standard_normal((200, 3))
+    assert np.allclose(hss_matvec(H, x), A @ x, rtol=1e-12, atol=1e-12 * np.abs(A).max())
+
+
+def test_row_id_skeleton_rows_exact():
+    rng = np.random.default_rng(4)
+    S = rng.standard_normal((60, 8)) @ rng.standard_normal((8, 40))
+    J, X = row_id(S, 1e-12, 40)
+    assert len(J) == 8
+    assert np.array_equal(X[J], np.eye(8))
+    assert np.linalg.norm(X @ S[J] - S) <= 1e-10 * np.linalg.norm(S)
+
+
+def test_estimator_detects_truncation():
+    """Too small a rank budget leaves an error the estimator (Eq. 2.7) sees."""
+    x = np.linspace(0, 1, 256)
+    A = 1.0 / (1.0 + 30 * np.abs(x[:, None] - x[None, :]))      # smooth, numerically low HSS rank
+    T = cluster_tree(256, 128, 32)
+    H = hss_compress(A, T, 1e-10, k0=4, r=4, seed=5, rank_cap=6)
+    err = np.linalg.norm(hss_dense(H) - A) / np.linalg.norm(A)
+    assert err > 1e-8                                   # truncated by the rank cap
+    H2 = hss_compress(A, T, 1e-8, k0=4, r=4, seed=5)
+    assert np.linalg.norm(hss_dense(H2) - A) <= 1e-7 * np.linalg.norm(A)
+    assert H2.rounds > 1                                # the adaptive loop grew the rank
+
+
+def test_lowrank_rows():
+    rng = np.random.default_rng(6)
+    R = (rng.standard_normal((120, 15)) @ rng.standard_normal((15, 90))).astype(complex)
+    lr = lowrank_rows(R, 1e-8, k0=8, r=8, seed=1)
+    assert lr.X.shape[1] == 15
+    assert np.linalg.norm(lr.matmat(np.eye(90)) - R) <= 1e-10 * np.linalg.norm(R)
+
+
+@pytest.fixture(scope="module", params=["poisson", "helmholtz"])
+def compressed(request):
+    P = poisson_dirichlet(64) if request.param == "poisson" else helmholtz_impedance(48, 2, 12.0, seed=3)
+    T = build_tree(P.coords, P.A.indptr, P.A.indices, 64)
+    return P, T, factor_compressed(T, P.A, hss_levels=3, eps=1e-6)
+
+
+def test_compressed_schur_within_tolerance(compressed):
+    """Every compressed S meets the HSS tolerance measured directly (Sec. 3.2)."""
+    P, T, fac = compressed
+    assert fac.hss
+    for s, H in fac.hss.items():
+        Se = fac.S_exact[s]
+        assert np.linalg.norm(hss_dense(H) - Se) <= 20 * 1e-6 * np.linalg.norm(Se), s
+
+
+def test_compressed_preconditioner_converges_fast(compressed):
+    P, T, fac = compressed
+    r = gmres(P.A, P.b, lambda v: apply_compressed(fac, v), tol=1e-8)
+    assert r.converged and r.iters <= 5
+    # without compression the same routine is the exact factorization
+    fac0 = factor_compressed(T, P.A, hss_levels=T.depth + 1)
+    assert not fac0.hss
+    x0 = apply_compressed(fac0, P.b)
+    assert np.allclose(x0, apply_inverse(factor_dense(T, P.A), P.b), rtol=1e-10, atol=1e-14)
