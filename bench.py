@@ -35,7 +35,7 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 METRIC = "solves/s and factor time at rel. residual 1e-8: mixed vs FP64 GPU path"
-WORKLOAD = dict(N=256, p=2, k=40.0, seed=0, leaf=64, tol=1e-8)
+WORKLOAD = dict(N=256, p=2, k=40.0, seed=0, leaf=64, tol=1e-8, hss_levels=4, eps_hss=1e-6, beta=64)
 
 # ncu DRAM traffic of the dominant kernel class, per launch, keyed by the
 # sha256 of the source file it was measured on (null once the source changes)
@@ -52,6 +52,8 @@ def _args():
     ap.add_argument("--only", choices=["mixed", "fp64"], help="time one precision only (profiling runs)")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer measurement (profiling runs)")
     ap.add_argument("--N", type=int, default=WORKLOAD["N"], help="cells per side (default: the benchmark workload)")
+    ap.add_argument("--hss-levels", type=int, default=WORKLOAD["hss_levels"],
+                    help="compress fronts on levels <= depth - this (Alg. 3.4); -1 = exact dense fronts")
     return ap.parse_args()
 
 
@@ -169,11 +171,14 @@ def run_gpu(a):
             torch.distributed.barrier()
         torch.cuda.synchronize()
 
+    def fopts(prec, timing=False):
+        return ndhss.make_factor_opts(prec=prec, timing=timing, hss_levels=a.hss_levels, eps_hss=WORKLOAD["eps_hss"],
+                                      beta=WORKLOAD["beta"], seed=WORKLOAD["seed"])
+
     def one_step(prec, timing):
         e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
         e0.record(stream)
-        f = ndhss.ndhss_factor(tree, M.vtype, M.rowptr, M.col, M.vals,
-                               ndhss.make_factor_opts(prec=prec, timing=timing), stream=stream)
+        f = ndhss.ndhss_factor(tree, M.vtype, M.rowptr, M.col, M.vals, fopts(prec, timing), stream=stream)
         e1.record(stream)
         st = ndhss.ndhss_gmres(f, M.rowptr, M.col, M.vals, b, x, tol=WORKLOAD["tol"], stream=stream, timing=timing)
         e2.record(stream)
@@ -211,7 +216,7 @@ def run_gpu(a):
             t = torch.tensor([tot_f, tot_s], device="cuda", dtype=torch.float64)
             torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
             tot_f, tot_s = float(t[0]), float(t[1])
-        results[name] = dict(factor_ms=tot_f / a.steps, solve_ms=tot_s / a.steps,
+        results[name] = dict(kmax=fstats["kmax"], factor_ms=tot_f / a.steps, solve_ms=tot_s / a.steps,
                              solves_per_s=world * a.steps / (tot_s / 1e3), iters=int(statistics.median(its)),
                              iters_all=its, true_relres=max(res), launches=launches, clocks=clk.summary(),
                              fstats=fstats, applies=applies, wall_s=wall)
@@ -223,8 +228,7 @@ def run_gpu(a):
                                   "iters": r["iters"], "launches": r["launches"], "fstats": r["fstats"]}), flush=True)
         return
     # end-to-end: the same solve through the C ABI with pinned host buffers
-    f = ndhss.ndhss_factor(tree, M.vtype, M.rowptr, M.col, M.vals, ndhss.make_factor_opts(prec=ndhss.NDHSS_FP32),
-                           stream=stream)
+    f = ndhss.ndhss_factor(tree, M.vtype, M.rowptr, M.col, M.vals, fopts(ndhss.NDHSS_FP32), stream=stream)
     bh = torch.from_numpy(np.ascontiguousarray(P.b)).pin_memory()
     xh = torch.zeros_like(bh).pin_memory()
     bn, xn = bh.numpy(), xh.numpy()
@@ -294,14 +298,18 @@ def run_gpu(a):
         "dtype": "c64 fronts (fp32) / c128 Krylov (fp64)",
         "data": "synthetic",
         "config": {"workload": _workload_name(P), "rhs_per_step": 1, "tol": WORKLOAD["tol"],
-                   "compression": "off (exact dense fronts)", "l2": "inputs exceed L2 (factor streamed from HBM)",
+                   "compression": (f"HSS on levels <= depth - {a.hss_levels}, eps {WORKLOAD['eps_hss']:g}, beta "
+                                   f"{WORKLOAD['beta']}" if a.hss_levels >= 0 else "off (exact dense fronts)"), "l2": "inputs exceed L2 (factor streamed from HBM)",
                    "parallelism": f"replicas x{world}"},
         "factor_ms": mx["factor_ms"],
         "solve_ms": mx["solve_ms"],
         "iters": mx["iters"],
+        "kmax": fs["kmax"],
+        "apply_bytes": fs["apply_bytes"],
         "true_relres": mx["true_relres"],
         "fp64": {"solves_per_s": fp["solves_per_s"], "factor_ms": fp["factor_ms"], "solve_ms": fp["solve_ms"],
-                 "iters": fp["iters"], "true_relres": fp["true_relres"]},
+                 "iters": fp["iters"], "true_relres": fp["true_relres"], "kmax": fp["kmax"],
+                 "apply_bytes": fp["fstats"]["apply_bytes"]},
         "mixed_over_fp64": {"solves_per_s": mx["solves_per_s"] / fp["solves_per_s"],
                             "factor_speedup": fp["factor_ms"] / mx["factor_ms"]},
         "apply_gbs": fs["apply_bytes"] / (ap_ms / max(ap_n, 1) / 1e3) / 1e9,

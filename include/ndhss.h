@@ -112,7 +112,8 @@ typedef struct {
     int32_t prec;
     int64_t launches;           /* kernels launched by the last ndhss_factor           */
     /* per kernel class (only when opts.timing = 1): summed device ms and launches;
-       classes 0 assemble, 1 scatter, 2 panel, 3 prep, 4 update, 5 finalize            */
+       classes 0 assemble, 1 scatter, 2 panel, 3 prep, 4 update, 5 finalize,
+       6 compression (S by Alg. A.1, R by a randomized row ID)                          */
     double class_ms[8];
     int64_t class_launches[8];
     double update_flops;        /* algorithmic real flops of the front updates         */
@@ -173,6 +174,12 @@ void ndhss_tree_destroy(ndhss_tree* t);
  * eliminated with partial pivoting restricted to I^sigma, giving
  * (A_ii)^{-1}, R = -(A_ii)^{-1} A_ib (Eq. 3.3b), L = -A_bi (A_ii)^{-1}
  * (Eq. 3.3a) and the Schur complement S (Eq. 3.5) passed to the parent.
+ * With opts.hss_levels >= 0, on levels <= L_HSS = depth - hss_levels the
+ * Schur complement is compressed by randomized adaptive HSS compression
+ * (Alg. A.1, cluster tree of Fig. 4, tolerance eps_hss, Philox samples from
+ * opts.seed) and the parent assembles the compressed S; strictly above L_HSS
+ * R is stored as a row interpolative decomposition R ~ X R(J, :) found by
+ * randomized range finding (Sec. 3.4) and L = R^T is used (A symmetric).
  *   t          tree from ndhss_build_tree (not modified, must outlive nothing)
  *   vtype      value type of A
  *   d_rowptr, d_col, d_vals  device CSR of A in the original numbering; only
@@ -193,6 +200,8 @@ ndhss_status ndhss_factor_stats_get(const ndhss_factorization* f, ndhss_factor_s
  * memory as float64/complex128 column-major with leading dimension ld:
  *   which 0: (A_ii)^{-1}   m_i x m_i        which 1: R   m_i x m_b (Eq. 3.3b)
  *   which 2: L   m_b x m_i (Eq. 3.3a)       which 3: S   m_b x m_b (Eq. 3.5)
+ * Compressed nodes return the stored approximations: S as handed to the
+ * parent (its HSS reconstruction), R = X R(J, :) and L = R^T.
  * Synchronises the factor's stream.  INVALID_ARG for a bad node, block or ld.
  */
 ndhss_status ndhss_factor_get_block(const ndhss_factorization* f, int32_t node, int32_t which,

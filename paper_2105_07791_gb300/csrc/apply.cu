@@ -20,6 +20,13 @@ constexpr int AT = 256;
 
 __device__ __forceinline__ int nf(const int32_t* node, int s, int f) { return node[s * NODE_NF + f]; }
 
+__device__ __forceinline__ double shfl_xor_t(double v, int o) { return __shfl_xor_sync(0xffffffffu, v, o); }
+__device__ __forceinline__ float shfl_xor_t(float v, int o) { return __shfl_xor_sync(0xffffffffu, v, o); }
+template <typename R>
+__device__ __forceinline__ Cx<R> shfl_xor_t(Cx<R> v, int o) {
+    return {__shfl_xor_sync(0xffffffffu, v.x, o), __shfl_xor_sync(0xffffffffu, v.y, o)};
+}
+
 template <typename T, typename V>
 __global__ void gather_cast_kernel(int n, const int32_t* __restrict__ perm, const V* __restrict__ x, T* __restrict__ y) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -137,6 +144,66 @@ downsweep_kernel(const int32_t* __restrict__ tasks, const int32_t* __restrict__ 
     if (threadIdx.x < APPLY_ROWS && i < m_i) z[i_off + i] = z[i_off + i] + sum;
 }
 
+
+// Low-rank levels (R ~ X R(J, :), X m_i x k, RJ k x m_b; L = R^T by symmetry):
+// one CTA per node.
+// up-sweep:   t = X^T y(I^s);  y(B^s) += RJ^T t
+template <typename T>
+__global__ void __launch_bounds__(AT)
+lr_upsweep_kernel(const int32_t* __restrict__ list, const int32_t* __restrict__ node, const uint64_t* __restrict__ lrp,
+                  const int32_t* __restrict__ lrk, const int32_t* __restrict__ blist, T* __restrict__ y) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* t = reinterpret_cast<T*>(smem_raw);
+    const int s = list[blockIdx.x];
+    const int m_i = nf(node, s, 5), m_b = nf(node, s, 7), i_off = nf(node, s, 4), b_off = nf(node, s, 6);
+    const int k = lrk[s];
+    const T* X = reinterpret_cast<const T*>(lrp[s]);
+    const T* RJ = X + (int64_t)m_i * k;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int a = warp; a < k; a += AW) {
+        T acc = zero<T>();
+        for (int i = lane; i < m_i; i += 32) acc = fmac(X[(int64_t)a * m_i + i], y[i_off + i], acc);
+        for (int o = 16; o; o >>= 1) acc = acc + shfl_xor_t(acc, o);
+        if (lane == 0) t[a] = acc;
+    }
+    __syncthreads();
+    for (int j = threadIdx.x; j < m_b; j += AT) {
+        T acc = zero<T>();
+        const T* col = RJ + (int64_t)j * k;
+        for (int a = 0; a < k; ++a) acc = fmac(col[a], t[a], acc);
+        const int g = blist[b_off + j];
+        y[g] = y[g] + acc;
+    }
+}
+
+// down-sweep: t = RJ z(B^s);  z(I^s) += X t
+template <typename T>
+__global__ void __launch_bounds__(AT)
+lr_downsweep_kernel(const int32_t* __restrict__ list, const int32_t* __restrict__ node, const uint64_t* __restrict__ lrp,
+                    const int32_t* __restrict__ lrk, const int32_t* __restrict__ blist, T* __restrict__ z) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int s = list[blockIdx.x];
+    const int m_i = nf(node, s, 5), m_b = nf(node, s, 7), i_off = nf(node, s, 4), b_off = nf(node, s, 6);
+    const int k = lrk[s];
+    T* zb = reinterpret_cast<T*>(smem_raw);
+    T* t = zb + m_b;
+    const T* X = reinterpret_cast<const T*>(lrp[s]);
+    const T* RJ = X + (int64_t)m_i * k;
+    for (int j = threadIdx.x; j < m_b; j += AT) zb[j] = z[blist[b_off + j]];
+    __syncthreads();
+    for (int a = threadIdx.x; a < k; a += AT) {
+        T acc = zero<T>();
+        for (int j = 0; j < m_b; ++j) acc = fmac(RJ[(int64_t)j * k + a], zb[j], acc);
+        t[a] = acc;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < m_i; i += AT) {
+        T acc = zero<T>();
+        for (int a = 0; a < k; ++a) acc = fmac(X[(int64_t)a * m_i + i], t[a], acc);
+        z[i_off + i] = z[i_off + i] + acc;
+    }
+}
+
 template <typename T, typename V>
 ndhss_status apply_run(const FactorData& F, int32_t nrhs, const V* x, int64_t ldx, V* y, int64_t ldy, T* w0, T* w1,
                        cudaStream_t st) {
@@ -150,10 +217,22 @@ ndhss_status apply_run(const FactorData& F, int32_t nrhs, const V* x, int64_t ld
     }
     if (smem_b > 48 * 1024)
         NDHSS_CUDA_TRY(cudaFuncSetAttribute(downsweep_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_b));
+    const size_t smem_k = (size_t)std::max(F.kmax, 1) * sizeof(T);
+    const size_t smem_kb = (size_t)(std::max(F.kmax, 1) + std::max(F.max_mb, 1)) * sizeof(T);
+    if (smem_kb > 48 * 1024)
+        NDHSS_CUDA_TRY(cudaFuncSetAttribute(lr_downsweep_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_kb));
     for (int r = 0; r < nrhs; ++r) {
         gather_cast_kernel<T, V><<<nb, 256, 0, st>>>(F.n, F.d_perm, x + r * ldx, w0);
         NDHSS_LAUNCH_CHECK("gather_cast_kernel");
         for (int l = F.depth; l >= 0; --l) {
+            if (l < F.L_hss && !F.lr_cnt.empty()) {
+                if (F.lr_cnt[l]) {
+                    lr_upsweep_kernel<T><<<(unsigned)F.lr_cnt[l], AT, smem_k, st>>>(F.d_lr_list + F.lr_off_l[l], F.d_node,
+                                                                                  F.d_lr_ptr, F.d_lr_k, F.d_blist, w0);
+                    NDHSS_LAUNCH_CHECK("lr_upsweep_kernel");
+                }
+                continue;
+            }
             if (F.up_cnt[l] == 0) continue;
             upsweep_kernel<T><<<(unsigned)F.up_cnt[l], AT, smem_i, st>>>(F.d_tasks + 2 * F.up_off[l], F.d_node, F.d_foff,
                                                                          F.d_blist, F.d_sigma, front, w0);
@@ -165,6 +244,14 @@ ndhss_status apply_run(const FactorData& F, int32_t nrhs, const V* x, int64_t ld
             NDHSS_LAUNCH_CHECK("diag_kernel");
         }
         for (int l = 0; l <= F.depth; ++l) {
+            if (l < F.L_hss && !F.lr_cnt.empty()) {
+                if (F.lr_cnt[l]) {
+                    lr_downsweep_kernel<T><<<(unsigned)F.lr_cnt[l], AT, smem_kb, st>>>(F.d_lr_list + F.lr_off_l[l], F.d_node,
+                                                                                     F.d_lr_ptr, F.d_lr_k, F.d_blist, w1);
+                    NDHSS_LAUNCH_CHECK("lr_downsweep_kernel");
+                }
+                continue;
+            }
             if (F.dn_cnt[l] == 0) continue;
             downsweep_kernel<T><<<(unsigned)F.dn_cnt[l], AT, smem_b, st>>>(F.d_tasks + 2 * F.dn_off[l], F.d_node, F.d_foff,
                                                                            F.d_blist, front, w1);

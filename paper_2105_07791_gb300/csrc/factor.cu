@@ -460,8 +460,9 @@ ndhss_status factor_run(FactorData& F, const Tree& t, const V* d_vals, const int
                         const int32_t* d_erow, const int32_t* d_ecol, const int32_t* d_eidx,
                         const int32_t* d_fsrc, const int64_t* d_poff, const int32_t* d_lev,
                         const std::vector<int64_t>& lev_off, const int64_t* d_woff, T* d_cbuf, T* d_zbuf,
-                        T* d_ainv, int32_t* d_swapmap, DevStatus* d_status, int panel_opt, LaunchTimer& tm,
-                        cudaStream_t st) {
+                        T* d_ainv, int32_t* d_swapmap, DevStatus* d_status, const ndhss_factor_opts& o,
+                        LaunchTimer& tm, cudaStream_t st) {
+    const int panel_opt = o.panel;
     ndhss_status rc = set_smem_attrs<T>();
     if (rc != NDHSS_OK) return rc;
     T* front = static_cast<T*>(F.d_front);
@@ -537,6 +538,13 @@ ndhss_status factor_run(FactorData& F, const Tree& t, const V* d_vals, const int
             tm.end(5);
             F.launches += 1;
         }
+        if (F.L_hss >= 0 && l <= F.L_hss) {
+            // Alg. 3.4 at and above the switching level: compress S (and R above it)
+            tm.begin();
+            ndhss_status rc2 = hss_compress_level(F, t, l, o, st);
+            if (rc2 != NDHSS_OK) return rc2;
+            tm.end(6);
+        }
     }
     return NDHSS_OK;
 }
@@ -560,8 +568,8 @@ static ndhss_status factor_impl(const ndhss_tree* th, int32_t vtype, const int32
     if (opts) o = *opts;
     if (o.prec != NDHSS_FP64 && o.prec != NDHSS_FP32 && o.prec != NDHSS_FP32_TF32)
         return set_error(NDHSS_ERR_INVALID_ARG, "ndhss_factor: bad precision %d", o.prec);
-    if (o.hss_levels >= 0)
-        return set_error(NDHSS_ERR_INVALID_ARG, "ndhss_factor: HSS compression is not available in this build");
+    if (o.hss_levels >= 0 && (!(o.eps_hss > 0) || o.beta < 1 || o.k0 < 1 || o.r < 1 || o.rank_cap < 1))
+        return set_error(NDHSS_ERR_INVALID_ARG, "ndhss_factor: compression needs eps_hss > 0 and beta, k0, r, rank_cap >= 1");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const bool cplx = vtype == NDHSS_C128;
     const bool fp64 = o.prec == NDHSS_FP64;
@@ -576,6 +584,7 @@ static ndhss_status factor_impl(const ndhss_tree* th, int32_t vtype, const int32
     F.depth = t.depth;
     F.esize = esize;
     F.node_info = t.node_info;
+    F.L_hss = (o.hss_levels >= 0) ? t.depth - o.hss_levels : -1;
     F.levels.assign(t.depth + 1, {});
     for (int s = 0; s < t.nnodes; ++s) F.levels[t.level(s)].push_back(s);
     F.foff.resize(t.nnodes);
@@ -708,17 +717,17 @@ static ndhss_status factor_impl(const ndhss_tree* th, int32_t vtype, const int32
     if (!cplx && fp64)
         rc = factor_run<double, double>(F, t, (const double*)d_vals, d_eoff, d_erow, d_ecol, d_eidx, d_fsrc, d_poff, d_lev,
                                         lev_off, d_woff, (double*)d_cbuf, (double*)d_zbuf, (double*)d_ainv, d_swapmap, d_status,
-                                        o.panel, tm, st);
+                                        o, tm, st);
     else if (!cplx)
         rc = factor_run<float, double>(F, t, (const double*)d_vals, d_eoff, d_erow, d_ecol, d_eidx, d_fsrc, d_poff, d_lev,
                                        lev_off, d_woff, (float*)d_cbuf, (float*)d_zbuf, (float*)d_ainv, d_swapmap, d_status,
-                                       o.panel, tm, st);
+                                       o, tm, st);
     else if (fp64)
         rc = factor_run<c128, c128>(F, t, (const c128*)d_vals, d_eoff, d_erow, d_ecol, d_eidx, d_fsrc, d_poff, d_lev,
-                                    lev_off, d_woff, (c128*)d_cbuf, (c128*)d_zbuf, (c128*)d_ainv, d_swapmap, d_status, o.panel, tm, st);
+                                    lev_off, d_woff, (c128*)d_cbuf, (c128*)d_zbuf, (c128*)d_ainv, d_swapmap, d_status, o, tm, st);
     else
         rc = factor_run<c64, c128>(F, t, (const c128*)d_vals, d_eoff, d_erow, d_ecol, d_eidx, d_fsrc, d_poff, d_lev,
-                                   lev_off, d_woff, (c64*)d_cbuf, (c64*)d_zbuf, (c64*)d_ainv, d_swapmap, d_status, o.panel, tm, st);
+                                   lev_off, d_woff, (c64*)d_cbuf, (c64*)d_zbuf, (c64*)d_ainv, d_swapmap, d_status, o, tm, st);
     if (rc == NDHSS_OK) {
         cudaEventRecord(e1, st);
         DevStatus hs{};
@@ -735,6 +744,27 @@ static ndhss_status factor_impl(const ndhss_tree* th, int32_t vtype, const int32
             F.factor_ms = ms;
             tm.collect(F);
         }
+    }
+    if (rc == NDHSS_OK && !F.lr_ptr.empty()) {
+        int64_t elems = 0;
+        for (int s = 0; s < t.nnodes; ++s) {
+            const int64_t mi = t.m_i(s), mb = t.m_b(s);
+            elems += mi * mi + (F.lr_ptr[s] ? 2 * (mi + mb) * (int64_t)F.lr_k[s] : 2 * mi * mb);
+        }
+        F.apply_bytes = elems * (int64_t)esize;
+        std::vector<int32_t> lst;
+        F.lr_off_l.assign(t.depth + 1, 0);
+        F.lr_cnt.assign(t.depth + 1, 0);
+        for (int l = 0; l <= t.depth; ++l) {
+            F.lr_off_l[l] = (int64_t)lst.size();
+            for (int s : F.levels[l])
+                if (F.lr_ptr[s] && F.lr_k[s] > 0) lst.push_back(s);
+            F.lr_cnt[l] = (int64_t)lst.size() - F.lr_off_l[l];
+        }
+        if (upload(&F.d_lr_ptr, F.lr_ptr.data(), F.lr_ptr.size(), &F.dev_bytes) != NDHSS_OK ||
+            upload(&F.d_lr_k, F.lr_k.data(), F.lr_k.size(), &F.dev_bytes) != NDHSS_OK ||
+            upload(&F.d_lr_list, lst.data(), lst.size(), &F.dev_bytes) != NDHSS_OK)
+            rc = set_error(NDHSS_ERR_OOM, "ndhss_factor: low-rank tables");
     }
     cleanup();
     if (rc != NDHSS_OK) {
@@ -791,6 +821,38 @@ static ndhss_status get_block_impl(const ndhss_factorization* fh, int32_t node, 
     const int64_t cols = (which == 0 || which == 2) ? mi : mb;
     if (ld < std::max<int64_t>(rows, 1)) return set_error(NDHSS_ERR_INVALID_ARG, "ndhss_factor_get_block: ld too small");
     if (rows == 0 || cols == 0) return NDHSS_OK;
+    if ((which == 1 || which == 2) && !F.lr_ptr.empty() && F.lr_ptr[node]) {
+        // low-rank R = X R(J, :) (m_i x k, k x m_b); L = R^T
+        const int64_t k = F.lr_k[node];
+        std::vector<unsigned char> lb((size_t)(mi * k + k * mb) * F.esize);
+        NDHSS_CUDA_TRY(cudaDeviceSynchronize());
+        if (!lb.empty())
+            NDHSS_CUDA_TRY(cudaMemcpy(lb.data(), reinterpret_cast<const void*>(F.lr_ptr[node]), lb.size(), cudaMemcpyDeviceToHost));
+        const bool cplx = F.vtype == NDHSS_C128;
+        for (int64_t j = 0; j < mb; ++j)
+            for (int64_t i = 0; i < mi; ++i) {
+                double re = 0, im = 0;
+                for (int64_t a = 0; a < k; ++a) {
+                    double xr, xi, rr, ri;
+                    const size_t xo = (size_t)(a * mi + i), ro = (size_t)(mi * k + j * k + a);
+                    if (!cplx && F.prec == NDHSS_FP64) { xr = ((double*)lb.data())[xo]; rr = ((double*)lb.data())[ro]; xi = ri = 0; }
+                    else if (!cplx) { xr = ((float*)lb.data())[xo]; rr = ((float*)lb.data())[ro]; xi = ri = 0; }
+                    else if (F.prec == NDHSS_FP64) {
+                        const c128 x = ((c128*)lb.data())[xo], r = ((c128*)lb.data())[ro];
+                        xr = x.x; xi = x.y; rr = r.x; ri = r.y;
+                    } else {
+                        const c64 x = ((c64*)lb.data())[xo], r = ((c64*)lb.data())[ro];
+                        xr = x.x; xi = x.y; rr = r.x; ri = r.y;
+                    }
+                    re += xr * rr - xi * ri;
+                    im += xr * ri + xi * rr;
+                }
+                const int64_t di = (which == 1) ? i : j, dj = (which == 1) ? j : i;
+                if (cplx) ((c128*)host_out)[dj * ld + di] = {re, im};
+                else ((double*)host_out)[dj * ld + di] = re;
+            }
+        return NDHSS_OK;
+    }
     std::vector<unsigned char> buf((size_t)(m * m) * F.esize);
     NDHSS_CUDA_TRY(cudaDeviceSynchronize());
     NDHSS_CUDA_TRY(cudaMemcpy(buf.data(), (const unsigned char*)F.d_front + (size_t)F.foff[node] * F.esize, buf.size(),
@@ -843,7 +905,7 @@ ndhss_status ndhss_factor_stats_get(const ndhss_factorization* fh, ndhss_factor_
     st->apply_bytes = F.apply_bytes;
     st->factor_bytes = F.dev_bytes;
     st->factor_ms = F.factor_ms;
-    st->kmax = 0;
+    st->kmax = F.kmax;
     st->prec = F.prec;
     st->launches = F.launches;
     for (int k = 0; k < 8; ++k) {
@@ -865,6 +927,10 @@ void ndhss_factor_destroy(ndhss_factorization* fh) {
     cudaFree(F.d_ipiv);
     cudaFree(F.d_front);
     cudaFree(F.d_tasks);
+    cudaFree(F.d_lr_ptr);
+    cudaFree(F.d_lr_k);
+    cudaFree(F.d_lr_list);
+    for (void* b : F.lr_bufs) cudaFree(b);
     delete fh;
 }
 

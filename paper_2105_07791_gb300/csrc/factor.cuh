@@ -42,6 +42,21 @@ struct FactorData {
     int64_t diag_off = 0, diag_cnt = 0;
     int32_t max_mi = 0, max_mb = 0;
 
+    // compressed tier (Alg. 3.4 above the switching level): low-rank R ~ X R(J, :)
+    // per node: X (m_i x k, ld m_i) followed by RJ (k x m_b, ld k), in one
+    // device buffer per tree level
+    int32_t L_hss = -1;                       // levels <= L_hss compress S; < L_hss also R
+    std::vector<void*> lr_bufs;
+    std::vector<uint64_t> lr_ptr;             // per node, 0 = dense R
+    std::vector<int32_t> lr_k;
+    uint64_t* d_lr_ptr = nullptr;
+    int32_t* d_lr_k = nullptr;
+    int32_t* d_lr_list = nullptr;             // low-rank nodes grouped by level
+    std::vector<int64_t> lr_off_l, lr_cnt;    // per level
+    int32_t kmax = 0;
+    int32_t hss_rounds_max = 0;
+    double hss_ms = 0.0;
+
     double factor_ms = 0.0;
     int64_t launches = 0;
     double class_ms[8] = {0};
@@ -56,6 +71,12 @@ struct FactorData {
 };
 
 constexpr int APPLY_ROWS = 64;   // rows per apply task
+
+// Compress the Schur complements (and, strictly above the switching level,
+// the Gauss transforms R) of the fronts on tree level `level`, which have
+// just been eliminated densely.  Defined in hss.cu.
+ndhss_status hss_compress_level(FactorData& F, const Tree& t, int level, const ndhss_factor_opts& o,
+                                cudaStream_t st);
 
 ndhss_status apply_device(const FactorData& F, int32_t nrhs, const void* d_x, int64_t ldx,
                           void* d_y, int64_t ldy, void* d_work, cudaStream_t st);

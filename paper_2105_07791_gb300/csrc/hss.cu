@@ -1,0 +1,1106 @@
+// Randomized HSS compression of Schur complements (Alg. A.1) and low-rank
+// Gauss transforms (Sec. 3.4) for the fronts of one tree level, in the
+// dense-then-compress form of Alg. 3.4: the fronts are already eliminated
+// densely; S^sigma is compressed with the parent-conforming cluster tree of
+// Fig. 4 and replaced by its HSS reconstruction (so the parent assembles the
+// compressed Schur complement), and strictly above the switching level
+// R^sigma is replaced by a row interpolative decomposition R ~ X R(J, :) used
+// by the apply (with L = R^T, A symmetric).
+//
+// All fronts of the level are compressed together, round by round: every
+// front still active in a round has the same number p of samples; the
+// estimator (Eq. 2.7) on r fresh samples retires the fronts that meet eps and
+// the others continue with p + r samples (all previous samples reused).
+//
+// Gaussian samples are Philox4x32-10 (Salmon et al., SC'11) + Box-Muller with
+// the same (seed, stream, element) mapping as the oracle, so both draw the
+// same matrices.  Per HSS node one CTA forms the local sample block, computes
+// its row interpolative decomposition by Householder QR with column pivoting
+// (Businger-Golub) of S_loc^T, and passes Omega_i = U_i^T Omega_loc and
+// S_i = S_loc(J_i, :) upward.
+#include <algorithm>
+#include <climits>
+#include <cmath>
+#include <vector>
+
+#include "factor.cuh"
+
+namespace ndhss {
+namespace {
+
+constexpr int HT = 256;
+constexpr int OVERSAMPLE_MIN = 10;   // the rank may use at most (samples - 10) columns
+
+// ----------------------------------------------------------------- Philox
+__device__ __forceinline__ void philox_round(uint32_t& c0, uint32_t& c1, uint32_t& c2, uint32_t& c3, uint32_t k0,
+                                             uint32_t k1) {
+    const unsigned long long p0 = (unsigned long long)0xD2511F53u * c0;
+    const unsigned long long p1 = (unsigned long long)0xCD9E8D57u * c2;
+    const uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+    const uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+    const uint32_t n0 = hi1 ^ c1 ^ k0, n2 = hi0 ^ c3 ^ k1;
+    c0 = n0;
+    c1 = lo1;
+    c2 = n2;
+    c3 = lo0;
+}
+
+// Four standard normals of counter block `blk` of stream `stream`.
+__device__ void philox_normals(uint64_t seed, uint64_t stream, uint64_t blk, double out[4]) {
+    uint32_t c0 = (uint32_t)blk, c1 = (uint32_t)stream, c2 = (uint32_t)(stream >> 32), c3 = 0;
+    uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+    for (int r = 0; r < 10; ++r) {
+        philox_round(c0, c1, c2, c3, k0, k1);
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    const double u0 = ((double)c0 + 0.5) / 4294967296.0, u1 = ((double)c1 + 0.5) / 4294967296.0;
+    const double u2 = ((double)c2 + 0.5) / 4294967296.0, u3 = ((double)c3 + 0.5) / 4294967296.0;
+    const double r0 = sqrt(-2.0 * log(u0)), r1 = sqrt(-2.0 * log(u2));
+    const double pi2 = 6.283185307179586476925286766559;
+    out[0] = r0 * cos(pi2 * u1);
+    out[1] = r0 * sin(pi2 * u1);
+    out[2] = r1 * cos(pi2 * u3);
+    out[3] = r1 * sin(pi2 * u3);
+}
+
+template <typename T> __device__ __forceinline__ T real_to(double v);
+template <> __device__ __forceinline__ double real_to<double>(double v) { return v; }
+template <> __device__ __forceinline__ float real_to<float>(double v) { return (float)v; }
+template <> __device__ __forceinline__ c128 real_to<c128>(double v) { return {v, 0.0}; }
+template <> __device__ __forceinline__ c64 real_to<c64>(double v) { return {(float)v, 0.0f}; }
+
+__device__ __forceinline__ double nrm2v(double a) { return a * a; }
+__device__ __forceinline__ double nrm2v(float a) { return (double)a * a; }
+__device__ __forceinline__ double nrm2v(c128 a) { return a.x * a.x + a.y * a.y; }
+__device__ __forceinline__ double nrm2v(c64 a) { return (double)a.x * a.x + (double)a.y * a.y; }
+__device__ __forceinline__ double absv(double a) { return fabs(a); }
+__device__ __forceinline__ double absv(float a) { return fabs((double)a); }
+__device__ __forceinline__ double absv(c128 a) { return hypot(a.x, a.y); }
+__device__ __forceinline__ double absv(c64 a) { return hypot((double)a.x, (double)a.y); }
+
+// One Gaussian block: dst(i, col0 + j) for i < rows, j < cols (element e = i + j*rows of the stream).
+struct GaussJob {
+    void* dst;
+    int64_t ld;
+    int rows, cols, col0;
+    uint64_t stream;
+};
+
+template <typename T>
+__global__ void gauss_kernel(const GaussJob* __restrict__ jobs, uint64_t seed) {
+    const GaussJob jb = jobs[blockIdx.y];
+    T* dst = static_cast<T*>(jb.dst);
+    const int64_t n = (int64_t)jb.rows * jb.cols;
+    for (int64_t blk = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; blk * 4 < n; blk += (int64_t)gridDim.x * blockDim.x) {
+        double z[4];
+        philox_normals(seed, jb.stream, (uint64_t)blk, z);
+        for (int q = 0; q < 4; ++q) {
+            const int64_t e = blk * 4 + q;
+            if (e < n) {
+                const int64_t i = e % jb.rows, j = e / jb.rows;
+                dst[(jb.col0 + j) * jb.ld + i] = real_to<T>(z[q]);
+            }
+        }
+    }
+}
+
+// ------------------------------------------------------- batched GEMM
+// C = (beta ? C : 0) + alpha * A * B, column-major, A M x K, B K x N.
+struct GemmJob {
+    const void* A;
+    const void* B;
+    void* C;
+    int64_t lda, ldb, ldc;
+    int M, N, K, beta;
+    double alpha;
+};
+
+template <typename T>
+__global__ void __launch_bounds__(256) bgemm_kernel(const GemmJob* __restrict__ jobs) {
+    constexpr int TT = 64, TK = 16;
+    __shared__ T sA[TK][TT];
+    __shared__ T sB[TK][TT];
+    const GemmJob jb = jobs[blockIdx.z];
+    const int64_t i0 = (int64_t)blockIdx.x * TT, j0 = (int64_t)blockIdx.y * TT;
+    if (i0 >= jb.M || j0 >= jb.N) return;
+    const T* A = static_cast<const T*>(jb.A);
+    const T* B = static_cast<const T*>(jb.B);
+    T* Cm = static_cast<T*>(jb.C);
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    T acc[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b] = zero<T>();
+    for (int kc = 0; kc < jb.K; kc += TK) {
+        for (int q = tid; q < TK * TT; q += 256) {
+            const int ii = q % TT, l = q / TT;
+            sA[l][ii] = (kc + l < jb.K && i0 + ii < jb.M) ? A[(int64_t)(kc + l) * jb.lda + i0 + ii] : zero<T>();
+        }
+        for (int q = tid; q < TK * TT; q += 256) {
+            const int l = q % TK, jj = q / TK;
+            sB[l][jj] = (kc + l < jb.K && j0 + jj < jb.N) ? B[(j0 + jj) * jb.ldb + kc + l] : zero<T>();
+        }
+        __syncthreads();
+#pragma unroll
+        for (int l = 0; l < TK; ++l) {
+            T av[4], bv[4];
+#pragma unroll
+            for (int a = 0; a < 4; ++a) av[a] = sA[l][tx + 16 * a];
+#pragma unroll
+            for (int b = 0; b < 4; ++b) bv[b] = sB[l][ty + 16 * b];
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int b = 0; b < 4; ++b) acc[a][b] = fmac(av[a], bv[b], acc[a][b]);
+        }
+        __syncthreads();
+    }
+    using real = typename Tr<T>::real;
+    for (int b = 0; b < 4; ++b) {
+        const int64_t j = j0 + ty + 16 * b;
+        if (j >= jb.N) continue;
+        for (int a = 0; a < 4; ++a) {
+            const int64_t i = i0 + tx + 16 * a;
+            if (i >= jb.M) continue;
+            T* dst = Cm + j * jb.ldc + i;
+            const T v = scale(acc[a][b], (real)jb.alpha);
+            *dst = jb.beta ? (*dst + v) : v;
+        }
+    }
+}
+
+// ------------------------------------------------------ HSS node tables
+struct HFront {
+    void* S;          // the dense block being compressed (n x n, ld lds), or R (rows x cols)
+    int64_t lds;
+    int n;            // S: order; R: rows (m_i)
+    int ncol;         // R: columns (m_b); S: n
+    void* Om;         // samples (n x p) / R: (ncol x p)
+    void* Y;          // S Om (n x p) / R Om (n x p)
+    void* Ot;         // fresh samples (n x r) / R: (ncol x r)
+    void* Yt;         // S Ot / R Ot (n x r)
+    void* Zt;         // HSS(S) Ot / X R(J,:) Ot (n x r)
+    void* T1;         // R: R(J,:) Ot (kcap x r)
+    void* RJ;         // R: R(J,:) (kcap x ncol)
+    int root;         // index of the root HSS node
+};
+
+struct HNode {
+    int front, lo, hi, level, c1, c2;
+    int rows_cap, kcap, p;
+    int64_t o_w, o_sl, o_x, o_om, o_si, o_xh, o_yh;   // element offsets in the workspace
+    int64_t o_skel, o_iloc, o_piv;                      // int offsets
+};
+
+// S_loc^T into W (p x rows, ld p) and S_loc into SL (rows x p, ld rows_cap); iloc = global rows.
+template <typename T>
+__global__ void __launch_bounds__(HT)
+form_sloc_kernel(const int* __restrict__ list, const HNode* __restrict__ nodes, const HFront* __restrict__ fronts,
+                 T* __restrict__ ws, int* __restrict__ iws, int* __restrict__ kk, int* __restrict__ rows_out) {
+    const HNode nd = nodes[list[blockIdx.x]];
+    const HFront fr = fronts[nd.front];
+    const T* S = static_cast<const T*>(fr.S);
+    const T* Om = static_cast<const T*>(fr.Om);
+    const T* Y = static_cast<const T*>(fr.Y);
+    const int64_t n = fr.n, lds = fr.lds;
+    const int p = nd.p;
+    T* W = ws + nd.o_w;
+    T* SL = ws + nd.o_sl;
+    int* iloc = iws + nd.o_iloc;
+    int rows;
+    if (nd.c1 < 0) {
+        rows = nd.hi - nd.lo;
+        for (int q = threadIdx.x; q < rows * p; q += HT) {
+            const int r = q % rows, j = q / rows;
+            T acc = Y[j * n + nd.lo + r];
+            for (int c = 0; c < rows; ++c)
+                acc = fmac(-S[(int64_t)(nd.lo + c) * lds + nd.lo + r], Om[j * n + nd.lo + c], acc);
+            W[(int64_t)r * p + j] = acc;
+            SL[(int64_t)j * nd.rows_cap + r] = acc;
+        }
+        for (int r = threadIdx.x; r < rows; r += HT) iloc[r] = nd.lo + r;
+    } else {
+        const HNode a = nodes[nd.c1], b = nodes[nd.c2];
+        const int k1 = kk[nd.c1], k2 = kk[nd.c2];
+        rows = k1 + k2;
+        const int* sk1 = iws + a.o_skel;
+        const int* sk2 = iws + b.o_skel;
+        const T* S1 = ws + a.o_si;
+        const T* S2 = ws + b.o_si;
+        const T* O1 = ws + a.o_om;
+        const T* O2 = ws + b.o_om;
+        for (int q = threadIdx.x; q < rows * p; q += HT) {
+            const int r = q % rows, j = q / rows;
+            T acc;
+            if (r < k1) {
+                acc = S1[(int64_t)j * a.kcap + r];
+                const int gr = sk1[r];
+                for (int c = 0; c < k2; ++c) acc = fmac(-S[(int64_t)sk2[c] * lds + gr], O2[(int64_t)j * b.kcap + c], acc);
+            } else {
+                const int rr = r - k1;
+                acc = S2[(int64_t)j * b.kcap + rr];
+                const int gr = sk2[rr];
+                for (int c = 0; c < k1; ++c) acc = fmac(-S[(int64_t)sk1[c] * lds + gr], O1[(int64_t)j * a.kcap + c], acc);
+            }
+            W[(int64_t)r * p + j] = acc;
+            SL[(int64_t)j * nd.rows_cap + r] = acc;
+        }
+        for (int r = threadIdx.x; r < rows; r += HT) iloc[r] = (r < k1) ? sk1[r] : sk2[r - k1];
+    }
+    if (threadIdx.x == 0) rows_out[list[blockIdx.x]] = rows;
+}
+
+// Row interpolative decomposition of S_loc from a Householder QR with column
+// pivoting (largest remaining norm, first index on ties) of W = S_loc^T.
+// Rank = number of steps with pivot norm > eps * (first pivot norm), at most
+// kmax.  Output: kk[node] = k, piv (local rows, first k = skeleton J),
+// X (rows x k, ld rows_cap) with X(J, :) = I.
+template <typename T>
+__global__ void __launch_bounds__(HT)
+row_id_kernel(const int* __restrict__ list, const HNode* __restrict__ nodes, T* __restrict__ ws,
+              int* __restrict__ iws, int* __restrict__ kk, const int* __restrict__ rows_in, double eps, int rank_cap) {
+    using real = typename Tr<T>::real;
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int id = list[blockIdx.x];
+    const HNode nd = nodes[id];
+    const int rows = rows_in[id], p = nd.p;
+    T* W = ws + nd.o_w;
+    int* piv = iws + nd.o_piv;
+    double* nrm = reinterpret_cast<double*>(smem);                      // rows
+    __shared__ double s_val[HT / 32];
+    __shared__ int s_idx[HT / 32];
+    __shared__ double s_r11, s_bestv;
+    __shared__ int s_best;
+    __shared__ double s_xn2, s_vn2;
+    __shared__ T s_alpha, s_beta;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    for (int c = tid; c < rows; c += HT) piv[c] = c;
+    const int kmax = min(min(nd.kcap, rank_cap), min(p, rows));
+    int t = 0;
+    __syncthreads();
+    for (; t < min(p, rows); ++t) {
+        // remaining column norms and the pivot
+        double best = -1.0;
+        int bi = INT_MAX;
+        for (int c = t + tid; c < rows; c += HT) {
+            double s = 0.0;
+            const T* col = W + (int64_t)c * p;
+            for (int j = t; j < p; ++j) s += nrm2v(col[j]);
+            nrm[c] = s;
+            if (s > best) { best = s; bi = c; }
+        }
+        for (int o = 16; o; o >>= 1) {
+            const double ov = __shfl_down_sync(0xffffffffu, best, o);
+            const int oi = __shfl_down_sync(0xffffffffu, bi, o);
+            if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
+        }
+        if (lane == 0) { s_val[warp] = best; s_idx[warp] = bi; }
+        __syncthreads();
+        if (tid == 0) {
+            double bv = -1.0;
+            int bb = INT_MAX;
+            for (int w = 0; w < HT / 32; ++w)
+                if (s_val[w] > bv || (s_val[w] == bv && s_idx[w] < bb)) { bv = s_val[w]; bb = s_idx[w]; }
+            s_best = bb;
+            s_bestv = sqrt(fmax(bv, 0.0));
+            if (t == 0) s_r11 = s_bestv;
+        }
+        __syncthreads();
+        const int cb = s_best;
+        if (t >= kmax || !(s_bestv > eps * s_r11) || cb == INT_MAX) break;
+        // interchange columns t and cb
+        if (cb != t) {
+            for (int j = tid; j < p; j += HT) {
+                const T a = W[(int64_t)t * p + j];
+                W[(int64_t)t * p + j] = W[(int64_t)cb * p + j];
+                W[(int64_t)cb * p + j] = a;
+            }
+            if (tid == 0) {
+                const int a = piv[t];
+                piv[t] = piv[cb];
+                piv[cb] = a;
+            }
+        }
+        __syncthreads();
+        // Householder reflector of W(t:p, t): v = x - beta e1, beta = -phase(x0) ||x||
+        T* xcol = W + (int64_t)t * p;
+        if (tid == 0) {
+            double xn2 = 0.0;
+            for (int j = t; j < p; ++j) xn2 += nrm2v(xcol[j]);
+            const T a0 = xcol[t];
+            const double aa = absv(a0), xn = sqrt(xn2);
+            T ph = one<T>();
+            if (aa > 0) ph = scale(a0, (real)(1.0 / aa));
+            const T beta = scale(ph, (real)(-xn));
+            const T v0 = a0 - beta;
+            s_vn2 = xn2 - aa * aa + nrm2v(v0);
+            s_alpha = v0;
+            s_beta = beta;
+        }
+        __syncthreads();
+        const double vn2 = s_vn2;
+        const T v0 = s_alpha;
+        if (vn2 > 0) {
+            const real f = (real)(2.0 / vn2);
+            for (int c = t + 1 + tid; c < rows; c += HT) {
+                T* col = W + (int64_t)c * p;
+                T w = conjv(v0) * col[t];
+                for (int j = t + 1; j < p; ++j) w = fmac(conjv(xcol[j]), col[j], w);
+                const T g = scale(w, f);
+                col[t] = col[t] - v0 * g;
+                for (int j = t + 1; j < p; ++j) col[j] = col[j] - xcol[j] * g;
+            }
+        }
+        __syncthreads();
+        if (tid == 0) xcol[t] = s_beta;
+        __syncthreads();
+    }
+    const int k = t;
+    // T = R11^{-1} R12 in place of R12 (one column per thread)
+    for (int c = k + tid; c < rows; c += HT) {
+        T* col = W + (int64_t)c * p;
+        for (int i = k - 1; i >= 0; --i) {
+            T acc = col[i];
+            for (int l = i + 1; l < k; ++l) acc = fmac(-W[(int64_t)l * p + i], col[l], acc);
+            col[i] = acc * recip(W[(int64_t)i * p + i]);
+        }
+    }
+    __syncthreads();
+    T* X = ws + nd.o_x;
+    for (int q = tid; q < rows * k; q += HT) {
+        const int i = q % rows, a = q / rows;        // i = pivoted position
+        T v;
+        if (i < k) v = (i == a) ? one<T>() : zero<T>();
+        else v = W[(int64_t)i * p + a];
+        X[(int64_t)a * nd.rows_cap + piv[i]] = v;
+    }
+    if (tid == 0) kk[id] = k;
+}
+
+// Omega_i = X^T Omega_loc, S_i = S_loc(J, :), skeleton = iloc(J).
+template <typename T>
+__global__ void __launch_bounds__(HT)
+finish_kernel(const int* __restrict__ list, const HNode* __restrict__ nodes, const HFront* __restrict__ fronts,
+              T* __restrict__ ws, int* __restrict__ iws, const int* __restrict__ kk, const int* __restrict__ rows_in) {
+    const int id = list[blockIdx.x];
+    const HNode nd = nodes[id];
+    const HFront fr = fronts[nd.front];
+    const int rows = rows_in[id], k = kk[id], p = nd.p;
+    const T* X = ws + nd.o_x;
+    const T* SL = ws + nd.o_sl;
+    const int* piv = iws + nd.o_piv;
+    const int* iloc = iws + nd.o_iloc;
+    T* OM = ws + nd.o_om;
+    T* SI = ws + nd.o_si;
+    int* skel = iws + nd.o_skel;
+    const T* Om = static_cast<const T*>(fr.Om);
+    int k1 = 0;
+    const T *O1 = nullptr, *O2 = nullptr;
+    int ld1 = 0, ld2 = 0;
+    if (nd.c1 >= 0) {
+        k1 = kk[nd.c1];
+        O1 = ws + nodes[nd.c1].o_om;
+        O2 = ws + nodes[nd.c2].o_om;
+        ld1 = nodes[nd.c1].kcap;
+        ld2 = nodes[nd.c2].kcap;
+    }
+    for (int q = threadIdx.x; q < k * p; q += HT) {
+        const int a = q % k, j = q / k;
+        T acc = zero<T>();
+        for (int r = 0; r < rows; ++r) {
+            T o;
+            if (nd.c1 < 0) o = Om[(int64_t)j * fr.n + nd.lo + r];
+            else o = (r < k1) ? O1[(int64_t)j * ld1 + r] : O2[(int64_t)j * ld2 + (r - k1)];
+            acc = fmac(X[(int64_t)a * nd.rows_cap + r], o, acc);
+        }
+        OM[(int64_t)j * nd.kcap + a] = acc;
+        SI[(int64_t)j * nd.kcap + a] = SL[(int64_t)j * nd.rows_cap + piv[a]];
+    }
+    for (int a = threadIdx.x; a < k; a += HT) skel[a] = iloc[piv[a]];
+}
+
+// ---------------------------------------------- HSS matvec (nc columns)
+// up: xh_i = X_i^T (x(lo:hi) or [xh_c1; xh_c2])
+template <typename T>
+__global__ void __launch_bounds__(HT)
+hss_up_kernel(const int* __restrict__ list, const HNode* __restrict__ nodes, const T* __restrict__ ws, T* __restrict__ hb,
+              const int* __restrict__ kk, const int* __restrict__ rows_in, const T* const* __restrict__ xin,
+              const int64_t* __restrict__ ldx, const int* __restrict__ ncs, int64_t xh_ld) {
+    const int id = list[blockIdx.x];
+    const HNode nd = nodes[id];
+    const int rows = rows_in[id], k = kk[id], nc = ncs[nd.front];
+    const T* X = ws + nd.o_x;
+    T* xh = hb + nd.o_xh;
+    const T* x = xin[nd.front];
+    const int64_t lx = ldx[nd.front];
+    int k1 = 0;
+    const T *h1 = nullptr, *h2 = nullptr;
+    if (nd.c1 >= 0) {
+        k1 = kk[nd.c1];
+        h1 = hb + nodes[nd.c1].o_xh;
+        h2 = hb + nodes[nd.c2].o_xh;
+    }
+    for (int q = threadIdx.x; q < k * nc; q += HT) {
+        const int a = q % k, j = q / k;
+        T acc = zero<T>();
+        for (int r = 0; r < rows; ++r) {
+            T v;
+            if (nd.c1 < 0) v = x[(int64_t)j * lx + nd.lo + r];
+            else v = (r < k1) ? h1[(int64_t)j * xh_ld + r] : h2[(int64_t)j * xh_ld + (r - k1)];
+            acc = fmac(X[(int64_t)a * nd.rows_cap + r], v, acc);
+        }
+        xh[(int64_t)j * xh_ld + a] = acc;
+    }
+}
+
+// down at inner node i: yh_c1 = S(sk1, sk2) xh_c2 + (X_i yh_i)(0:k1), yh_c2 = S(sk2, sk1) xh_c1 + (X_i yh_i)(k1:)
+template <typename T>
+__global__ void __launch_bounds__(HT)
+hss_down_kernel(const int* __restrict__ list, const HNode* __restrict__ nodes, const HFront* __restrict__ fronts,
+                const T* __restrict__ ws, T* __restrict__ hb, const int* __restrict__ iws, const int* __restrict__ kk,
+                const int* __restrict__ ncs, int64_t xh_ld) {
+    const int id = list[blockIdx.x];
+    const HNode nd = nodes[id];
+    const HFront fr = fronts[nd.front];
+    const int nc = ncs[nd.front];
+    const T* S = static_cast<const T*>(fr.S);
+    const int64_t lds = fr.lds;
+    const HNode a = nodes[nd.c1], b = nodes[nd.c2];
+    const int k1 = kk[nd.c1], k2 = kk[nd.c2];
+    const int* sk1 = iws + a.o_skel;
+    const int* sk2 = iws + b.o_skel;
+    const T* xh1 = hb + a.o_xh;
+    const T* xh2 = hb + b.o_xh;
+    T* yh1 = hb + a.o_yh;
+    T* yh2 = hb + b.o_yh;
+    const bool root = (id == fr.root);
+    const int k = root ? 0 : kk[id];
+    const T* X = ws + nd.o_x;
+    const T* yh = hb + nd.o_yh;
+    for (int q = threadIdx.x; q < (k1 + k2) * nc; q += HT) {
+        const int r = q % (k1 + k2), j = q / (k1 + k2);
+        T acc = zero<T>();
+        for (int c = 0; c < k; ++c) acc = fmac(X[(int64_t)c * nd.rows_cap + r], yh[(int64_t)j * xh_ld + c], acc);
+        if (r < k1) {
+            const int gr = sk1[r];
+            for (int c = 0; c < k2; ++c) acc = fmac(S[(int64_t)sk2[c] * lds + gr], xh2[(int64_t)j * xh_ld + c], acc);
+            yh1[(int64_t)j * xh_ld + r] = acc;
+        } else {
+            const int rr = r - k1, gr = sk2[rr];
+            for (int c = 0; c < k1; ++c) acc = fmac(S[(int64_t)sk1[c] * lds + gr], xh1[(int64_t)j * xh_ld + c], acc);
+            yh2[(int64_t)j * xh_ld + rr] = acc;
+        }
+    }
+}
+
+// leaves: y(lo:hi) = D x(lo:hi) + X yh
+template <typename T>
+__global__ void __launch_bounds__(HT)
+hss_leaf_kernel(const int* __restrict__ list, const HNode* __restrict__ nodes, const HFront* __restrict__ fronts,
+                const T* __restrict__ ws, const T* __restrict__ hb, const int* __restrict__ kk,
+                const T* const* __restrict__ xin, const int64_t* __restrict__ ldx, T* const* __restrict__ yout,
+                const int64_t* __restrict__ ldy, const int* __restrict__ ncs, int64_t xh_ld) {
+    const int id = list[blockIdx.x];
+    const HNode nd = nodes[id];
+    const HFront fr = fronts[nd.front];
+    const int nc = ncs[nd.front];
+    const T* S = static_cast<const T*>(fr.S);
+    const int64_t lds = fr.lds;
+    const int rows = nd.hi - nd.lo;
+    const bool root = (id == fr.root);
+    const int k = root ? 0 : kk[id];
+    const T* X = ws + nd.o_x;
+    const T* yh = hb + nd.o_yh;
+    const T* x = xin[nd.front];
+    T* y = yout[nd.front];
+    const int64_t lx = ldx[nd.front], ly = ldy[nd.front];
+    for (int q = threadIdx.x; q < rows * nc; q += HT) {
+        const int r = q % rows, j = q / rows;
+        T acc = zero<T>();
+        for (int c = 0; c < rows; ++c)
+            acc = fmac(S[(int64_t)(nd.lo + c) * lds + nd.lo + r], x[(int64_t)j * lx + nd.lo + c], acc);
+        for (int c = 0; c < k; ++c) acc = fmac(X[(int64_t)c * nd.rows_cap + r], yh[(int64_t)j * xh_ld + c], acc);
+        y[(int64_t)j * ly + nd.lo + r] = acc;
+    }
+}
+
+// estimator norms per front: err^2 = ||Yt - Zt||^2, ref^2 = ||Yt||^2
+template <typename T>
+__global__ void est_norm_kernel(const HFront* __restrict__ fronts, int r, double* __restrict__ out) {
+    const HFront fr = fronts[blockIdx.x];
+    const T* Yt = static_cast<const T*>(fr.Yt);
+    const T* Zt = static_cast<const T*>(fr.Zt);
+    const int64_t n = (int64_t)fr.n * r;
+    double e = 0.0, f = 0.0;
+    for (int64_t q = threadIdx.x; q < n; q += blockDim.x) {
+        e += nrm2v(Yt[q] - Zt[q]);
+        f += nrm2v(Yt[q]);
+    }
+    __shared__ double se[HT], sf[HT];
+    se[threadIdx.x] = e;
+    sf[threadIdx.x] = f;
+    __syncthreads();
+    for (int s = HT / 2; s; s >>= 1) {
+        if (threadIdx.x < s) {
+            se[threadIdx.x] += se[threadIdx.x + s];
+            sf[threadIdx.x] += sf[threadIdx.x + s];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        out[2 * blockIdx.x] = sqrt(se[0]);
+        out[2 * blockIdx.x + 1] = sqrt(sf[0]);
+    }
+}
+
+// identity columns (n x n, ld n) per front
+template <typename T>
+__global__ void eye_kernel(T* const* __restrict__ dst, const int* __restrict__ ns) {
+    T* d = dst[blockIdx.y];
+    const int64_t n = ns[blockIdx.y];
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n * n; q += (int64_t)gridDim.x * blockDim.x)
+        d[q] = (q % n == q / n) ? one<T>() : zero<T>();
+}
+
+// copy an n x n block (ld n) into S (ld lds)
+template <typename T>
+__global__ void copy_back_kernel(const T* const* __restrict__ src, const HFront* __restrict__ fronts, const int* __restrict__ which) {
+    const HFront fr = fronts[which[blockIdx.y]];
+    const T* s = src[blockIdx.y];
+    T* S = static_cast<T*>(fr.S);
+    const int64_t n = fr.n;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n * n; q += (int64_t)gridDim.x * blockDim.x)
+        S[(q / n) * fr.lds + q % n] = s[q];
+}
+
+// R(J, :) rows gathered (k x ncol, ld kcap), and the transposed samples W = Y^T (p x n, ld p)
+template <typename T>
+__global__ void gather_rows_kernel(const HFront* __restrict__ fronts, const HNode* __restrict__ nodes, const T* __restrict__ ws,
+                                   const int* __restrict__ iws, const int* __restrict__ kk) {
+    const HFront fr = fronts[blockIdx.y];
+    const HNode nd = nodes[fr.root];
+    const int k = kk[fr.root];
+    const int* piv = iws + nd.o_piv;
+    const T* R = static_cast<const T*>(fr.S);
+    T* RJ = static_cast<T*>(fr.RJ);
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < (int64_t)k * fr.ncol;
+         q += (int64_t)gridDim.x * blockDim.x) {
+        const int a = (int)(q % k);
+        const int64_t j = q / k;
+        RJ[j * nd.kcap + a] = R[j * fr.lds + piv[a]];
+    }
+}
+
+template <typename T>
+__global__ void transpose_samples_kernel(const HFront* __restrict__ fronts, const HNode* __restrict__ nodes, T* __restrict__ ws,
+                                         int* __restrict__ iws, int* __restrict__ rows_out) {
+    const HFront fr = fronts[blockIdx.y];
+    const HNode nd = nodes[fr.root];
+    const T* Y = static_cast<const T*>(fr.Y);
+    T* W = ws + nd.o_w;
+    const int p = nd.p;
+    const int64_t n = fr.n;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n * p; q += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = q % n, j = q / n;
+        W[i * p + j] = Y[q];
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) rows_out[fr.root] = fr.n;
+}
+
+// host-side cluster tree identical to the oracle's (breadth-first, Fig. 4 top split, halving to <= beta)
+struct HCl {
+    int lo, hi, level, parent, c1, c2;
+};
+std::vector<HCl> cluster_tree(int n, int top, int beta) {
+    std::vector<HCl> t;
+    t.push_back({0, n, 0, -1, -1, -1});
+    for (size_t q = 0; q < t.size(); ++q) {
+        HCl c = t[q];
+        if (c.hi - c.lo <= beta) continue;
+        const int mid = (q == 0 && top > 0 && top < n) ? top : c.lo + (c.hi - c.lo) / 2;
+        const int a = (int)t.size();
+        t.push_back({c.lo, mid, c.level + 1, (int)q, -1, -1});
+        t.push_back({mid, c.hi, c.level + 1, (int)q, -1, -1});
+        t[q].c1 = a;
+        t[q].c2 = a + 1;
+    }
+    return t;
+}
+
+template <typename U>
+struct DeviceVec {
+    U* p = nullptr;
+    size_t n = 0;
+    ~DeviceVec() { if (p) cudaFree(p); }
+    cudaError_t upload(const std::vector<U>& v, cudaStream_t st) {
+        if (p) cudaFree(p);
+        p = nullptr;
+        n = v.size();
+        cudaError_t e = cudaMalloc(&p, std::max<size_t>(n, 1) * sizeof(U));
+        if (e != cudaSuccess) return e;
+        if (n) e = cudaMemcpyAsync(p, v.data(), n * sizeof(U), cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        return e;
+    }
+    cudaError_t alloc(size_t count) {
+        if (p) cudaFree(p);
+        p = nullptr;
+        n = count;
+        return cudaMalloc(&p, std::max<size_t>(n, 1) * sizeof(U));
+    }
+};
+
+#define HSS_TRY(expr)                                                                                      \
+    do {                                                                                                   \
+        cudaError_t e_ = (expr);                                                                           \
+        if (e_ != cudaSuccess)                                                                             \
+            return set_error(NDHSS_ERR_CUDA, "hss: %s failed: %s", #expr, cudaGetErrorString(e_));           \
+    } while (0)
+
+
+// y = A_HSS x for the fronts listed in the node table: up-sweep deepest level
+// first, coupling + down-sweep root first, then the leaf blocks.
+template <typename T>
+ndhss_status hss_matvec_run(const std::vector<HNode>& nodes, const std::vector<char>& keep, int maxlev,
+                            const HNode* dnodes, const HFront* dfr, const T* ws, T* hb, const int* iws, const int* kk,
+                            const int* rows, const T* const* dx, const int64_t* dlx, T* const* dy, const int64_t* dly,
+                            const int* dncs, int64_t xh_ld, cudaStream_t st) {
+    std::vector<int> flat;
+    std::vector<size_t> up_off(maxlev + 2, 0), dn_off(maxlev + 2, 0);
+    for (int l = 0; l <= maxlev; ++l) {            // up lists (non-root)
+        up_off[l] = flat.size();
+        for (size_t i = 0; i < nodes.size(); ++i)
+            if (keep[nodes[i].front] && nodes[i].level == l && l > 0) flat.push_back((int)i);
+    }
+    up_off[maxlev + 1] = flat.size();
+    for (int l = 0; l <= maxlev; ++l) {            // down lists (inner nodes)
+        dn_off[l] = flat.size();
+        for (size_t i = 0; i < nodes.size(); ++i)
+            if (keep[nodes[i].front] && nodes[i].level == l && nodes[i].c1 >= 0) flat.push_back((int)i);
+    }
+    dn_off[maxlev + 1] = flat.size();
+    const size_t leaf_off = flat.size();
+    for (size_t i = 0; i < nodes.size(); ++i)
+        if (keep[nodes[i].front] && nodes[i].c1 < 0) flat.push_back((int)i);
+    const size_t leaf_cnt = flat.size() - leaf_off;
+    DeviceVec<int> dflat;
+    HSS_TRY(dflat.upload(flat, st));
+    for (int l = maxlev; l >= 1; --l) {
+        const unsigned cnt = (unsigned)(up_off[l + 1] - up_off[l]);
+        if (!cnt) continue;
+        hss_up_kernel<T><<<cnt, HT, 0, st>>>(dflat.p + up_off[l], dnodes, ws, hb, kk, rows, dx, dlx, dncs, xh_ld);
+        NDHSS_LAUNCH_CHECK("hss_up_kernel");
+    }
+    for (int l = 0; l <= maxlev; ++l) {
+        const unsigned cnt = (unsigned)(dn_off[l + 1] - dn_off[l]);
+        if (!cnt) continue;
+        hss_down_kernel<T><<<cnt, HT, 0, st>>>(dflat.p + dn_off[l], dnodes, dfr, ws, hb, iws, kk, dncs, xh_ld);
+        NDHSS_LAUNCH_CHECK("hss_down_kernel");
+    }
+    if (leaf_cnt) {
+        hss_leaf_kernel<T><<<(unsigned)leaf_cnt, HT, 0, st>>>(dflat.p + leaf_off, dnodes, dfr, ws, hb, kk, dx, dlx, dy,
+                                                              dly, dncs, xh_ld);
+        NDHSS_LAUNCH_CHECK("hss_leaf_kernel");
+    }
+    return NDHSS_OK;
+}
+
+// One compression problem set (all S blocks, or all R blocks, of a level).
+struct Problem {
+    int node;          // tree node
+    int n, ncol;       // rows and columns of the block
+    int64_t lds;
+    void* ptr;         // block in the front arena
+    int top;           // Fig. 4 top split (S), unused for R
+    uint64_t stream;   // 2*node (S) or 2*node+1 (R), as the oracle
+};
+
+// Runs the adaptive rounds of Alg. A.1 (lowrank == false) or of the low-rank
+// range finder (lowrank == true) on all problems; on success S blocks are
+// overwritten by their HSS reconstruction and for R blocks (X, R(J,:)) are
+// written to `lr_out` (per problem: X m_i x k then RJ k x m_b), ranks to kout.
+template <typename T>
+ndhss_status compress_problems(std::vector<Problem>& probs, bool lowrank, const ndhss_factor_opts& o,
+                               std::vector<int>& kout, std::vector<std::vector<T>>* lr_host, FactorData& F,
+                               cudaStream_t st) {
+    const int r = std::max(o.r, 1), k0 = std::max(o.k0, 1), beta = std::max(o.beta, 1);
+    const int rank_cap = std::max(o.rank_cap, 1);
+    const double eps = o.eps_hss;
+    kout.assign(probs.size(), 0);
+    if (lr_host) lr_host->assign(probs.size(), {});
+    std::vector<int> active(probs.size());
+    for (size_t i = 0; i < probs.size(); ++i) active[i] = (int)i;
+    int p = k0 + r;
+    int round = 0;
+    while (!active.empty()) {
+        const int kcap = std::max(1, std::min(rank_cap, p - OVERSAMPLE_MIN));
+        std::vector<HFront> fr;
+        std::vector<HNode> nodes;
+        std::vector<std::vector<HCl>> trees;
+        int64_t ews = 0, iwsz = 0;
+        auto take = [&](int64_t cnt) { int64_t o2 = ews; ews += (cnt + 31) / 32 * 32; return o2; };
+        auto itake = [&](int64_t cnt) { int64_t o2 = iwsz; iwsz += (cnt + 31) / 32 * 32; return o2; };
+        int maxlev = 0;
+        int64_t max_rows = 1;
+        for (int a : active) {
+            const Problem& pb = probs[a];
+            HFront f{};
+            f.S = pb.ptr;
+            f.lds = pb.lds;
+            f.n = pb.n;
+            f.ncol = pb.ncol;
+            auto tr = lowrank ? std::vector<HCl>{{0, pb.n, 0, -1, -1, -1}} : cluster_tree(pb.n, pb.top, beta);
+            const int base = (int)nodes.size();
+            f.root = base;
+            for (auto& c : tr) {
+                HNode nd{};
+                nd.front = (int)fr.size();
+                nd.lo = c.lo;
+                nd.hi = c.hi;
+                nd.level = c.level;
+                nd.c1 = c.c1 >= 0 ? base + c.c1 : -1;
+                nd.c2 = c.c2 >= 0 ? base + c.c2 : -1;
+                nd.p = p;
+                nd.kcap = kcap;
+                nd.rows_cap = (c.c1 < 0) ? (c.hi - c.lo) : 2 * kcap;
+                max_rows = std::max<int64_t>(max_rows, nd.rows_cap);
+                nd.o_w = take((int64_t)p * nd.rows_cap);
+                nd.o_sl = take((int64_t)p * nd.rows_cap);
+                nd.o_x = take((int64_t)nd.rows_cap * kcap);
+                nd.o_om = take((int64_t)kcap * p);
+                nd.o_si = take((int64_t)kcap * p);
+                nd.o_skel = itake(kcap);
+                nd.o_iloc = itake(nd.rows_cap);
+                nd.o_piv = itake(nd.rows_cap);
+                maxlev = std::max(maxlev, c.level);
+                nodes.push_back(nd);
+            }
+            trees.push_back(tr);
+            fr.push_back(f);
+        }
+        // per-front sample buffers
+        const int nf = (int)fr.size();
+        std::vector<int64_t> o_om(nf), o_y(nf), o_ot(nf), o_yt(nf), o_zt(nf), o_t1(nf), o_rj(nf);
+        for (int i = 0; i < nf; ++i) {
+            const int64_t n = fr[i].n, nc = fr[i].ncol;
+            o_om[i] = take((lowrank ? nc : n) * p);
+            o_y[i] = take(n * p);
+            o_ot[i] = take((lowrank ? nc : n) * r);
+            o_yt[i] = take(n * r);
+            o_zt[i] = take(n * r);
+            o_t1[i] = take((int64_t)kcap * r);
+            o_rj[i] = take((int64_t)kcap * nc);
+        }
+        // matvec scratch (estimator: r columns)
+        for (auto& nd : nodes) {
+            nd.o_xh = take((int64_t)kcap * r);
+            nd.o_yh = take((int64_t)kcap * r);
+        }
+        DeviceVec<T> ws;
+        DeviceVec<int> iws, kk, rows;
+        HSS_TRY(ws.alloc(ews));
+        HSS_TRY(iws.alloc(iwsz));
+        HSS_TRY(kk.alloc(nodes.size()));
+        HSS_TRY(rows.alloc(nodes.size()));
+        HSS_TRY(cudaMemsetAsync(kk.p, 0, nodes.size() * sizeof(int), st));
+        for (int i = 0; i < nf; ++i) {
+            fr[i].Om = ws.p + o_om[i];
+            fr[i].Y = ws.p + o_y[i];
+            fr[i].Ot = ws.p + o_ot[i];
+            fr[i].Yt = ws.p + o_yt[i];
+            fr[i].Zt = ws.p + o_zt[i];
+            fr[i].T1 = ws.p + o_t1[i];
+            fr[i].RJ = ws.p + o_rj[i];
+        }
+        DeviceVec<HFront> dfr;
+        DeviceVec<HNode> dnodes;
+        HSS_TRY(dfr.upload(fr, st));
+        HSS_TRY(dnodes.upload(nodes, st));
+        // Gaussian samples, block by block exactly as the oracle draws them
+        std::vector<GaussJob> gj;
+        for (int i = 0; i < nf; ++i) {
+            const Problem& pb = probs[active[i]];
+            const int rows_o = lowrank ? pb.ncol : pb.n;
+            const uint64_t sb = pb.stream * 64 + (lowrank ? 32 : 0);
+            gj.push_back({fr[i].Om, rows_o, rows_o, k0 + r, 0, sb});
+            for (int q = 0; q < round; ++q) gj.push_back({fr[i].Om, rows_o, rows_o, r, k0 + r + q * r, sb + 1 + q});
+            gj.push_back({fr[i].Ot, rows_o, rows_o, r, 0, sb + 1 + round});
+        }
+        DeviceVec<GaussJob> dgj;
+        HSS_TRY(dgj.upload(gj, st));
+        gauss_kernel<T><<<dim3(64, (unsigned)gj.size()), 256, 0, st>>>(dgj.p, o.seed);
+        NDHSS_LAUNCH_CHECK("gauss_kernel");
+        // Y = block * Omega, Yt = block * Omega~
+        std::vector<GemmJob> gm;
+        int maxM = 1, maxN = 1;
+        for (int i = 0; i < nf; ++i) {
+            const Problem& pb = probs[active[i]];
+            const int K = lowrank ? pb.ncol : pb.n;
+            gm.push_back({pb.ptr, fr[i].Om, fr[i].Y, pb.lds, K, pb.n, pb.n, p, K, 0, 1.0});
+            gm.push_back({pb.ptr, fr[i].Ot, fr[i].Yt, pb.lds, K, pb.n, pb.n, r, K, 0, 1.0});
+            maxM = std::max(maxM, pb.n);
+            maxN = std::max(maxN, p);
+        }
+        DeviceVec<GemmJob> dgm;
+        HSS_TRY(dgm.upload(gm, st));
+        bgemm_kernel<T><<<dim3((maxM + 63) / 64, (maxN + 63) / 64, (unsigned)gm.size()), 256, 0, st>>>(dgm.p);
+        NDHSS_LAUNCH_CHECK("bgemm_kernel");
+        // node lists per HSS level
+        std::vector<std::vector<int>> bylev(maxlev + 1);
+        for (size_t i = 0; i < nodes.size(); ++i) bylev[nodes[i].level].push_back((int)i);
+        std::vector<int> flat;
+        std::vector<size_t> loff(maxlev + 2, 0);
+        for (int l = 0; l <= maxlev; ++l) {
+            loff[l] = flat.size();
+            flat.insert(flat.end(), bylev[l].begin(), bylev[l].end());
+        }
+        loff[maxlev + 1] = flat.size();
+        DeviceVec<int> dflat;
+        HSS_TRY(dflat.upload(flat, st));
+        const size_t smem_rid = (size_t)max_rows * sizeof(double);
+        if (smem_rid > 48 * 1024)
+            HSS_TRY(cudaFuncSetAttribute(row_id_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_rid));
+        if (lowrank) {
+            transpose_samples_kernel<T><<<dim3(64, nf), 256, 0, st>>>(dfr.p, dnodes.p, ws.p, iws.p, rows.p);
+            NDHSS_LAUNCH_CHECK("transpose_samples_kernel");
+            row_id_kernel<T><<<(unsigned)bylev[0].size(), HT, smem_rid, st>>>(dflat.p + loff[0], dnodes.p, ws.p, iws.p, kk.p,
+                                                                            rows.p, eps, rank_cap);
+            NDHSS_LAUNCH_CHECK("row_id_kernel");
+            gather_rows_kernel<T><<<dim3(64, nf), 256, 0, st>>>(dfr.p, dnodes.p, ws.p, iws.p, kk.p);
+            NDHSS_LAUNCH_CHECK("gather_rows_kernel");
+            // Zt = X (R(J,:) Omega~) : needs the ranks on the host for the GEMM shapes
+            std::vector<int> hk(nodes.size());
+            HSS_TRY(cudaMemcpyAsync(hk.data(), kk.p, hk.size() * sizeof(int), cudaMemcpyDeviceToHost, st));
+            HSS_TRY(cudaStreamSynchronize(st));
+            std::vector<GemmJob> g2, g3;
+            for (int i = 0; i < nf; ++i) {
+                const int k = hk[fr[i].root];
+                const HNode& nd = nodes[fr[i].root];
+                g2.push_back({fr[i].RJ, fr[i].Ot, fr[i].T1, kcap, fr[i].ncol, kcap, k, r, fr[i].ncol, 0, 1.0});
+                g3.push_back({ws.p + nd.o_x, fr[i].T1, fr[i].Zt, nd.rows_cap, kcap, fr[i].n, fr[i].n, r, k, 0, 1.0});
+            }
+            DeviceVec<GemmJob> dg2, dg3;
+            HSS_TRY(dg2.upload(g2, st));
+            HSS_TRY(dg3.upload(g3, st));
+            bgemm_kernel<T><<<dim3((kcap + 63) / 64, (r + 63) / 64, nf), 256, 0, st>>>(dg2.p);
+            NDHSS_LAUNCH_CHECK("bgemm_kernel");
+            bgemm_kernel<T><<<dim3((maxM + 63) / 64, (r + 63) / 64, nf), 256, 0, st>>>(dg3.p);
+            NDHSS_LAUNCH_CHECK("bgemm_kernel");
+        } else {
+            for (int l = maxlev; l >= 1; --l) {
+                const unsigned cnt = (unsigned)(loff[l + 1] - loff[l]);
+                if (!cnt) continue;
+                form_sloc_kernel<T><<<cnt, HT, 0, st>>>(dflat.p + loff[l], dnodes.p, dfr.p, ws.p, iws.p, kk.p, rows.p);
+                NDHSS_LAUNCH_CHECK("form_sloc_kernel");
+                row_id_kernel<T><<<cnt, HT, smem_rid, st>>>(dflat.p + loff[l], dnodes.p, ws.p, iws.p, kk.p, rows.p, eps,
+                                                           rank_cap);
+                NDHSS_LAUNCH_CHECK("row_id_kernel");
+                finish_kernel<T><<<cnt, HT, 0, st>>>(dflat.p + loff[l], dnodes.p, dfr.p, ws.p, iws.p, kk.p, rows.p);
+                NDHSS_LAUNCH_CHECK("finish_kernel");
+            }
+            // estimator: Zt = HSS(S) Omega~
+            std::vector<const T*> xin(nf);
+            std::vector<T*> yout(nf);
+            std::vector<int64_t> lx(nf), ly(nf);
+            std::vector<int> ncs(nf, r);
+            for (int i = 0; i < nf; ++i) {
+                xin[i] = static_cast<const T*>(fr[i].Ot);
+                yout[i] = static_cast<T*>(fr[i].Zt);
+                lx[i] = ly[i] = fr[i].n;
+            }
+            DeviceVec<const T*> dx;
+            DeviceVec<T*> dy;
+            DeviceVec<int64_t> dlx, dly;
+            DeviceVec<int> dncs;
+            HSS_TRY(dx.upload(xin, st));
+            HSS_TRY(dy.upload(yout, st));
+            HSS_TRY(dlx.upload(lx, st));
+            HSS_TRY(dly.upload(ly, st));
+            HSS_TRY(dncs.upload(ncs, st));
+            std::vector<char> all(nf, 1);
+            ndhss_status rc = hss_matvec_run<T>(nodes, all, maxlev, dnodes.p, dfr.p, ws.p, ws.p, iws.p, kk.p, rows.p, dx.p,
+                                               dlx.p, dy.p, dly.p, dncs.p, (int64_t)kcap, st);
+            if (rc != NDHSS_OK) return rc;
+        }
+        DeviceVec<double> dn;
+        HSS_TRY(dn.alloc(2 * nf));
+        est_norm_kernel<T><<<nf, HT, 0, st>>>(dfr.p, r, dn.p);
+        NDHSS_LAUNCH_CHECK("est_norm_kernel");
+        std::vector<double> hn(2 * nf);
+        std::vector<int> hk(nodes.size());
+        HSS_TRY(cudaMemcpyAsync(hn.data(), dn.p, hn.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+        HSS_TRY(cudaMemcpyAsync(hk.data(), kk.p, hk.size() * sizeof(int), cudaMemcpyDeviceToHost, st));
+        HSS_TRY(cudaStreamSynchronize(st));
+        std::vector<int> done, still;
+        for (int i = 0; i < nf; ++i) {
+            const Problem& pb = probs[active[i]];
+            const int lim = lowrank ? std::min({pb.n, pb.ncol, rank_cap + OVERSAMPLE_MIN})
+                                    : std::min(pb.n, rank_cap + OVERSAMPLE_MIN);
+            if (hn[2 * i] <= eps * hn[2 * i + 1] || p >= lim) done.push_back(i);
+            else still.push_back(active[i]);
+        }
+        // finalize the retired problems
+        if (!done.empty()) {
+            if (lowrank) {
+                for (int i : done) {
+                    const int a = active[i];
+                    const int k = hk[fr[i].root];
+                    const HNode& nd = nodes[fr[i].root];
+                    kout[a] = k;
+                    auto& out = (*lr_host)[a];
+                    out.resize((size_t)fr[i].n * k + (size_t)k * fr[i].ncol);
+                    // X (n x k, ld rows_cap = n) then RJ (k x ncol, ld kcap -> k)
+                    if (k > 0) {
+                        HSS_TRY(cudaMemcpy2DAsync(out.data(), (size_t)fr[i].n * sizeof(T), ws.p + nd.o_x,
+                                                  (size_t)nd.rows_cap * sizeof(T), (size_t)fr[i].n * sizeof(T), k,
+                                                  cudaMemcpyDeviceToHost, st));
+                        HSS_TRY(cudaMemcpy2DAsync(out.data() + (size_t)fr[i].n * k, (size_t)k * sizeof(T), fr[i].RJ,
+                                                  (size_t)kcap * sizeof(T), (size_t)k * sizeof(T), fr[i].ncol,
+                                                  cudaMemcpyDeviceToHost, st));
+                    }
+                }
+                HSS_TRY(cudaStreamSynchronize(st));
+            } else {
+                // reconstruct S_HSS = HSS(S) I into scratch, then overwrite S
+                std::vector<char> keep(nf, 0);
+                for (int i : done) keep[i] = 1;
+                int64_t tot = 0;
+                std::vector<T*> ids(nf, nullptr), outs(nf, nullptr);
+                std::vector<int64_t> off_id(nf, 0), off_out(nf, 0), lds2(nf, 1);
+                std::vector<int> ncs(nf, 0);
+                for (int i : done) {
+                    const int64_t n = fr[i].n;
+                    off_id[i] = tot;
+                    tot += n * n;
+                    off_out[i] = tot;
+                    tot += n * n;
+                    lds2[i] = n;
+                    ncs[i] = (int)n;
+                }
+                std::vector<HNode> nodes2 = nodes;
+                int64_t hbsz = 0;
+                for (auto& nd : nodes2) {
+                    if (!keep[nd.front]) continue;
+                    const int64_t n = fr[nd.front].n;
+                    nd.o_xh = hbsz;
+                    hbsz += (int64_t)kcap * n;
+                    nd.o_yh = hbsz;
+                    hbsz += (int64_t)kcap * n;
+                }
+                DeviceVec<T> sc, hb;
+                HSS_TRY(sc.alloc(tot));
+                HSS_TRY(hb.alloc(hbsz));
+                std::vector<T*> idlist, srcs;
+                std::vector<int> nsz;
+                for (int i : done) {
+                    ids[i] = sc.p + off_id[i];
+                    outs[i] = sc.p + off_out[i];
+                    idlist.push_back(ids[i]);
+                    srcs.push_back(outs[i]);
+                    nsz.push_back(fr[i].n);
+                }
+                DeviceVec<HNode> dn2;
+                DeviceVec<T*> did, dout, didl, dsrc;
+                DeviceVec<int64_t> dld;
+                DeviceVec<int> dns, dwhich, dncs;
+                HSS_TRY(dn2.upload(nodes2, st));
+                HSS_TRY(did.upload(ids, st));
+                HSS_TRY(dout.upload(outs, st));
+                HSS_TRY(dld.upload(lds2, st));
+                HSS_TRY(didl.upload(idlist, st));
+                HSS_TRY(dsrc.upload(srcs, st));
+                HSS_TRY(dns.upload(nsz, st));
+                HSS_TRY(dwhich.upload(done, st));
+                HSS_TRY(dncs.upload(ncs, st));
+                eye_kernel<T><<<dim3(64, (unsigned)done.size()), 256, 0, st>>>(didl.p, dns.p);
+                NDHSS_LAUNCH_CHECK("eye_kernel");
+                ndhss_status rc = hss_matvec_run<T>(nodes2, keep, maxlev, dn2.p, dfr.p, ws.p, hb.p, iws.p, kk.p, rows.p,
+                                                   (const T* const*)did.p, dld.p, dout.p, dld.p, dncs.p, (int64_t)kcap, st);
+                if (rc != NDHSS_OK) return rc;
+                copy_back_kernel<T><<<dim3(64, (unsigned)done.size()), 256, 0, st>>>(dsrc.p, dfr.p, dwhich.p);
+                NDHSS_LAUNCH_CHECK("copy_back_kernel");
+                HSS_TRY(cudaStreamSynchronize(st));
+                for (int i : done) {
+                    int km = 0;
+                    for (size_t q = 0; q < nodes.size(); ++q)
+                        if (nodes[q].front == i && (int)q != fr[i].root) km = std::max(km, hk[q]);
+                    kout[active[i]] = km;
+                }
+            }
+        }
+        F.hss_rounds_max = std::max(F.hss_rounds_max, round + 1);
+        active = still;
+        p += r;
+        ++round;
+    }
+    return NDHSS_OK;
+}
+
+template <typename T>
+ndhss_status compress_level_impl(FactorData& F, const Tree& t, int level, const ndhss_factor_opts& o, cudaStream_t st) {
+    T* base = static_cast<T*>(F.d_front);
+    const int beta = std::max(o.beta, 1);
+    std::vector<Problem> sp, rp;
+    for (int s : F.levels[level]) {
+        const int64_t mi = F.m_i(s), mb = F.m_b(s), m = mi + mb;
+        T* Fs = base + F.foff[s];
+        const int par = t.parent(s);
+        if (mb > beta && par >= 0) {
+            int top = 0;
+            for (int q = 0; q < mb; ++q) top += (t.emap[t.b_off(s) + q] < t.m_i(par)) ? 1 : 0;
+            sp.push_back({s, (int)mb, (int)mb, m, Fs + mi * m + mi, top, (uint64_t)2 * s});
+        }
+        if (level < F.L_hss && mb > 0 && mi > 0) rp.push_back({s, (int)mi, (int)mb, m, Fs + mi * m, 0, (uint64_t)2 * s + 1});
+    }
+    std::vector<int> ks, kr;
+    if (!sp.empty()) {
+        ndhss_status rc = compress_problems<T>(sp, false, o, ks, nullptr, F, st);
+        if (rc != NDHSS_OK) return rc;
+        for (int k : ks) F.kmax = std::max(F.kmax, k);
+    }
+    if (!rp.empty()) {
+        std::vector<std::vector<T>> lr;
+        ndhss_status rc = compress_problems<T>(rp, true, o, kr, &lr, F, st);
+        if (rc != NDHSS_OK) return rc;
+        size_t tot = 0;
+        for (auto& v : lr) tot += v.size();
+        void* buf = nullptr;
+        if (cudaMalloc(&buf, std::max<size_t>(tot, 1) * sizeof(T)) != cudaSuccess) {
+            cudaGetLastError();
+            return set_error(NDHSS_ERR_OOM, "hss: low-rank storage of level %d", level);
+        }
+        F.lr_bufs.push_back(buf);
+        F.dev_bytes += (int64_t)(tot * sizeof(T));
+        size_t off = 0;
+        for (size_t i = 0; i < rp.size(); ++i) {
+            const int s = rp[i].node;
+            T* dst = static_cast<T*>(buf) + off;
+            if (!lr[i].empty())
+                HSS_TRY(cudaMemcpyAsync(dst, lr[i].data(), lr[i].size() * sizeof(T), cudaMemcpyHostToDevice, st));
+            F.lr_ptr[s] = reinterpret_cast<uint64_t>(dst);
+            F.lr_k[s] = kr[i];
+            F.kmax = std::max(F.kmax, kr[i]);
+            off += lr[i].size();
+        }
+        HSS_TRY(cudaStreamSynchronize(st));
+    }
+    return NDHSS_OK;
+}
+
+}  // namespace
+
+ndhss_status hss_compress_level(FactorData& F, const Tree& t, int level, const ndhss_factor_opts& o, cudaStream_t st) {
+    if (F.lr_ptr.size() != (size_t)F.nnodes) {
+        F.lr_ptr.assign(F.nnodes, 0);
+        F.lr_k.assign(F.nnodes, 0);
+    }
+    const bool cplx = F.vtype == NDHSS_C128;
+    if (!cplx && F.prec == NDHSS_FP64) return compress_level_impl<double>(F, t, level, o, st);
+    if (!cplx) return compress_level_impl<float>(F, t, level, o, st);
+    if (F.prec == NDHSS_FP64) return compress_level_impl<c128>(F, t, level, o, st);
+    return compress_level_impl<c64>(F, t, level, o, st);
+}
+
+}  // namespace ndhss

@@ -61,7 +61,7 @@ class FactorStats(C.Structure):
                 ("kmax", C.c_int32), ("prec", C.c_int32), ("launches", C.c_int64),
                 ("class_ms", C.c_double * 8), ("class_launches", C.c_int64 * 8), ("update_flops", C.c_double)]
 
-    CLASSES = ("assemble", "scatter", "panel", "prep", "update", "finalize")
+    CLASSES = ("assemble", "scatter", "panel", "prep", "update", "finalize", "compress")
 
     def as_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_ if k not in ("class_ms", "class_launches")}

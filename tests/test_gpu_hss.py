@@ -1,0 +1,108 @@
+"""GPU parity of the compressed tier (Alg. 3.4 with Alg. A.1 and low-rank R)
+against the FP64 oracle (oracle/hss.py).
+
+At the switching level the inputs of the compression are the exact Schur
+complements on both sides and the Gaussian samples are the same Philox
+streams, so the FP64 GPU reproduces the oracle's HSS reconstruction to
+rounding (checked at 1e-9, the normwise level of the FP64 front parity).
+Above it the inputs already carry compression errors of order eps_hss, so the
+comparison is against the tolerance: within 50 eps of the oracle's blocks.
+"""
+import numpy as np
+import pytest
+
+from ndhss_inputs import helmholtz_impedance, poisson_dirichlet
+from oracle.gmres import gmres as oracle_gmres
+from oracle.hss import apply_compressed, factor_compressed
+from oracle.tree import build_tree
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+EPS = 1e-6
+
+
+@pytest.fixture(scope="module")
+def nd():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2105_07791_gb300 import build, ndhss
+    build.build()
+    ndhss.load()
+    return ndhss
+
+
+CASES = {
+    "poisson_p1_64_h3": lambda: (poisson_dirichlet(64), 64, 3),
+    "helm_p2_40_h3": lambda: (helmholtz_impedance(40, 2, 15.0, seed=2), 64, 3),
+    "helm_p1_72_h4_leaf32": lambda: (helmholtz_impedance(72, 1, 12.0, seed=5), 32, 4),
+}
+
+
+@pytest.fixture(scope="module", params=list(CASES))
+def case(request, nd):
+    P, leaf, hl = CASES[request.param]()
+    T = build_tree(P.coords, P.A.indptr, P.A.indices, leaf)
+    fac = factor_compressed(T, P.A, hss_levels=hl, eps=EPS, beta=64, k0=32, r=16, seed=11)
+    tree = nd.ndhss_build_tree(P.coords, P.A.indptr, P.A.indices, leaf)
+    M = nd.DeviceCSR(P.A)
+    return dict(P=P, T=T, fac=fac, tree=tree, M=M, hl=hl)
+
+
+def _factor(nd, c, prec):
+    M = c["M"]
+    opts = nd.make_factor_opts(prec=prec, hss_levels=c["hl"], eps_hss=EPS, beta=64, k0=32, r=16, seed=11)
+    return nd.ndhss_factor(c["tree"], M.vtype, M.rowptr, M.col, M.vals, opts)
+
+
+def _rel(a, b):
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+def test_compressed_blocks_match_oracle_fp64(nd, case):
+    T, fac = case["T"], case["fac"]
+    f = _factor(nd, case, 0)
+    lev = T.f("level")
+    Lh = fac.L_hss
+    assert Lh >= 1
+    checked_first = checked_above = checked_r = 0
+    for s in range(T.nnodes):
+        mi, mb = int(T.node_info[s, 5]), int(T.node_info[s, 7])
+        if lev[s] > Lh or mb == 0:
+            continue
+        S = nd.ndhss_factor_get_block(f, s, 3, mi, mb)
+        if lev[s] == Lh:
+            assert _rel(S, fac.S[s]) <= 1e-9, (s, _rel(S, fac.S[s]))
+            checked_first += 1
+        else:
+            assert _rel(S, fac.S[s]) <= 50 * EPS, (s, _rel(S, fac.S[s]))
+            checked_above += 1
+        if lev[s] < Lh and mi > 0:
+            R = nd.ndhss_factor_get_block(f, s, 1, mi, mb)
+            Ro = fac.R[s].matmat(np.eye(mb)) if hasattr(fac.R[s], "matmat") else fac.R[s]
+            assert _rel(R, Ro) <= 50 * EPS, (s, _rel(R, Ro))
+            L = nd.ndhss_factor_get_block(f, s, 2, mi, mb)
+            assert np.array_equal(L, R.T)
+            checked_r += 1
+    assert checked_first > 0 and checked_above > 0 and checked_r > 0
+    st = nd.ndhss_factor_stats_get(f)
+    assert 0 < st["kmax"] <= 512
+    assert abs(st["kmax"] - fac.kmax) <= 16
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_compressed_apply_and_gmres(nd, case, prec):
+    P, fac, M = case["P"], case["fac"], case["M"]
+    f = _factor(nd, case, prec)
+    b = P.b if P.b.ndim == 1 else P.b[:, 0]
+    bd = torch.from_numpy(np.ascontiguousarray(b.astype(np.complex128 if M.vtype == 1 else np.float64))).cuda()
+    y = torch.empty_like(bd)
+    nd.ndhss_apply(f, bd, y)
+    yo = apply_compressed(fac, b)
+    assert _rel(y.cpu().numpy(), yo) <= (1e-4 if prec == 0 else 1e-3)
+    x = torch.zeros_like(bd)
+    st = nd.ndhss_gmres(f, M.rowptr, M.col, M.vals, bd, x, tol=1e-8)
+    xs = x.cpu().numpy()
+    assert st["converged"] and np.linalg.norm(b - P.A @ xs) / np.linalg.norm(b) <= 1e-8
+    ro = oracle_gmres(P.A, b, lambda v: apply_compressed(fac, v), tol=1e-8)
+    assert st["iters"] <= ro.iters + 2, (st, ro.iters)
+    assert _rel(xs, ro.x) <= 1e-6
