@@ -14,7 +14,10 @@ TEST INFRASTRUCTURE ONLY (see ``oracle/__init__.py``).
   processed bottom-up; a row interpolative decomposition (Eq. A.1) of every
   local sample block S_loc ~ U_i S_loc(J_i, :) chooses the skeleton rows; the
   estimator of Eq. 2.7 on r fresh samples decides whether to stop or to
-  increase k by r and reuse all samples.
+  increase k by r and reuse all samples.  Where the paper is silent (an
+  estimate that never reaches eps) the rank stops growing once a round of r
+  more samples fails to halve the estimated error: the estimate then sits at
+  the floor set by the arithmetic, not by the rank.
 * Gaussian samples come from Philox4x32-10 (Salmon et al., SC'11) with the
   Box-Muller transform, keyed by (seed, stream), so any implementation of
   the same definition draws the same matrices.
@@ -227,6 +230,7 @@ def hss_compress(A: np.ndarray, tree: list, eps: float, k0: int = 32, r: int = 1
     Om = gaussian(n, k + r, seed, stream * 64 + 0)
     S = A @ Om
     rnd = 0
+    prev_err = np.inf
     while True:
         H = HSS(n=n, tree=tree, dtype=dtype)
         Hd = {}                                    # node -> (Omega_i, S_i)
@@ -270,8 +274,12 @@ def hss_compress(A: np.ndarray, tree: list, eps: float, k0: int = 32, r: int = 1
         St = A @ Ot
         err = np.linalg.norm(St - hss_matvec(H, Ot))
         ref = np.linalg.norm(St)
-        if err <= eps * ref or nsamp >= min(n, rank_cap + oversample_min) or len(tree) == 1:
+        # stop at eps, when the samples exhaust the matrix, or when r more samples did not
+        # halve the estimated error (the estimate then sits at the arithmetic's floor)
+        if (err <= eps * ref or nsamp >= min(n, rank_cap + oversample_min) or len(tree) == 1
+                or err > 0.5 * prev_err):
             return H
+        prev_err = err
         Om = np.hstack([Om, Ot])
         S = np.hstack([S, St])
         k += r
@@ -307,6 +315,7 @@ def lowrank_rows(R: np.ndarray, eps: float, k0: int = 32, r: int = 16, seed: int
     Om = gaussian(nb, k + r, seed, stream * 64 + 32)
     Y = R @ Om
     rnd = 0
+    prev_err = np.inf
     while True:
         maxr = min(rank_cap, max(1, Y.shape[1] - oversample_min), m)
         J, X = row_id(Y, eps, maxr)
@@ -314,8 +323,10 @@ def lowrank_rows(R: np.ndarray, eps: float, k0: int = 32, r: int = 16, seed: int
         Ot = gaussian(nb, r, seed, stream * 64 + 33 + rnd)
         Yt = R @ Ot
         err = np.linalg.norm(Yt - lr.matmat(Ot))
-        if err <= eps * np.linalg.norm(Yt) or Y.shape[1] >= min(m, nb, rank_cap + oversample_min):
+        if (err <= eps * np.linalg.norm(Yt) or Y.shape[1] >= min(m, nb, rank_cap + oversample_min)
+                or err > 0.5 * prev_err):
             return lr
+        prev_err = err
         Om = np.hstack([Om, Ot])
         Y = np.hstack([Y, Yt])
         k += r

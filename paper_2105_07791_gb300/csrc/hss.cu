@@ -629,26 +629,27 @@ std::vector<HCl> cluster_tree(int n, int top, int beta) {
     return t;
 }
 
+// Stream-ordered scratch (pool allocator): no device-wide synchronisation on
+// allocation or release, uploads from pageable host memory are staged by the
+// runtime before cudaMemcpyAsync returns.
 template <typename U>
 struct DeviceVec {
     U* p = nullptr;
     size_t n = 0;
-    ~DeviceVec() { if (p) cudaFree(p); }
-    cudaError_t upload(const std::vector<U>& v, cudaStream_t st) {
-        if (p) cudaFree(p);
-        p = nullptr;
-        n = v.size();
-        cudaError_t e = cudaMalloc(&p, std::max<size_t>(n, 1) * sizeof(U));
-        if (e != cudaSuccess) return e;
-        if (n) e = cudaMemcpyAsync(p, v.data(), n * sizeof(U), cudaMemcpyHostToDevice, st);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-        return e;
-    }
+    cudaStream_t st = nullptr;
+    explicit DeviceVec(cudaStream_t s = nullptr) : st(s) {}
+    ~DeviceVec() { if (p) cudaFreeAsync(p, st); }
     cudaError_t alloc(size_t count) {
-        if (p) cudaFree(p);
+        if (p) cudaFreeAsync(p, st);
         p = nullptr;
         n = count;
-        return cudaMalloc(&p, std::max<size_t>(n, 1) * sizeof(U));
+        return cudaMallocAsync((void**)&p, std::max<size_t>(n, 1) * sizeof(U), st);
+    }
+    cudaError_t upload(const std::vector<U>& v, cudaStream_t s) {
+        st = s;
+        cudaError_t e = alloc(v.size());
+        if (e == cudaSuccess && !v.empty()) e = cudaMemcpyAsync(p, v.data(), v.size() * sizeof(U), cudaMemcpyHostToDevice, st);
+        return e;
     }
 };
 
@@ -685,7 +686,7 @@ ndhss_status hss_matvec_run(const std::vector<HNode>& nodes, const std::vector<c
     for (size_t i = 0; i < nodes.size(); ++i)
         if (keep[nodes[i].front] && nodes[i].c1 < 0) flat.push_back((int)i);
     const size_t leaf_cnt = flat.size() - leaf_off;
-    DeviceVec<int> dflat;
+    DeviceVec<int> dflat(st);
     HSS_TRY(dflat.upload(flat, st));
     for (int l = maxlev; l >= 1; --l) {
         const unsigned cnt = (unsigned)(up_off[l + 1] - up_off[l]);
@@ -732,6 +733,7 @@ ndhss_status compress_problems(std::vector<Problem>& probs, bool lowrank, const 
     if (lr_host) lr_host->assign(probs.size(), {});
     std::vector<int> active(probs.size());
     for (size_t i = 0; i < probs.size(); ++i) active[i] = (int)i;
+    std::vector<double> prev_err(probs.size(), INFINITY);
     int p = k0 + r;
     int round = 0;
     while (!active.empty()) {
@@ -798,8 +800,8 @@ ndhss_status compress_problems(std::vector<Problem>& probs, bool lowrank, const 
             nd.o_xh = take((int64_t)kcap * r);
             nd.o_yh = take((int64_t)kcap * r);
         }
-        DeviceVec<T> ws;
-        DeviceVec<int> iws, kk, rows;
+        DeviceVec<T> ws(st);
+        DeviceVec<int> iws(st), kk(st), rows(st);
         HSS_TRY(ws.alloc(ews));
         HSS_TRY(iws.alloc(iwsz));
         HSS_TRY(kk.alloc(nodes.size()));
@@ -814,8 +816,8 @@ ndhss_status compress_problems(std::vector<Problem>& probs, bool lowrank, const 
             fr[i].T1 = ws.p + o_t1[i];
             fr[i].RJ = ws.p + o_rj[i];
         }
-        DeviceVec<HFront> dfr;
-        DeviceVec<HNode> dnodes;
+        DeviceVec<HFront> dfr(st);
+        DeviceVec<HNode> dnodes(st);
         HSS_TRY(dfr.upload(fr, st));
         HSS_TRY(dnodes.upload(nodes, st));
         // Gaussian samples, block by block exactly as the oracle draws them
@@ -828,7 +830,7 @@ ndhss_status compress_problems(std::vector<Problem>& probs, bool lowrank, const 
             for (int q = 0; q < round; ++q) gj.push_back({fr[i].Om, rows_o, rows_o, r, k0 + r + q * r, sb + 1 + q});
             gj.push_back({fr[i].Ot, rows_o, rows_o, r, 0, sb + 1 + round});
         }
-        DeviceVec<GaussJob> dgj;
+        DeviceVec<GaussJob> dgj(st);
         HSS_TRY(dgj.upload(gj, st));
         gauss_kernel<T><<<dim3(64, (unsigned)gj.size()), 256, 0, st>>>(dgj.p, o.seed);
         NDHSS_LAUNCH_CHECK("gauss_kernel");
@@ -843,7 +845,7 @@ ndhss_status compress_problems(std::vector<Problem>& probs, bool lowrank, const 
             maxM = std::max(maxM, pb.n);
             maxN = std::max(maxN, p);
         }
-        DeviceVec<GemmJob> dgm;
+        DeviceVec<GemmJob> dgm(st);
         HSS_TRY(dgm.upload(gm, st));
         bgemm_kernel<T><<<dim3((maxM + 63) / 64, (maxN + 63) / 64, (unsigned)gm.size()), 256, 0, st>>>(dgm.p);
         NDHSS_LAUNCH_CHECK("bgemm_kernel");
@@ -857,7 +859,7 @@ ndhss_status compress_problems(std::vector<Problem>& probs, bool lowrank, const 
             flat.insert(flat.end(), bylev[l].begin(), bylev[l].end());
         }
         loff[maxlev + 1] = flat.size();
-        DeviceVec<int> dflat;
+        DeviceVec<int> dflat(st);
         HSS_TRY(dflat.upload(flat, st));
         const size_t smem_rid = (size_t)max_rows * sizeof(double);
         if (smem_rid > 48 * 1024)
@@ -881,7 +883,7 @@ ndhss_status compress_problems(std::vector<Problem>& probs, bool lowrank, const 
                 g2.push_back({fr[i].RJ, fr[i].Ot, fr[i].T1, kcap, fr[i].ncol, kcap, k, r, fr[i].ncol, 0, 1.0});
                 g3.push_back({ws.p + nd.o_x, fr[i].T1, fr[i].Zt, nd.rows_cap, kcap, fr[i].n, fr[i].n, r, k, 0, 1.0});
             }
-            DeviceVec<GemmJob> dg2, dg3;
+            DeviceVec<GemmJob> dg2(st), dg3(st);
             HSS_TRY(dg2.upload(g2, st));
             HSS_TRY(dg3.upload(g3, st));
             bgemm_kernel<T><<<dim3((kcap + 63) / 64, (r + 63) / 64, nf), 256, 0, st>>>(dg2.p);
@@ -910,10 +912,10 @@ ndhss_status compress_problems(std::vector<Problem>& probs, bool lowrank, const 
                 yout[i] = static_cast<T*>(fr[i].Zt);
                 lx[i] = ly[i] = fr[i].n;
             }
-            DeviceVec<const T*> dx;
-            DeviceVec<T*> dy;
-            DeviceVec<int64_t> dlx, dly;
-            DeviceVec<int> dncs;
+            DeviceVec<const T*> dx(st);
+            DeviceVec<T*> dy(st);
+            DeviceVec<int64_t> dlx(st), dly(st);
+            DeviceVec<int> dncs(st);
             HSS_TRY(dx.upload(xin, st));
             HSS_TRY(dy.upload(yout, st));
             HSS_TRY(dlx.upload(lx, st));
@@ -924,7 +926,7 @@ ndhss_status compress_problems(std::vector<Problem>& probs, bool lowrank, const 
                                                dlx.p, dy.p, dly.p, dncs.p, (int64_t)kcap, st);
             if (rc != NDHSS_OK) return rc;
         }
-        DeviceVec<double> dn;
+        DeviceVec<double> dn(st);
         HSS_TRY(dn.alloc(2 * nf));
         est_norm_kernel<T><<<nf, HT, 0, st>>>(dfr.p, r, dn.p);
         NDHSS_LAUNCH_CHECK("est_norm_kernel");
@@ -938,8 +940,12 @@ ndhss_status compress_problems(std::vector<Problem>& probs, bool lowrank, const 
             const Problem& pb = probs[active[i]];
             const int lim = lowrank ? std::min({pb.n, pb.ncol, rank_cap + OVERSAMPLE_MIN})
                                     : std::min(pb.n, rank_cap + OVERSAMPLE_MIN);
-            if (hn[2 * i] <= eps * hn[2 * i + 1] || p >= lim) done.push_back(i);
+            // stop when eps is met, when the samples exhaust the block, or when a round did
+            // not halve the estimated error (it then sits at the arithmetic's floor)
+            const double err = hn[2 * i];
+            if (err <= eps * hn[2 * i + 1] || p >= lim || err > 0.5 * prev_err[active[i]]) done.push_back(i);
             else still.push_back(active[i]);
+            prev_err[active[i]] = err;
         }
         // finalize the retired problems
         if (!done.empty()) {
@@ -989,7 +995,7 @@ ndhss_status compress_problems(std::vector<Problem>& probs, bool lowrank, const 
                     nd.o_yh = hbsz;
                     hbsz += (int64_t)kcap * n;
                 }
-                DeviceVec<T> sc, hb;
+                DeviceVec<T> sc(st), hb(st);
                 HSS_TRY(sc.alloc(tot));
                 HSS_TRY(hb.alloc(hbsz));
                 std::vector<T*> idlist, srcs;
@@ -1001,10 +1007,10 @@ ndhss_status compress_problems(std::vector<Problem>& probs, bool lowrank, const 
                     srcs.push_back(outs[i]);
                     nsz.push_back(fr[i].n);
                 }
-                DeviceVec<HNode> dn2;
-                DeviceVec<T*> did, dout, didl, dsrc;
-                DeviceVec<int64_t> dld;
-                DeviceVec<int> dns, dwhich, dncs;
+                DeviceVec<HNode> dn2(st);
+                DeviceVec<T*> did(st), dout(st), didl(st), dsrc(st);
+                DeviceVec<int64_t> dld(st);
+                DeviceVec<int> dns(st), dwhich(st), dncs(st);
                 HSS_TRY(dn2.upload(nodes2, st));
                 HSS_TRY(did.upload(ids, st));
                 HSS_TRY(dout.upload(outs, st));
