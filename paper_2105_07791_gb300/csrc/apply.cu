@@ -145,9 +145,10 @@ downsweep_kernel(const int32_t* __restrict__ tasks, const int32_t* __restrict__ 
 }
 
 
-// Low-rank levels (R ~ X R(J, :), X m_i x k, RJ k x m_b; L = R^T by symmetry):
-// one CTA per node.
-// up-sweep:   t = X^T y(I^s);  y(B^s) += RJ^T t
+// Low-rank levels (R ~ X R(J, :), stored as X (m_i x k) and RJt = R(J, :)^T
+// (m_b x k), both column-major; L = R^T by symmetry): one CTA per node, warps
+// reduce along contiguous columns.
+// up-sweep:   t = X^T y(I^s);  y(B^s) += RJt t
 template <typename T>
 __global__ void __launch_bounds__(AT)
 lr_upsweep_kernel(const int32_t* __restrict__ list, const int32_t* __restrict__ node, const uint64_t* __restrict__ lrp,
@@ -158,7 +159,7 @@ lr_upsweep_kernel(const int32_t* __restrict__ list, const int32_t* __restrict__ 
     const int m_i = nf(node, s, 5), m_b = nf(node, s, 7), i_off = nf(node, s, 4), b_off = nf(node, s, 6);
     const int k = lrk[s];
     const T* X = reinterpret_cast<const T*>(lrp[s]);
-    const T* RJ = X + (int64_t)m_i * k;
+    const T* RJt = X + (int64_t)m_i * k;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int a = warp; a < k; a += AW) {
         T acc = zero<T>();
@@ -169,14 +170,13 @@ lr_upsweep_kernel(const int32_t* __restrict__ list, const int32_t* __restrict__ 
     __syncthreads();
     for (int j = threadIdx.x; j < m_b; j += AT) {
         T acc = zero<T>();
-        const T* col = RJ + (int64_t)j * k;
-        for (int a = 0; a < k; ++a) acc = fmac(col[a], t[a], acc);
+        for (int a = 0; a < k; ++a) acc = fmac(RJt[(int64_t)a * m_b + j], t[a], acc);
         const int g = blist[b_off + j];
         y[g] = y[g] + acc;
     }
 }
 
-// down-sweep: t = RJ z(B^s);  z(I^s) += X t
+// down-sweep: t = RJt^T z(B^s);  z(I^s) += X t
 template <typename T>
 __global__ void __launch_bounds__(AT)
 lr_downsweep_kernel(const int32_t* __restrict__ list, const int32_t* __restrict__ node, const uint64_t* __restrict__ lrp,
@@ -188,13 +188,15 @@ lr_downsweep_kernel(const int32_t* __restrict__ list, const int32_t* __restrict_
     T* zb = reinterpret_cast<T*>(smem_raw);
     T* t = zb + m_b;
     const T* X = reinterpret_cast<const T*>(lrp[s]);
-    const T* RJ = X + (int64_t)m_i * k;
+    const T* RJt = X + (int64_t)m_i * k;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int j = threadIdx.x; j < m_b; j += AT) zb[j] = z[blist[b_off + j]];
     __syncthreads();
-    for (int a = threadIdx.x; a < k; a += AT) {
+    for (int a = warp; a < k; a += AW) {
         T acc = zero<T>();
-        for (int j = 0; j < m_b; ++j) acc = fmac(RJ[(int64_t)j * k + a], zb[j], acc);
-        t[a] = acc;
+        for (int j = lane; j < m_b; j += 32) acc = fmac(RJt[(int64_t)a * m_b + j], zb[j], acc);
+        for (int o = 16; o; o >>= 1) acc = acc + shfl_xor_t(acc, o);
+        if (lane == 0) t[a] = acc;
     }
     __syncthreads();
     for (int i = threadIdx.x; i < m_i; i += AT) {

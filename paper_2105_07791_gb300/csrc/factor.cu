@@ -822,7 +822,7 @@ static ndhss_status get_block_impl(const ndhss_factorization* fh, int32_t node, 
     if (ld < std::max<int64_t>(rows, 1)) return set_error(NDHSS_ERR_INVALID_ARG, "ndhss_factor_get_block: ld too small");
     if (rows == 0 || cols == 0) return NDHSS_OK;
     if ((which == 1 || which == 2) && !F.lr_ptr.empty() && F.lr_ptr[node]) {
-        // low-rank R = X R(J, :) (m_i x k, k x m_b); L = R^T
+        // low-rank R = X R(J, :): X (m_i x k) then R(J, :)^T (m_b x k); L = R^T
         const int64_t k = F.lr_k[node];
         std::vector<unsigned char> lb((size_t)(mi * k + k * mb) * F.esize);
         NDHSS_CUDA_TRY(cudaDeviceSynchronize());
@@ -834,7 +834,7 @@ static ndhss_status get_block_impl(const ndhss_factorization* fh, int32_t node, 
                 double re = 0, im = 0;
                 for (int64_t a = 0; a < k; ++a) {
                     double xr, xi, rr, ri;
-                    const size_t xo = (size_t)(a * mi + i), ro = (size_t)(mi * k + j * k + a);
+                    const size_t xo = (size_t)(a * mi + i), ro = (size_t)(mi * k + a * mb + j);
                     if (!cplx && F.prec == NDHSS_FP64) { xr = ((double*)lb.data())[xo]; rr = ((double*)lb.data())[ro]; xi = ri = 0; }
                     else if (!cplx) { xr = ((float*)lb.data())[xo]; rr = ((float*)lb.data())[ro]; xi = ri = 0; }
                     else if (F.prec == NDHSS_FP64) {

@@ -64,6 +64,13 @@ __device__ void philox_normals(uint64_t seed, uint64_t stream, uint64_t blk, dou
     out[3] = r1 * sin(pi2 * u3);
 }
 
+__device__ __forceinline__ double shfl_xor_h(double v, int o) { return __shfl_xor_sync(0xffffffffu, v, o); }
+__device__ __forceinline__ float shfl_xor_h(float v, int o) { return __shfl_xor_sync(0xffffffffu, v, o); }
+template <typename R>
+__device__ __forceinline__ Cx<R> shfl_xor_h(Cx<R> v, int o) {
+    return {__shfl_xor_sync(0xffffffffu, v.x, o), __shfl_xor_sync(0xffffffffu, v.y, o)};
+}
+
 template <typename T> __device__ __forceinline__ T real_to(double v);
 template <> __device__ __forceinline__ double real_to<double>(double v) { return v; }
 template <> __device__ __forceinline__ float real_to<float>(double v) { return (float)v; }
@@ -114,6 +121,7 @@ struct GemmJob {
     int64_t lda, ldb, ldc;
     int M, N, K, beta;
     double alpha;
+    int transA = 0, transB = 0;   // operand stored transposed (plain transpose, no conjugation)
 };
 
 template <typename T>
@@ -134,13 +142,27 @@ __global__ void __launch_bounds__(256) bgemm_kernel(const GemmJob* __restrict__ 
 #pragma unroll
         for (int b = 0; b < 4; ++b) acc[a][b] = zero<T>();
     for (int kc = 0; kc < jb.K; kc += TK) {
-        for (int q = tid; q < TK * TT; q += 256) {
-            const int ii = q % TT, l = q / TT;
-            sA[l][ii] = (kc + l < jb.K && i0 + ii < jb.M) ? A[(int64_t)(kc + l) * jb.lda + i0 + ii] : zero<T>();
+        if (!jb.transA) {
+            for (int q = tid; q < TK * TT; q += 256) {
+                const int ii = q % TT, l = q / TT;
+                sA[l][ii] = (kc + l < jb.K && i0 + ii < jb.M) ? A[(int64_t)(kc + l) * jb.lda + i0 + ii] : zero<T>();
+            }
+        } else {
+            for (int q = tid; q < TK * TT; q += 256) {
+                const int l = q % TK, ii = q / TK;
+                sA[l][ii] = (kc + l < jb.K && i0 + ii < jb.M) ? A[(i0 + ii) * jb.lda + kc + l] : zero<T>();
+            }
         }
-        for (int q = tid; q < TK * TT; q += 256) {
-            const int l = q % TK, jj = q / TK;
-            sB[l][jj] = (kc + l < jb.K && j0 + jj < jb.N) ? B[(j0 + jj) * jb.ldb + kc + l] : zero<T>();
+        if (!jb.transB) {
+            for (int q = tid; q < TK * TT; q += 256) {
+                const int l = q % TK, jj = q / TK;
+                sB[l][jj] = (kc + l < jb.K && j0 + jj < jb.N) ? B[(j0 + jj) * jb.ldb + kc + l] : zero<T>();
+            }
+        } else {
+            for (int q = tid; q < TK * TT; q += 256) {
+                const int jj = q % TT, l = q / TT;
+                sB[l][jj] = (kc + l < jb.K && j0 + jj < jb.N) ? B[(int64_t)(kc + l) * jb.ldb + j0 + jj] : zero<T>();
+            }
         }
         __syncthreads();
 #pragma unroll
@@ -266,30 +288,35 @@ row_id_kernel(const int* __restrict__ list, const HNode* __restrict__ nodes, T* 
     const int id = list[blockIdx.x];
     const HNode nd = nodes[id];
     const int rows = rows_in[id], p = nd.p;
-    T* W = ws + nd.o_w;
+    T* W = ws + nd.o_w;                  // p x rows, column c = row c of S_loc (contiguous)
     int* piv = iws + nd.o_piv;
-    double* nrm = reinterpret_cast<double*>(smem);                      // rows
+    double* nrm = reinterpret_cast<double*>(smem);          // remaining squared norms (rows)
+    T* vsh = reinterpret_cast<T*>(nrm + ((rows + 1) & ~1));  // reflector (p), 16-byte aligned
     __shared__ double s_val[HT / 32];
     __shared__ int s_idx[HT / 32];
-    __shared__ double s_r11, s_bestv;
+    __shared__ double s_r11, s_bestv, s_vn2;
     __shared__ int s_best;
-    __shared__ double s_xn2, s_vn2;
-    __shared__ T s_alpha, s_beta;
+    __shared__ T s_beta;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    constexpr int NW = HT / 32;
+    // initial squared row norms, one warp per column
+    for (int c = warp; c < rows; c += NW) {
+        const T* col = W + (int64_t)c * p;
+        double sacc = 0.0;
+        for (int j = lane; j < p; j += 32) sacc += nrm2v(col[j]);
+        for (int o = 16; o; o >>= 1) sacc += __shfl_xor_sync(0xffffffffu, sacc, o);
+        if (lane == 0) nrm[c] = sacc;
+    }
     for (int c = tid; c < rows; c += HT) piv[c] = c;
     const int kmax = min(min(nd.kcap, rank_cap), min(p, rows));
     int t = 0;
     __syncthreads();
     for (; t < min(p, rows); ++t) {
-        // remaining column norms and the pivot
         double best = -1.0;
         int bi = INT_MAX;
         for (int c = t + tid; c < rows; c += HT) {
-            double s = 0.0;
-            const T* col = W + (int64_t)c * p;
-            for (int j = t; j < p; ++j) s += nrm2v(col[j]);
-            nrm[c] = s;
-            if (s > best) { best = s; bi = c; }
+            const double v = nrm[c];
+            if (v > best) { best = v; bi = c; }
         }
         for (int o = 16; o; o >>= 1) {
             const double ov = __shfl_down_sync(0xffffffffu, best, o);
@@ -298,19 +325,23 @@ row_id_kernel(const int* __restrict__ list, const HNode* __restrict__ nodes, T* 
         }
         if (lane == 0) { s_val[warp] = best; s_idx[warp] = bi; }
         __syncthreads();
-        if (tid == 0) {
-            double bv = -1.0;
-            int bb = INT_MAX;
-            for (int w = 0; w < HT / 32; ++w)
-                if (s_val[w] > bv || (s_val[w] == bv && s_idx[w] < bb)) { bv = s_val[w]; bb = s_idx[w]; }
-            s_best = bb;
-            s_bestv = sqrt(fmax(bv, 0.0));
-            if (t == 0) s_r11 = s_bestv;
+        if (warp == 0) {
+            double bv = lane < NW ? s_val[lane] : -1.0;
+            int bb = lane < NW ? s_idx[lane] : INT_MAX;
+            for (int o = 16; o; o >>= 1) {
+                const double ov = __shfl_down_sync(0xffffffffu, bv, o);
+                const int oi = __shfl_down_sync(0xffffffffu, bb, o);
+                if (ov > bv || (ov == bv && oi < bb)) { bv = ov; bb = oi; }
+            }
+            if (lane == 0) {
+                s_best = bb;
+                s_bestv = sqrt(fmax(bv, 0.0));
+                if (t == 0) s_r11 = s_bestv;
+            }
         }
         __syncthreads();
         const int cb = s_best;
-        if (t >= kmax || !(s_bestv > eps * s_r11) || cb == INT_MAX) break;
-        // interchange columns t and cb
+        if (t >= kmax || cb == INT_MAX || !(s_bestv > eps * s_r11)) break;
         if (cb != t) {
             for (int j = tid; j < p; j += HT) {
                 const T a = W[(int64_t)t * p + j];
@@ -321,36 +352,47 @@ row_id_kernel(const int* __restrict__ list, const HNode* __restrict__ nodes, T* 
                 const int a = piv[t];
                 piv[t] = piv[cb];
                 piv[cb] = a;
+                const double n1 = nrm[t];
+                nrm[t] = nrm[cb];
+                nrm[cb] = n1;
             }
         }
         __syncthreads();
-        // Householder reflector of W(t:p, t): v = x - beta e1, beta = -phase(x0) ||x||
+        // reflector v = x - beta e1 of x = W(t:p, t), beta = -phase(x0) ||x||
         T* xcol = W + (int64_t)t * p;
+        for (int j = t + tid; j < p; j += HT) vsh[j] = xcol[j];
+        __syncthreads();
         if (tid == 0) {
-            double xn2 = 0.0;
-            for (int j = t; j < p; ++j) xn2 += nrm2v(xcol[j]);
-            const T a0 = xcol[t];
-            const double aa = absv(a0), xn = sqrt(xn2);
+            const double xn = s_bestv;
+            const T a0 = vsh[t];
+            const double aa = absv(a0);
             T ph = one<T>();
             if (aa > 0) ph = scale(a0, (real)(1.0 / aa));
             const T beta = scale(ph, (real)(-xn));
             const T v0 = a0 - beta;
-            s_vn2 = xn2 - aa * aa + nrm2v(v0);
-            s_alpha = v0;
+            s_vn2 = xn * xn - aa * aa + nrm2v(v0);
+            vsh[t] = v0;
             s_beta = beta;
         }
         __syncthreads();
         const double vn2 = s_vn2;
-        const T v0 = s_alpha;
         if (vn2 > 0) {
             const real f = (real)(2.0 / vn2);
-            for (int c = t + 1 + tid; c < rows; c += HT) {
+            for (int c = t + 1 + warp; c < rows; c += NW) {
                 T* col = W + (int64_t)c * p;
-                T w = conjv(v0) * col[t];
-                for (int j = t + 1; j < p; ++j) w = fmac(conjv(xcol[j]), col[j], w);
+                T w = zero<T>();
+                for (int j = t + lane; j < p; j += 32) w = fmac(conjv(vsh[j]), col[j], w);
+                for (int o = 16; o; o >>= 1) w = w + shfl_xor_h(w, o);
                 const T g = scale(w, f);
-                col[t] = col[t] - v0 * g;
-                for (int j = t + 1; j < p; ++j) col[j] = col[j] - xcol[j] * g;
+                // update, and the exact remaining norm in the same pass
+                double sacc = 0.0;
+                for (int j = t + lane; j < p; j += 32) {
+                    const T u = col[j] - vsh[j] * g;
+                    col[j] = u;
+                    if (j > t) sacc += nrm2v(u);
+                }
+                for (int o = 16; o; o >>= 1) sacc += __shfl_xor_sync(0xffffffffu, sacc, o);
+                if (lane == 0) nrm[c] = sacc;
             }
         }
         __syncthreads();
@@ -358,7 +400,7 @@ row_id_kernel(const int* __restrict__ list, const HNode* __restrict__ nodes, T* 
         __syncthreads();
     }
     const int k = t;
-    // T = R11^{-1} R12 in place of R12 (one column per thread)
+    // T = R11^{-1} R12 in place of R12, one warp per column (rows of T in lanes sequentially)
     for (int c = k + tid; c < rows; c += HT) {
         T* col = W + (int64_t)c * p;
         for (int i = k - 1; i >= 0; --i) {
@@ -370,7 +412,7 @@ row_id_kernel(const int* __restrict__ list, const HNode* __restrict__ nodes, T* 
     __syncthreads();
     T* X = ws + nd.o_x;
     for (int q = tid; q < rows * k; q += HT) {
-        const int i = q % rows, a = q / rows;        // i = pivoted position
+        const int i = q % rows, a = q / rows;
         T v;
         if (i < k) v = (i == a) ? one<T>() : zero<T>();
         else v = W[(int64_t)i * p + a];
@@ -523,6 +565,29 @@ hss_leaf_kernel(const int* __restrict__ list, const HNode* __restrict__ nodes, c
             acc = fmac(S[(int64_t)(nd.lo + c) * lds + nd.lo + r], x[(int64_t)j * lx + nd.lo + c], acc);
         for (int c = 0; c < k; ++c) acc = fmac(X[(int64_t)c * nd.rows_cap + r], yh[(int64_t)j * xh_ld + c], acc);
         y[(int64_t)j * ly + nd.lo + r] = acc;
+    }
+}
+
+// coupling blocks of inner node i: B12 = S(skel_c1, skel_c2) (k1 x k2), B21 = S(skel_c2, skel_c1)
+template <typename T>
+__global__ void gather_b_kernel(const int* __restrict__ list, const HNode* __restrict__ nodes,
+                                const HFront* __restrict__ fronts, const int* __restrict__ iws, const int* __restrict__ kk,
+                                T* const* __restrict__ b12, T* const* __restrict__ b21) {
+    const HNode nd = nodes[list[blockIdx.x]];
+    const HFront fr = fronts[nd.front];
+    const T* S = static_cast<const T*>(fr.S);
+    const int k1 = kk[nd.c1], k2 = kk[nd.c2];
+    const int* sk1 = iws + nodes[nd.c1].o_skel;
+    const int* sk2 = iws + nodes[nd.c2].o_skel;
+    T* a = b12[blockIdx.x];
+    T* b = b21[blockIdx.x];
+    for (int q = threadIdx.x; q < k1 * k2; q += blockDim.x) {
+        const int i = q % k1, j = q / k1;
+        a[q] = S[(int64_t)sk2[j] * fr.lds + sk1[i]];
+    }
+    for (int q = threadIdx.x; q < k1 * k2; q += blockDim.x) {
+        const int i = q % k2, j = q / k2;
+        b[q] = S[(int64_t)sk1[j] * fr.lds + sk2[i]];
     }
 }
 
@@ -861,7 +926,7 @@ ndhss_status compress_problems(std::vector<Problem>& probs, bool lowrank, const 
         loff[maxlev + 1] = flat.size();
         DeviceVec<int> dflat(st);
         HSS_TRY(dflat.upload(flat, st));
-        const size_t smem_rid = (size_t)max_rows * sizeof(double);
+        const size_t smem_rid = (size_t)(max_rows + 1) * sizeof(double) + (size_t)p * sizeof(T) + 64;
         if (smem_rid > 48 * 1024)
             HSS_TRY(cudaFuncSetAttribute(row_id_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_rid));
         if (lowrank) {
@@ -956,77 +1021,135 @@ ndhss_status compress_problems(std::vector<Problem>& probs, bool lowrank, const 
                     const HNode& nd = nodes[fr[i].root];
                     kout[a] = k;
                     auto& out = (*lr_host)[a];
-                    out.resize((size_t)fr[i].n * k + (size_t)k * fr[i].ncol);
-                    // X (n x k, ld rows_cap = n) then RJ (k x ncol, ld kcap -> k)
+                    const size_t n = fr[i].n, nc = fr[i].ncol;
+                    out.resize(n * k + nc * k);
+                    std::vector<T> rj((size_t)k * nc);
+                    // X (n x k, ld n) then R(J, :)^T (ncol x k, ld ncol)
                     if (k > 0) {
-                        HSS_TRY(cudaMemcpy2DAsync(out.data(), (size_t)fr[i].n * sizeof(T), ws.p + nd.o_x,
-                                                  (size_t)nd.rows_cap * sizeof(T), (size_t)fr[i].n * sizeof(T), k,
-                                                  cudaMemcpyDeviceToHost, st));
-                        HSS_TRY(cudaMemcpy2DAsync(out.data() + (size_t)fr[i].n * k, (size_t)k * sizeof(T), fr[i].RJ,
-                                                  (size_t)kcap * sizeof(T), (size_t)k * sizeof(T), fr[i].ncol,
-                                                  cudaMemcpyDeviceToHost, st));
+                        HSS_TRY(cudaMemcpy2DAsync(out.data(), n * sizeof(T), ws.p + nd.o_x, (size_t)nd.rows_cap * sizeof(T),
+                                                  n * sizeof(T), k, cudaMemcpyDeviceToHost, st));
+                        HSS_TRY(cudaMemcpy2DAsync(rj.data(), (size_t)k * sizeof(T), fr[i].RJ, (size_t)kcap * sizeof(T),
+                                                  (size_t)k * sizeof(T), nc, cudaMemcpyDeviceToHost, st));
+                        HSS_TRY(cudaStreamSynchronize(st));
+                        for (size_t j = 0; j < nc; ++j)
+                            for (int aa = 0; aa < k; ++aa) out[n * k + j + (size_t)aa * nc] = rj[j * k + aa];
                     }
                 }
                 HSS_TRY(cudaStreamSynchronize(st));
             } else {
-                // reconstruct S_HSS = HSS(S) I into scratch, then overwrite S
+                // S_HSS written over S: leaf diagonal blocks stay; every off-diagonal block
+                // S(I_c1, I_c2) = U~_c1 B12 U~_c2^T with the expanded nested bases
+                // U~_leaf = X_leaf, U~_i = blockdiag(U~_c1, U~_c2) X_i (Eq. 2.3)
                 std::vector<char> keep(nf, 0);
                 for (int i : done) keep[i] = 1;
-                int64_t tot = 0;
-                std::vector<T*> ids(nf, nullptr), outs(nf, nullptr);
-                std::vector<int64_t> off_id(nf, 0), off_out(nf, 0), lds2(nf, 1);
-                std::vector<int> ncs(nf, 0);
-                for (int i : done) {
-                    const int64_t n = fr[i].n;
-                    off_id[i] = tot;
-                    tot += n * n;
-                    off_out[i] = tot;
-                    tot += n * n;
-                    lds2[i] = n;
-                    ncs[i] = (int)n;
+                std::vector<const T*> up(nodes.size(), nullptr);
+                std::vector<int64_t> uld(nodes.size(), 1), uoff(nodes.size(), -1);
+                int64_t utot = 0;
+                for (size_t q = 0; q < nodes.size(); ++q) {
+                    const HNode& nd = nodes[q];
+                    if (!keep[nd.front] || (int)q == fr[nd.front].root) continue;
+                    if (nd.c1 < 0) {
+                        up[q] = ws.p + nd.o_x;
+                        uld[q] = nd.rows_cap;
+                    } else {
+                        uoff[q] = utot;
+                        uld[q] = nd.hi - nd.lo;
+                        utot += (int64_t)(nd.hi - nd.lo) * std::max(hk[q], 1);
+                    }
                 }
-                std::vector<HNode> nodes2 = nodes;
-                int64_t hbsz = 0;
-                for (auto& nd : nodes2) {
-                    if (!keep[nd.front]) continue;
-                    const int64_t n = fr[nd.front].n;
-                    nd.o_xh = hbsz;
-                    hbsz += (int64_t)kcap * n;
-                    nd.o_yh = hbsz;
-                    hbsz += (int64_t)kcap * n;
+                int64_t btot = 0;
+                std::vector<int> inner;
+                std::vector<int64_t> o12, o21, ot12, ot21;
+                for (size_t q = 0; q < nodes.size(); ++q) {
+                    const HNode& nd = nodes[q];
+                    if (!keep[nd.front] || nd.c1 < 0) continue;
+                    const int64_t k1 = hk[nd.c1], k2 = hk[nd.c2];
+                    const int64_t s1 = nodes[nd.c1].hi - nodes[nd.c1].lo, s2 = nodes[nd.c2].hi - nodes[nd.c2].lo;
+                    inner.push_back((int)q);
+                    o12.push_back(btot); btot += std::max<int64_t>(k1 * k2, 1);
+                    o21.push_back(btot); btot += std::max<int64_t>(k1 * k2, 1);
+                    ot12.push_back(btot); btot += std::max<int64_t>(k1 * s2, 1);
+                    ot21.push_back(btot); btot += std::max<int64_t>(k2 * s1, 1);
                 }
-                DeviceVec<T> sc(st), hb(st);
-                HSS_TRY(sc.alloc(tot));
-                HSS_TRY(hb.alloc(hbsz));
-                std::vector<T*> idlist, srcs;
-                std::vector<int> nsz;
-                for (int i : done) {
-                    ids[i] = sc.p + off_id[i];
-                    outs[i] = sc.p + off_out[i];
-                    idlist.push_back(ids[i]);
-                    srcs.push_back(outs[i]);
-                    nsz.push_back(fr[i].n);
+                DeviceVec<T> ub(st), bb(st);
+                HSS_TRY(ub.alloc(utot));
+                HSS_TRY(bb.alloc(btot));
+                for (size_t q = 0; q < nodes.size(); ++q)
+                    if (uoff[q] >= 0) up[q] = ub.p + uoff[q];
+                // expanded bases, deepest level first
+                for (int l = maxlev; l >= 1; --l) {
+                    std::vector<GemmJob> gj2;
+                    for (size_t q = 0; q < nodes.size(); ++q) {
+                        const HNode& nd = nodes[q];
+                        if (nd.level != l || uoff[q] < 0) continue;
+                        const int k = hk[q], k1 = hk[nd.c1], k2 = hk[nd.c2];
+                        const int s1 = nodes[nd.c1].hi - nodes[nd.c1].lo, s2 = nodes[nd.c2].hi - nodes[nd.c2].lo;
+                        const T* X = ws.p + nd.o_x;
+                        T* U = const_cast<T*>(up[q]);
+                        gj2.push_back({up[nd.c1], X, U, uld[nd.c1], nd.rows_cap, uld[q], s1, k, k1, 0, 1.0});
+                        gj2.push_back({up[nd.c2], X + k1, U + s1, uld[nd.c2], nd.rows_cap, uld[q], s2, k, k2, 0, 1.0});
+                    }
+                    if (gj2.empty()) continue;
+                    int mM = 1, mN = 1;
+                    for (auto& g : gj2) { mM = std::max(mM, g.M); mN = std::max(mN, g.N); }
+                    DeviceVec<GemmJob> dg(st);
+                    HSS_TRY(dg.upload(gj2, st));
+                    bgemm_kernel<T><<<dim3((mM + 63) / 64, (mN + 63) / 64, (unsigned)gj2.size()), 256, 0, st>>>(dg.p);
+                    NDHSS_LAUNCH_CHECK("bgemm_kernel");
                 }
-                DeviceVec<HNode> dn2(st);
-                DeviceVec<T*> did(st), dout(st), didl(st), dsrc(st);
-                DeviceVec<int64_t> dld(st);
-                DeviceVec<int> dns(st), dwhich(st), dncs(st);
-                HSS_TRY(dn2.upload(nodes2, st));
-                HSS_TRY(did.upload(ids, st));
-                HSS_TRY(dout.upload(outs, st));
-                HSS_TRY(dld.upload(lds2, st));
-                HSS_TRY(didl.upload(idlist, st));
-                HSS_TRY(dsrc.upload(srcs, st));
-                HSS_TRY(dns.upload(nsz, st));
-                HSS_TRY(dwhich.upload(done, st));
-                HSS_TRY(dncs.upload(ncs, st));
-                eye_kernel<T><<<dim3(64, (unsigned)done.size()), 256, 0, st>>>(didl.p, dns.p);
-                NDHSS_LAUNCH_CHECK("eye_kernel");
-                ndhss_status rc = hss_matvec_run<T>(nodes2, keep, maxlev, dn2.p, dfr.p, ws.p, hb.p, iws.p, kk.p, rows.p,
-                                                   (const T* const*)did.p, dld.p, dout.p, dld.p, dncs.p, (int64_t)kcap, st);
-                if (rc != NDHSS_OK) return rc;
-                copy_back_kernel<T><<<dim3(64, (unsigned)done.size()), 256, 0, st>>>(dsrc.p, dfr.p, dwhich.p);
-                NDHSS_LAUNCH_CHECK("copy_back_kernel");
+                // coupling blocks (all gathered before any block of S is overwritten)
+                std::vector<T*> p12, p21;
+                for (size_t q = 0; q < inner.size(); ++q) {
+                    p12.push_back(bb.p + o12[q]);
+                    p21.push_back(bb.p + o21[q]);
+                }
+                DeviceVec<int> dinner(st);
+                DeviceVec<T*> dp12(st), dp21(st);
+                HSS_TRY(dinner.upload(inner, st));
+                HSS_TRY(dp12.upload(p12, st));
+                HSS_TRY(dp21.upload(p21, st));
+                if (!inner.empty()) {
+                    gather_b_kernel<T><<<(unsigned)inner.size(), HT, 0, st>>>(dinner.p, dnodes.p, dfr.p, iws.p, kk.p, dp12.p,
+                                                                             dp21.p);
+                    NDHSS_LAUNCH_CHECK("gather_b_kernel");
+                }
+                // T12 = B12 U~_c2^T, T21 = B21 U~_c1^T; then the blocks of S
+                std::vector<GemmJob> g1, g2;
+                int m1 = 1, n1 = 1, m2 = 1, n2 = 1;
+                for (size_t q = 0; q < inner.size(); ++q) {
+                    const HNode& nd = nodes[inner[q]];
+                    const HFront& f = fr[nd.front];
+                    const int k1 = hk[nd.c1], k2 = hk[nd.c2];
+                    const HNode& a = nodes[nd.c1];
+                    const HNode& b = nodes[nd.c2];
+                    const int s1 = a.hi - a.lo, s2 = b.hi - b.lo;
+                    T* t12 = bb.p + ot12[q];
+                    T* t21 = bb.p + ot21[q];
+                    GemmJob x{p12[q], up[nd.c2], t12, std::max(k1, 1), uld[nd.c2], std::max(k1, 1), k1, s2, k2, 0, 1.0};
+                    x.transB = 1;
+                    GemmJob y{p21[q], up[nd.c1], t21, std::max(k2, 1), uld[nd.c1], std::max(k2, 1), k2, s1, k1, 0, 1.0};
+                    y.transB = 1;
+                    g1.push_back(x);
+                    g1.push_back(y);
+                    T* Sb = static_cast<T*>(f.S);
+                    g2.push_back({up[nd.c1], t12, Sb + (int64_t)b.lo * f.lds + a.lo, uld[nd.c1], std::max(k1, 1), f.lds, s1,
+                                  s2, k1, 0, 1.0});
+                    g2.push_back({up[nd.c2], t21, Sb + (int64_t)a.lo * f.lds + b.lo, uld[nd.c2], std::max(k2, 1), f.lds, s2,
+                                  s1, k2, 0, 1.0});
+                    m1 = std::max({m1, k1, k2});
+                    n1 = std::max({n1, s1, s2});
+                    m2 = std::max({m2, s1, s2});
+                    n2 = std::max({n2, s1, s2});
+                }
+                if (!g1.empty()) {
+                    DeviceVec<GemmJob> dg1(st), dg2(st);
+                    HSS_TRY(dg1.upload(g1, st));
+                    HSS_TRY(dg2.upload(g2, st));
+                    bgemm_kernel<T><<<dim3((m1 + 63) / 64, (n1 + 63) / 64, (unsigned)g1.size()), 256, 0, st>>>(dg1.p);
+                    NDHSS_LAUNCH_CHECK("bgemm_kernel");
+                    bgemm_kernel<T><<<dim3((m2 + 63) / 64, (n2 + 63) / 64, (unsigned)g2.size()), 256, 0, st>>>(dg2.p);
+                    NDHSS_LAUNCH_CHECK("bgemm_kernel");
+                }
                 HSS_TRY(cudaStreamSynchronize(st));
                 for (int i : done) {
                     int km = 0;
