@@ -280,7 +280,7 @@ form_sloc_kernel(const int* __restrict__ list, const HNode* __restrict__ nodes, 
 // kmax.  Output: kk[node] = k, piv (local rows, first k = skeleton J),
 // X (rows x k, ld rows_cap) with X(J, :) = I.
 template <typename T>
-__global__ void __launch_bounds__(HT)
+__global__ void __launch_bounds__(1024)
 row_id_kernel(const int* __restrict__ list, const HNode* __restrict__ nodes, T* __restrict__ ws,
               int* __restrict__ iws, int* __restrict__ kk, const int* __restrict__ rows_in, double eps, int rank_cap) {
     using real = typename Tr<T>::real;
@@ -290,31 +290,33 @@ row_id_kernel(const int* __restrict__ list, const HNode* __restrict__ nodes, T* 
     const int rows = rows_in[id], p = nd.p;
     T* W = ws + nd.o_w;                  // p x rows, column c = row c of S_loc (contiguous)
     int* piv = iws + nd.o_piv;
-    double* nrm = reinterpret_cast<double*>(smem);          // remaining squared norms (rows)
-    T* vsh = reinterpret_cast<T*>(nrm + ((rows + 1) & ~1));  // reflector (p), 16-byte aligned
-    __shared__ double s_val[HT / 32];
-    __shared__ int s_idx[HT / 32];
+    const int rr = (rows + 1) & ~1;
+    double* nrm = reinterpret_cast<double*>(smem);          // remaining column norms (rows)
+    double* nrm0 = nrm + rr;                                 // norms at the last recomputation
+    T* vsh = reinterpret_cast<T*>(nrm0 + rr);                // reflector (p), 16-byte aligned
+    __shared__ double s_val[32];
+    __shared__ int s_idx[32];
     __shared__ double s_r11, s_bestv, s_vn2;
     __shared__ int s_best;
     __shared__ T s_beta;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    constexpr int NW = HT / 32;
-    // initial squared row norms, one warp per column
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, NW = blockDim.x >> 5, NT = blockDim.x;
     for (int c = warp; c < rows; c += NW) {
         const T* col = W + (int64_t)c * p;
         double sacc = 0.0;
         for (int j = lane; j < p; j += 32) sacc += nrm2v(col[j]);
         for (int o = 16; o; o >>= 1) sacc += __shfl_xor_sync(0xffffffffu, sacc, o);
-        if (lane == 0) nrm[c] = sacc;
+        if (lane == 0) { nrm[c] = sqrt(sacc); nrm0[c] = nrm[c]; }
     }
-    for (int c = tid; c < rows; c += HT) piv[c] = c;
+    for (int c = tid; c < rows; c += NT) piv[c] = c;
     const int kmax = min(min(nd.kcap, rank_cap), min(p, rows));
+    // recompute a downdated norm once it has lost about half its digits
+    const double tol3z = sizeof(real) == 4 ? 3.4526698e-4 : 1.4901161193847656e-8;
     int t = 0;
     __syncthreads();
     for (; t < min(p, rows); ++t) {
         double best = -1.0;
         int bi = INT_MAX;
-        for (int c = t + tid; c < rows; c += HT) {
+        for (int c = t + tid; c < rows; c += NT) {
             const double v = nrm[c];
             if (v > best) { best = v; bi = c; }
         }
@@ -333,9 +335,14 @@ row_id_kernel(const int* __restrict__ list, const HNode* __restrict__ nodes, T* 
                 const int oi = __shfl_down_sync(0xffffffffu, bb, o);
                 if (ov > bv || (ov == bv && oi < bb)) { bv = ov; bb = oi; }
             }
+            // exact norm of the chosen column (the rank test uses it)
+            double xn2 = 0.0;
+            if (bb != INT_MAX)
+                for (int j = t + lane; j < p; j += 32) xn2 += nrm2v(W[(int64_t)bb * p + j]);
+            for (int o = 16; o; o >>= 1) xn2 += __shfl_xor_sync(0xffffffffu, xn2, o);
             if (lane == 0) {
                 s_best = bb;
-                s_bestv = sqrt(fmax(bv, 0.0));
+                s_bestv = sqrt(xn2);
                 if (t == 0) s_r11 = s_bestv;
             }
         }
@@ -343,7 +350,7 @@ row_id_kernel(const int* __restrict__ list, const HNode* __restrict__ nodes, T* 
         const int cb = s_best;
         if (t >= kmax || cb == INT_MAX || !(s_bestv > eps * s_r11)) break;
         if (cb != t) {
-            for (int j = tid; j < p; j += HT) {
+            for (int j = tid; j < p; j += NT) {
                 const T a = W[(int64_t)t * p + j];
                 W[(int64_t)t * p + j] = W[(int64_t)cb * p + j];
                 W[(int64_t)cb * p + j] = a;
@@ -352,15 +359,17 @@ row_id_kernel(const int* __restrict__ list, const HNode* __restrict__ nodes, T* 
                 const int a = piv[t];
                 piv[t] = piv[cb];
                 piv[cb] = a;
-                const double n1 = nrm[t];
+                const double n1 = nrm[t], n0 = nrm0[t];
                 nrm[t] = nrm[cb];
+                nrm0[t] = nrm0[cb];
                 nrm[cb] = n1;
+                nrm0[cb] = n0;
             }
         }
         __syncthreads();
         // reflector v = x - beta e1 of x = W(t:p, t), beta = -phase(x0) ||x||
         T* xcol = W + (int64_t)t * p;
-        for (int j = t + tid; j < p; j += HT) vsh[j] = xcol[j];
+        for (int j = t + tid; j < p; j += NT) vsh[j] = xcol[j];
         __syncthreads();
         if (tid == 0) {
             const double xn = s_bestv;
@@ -384,15 +393,26 @@ row_id_kernel(const int* __restrict__ list, const HNode* __restrict__ nodes, T* 
                 for (int j = t + lane; j < p; j += 32) w = fmac(conjv(vsh[j]), col[j], w);
                 for (int o = 16; o; o >>= 1) w = w + shfl_xor_h(w, o);
                 const T g = scale(w, f);
-                // update, and the exact remaining norm in the same pass
-                double sacc = 0.0;
-                for (int j = t + lane; j < p; j += 32) {
-                    const T u = col[j] - vsh[j] * g;
-                    col[j] = u;
-                    if (j > t) sacc += nrm2v(u);
+                for (int j = t + lane; j < p; j += 32) col[j] = col[j] - vsh[j] * g;
+                // downdate the remaining norm by the entry that left for row t; recompute
+                // it from the column when cancellation has eaten half the digits
+                double nc = nrm[c];
+                if (nc > 0) {
+                    __syncwarp();
+                    const double rt = absv(col[t]) / nc;
+                    double tmp = fmax(0.0, (1.0 + rt) * (1.0 - rt));
+                    const double q = nc / nrm0[c];
+                    if (tmp * q * q <= tol3z) {
+                        double sacc = 0.0;
+                        for (int j = t + 1 + lane; j < p; j += 32) sacc += nrm2v(col[j]);
+                        for (int o = 16; o; o >>= 1) sacc += __shfl_xor_sync(0xffffffffu, sacc, o);
+                        nc = sqrt(sacc);
+                        if (lane == 0) nrm0[c] = nc;
+                    } else {
+                        nc *= sqrt(tmp);
+                    }
+                    if (lane == 0) nrm[c] = nc;
                 }
-                for (int o = 16; o; o >>= 1) sacc += __shfl_xor_sync(0xffffffffu, sacc, o);
-                if (lane == 0) nrm[c] = sacc;
             }
         }
         __syncthreads();
@@ -400,8 +420,8 @@ row_id_kernel(const int* __restrict__ list, const HNode* __restrict__ nodes, T* 
         __syncthreads();
     }
     const int k = t;
-    // T = R11^{-1} R12 in place of R12, one warp per column (rows of T in lanes sequentially)
-    for (int c = k + tid; c < rows; c += HT) {
+    // T = R11^{-1} R12 in place of R12 (one column per thread)
+    for (int c = k + tid; c < rows; c += NT) {
         T* col = W + (int64_t)c * p;
         for (int i = k - 1; i >= 0; --i) {
             T acc = col[i];
@@ -411,7 +431,7 @@ row_id_kernel(const int* __restrict__ list, const HNode* __restrict__ nodes, T* 
     }
     __syncthreads();
     T* X = ws + nd.o_x;
-    for (int q = tid; q < rows * k; q += HT) {
+    for (int q = tid; q < rows * k; q += NT) {
         const int i = q % rows, a = q / rows;
         T v;
         if (i < k) v = (i == a) ? one<T>() : zero<T>();
@@ -926,14 +946,14 @@ ndhss_status compress_problems(std::vector<Problem>& probs, bool lowrank, const 
         loff[maxlev + 1] = flat.size();
         DeviceVec<int> dflat(st);
         HSS_TRY(dflat.upload(flat, st));
-        const size_t smem_rid = (size_t)(max_rows + 1) * sizeof(double) + (size_t)p * sizeof(T) + 64;
+        const size_t smem_rid = (size_t)(max_rows + 1) * 2 * sizeof(double) + (size_t)p * sizeof(T) + 64;
         if (smem_rid > 48 * 1024)
             HSS_TRY(cudaFuncSetAttribute(row_id_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_rid));
         if (lowrank) {
             transpose_samples_kernel<T><<<dim3(64, nf), 256, 0, st>>>(dfr.p, dnodes.p, ws.p, iws.p, rows.p);
             NDHSS_LAUNCH_CHECK("transpose_samples_kernel");
-            row_id_kernel<T><<<(unsigned)bylev[0].size(), HT, smem_rid, st>>>(dflat.p + loff[0], dnodes.p, ws.p, iws.p, kk.p,
-                                                                            rows.p, eps, rank_cap);
+            row_id_kernel<T><<<(unsigned)bylev[0].size(), 1024, smem_rid, st>>>(dflat.p + loff[0], dnodes.p, ws.p, iws.p,
+                                                                              kk.p, rows.p, eps, rank_cap);
             NDHSS_LAUNCH_CHECK("row_id_kernel");
             gather_rows_kernel<T><<<dim3(64, nf), 256, 0, st>>>(dfr.p, dnodes.p, ws.p, iws.p, kk.p);
             NDHSS_LAUNCH_CHECK("gather_rows_kernel");
