@@ -291,9 +291,8 @@ row_id_kernel(const int* __restrict__ list, const HNode* __restrict__ nodes, T* 
     T* W = ws + nd.o_w;                  // p x rows, column c = row c of S_loc (contiguous)
     int* piv = iws + nd.o_piv;
     const int rr = (rows + 1) & ~1;
-    double* nrm = reinterpret_cast<double*>(smem);          // remaining column norms (rows)
-    double* nrm0 = nrm + rr;                                 // norms at the last recomputation
-    T* vsh = reinterpret_cast<T*>(nrm0 + rr);                // reflector (p), 16-byte aligned
+    double* nrm = reinterpret_cast<double*>(smem);          // remaining squared column norms (rows)
+    T* vsh = reinterpret_cast<T*>(nrm + rr);                 // reflector (p), 16-byte aligned
     __shared__ double s_val[32];
     __shared__ int s_idx[32];
     __shared__ double s_r11, s_bestv, s_vn2;
@@ -305,12 +304,10 @@ row_id_kernel(const int* __restrict__ list, const HNode* __restrict__ nodes, T* 
         double sacc = 0.0;
         for (int j = lane; j < p; j += 32) sacc += nrm2v(col[j]);
         for (int o = 16; o; o >>= 1) sacc += __shfl_xor_sync(0xffffffffu, sacc, o);
-        if (lane == 0) { nrm[c] = sqrt(sacc); nrm0[c] = nrm[c]; }
+        if (lane == 0) nrm[c] = sacc;
     }
     for (int c = tid; c < rows; c += NT) piv[c] = c;
     const int kmax = min(min(nd.kcap, rank_cap), min(p, rows));
-    // recompute a downdated norm once it has lost about half its digits
-    const double tol3z = sizeof(real) == 4 ? 3.4526698e-4 : 1.4901161193847656e-8;
     int t = 0;
     __syncthreads();
     for (; t < min(p, rows); ++t) {
@@ -335,14 +332,9 @@ row_id_kernel(const int* __restrict__ list, const HNode* __restrict__ nodes, T* 
                 const int oi = __shfl_down_sync(0xffffffffu, bb, o);
                 if (ov > bv || (ov == bv && oi < bb)) { bv = ov; bb = oi; }
             }
-            // exact norm of the chosen column (the rank test uses it)
-            double xn2 = 0.0;
-            if (bb != INT_MAX)
-                for (int j = t + lane; j < p; j += 32) xn2 += nrm2v(W[(int64_t)bb * p + j]);
-            for (int o = 16; o; o >>= 1) xn2 += __shfl_xor_sync(0xffffffffu, xn2, o);
             if (lane == 0) {
                 s_best = bb;
-                s_bestv = sqrt(xn2);
+                s_bestv = sqrt(fmax(bv, 0.0));
                 if (t == 0) s_r11 = s_bestv;
             }
         }
@@ -359,11 +351,9 @@ row_id_kernel(const int* __restrict__ list, const HNode* __restrict__ nodes, T* 
                 const int a = piv[t];
                 piv[t] = piv[cb];
                 piv[cb] = a;
-                const double n1 = nrm[t], n0 = nrm0[t];
+                const double n1 = nrm[t];
                 nrm[t] = nrm[cb];
-                nrm0[t] = nrm0[cb];
                 nrm[cb] = n1;
-                nrm0[cb] = n0;
             }
         }
         __syncthreads();
@@ -393,26 +383,15 @@ row_id_kernel(const int* __restrict__ list, const HNode* __restrict__ nodes, T* 
                 for (int j = t + lane; j < p; j += 32) w = fmac(conjv(vsh[j]), col[j], w);
                 for (int o = 16; o; o >>= 1) w = w + shfl_xor_h(w, o);
                 const T g = scale(w, f);
-                for (int j = t + lane; j < p; j += 32) col[j] = col[j] - vsh[j] * g;
-                // downdate the remaining norm by the entry that left for row t; recompute
-                // it from the column when cancellation has eaten half the digits
-                double nc = nrm[c];
-                if (nc > 0) {
-                    __syncwarp();
-                    const double rt = absv(col[t]) / nc;
-                    double tmp = fmax(0.0, (1.0 + rt) * (1.0 - rt));
-                    const double q = nc / nrm0[c];
-                    if (tmp * q * q <= tol3z) {
-                        double sacc = 0.0;
-                        for (int j = t + 1 + lane; j < p; j += 32) sacc += nrm2v(col[j]);
-                        for (int o = 16; o; o >>= 1) sacc += __shfl_xor_sync(0xffffffffu, sacc, o);
-                        nc = sqrt(sacc);
-                        if (lane == 0) nrm0[c] = nc;
-                    } else {
-                        nc *= sqrt(tmp);
-                    }
-                    if (lane == 0) nrm[c] = nc;
+                // update, and the exact remaining norm in the same pass
+                double sacc = 0.0;
+                for (int j = t + lane; j < p; j += 32) {
+                    const T u = col[j] - vsh[j] * g;
+                    col[j] = u;
+                    if (j > t) sacc += nrm2v(u);
                 }
+                for (int o = 16; o; o >>= 1) sacc += __shfl_xor_sync(0xffffffffu, sacc, o);
+                if (lane == 0) nrm[c] = sacc;
             }
         }
         __syncthreads();
