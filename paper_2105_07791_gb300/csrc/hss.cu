@@ -71,6 +71,8 @@ __device__ __forceinline__ Cx<R> shfl_xor_h(Cx<R> v, int o) {
     return {__shfl_xor_sync(0xffffffffu, v.x, o), __shfl_xor_sync(0xffffffffu, v.y, o)};
 }
 
+__host__ __device__ __forceinline__ int rows_cap_even(int r) { return (r + 1) & ~1; }
+
 template <typename T> __device__ __forceinline__ T real_to(double v);
 template <> __device__ __forceinline__ double real_to<double>(double v) { return v; }
 template <> __device__ __forceinline__ float real_to<float>(double v) { return (float)v; }
@@ -280,25 +282,33 @@ form_sloc_kernel(const int* __restrict__ list, const HNode* __restrict__ nodes, 
 // kmax.  Output: kk[node] = k, piv (local rows, first k = skeleton J),
 // X (rows x k, ld rows_cap) with X(J, :) = I.
 template <typename T>
-__global__ void __launch_bounds__(1024)
+__global__ void __launch_bounds__(512)
 row_id_kernel(const int* __restrict__ list, const HNode* __restrict__ nodes, T* __restrict__ ws,
-              int* __restrict__ iws, int* __restrict__ kk, const int* __restrict__ rows_in, double eps, int rank_cap) {
+              int* __restrict__ iws, int* __restrict__ kk, const int* __restrict__ rows_in, double eps, int rank_cap,
+              int w_in_smem) {
     using real = typename Tr<T>::real;
+    constexpr int CH = 8;                // column entries per lane held in registers (p <= 256)
     extern __shared__ __align__(16) unsigned char smem[];
     const int id = list[blockIdx.x];
     const HNode nd = nodes[id];
     const int rows = rows_in[id], p = nd.p;
-    T* W = ws + nd.o_w;                  // p x rows, column c = row c of S_loc (contiguous)
     int* piv = iws + nd.o_piv;
-    const int rr = (rows + 1) & ~1;
-    double* nrm = reinterpret_cast<double*>(smem);          // remaining squared column norms (rows)
+    const int rr = (rows_cap_even(nd.rows_cap));
+    double* nrm = reinterpret_cast<double*>(smem);          // remaining squared column norms
     T* vsh = reinterpret_cast<T*>(nrm + rr);                 // reflector (p), 16-byte aligned
+    T* W = ws + nd.o_w;                                      // p x rows, column c = row c of S_loc
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, NW = blockDim.x >> 5, NT = blockDim.x;
+    if (w_in_smem) {
+        T* Ws = vsh + ((p + 1) & ~1);
+        for (int64_t q = tid; q < (int64_t)p * rows; q += NT) Ws[q] = W[q];
+        W = Ws;
+        __syncthreads();
+    }
     __shared__ double s_val[32];
     __shared__ int s_idx[32];
     __shared__ double s_r11, s_bestv, s_vn2;
     __shared__ int s_best;
     __shared__ T s_beta;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, NW = blockDim.x >> 5, NT = blockDim.x;
     for (int c = warp; c < rows; c += NW) {
         const T* col = W + (int64_t)c * p;
         double sacc = 0.0;
@@ -377,18 +387,34 @@ row_id_kernel(const int* __restrict__ list, const HNode* __restrict__ nodes, T* 
         const double vn2 = s_vn2;
         if (vn2 > 0) {
             const real f = (real)(2.0 / vn2);
+            T vl[CH];
+#pragma unroll
+            for (int q = 0; q < CH; ++q) {
+                const int j = t + lane + 32 * q;
+                vl[q] = (j < p) ? vsh[j] : zero<T>();
+            }
             for (int c = t + 1 + warp; c < rows; c += NW) {
                 T* col = W + (int64_t)c * p;
+                T cv[CH];
                 T w = zero<T>();
-                for (int j = t + lane; j < p; j += 32) w = fmac(conjv(vsh[j]), col[j], w);
+#pragma unroll
+                for (int q = 0; q < CH; ++q) {
+                    const int j = t + lane + 32 * q;
+                    cv[q] = (j < p) ? col[j] : zero<T>();
+                }
+#pragma unroll
+                for (int q = 0; q < CH; ++q) w = fmac(conjv(vl[q]), cv[q], w);
                 for (int o = 16; o; o >>= 1) w = w + shfl_xor_h(w, o);
                 const T g = scale(w, f);
-                // update, and the exact remaining norm in the same pass
                 double sacc = 0.0;
-                for (int j = t + lane; j < p; j += 32) {
-                    const T u = col[j] - vsh[j] * g;
-                    col[j] = u;
-                    if (j > t) sacc += nrm2v(u);
+#pragma unroll
+                for (int q = 0; q < CH; ++q) {
+                    const int j = t + lane + 32 * q;
+                    if (j < p) {
+                        const T u = cv[q] - vl[q] * g;
+                        col[j] = u;
+                        if (j > t) sacc += nrm2v(u);
+                    }
                 }
                 for (int o = 16; o; o >>= 1) sacc += __shfl_xor_sync(0xffffffffu, sacc, o);
                 if (lane == 0) nrm[c] = sacc;
@@ -925,14 +951,18 @@ ndhss_status compress_problems(std::vector<Problem>& probs, bool lowrank, const 
         loff[maxlev + 1] = flat.size();
         DeviceVec<int> dflat(st);
         HSS_TRY(dflat.upload(flat, st));
-        const size_t smem_rid = (size_t)(max_rows + 1) * 2 * sizeof(double) + (size_t)p * sizeof(T) + 64;
-        if (smem_rid > 48 * 1024)
-            HSS_TRY(cudaFuncSetAttribute(row_id_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_rid));
+        // the sample block of a node sits in shared memory when it fits (p <= 256 always)
+        if (p > 256) return set_error(NDHSS_ERR_RANK_CAP, "hss: more than 256 samples per block (rank_cap too large)");
+        const size_t smem_base = (size_t)(rows_cap_even((int)max_rows)) * sizeof(double) + (size_t)(p + 2) * sizeof(T) + 64;
+        const size_t smem_w = smem_base + (size_t)p * max_rows * sizeof(T);
+        const int w_in_smem = smem_w <= 200 * 1024 ? 1 : 0;
+        const size_t smem_rid = w_in_smem ? smem_w : smem_base;
+        HSS_TRY(cudaFuncSetAttribute(row_id_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)std::max<size_t>(smem_rid, 48 * 1024)));
         if (lowrank) {
             transpose_samples_kernel<T><<<dim3(64, nf), 256, 0, st>>>(dfr.p, dnodes.p, ws.p, iws.p, rows.p);
             NDHSS_LAUNCH_CHECK("transpose_samples_kernel");
-            row_id_kernel<T><<<(unsigned)bylev[0].size(), 1024, smem_rid, st>>>(dflat.p + loff[0], dnodes.p, ws.p, iws.p,
-                                                                              kk.p, rows.p, eps, rank_cap);
+            row_id_kernel<T><<<(unsigned)bylev[0].size(), 512, smem_rid, st>>>(dflat.p + loff[0], dnodes.p, ws.p, iws.p,
+                                                                              kk.p, rows.p, eps, rank_cap, w_in_smem);
             NDHSS_LAUNCH_CHECK("row_id_kernel");
             gather_rows_kernel<T><<<dim3(64, nf), 256, 0, st>>>(dfr.p, dnodes.p, ws.p, iws.p, kk.p);
             NDHSS_LAUNCH_CHECK("gather_rows_kernel");
@@ -961,7 +991,7 @@ ndhss_status compress_problems(std::vector<Problem>& probs, bool lowrank, const 
                 form_sloc_kernel<T><<<cnt, HT, 0, st>>>(dflat.p + loff[l], dnodes.p, dfr.p, ws.p, iws.p, kk.p, rows.p);
                 NDHSS_LAUNCH_CHECK("form_sloc_kernel");
                 row_id_kernel<T><<<cnt, HT, smem_rid, st>>>(dflat.p + loff[l], dnodes.p, ws.p, iws.p, kk.p, rows.p, eps,
-                                                           rank_cap);
+                                                           rank_cap, w_in_smem);
                 NDHSS_LAUNCH_CHECK("row_id_kernel");
                 finish_kernel<T><<<cnt, HT, 0, st>>>(dflat.p + loff[l], dnodes.p, dfr.p, ws.p, iws.p, kk.p, rows.p);
                 NDHSS_LAUNCH_CHECK("finish_kernel");
