@@ -83,6 +83,11 @@ __device__ __forceinline__ double nrm2v(double a) { return a * a; }
 __device__ __forceinline__ double nrm2v(float a) { return (double)a * a; }
 __device__ __forceinline__ double nrm2v(c128 a) { return a.x * a.x + a.y * a.y; }
 __device__ __forceinline__ double nrm2v(c64 a) { return (double)a.x * a.x + (double)a.y * a.y; }
+// |a|^2 in the element's own real type (GB300's FP64 pipe is narrow: FP32 paths stay FP32)
+__device__ __forceinline__ double nrm2r(double a) { return a * a; }
+__device__ __forceinline__ float nrm2r(float a) { return a * a; }
+__device__ __forceinline__ double nrm2r(c128 a) { return a.x * a.x + a.y * a.y; }
+__device__ __forceinline__ float nrm2r(c64 a) { return fmaf(a.x, a.x, a.y * a.y); }
 __device__ __forceinline__ double absv(double a) { return fabs(a); }
 __device__ __forceinline__ double absv(float a) { return fabs((double)a); }
 __device__ __forceinline__ double absv(c128 a) { return hypot(a.x, a.y); }
@@ -96,6 +101,28 @@ struct GaussJob {
     uint64_t stream;
 };
 
+// Four standard normals in single precision (same Philox words, float Box-Muller).
+__device__ void philox_normals_f(uint64_t seed, uint64_t stream, uint64_t blk, double out[4]) {
+    uint32_t c0 = (uint32_t)blk, c1 = (uint32_t)stream, c2 = (uint32_t)(stream >> 32), c3 = 0;
+    uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+    for (int r = 0; r < 10; ++r) {
+        philox_round(c0, c1, c2, c3, k0, k1);
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    const float s = 2.3283064365386963e-10f;            // 2^-32
+    const float u0 = ((float)c0 + 0.5f) * s, u1 = ((float)c1 + 0.5f) * s;
+    const float u2 = ((float)c2 + 0.5f) * s, u3 = ((float)c3 + 0.5f) * s;
+    const float r0 = sqrtf(-2.0f * logf(fmaxf(u0, 1e-38f))), r1 = sqrtf(-2.0f * logf(fmaxf(u2, 1e-38f)));
+    float s1, cs1, s3, cs3;
+    sincospif(2.0f * u1, &s1, &cs1);
+    sincospif(2.0f * u3, &s3, &cs3);
+    out[0] = r0 * cs1;
+    out[1] = r0 * s1;
+    out[2] = r1 * cs3;
+    out[3] = r1 * s3;
+}
+
 template <typename T>
 __global__ void gauss_kernel(const GaussJob* __restrict__ jobs, uint64_t seed) {
     const GaussJob jb = jobs[blockIdx.y];
@@ -103,7 +130,8 @@ __global__ void gauss_kernel(const GaussJob* __restrict__ jobs, uint64_t seed) {
     const int64_t n = (int64_t)jb.rows * jb.cols;
     for (int64_t blk = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; blk * 4 < n; blk += (int64_t)gridDim.x * blockDim.x) {
         double z[4];
-        philox_normals(seed, jb.stream, (uint64_t)blk, z);
+        if (sizeof(typename Tr<T>::real) == 4) philox_normals_f(seed, jb.stream, (uint64_t)blk, z);
+        else philox_normals(seed, jb.stream, (uint64_t)blk, z);
         for (int q = 0; q < 4; ++q) {
             const int64_t e = blk * 4 + q;
             if (e < n) {
@@ -311,10 +339,10 @@ row_id_kernel(const int* __restrict__ list, const HNode* __restrict__ nodes, T* 
     __shared__ T s_beta;
     for (int c = warp; c < rows; c += NW) {
         const T* col = W + (int64_t)c * p;
-        double sacc = 0.0;
-        for (int j = lane; j < p; j += 32) sacc += nrm2v(col[j]);
+        real sacc = real(0);
+        for (int j = lane; j < p; j += 32) sacc += nrm2r(col[j]);
         for (int o = 16; o; o >>= 1) sacc += __shfl_xor_sync(0xffffffffu, sacc, o);
-        if (lane == 0) nrm[c] = sacc;
+        if (lane == 0) nrm[c] = (double)sacc;
     }
     for (int c = tid; c < rows; c += NT) piv[c] = c;
     const int kmax = min(min(nd.kcap, rank_cap), min(p, rows));
@@ -406,18 +434,18 @@ row_id_kernel(const int* __restrict__ list, const HNode* __restrict__ nodes, T* 
                 for (int q = 0; q < CH; ++q) w = fmac(conjv(vl[q]), cv[q], w);
                 for (int o = 16; o; o >>= 1) w = w + shfl_xor_h(w, o);
                 const T g = scale(w, f);
-                double sacc = 0.0;
+                real sacc = real(0);
 #pragma unroll
                 for (int q = 0; q < CH; ++q) {
                     const int j = t + lane + 32 * q;
                     if (j < p) {
                         const T u = cv[q] - vl[q] * g;
                         col[j] = u;
-                        if (j > t) sacc += nrm2v(u);
+                        if (j > t) sacc += nrm2r(u);
                     }
                 }
                 for (int o = 16; o; o >>= 1) sacc += __shfl_xor_sync(0xffffffffu, sacc, o);
-                if (lane == 0) nrm[c] = sacc;
+                if (lane == 0) nrm[c] = (double)sacc;
             }
         }
         __syncthreads();
