@@ -146,63 +146,85 @@ downsweep_kernel(const int32_t* __restrict__ tasks, const int32_t* __restrict__ 
 
 
 // Low-rank levels (R ~ X R(J, :), stored as X (m_i x k) and RJt = R(J, :)^T
-// (m_b x k), both column-major; L = R^T by symmetry): one CTA per node, warps
-// reduce along contiguous columns.
-// up-sweep:   t = X^T y(I^s);  y(B^s) += RJt t
+// (m_b x k), both column-major; L = R^T by symmetry).  Each level is two
+// launches over all its nodes:
+//   dot   tasks (node, 8 outputs): warp w forms t[a0 + w] as a coalesced,
+//         4-way unrolled dot product of a stored column with the gathered
+//         vector, written to scratch;
+//   axpy  tasks (node, 256 rows): each thread adds sum_a M(row, a) t[a].
+// up-sweep (mode 0):   t = X^T y(I^s);     y(B^s) += RJt t
+// down-sweep (mode 1): t = RJt^T z(B^s);   z(I^s) += X t
 template <typename T>
 __global__ void __launch_bounds__(AT)
-lr_upsweep_kernel(const int32_t* __restrict__ list, const int32_t* __restrict__ node, const uint64_t* __restrict__ lrp,
-                  const int32_t* __restrict__ lrk, const int32_t* __restrict__ blist, T* __restrict__ y) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    T* t = reinterpret_cast<T*>(smem_raw);
-    const int s = list[blockIdx.x];
+lr_dot_kernel(const int32_t* __restrict__ tasks, const int32_t* __restrict__ node, const uint64_t* __restrict__ lrp,
+              const int32_t* __restrict__ lrk, const int64_t* __restrict__ toff, const int32_t* __restrict__ blist,
+              const T* __restrict__ v, T* __restrict__ tsc, int mode) {
+    const int s = tasks[2 * blockIdx.x], a0 = tasks[2 * blockIdx.x + 1];
     const int m_i = nf(node, s, 5), m_b = nf(node, s, 7), i_off = nf(node, s, 4), b_off = nf(node, s, 6);
     const int k = lrk[s];
-    const T* X = reinterpret_cast<const T*>(lrp[s]);
-    const T* RJt = X + (int64_t)m_i * k;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int a = warp; a < k; a += AW) {
-        T acc = zero<T>();
-        for (int i = lane; i < m_i; i += 32) acc = fmac(X[(int64_t)a * m_i + i], y[i_off + i], acc);
-        for (int o = 16; o; o >>= 1) acc = acc + shfl_xor_t(acc, o);
-        if (lane == 0) t[a] = acc;
+    const int a = a0 + warp;
+    if (a >= k) return;
+    const T* X = reinterpret_cast<const T*>(lrp[s]);
+    const T* col = (mode == 0) ? X + (int64_t)a * m_i : X + (int64_t)m_i * k + (int64_t)a * m_b;
+    const int len = (mode == 0) ? m_i : m_b;
+    T acc0 = zero<T>(), acc1 = zero<T>(), acc2 = zero<T>(), acc3 = zero<T>();
+    int i = lane;
+    if (mode == 0) {
+        const T* x = v + i_off;
+        for (; i + 96 < len; i += 128) {
+            acc0 = fmac(col[i], x[i], acc0);
+            acc1 = fmac(col[i + 32], x[i + 32], acc1);
+            acc2 = fmac(col[i + 64], x[i + 64], acc2);
+            acc3 = fmac(col[i + 96], x[i + 96], acc3);
+        }
+        for (; i < len; i += 32) acc0 = fmac(col[i], x[i], acc0);
+    } else {
+        const int32_t* bl = blist + b_off;
+        for (; i + 96 < len; i += 128) {
+            acc0 = fmac(col[i], v[bl[i]], acc0);
+            acc1 = fmac(col[i + 32], v[bl[i + 32]], acc1);
+            acc2 = fmac(col[i + 64], v[bl[i + 64]], acc2);
+            acc3 = fmac(col[i + 96], v[bl[i + 96]], acc3);
+        }
+        for (; i < len; i += 32) acc0 = fmac(col[i], v[bl[i]], acc0);
     }
-    __syncthreads();
-    for (int j = threadIdx.x; j < m_b; j += AT) {
-        T acc = zero<T>();
-        for (int a = 0; a < k; ++a) acc = fmac(RJt[(int64_t)a * m_b + j], t[a], acc);
-        const int g = blist[b_off + j];
-        y[g] = y[g] + acc;
-    }
+    T acc = (acc0 + acc1) + (acc2 + acc3);
+    for (int o = 16; o; o >>= 1) acc = acc + shfl_xor_t(acc, o);
+    if (lane == 0) tsc[toff[s] + a] = acc;
 }
 
-// down-sweep: t = RJt^T z(B^s);  z(I^s) += X t
 template <typename T>
 __global__ void __launch_bounds__(AT)
-lr_downsweep_kernel(const int32_t* __restrict__ list, const int32_t* __restrict__ node, const uint64_t* __restrict__ lrp,
-                    const int32_t* __restrict__ lrk, const int32_t* __restrict__ blist, T* __restrict__ z) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int s = list[blockIdx.x];
+lr_axpy_kernel(const int32_t* __restrict__ tasks, const int32_t* __restrict__ node, const uint64_t* __restrict__ lrp,
+               const int32_t* __restrict__ lrk, const int64_t* __restrict__ toff, const int32_t* __restrict__ blist,
+               const T* __restrict__ tsc, T* __restrict__ v, int mode) {
+    __shared__ T ts[512];
+    const int s = tasks[2 * blockIdx.x], r0 = tasks[2 * blockIdx.x + 1];
     const int m_i = nf(node, s, 5), m_b = nf(node, s, 7), i_off = nf(node, s, 4), b_off = nf(node, s, 6);
     const int k = lrk[s];
-    T* zb = reinterpret_cast<T*>(smem_raw);
-    T* t = zb + m_b;
+    for (int a = threadIdx.x; a < k && a < 512; a += AT) ts[a] = tsc[toff[s] + a];
+    __syncthreads();
     const T* X = reinterpret_cast<const T*>(lrp[s]);
-    const T* RJt = X + (int64_t)m_i * k;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int j = threadIdx.x; j < m_b; j += AT) zb[j] = z[blist[b_off + j]];
-    __syncthreads();
-    for (int a = warp; a < k; a += AW) {
-        T acc = zero<T>();
-        for (int j = lane; j < m_b; j += 32) acc = fmac(RJt[(int64_t)a * m_b + j], zb[j], acc);
-        for (int o = 16; o; o >>= 1) acc = acc + shfl_xor_t(acc, o);
-        if (lane == 0) t[a] = acc;
+    const T* M = (mode == 0) ? X + (int64_t)m_i * k : X;       // RJt (m_b x k) or X (m_i x k)
+    const int len = (mode == 0) ? m_b : m_i;
+    const int r = r0 + threadIdx.x;
+    if (r >= len) return;
+    T acc0 = zero<T>(), acc1 = zero<T>(), acc2 = zero<T>(), acc3 = zero<T>();
+    int a = 0;
+    for (; a + 3 < k; a += 4) {
+        acc0 = fmac(M[(int64_t)a * len + r], ts[a], acc0);
+        acc1 = fmac(M[(int64_t)(a + 1) * len + r], ts[a + 1], acc1);
+        acc2 = fmac(M[(int64_t)(a + 2) * len + r], ts[a + 2], acc2);
+        acc3 = fmac(M[(int64_t)(a + 3) * len + r], ts[a + 3], acc3);
     }
-    __syncthreads();
-    for (int i = threadIdx.x; i < m_i; i += AT) {
-        T acc = zero<T>();
-        for (int a = 0; a < k; ++a) acc = fmac(X[(int64_t)a * m_i + i], t[a], acc);
-        z[i_off + i] = z[i_off + i] + acc;
+    for (; a < k; ++a) acc0 = fmac(M[(int64_t)a * len + r], ts[a], acc0);
+    const T acc = (acc0 + acc1) + (acc2 + acc3);
+    if (mode == 0) {
+        const int g = blist[b_off + r];
+        v[g] = v[g] + acc;
+    } else {
+        v[i_off + r] = v[i_off + r] + acc;
     }
 }
 
@@ -219,19 +241,21 @@ ndhss_status apply_run(const FactorData& F, int32_t nrhs, const V* x, int64_t ld
     }
     if (smem_b > 48 * 1024)
         NDHSS_CUDA_TRY(cudaFuncSetAttribute(downsweep_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_b));
-    const size_t smem_k = (size_t)std::max(F.kmax, 1) * sizeof(T);
-    const size_t smem_kb = (size_t)(std::max(F.kmax, 1) + std::max(F.max_mb, 1)) * sizeof(T);
-    if (smem_kb > 48 * 1024)
-        NDHSS_CUDA_TRY(cudaFuncSetAttribute(lr_downsweep_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_kb));
+    T* tsc = reinterpret_cast<T*>(reinterpret_cast<unsigned char*>(w1) + ((size_t)F.n * sizeof(T) + 255) / 256 * 256);
     for (int r = 0; r < nrhs; ++r) {
         gather_cast_kernel<T, V><<<nb, 256, 0, st>>>(F.n, F.d_perm, x + r * ldx, w0);
         NDHSS_LAUNCH_CHECK("gather_cast_kernel");
         for (int l = F.depth; l >= 0; --l) {
             if (l < F.L_hss && !F.lr_cnt.empty()) {
-                if (F.lr_cnt[l]) {
-                    lr_upsweep_kernel<T><<<(unsigned)F.lr_cnt[l], AT, smem_k, st>>>(F.d_lr_list + F.lr_off_l[l], F.d_node,
-                                                                                  F.d_lr_ptr, F.d_lr_k, F.d_blist, w0);
-                    NDHSS_LAUNCH_CHECK("lr_upsweep_kernel");
+                if (F.lr_dot_cnt[l]) {
+                    lr_dot_kernel<T><<<(unsigned)F.lr_dot_cnt[l], AT, 0, st>>>(F.d_tasks + 2 * F.lr_dot_off[l], F.d_node,
+                                                                             F.d_lr_ptr, F.d_lr_k, F.d_lr_toff, F.d_blist,
+                                                                             w0, tsc, 0);
+                    NDHSS_LAUNCH_CHECK("lr_dot_kernel");
+                    lr_axpy_kernel<T><<<(unsigned)F.lr_bax_cnt[l], AT, 0, st>>>(F.d_tasks + 2 * F.lr_bax_off[l], F.d_node,
+                                                                              F.d_lr_ptr, F.d_lr_k, F.d_lr_toff, F.d_blist,
+                                                                              tsc, w0, 0);
+                    NDHSS_LAUNCH_CHECK("lr_axpy_kernel");
                 }
                 continue;
             }
@@ -247,10 +271,15 @@ ndhss_status apply_run(const FactorData& F, int32_t nrhs, const V* x, int64_t ld
         }
         for (int l = 0; l <= F.depth; ++l) {
             if (l < F.L_hss && !F.lr_cnt.empty()) {
-                if (F.lr_cnt[l]) {
-                    lr_downsweep_kernel<T><<<(unsigned)F.lr_cnt[l], AT, smem_kb, st>>>(F.d_lr_list + F.lr_off_l[l], F.d_node,
-                                                                                     F.d_lr_ptr, F.d_lr_k, F.d_blist, w1);
-                    NDHSS_LAUNCH_CHECK("lr_downsweep_kernel");
+                if (F.lr_dot_cnt[l]) {
+                    lr_dot_kernel<T><<<(unsigned)F.lr_dot_cnt[l], AT, 0, st>>>(F.d_tasks + 2 * F.lr_dot_off[l], F.d_node,
+                                                                             F.d_lr_ptr, F.d_lr_k, F.d_lr_toff, F.d_blist,
+                                                                             w1, tsc, 1);
+                    NDHSS_LAUNCH_CHECK("lr_dot_kernel");
+                    lr_axpy_kernel<T><<<(unsigned)F.lr_iax_cnt[l], AT, 0, st>>>(F.d_tasks + 2 * F.lr_iax_off[l], F.d_node,
+                                                                              F.d_lr_ptr, F.d_lr_k, F.d_lr_toff, F.d_blist,
+                                                                              tsc, w1, 1);
+                    NDHSS_LAUNCH_CHECK("lr_axpy_kernel");
                 }
                 continue;
             }
@@ -267,7 +296,10 @@ ndhss_status apply_run(const FactorData& F, int32_t nrhs, const V* x, int64_t ld
 
 }  // namespace
 
-size_t apply_work_bytes(const FactorData& F) { return 2 * (size_t)F.n * F.esize + 256; }
+// two permuted work vectors plus the low-rank scratch t (one slot per rank of every low-rank node)
+size_t apply_work_bytes(const FactorData& F) {
+    return 2 * (((size_t)F.n * F.esize + 255) / 256 * 256) + (size_t)std::max<int64_t>(F.lr_t_total, 1) * F.esize + 256;
+}
 
 ndhss_status apply_device(const FactorData& F, int32_t nrhs, const void* d_x, int64_t ldx, void* d_y, int64_t ldy,
                           void* d_work, cudaStream_t st) {

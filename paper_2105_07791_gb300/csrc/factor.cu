@@ -761,9 +761,36 @@ static ndhss_status factor_impl(const ndhss_tree* th, int32_t vtype, const int32
                 if (F.lr_ptr[s] && F.lr_k[s] > 0) lst.push_back(s);
             F.lr_cnt[l] = (int64_t)lst.size() - F.lr_off_l[l];
         }
+        // low-rank apply task lists, appended to the existing task array
+        std::vector<int32_t> tasks2(tasks);
+        std::vector<int64_t> toff(t.nnodes, 0);
+        F.lr_t_total = 0;
+        for (int s = 0; s < t.nnodes; ++s)
+            if (F.lr_ptr[s] && F.lr_k[s] > 0) { toff[s] = F.lr_t_total; F.lr_t_total += F.lr_k[s]; }
+        auto push_list = [&](std::vector<int64_t>& off, std::vector<int64_t>& cnt, int l, int step, bool over_k,
+                             bool over_b) {
+            off[l] = (int64_t)tasks2.size() / 2;
+            for (int s : F.levels[l]) {
+                if (!(F.lr_ptr[s] && F.lr_k[s] > 0)) continue;
+                const int len = over_k ? F.lr_k[s] : (over_b ? t.m_b(s) : t.m_i(s));
+                for (int r0 = 0; r0 < len; r0 += step) { tasks2.push_back(s); tasks2.push_back(r0); }
+            }
+            cnt[l] = (int64_t)tasks2.size() / 2 - off[l];
+        };
+        for (auto* v : {&F.lr_dot_off, &F.lr_dot_cnt, &F.lr_bax_off, &F.lr_bax_cnt, &F.lr_iax_off, &F.lr_iax_cnt})
+            v->assign(t.depth + 1, 0);
+        for (int l = 0; l <= t.depth; ++l) {
+            push_list(F.lr_dot_off, F.lr_dot_cnt, l, 8, true, false);
+            push_list(F.lr_bax_off, F.lr_bax_cnt, l, 256, false, true);
+            push_list(F.lr_iax_off, F.lr_iax_cnt, l, 256, false, false);
+        }
+        cudaFree(F.d_tasks);
+        F.d_tasks = nullptr;
         if (upload(&F.d_lr_ptr, F.lr_ptr.data(), F.lr_ptr.size(), &F.dev_bytes) != NDHSS_OK ||
             upload(&F.d_lr_k, F.lr_k.data(), F.lr_k.size(), &F.dev_bytes) != NDHSS_OK ||
-            upload(&F.d_lr_list, lst.data(), lst.size(), &F.dev_bytes) != NDHSS_OK)
+            upload(&F.d_lr_list, lst.data(), lst.size(), &F.dev_bytes) != NDHSS_OK ||
+            upload(&F.d_lr_toff, toff.data(), toff.size(), &F.dev_bytes) != NDHSS_OK ||
+            upload(&F.d_tasks, tasks2.data(), tasks2.size(), &F.dev_bytes) != NDHSS_OK)
             rc = set_error(NDHSS_ERR_OOM, "ndhss_factor: low-rank tables");
     }
     cleanup();
@@ -930,6 +957,7 @@ void ndhss_factor_destroy(ndhss_factorization* fh) {
     cudaFree(F.d_lr_ptr);
     cudaFree(F.d_lr_k);
     cudaFree(F.d_lr_list);
+    cudaFree(F.d_lr_toff);
     for (void* b : F.lr_bufs) cudaFree(b);
     delete fh;
 }

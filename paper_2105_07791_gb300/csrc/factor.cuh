@@ -53,6 +53,11 @@ struct FactorData {
     int32_t* d_lr_k = nullptr;
     int32_t* d_lr_list = nullptr;             // low-rank nodes grouped by level
     std::vector<int64_t> lr_off_l, lr_cnt;    // per level
+    // low-rank apply tasks (pairs in d_tasks): dot (node, first output), up-axpy over
+    // B rows, down-axpy over I rows; and the scratch offset of each node's t
+    std::vector<int64_t> lr_dot_off, lr_dot_cnt, lr_bax_off, lr_bax_cnt, lr_iax_off, lr_iax_cnt;
+    int64_t* d_lr_toff = nullptr;
+    int64_t lr_t_total = 0;
     int32_t kmax = 0;
     int32_t hss_rounds_max = 0;
     double hss_ms = 0.0;

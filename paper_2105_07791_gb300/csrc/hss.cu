@@ -326,10 +326,14 @@ row_id_kernel(const int* __restrict__ list, const HNode* __restrict__ nodes, T* 
     T* vsh = reinterpret_cast<T*>(nrm + rr);                 // reflector (p), 16-byte aligned
     T* W = ws + nd.o_w;                                      // p x rows, column c = row c of S_loc
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, NW = blockDim.x >> 5, NT = blockDim.x;
+    int ldw = p;                          // column stride of W
     if (w_in_smem) {
+        // staged copy with an odd column stride: thread-per-column loops stay free of bank conflicts
         T* Ws = vsh + ((p + 1) & ~1);
-        for (int64_t q = tid; q < (int64_t)p * rows; q += NT) Ws[q] = W[q];
+        const int lds = p | 1;
+        for (int64_t q = tid; q < (int64_t)p * rows; q += NT) Ws[(q / p) * lds + q % p] = W[q];
         W = Ws;
+        ldw = lds;
         __syncthreads();
     }
     __shared__ double s_val[32];
@@ -338,7 +342,7 @@ row_id_kernel(const int* __restrict__ list, const HNode* __restrict__ nodes, T* 
     __shared__ int s_best;
     __shared__ T s_beta;
     for (int c = warp; c < rows; c += NW) {
-        const T* col = W + (int64_t)c * p;
+        const T* col = W + (int64_t)c * ldw;
         real sacc = real(0);
         for (int j = lane; j < p; j += 32) sacc += nrm2r(col[j]);
         for (int o = 16; o; o >>= 1) sacc += __shfl_xor_sync(0xffffffffu, sacc, o);
@@ -381,9 +385,9 @@ row_id_kernel(const int* __restrict__ list, const HNode* __restrict__ nodes, T* 
         if (t >= kmax || cb == INT_MAX || !(s_bestv > eps * s_r11)) break;
         if (cb != t) {
             for (int j = tid; j < p; j += NT) {
-                const T a = W[(int64_t)t * p + j];
-                W[(int64_t)t * p + j] = W[(int64_t)cb * p + j];
-                W[(int64_t)cb * p + j] = a;
+                const T a = W[(int64_t)t * ldw + j];
+                W[(int64_t)t * ldw + j] = W[(int64_t)cb * ldw + j];
+                W[(int64_t)cb * ldw + j] = a;
             }
             if (tid == 0) {
                 const int a = piv[t];
@@ -396,7 +400,7 @@ row_id_kernel(const int* __restrict__ list, const HNode* __restrict__ nodes, T* 
         }
         __syncthreads();
         // reflector v = x - beta e1 of x = W(t:p, t), beta = -phase(x0) ||x||
-        T* xcol = W + (int64_t)t * p;
+        T* xcol = W + (int64_t)t * ldw;
         for (int j = t + tid; j < p; j += NT) vsh[j] = xcol[j];
         __syncthreads();
         if (tid == 0) {
@@ -422,7 +426,7 @@ row_id_kernel(const int* __restrict__ list, const HNode* __restrict__ nodes, T* 
                 vl[q] = (j < p) ? vsh[j] : zero<T>();
             }
             for (int c = t + 1 + warp; c < rows; c += NW) {
-                T* col = W + (int64_t)c * p;
+                T* col = W + (int64_t)c * ldw;
                 T cv[CH];
                 T w = zero<T>();
 #pragma unroll
@@ -455,11 +459,11 @@ row_id_kernel(const int* __restrict__ list, const HNode* __restrict__ nodes, T* 
     const int k = t;
     // T = R11^{-1} R12 in place of R12 (one column per thread)
     for (int c = k + tid; c < rows; c += NT) {
-        T* col = W + (int64_t)c * p;
+        T* col = W + (int64_t)c * ldw;
         for (int i = k - 1; i >= 0; --i) {
             T acc = col[i];
-            for (int l = i + 1; l < k; ++l) acc = fmac(-W[(int64_t)l * p + i], col[l], acc);
-            col[i] = acc * recip(W[(int64_t)i * p + i]);
+            for (int l = i + 1; l < k; ++l) acc = fmac(-W[(int64_t)l * ldw + i], col[l], acc);
+            col[i] = acc * recip(W[(int64_t)i * ldw + i]);
         }
     }
     __syncthreads();
@@ -468,7 +472,7 @@ row_id_kernel(const int* __restrict__ list, const HNode* __restrict__ nodes, T* 
         const int i = q % rows, a = q / rows;
         T v;
         if (i < k) v = (i == a) ? one<T>() : zero<T>();
-        else v = W[(int64_t)i * p + a];
+        else v = W[(int64_t)i * ldw + a];
         X[(int64_t)a * nd.rows_cap + piv[i]] = v;
     }
     if (tid == 0) kk[id] = k;
@@ -982,7 +986,7 @@ ndhss_status compress_problems(std::vector<Problem>& probs, bool lowrank, const 
         // the sample block of a node sits in shared memory when it fits (p <= 256 always)
         if (p > 256) return set_error(NDHSS_ERR_RANK_CAP, "hss: more than 256 samples per block (rank_cap too large)");
         const size_t smem_base = (size_t)(rows_cap_even((int)max_rows)) * sizeof(double) + (size_t)(p + 2) * sizeof(T) + 64;
-        const size_t smem_w = smem_base + (size_t)p * max_rows * sizeof(T);
+        const size_t smem_w = smem_base + (size_t)(p | 1) * max_rows * sizeof(T);
         const int w_in_smem = smem_w <= 200 * 1024 ? 1 : 0;
         const size_t smem_rid = w_in_smem ? smem_w : smem_base;
         HSS_TRY(cudaFuncSetAttribute(row_id_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)std::max<size_t>(smem_rid, 48 * 1024)));
