@@ -219,6 +219,16 @@ void ndhss_factor_destroy(ndhss_factorization* f);
  *             numbering; device or host pointers (host buffers are staged
  *             through device memory inside the call).  x and y may alias.
  * Stream-ordered; synchronises only when x or y is host memory.
+ * Each right-hand side is one persistent kernel launch working through a
+ * queue of row tasks in dependency order (plus one memset of its control
+ * words).  Every wait inside that kernel is bounded (2 s); when one gives
+ * up, the kernel returns early, y is undefined and the factorization keeps
+ * an error mark: this call (if it synchronises), ndhss_gmres and every later
+ * ndhss_apply that synchronises then return NDHSS_ERR_TIMEOUT, and later
+ * applies of that factorization return at once.  Destroy it and factor again.
+ * Setting the environment variable NDHSS_APPLY_SCHEDULE=levels selects one
+ * launch per tree level and phase instead (same arithmetic, bit-identical
+ * result; kept as a cross-check).
  */
 ndhss_status ndhss_apply(const ndhss_factorization* f, int32_t nrhs, const void* x, int64_t ldx,
                          void* y, int64_t ldy, void* stream);
@@ -234,10 +244,12 @@ ndhss_status ndhss_apply(const ndhss_factorization* f, int32_t nrhs, const void*
  *   d_x, d_y   DEVICE pointers, n float64/complex128 values (original
  *              numbering); host pointers are rejected with INVALID_ARG
  *   stream     stream the kernels are ordered on
- * The two work vectors live in one static device array of 16 MiB that every
+ * The work area (two vectors of n elements of the factor's type, one slot per
+ * rank component of every low-rank node for each sweep, and 4 + 5 x nodes
+ * 32-bit control words) lives in one static device array of 16 MiB that every
  * GPU loading the library holds until the process exits; problems needing
- * more (2 n x element size of the factor, i.e. n <= 524272 for complex128
- * fronts, n <= 1048560 for complex64 or float64 fronts) get INVALID_ARG.
+ * more (about n > 520000 for complex128 fronts, n > 1000000 for complex64 or
+ * float64 fronts) get INVALID_ARG.
  * The first call on a device looks up that array's device address (once per
  * device, with that device current): make that first call before any stream
  * capture.  All calls share the array and each overwrites it completely
@@ -245,6 +257,17 @@ ndhss_status ndhss_apply(const ndhss_factorization* f, int32_t nrhs, const void*
  * GPU (other streams, other threads) race on it and must be serialised.
  */
 ndhss_status ndhss_apply_noalloc(const ndhss_factorization* f, const void* d_x, void* d_y, void* stream);
+
+/*
+ * ndhss_testing_stall_apply -- failure-detection hook for tests (no
+ * counterpart in the paper).  Raises the completion requirement of the
+ * root's diagonal step by one, a count that no task will ever reach, so the
+ * down-sweep tasks of the next apply wait until their bound runs out.  That
+ * apply then ends early with the factorization marked as failed (see
+ * ndhss_apply).  Synchronous.  INVALID_ARG for NULL or a factorization
+ * without a dataflow queue.
+ */
+ndhss_status ndhss_testing_stall_apply(ndhss_factorization* f);
 
 /*
  * ndhss_spmv -- y = A x for a CSR matrix in float64 / complex128 (the

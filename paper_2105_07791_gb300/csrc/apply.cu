@@ -2,13 +2,41 @@
 //
 //   gather/cast   y = x(perm) converted to the factor precision
 //   up-sweep      levels bottom-up:  y(B^s) += L^s y(I^s)          (L = -BL P)
-//   diagonal      all nodes at once: z(I^s) = A_ii^{-1} y(I^s)     ("fully in parallel")
+//   diagonal      all nodes:         z(I^s) = A_ii^{-1} y(I^s)     ("fully in parallel")
 //   down-sweep    levels top-down:   z(I^s) += R^s z(B^s)
-//   scatter/cast  out(perm) = z converted back to float64
+//   scatter/cast  out(perm) = z converted back to float64, by whichever task
+//                 writes a row's final value
 //
-// Work is split into tasks of APPLY_ROWS output rows of one node; the tasks
-// of a level (or of the diagonal step) form one launch.  The whole factor is
-// streamed once per apply: A_ii^{-1}, L and R of every node once each.
+// The apply is a queue of row tasks, built once per factorization in
+// topological order.  Dense nodes with m_i <= DIAG_COLS take one pass over
+// the first m_i columns of the eliminated front, [A_ii^{-1} P^T ; -L P^T]:
+// the diagonal solve and the up-sweep product share the input y(I^s) and
+// the same dependencies, so one 64-row task gives z rows or y(B^s) updates.
+// A_ii^{-1} of larger nodes is split into DIAG_COLS-column chunks whose
+// partial products a second task sums (a 1539-column row is otherwise one
+// long dependent chain on the critical path).  Low-rank nodes use dot tasks
+// over LR_CHUNK-row chunks and 64-row axpy tasks.  Every task first issues
+// the loads that do not depend on other tasks (its first group of matrix
+// entries, the gather indices of its vector), then waits, then stages the
+// vector and finishes: the wait overlaps the matrix traffic.
+//
+// Two schedules run the same queue:
+// * dataflow (default): ONE persistent launch.  A CTA takes the next ticket
+//   with one atomic (prefetched while the previous task runs), waits until
+//   the nodes its task depends on have signalled their counters, runs the
+//   task and signals.  The boxes of one level own disjoint unknowns (B^s is
+//   part of box s), so a node's up-sweep and diagonal step need only its two
+//   children finished, and its down-sweep its parent's final rows.  A CTA
+//   only ever waits for tickets handed out before its own, which running
+//   CTAs hold, so the queue cannot deadlock for any grid size.  Every wait
+//   is bounded: after APPLY_WAIT_NS the CTA raises the sticky error word of
+//   the factorization and every CTA leaves (NDHSS_ERR_TIMEOUT at the next
+//   synchronising call).
+// * levels: the queue cut into its dependency groups (one tree level and
+//   phase each), one launch per group; selected with
+//   NDHSS_APPLY_SCHEDULE=levels and kept as the bit-exact cross-check.
+#include <cstdlib>
+#include <cstring>
 #include <mutex>
 
 #include "factor.cuh"
@@ -17,6 +45,11 @@ namespace ndhss {
 namespace {
 
 constexpr int AT = 256;
+constexpr int AW = AT / 32;
+constexpr int GATHER_CHUNK = 8 * AT;
+constexpr int DIAG_COLS = 256;    // column chunk of A_ii^{-1} per task (and fused-pass limit)
+constexpr int SUM_ROWS = AT;      // rows per partial-sum task
+constexpr uint64_t APPLY_WAIT_NS = 2000000000ull;   // 2 s
 
 __device__ __forceinline__ int nf(const int32_t* node, int s, int f) { return node[s * NODE_NF + f]; }
 
@@ -27,35 +60,106 @@ __device__ __forceinline__ Cx<R> shfl_xor_t(Cx<R> v, int o) {
     return {__shfl_xor_sync(0xffffffffu, v.x, o), __shfl_xor_sync(0xffffffffu, v.y, o)};
 }
 
-template <typename T, typename V>
-__global__ void gather_cast_kernel(int n, const int32_t* __restrict__ perm, const V* __restrict__ x, T* __restrict__ y) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) y[i] = from_val<T>(x[perm[i]]);
+// Loads and stores of the work vectors go through L2 (ld/st.cg): other CTAs
+// of the same launch write them, so no copy may come from a stale L1 line.
+__device__ __forceinline__ double ldw(const double* p) { return __ldcg(p); }
+__device__ __forceinline__ float ldw(const float* p) { return __ldcg(p); }
+__device__ __forceinline__ c128 ldw(const c128* p) {
+    const double2 v = __ldcg(reinterpret_cast<const double2*>(p));
+    return {v.x, v.y};
 }
-
-template <typename T, typename V>
-__global__ void scatter_cast_kernel(int n, const int32_t* __restrict__ perm, const T* __restrict__ z, V* __restrict__ out) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) out[perm[i]] = to_val(z[i]);
+__device__ __forceinline__ c64 ldw(const c64* p) {
+    const float2 v = __ldcg(reinterpret_cast<const float2*>(p));
+    return {v.x, v.y};
 }
+__device__ __forceinline__ void stw(double* p, double v) { __stcg(p, v); }
+__device__ __forceinline__ void stw(float* p, float v) { __stcg(p, v); }
+__device__ __forceinline__ void stw(c128* p, c128 v) { __stcg(reinterpret_cast<double2*>(p), make_double2(v.x, v.y)); }
+__device__ __forceinline__ void stw(c64* p, c64 v) { __stcg(reinterpret_cast<float2*>(p), make_float2(v.x, v.y)); }
 
+// Task kinds of the queue.
+enum : int {
+    TK_GATHER = 0,
+    TK_UPDIAG,    // dense, m_i <= DIAG_COLS: 64 rows of [A_ii^{-1}; -L] (z rows / y(B) updates)
+    TK_UP,        // dense, larger m_i: 64 rows of -L
+    TK_UPDOT,     // low-rank: partial X(chunk, :)^T y(I)(chunk)
+    TK_UPAXPY,    // low-rank: 64 rows of y(B) += RJt t
+    TK_UPNOP,     // completes a node with no up-sweep work
+    TK_DPART,     // 64 rows x DIAG_COLS columns of A_ii^{-1} y(I), partial
+    TK_DSUM,      // 256 rows: z(I) = sum of the partials
+    TK_DN,        // dense: 64 rows of z(I) += R z(B)
+    TK_DNDOT,     // low-rank: partial RJt(chunk, :)^T z(B)(chunk)
+    TK_DNAXPY,    // low-rank: 64 rows of z(I) += X t
+    TK_FINNOP     // completes a node without interior rows
+};
+// per-node counters (NCNT arrays of nnodes each) and what signals them
+enum : int { CN_UP = 0, CN_DOT, CN_DIAG, CN_DDOT, CN_FIN, CN_DPART, NCNT };
+constexpr int TK_SHIFT = 26;       // entry word 0 = kind << TK_SHIFT | node
+constexpr int TK_FINAL = 1 << 30;  // entry word 0 flag: the task writes final rows (scatter)
+constexpr int CTL_WORDS = 4;       // ticket, gather count, abort, pad
+// ints per queue entry: flags | kind | node, a, b, m_i, m_b, i_off, b_off, k,
+// base (64-bit: front offset, or low-rank storage address), aux (64-bit:
+// partial-product slot); everything a task reads before its first matrix load
+constexpr int QW = 12;
+
+// Read-only views of the factor for one apply (per-task sizes, offsets and
+// pointers travel in the queue entries).
+template <typename T>
+struct ApplyCtx {
+    const int32_t* node;
+    const int32_t* blist;
+    const int32_t* sigma;
+    const int32_t* perm;
+    const T* front;
+};
+
+// Registers a task fills before its wait: the first group of matrix entries
+// and the gather / scatter index of its own output row.
+template <typename T>
+struct Pre {
+    T v[8];
+    int gi, pi;
+};
+
+// ---- 64-row GEMV ----------------------------------------------------------
 // Rows [r0, r0 + 64) of (block A, column-major, leading dimension lda) times
 // the vector xs (shared memory): 8 warps take every 8th column, each lane
 // owns rows r0 + lane and r0 + lane + 32, and four columns are in flight per
 // step, so a thread keeps eight independent loads outstanding and a warp
-// reads each column segment as one contiguous 64-row access.  The eight warp
-// partial sums are added in shared memory; lanes of warp 0 and 1 return the
-// results for rows r0 + tid (tid < 64).
-constexpr int AW = AT / 32;
+// reads each column segment as one contiguous 64-row access.  The first
+// group of four columns is loaded by gemv_pre before the task's wait.  The
+// eight warp partial sums are added in shared memory; lanes of warp 0 and 1
+// return the results for rows r0 + tid (tid < 64).
+template <typename T>
+__device__ __forceinline__ void gemv_pre(const T* __restrict__ A, int64_t lda, int rows, int cols, int r0, T (&pre)[8]) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int ra = r0 + lane, rb = r0 + lane + 32;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        const int c = warp + u * AW;
+        const T* col = A + (int64_t)c * lda;
+        pre[u] = (c < cols && ra < rows) ? col[ra] : zero<T>();
+        pre[4 + u] = (c < cols && rb < rows) ? col[rb] : zero<T>();
+    }
+}
 
 template <typename T>
 __device__ __forceinline__ T gemv_rows64(const T* __restrict__ A, int64_t lda, int rows, int cols, int r0,
-                                         const T* __restrict__ xs, T (*red)[APPLY_ROWS]) {
+                                         const T* __restrict__ xs, T (*red)[APPLY_ROWS], const T (&pre)[8]) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int ra = r0 + lane, rb = r0 + lane + 32;
     const bool va = ra < rows, vb = rb < rows;
     T acc0 = zero<T>(), acc1 = zero<T>();
-    int c = warp;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        const int c = warp + u * AW;
+        if (c < cols) {
+            const T x = xs[c];
+            acc0 = fmac(pre[u], x, acc0);
+            acc1 = fmac(pre[4 + u], x, acc1);
+        }
+    }
+    int c = warp + 4 * AW;
     for (; c + 3 * AW < cols; c += 4 * AW) {
         T a[4], b[4], x[4];
 #pragma unroll
@@ -86,233 +190,716 @@ __device__ __forceinline__ T gemv_rows64(const T* __restrict__ A, int64_t lda, i
     return sum;
 }
 
-// y(B^s) -= BL y(I^s)(sigma)   (= L^s y(I^s), Eq. 3.3a)
+// ---- one task: pre-phase (independent loads) and run-phase ----------------
+
+struct Entry {
+    int kind, s, a, b;
+    bool fin;
+    int m_i, m_b, i_off, b_off, k;
+    int64_t base, aux;
+};
+__device__ __forceinline__ Entry decode(const int32_t* q, int64_t t) {
+    const int4* p = reinterpret_cast<const int4*>(q + QW * t);
+    const int4 v0 = p[0], v1 = p[1], v2 = p[2];
+    Entry e;
+    e.fin = (v0.x & TK_FINAL) != 0;
+    e.kind = (v0.x >> TK_SHIFT) & 15;
+    e.s = v0.x & ((1 << TK_SHIFT) - 1);
+    e.a = v0.y;
+    e.b = v0.z;
+    e.m_i = v0.w;
+    e.m_b = v1.x;
+    e.i_off = v1.y;
+    e.b_off = v1.z;
+    e.k = v1.w;
+    e.base = (int64_t)(((uint64_t)(uint32_t)v2.y << 32) | (uint32_t)v2.x);
+    e.aux = (int64_t)(((uint64_t)(uint32_t)v2.w << 32) | (uint32_t)v2.z);
+    return e;
+}
+
+// Loads every task can issue before its dependencies are met: matrix
+// entries (read-only during the apply) and index lists.  idx: shared int
+// array of at least max(m_i, m_b, LR_CHUNK) entries.
 template <typename T>
-__global__ void __launch_bounds__(AT)
-upsweep_kernel(const int32_t* __restrict__ tasks, const int32_t* __restrict__ node, const int64_t* __restrict__ foff,
-               const int32_t* __restrict__ blist, const int32_t* __restrict__ sigma, const T* __restrict__ front,
-               T* __restrict__ y) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ T red[AW][APPLY_ROWS];
-    T* ys = reinterpret_cast<T*>(smem_raw);
-    const int s = tasks[2 * blockIdx.x], j0 = tasks[2 * blockIdx.x + 1];
-    const int m_i = nf(node, s, 5), m_b = nf(node, s, 7), i_off = nf(node, s, 4), b_off = nf(node, s, 6);
+__device__ __forceinline__ void task_pre(const ApplyCtx<T>& C, const Entry& e, Pre<T>& P, int* idx) {
+    const int s = e.s;
+    const int tid = threadIdx.x;
+    P.gi = -1;
+    P.pi = -1;
+    if (e.kind == TK_GATHER) return;
+    const int m_i = e.m_i, m_b = e.m_b, i_off = e.i_off, b_off = e.b_off;
     const int64_t m = (int64_t)m_i + m_b;
-    for (int c = threadIdx.x; c < m_i; c += AT) ys[c] = y[i_off + sigma[i_off + c]];
-    __syncthreads();
-    const T sum = gemv_rows64(front + foff[s] + m_i, m, m_b, m_i, j0, ys, red);
-    const int j = j0 + threadIdx.x;
-    if (threadIdx.x < APPLY_ROWS && j < m_b) {
-        const int g = blist[b_off + j];
-        y[g] = y[g] - sum;
+    const T* F = C.front + e.base;
+    switch (e.kind) {
+    case TK_UPDIAG: {
+        gemv_pre(F, m, (int)m, m_i, e.a, P.v);
+        for (int c = tid; c < m_i; c += AT) idx[c] = C.sigma[i_off + c];
+        const int r = e.a + tid;
+        if (tid < APPLY_ROWS && r < m) {
+            if (r >= m_i) P.gi = C.blist[b_off + r - m_i];
+            else if (e.fin) P.pi = C.perm[i_off + r];
+        }
+        break;
+    }
+    case TK_UP: {
+        gemv_pre(F + m_i, m, m_b, m_i, e.a, P.v);
+        for (int c = tid; c < m_i; c += AT) idx[c] = C.sigma[i_off + c];
+        if (tid < APPLY_ROWS && e.a + tid < m_b) P.gi = C.blist[b_off + e.a + tid];
+        break;
+    }
+    case TK_DPART: {
+        const int nc = min(DIAG_COLS, m_i - e.b);
+        gemv_pre(F + (int64_t)e.b * m, m, m_i, nc, e.a, P.v);
+        for (int c = tid; c < nc; c += AT) idx[c] = C.sigma[i_off + e.b + c];
+        break;
+    }
+    case TK_DSUM:
+        if (e.fin && e.a + tid < m_i) P.pi = C.perm[i_off + e.a + tid];
+        break;
+    case TK_DN: {
+        gemv_pre(F + (int64_t)m_i * m, m, m_i, m_b, e.a, P.v);
+        for (int j = tid; j < m_b; j += AT) idx[j] = C.blist[b_off + j];
+        if (tid < APPLY_ROWS && e.a + tid < m_i) P.pi = C.perm[i_off + e.a + tid];
+        break;
+    }
+    case TK_UPDOT: case TK_DNDOT: {
+        const int k = e.k;
+        const bool up = e.kind == TK_UPDOT;
+        const int len = up ? m_i : m_b;
+        const int rn = min(LR_CHUNK, len - e.a);
+        const T* X = reinterpret_cast<const T*>(e.base);
+        const T* M = (up ? X : X + (int64_t)m_i * k) + e.a;
+        const int lane = tid & 31, warp = tid >> 5;
+        const int a = e.b + warp;           // first column of this warp in the task's column group
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int i = lane + 32 * u;
+            P.v[u] = (a < k && i < rn) ? M[(int64_t)a * len + i] : zero<T>();
+        }
+        if (!up)
+            for (int i = tid; i < rn; i += AT) idx[i] = C.blist[b_off + e.a + i];
+        break;
+    }
+    case TK_UPAXPY: {
+        const int k = e.k;
+        const T* X = reinterpret_cast<const T*>(e.base);
+        gemv_pre(X + (int64_t)m_i * k, m_b, m_b, k, e.a, P.v);
+        if (tid < APPLY_ROWS && e.a + tid < m_b) P.gi = C.blist[b_off + e.a + tid];
+        break;
+    }
+    case TK_DNAXPY: {
+        const int k = e.k;
+        const T* X = reinterpret_cast<const T*>(e.base);
+        gemv_pre(X, m_i, m_i, k, e.a, P.v);
+        if (tid < APPLY_ROWS && e.a + tid < m_i) P.pi = C.perm[i_off + e.a + tid];
+        break;
+    }
+    default: break;
     }
 }
 
-// z(I^s) = X y(I^s)(sigma)   (= A_ii^{-1} y(I^s))
-template <typename T>
-__global__ void __launch_bounds__(AT)
-diag_kernel(const int32_t* __restrict__ tasks, const int32_t* __restrict__ node, const int64_t* __restrict__ foff,
-            const int32_t* __restrict__ sigma, const T* __restrict__ front, const T* __restrict__ y, T* __restrict__ z) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ T red[AW][APPLY_ROWS];
-    T* ys = reinterpret_cast<T*>(smem_raw);
-    const int s = tasks[2 * blockIdx.x], i0 = tasks[2 * blockIdx.x + 1];
-    const int m_i = nf(node, s, 5), i_off = nf(node, s, 4);
-    const int64_t m = (int64_t)m_i + nf(node, s, 7);
-    for (int c = threadIdx.x; c < m_i; c += AT) ys[c] = y[i_off + sigma[i_off + c]];
+// The rest of the task, once the tasks it depends on have finished.  vec:
+// shared T array of at least max(m_i, m_b, LR_CHUNK) entries.  Starts with a
+// barrier (idx was written in the pre-phase) and ends with its last shared
+// memory use before the caller's next barrier.
+template <typename T, typename V>
+__device__ __forceinline__ void task_run(const ApplyCtx<T>& C, const Entry& e, const Pre<T>& P, const int* idx, T* vec,
+                                         T (*red)[APPLY_ROWS], int n, const V* __restrict__ x, V* __restrict__ out,
+                                         T* y, T* z, T* tup, T* tdn, T* dpart) {
+    const int s = e.s;
+    const int tid = threadIdx.x;
+    if (e.kind == TK_GATHER) {
+        const int i1 = min(n, e.a + GATHER_CHUNK);
+        for (int i = e.a + tid; i < i1; i += AT) stw(y + i, from_val<T>(x[C.perm[i]]));
+        return;
+    }
     __syncthreads();
-    const T sum = gemv_rows64(front + foff[s], m, m_i, m_i, i0, ys, red);
-    const int i = i0 + threadIdx.x;
-    if (threadIdx.x < APPLY_ROWS && i < m_i) z[i_off + i] = sum;
-}
-
-// z(I^s) += R z(B^s)   (Eq. 3.3b)
-template <typename T>
-__global__ void __launch_bounds__(AT)
-downsweep_kernel(const int32_t* __restrict__ tasks, const int32_t* __restrict__ node, const int64_t* __restrict__ foff,
-                 const int32_t* __restrict__ blist, const T* __restrict__ front, T* __restrict__ z) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ T red[AW][APPLY_ROWS];
-    T* zb = reinterpret_cast<T*>(smem_raw);
-    const int s = tasks[2 * blockIdx.x], i0 = tasks[2 * blockIdx.x + 1];
-    const int m_i = nf(node, s, 5), m_b = nf(node, s, 7), i_off = nf(node, s, 4), b_off = nf(node, s, 6);
+    const int m_i = e.m_i, m_b = e.m_b, i_off = e.i_off;
     const int64_t m = (int64_t)m_i + m_b;
-    for (int j = threadIdx.x; j < m_b; j += AT) zb[j] = z[blist[b_off + j]];
-    __syncthreads();
-    const T sum = gemv_rows64(front + foff[s] + (int64_t)m_i * m, m, m_i, m_b, i0, zb, red);
-    const int i = i0 + threadIdx.x;
-    if (threadIdx.x < APPLY_ROWS && i < m_i) z[i_off + i] = z[i_off + i] + sum;
+    const T* F = C.front + e.base;
+    switch (e.kind) {
+    case TK_UPDIAG: {
+        for (int c = tid; c < m_i; c += AT) vec[c] = ldw(y + i_off + idx[c]);
+        __syncthreads();
+        const T sum = gemv_rows64(F, m, (int)m, m_i, e.a, vec, red, P.v);
+        const int r = e.a + tid;
+        if (tid < APPLY_ROWS && r < m) {
+            if (r < m_i) {
+                stw(z + i_off + r, sum);
+                if (e.fin) out[P.pi] = to_val(sum);
+            } else {
+                stw(y + P.gi, ldw(y + P.gi) - sum);
+            }
+        }
+        break;
+    }
+    case TK_UP: {
+        for (int c = tid; c < m_i; c += AT) vec[c] = ldw(y + i_off + idx[c]);
+        __syncthreads();
+        const T sum = gemv_rows64(F + m_i, m, m_b, m_i, e.a, vec, red, P.v);
+        if (P.gi >= 0) stw(y + P.gi, ldw(y + P.gi) - sum);
+        break;
+    }
+    case TK_DPART: {
+        const int nc = min(DIAG_COLS, m_i - e.b);
+        for (int c = tid; c < nc; c += AT) vec[c] = ldw(y + i_off + idx[c]);
+        __syncthreads();
+        const T sum = gemv_rows64(F + (int64_t)e.b * m, m, m_i, nc, e.a, vec, red, P.v);
+        const int r = e.a + tid;
+        if (tid < APPLY_ROWS && r < m_i) stw(dpart + e.aux + (int64_t)(e.b / DIAG_COLS) * m_i + r, sum);
+        break;
+    }
+    case TK_DSUM: {
+        const int r = e.a + tid;
+        if (r < m_i) {
+            const int nch = (m_i + DIAG_COLS - 1) / DIAG_COLS;
+            const T* p = dpart + e.aux + r;
+            T acc = ldw(p);
+            for (int c = 1; c < nch; ++c) acc = acc + ldw(p + (int64_t)c * m_i);
+            stw(z + i_off + r, acc);
+            if (e.fin) out[P.pi] = to_val(acc);
+        }
+        break;
+    }
+    case TK_DN: {
+        for (int j = tid; j < m_b; j += AT) vec[j] = ldw(z + idx[j]);
+        __syncthreads();
+        const T sum = gemv_rows64(F + (int64_t)m_i * m, m, m_i, m_b, e.a, vec, red, P.v);
+        const int r = e.a + tid;
+        if (tid < APPLY_ROWS && r < m_i) {
+            const T v = ldw(z + i_off + r) + sum;
+            stw(z + i_off + r, v);
+            out[P.pi] = to_val(v);
+        }
+        break;
+    }
+    case TK_UPDOT: case TK_DNDOT: {
+        // Low-rank (R ~ X R(J, :), stored as X (m_i x k) then RJt = R(J, :)^T
+        // (m_b x k), column-major; L = R^T): t_c = M(chunk, :)^T v(chunk) with
+        // M = X going up (v = y(I)), M = RJt coming down (v = z(B)); warp w
+        // takes columns w, w + 8, ...; each lane 8 rows of each column.
+        const bool up = e.kind == TK_UPDOT;
+        const int k = e.k;
+        const int len = up ? m_i : m_b;
+        const int rn = min(LR_CHUNK, len - e.a);
+        for (int i = tid; i < rn; i += AT) vec[i] = up ? ldw(y + i_off + e.a + i) : ldw(z + idx[i]);
+        __syncthreads();
+        const int lane = tid & 31, warp = tid >> 5;
+        const T* X = reinterpret_cast<const T*>(e.base);
+        const T* M = (up ? X : X + (int64_t)m_i * k) + e.a;
+        T* dst = (up ? tup : tdn) + e.aux + (int64_t)(e.a / LR_CHUNK) * k;
+        // the task's column group: columns b + warp + v * AW, v < CPS (two per
+        // warp for 8-byte types, one for 16-byte types); v = 0 was loaded in
+        // the pre-phase
+        constexpr int CPS = sizeof(T) <= 8 ? 2 : 1;
+        T p[CPS][8];
+#pragma unroll
+        for (int v = 0; v < CPS; ++v)
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int i = lane + 32 * u, av = e.b + warp + v * AW;
+                p[v][u] = (v == 0) ? P.v[u] : ((av < k && i < rn) ? M[(int64_t)av * len + i] : zero<T>());
+            }
+        T sp[CPS];
+#pragma unroll
+        for (int v = 0; v < CPS; ++v) sp[v] = zero<T>();
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int i = lane + 32 * u;
+            const T xv = (i < rn) ? vec[i] : zero<T>();
+#pragma unroll
+            for (int v = 0; v < CPS; ++v) sp[v] = fmac(p[v][u], xv, sp[v]);
+        }
+#pragma unroll
+        for (int v = 0; v < CPS; ++v) {
+            for (int o = 16; o; o >>= 1) sp[v] = sp[v] + shfl_xor_t(sp[v], o);
+            const int av = e.b + warp + v * AW;
+            if (lane == 0 && av < k) stw(dst + av, sp[v]);
+        }
+        break;
+    }
+    case TK_UPAXPY: case TK_DNAXPY: {
+        // t = sum of the dot tasks' chunk partials, then 64 rows of M t with
+        // M = RJt going up (rows of B), X coming down (rows of I)
+        const bool up = e.kind == TK_UPAXPY;
+        const int k = e.k;
+        const int len_in = up ? m_i : m_b, len = up ? m_b : m_i;
+        const int nch = (len_in + LR_CHUNK - 1) / LR_CHUNK;
+        const T* tp = (up ? tup : tdn) + e.aux;
+        for (int a = tid; a < k; a += AT) {
+            T acc = ldw(tp + a);
+            for (int c = 1; c < nch; ++c) acc = acc + ldw(tp + (int64_t)c * k + a);
+            vec[a] = acc;
+        }
+        __syncthreads();
+        const T* X = reinterpret_cast<const T*>(e.base);
+        const T sum = gemv_rows64(up ? X + (int64_t)m_i * k : X, len, len, k, e.a, vec, red, P.v);
+        const int r = e.a + tid;
+        if (tid < APPLY_ROWS && r < len) {
+            if (up) {
+                stw(y + P.gi, ldw(y + P.gi) + sum);
+            } else {
+                const T v = ldw(z + i_off + r) + sum;
+                stw(z + i_off + r, v);
+                out[P.pi] = to_val(v);
+            }
+        }
+        break;
+    }
+    default: break;
+    }
 }
 
+// ---- dataflow schedule: one persistent launch -----------------------------
 
-// Low-rank levels (R ~ X R(J, :), stored as X (m_i x k) and RJt = R(J, :)^T
-// (m_b x k), both column-major; L = R^T by symmetry).  Each level is two
-// launches over all its nodes:
-//   dot   tasks (node, 8 outputs): warp w forms t[a0 + w] as a coalesced,
-//         4-way unrolled dot product of a stored column with the gathered
-//         vector, written to scratch;
-//   axpy  tasks (node, 256 rows): each thread adds sum_a M(row, a) t[a].
-// up-sweep (mode 0):   t = X^T y(I^s);     y(B^s) += RJt t
-// down-sweep (mode 1): t = RJt^T z(B^s);   z(I^s) += X t
-template <typename T>
-__global__ void __launch_bounds__(AT)
-lr_dot_kernel(const int32_t* __restrict__ tasks, const int32_t* __restrict__ node, const uint64_t* __restrict__ lrp,
-              const int32_t* __restrict__ lrk, const int64_t* __restrict__ toff, const int32_t* __restrict__ blist,
-              const T* __restrict__ v, T* __restrict__ tsc, int mode) {
-    const int s = tasks[2 * blockIdx.x], a0 = tasks[2 * blockIdx.x + 1];
-    const int m_i = nf(node, s, 5), m_b = nf(node, s, 7), i_off = nf(node, s, 4), b_off = nf(node, s, 6);
-    const int k = lrk[s];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int a = a0 + warp;
-    if (a >= k) return;
-    const T* X = reinterpret_cast<const T*>(lrp[s]);
-    const T* col = (mode == 0) ? X + (int64_t)a * m_i : X + (int64_t)m_i * k + (int64_t)a * m_b;
-    const int len = (mode == 0) ? m_i : m_b;
-    T acc0 = zero<T>(), acc1 = zero<T>(), acc2 = zero<T>(), acc3 = zero<T>();
-    int i = lane;
-    if (mode == 0) {
-        const T* x = v + i_off;
-        for (; i + 96 < len; i += 128) {
-            acc0 = fmac(col[i], x[i], acc0);
-            acc1 = fmac(col[i + 32], x[i + 32], acc1);
-            acc2 = fmac(col[i + 64], x[i + 64], acc2);
-            acc3 = fmac(col[i + 96], x[i + 96], acc3);
+__device__ __forceinline__ int ld_acquire(const int32_t* p) {
+    int v;
+    asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ int ld_relaxed(const int32_t* p) {
+    int v;
+    asm volatile("ld.relaxed.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+struct Sched {
+    const int32_t* q;          // [QW * nq] entries
+    int32_t nq, ngather, nn, pad;
+    const int32_t* need;       // [NCNT * nn]
+    int32_t* ctl;              // [CTL_WORDS + NCNT * nn], zeroed before the launch
+    int32_t* err;              // sticky error word of the factorization
+};
+
+// Bounded wait until *ctr >= need; false once the wait gave up or another
+// CTA reported a failure.
+__device__ bool wait_geq(const Sched& S, const int32_t* ctr, int need, uint64_t& t0) {
+    if (need <= 0 || ld_acquire(ctr) >= need) return true;
+    unsigned sleep = 32;
+    for (;;) {
+        if (ld_acquire(ctr) >= need) return true;
+        if (ld_acquire(S.ctl + 2)) return false;
+        __nanosleep(sleep);
+        if (sleep < 256) sleep *= 2;
+        const uint64_t now = global_ns();
+        if (t0 == 0) t0 = now;
+        else if (now - t0 > APPLY_WAIT_NS) {
+            atomicExch(S.ctl + 2, 1);
+            atomicExch(S.err, 1);
+            return false;
         }
-        for (; i < len; i += 32) acc0 = fmac(col[i], x[i], acc0);
-    } else {
-        const int32_t* bl = blist + b_off;
-        for (; i + 96 < len; i += 128) {
-            acc0 = fmac(col[i], v[bl[i]], acc0);
-            acc1 = fmac(col[i + 32], v[bl[i + 32]], acc1);
-            acc2 = fmac(col[i + 64], v[bl[i + 64]], acc2);
-            acc3 = fmac(col[i + 96], v[bl[i + 96]], acc3);
-        }
-        for (; i < len; i += 32) acc0 = fmac(col[i], v[bl[i]], acc0);
     }
-    T acc = (acc0 + acc1) + (acc2 + acc3);
-    for (int o = 16; o; o >>= 1) acc = acc + shfl_xor_t(acc, o);
-    if (lane == 0) tsc[toff[s] + a] = acc;
+}
+
+// Up to three (counter, requirement) pairs a task waits for.
+struct Deps {
+    const int32_t* c[3];
+    int need[3];
+    int n;
+};
+
+__device__ __forceinline__ Deps task_deps(const Sched& S, const int32_t* node, const Entry& e) {
+    Deps d;
+    d.n = 0;
+    const int32_t* cnt = S.ctl + CTL_WORDS;
+    const int nn = S.nn, s = e.s;
+    auto add = [&](int c, int which) {
+        d.c[d.n] = cnt + which * nn + c;
+        d.need[d.n] = S.need[which * nn + c];
+        ++d.n;
+    };
+    switch (e.kind) {
+    case TK_UPDIAG: case TK_UP: case TK_UPDOT: case TK_UPNOP: case TK_DPART: {
+        d.c[0] = S.ctl + 1;
+        d.need[0] = S.ngather;
+        d.n = 1;
+        const int c0 = nf(node, s, 2), c1 = nf(node, s, 3);
+        if (c0 >= 0) add(c0, CN_UP);
+        if (c1 >= 0) add(c1, CN_UP);
+        break;
+    }
+    case TK_UPAXPY: add(s, CN_DOT); break;
+    case TK_DSUM: add(s, CN_DPART); break;
+    case TK_DN: case TK_DNDOT: case TK_FINNOP: {
+        const int p = nf(node, s, 1);
+        if (p >= 0) add(p, CN_FIN);
+        if (e.kind == TK_DN) add(s, CN_DIAG);
+        break;
+    }
+    case TK_DNAXPY: add(s, CN_DDOT); add(s, CN_DIAG); break;
+    default: break;
+    }
+    return d;
+}
+
+// All requirements read at once with relaxed loads (the common case: already
+// met), then a fence for acquire ordering; otherwise bounded spins.
+__device__ bool wait_deps(const Sched& S, const int32_t* node, const Entry& e) {
+    if (ld_relaxed(S.ctl + 2) || ld_relaxed(S.err)) return false;
+    const Deps d = task_deps(S, node, e);
+    int v[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) v[i] = (i < d.n) ? ld_relaxed(d.c[i]) : 0;
+    bool met = true;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) met = met && (i >= d.n || v[i] >= d.need[i]);
+    if (!met) {
+        uint64_t t0 = 0;
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+            if (i < d.n && !wait_geq(S, d.c[i], d.need[i], t0)) return false;
+    }
+    __threadfence();
+    return true;
+}
+
+// counters a finished task signals (bit per CN_*), -1 bit 31 for the gather count
+__device__ __forceinline__ unsigned task_signals(const Entry& e) {
+    switch (e.kind) {
+    case TK_GATHER: return 1u << 31;
+    case TK_UPDIAG: return (1u << CN_UP) | (1u << CN_DIAG) | (e.fin ? (1u << CN_FIN) : 0u);
+    case TK_UP: case TK_UPAXPY: case TK_UPNOP: return 1u << CN_UP;
+    case TK_UPDOT: return 1u << CN_DOT;
+    case TK_DPART: return 1u << CN_DPART;
+    case TK_DSUM: return (1u << CN_DIAG) | (e.fin ? (1u << CN_FIN) : 0u);
+    case TK_DN: case TK_DNAXPY: case TK_FINNOP: return 1u << CN_FIN;
+    case TK_DNDOT: return 1u << CN_DDOT;
+    default: return 0u;
+    }
+}
+
+// resident CTAs per SM the register budget is sized for (latency hiding)
+template <typename T> constexpr int apply_min_blocks() { return sizeof(T) <= 8 ? 4 : 3; }
+
+template <typename T, typename V>
+__global__ void __launch_bounds__(AT, apply_min_blocks<T>()) apply_dataflow_kernel(ApplyCtx<T> C, Sched S, int n, const V* __restrict__ x,
+                                                            V* __restrict__ out, T* y, T* z, T* tup, T* tdn, T* dpart,
+                                                            int vlen) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ T red[AW][APPLY_ROWS];
+    __shared__ int s_task, s_ok;
+    T* vec = reinterpret_cast<T*>(smem_raw);
+    int* idx = reinterpret_cast<int*>(vec + vlen);
+    int32_t* cnt = S.ctl + CTL_WORDS;
+    // thread 0 holds the next ticket while the CTA works on the current task:
+    // the ticket's atomic overlaps the work (deadlock-free: a held ticket is
+    // only waited on by higher tickets, and its holder starts it as soon as
+    // its current task ends)
+    int next = (threadIdx.x == 0) ? atomicAdd(S.ctl, 1) : 0;
+    for (;;) {
+        if (threadIdx.x == 0) s_task = next;
+        __syncthreads();
+        const int t = s_task;
+        if (t >= S.nq) break;
+        const Entry e = decode(S.q, t);
+        Pre<T> P;
+        task_pre(C, e, P, idx);
+        if (threadIdx.x == 0) {
+            const int ok = wait_deps(S, C.node, e) ? 1 : 0;
+            s_ok = ok;
+            if (ok) next = atomicAdd(S.ctl, 1);
+        }
+        __syncthreads();
+        if (!s_ok) break;
+        task_run<T, V>(C, e, P, idx, vec, red, n, x, out, y, z, tup, tdn, dpart);
+        // publish: the barrier orders every thread's stores before thread 0's
+        // gpu-scope fence, which orders them before the signals
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            __threadfence();
+            const unsigned sig = task_signals(e);
+            if (sig >> 31) atomicAdd(S.ctl + 1, 1);
+#pragma unroll
+            for (int w = 0; w < NCNT; ++w)
+                if ((sig >> w) & 1u) atomicAdd(cnt + w * S.nn + e.s, 1);
+        }
+    }
+}
+
+// ---- level schedule: one launch per dependency group of the queue ---------
+
+template <typename T, typename V>
+__global__ void __launch_bounds__(AT, apply_min_blocks<T>()) apply_group_kernel(ApplyCtx<T> C, const int32_t* __restrict__ q, int n,
+                                                         const V* __restrict__ x, V* __restrict__ out, T* y, T* z, T* tup,
+                                                         T* tdn, T* dpart, int vlen) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ T red[AW][APPLY_ROWS];
+    T* vec = reinterpret_cast<T*>(smem_raw);
+    int* idx = reinterpret_cast<int*>(vec + vlen);
+    const Entry e = decode(q, blockIdx.x);
+    Pre<T> P;
+    task_pre(C, e, P, idx);
+    task_run<T, V>(C, e, P, idx, vec, red, n, x, out, y, z, tup, tdn, dpart);
+}
+
+bool levels_schedule_requested() {
+    const char* e = std::getenv("NDHSS_APPLY_SCHEDULE");
+    return e && std::strcmp(e, "levels") == 0;
 }
 
 template <typename T>
-__global__ void __launch_bounds__(AT)
-lr_axpy_kernel(const int32_t* __restrict__ tasks, const int32_t* __restrict__ node, const uint64_t* __restrict__ lrp,
-               const int32_t* __restrict__ lrk, const int64_t* __restrict__ toff, const int32_t* __restrict__ blist,
-               const T* __restrict__ tsc, T* __restrict__ v, int mode) {
-    __shared__ T ts[512];
-    const int s = tasks[2 * blockIdx.x], r0 = tasks[2 * blockIdx.x + 1];
-    const int m_i = nf(node, s, 5), m_b = nf(node, s, 7), i_off = nf(node, s, 4), b_off = nf(node, s, 6);
-    const int k = lrk[s];
-    for (int a = threadIdx.x; a < k && a < 512; a += AT) ts[a] = tsc[toff[s] + a];
-    __syncthreads();
-    const T* X = reinterpret_cast<const T*>(lrp[s]);
-    const T* M = (mode == 0) ? X + (int64_t)m_i * k : X;       // RJt (m_b x k) or X (m_i x k)
-    const int len = (mode == 0) ? m_b : m_i;
-    const int r = r0 + threadIdx.x;
-    if (r >= len) return;
-    T acc0 = zero<T>(), acc1 = zero<T>(), acc2 = zero<T>(), acc3 = zero<T>();
-    int a = 0;
-    for (; a + 3 < k; a += 4) {
-        acc0 = fmac(M[(int64_t)a * len + r], ts[a], acc0);
-        acc1 = fmac(M[(int64_t)(a + 1) * len + r], ts[a + 1], acc1);
-        acc2 = fmac(M[(int64_t)(a + 2) * len + r], ts[a + 2], acc2);
-        acc3 = fmac(M[(int64_t)(a + 3) * len + r], ts[a + 3], acc3);
-    }
-    for (; a < k; ++a) acc0 = fmac(M[(int64_t)a * len + r], ts[a], acc0);
-    const T acc = (acc0 + acc1) + (acc2 + acc3);
-    if (mode == 0) {
-        const int g = blist[b_off + r];
-        v[g] = v[g] + acc;
-    } else {
-        v[i_off + r] = v[i_off + r] + acc;
-    }
+ApplyCtx<T> make_ctx(const FactorData& F) {
+    return ApplyCtx<T>{F.d_node, F.d_blist, F.d_sigma, F.d_perm, static_cast<const T*>(F.d_front)};
+}
+
+// work space: y, z (n each), low-rank partials for each sweep, diagonal
+// partials, control words
+struct WorkLayout {
+    size_t y, z, tup, tdn, dpart, ctl, total;
+};
+WorkLayout work_layout(const FactorData& F) {
+    auto r256 = [](size_t b) { return (b + 255) / 256 * 256; };
+    WorkLayout L{};
+    const size_t vec = r256((size_t)F.n * F.esize);
+    const size_t tb = r256((size_t)std::max<int64_t>(F.lr_t_total, 1) * F.esize);
+    L.y = 0;
+    L.z = vec;
+    L.tup = 2 * vec;
+    L.tdn = L.tup + tb;
+    L.dpart = L.tdn + tb;
+    L.ctl = L.dpart + r256((size_t)std::max<int64_t>(F.dpart_total, 1) * F.esize);
+    L.total = L.ctl + r256(sizeof(int32_t) * (CTL_WORDS + (size_t)NCNT * std::max(F.nnodes, 1)));
+    return L;
+}
+
+size_t smem_bytes(const FactorData& F, size_t esize) {
+    return (size_t)F.sched_vlen * (esize + sizeof(int));
 }
 
 template <typename T, typename V>
-ndhss_status apply_run(const FactorData& F, int32_t nrhs, const V* x, int64_t ldx, V* y, int64_t ldy, T* w0, T* w1,
+ndhss_status apply_run(const FactorData& F, int32_t nrhs, const V* x, int64_t ldx, V* y, int64_t ldy, unsigned char* w,
                        cudaStream_t st) {
-    const T* front = static_cast<const T*>(F.d_front);
-    const int nb = (F.n + 255) / 256;
-    const size_t smem_i = (size_t)std::max(F.max_mi, 1) * sizeof(T);
-    const size_t smem_b = (size_t)std::max(F.max_mb, 1) * sizeof(T);
-    if (smem_i > 48 * 1024) {
-        NDHSS_CUDA_TRY(cudaFuncSetAttribute(upsweep_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_i));
-        NDHSS_CUDA_TRY(cudaFuncSetAttribute(diag_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_i));
+    if (!F.d_sched) return set_error(NDHSS_ERR_INTERNAL, "apply: factorization has no task queue");
+    const WorkLayout WL = work_layout(F);
+    const ApplyCtx<T> C = make_ctx<T>(F);
+    T* wy = reinterpret_cast<T*>(w + WL.y);
+    T* wz = reinterpret_cast<T*>(w + WL.z);
+    T* tup = reinterpret_cast<T*>(w + WL.tup);
+    T* tdn = reinterpret_cast<T*>(w + WL.tdn);
+    T* dpart = reinterpret_cast<T*>(w + WL.dpart);
+    const size_t smem = smem_bytes(F, sizeof(T));
+    const int vlen = F.sched_vlen;
+    if (levels_schedule_requested()) {
+        for (int r = 0; r < nrhs; ++r)
+            for (size_t g = 0; g + 1 < F.sched_groups.size(); ++g) {
+                const int64_t g0 = F.sched_groups[g], g1 = F.sched_groups[g + 1];
+                if (g1 == g0) continue;
+                apply_group_kernel<T, V><<<(unsigned)(g1 - g0), AT, smem, st>>>(
+                    C, F.d_sched + QW * g0, F.n, x + r * ldx, y + r * ldy, wy, wz, tup, tdn, dpart, vlen);
+                NDHSS_LAUNCH_CHECK("apply_group_kernel");
+            }
+        return NDHSS_OK;
     }
-    if (smem_b > 48 * 1024)
-        NDHSS_CUDA_TRY(cudaFuncSetAttribute(downsweep_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_b));
-    T* tsc = reinterpret_cast<T*>(reinterpret_cast<unsigned char*>(w1) + ((size_t)F.n * sizeof(T) + 255) / 256 * 256);
+    Sched S{F.d_sched, (int32_t)F.sched_n, F.sched_ngather, F.nnodes, 0, F.d_need,
+            reinterpret_cast<int32_t*>(w + WL.ctl), F.d_apply_err};
+    const size_t ctl_bytes = sizeof(int32_t) * (CTL_WORDS + (size_t)NCNT * F.nnodes);
     for (int r = 0; r < nrhs; ++r) {
-        gather_cast_kernel<T, V><<<nb, 256, 0, st>>>(F.n, F.d_perm, x + r * ldx, w0);
-        NDHSS_LAUNCH_CHECK("gather_cast_kernel");
-        for (int l = F.depth; l >= 0; --l) {
-            if (l < F.L_hss && !F.lr_cnt.empty()) {
-                if (F.lr_dot_cnt[l]) {
-                    lr_dot_kernel<T><<<(unsigned)F.lr_dot_cnt[l], AT, 0, st>>>(F.d_tasks + 2 * F.lr_dot_off[l], F.d_node,
-                                                                             F.d_lr_ptr, F.d_lr_k, F.d_lr_toff, F.d_blist,
-                                                                             w0, tsc, 0);
-                    NDHSS_LAUNCH_CHECK("lr_dot_kernel");
-                    lr_axpy_kernel<T><<<(unsigned)F.lr_bax_cnt[l], AT, 0, st>>>(F.d_tasks + 2 * F.lr_bax_off[l], F.d_node,
-                                                                              F.d_lr_ptr, F.d_lr_k, F.d_lr_toff, F.d_blist,
-                                                                              tsc, w0, 0);
-                    NDHSS_LAUNCH_CHECK("lr_axpy_kernel");
-                }
-                continue;
-            }
-            if (F.up_cnt[l] == 0) continue;
-            upsweep_kernel<T><<<(unsigned)F.up_cnt[l], AT, smem_i, st>>>(F.d_tasks + 2 * F.up_off[l], F.d_node, F.d_foff,
-                                                                         F.d_blist, F.d_sigma, front, w0);
-            NDHSS_LAUNCH_CHECK("upsweep_kernel");
-        }
-        if (F.diag_cnt > 0) {
-            diag_kernel<T><<<(unsigned)F.diag_cnt, AT, smem_i, st>>>(F.d_tasks + 2 * F.diag_off, F.d_node, F.d_foff,
-                                                                     F.d_sigma, front, w0, w1);
-            NDHSS_LAUNCH_CHECK("diag_kernel");
-        }
-        for (int l = 0; l <= F.depth; ++l) {
-            if (l < F.L_hss && !F.lr_cnt.empty()) {
-                if (F.lr_dot_cnt[l]) {
-                    lr_dot_kernel<T><<<(unsigned)F.lr_dot_cnt[l], AT, 0, st>>>(F.d_tasks + 2 * F.lr_dot_off[l], F.d_node,
-                                                                             F.d_lr_ptr, F.d_lr_k, F.d_lr_toff, F.d_blist,
-                                                                             w1, tsc, 1);
-                    NDHSS_LAUNCH_CHECK("lr_dot_kernel");
-                    lr_axpy_kernel<T><<<(unsigned)F.lr_iax_cnt[l], AT, 0, st>>>(F.d_tasks + 2 * F.lr_iax_off[l], F.d_node,
-                                                                              F.d_lr_ptr, F.d_lr_k, F.d_lr_toff, F.d_blist,
-                                                                              tsc, w1, 1);
-                    NDHSS_LAUNCH_CHECK("lr_axpy_kernel");
-                }
-                continue;
-            }
-            if (F.dn_cnt[l] == 0) continue;
-            downsweep_kernel<T><<<(unsigned)F.dn_cnt[l], AT, smem_b, st>>>(F.d_tasks + 2 * F.dn_off[l], F.d_node, F.d_foff,
-                                                                           F.d_blist, front, w1);
-            NDHSS_LAUNCH_CHECK("downsweep_kernel");
-        }
-        scatter_cast_kernel<T, V><<<nb, 256, 0, st>>>(F.n, F.d_perm, w1, y + r * ldy);
-        NDHSS_LAUNCH_CHECK("scatter_cast_kernel");
+        NDHSS_CUDA_TRY(cudaMemsetAsync(S.ctl, 0, ctl_bytes, st));
+        apply_dataflow_kernel<T, V><<<(unsigned)F.sched_grid, AT, smem, st>>>(C, S, F.n, x + r * ldx, y + r * ldy, wy, wz,
+                                                                              tup, tdn, dpart, vlen);
+        NDHSS_LAUNCH_CHECK("apply_dataflow_kernel");
     }
+    return NDHSS_OK;
+}
+
+// Grid of the persistent launch: every SM filled to its occupancy limit.
+template <typename T, typename V>
+ndhss_status launch_shape(FactorData& F) {
+    const size_t smem = smem_bytes(F, sizeof(T));
+    if (smem > 48 * 1024) {
+        NDHSS_CUDA_TRY(cudaFuncSetAttribute(apply_dataflow_kernel<T, V>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            (int)smem));
+        NDHSS_CUDA_TRY(cudaFuncSetAttribute(apply_group_kernel<T, V>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            (int)smem));
+    }
+    int dev = 0, sms = 0, per_sm = 0;
+    NDHSS_CUDA_TRY(cudaGetDevice(&dev));
+    NDHSS_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    NDHSS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, apply_dataflow_kernel<T, V>, AT, smem));
+    if (per_sm < 1) return set_error(NDHSS_ERR_INVALID_ARG, "apply: %zu bytes of shared memory per CTA do not fit an SM", smem);
+    F.sched_grid = sms * per_sm;
     return NDHSS_OK;
 }
 
 }  // namespace
 
-// two permuted work vectors plus the low-rank scratch t (one slot per rank of every low-rank node)
-size_t apply_work_bytes(const FactorData& F) {
-    return 2 * (((size_t)F.n * F.esize + 255) / 256 * 256) + (size_t)std::max<int64_t>(F.lr_t_total, 1) * F.esize + 256;
+// Host-built task queue of the apply (see the top of this file).
+ndhss_status build_apply_schedule(FactorData& F) {
+    const int nn = F.nnodes;
+    if ((int64_t)nn >= (int64_t(1) << TK_SHIFT)) return set_error(NDHSS_ERR_INVALID_ARG, "apply: too many tree nodes");
+    std::vector<int32_t> q, need((size_t)NCNT * std::max(nn, 1), 0);
+    std::vector<int64_t> groups{0};
+    std::vector<int64_t> dpoff(std::max(nn, 1), 0);
+    auto push = [&](int kind, int s, int a, int b, bool fin) {
+        const bool lr = kind == TK_UPDOT || kind == TK_UPAXPY || kind == TK_DNDOT || kind == TK_DNAXPY;
+        const int64_t base = kind == TK_GATHER ? 0 : lr ? (int64_t)F.lr_ptr[s] : F.foff[s];
+        const int64_t aux = lr ? F.lr_toff[s] : (kind == TK_DPART || kind == TK_DSUM) ? dpoff[s] : 0;
+        const bool g = kind == TK_GATHER;
+        const int32_t w[QW] = {(fin ? TK_FINAL : 0) | (kind << TK_SHIFT) | s, a, b,
+                               g ? 0 : F.m_i(s), g ? 0 : F.m_b(s), g ? 0 : F.info(s, 4), g ? 0 : F.info(s, 6),
+                               lr ? F.lr_k[s] : 0,
+                               (int32_t)(uint32_t)(uint64_t)base, (int32_t)(uint32_t)((uint64_t)base >> 32),
+                               (int32_t)(uint32_t)(uint64_t)aux, (int32_t)(uint32_t)((uint64_t)aux >> 32)};
+        q.insert(q.end(), w, w + QW);
+    };
+    auto cut = [&]() {
+        if ((int64_t)q.size() / QW != groups.back()) groups.push_back((int64_t)q.size() / QW);
+    };
+    auto ceil_div = [](int a, int b) { return (a + b - 1) / b; };
+    // node mode: 0 dense, 1 low-rank with rank k > 0, 2 low-rank with k = 0
+    auto mode = [&](int s) {
+        if (F.lr_ptr.empty() || !F.lr_ptr[s]) return 0;
+        return F.lr_k[s] > 0 ? 1 : 2;
+    };
+    auto fused = [&](int s) { return F.m_i(s) > 0 && mode(s) == 0 && F.m_i(s) <= DIAG_COLS; };
+    // the tasks that write z(I^s) last: the diagonal step when nothing is added later
+    auto diag_final = [&](int s) { return F.m_b(s) == 0 || mode(s) == 2; };
+    F.dpart_total = 0;
+    // low-rank dot tasks: one LR_CHUNK-row chunk times one column group
+    const int dgw = (AT / 32) * (F.esize <= 8 ? 2 : 1);
+    const int ng = ceil_div(F.n, GATHER_CHUNK);
+    for (int i = 0; i < ng; ++i) push(TK_GATHER, 0, i * GATHER_CHUNK, 0, false);
+    cut();
+    for (int l = F.depth; l >= 0; --l) {
+        // fused / dense / low-rank-dot tasks of the level, then what completes each node
+        for (int s : F.levels[l]) {
+            const int mi = F.m_i(s), mb = F.m_b(s);
+            if (fused(s)) {
+                const int rows = mi + mb, cnt = ceil_div(rows, APPLY_ROWS);
+                for (int r0 = 0; r0 < rows; r0 += APPLY_ROWS) push(TK_UPDIAG, s, r0, 0, diag_final(s));
+                need[CN_UP * nn + s] = cnt;
+                need[CN_DIAG * nn + s] = cnt;
+                if (diag_final(s)) need[CN_FIN * nn + s] = cnt;
+            } else if (mi > 0 && mb > 0 && mode(s) == 0) {
+                for (int j0 = 0; j0 < mb; j0 += APPLY_ROWS) push(TK_UP, s, j0, 0, false);
+                need[CN_UP * nn + s] = ceil_div(mb, APPLY_ROWS);
+            } else if (mi > 0 && mb > 0 && mode(s) == 1) {
+                for (int r0 = 0; r0 < mi; r0 += LR_CHUNK)
+                    for (int a0 = 0; a0 < F.lr_k[s]; a0 += dgw) push(TK_UPDOT, s, r0, a0, false);
+                need[CN_DOT * nn + s] = ceil_div(mi, LR_CHUNK) * ceil_div(F.lr_k[s], dgw);
+            }
+        }
+        cut();
+        for (int s : F.levels[l]) {
+            if (fused(s) || (F.m_i(s) > 0 && F.m_b(s) > 0 && mode(s) == 0)) continue;
+            if (F.m_i(s) > 0 && F.m_b(s) > 0 && mode(s) == 1) {
+                for (int r0 = 0; r0 < F.m_b(s); r0 += APPLY_ROWS) push(TK_UPAXPY, s, r0, 0, false);
+                need[CN_UP * nn + s] = ceil_div(F.m_b(s), APPLY_ROWS);
+            } else if (F.info(s, 1) >= 0) {
+                push(TK_UPNOP, s, 0, 0, false);
+                need[CN_UP * nn + s] = 1;
+            }
+        }
+        cut();
+    }
+    // diagonal step of the nodes not fused above, deepest level first (ready
+    // early; they fill the GPU while the top levels' up-sweep chain runs):
+    // column-chunk partial products, then their sums
+    for (int l = F.depth; l >= 0; --l)
+        for (int s : F.levels[l]) {
+            const int mi = F.m_i(s);
+            if (mi == 0 || fused(s)) continue;
+            const int nch = ceil_div(mi, DIAG_COLS);
+            dpoff[s] = F.dpart_total;
+            F.dpart_total += (int64_t)nch * mi;
+            for (int c0 = 0; c0 < mi; c0 += DIAG_COLS)
+                for (int r0 = 0; r0 < mi; r0 += APPLY_ROWS) push(TK_DPART, s, r0, c0, false);
+            need[CN_DPART * nn + s] = nch * ceil_div(mi, APPLY_ROWS);
+        }
+    cut();
+    for (int l = F.depth; l >= 0; --l)
+        for (int s : F.levels[l]) {
+            const int mi = F.m_i(s);
+            if (mi == 0 || fused(s)) continue;
+            for (int r0 = 0; r0 < mi; r0 += SUM_ROWS) push(TK_DSUM, s, r0, 0, diag_final(s));
+            need[CN_DIAG * nn + s] = ceil_div(mi, SUM_ROWS);
+            if (diag_final(s)) need[CN_FIN * nn + s] = need[CN_DIAG * nn + s];
+        }
+    cut();
+    for (int l = 0; l <= F.depth; ++l) {
+        for (int s : F.levels[l]) {
+            if (F.m_i(s) == 0 || diag_final(s) || mode(s) != 1) continue;
+            for (int r0 = 0; r0 < F.m_b(s); r0 += LR_CHUNK)
+                for (int a0 = 0; a0 < F.lr_k[s]; a0 += dgw) push(TK_DNDOT, s, r0, a0, false);
+            need[CN_DDOT * nn + s] = ceil_div(F.m_b(s), LR_CHUNK) * ceil_div(F.lr_k[s], dgw);
+        }
+        cut();
+        for (int s : F.levels[l]) {
+            if (F.m_i(s) == 0) {
+                push(TK_FINNOP, s, 0, 0, false);
+                need[CN_FIN * nn + s] = 1;
+                continue;
+            }
+            if (diag_final(s)) continue;
+            if (mode(s) == 0) {
+                for (int i0 = 0; i0 < F.m_i(s); i0 += APPLY_ROWS) push(TK_DN, s, i0, 0, true);
+            } else {
+                for (int r0 = 0; r0 < F.m_i(s); r0 += APPLY_ROWS) push(TK_DNAXPY, s, r0, 0, true);
+            }
+            need[CN_FIN * nn + s] = ceil_div(F.m_i(s), APPLY_ROWS);
+        }
+        cut();
+    }
+    F.sched_n = (int64_t)q.size() / QW;
+    F.sched_ngather = ng;
+    F.sched_groups = groups;
+    F.sched_vlen = std::max(std::max(F.max_mi, F.max_mb), LR_CHUNK);
+    if (F.sched_n >= (int64_t)INT32_MAX / QW) return set_error(NDHSS_ERR_INVALID_ARG, "apply: task queue too long");
+    ndhss_status rc = NDHSS_OK;
+    auto up = [&](auto** dst, const auto& v) {
+        if (rc != NDHSS_OK) return;
+        const size_t bytes = v.size() * sizeof(v[0]);
+        if (cudaMalloc((void**)dst, std::max<size_t>(bytes, 8)) != cudaSuccess ||
+            cudaMemcpy(*dst, v.data(), bytes, cudaMemcpyHostToDevice) != cudaSuccess) {
+            cudaGetLastError();
+            rc = set_error(NDHSS_ERR_OOM, "apply: schedule tables");
+            return;
+        }
+        F.dev_bytes += (int64_t)bytes;
+    };
+    up(&F.d_sched, q);
+    up(&F.d_need, need);
+    if (rc == NDHSS_OK && (cudaMalloc(&F.d_apply_err, sizeof(int32_t)) != cudaSuccess ||
+                           cudaMemset(F.d_apply_err, 0, sizeof(int32_t)) != cudaSuccess)) {
+        cudaGetLastError();
+        rc = set_error(NDHSS_ERR_OOM, "apply: error word");
+    }
+    if (rc != NDHSS_OK) return rc;
+    const bool cplx = F.vtype == NDHSS_C128;
+    if (!cplx && F.prec == NDHSS_FP64) return launch_shape<double, double>(F);
+    if (!cplx) return launch_shape<float, double>(F);
+    if (F.prec == NDHSS_FP64) return launch_shape<c128, c128>(F);
+    return launch_shape<c64, c128>(F);
 }
+
+// Sticky failure of an earlier asynchronous apply (a bounded wait gave up).
+ndhss_status apply_check_error(const FactorData& F, const char* who) {
+    if (!F.d_apply_err) return NDHSS_OK;
+    int32_t e = 0;
+    NDHSS_CUDA_TRY(cudaMemcpy(&e, F.d_apply_err, sizeof(e), cudaMemcpyDeviceToHost));
+    if (e) return set_error(NDHSS_ERR_TIMEOUT, "%s: a wait of the persistent apply kernel gave up after %.1f s",
+                            who, APPLY_WAIT_NS * 1e-9);
+    return NDHSS_OK;
+}
+
+size_t apply_work_bytes(const FactorData& F) { return work_layout(F).total; }
 
 ndhss_status apply_device(const FactorData& F, int32_t nrhs, const void* d_x, int64_t ldx, void* d_y, int64_t ldy,
                           void* d_work, cudaStream_t st) {
     const bool cplx = F.vtype == NDHSS_C128;
     unsigned char* w = static_cast<unsigned char*>(d_work);
-    const size_t half = ((size_t)F.n * F.esize + 255) / 256 * 256;
     if (!cplx && F.prec == NDHSS_FP64)
-        return apply_run<double, double>(F, nrhs, (const double*)d_x, ldx, (double*)d_y, ldy, (double*)w, (double*)(w + half), st);
+        return apply_run<double, double>(F, nrhs, (const double*)d_x, ldx, (double*)d_y, ldy, w, st);
     if (!cplx)
-        return apply_run<float, double>(F, nrhs, (const double*)d_x, ldx, (double*)d_y, ldy, (float*)w, (float*)(w + half), st);
+        return apply_run<float, double>(F, nrhs, (const double*)d_x, ldx, (double*)d_y, ldy, w, st);
     if (F.prec == NDHSS_FP64)
-        return apply_run<c128, c128>(F, nrhs, (const c128*)d_x, ldx, (c128*)d_y, ldy, (c128*)w, (c128*)(w + half), st);
-    return apply_run<c64, c128>(F, nrhs, (const c128*)d_x, ldx, (c128*)d_y, ldy, (c64*)w, (c64*)(w + half), st);
+        return apply_run<c128, c128>(F, nrhs, (const c128*)d_x, ldx, (c128*)d_y, ldy, w, st);
+    return apply_run<c64, c128>(F, nrhs, (const c128*)d_x, ldx, (c128*)d_y, ldy, w, st);
 }
 
 }  // namespace ndhss
@@ -360,6 +947,7 @@ extern "C" ndhss_status ndhss_apply(const ndhss_factorization* fh, int32_t nrhs,
     if (!xdev || !ydev) {
         if (cudaStreamSynchronize(st) != cudaSuccess && rc == NDHSS_OK)
             rc = set_error(NDHSS_ERR_CUDA, "ndhss_apply: stream synchronisation failed");
+        if (rc == NDHSS_OK) rc = apply_check_error(F, "ndhss_apply");
     }
     return rc;
 }
@@ -373,10 +961,11 @@ extern "C" ndhss_status ndhss_apply(const ndhss_factorization* fh, int32_t nrhs,
 // allocations.  The array is part of the module image, so every device that
 // loads the library holds it until exit.  Host code must not take its address
 // directly (that would be a host-side shadow): the device address is looked
-// up once per device with cudaGetSymbolAddress.  Every call overwrites the
-// whole work area it uses before reading it (gather writes all of the first
-// vector, the diagonal step all of the second), so nothing needs clearing;
-// overlapping calls race on the array.
+// up once per device with cudaGetSymbolAddress.  Every call writes the work
+// area before reading it (the gather all of the first vector, the diagonal
+// step all of the second, an asynchronous memset the queue's control words),
+// so nothing needs clearing between calls; overlapping calls race on the
+// array.
 namespace ndhss {
 namespace {
 
@@ -425,4 +1014,20 @@ extern "C" ndhss_status ndhss_apply_noalloc(const ndhss_factorization* fh, const
     const ndhss_status rc = scratch_for_current_device(&scratch);
     if (rc != NDHSS_OK) return rc;
     return apply_device(F, 1, d_x, F.n, d_y, F.n, scratch, static_cast<cudaStream_t>(stream));
+}
+
+// Failure-detection hook: one requirement that no task will ever satisfy.
+extern "C" ndhss_status ndhss_testing_stall_apply(ndhss_factorization* fh) {
+    using namespace ndhss;
+    clear_error();
+    if (!fh || !fh->f.d_need || fh->f.levels.empty() || fh->f.levels[0].empty())
+        return set_error(NDHSS_ERR_INVALID_ARG, "ndhss_testing_stall_apply: no dataflow queue");
+    FactorData& F = fh->f;
+    const int root = F.levels[0][0];
+    int32_t* p = F.d_need + (size_t)CN_FIN * F.nnodes + root;
+    int32_t v = 0;
+    NDHSS_CUDA_TRY(cudaMemcpy(&v, p, sizeof(v), cudaMemcpyDeviceToHost));
+    ++v;
+    NDHSS_CUDA_TRY(cudaMemcpy(p, &v, sizeof(v), cudaMemcpyHostToDevice));
+    return NDHSS_OK;
 }

@@ -625,30 +625,6 @@ static ndhss_status factor_impl(const ndhss_tree* th, int32_t vtype, const int32
         lmax = std::max<int64_t>(lmax, (int64_t)F.levels[l].size());
     }
     lev_off[t.depth + 1] = (int64_t)lev_flat.size();
-    // apply task lists
-    std::vector<int32_t> tasks;
-    F.up_off.assign(t.depth + 1, 0);
-    F.up_cnt.assign(t.depth + 1, 0);
-    F.dn_off.assign(t.depth + 1, 0);
-    F.dn_cnt.assign(t.depth + 1, 0);
-    for (int l = 0; l <= t.depth; ++l) {
-        F.up_off[l] = (int64_t)tasks.size() / 2;
-        for (int s : F.levels[l])
-            if (t.m_i(s) > 0)
-                for (int j0 = 0; j0 < t.m_b(s); j0 += APPLY_ROWS) { tasks.push_back(s); tasks.push_back(j0); }
-        F.up_cnt[l] = (int64_t)tasks.size() / 2 - F.up_off[l];
-    }
-    F.diag_off = (int64_t)tasks.size() / 2;
-    for (int s = 0; s < t.nnodes; ++s)
-        for (int i0 = 0; i0 < t.m_i(s); i0 += APPLY_ROWS) { tasks.push_back(s); tasks.push_back(i0); }
-    F.diag_cnt = (int64_t)tasks.size() / 2 - F.diag_off;
-    for (int l = 0; l <= t.depth; ++l) {
-        F.dn_off[l] = (int64_t)tasks.size() / 2;
-        for (int s : F.levels[l])
-            if (t.m_b(s) > 0)
-                for (int i0 = 0; i0 < t.m_i(s); i0 += APPLY_ROWS) { tasks.push_back(s); tasks.push_back(i0); }
-        F.dn_cnt[l] = (int64_t)tasks.size() / 2 - F.dn_off[l];
-    }
     int64_t apply_elems = 0;
     for (int s = 0; s < t.nnodes; ++s)
         apply_elems += (int64_t)t.m_i(s) * t.m_i(s) + 2 * (int64_t)t.m_i(s) * t.m_b(s);
@@ -674,7 +650,6 @@ static ndhss_status factor_impl(const ndhss_tree* th, int32_t vtype, const int32
     UP(F.d_foff, F.foff);
     UP(F.d_blist, t.blist);
     UP(F.d_perm, t.perm);
-    UP(F.d_tasks, tasks);
     UPT(d_eoff, t.e_off);
     UPT(d_erow, t.e_row);
     UPT(d_ecol, t.e_col);
@@ -761,39 +736,23 @@ static ndhss_status factor_impl(const ndhss_tree* th, int32_t vtype, const int32
                 if (F.lr_ptr[s] && F.lr_k[s] > 0) lst.push_back(s);
             F.lr_cnt[l] = (int64_t)lst.size() - F.lr_off_l[l];
         }
-        // low-rank apply task lists, appended to the existing task array
-        std::vector<int32_t> tasks2(tasks);
-        std::vector<int64_t> toff(t.nnodes, 0);
+        // each low-rank node's slot for the apply's per-chunk partial products
+        std::vector<int64_t>& toff = F.lr_toff;
+        toff.assign(t.nnodes, 0);
         F.lr_t_total = 0;
         for (int s = 0; s < t.nnodes; ++s)
-            if (F.lr_ptr[s] && F.lr_k[s] > 0) { toff[s] = F.lr_t_total; F.lr_t_total += F.lr_k[s]; }
-        auto push_list = [&](std::vector<int64_t>& off, std::vector<int64_t>& cnt, int l, int step, bool over_k,
-                             bool over_b) {
-            off[l] = (int64_t)tasks2.size() / 2;
-            for (int s : F.levels[l]) {
-                if (!(F.lr_ptr[s] && F.lr_k[s] > 0)) continue;
-                const int len = over_k ? F.lr_k[s] : (over_b ? t.m_b(s) : t.m_i(s));
-                for (int r0 = 0; r0 < len; r0 += step) { tasks2.push_back(s); tasks2.push_back(r0); }
+            if (F.lr_ptr[s] && F.lr_k[s] > 0) {
+                const int64_t nch = (std::max(t.m_i(s), t.m_b(s)) + LR_CHUNK - 1) / LR_CHUNK;
+                toff[s] = F.lr_t_total;
+                F.lr_t_total += nch * F.lr_k[s];
             }
-            cnt[l] = (int64_t)tasks2.size() / 2 - off[l];
-        };
-        for (auto* v : {&F.lr_dot_off, &F.lr_dot_cnt, &F.lr_bax_off, &F.lr_bax_cnt, &F.lr_iax_off, &F.lr_iax_cnt})
-            v->assign(t.depth + 1, 0);
-        for (int l = 0; l <= t.depth; ++l) {
-            push_list(F.lr_dot_off, F.lr_dot_cnt, l, 8, true, false);
-            push_list(F.lr_bax_off, F.lr_bax_cnt, l, 256, false, true);
-            push_list(F.lr_iax_off, F.lr_iax_cnt, l, 256, false, false);
-        }
-        cudaFree(F.d_tasks);
-        F.d_tasks = nullptr;
         if (upload(&F.d_lr_ptr, F.lr_ptr.data(), F.lr_ptr.size(), &F.dev_bytes) != NDHSS_OK ||
             upload(&F.d_lr_k, F.lr_k.data(), F.lr_k.size(), &F.dev_bytes) != NDHSS_OK ||
-            upload(&F.d_lr_list, lst.data(), lst.size(), &F.dev_bytes) != NDHSS_OK ||
-            upload(&F.d_lr_toff, toff.data(), toff.size(), &F.dev_bytes) != NDHSS_OK ||
-            upload(&F.d_tasks, tasks2.data(), tasks2.size(), &F.dev_bytes) != NDHSS_OK)
+            upload(&F.d_lr_list, lst.data(), lst.size(), &F.dev_bytes) != NDHSS_OK)
             rc = set_error(NDHSS_ERR_OOM, "ndhss_factor: low-rank tables");
     }
     cleanup();
+    if (rc == NDHSS_OK) rc = build_apply_schedule(F);
     if (rc != NDHSS_OK) {
         cudaStreamSynchronize(st);
         ndhss_factor_destroy(h);
@@ -953,11 +912,12 @@ void ndhss_factor_destroy(ndhss_factorization* fh) {
     cudaFree(F.d_sigma);
     cudaFree(F.d_ipiv);
     cudaFree(F.d_front);
-    cudaFree(F.d_tasks);
     cudaFree(F.d_lr_ptr);
     cudaFree(F.d_lr_k);
     cudaFree(F.d_lr_list);
-    cudaFree(F.d_lr_toff);
+    cudaFree(F.d_sched);
+    cudaFree(F.d_need);
+    cudaFree(F.d_apply_err);
     for (void* b : F.lr_bufs) cudaFree(b);
     delete fh;
 }

@@ -35,12 +35,21 @@ struct FactorData {
     int32_t* d_ipiv = nullptr;                // [n]
     void* d_front = nullptr;
 
-    // apply work lists: pairs (node, first row) of 64-row tasks
-    int32_t* d_tasks = nullptr;
-    std::vector<int64_t> up_off, up_cnt;      // per level
-    std::vector<int64_t> dn_off, dn_cnt;      // per level
-    int64_t diag_off = 0, diag_cnt = 0;
     int32_t max_mi = 0, max_mb = 0;
+
+    // task queue of the apply (apply.cu): entries (flags | kind | node, a, b),
+    // its dependency groups (level schedule), per-node completion requirements
+    // [6][nnodes], slots of the diagonal partial products, and a sticky error
+    // word set when a bounded wait of the persistent kernel gives up
+    int32_t* d_sched = nullptr;                 // [QW * sched_n], 16-byte aligned entries
+    int64_t sched_n = 0;
+    std::vector<int64_t> sched_groups;
+    int32_t sched_ngather = 0;
+    int32_t sched_grid = 0;
+    int32_t sched_vlen = 0;
+    int32_t* d_need = nullptr;
+    int64_t dpart_total = 0;
+    int32_t* d_apply_err = nullptr;
 
     // compressed tier (Alg. 3.4 above the switching level): low-rank R ~ X R(J, :)
     // per node: X (m_i x k, ld m_i) followed by RJ (k x m_b, ld k), in one
@@ -53,10 +62,9 @@ struct FactorData {
     int32_t* d_lr_k = nullptr;
     int32_t* d_lr_list = nullptr;             // low-rank nodes grouped by level
     std::vector<int64_t> lr_off_l, lr_cnt;    // per level
-    // low-rank apply tasks (pairs in d_tasks): dot (node, first output), up-axpy over
-    // B rows, down-axpy over I rows; and the scratch offset of each node's t
-    std::vector<int64_t> lr_dot_off, lr_dot_cnt, lr_bax_off, lr_bax_cnt, lr_iax_off, lr_iax_cnt;
-    int64_t* d_lr_toff = nullptr;
+    // each low-rank node's slot for the apply's per-chunk partial products
+    // (ceil(max(m_i, m_b) / LR_CHUNK) x k values)
+    std::vector<int64_t> lr_toff;
     int64_t lr_t_total = 0;
     int32_t kmax = 0;
     int32_t hss_rounds_max = 0;
@@ -76,6 +84,7 @@ struct FactorData {
 };
 
 constexpr int APPLY_ROWS = 64;   // rows per apply task
+constexpr int LR_CHUNK = 256;    // input rows per low-rank dot task
 
 // Compress the Schur complements (and, strictly above the switching level,
 // the Gauss transforms R) of the fronts on tree level `level`, which have
@@ -86,6 +95,11 @@ ndhss_status hss_compress_level(FactorData& F, const Tree& t, int level, const n
 ndhss_status apply_device(const FactorData& F, int32_t nrhs, const void* d_x, int64_t ldx,
                           void* d_y, int64_t ldy, void* d_work, cudaStream_t st);
 size_t apply_work_bytes(const FactorData& F);
+// Builds and uploads the dataflow queue once the factor (and its low-rank
+// tier) is complete; defined in apply.cu.
+ndhss_status build_apply_schedule(FactorData& F);
+// NDHSS_ERR_TIMEOUT if an earlier apply of this factorization gave up a wait.
+ndhss_status apply_check_error(const FactorData& F, const char* who);
 
 }  // namespace ndhss
 

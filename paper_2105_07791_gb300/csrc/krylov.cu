@@ -122,10 +122,13 @@ mdot_kernel(int n, const V* __restrict__ Vb, int64_t ldv, int k, const V* __rest
     if (threadIdx.x == 0) s_last = (atomicAdd(counter, 1u) == gridDim.x - 1);
     __syncthreads();
     if (s_last) {
-        if (threadIdx.x < k) {
+        // warp w reduces outputs w, w + 8, ...: lanes take fixed block strides, then a
+        // fixed shuffle tree, so the result does not depend on block completion order
+        for (int i = warp; i < k; i += RT / 32) {
             V sum = zero<V>();
-            for (unsigned b = 0; b < gridDim.x; ++b) sum += ldcg(partial + b * KMAX + threadIdx.x);
-            out[threadIdx.x] = sum;
+            for (unsigned b = lane; b < gridDim.x; b += 32) sum += ldcg(partial + b * KMAX + i);
+            sum = warp_sum(sum);
+            if (lane == 0) out[i] = sum;
         }
         if (threadIdx.x == 0) *counter = 0;
     }
@@ -151,11 +154,14 @@ nrm2_kernel(int n, const V* __restrict__ w, double* __restrict__ partial, double
     __threadfence();
     if (threadIdx.x == 0) s_last = (atomicAdd(counter, 1u) == gridDim.x - 1);
     __syncthreads();
-    if (s_last && threadIdx.x == 0) {
+    if (s_last && threadIdx.x < 32) {
         double s = 0.0;
-        for (unsigned b = 0; b < gridDim.x; ++b) s += __ldcg(partial + b);
-        *out = s;
-        *counter = 0;
+        for (unsigned b = threadIdx.x; b < gridDim.x; b += 32) s += __ldcg(partial + b);
+        s = warp_sum(s);
+        if (threadIdx.x == 0) {
+            *out = s;
+            *counter = 0;
+        }
     }
 }
 
@@ -512,6 +518,7 @@ ndhss_status ndhss_gmres(const ndhss_factorization* fh, const int32_t* d_rowptr,
     cudaFreeAsync(work, st);
     if (cudaStreamSynchronize(st) != cudaSuccess && rc == NDHSS_OK)
         rc = set_error(NDHSS_ERR_CUDA, "ndhss_gmres: stream synchronisation failed");
+    if (rc == NDHSS_OK) rc = apply_check_error(F, "ndhss_gmres");
     if (rc == NDHSS_OK && any_fail)
         rc = set_error(NDHSS_ERR_NOT_CONVERGED, "ndhss_gmres: tolerance not reached within maxit");
     return rc;

@@ -24,7 +24,8 @@ STATUS = {0: "OK", 1: "INVALID_ARG", 2: "OOM", 3: "SINGULAR", 4: "RANK_CAP", 5: 
 
 EXPORTED = ("ndhss_version", "ndhss_last_error", "ndhss_kernel_launches", "ndhss_build_tree", "ndhss_tree_sizes", "ndhss_tree_export",
             "ndhss_tree_destroy", "ndhss_factor", "ndhss_factor_stats_get", "ndhss_factor_get_block",
-            "ndhss_factor_destroy", "ndhss_apply", "ndhss_apply_noalloc", "ndhss_spmv", "ndhss_gmres")
+            "ndhss_factor_destroy", "ndhss_apply", "ndhss_apply_noalloc", "ndhss_spmv", "ndhss_gmres",
+            "ndhss_testing_stall_apply")
 
 
 class NdhssError(RuntimeError):
@@ -97,6 +98,7 @@ def load(path: str | None = None):
         "ndhss_factor_destroy": (None, [P]),
         "ndhss_apply": (I32, [P, I32, P, I64, P, I64, V]),
         "ndhss_apply_noalloc": (I32, [P, P, P, V]),
+        "ndhss_testing_stall_apply": (I32, [P]),
         "ndhss_spmv": (I32, [I32, I32, P, P, P, P, P, V]),
         "ndhss_gmres": (I32, [P, P, P, P, I32, P, I64, P, I64, C.POINTER(GmresOpts), C.POINTER(GmresStats), V]),
     }
@@ -226,15 +228,30 @@ def ndhss_apply(f: Factor, x, y, stream=None):
     n = f.n
     nrhs = 1 if x.ndim == 1 else x.shape[1]
     if x.ndim == 2:
-        raise ValueError("pass one right-hand side per call or a Fortran-ordered block via ndhss_apply_block")
+        raise ValueError("pass one right-hand side per call, or several as rows of a block via ndhss_apply_block")
     _check(load().ndhss_apply(f.handle, nrhs, _ptr(x), n, _ptr(y), n, _stream(stream)))
     return y
+
+
+def ndhss_apply_block(f: Factor, X, Y, stream=None):
+    """Y[j] = P^{-1} X[j] for the rows j of contiguous (nrhs, n) blocks, i.e.
+    column-major n x nrhs with leading dimension n (one C-ABI call)."""
+    n = f.n
+    if X.ndim != 2 or X.shape[1] != n or tuple(Y.shape) != tuple(X.shape):
+        raise ValueError("X and Y must both have shape (nrhs, n)")
+    _check(load().ndhss_apply(f.handle, int(X.shape[0]), _ptr(X), n, _ptr(Y), n, _stream(stream)))
+    return Y
 
 
 def ndhss_apply_noalloc(f: Factor, d_x, d_y, stream=None):
     """y = P^{-1} x without any allocation (device tensors of n values; see include/ndhss.h)."""
     _check(load().ndhss_apply_noalloc(f.handle, _ptr(d_x), _ptr(d_y), _stream(stream)))
     return d_y
+
+
+def ndhss_testing_stall_apply(f: Factor):
+    """Failure-detection hook: makes the next apply's bounded waits run out."""
+    _check(load().ndhss_testing_stall_apply(f.handle))
 
 
 def ndhss_spmv(n: int, vtype: int, d_rowptr, d_col, d_vals, d_x, d_y, stream=None):
