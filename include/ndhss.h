@@ -207,6 +207,14 @@ ndhss_status ndhss_factor_stats_get(const ndhss_factorization* f, ndhss_factor_s
 ndhss_status ndhss_factor_get_block(const ndhss_factorization* f, int32_t node, int32_t which,
                                     void* host_out, int64_t ld);
 
+/*
+ * ndhss_factor_destroy -- release a factorization (NULL is ignored).  Waits
+ * for all work on the device first, since any stream may still read it.
+ * Device memory of the library (factor storage and per-call work space)
+ * comes from one stream-ordered pool per device that keeps freed memory
+ * cached for the next call rather than returning it to the driver; it is
+ * released when the process exits.
+ */
 void ndhss_factor_destroy(ndhss_factorization* f);
 
 /*

@@ -729,7 +729,7 @@ ndhss_status launch_shape(FactorData& F) {
 }  // namespace
 
 // Host-built task queue of the apply (see the top of this file).
-ndhss_status build_apply_schedule(FactorData& F) {
+ndhss_status build_apply_schedule(FactorData& F, cudaStream_t st) {
     const int nn = F.nnodes;
     if ((int64_t)nn >= (int64_t(1) << TK_SHIFT)) return set_error(NDHSS_ERR_INVALID_ARG, "apply: too many tree nodes");
     std::vector<int32_t> q, need((size_t)NCNT * std::max(nn, 1), 0);
@@ -854,8 +854,8 @@ ndhss_status build_apply_schedule(FactorData& F) {
     auto up = [&](auto** dst, const auto& v) {
         if (rc != NDHSS_OK) return;
         const size_t bytes = v.size() * sizeof(v[0]);
-        if (cudaMalloc((void**)dst, std::max<size_t>(bytes, 8)) != cudaSuccess ||
-            cudaMemcpy(*dst, v.data(), bytes, cudaMemcpyHostToDevice) != cudaSuccess) {
+        if (pool_malloc_async((void**)dst, std::max<size_t>(bytes, 8), st) != cudaSuccess ||
+            cudaMemcpyAsync(*dst, v.data(), bytes, cudaMemcpyHostToDevice, st) != cudaSuccess) {
             cudaGetLastError();
             rc = set_error(NDHSS_ERR_OOM, "apply: schedule tables");
             return;
@@ -864,8 +864,8 @@ ndhss_status build_apply_schedule(FactorData& F) {
     };
     up(&F.d_sched, q);
     up(&F.d_need, need);
-    if (rc == NDHSS_OK && (cudaMalloc(&F.d_apply_err, sizeof(int32_t)) != cudaSuccess ||
-                           cudaMemset(F.d_apply_err, 0, sizeof(int32_t)) != cudaSuccess)) {
+    if (rc == NDHSS_OK && (pool_malloc_async((void**)&F.d_apply_err, sizeof(int32_t), st) != cudaSuccess ||
+                           cudaMemsetAsync(F.d_apply_err, 0, sizeof(int32_t), st) != cudaSuccess)) {
         cudaGetLastError();
         rc = set_error(NDHSS_ERR_OOM, "apply: error word");
     }
@@ -917,7 +917,7 @@ extern "C" ndhss_status ndhss_apply(const ndhss_factorization* fh, int32_t nrhs,
     const bool xdev = is_device_ptr(x), ydev = is_device_ptr(y);
     const size_t wb = apply_work_bytes(F) + (xdev ? 0 : (size_t)F.n * nrhs * vsz + 256) + (ydev ? 0 : (size_t)F.n * nrhs * vsz + 256);
     void* work = nullptr;
-    NDHSS_CUDA_TRY(cudaMallocAsync(&work, wb, st));
+    NDHSS_CUDA_TRY(pool_malloc_async(&work, wb, st));
     unsigned char* p = static_cast<unsigned char*>(work) + (apply_work_bytes(F) + 255) / 256 * 256;
     const void* dx = x;
     void* dy = y;

@@ -9,6 +9,10 @@
 
 namespace ndhss {
 
+// Stream-ordered allocation from the library's per-device pool (freed memory
+// stays cached between calls); release with cudaFreeAsync.  mempool.cpp.
+cudaError_t pool_malloc_async(void** p, size_t bytes, cudaStream_t st);
+
 // Interleaved complex number (re = x, im = y), layout-compatible with
 // std::complex / numpy complex64 and complex128.
 template <typename R>

@@ -407,21 +407,19 @@ ndhss_status set_smem_attrs() {
     return NDHSS_OK;
 }
 
-struct DevBuf {
-    void* p = nullptr;
-    ~DevBuf() { if (p) cudaFree(p); }
-};
-
+// Device copy of a host table, stream-ordered on st from the library pool
+// (the pageable source may be released once this returns).
 template <typename U>
-ndhss_status upload(U** dst, const U* src, size_t count, int64_t* acc) {
+ndhss_status upload(U** dst, const U* src, size_t count, int64_t* acc, cudaStream_t st) {
     *dst = nullptr;
     size_t bytes = std::max<size_t>(count, 1) * sizeof(U);
-    if (cudaMalloc((void**)dst, bytes) != cudaSuccess) {
+    if (pool_malloc_async((void**)dst, bytes, st) != cudaSuccess) {
         cudaGetLastError();
+        *dst = nullptr;
         return set_error(NDHSS_ERR_OOM, "device allocation of %zu bytes failed", bytes);
     }
     *acc += (int64_t)bytes;
-    if (count) NDHSS_CUDA_TRY(cudaMemcpy(*dst, src, count * sizeof(U), cudaMemcpyHostToDevice));
+    if (count) NDHSS_CUDA_TRY(cudaMemcpyAsync(*dst, src, count * sizeof(U), cudaMemcpyHostToDevice, st));
     return NDHSS_OK;
 }
 
@@ -639,13 +637,14 @@ static ndhss_status factor_impl(const ndhss_tree* th, int32_t vtype, const int32
     int64_t tmp_bytes = 0;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     auto cleanup = [&]() {
-        cudaFree(d_eoff); cudaFree(d_erow); cudaFree(d_ecol); cudaFree(d_eidx); cudaFree(d_fsrc); cudaFree(d_lev);
-        cudaFree(d_poff); cudaFree(d_woff); cudaFree(d_cbuf); cudaFree(d_zbuf); cudaFree(d_ainv); cudaFree(d_swapmap); cudaFree(d_status);
+        for (void* q : {(void*)d_eoff, (void*)d_erow, (void*)d_ecol, (void*)d_eidx, (void*)d_fsrc, (void*)d_lev,
+                        (void*)d_poff, (void*)d_woff, d_cbuf, d_zbuf, d_ainv, (void*)d_swapmap, (void*)d_status})
+            if (q) cudaFreeAsync(q, st);
         if (e0) cudaEventDestroy(e0);
         if (e1) cudaEventDestroy(e1);
     };
-#define UP(dst, vec) do { rc = upload(&dst, (vec).data(), (vec).size(), &F.dev_bytes); if (rc) { cleanup(); ndhss_factor_destroy(h); return rc; } } while (0)
-#define UPT(dst, vec) do { rc = upload(&dst, (vec).data(), (vec).size(), &tmp_bytes); if (rc) { cleanup(); ndhss_factor_destroy(h); return rc; } } while (0)
+#define UP(dst, vec) do { rc = upload(&dst, (vec).data(), (vec).size(), &F.dev_bytes, st); if (rc) { cleanup(); ndhss_factor_destroy(h); return rc; } } while (0)
+#define UPT(dst, vec) do { rc = upload(&dst, (vec).data(), (vec).size(), &tmp_bytes, st); if (rc) { cleanup(); ndhss_factor_destroy(h); return rc; } } while (0)
     UP(F.d_node, t.node_info);
     UP(F.d_foff, F.foff);
     UP(F.d_blist, t.blist);
@@ -661,7 +660,7 @@ static ndhss_status factor_impl(const ndhss_tree* th, int32_t vtype, const int32
 #undef UP
 #undef UPT
     auto dalloc = [&](void** p, size_t bytes, int64_t* accb) -> bool {
-        if (cudaMalloc(p, std::max<size_t>(bytes, 16)) != cudaSuccess) {
+        if (pool_malloc_async(p, std::max<size_t>(bytes, 16), st) != cudaSuccess) {
             cudaGetLastError();
             *p = nullptr;
             return false;
@@ -746,13 +745,13 @@ static ndhss_status factor_impl(const ndhss_tree* th, int32_t vtype, const int32
                 toff[s] = F.lr_t_total;
                 F.lr_t_total += nch * F.lr_k[s];
             }
-        if (upload(&F.d_lr_ptr, F.lr_ptr.data(), F.lr_ptr.size(), &F.dev_bytes) != NDHSS_OK ||
-            upload(&F.d_lr_k, F.lr_k.data(), F.lr_k.size(), &F.dev_bytes) != NDHSS_OK ||
-            upload(&F.d_lr_list, lst.data(), lst.size(), &F.dev_bytes) != NDHSS_OK)
+        if (upload(&F.d_lr_ptr, F.lr_ptr.data(), F.lr_ptr.size(), &F.dev_bytes, st) != NDHSS_OK ||
+            upload(&F.d_lr_k, F.lr_k.data(), F.lr_k.size(), &F.dev_bytes, st) != NDHSS_OK ||
+            upload(&F.d_lr_list, lst.data(), lst.size(), &F.dev_bytes, st) != NDHSS_OK)
             rc = set_error(NDHSS_ERR_OOM, "ndhss_factor: low-rank tables");
     }
     cleanup();
-    if (rc == NDHSS_OK) rc = build_apply_schedule(F);
+    if (rc == NDHSS_OK) rc = build_apply_schedule(F, st);
     if (rc != NDHSS_OK) {
         cudaStreamSynchronize(st);
         ndhss_factor_destroy(h);
@@ -905,20 +904,16 @@ ndhss_status ndhss_factor_stats_get(const ndhss_factorization* fh, ndhss_factor_
 void ndhss_factor_destroy(ndhss_factorization* fh) {
     if (!fh) return;
     auto& F = fh->f;
-    cudaFree(F.d_node);
-    cudaFree(F.d_foff);
-    cudaFree(F.d_blist);
-    cudaFree(F.d_perm);
-    cudaFree(F.d_sigma);
-    cudaFree(F.d_ipiv);
-    cudaFree(F.d_front);
-    cudaFree(F.d_lr_ptr);
-    cudaFree(F.d_lr_k);
-    cudaFree(F.d_lr_list);
-    cudaFree(F.d_sched);
-    cudaFree(F.d_need);
-    cudaFree(F.d_apply_err);
-    for (void* b : F.lr_bufs) cudaFree(b);
+    // everything below came from the library's stream-ordered pool; work on
+    // any stream may still read it, so wait for the device first
+    cudaDeviceSynchronize();
+    for (void* p : {(void*)F.d_node, (void*)F.d_foff, (void*)F.d_blist, (void*)F.d_perm, (void*)F.d_sigma,
+                    (void*)F.d_ipiv, F.d_front, (void*)F.d_lr_ptr, (void*)F.d_lr_k, (void*)F.d_lr_list, (void*)F.d_sched,
+                    (void*)F.d_need, (void*)F.d_apply_err})
+        if (p) cudaFreeAsync(p, 0);
+    for (void* b : F.lr_bufs)
+        if (b) cudaFreeAsync(b, 0);
+    cudaStreamSynchronize(0);
     delete fh;
 }
 

@@ -97,7 +97,7 @@ ndhss_status apply_device(const FactorData& F, int32_t nrhs, const void* d_x, in
 size_t apply_work_bytes(const FactorData& F);
 // Builds and uploads the dataflow queue once the factor (and its low-rank
 // tier) is complete; defined in apply.cu.
-ndhss_status build_apply_schedule(FactorData& F);
+ndhss_status build_apply_schedule(FactorData& F, cudaStream_t st);
 // NDHSS_ERR_TIMEOUT if an earlier apply of this factorization gave up a wait.
 ndhss_status apply_check_error(const FactorData& F, const char* who);
 

@@ -765,7 +765,7 @@ struct DeviceVec {
         if (p) cudaFreeAsync(p, st);
         p = nullptr;
         n = count;
-        return cudaMallocAsync((void**)&p, std::max<size_t>(n, 1) * sizeof(U), st);
+        return pool_malloc_async((void**)&p, std::max<size_t>(n, 1) * sizeof(U), st);
     }
     cudaError_t upload(const std::vector<U>& v, cudaStream_t s) {
         st = s;
@@ -1257,7 +1257,7 @@ ndhss_status compress_level_impl(FactorData& F, const Tree& t, int level, const 
         size_t tot = 0;
         for (auto& v : lr) tot += v.size();
         void* buf = nullptr;
-        if (cudaMalloc(&buf, std::max<size_t>(tot, 1) * sizeof(T)) != cudaSuccess) {
+        if (pool_malloc_async(&buf, std::max<size_t>(tot, 1) * sizeof(T), st) != cudaSuccess) {
             cudaGetLastError();
             return set_error(NDHSS_ERR_OOM, "hss: low-rank storage of level %d", level);
         }

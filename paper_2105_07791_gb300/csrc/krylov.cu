@@ -55,15 +55,31 @@ __device__ __forceinline__ c128 cdiv(c128 a, c128 b) { return a * recip(b); }
 __device__ __forceinline__ double cdiv(double a, double b) { return a / b; }
 
 // ----------------------------------------------------------------- SpMV
-template <typename V, int TPR>
-__global__ void spmv_kernel(int n, const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col,
-                            const V* __restrict__ vals, const V* __restrict__ x, V* __restrict__ y) {
+// TPR threads per row; each issues all U of its column indices and values
+// at once, then the U gathers of x, so a row costs three dependent memory
+// round trips (row pointers, entries, x) instead of two per entry.
+template <typename V, int TPR, int U>
+__global__ void __launch_bounds__(256) spmv_kernel(int n, const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+                                                   const V* __restrict__ vals, const V* __restrict__ x, V* __restrict__ y) {
     const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t row = gt / TPR;
     const int lane = (int)(gt % TPR);
     if (row >= n) return;               // whole TPR groups leave together
+    const int k0 = rowptr[row], k1 = rowptr[row + 1];
     V acc = zero<V>();
-    for (int k = rowptr[row] + lane; k < rowptr[row + 1]; k += TPR) acc = fmac(vals[k], x[col[k]], acc);
+    for (int base = k0; base < k1; base += U * TPR) {
+        int c[U];
+        V a[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int k = base + lane + u * TPR;
+            c[u] = k < k1 ? col[k] : -1;
+            a[u] = k < k1 ? vals[k] : zero<V>();
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+            if (c[u] >= 0) acc = fmac(a[u], x[c[u]], acc);
+    }
     if constexpr (sizeof(V) == 8) {
         for (int o = TPR / 2; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o, TPR);
     } else {
@@ -76,59 +92,54 @@ __global__ void spmv_kernel(int n, const int32_t* __restrict__ rowptr, const int
 }
 
 template <typename V>
-ndhss_status spmv_launch(int n, int64_t nnz, const int32_t* rowptr, const int32_t* col, const V* vals, const V* x, V* y,
+ndhss_status spmv_launch(int n, const int32_t* rowptr, const int32_t* col, const V* vals, const V* x, V* y,
                          cudaStream_t st) {
-    const int tpr = (nnz > 8LL * n) ? 8 : 4;
-    const int64_t threads = (int64_t)n * tpr;
+    const int64_t threads = (int64_t)n * 4;
     const unsigned blocks = (unsigned)((threads + 255) / 256);
-    if (tpr == 8) spmv_kernel<V, 8><<<blocks, 256, 0, st>>>(n, rowptr, col, vals, x, y);
-    else spmv_kernel<V, 4><<<blocks, 256, 0, st>>>(n, rowptr, col, vals, x, y);
+    spmv_kernel<V, 4, 4><<<blocks, 256, 0, st>>>(n, rowptr, col, vals, x, y);
     NDHSS_LAUNCH_CHECK("spmv_kernel");
     return NDHSS_OK;
 }
 
 // ---------------------------------------------------------- reductions
-// out[i] = sum_rows conj(Vb(row, i)) * w(row), i < k
+// out[i] = sum_rows conj(Vb(row, i)) * w(row), i < k.  Grid (RB, k): block
+// (b, i) sums its grid-stride rows of column i into partial[i * RB + b]; the
+// last block to finish adds each column's partials with one warp in a fixed
+// order.
 template <typename V>
 __global__ void __launch_bounds__(RT)
 mdot_kernel(int n, const V* __restrict__ Vb, int64_t ldv, int k, const V* __restrict__ w, V* __restrict__ partial,
             V* __restrict__ out, unsigned* __restrict__ counter) {
-    __shared__ V sred[KMAX][RT / 32];
+    __shared__ V sred[RT / 32];
     __shared__ bool s_last;
-    V acc[KMAX];
-#pragma unroll
-    for (int i = 0; i < KMAX; ++i) acc[i] = zero<V>();
-    for (int64_t row = (int64_t)blockIdx.x * RT + threadIdx.x; row < n; row += (int64_t)gridDim.x * RT) {
-        const V wv = w[row];
-#pragma unroll
-        for (int i = 0; i < KMAX; ++i)
-            if (i < k) acc[i] = fmac(conjv(Vb[row + i * ldv]), wv, acc[i]);
+    const int i = blockIdx.y;
+    const V* v = Vb + (int64_t)i * ldv;
+    V acc0 = zero<V>(), acc1 = zero<V>();
+    const int64_t stride = (int64_t)gridDim.x * RT;
+    int64_t row = (int64_t)blockIdx.x * RT + threadIdx.x;
+    for (; row + stride < n; row += 2 * stride) {
+        acc0 = fmac(conjv(v[row]), w[row], acc0);
+        acc1 = fmac(conjv(v[row + stride]), w[row + stride], acc1);
     }
+    if (row < n) acc0 = fmac(conjv(v[row]), w[row], acc0);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-    for (int i = 0; i < KMAX; ++i) {
-        if (i < k) {
-            const V v = warp_sum(acc[i]);
-            if (lane == 0) sred[i][warp] = v;
-        }
-    }
+    const V ws = warp_sum(acc0 + acc1);
+    if (lane == 0) sred[warp] = ws;
     __syncthreads();
-    if (threadIdx.x < k) {
+    if (threadIdx.x == 0) {
         V sum = zero<V>();
-        for (int q = 0; q < RT / 32; ++q) sum += sred[threadIdx.x][q];
-        partial[blockIdx.x * KMAX + threadIdx.x] = sum;
+        for (int q = 0; q < RT / 32; ++q) sum += sred[q];
+        partial[(int64_t)i * gridDim.x + blockIdx.x] = sum;
     }
     __threadfence();
-    if (threadIdx.x == 0) s_last = (atomicAdd(counter, 1u) == gridDim.x - 1);
+    if (threadIdx.x == 0) s_last = (atomicAdd(counter, 1u) == gridDim.x * gridDim.y - 1);
     __syncthreads();
     if (s_last) {
-        // warp w reduces outputs w, w + 8, ...: lanes take fixed block strides, then a
-        // fixed shuffle tree, so the result does not depend on block completion order
-        for (int i = warp; i < k; i += RT / 32) {
+        for (int c = warp; c < k; c += RT / 32) {
             V sum = zero<V>();
-            for (unsigned b = lane; b < gridDim.x; b += 32) sum += ldcg(partial + b * KMAX + i);
+            for (unsigned b = lane; b < gridDim.x; b += 32) sum += ldcg(partial + (int64_t)c * gridDim.x + b);
             sum = warp_sum(sum);
-            if (lane == 0) out[i] = sum;
+            if (lane == 0) out[c] = sum;
         }
         if (threadIdx.x == 0) *counter = 0;
     }
@@ -265,7 +276,7 @@ __global__ void hsolve_kernel(int k, const V* __restrict__ H, int ldh, const V* 
 }
 
 template <typename V>
-ndhss_status gmres_one(const FactorData& F, const int32_t* rowptr, const int32_t* col, const V* vals, int64_t nnz,
+ndhss_status gmres_one(const FactorData& F, const int32_t* rowptr, const int32_t* col, const V* vals,
                        const V* b, V* x, const ndhss_gmres_opts& o, ndhss_gmres_stats* stats, unsigned char* ws,
                        cudaStream_t st) {
     const int n = F.n;
@@ -307,13 +318,20 @@ ndhss_status gmres_one(const FactorData& F, const int32_t* rowptr, const int32_t
 
     ndhss_gmres_stats S{};
     // optional CUDA-event timing of every apply and sparse product
+    // events come from a per-thread pool that lives as long as the thread, so
+    // timing adds two records per product and no event creation
+    thread_local std::vector<cudaEvent_t> pool;
+    size_t pool_next = 0;
     std::vector<cudaEvent_t> ev_apply, ev_spmv;
     auto event_pair = [&](std::vector<cudaEvent_t>& v) -> ndhss_status {
-        cudaEvent_t a, b2;
-        NDHSS_CUDA_TRY(cudaEventCreate(&a));
-        NDHSS_CUDA_TRY(cudaEventCreate(&b2));
-        v.push_back(a);
-        v.push_back(b2);
+        for (int q = 0; q < 2; ++q) {
+            if (pool_next == pool.size()) {
+                cudaEvent_t e;
+                NDHSS_CUDA_TRY(cudaEventCreate(&e));
+                pool.push_back(e);
+            }
+            v.push_back(pool[pool_next++]);
+        }
         return NDHSS_OK;
     };
     auto timed_apply = [&](const V* in, V* outv) -> ndhss_status {
@@ -333,7 +351,7 @@ ndhss_status gmres_one(const FactorData& F, const int32_t* rowptr, const int32_t
             if ((r2 = event_pair(ev_spmv))) return r2;
             cudaEventRecord(ev_spmv[ev_spmv.size() - 2], st);
         }
-        if ((r2 = spmv_launch<V>(n, nnz, rowptr, col, vals, in, outv, st))) return r2;
+        if ((r2 = spmv_launch<V>(n, rowptr, col, vals, in, outv, st))) return r2;
         if (o.timing) cudaEventRecord(ev_spmv.back(), st);
         S.nspmv++;
         return NDHSS_OK;
@@ -346,10 +364,9 @@ ndhss_status gmres_one(const FactorData& F, const int32_t* rowptr, const int32_t
             if (cudaEventElapsedTime(&ms, ev_apply[i], ev_apply[i + 1]) == cudaSuccess) S.apply_ms += ms;
         for (size_t i = 0; i + 1 < ev_spmv.size(); i += 2)
             if (cudaEventElapsedTime(&ms, ev_spmv[i], ev_spmv[i + 1]) == cudaSuccess) S.spmv_ms += ms;
-        for (auto e : ev_apply) cudaEventDestroy(e);
-        for (auto e : ev_spmv) cudaEventDestroy(e);
         ev_apply.clear();
         ev_spmv.clear();
+        pool_next = 0;
     };
     nrm2_kernel<V><<<RB, RT, 0, st>>>(n, b, dpart, nrm, counter);
     NDHSS_LAUNCH_CHECK("nrm2_kernel");
@@ -393,11 +410,11 @@ ndhss_status gmres_one(const FactorData& F, const int32_t* rowptr, const int32_t
             if ((rc = timed_spmv(vj, t))) return rc;
             if ((rc = timed_apply(t, w))) return rc;
             ++its;
-            mdot_kernel<V><<<RB, RT, 0, st>>>(n, Vb, ldv, j + 1, w, part, h1, counter);
+            mdot_kernel<V><<<dim3(RB, j + 1), RT, 0, st>>>(n, Vb, ldv, j + 1, w, part, h1, counter);
             NDHSS_LAUNCH_CHECK("mdot_kernel");
             maxpy_kernel<V><<<eb, 256, 0, st>>>(n, w, Vb, ldv, j + 1, h1, -1.0);
             NDHSS_LAUNCH_CHECK("maxpy_kernel");
-            mdot_kernel<V><<<RB, RT, 0, st>>>(n, Vb, ldv, j + 1, w, part, h2, counter);
+            mdot_kernel<V><<<dim3(RB, j + 1), RT, 0, st>>>(n, Vb, ldv, j + 1, w, part, h2, counter);
             NDHSS_LAUNCH_CHECK("mdot_kernel");
             maxpy_kernel<V><<<eb, 256, 0, st>>>(n, w, Vb, ldv, j + 1, h2, -1.0);
             NDHSS_LAUNCH_CHECK("maxpy_kernel");
@@ -450,12 +467,10 @@ ndhss_status ndhss_spmv(int32_t n, int32_t vtype, const int32_t* d_rowptr, const
     if (n < 0 || !d_rowptr || !d_col || !d_vals || !d_x || !d_y) return set_error(NDHSS_ERR_INVALID_ARG, "ndhss_spmv: bad argument");
     if (n == 0) return NDHSS_OK;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    int32_t nnz = 0;
-    NDHSS_CUDA_TRY(cudaMemcpy(&nnz, d_rowptr + n, sizeof(int32_t), cudaMemcpyDeviceToHost));
     if (vtype == NDHSS_R64)
-        return spmv_launch<double>(n, nnz, d_rowptr, d_col, (const double*)d_vals, (const double*)d_x, (double*)d_y, st);
+        return spmv_launch<double>(n, d_rowptr, d_col, (const double*)d_vals, (const double*)d_x, (double*)d_y, st);
     if (vtype == NDHSS_C128)
-        return spmv_launch<c128>(n, nnz, d_rowptr, d_col, (const c128*)d_vals, (const c128*)d_x, (c128*)d_y, st);
+        return spmv_launch<c128>(n, d_rowptr, d_col, (const c128*)d_vals, (const c128*)d_x, (c128*)d_y, st);
     return set_error(NDHSS_ERR_INVALID_ARG, "ndhss_spmv: bad vtype %d", vtype);
 }
 
@@ -477,13 +492,11 @@ ndhss_status ndhss_gmres(const ndhss_factorization* fh, const int32_t* d_rowptr,
     if (o.cycle_rtol < 0) o.cycle_rtol = (F.prec == NDHSS_FP64) ? 0.0 : 1e-4;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const size_t vsz = F.vtype == NDHSS_C128 ? 16 : 8;
-    int32_t nnz = 0;
-    NDHSS_CUDA_TRY(cudaMemcpy(&nnz, d_rowptr + F.n, sizeof(int32_t), cudaMemcpyDeviceToHost));
     const bool bdev = is_device_ptr(b), xdev = is_device_ptr(x);
     const size_t vec = ((size_t)F.n * vsz + 255) / 256 * 256;
     const size_t wb = gmres_work_bytes(F, o.restart, vsz) + (bdev ? 0 : vec) + (xdev ? 0 : vec);
     void* work = nullptr;
-    NDHSS_CUDA_TRY(cudaMallocAsync(&work, wb, st));
+    NDHSS_CUDA_TRY(pool_malloc_async(&work, wb, st));
     unsigned char* ws = static_cast<unsigned char*>(work);
     unsigned char* extra = ws + gmres_work_bytes(F, o.restart, vsz);
     void* db = bdev ? nullptr : extra;
@@ -505,9 +518,9 @@ ndhss_status ndhss_gmres(const ndhss_factorization* fh, const int32_t* d_rowptr,
         if (!xdev) xx = dx;
         ndhss_gmres_stats S{};
         if (F.vtype == NDHSS_R64)
-            rc = gmres_one<double>(F, d_rowptr, d_col, (const double*)d_vals, nnz, (const double*)bb, (double*)xx, o, &S, ws, st);
+            rc = gmres_one<double>(F, d_rowptr, d_col, (const double*)d_vals, (const double*)bb, (double*)xx, o, &S, ws, st);
         else
-            rc = gmres_one<c128>(F, d_rowptr, d_col, (const c128*)d_vals, nnz, (const c128*)bb, (c128*)xx, o, &S, ws, st);
+            rc = gmres_one<c128>(F, d_rowptr, d_col, (const c128*)d_vals, (const c128*)bb, (c128*)xx, o, &S, ws, st);
         if (rc == NDHSS_OK && !xdev) {
             if (cudaMemcpyAsync(xdst, dx, (size_t)F.n * vsz, cudaMemcpyDeviceToHost, st) != cudaSuccess)
                 rc = set_error(NDHSS_ERR_CUDA, "ndhss_gmres: device-to-host copy failed");
