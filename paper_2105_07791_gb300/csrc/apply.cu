@@ -90,8 +90,15 @@ enum : int {
     TK_DN,        // dense: 64 rows of z(I) += R z(B)
     TK_DNDOT,     // low-rank: partial RJt(chunk, :)^T z(B)(chunk)
     TK_DNAXPY,    // low-rank: 64 rows of z(I) += X t
-    TK_FINNOP     // completes a node without interior rows
+    TK_FINNOP,    // completes a node without interior rows
+    TK_UPW,       // up to 8 tiny dense nodes of a level, one per warp: [A_ii^{-1}; -L] y(I)
+    TK_DNW        // the same nodes coming down: z(I) += R z(B), final rows
 };
+// Tiny dense nodes (the bottom levels) are handled a warp per node, eight per
+// task: their blocks are a few KB, so one 64-row task per node would be all
+// latency.  Limits of a warp node (rows of the fused pass, interior rows,
+// boundary columns) and its per-warp shared-memory region.
+constexpr int WN_M = 96, WN_MI = 64, WREG = 128;
 // per-node counters (NCNT arrays of nnodes each) and what signals them
 enum : int { CN_UP = 0, CN_DOT, CN_DIAG, CN_DDOT, CN_FIN, CN_DPART, NCNT };
 constexpr int TK_SHIFT = 26;       // entry word 0 = kind << TK_SHIFT | node
@@ -111,6 +118,7 @@ struct ApplyCtx {
     const int32_t* sigma;
     const int32_t* perm;
     const T* front;
+    const int32_t* wdesc;     // warp nodes, 8 ints each: node, m_i, m_b, i_off, b_off, front offset (lo, hi), 0
 };
 
 // Registers a task fills before its wait: the first group of matrix entries
@@ -217,16 +225,95 @@ __device__ __forceinline__ Entry decode(const int32_t* q, int64_t t) {
     return e;
 }
 
+// ---- warp-node tasks (TK_UPW / TK_DNW) -------------------------------------
+// Warp w < e.a takes node e.base + w of the warp-node table; wd[w] receives
+// its descriptor, idx + w * WREG its gather indices, vec + w * WREG its
+// staged vector.
+__device__ __forceinline__ void taskw_pre(const int32_t* __restrict__ wdesc, const int32_t* __restrict__ sigma,
+                                          const int32_t* __restrict__ blist, const Entry& e, int* idx, int (*wd)[8]) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (w >= e.a) return;
+    if (lane < 8) wd[w][lane] = wdesc[(e.base + w) * 8 + lane];
+    __syncwarp();
+    const int m_i = wd[w][1], m_b = wd[w][2], i_off = wd[w][3], b_off = wd[w][4];
+    int* iw = idx + w * WREG;
+    if (e.kind == TK_UPW)
+        for (int c = lane; c < m_i; c += 32) iw[c] = sigma[i_off + c];
+    else
+        for (int j = lane; j < m_b; j += 32) iw[j] = blist[b_off + j];
+}
+
+template <typename T, typename V>
+__device__ __forceinline__ void taskw_run(const ApplyCtx<T>& C, const Entry& e, const int* idx, T* vec,
+                                          const int (*wd)[8], V* __restrict__ out, T* y, T* z) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (w >= e.a) return;
+    const int m_i = wd[w][1], m_b = wd[w][2], i_off = wd[w][3], b_off = wd[w][4];
+    const int64_t foff = (int64_t)(((uint64_t)(uint32_t)wd[w][6] << 32) | (uint32_t)wd[w][5]);
+    const int m = m_i + m_b;
+    const T* F = C.front + foff;
+    const int* iw = idx + w * WREG;
+    T* vw = vec + w * WREG;
+    constexpr int WU = sizeof(T) <= 8 ? 8 : 4;     // columns in flight per lane
+    if (e.kind == TK_UPW) {
+        // rows r of the first m_i columns, lanes over rows, WU columns in flight
+        for (int c = lane; c < m_i; c += 32) vw[c] = ldw(y + i_off + iw[c]);
+        __syncwarp();
+        for (int r0 = 0; r0 < m; r0 += 32) {
+            const int r = r0 + lane;
+            const int g = (r >= m_i && r < m) ? C.blist[b_off + r - m_i] : -1;
+            T acc = zero<T>();
+            for (int c0 = 0; c0 < m_i; c0 += WU) {
+                T a[WU];
+#pragma unroll
+                for (int u = 0; u < WU; ++u) a[u] = (r < m && c0 + u < m_i) ? F[(int64_t)(c0 + u) * m + r] : zero<T>();
+#pragma unroll
+                for (int u = 0; u < WU; ++u)
+                    if (c0 + u < m_i) acc = fmac(a[u], vw[c0 + u], acc);
+            }
+            if (r < m_i) stw(z + i_off + r, acc);
+            else if (r < m) stw(y + g, ldw(y + g) - acc);
+        }
+    } else {
+        // interior rows of R (m_i x m_b at column m_i), lanes over rows
+        for (int j = lane; j < m_b; j += 32) vw[j] = ldw(z + iw[j]);
+        __syncwarp();
+        const T* R = F + (int64_t)m_i * m;
+        for (int r0 = 0; r0 < m_i; r0 += 32) {
+            const int r = r0 + lane;
+            const int pi = r < m_i ? C.perm[i_off + r] : 0;
+            T acc = zero<T>();
+            for (int c0 = 0; c0 < m_b; c0 += WU) {
+                T a[WU];
+#pragma unroll
+                for (int u = 0; u < WU; ++u) a[u] = (r < m_i && c0 + u < m_b) ? R[(int64_t)(c0 + u) * m + r] : zero<T>();
+#pragma unroll
+                for (int u = 0; u < WU; ++u)
+                    if (c0 + u < m_b) acc = fmac(a[u], vw[c0 + u], acc);
+            }
+            if (r < m_i) {
+                const T v = ldw(z + i_off + r) + acc;
+                stw(z + i_off + r, v);
+                out[pi] = to_val(v);
+            }
+        }
+    }
+}
+
 // Loads every task can issue before its dependencies are met: matrix
 // entries (read-only during the apply) and index lists.  idx: shared int
 // array of at least max(m_i, m_b, LR_CHUNK) entries.
 template <typename T>
-__device__ __forceinline__ void task_pre(const ApplyCtx<T>& C, const Entry& e, Pre<T>& P, int* idx) {
+__device__ __forceinline__ void task_pre(const ApplyCtx<T>& C, const Entry& e, Pre<T>& P, int* idx, int (*wd)[8]) {
     const int s = e.s;
     const int tid = threadIdx.x;
     P.gi = -1;
     P.pi = -1;
     if (e.kind == TK_GATHER) return;
+    if (e.kind == TK_UPW || e.kind == TK_DNW) {
+        taskw_pre(C.wdesc, C.sigma, C.blist, e, idx, wd);
+        return;
+    }
     const int m_i = e.m_i, m_b = e.m_b, i_off = e.i_off, b_off = e.b_off;
     const int64_t m = (int64_t)m_i + m_b;
     const T* F = C.front + e.base;
@@ -304,16 +391,33 @@ __device__ __forceinline__ void task_pre(const ApplyCtx<T>& C, const Entry& e, P
 // memory use before the caller's next barrier.
 template <typename T, typename V>
 __device__ __forceinline__ void task_run(const ApplyCtx<T>& C, const Entry& e, const Pre<T>& P, const int* idx, T* vec,
-                                         T (*red)[APPLY_ROWS], int n, const V* __restrict__ x, V* __restrict__ out,
-                                         T* y, T* z, T* tup, T* tdn, T* dpart) {
+                                         T (*red)[APPLY_ROWS], const int (*wd)[8], int n, const V* __restrict__ x,
+                                         V* __restrict__ out, T* y, T* z, T* tup, T* tdn, T* dpart) {
     const int s = e.s;
     const int tid = threadIdx.x;
     if (e.kind == TK_GATHER) {
-        const int i1 = min(n, e.a + GATHER_CHUNK);
-        for (int i = e.a + tid; i < i1; i += AT) stw(y + i, from_val<T>(x[C.perm[i]]));
+        // index loads, then gathers, four at a time (register budget)
+        for (int h = 0; h < GATHER_CHUNK / AT; h += 4) {
+            int pi[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int i = e.a + tid + (h + u) * AT;
+                pi[u] = i < n ? C.perm[i] : -1;
+            }
+            V xv[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) xv[u] = pi[u] >= 0 ? x[pi[u]] : V{};
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                if (pi[u] >= 0) stw(y + e.a + tid + (h + u) * AT, from_val<T>(xv[u]));
+        }
         return;
     }
     __syncthreads();
+    if (e.kind == TK_UPW || e.kind == TK_DNW) {
+        taskw_run<T, V>(C, e, idx, vec, wd, out, y, z);
+        return;
+    }
     const int m_i = e.m_i, m_b = e.m_b, i_off = e.i_off;
     const int64_t m = (int64_t)m_i + m_b;
     const T* F = C.front + e.base;
@@ -558,6 +662,34 @@ __device__ bool wait_deps(const Sched& S, const int32_t* node, const Entry& e) {
     return true;
 }
 
+// Dependencies of a warp-node task, checked by warp 0: lane j < e.a waits for
+// node j's children (TK_UPW; lane 0 also for the gather) or for its parent's
+// final rows and its own diagonal rows (TK_DNW).  True on every lane when all
+// are met.
+__device__ bool wait_deps_w(const Sched& S, const int32_t* node, const int32_t* wdesc, const Entry& e) {
+    const int lane = threadIdx.x & 31;
+    bool ok = !(ld_relaxed(S.ctl + 2) || ld_relaxed(S.err));
+    const int32_t* cnt = S.ctl + CTL_WORDS;
+    const int nn = S.nn;
+    uint64_t t0 = 0;
+    if (ok && e.kind == TK_UPW && lane == 0) ok = wait_geq(S, S.ctl + 1, S.ngather, t0);
+    if (ok && lane < e.a) {
+        const int s = wdesc[(e.base + lane) * 8];
+        if (e.kind == TK_UPW) {
+            const int c0 = nf(node, s, 2), c1 = nf(node, s, 3);
+            if (c0 >= 0) ok = ok && wait_geq(S, cnt + CN_UP * nn + c0, S.need[CN_UP * nn + c0], t0);
+            if (c1 >= 0) ok = ok && wait_geq(S, cnt + CN_UP * nn + c1, S.need[CN_UP * nn + c1], t0);
+        } else {
+            const int p = nf(node, s, 1);
+            if (p >= 0) ok = ok && wait_geq(S, cnt + CN_FIN * nn + p, S.need[CN_FIN * nn + p], t0);
+            ok = ok && wait_geq(S, cnt + CN_DIAG * nn + s, S.need[CN_DIAG * nn + s], t0);
+        }
+    }
+    ok = __all_sync(0xffffffffu, ok);
+    __threadfence();
+    return ok;
+}
+
 // counters a finished task signals (bit per CN_*), -1 bit 31 for the gather count
 __device__ __forceinline__ unsigned task_signals(const Entry& e) {
     switch (e.kind) {
@@ -583,6 +715,7 @@ __global__ void __launch_bounds__(AT, apply_min_blocks<T>()) apply_dataflow_kern
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ T red[AW][APPLY_ROWS];
     __shared__ int s_task, s_ok;
+    __shared__ int wd[AW][8];
     T* vec = reinterpret_cast<T*>(smem_raw);
     int* idx = reinterpret_cast<int*>(vec + vlen);
     int32_t* cnt = S.ctl + CTL_WORDS;
@@ -598,19 +731,35 @@ __global__ void __launch_bounds__(AT, apply_min_blocks<T>()) apply_dataflow_kern
         if (t >= S.nq) break;
         const Entry e = decode(S.q, t);
         Pre<T> P;
-        task_pre(C, e, P, idx);
-        if (threadIdx.x == 0) {
-            const int ok = wait_deps(S, C.node, e) ? 1 : 0;
-            s_ok = ok;
-            if (ok) next = atomicAdd(S.ctl, 1);
+        task_pre(C, e, P, idx, wd);
+        const bool warp_nodes = e.kind == TK_UPW || e.kind == TK_DNW;
+        if (warp_nodes ? threadIdx.x < 32 : threadIdx.x == 0) {
+            const bool ok = warp_nodes ? wait_deps_w(S, C.node, C.wdesc, e) : wait_deps(S, C.node, e);
+            if (threadIdx.x == 0) {
+                s_ok = ok ? 1 : 0;
+                if (ok) next = atomicAdd(S.ctl, 1);
+            }
         }
         __syncthreads();
         if (!s_ok) break;
-        task_run<T, V>(C, e, P, idx, vec, red, n, x, out, y, z, tup, tdn, dpart);
-        // publish: the barrier orders every thread's stores before thread 0's
-        // gpu-scope fence, which orders them before the signals
+        task_run<T, V>(C, e, P, idx, vec, red, wd, n, x, out, y, z, tup, tdn, dpart);
+        // publish: the barrier orders every thread's stores before the
+        // signalling threads' gpu-scope fences, which order them before the
+        // signals
         __syncthreads();
-        if (threadIdx.x == 0) {
+        if (warp_nodes) {
+            const int lane = threadIdx.x;
+            if (lane < e.a) {
+                const int sj = wd[lane][0];
+                __threadfence();
+                if (e.kind == TK_UPW) {
+                    atomicAdd(cnt + CN_UP * S.nn + sj, 1);
+                    atomicAdd(cnt + CN_DIAG * S.nn + sj, 1);
+                } else {
+                    atomicAdd(cnt + CN_FIN * S.nn + sj, 1);
+                }
+            }
+        } else if (threadIdx.x == 0) {
             __threadfence();
             const unsigned sig = task_signals(e);
             if (sig >> 31) atomicAdd(S.ctl + 1, 1);
@@ -629,12 +778,13 @@ __global__ void __launch_bounds__(AT, apply_min_blocks<T>()) apply_group_kernel(
                                                          T* tdn, T* dpart, int vlen) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ T red[AW][APPLY_ROWS];
+    __shared__ int wd[AW][8];
     T* vec = reinterpret_cast<T*>(smem_raw);
     int* idx = reinterpret_cast<int*>(vec + vlen);
     const Entry e = decode(q, blockIdx.x);
     Pre<T> P;
-    task_pre(C, e, P, idx);
-    task_run<T, V>(C, e, P, idx, vec, red, n, x, out, y, z, tup, tdn, dpart);
+    task_pre(C, e, P, idx, wd);
+    task_run<T, V>(C, e, P, idx, vec, red, wd, n, x, out, y, z, tup, tdn, dpart);
 }
 
 bool levels_schedule_requested() {
@@ -644,7 +794,7 @@ bool levels_schedule_requested() {
 
 template <typename T>
 ApplyCtx<T> make_ctx(const FactorData& F) {
-    return ApplyCtx<T>{F.d_node, F.d_blist, F.d_sigma, F.d_perm, static_cast<const T*>(F.d_front)};
+    return ApplyCtx<T>{F.d_node, F.d_blist, F.d_sigma, F.d_perm, static_cast<const T*>(F.d_front), F.d_wdesc};
 }
 
 // work space: y, z (n each), low-rank partials for each sweep, diagonal
@@ -762,10 +912,49 @@ ndhss_status build_apply_schedule(FactorData& F, cudaStream_t st) {
     F.dpart_total = 0;
     // low-rank dot tasks: one LR_CHUNK-row chunk times one column group
     const int dgw = (AT / 32) * (F.esize <= 8 ? 2 : 1);
+    // warp-node levels: the bottom range of levels whose nodes are all dense
+    // and tiny; a task takes up to AW consecutive nodes of one level
+    auto tiny = [&](int s) {
+        return mode(s) == 0 && F.m_i(s) <= WN_MI && F.m_i(s) + F.m_b(s) <= WN_M && F.m_b(s) <= WREG;
+    };
+    int L_w = F.depth + 1;
+    for (int l = F.depth; l >= 0; --l) {
+        bool all = true;
+        for (int s : F.levels[l]) all = all && tiny(s);
+        if (!all) break;
+        L_w = l;
+    }
+    std::vector<int32_t> wdesc;
+    std::vector<int64_t> wlev(F.depth + 2, 0);      // first warp-node index of each level
+    for (int l = L_w; l <= F.depth; ++l) {
+        wlev[l] = (int64_t)wdesc.size() / 8;
+        for (int s : F.levels[l]) {
+            const uint64_t fo = (uint64_t)F.foff[s];
+            const int32_t d[8] = {s, F.m_i(s), F.m_b(s), F.info(s, 4), F.info(s, 6),
+                                  (int32_t)(uint32_t)fo, (int32_t)(uint32_t)(fo >> 32), 0};
+            wdesc.insert(wdesc.end(), d, d + 8);
+            need[CN_UP * nn + s] = 1;
+            need[CN_DIAG * nn + s] = 1;
+            need[CN_FIN * nn + s] = 1;
+        }
+    }
+    auto push_w = [&](int kind, int l) {
+        const int cnt = (int)F.levels[l].size();
+        for (int j = 0; j < cnt; j += AW) {
+            const int64_t base = wlev[l] + j;
+            const int32_t w[QW] = {(kind << TK_SHIFT) | F.levels[l][j], std::min(AW, cnt - j), l, 0, 0, 0, 0, 0,
+                                   (int32_t)(uint32_t)(uint64_t)base, (int32_t)(uint32_t)((uint64_t)base >> 32), 0, 0};
+            q.insert(q.end(), w, w + QW);
+        }
+    };
     const int ng = ceil_div(F.n, GATHER_CHUNK);
     for (int i = 0; i < ng; ++i) push(TK_GATHER, 0, i * GATHER_CHUNK, 0, false);
     cut();
-    for (int l = F.depth; l >= 0; --l) {
+    for (int l = F.depth; l >= L_w; --l) {
+        push_w(TK_UPW, l);
+        cut();
+    }
+    for (int l = std::min(F.depth, L_w - 1); l >= 0; --l) {
         // fused / dense / low-rank-dot tasks of the level, then what completes each node
         for (int s : F.levels[l]) {
             const int mi = F.m_i(s), mb = F.m_b(s);
@@ -800,7 +989,7 @@ ndhss_status build_apply_schedule(FactorData& F, cudaStream_t st) {
     // diagonal step of the nodes not fused above, deepest level first (ready
     // early; they fill the GPU while the top levels' up-sweep chain runs):
     // column-chunk partial products, then their sums
-    for (int l = F.depth; l >= 0; --l)
+    for (int l = std::min(F.depth, L_w - 1); l >= 0; --l)
         for (int s : F.levels[l]) {
             const int mi = F.m_i(s);
             if (mi == 0 || fused(s)) continue;
@@ -812,7 +1001,7 @@ ndhss_status build_apply_schedule(FactorData& F, cudaStream_t st) {
             need[CN_DPART * nn + s] = nch * ceil_div(mi, APPLY_ROWS);
         }
     cut();
-    for (int l = F.depth; l >= 0; --l)
+    for (int l = std::min(F.depth, L_w - 1); l >= 0; --l)
         for (int s : F.levels[l]) {
             const int mi = F.m_i(s);
             if (mi == 0 || fused(s)) continue;
@@ -821,7 +1010,7 @@ ndhss_status build_apply_schedule(FactorData& F, cudaStream_t st) {
             if (diag_final(s)) need[CN_FIN * nn + s] = need[CN_DIAG * nn + s];
         }
     cut();
-    for (int l = 0; l <= F.depth; ++l) {
+    for (int l = 0; l < L_w; ++l) {
         for (int s : F.levels[l]) {
             if (F.m_i(s) == 0 || diag_final(s) || mode(s) != 1) continue;
             for (int r0 = 0; r0 < F.m_b(s); r0 += LR_CHUNK)
@@ -845,10 +1034,16 @@ ndhss_status build_apply_schedule(FactorData& F, cudaStream_t st) {
         }
         cut();
     }
+    for (int l = L_w; l <= F.depth; ++l) {
+        push_w(TK_DNW, l);
+        cut();
+    }
     F.sched_n = (int64_t)q.size() / QW;
     F.sched_ngather = ng;
     F.sched_groups = groups;
     F.sched_vlen = std::max(std::max(F.max_mi, F.max_mb), LR_CHUNK);
+    if (L_w <= F.depth) F.sched_vlen = std::max(F.sched_vlen, AW * WREG);
+    F.sched_warp_level = L_w;
     if (F.sched_n >= (int64_t)INT32_MAX / QW) return set_error(NDHSS_ERR_INVALID_ARG, "apply: task queue too long");
     ndhss_status rc = NDHSS_OK;
     auto up = [&](auto** dst, const auto& v) {
@@ -864,6 +1059,7 @@ ndhss_status build_apply_schedule(FactorData& F, cudaStream_t st) {
     };
     up(&F.d_sched, q);
     up(&F.d_need, need);
+    up(&F.d_wdesc, wdesc);
     if (rc == NDHSS_OK && (pool_malloc_async((void**)&F.d_apply_err, sizeof(int32_t), st) != cudaSuccess ||
                            cudaMemsetAsync(F.d_apply_err, 0, sizeof(int32_t), st) != cudaSuccess)) {
         cudaGetLastError();

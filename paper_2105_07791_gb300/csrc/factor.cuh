@@ -48,6 +48,8 @@ struct FactorData {
     int32_t sched_grid = 0;
     int32_t sched_vlen = 0;
     int32_t* d_need = nullptr;
+    int32_t* d_wdesc = nullptr;               // warp-node descriptors (8 ints per node)
+    int32_t sched_warp_level = 0;             // first level handled a warp per node
     int64_t dpart_total = 0;
     int32_t* d_apply_err = nullptr;
 

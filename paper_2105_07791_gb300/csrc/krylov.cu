@@ -55,6 +55,21 @@ __device__ __forceinline__ c128 cdiv(c128 a, c128 b) { return a * recip(b); }
 __device__ __forceinline__ double cdiv(double a, double b) { return a / b; }
 
 // ----------------------------------------------------------------- SpMV
+// acc + a * b.  GB300's FP64 pipe is what bounds the complex product, and
+// most entries of the FEM matrices are real (the impedance term is on the
+// boundary only): the FMAs with a zero imaginary part are skipped.  The
+// rounding of the remaining operations is that of the full product.
+__device__ __forceinline__ double spmv_mac(double a, double b, double c) { return fma(a, b, c); }
+__device__ __forceinline__ c128 spmv_mac(c128 a, c128 b, c128 c) {
+    c.x = fma(a.x, b.x, c.x);
+    c.y = fma(a.x, b.y, c.y);
+    if (a.y != 0.0) {
+        c.x = fma(-a.y, b.y, c.x);
+        c.y = fma(a.y, b.x, c.y);
+    }
+    return c;
+}
+
 // TPR threads per row; each issues all U of its column indices and values
 // at once, then the U gathers of x, so a row costs three dependent memory
 // round trips (row pointers, entries, x) instead of two per entry.
@@ -78,7 +93,7 @@ __global__ void __launch_bounds__(256) spmv_kernel(int n, const int32_t* __restr
         }
 #pragma unroll
         for (int u = 0; u < U; ++u)
-            if (c[u] >= 0) acc = fmac(a[u], x[c[u]], acc);
+            if (c[u] >= 0) acc = spmv_mac(a[u], x[c[u]], acc);
     }
     if constexpr (sizeof(V) == 8) {
         for (int o = TPR / 2; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o, TPR);
