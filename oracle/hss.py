@@ -287,6 +287,152 @@ def hss_compress(A: np.ndarray, tree: list, eps: float, k0: int = 32, r: int = 1
 
 
 # ----------------------------------------------------------------------------
+# ULV factorization of an HSS matrix and its solve
+# ----------------------------------------------------------------------------
+
+@dataclass
+class ULV:
+    """ULV factorization of a (complex) symmetric HSS matrix (V = U; the
+    coupling A(I_i, I_j) = U_i B_ij U_j^T uses transposes).
+
+    Bottom-up, every node holds a current block D (m x m) with row basis U
+    and column basis V (m x k).  A unitary Q with Q^H U = [R; 0] leaves the
+    last ne = m - k equations without coupling to the rest of the matrix; a
+    unitary W from the LQ factorization of those rows, (Q^H D)_b W = [L 0],
+    turns them into ne triangular equations for the first ne transformed
+    unknowns, which are eliminated.  The remaining k equations form the
+    reduced block D^ = (Q^H D W)_t,2 with row basis U^ = R and column basis
+    V^ (V^T W = [P1, V^^T]); siblings merge into the parent's block
+    [[D^_a, U^_a B12 V^_b^T], [U^_b B21 V^_a^T, D^_b]] with bases
+    blockdiag(U^_a, U^_b) E and blockdiag(V^_a, V^_b) E (E the nested
+    transfer matrix); the root block is inverted densely.
+
+    Solve data per node (everything the two sweeps need is a matrix-vector
+    product): Mup = [L^-1 Q^H_b; Q^H_t - C L^-1 Q^H_b; P1 L^-1 Q^H_b] maps
+    the node's right-hand side to (y1, r^, G): the eliminated unknowns, the
+    reduced right-hand side and the eliminated unknowns' coupling to the
+    outside (G accumulates E^T [G_a; G_b] from the children); Mm corrects a
+    merged right-hand side for the children's G; W maps [y1; x^2] back to
+    the node's unknowns on the way down."""
+    tree: list
+    n: int
+    ne: dict = field(default_factory=dict)
+    kt: dict = field(default_factory=dict)      # remaining unknowns after elimination
+    k: dict = field(default_factory=dict)       # basis width (coupling rank)
+    Mup: dict = field(default_factory=dict)
+    W: dict = field(default_factory=dict)
+    Mm: dict = field(default_factory=dict)      # inner nodes (incl. the root)
+    E: dict = field(default_factory=dict)       # inner non-root nodes
+    Dinv: object = None                          # root
+
+
+def _blockdiag(a, b):
+    out = np.zeros((a.shape[0] + b.shape[0], a.shape[1] + b.shape[1]), dtype=np.result_type(a.dtype, b.dtype))
+    out[:a.shape[0], :a.shape[1]] = a
+    out[a.shape[0]:, a.shape[1]:] = b
+    return out
+
+
+def ulv_factor(H: HSS) -> ULV:
+    T = H.tree
+    F = ULV(tree=T, n=H.n)
+    red = {}
+    for i in sorted(range(len(T)), key=lambda i: -T[i].level):          # deepest first
+        c = T[i]
+        if not c.children:
+            D = np.asarray(H.D[i], dtype=H.dtype)
+            U = V = (H.U[i] if i != 0 else None)
+        else:
+            a, b = c.children
+            Da, Ua, Va = red[a]
+            Db, Ub, Vb = red[b]
+            A12 = Ua @ H.B12[i]
+            A21 = Ub @ H.B21[i]
+            D = np.block([[Da, A12 @ Vb.T], [A21 @ Va.T, Db]])
+            ka, kb = H.B12[i].shape
+            Mm = np.zeros((Da.shape[0] + Db.shape[0], ka + kb), dtype=D.dtype)
+            Mm[:Da.shape[0], ka:] = A12
+            Mm[Da.shape[0]:, :ka] = A21
+            F.Mm[i] = Mm
+            if i != 0:
+                F.E[i] = H.U[i]
+                U = _blockdiag(Ua, Ub) @ H.U[i]
+                V = _blockdiag(Va, Vb) @ H.U[i]
+        if i == 0:
+            F.Dinv = np.linalg.inv(D)
+            break
+        m, k = D.shape[0], U.shape[1]
+        ne = max(0, m - k)
+        F.ne[i], F.k[i] = ne, k
+        if ne == 0:
+            F.kt[i] = m
+            F.Mup[i] = np.vstack([np.eye(m, dtype=D.dtype), np.zeros((k, m), dtype=D.dtype)])
+            F.W[i] = np.eye(m, dtype=D.dtype)
+            red[i] = (D, U, V)
+            continue
+        Q, R = sla.qr(U, mode="full")                  # Q^H U = [R; 0]
+        QH = Q.conj().T
+        Dt = QH @ D
+        Wq, Rl = sla.qr(Dt[k:, :].conj().T, mode="full")   # (Q^H D)_b = Rl^H Wq^H
+        L = Rl[:ne, :ne].conj().T                      # (Q^H D)_b W = [L 0]
+        DtW = Dt @ Wq
+        C = DtW[:k, :ne]
+        VtW = V.T @ Wq
+        P1 = VtW[:, :ne]
+        Linv = sla.solve_triangular(L, np.eye(ne, dtype=L.dtype), lower=True)
+        Y = Linv @ QH[k:]
+        F.Mup[i] = np.vstack([Y, QH[:k] - C @ Y, P1 @ Y])
+        F.W[i] = Wq
+        F.kt[i] = k
+        red[i] = (DtW[:k, ne:], R[:k, :], VtW[:, ne:].T)
+    return F
+
+
+def ulv_solve(F: ULV, b: np.ndarray) -> np.ndarray:
+    """x = A_HSS^{-1} b with the factors of ulv_factor (b: (n,) or (n, nrhs))."""
+    T = F.tree
+    b2 = b.reshape(F.n, -1)
+    dt = np.result_type(b2.dtype, F.Dinv.dtype)
+    if len(T) == 1:
+        x = F.Dinv @ b2
+        return x.reshape(b.shape) if b.ndim == 1 else x
+    y1, rh, G = {}, {}, {}
+    order = sorted(range(len(T)), key=lambda i: -T[i].level)
+    for i in order:
+        c = T[i]
+        if c.children:
+            a, bb = c.children
+            r = np.vstack([rh[a], rh[bb]]) - F.Mm[i] @ np.vstack([G[a], G[bb]])
+        else:
+            r = b2[c.lo:c.hi].astype(dt)
+        if i == 0:
+            xt = F.Dinv @ r
+            break
+        out = F.Mup[i] @ r
+        ne, kt, k = F.ne[i], F.kt[i], F.k[i]
+        y1[i] = out[:ne]
+        rh[i] = out[ne:ne + kt]
+        G[i] = out[ne + kt:ne + kt + k]
+        if c.children:
+            G[i] = G[i] + F.E[i].T @ np.vstack([G[a], G[bb]])
+    x = np.zeros((F.n, b2.shape[1]), dtype=dt)
+    x2 = {}
+    a, bb = T[0].children
+    x2[a], x2[bb] = xt[:F.kt[a]], xt[F.kt[a]:]
+    for i in sorted(range(len(T)), key=lambda i: T[i].level):
+        if i == 0:
+            continue
+        c = T[i]
+        xt_i = F.W[i] @ np.vstack([y1[i], x2[i]])
+        if c.children:
+            a, bb = c.children
+            x2[a], x2[bb] = xt_i[:F.kt[a]], xt_i[F.kt[a]:]
+        else:
+            x[c.lo:c.hi] = xt_i
+    return x.reshape(b.shape) if b.ndim == 1 else x
+
+
+# ----------------------------------------------------------------------------
 # low-rank factors (Sec. 3.4)
 # ----------------------------------------------------------------------------
 
@@ -348,17 +494,38 @@ class CompressedFactor:
     S: list = field(default_factory=list)       # the Schur complement handed to the parent
     S_exact: list = field(default_factory=list)  # before compression (for tests)
     hss: dict = field(default_factory=dict)     # node -> HSS of S
+    ulv: dict = field(default_factory=dict)     # node -> ULV of HSS(A_ii) (strictly above the switching level)
     kmax: int = 0
 
 
+def ulv_order(tree, s: int) -> np.ndarray:
+    """Order of I^s for its HSS form: by the coordinate along the node's cut,
+    ties by position in I^s.  I^s = [F(mu); F(nu)] lists each child's side of
+    the cut in that coordinate already (Sec. 3.3 numbering); merging the two
+    puts the DOFs facing each other across the cut in the same cluster, so
+    the off-diagonal blocks of every level couple separated stretches of the
+    separator only (low rank), where the split [F(mu); F(nu)] would leave the
+    band of couplings across the cut, a full-rank block, at the top."""
+    m_i = int(tree.node_info[s, 5])
+    axis = int(tree.node_info[s, 12])
+    dofs = tree.perm[tree.I(s)]
+    along = tree.coords[dofs, 1 - axis] if axis in (0, 1) else np.zeros(m_i, dtype=np.int64)
+    return np.lexsort((np.arange(m_i), along)).astype(np.int64)
+
+
 def factor_compressed(tree, A, hss_levels: int = 4, eps: float = 1e-6, beta: int = 64, k0: int = 32,
-                      r: int = 16, seed: int = 0, rank_cap: int = 512) -> CompressedFactor:
+                      r: int = 16, seed: int = 0, rank_cap: int = 512, ulv: bool = False) -> CompressedFactor:
     """Alg. 3.4 with every front formed densely (the matrix-free upper tier of
     Sec. 3.5 is not used): nodes on levels <= L_HSS = depth - hss_levels
     compress their Schur complement by Alg. A.1 with the parent-conforming
     cluster tree of Fig. 4, and the parent assembles the compressed S; nodes
     strictly above the switching level also store R (Eq. 3.3b) in low-rank
-    form (Sec. 3.4) and use L = R^T (A symmetric).  A_ii is factored densely."""
+    form (Sec. 3.4) and use L = R^T (A symmetric).  R, L and S come from the
+    dense elimination of the assembled front.  With ulv=True the assembled
+    A_ii of the nodes strictly above the switching level is compressed too
+    (Alg. A.1, top split [F(mu); F(nu)], Philox stream 2 nnodes + s) and its
+    ULV factorization replaces the dense LU in the diagonal step of the
+    apply; otherwise A_ii is factored densely everywhere."""
     from .frontal import assemble_front, factor_node
     depth = tree.depth
     Lh = depth - hss_levels
@@ -377,6 +544,12 @@ def factor_compressed(tree, A, hss_levels: int = 4, eps: float = 1e-6, beta: int
             fac.hss[s] = H
             fac.kmax = max(fac.kmax, H.kmax())
             S = hss_dense(H)
+        if ulv and lev < Lh and m_i > 0:
+            order = ulv_order(tree, s)
+            Hii = hss_compress(F[:m_i, :m_i][np.ix_(order, order)], cluster_tree(m_i, None, beta), eps, k0, r, seed,
+                               stream=2 * tree.nnodes + s, rank_cap=rank_cap)
+            fac.ulv[s] = (order, ulv_factor(Hii))
+            fac.kmax = max(fac.kmax, Hii.kmax())
         if lev < Lh and m_b > 0 and m_i > 0:
             R = lowrank_rows(R, eps, k0, r, seed, stream=2 * s + 1, rank_cap=rank_cap)
             fac.kmax = max(fac.kmax, R.X.shape[1])
@@ -392,7 +565,8 @@ def factor_compressed(tree, A, hss_levels: int = 4, eps: float = 1e-6, beta: int
 
 
 def apply_compressed(fac: CompressedFactor, b: np.ndarray) -> np.ndarray:
-    """Algorithm 3.1 with low-rank R, L where stored so (Sec. 3.5, last paragraph)."""
+    """Algorithm 3.1 with low-rank R, L where stored so (Sec. 3.5, last
+    paragraph) and ULV solves for the diagonal blocks held in HSS form."""
     tree = fac.tree
     y = np.array(b, dtype=np.result_type(b.dtype, fac.dtype), copy=True)[tree.perm]
     for s in range(tree.nnodes):
@@ -403,7 +577,13 @@ def apply_compressed(fac: CompressedFactor, b: np.ndarray) -> np.ndarray:
     for s in range(tree.nnodes):
         I = tree.I(s)
         if I.size:
-            y[I] = sla.lu_solve(fac.lu[s], y[I], check_finite=False)
+            if s in fac.ulv:
+                order, U = fac.ulv[s]
+                v = np.empty_like(y[I])
+                v[order] = ulv_solve(U, y[I][order])
+                y[I] = v
+            else:
+                y[I] = sla.lu_solve(fac.lu[s], y[I], check_finite=False)
     for s in range(tree.nnodes - 1, -1, -1):
         if tree.node_info[s, 7]:
             I, B = tree.I(s), tree.B(s)

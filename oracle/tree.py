@@ -64,6 +64,7 @@ class Tree:
     e_col: np.ndarray          # int32 [nnz] front-local column
     e_idx: np.ndarray          # int32 [nnz] CSR position of the entry
     leaf_of: np.ndarray        # int32 [n] leaf node holding each DOF (old numbering)
+    coords: np.ndarray = None  # int64 [n, 2] lattice coordinates (old numbering)
 
     @property
     def nnodes(self) -> int:
@@ -309,4 +310,4 @@ def build_tree(coords: np.ndarray, rowptr: np.ndarray, col: np.ndarray, leaf_siz
     i32 = lambda v: np.ascontiguousarray(v, dtype=np.int32)
     return Tree(n=n, node_info=i32(node_info), perm=i32(perm), iperm=i32(iperm), blist=i32(blist),
                 emap=i32(emap), e_off=i32(e_off), e_row=i32(e_r[eorder]), e_col=i32(e_c[eorder]),
-                e_idx=i32(eorder), leaf_of=i32(leaf_of))
+                e_idx=i32(eorder), leaf_of=i32(leaf_of), coords=coords)

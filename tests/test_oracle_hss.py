@@ -9,7 +9,7 @@ from ndhss_inputs import helmholtz_impedance, poisson_dirichlet
 from oracle.frontal import apply_inverse, factor_dense
 from oracle.gmres import gmres
 from oracle.hss import (HSS, apply_compressed, cluster_tree, factor_compressed, gaussian, hss_compress,
-                        hss_dense, hss_matvec, lowrank_rows, philox4x32_10, row_id)
+                        hss_dense, hss_matvec, lowrank_rows, philox4x32_10, row_id, ulv_factor, ulv_solve)
 from oracle.tree import build_tree
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
@@ -141,3 +141,58 @@ def test_compressed_preconditioner_converges_fast(compressed):
     assert not fac0.hss
     x0 = apply_compressed(fac0, P.b)
     assert np.allclose(x0, apply_inverse(factor_dense(T, P.A), P.b), rtol=1e-10, atol=1e-14)
+
+
+def _kernel_matrix(n, dtype, seed):
+    rng = np.random.default_rng(seed)
+    x = np.sort(rng.random(n))
+    A = 1.0 / (1.0 + 40 * np.abs(x[:, None] - x[None, :])) + np.diag(0.5 + rng.random(n))
+    if dtype == np.complex128:
+        A = A + 1j * (np.cos(7 * x[:, None] + 7 * x[None, :]) / (1 + 30 * np.abs(x[:, None] - x[None, :])))
+    return (A + A.T) / 2                               # symmetric, complex symmetric when complex
+
+
+@pytest.mark.parametrize("dtype", [np.float64, np.complex128])
+@pytest.mark.parametrize("n,top,beta,eps", [(300, 140, 40, 1e-10), (257, None, 24, 1e-4), (90, 30, 16, 1e-14),
+                                            (50, None, 64, 1e-8)])
+def test_ulv_solve_equals_dense_solve_of_the_hss_matrix(dtype, n, top, beta, eps):
+    """The ULV factorization is exact for the HSS matrix it factors: its solve
+    equals a dense solve of the reconstruction (to rounding), including
+    nodes whose rank reaches their size (nothing to eliminate, eps 1e-14)
+    and the single-block tree (beta >= n)."""
+    A = _kernel_matrix(n, dtype, 1)
+    H = hss_compress(A, cluster_tree(n, top, beta), eps, seed=5)
+    F = ulv_factor(H)
+    rng = np.random.default_rng(2)
+    b = rng.standard_normal((n, 3)).astype(dtype)
+    xd = np.linalg.solve(hss_dense(H), b)
+    assert np.linalg.norm(ulv_solve(F, b) - xd) <= 1e-11 * np.linalg.norm(xd)
+    assert np.linalg.norm(ulv_solve(F, b[:, 0]) - xd[:, 0]) <= 1e-11 * np.linalg.norm(xd[:, 0])
+
+
+def test_ulv_uses_transposes_not_conjugates():
+    """For a complex symmetric (not Hermitian) HSS matrix the column bases
+    enter as U^T; the same factorization of the Hermitian-ised coupling
+    (conjugated column bases) would solve a different matrix."""
+    A = _kernel_matrix(200, np.complex128, 3)
+    H = hss_compress(A, cluster_tree(200, 90, 32), 1e-10, seed=1)
+    b = np.ones(200, dtype=np.complex128)
+    x = ulv_solve(ulv_factor(H), b)
+    assert np.linalg.norm(A @ x - b) <= 1e-8 * np.linalg.norm(b)
+    Hc = HSS(n=H.n, tree=H.tree, U=dict(H.U), D=dict(H.D), B12={i: v.conj() for i, v in H.B12.items()},
+             B21={i: v.conj() for i, v in H.B21.items()}, skel=H.skel, dtype=H.dtype)
+    xc = ulv_solve(ulv_factor(Hc), b)
+    assert np.linalg.norm(A @ xc - b) > 1e-3 * np.linalg.norm(b)
+
+
+def test_ulv_preconditioner_matches_dense_diagonal_within_tolerance(compressed):
+    """A_ii in HSS form with its ULV solve changes the preconditioner by the
+    compression tolerance only, and GMRES still converges as fast."""
+    P, T, fac = compressed
+    facu = factor_compressed(T, P.A, hss_levels=3, eps=1e-6, ulv=True)
+    assert facu.ulv and all(int(T.node_info[s, 0]) < facu.L_hss for s in facu.ulv)
+    b = P.b if P.b.ndim == 1 else P.b[:, 0]
+    y0, y1 = apply_compressed(fac, b), apply_compressed(facu, b)
+    assert np.linalg.norm(y1 - y0) <= 1e-4 * np.linalg.norm(y0)
+    r = gmres(P.A, b, lambda v: apply_compressed(facu, v), tol=1e-8)
+    assert r.converged and r.iters <= 5
