@@ -73,7 +73,11 @@ typedef struct {
     int32_t panel;              /* pivot block width of the front kernels, 0 = auto    */
     uint64_t seed;              /* random sampling seed                                */
     int32_t timing;             /* 1: time every kernel class with CUDA events         */
-    int32_t pad;
+    int32_t ulv;                /* 1: A_ii of the fronts strictly above the switching
+                                   level in HSS form (Alg. A.1, ordered along the cut)
+                                   with a ULV factorization; the apply's diagonal step
+                                   of those fronts is the ULV solve.  0: A_ii^{-1}
+                                   formed densely at every level                      */
 } ndhss_factor_opts;
 
 typedef struct {

@@ -92,7 +92,10 @@ enum : int {
     TK_DNAXPY,    // low-rank: 64 rows of z(I) += X t
     TK_FINNOP,    // completes a node without interior rows
     TK_UPW,       // up to 8 tiny dense nodes of a level, one per warp: [A_ii^{-1}; -L] y(I)
-    TK_DNW        // the same nodes coming down: z(I) += R z(B), final rows
+    TK_DNW,       // the same nodes coming down: z(I) += R z(B), final rows
+    TK_HUP,       // ULV solve of HSS(A_ii), one HSS node going up (entry node = ULV record)
+    TK_HROOT,     // the root block of a ULV front
+    TK_HDN        // one HSS node coming down (leaves write z(I) rows)
 };
 // Tiny dense nodes (the bottom levels) are handled a warp per node, eight per
 // task: their blocks are a few KB, so one 64-row task per node would be all
@@ -101,7 +104,7 @@ enum : int {
 constexpr int WN_M = 96, WN_MI = 64, WREG = 128;
 // per-node counters (NCNT arrays of nnodes each) and what signals them
 enum : int { CN_UP = 0, CN_DOT, CN_DIAG, CN_DDOT, CN_FIN, CN_DPART, NCNT };
-constexpr int TK_SHIFT = 26;       // entry word 0 = kind << TK_SHIFT | node
+constexpr int TK_SHIFT = 25;       // entry word 0 = kind << TK_SHIFT | node (5 bits of kind)
 constexpr int TK_FINAL = 1 << 30;  // entry word 0 flag: the task writes final rows (scatter)
 constexpr int CTL_WORDS = 4;       // ticket, gather count, abort, pad
 // ints per queue entry: flags | kind | node, a, b, m_i, m_b, i_off, b_off, k,
@@ -119,6 +122,16 @@ struct ApplyCtx {
     const int32_t* perm;
     const T* front;
     const int32_t* wdesc;     // warp nodes, 8 ints each: node, m_i, m_b, i_off, b_off, front offset (lo, hi), 0
+    const struct UlvDev* ulv; // ULV records (HSS nodes of the ULV fronts)
+    const int32_t* ulv_ord;   // HSS order of each ULV front's I^s
+};
+
+// One HSS node of a ULV front on the device: sizes, links, its front, the
+// apply scratch slots of its vectors and the addresses of its solve data.
+struct UlvDev {
+    int32_t s, lo, hi, m, k, ne, kt, ka, kb, parent, c1, c2, leaf, root, i_off, pad;
+    int64_t ord_off, o_y1, o_rh, o_g, o_x2;
+    uint64_t Mup, W, Mm, E, Dinv;
 };
 
 // Registers a task fills before its wait: the first group of matrix entries
@@ -211,7 +224,7 @@ __device__ __forceinline__ Entry decode(const int32_t* q, int64_t t) {
     const int4 v0 = p[0], v1 = p[1], v2 = p[2];
     Entry e;
     e.fin = (v0.x & TK_FINAL) != 0;
-    e.kind = (v0.x >> TK_SHIFT) & 15;
+    e.kind = (v0.x >> TK_SHIFT) & 31;
     e.s = v0.x & ((1 << TK_SHIFT) - 1);
     e.a = v0.y;
     e.b = v0.z;
@@ -300,6 +313,101 @@ __device__ __forceinline__ void taskw_run(const ApplyCtx<T>& C, const Entry& e, 
     }
 }
 
+// ---- ULV solve tasks (TK_HUP / TK_HROOT / TK_HDN) --------------------------
+// Every step is a matrix-vector product with precomputed ULV data (ulv.cu):
+// up: r (the front's rows of y in HSS order at a leaf; the children's
+// reduced right-hand sides corrected by their couplings G at an inner node)
+// -> Mup r = (y1, r^, G); root: x = Dinv r; down: x~ = W [y1; x2], split
+// among the children or (leaf) written to z(I^s) in the front's order.
+template <typename T, typename Fn>
+__device__ __forceinline__ void ulv_gemv(const T* A, int rows, int cols, const T* xs, T (*red)[APPLY_ROWS], Fn&& emit) {
+    for (int r0 = 0; r0 < rows; r0 += APPLY_ROWS) {
+        T pre[8];
+        gemv_pre(A, rows, rows, cols, r0, pre);
+        const T sum = gemv_rows64(A, rows, rows, cols, r0, xs, red, pre);
+        if (threadIdx.x < APPLY_ROWS && r0 + (int)threadIdx.x < rows) emit(r0 + (int)threadIdx.x, sum);
+        __syncthreads();
+    }
+}
+
+template <typename T, typename V>
+__device__ __forceinline__ void ulv_task(const ApplyCtx<T>& C, const Entry& e, const int* idx, T* vec,
+                                         T (*red)[APPLY_ROWS], V* __restrict__ out, const T* y, T* z, T* us) {
+    const UlvDev R = C.ulv[e.s];
+    const int tid = threadIdx.x;
+    const int m = R.m;
+    if (e.kind == TK_HUP || e.kind == TK_HROOT) {
+        T* g = vec + m;
+        int ka = 0, kb = 0;
+        if (R.leaf) {
+            for (int j = tid; j < m; j += AT) vec[j] = ldw(y + R.i_off + idx[j]);
+            __syncthreads();
+        } else {
+            const UlvDev A = C.ulv[R.c1], B = C.ulv[R.c2];
+            ka = R.ka;
+            kb = R.kb;
+            for (int c = tid; c < ka + kb; c += AT) g[c] = c < ka ? ldw(us + A.o_g + c) : ldw(us + B.o_g + c - ka);
+            __syncthreads();
+            // r = [r^_a; r^_b] - Mm [G_a; G_b]
+            const T* Mm = reinterpret_cast<const T*>(R.Mm);
+            ulv_gemv(Mm, m, ka + kb, g, red, [&](int j, T v) {
+                const T rh = j < A.kt ? ldw(us + A.o_rh + j) : ldw(us + B.o_rh + j - A.kt);
+                vec[j] = rh - v;
+            });
+        }
+        if (e.kind == TK_HROOT) {
+            const T* Di = reinterpret_cast<const T*>(R.Dinv);
+            if (R.leaf) {
+                ulv_gemv(Di, m, m, vec, red, [&](int j, T v) {
+                    const int row = R.i_off + idx[j];
+                    stw(z + row, v);
+                    if (e.fin) out[C.perm[row]] = to_val(v);
+                });
+            } else {
+                const UlvDev A = C.ulv[R.c1], B = C.ulv[R.c2];
+                ulv_gemv(Di, m, m, vec, red, [&](int j, T v) {
+                    if (j < A.kt) stw(us + A.o_x2 + j, v);
+                    else stw(us + B.o_x2 + j - A.kt, v);
+                });
+            }
+        } else {
+            const T* Mup = reinterpret_cast<const T*>(R.Mup);
+            const int ne = R.ne, kt = R.kt, k = R.k;
+            const T* E = reinterpret_cast<const T*>(R.E);
+            ulv_gemv(Mup, m + k, m, vec, red, [&](int j, T v) {
+                if (j < ne) {
+                    stw(us + R.o_y1 + j, v);
+                } else if (j < ne + kt) {
+                    stw(us + R.o_rh + j - ne, v);
+                } else {
+                    const int a = j - ne - kt;
+                    if (!R.leaf)       // G += E^T [G_a; G_b]
+                        for (int c = 0; c < ka + kb; ++c) v = fmac(E[(int64_t)a * (ka + kb) + c], g[c], v);
+                    stw(us + R.o_g + a, v);
+                }
+            });
+        }
+        return;
+    }
+    // TK_HDN: x~ = W [y1; x2]
+    for (int j = tid; j < m; j += AT) vec[j] = j < R.ne ? ldw(us + R.o_y1 + j) : ldw(us + R.o_x2 + j - R.ne);
+    __syncthreads();
+    const T* W = reinterpret_cast<const T*>(R.W);
+    if (R.leaf) {
+        ulv_gemv(W, m, m, vec, red, [&](int j, T v) {
+            const int row = R.i_off + idx[j];
+            stw(z + row, v);
+            if (e.fin) out[C.perm[row]] = to_val(v);
+        });
+    } else {
+        const UlvDev A = C.ulv[R.c1], B = C.ulv[R.c2];
+        ulv_gemv(W, m, m, vec, red, [&](int j, T v) {
+            if (j < A.kt) stw(us + A.o_x2 + j, v);
+            else stw(us + B.o_x2 + j - A.kt, v);
+        });
+    }
+}
+
 // Loads every task can issue before its dependencies are met: matrix
 // entries (read-only during the apply) and index lists.  idx: shared int
 // array of at least max(m_i, m_b, LR_CHUNK) entries.
@@ -312,6 +420,13 @@ __device__ __forceinline__ void task_pre(const ApplyCtx<T>& C, const Entry& e, P
     if (e.kind == TK_GATHER) return;
     if (e.kind == TK_UPW || e.kind == TK_DNW) {
         taskw_pre(C.wdesc, C.sigma, C.blist, e, idx, wd);
+        return;
+    }
+    if (e.kind == TK_HUP || e.kind == TK_HROOT || e.kind == TK_HDN) {
+        if (e.b_off & 1) {                       // leaf: the rows of I^s it owns, in HSS order
+            const UlvDev& R = C.ulv[e.s];
+            for (int j = tid; j < R.m; j += AT) idx[j] = C.ulv_ord[R.ord_off + R.lo + j];
+        }
         return;
     }
     const int m_i = e.m_i, m_b = e.m_b, i_off = e.i_off, b_off = e.b_off;
@@ -392,7 +507,7 @@ __device__ __forceinline__ void task_pre(const ApplyCtx<T>& C, const Entry& e, P
 template <typename T, typename V>
 __device__ __forceinline__ void task_run(const ApplyCtx<T>& C, const Entry& e, const Pre<T>& P, const int* idx, T* vec,
                                          T (*red)[APPLY_ROWS], const int (*wd)[8], int n, const V* __restrict__ x,
-                                         V* __restrict__ out, T* y, T* z, T* tup, T* tdn, T* dpart) {
+                                         V* __restrict__ out, T* y, T* z, T* tup, T* tdn, T* dpart, T* us) {
     const int s = e.s;
     const int tid = threadIdx.x;
     if (e.kind == TK_GATHER) {
@@ -416,6 +531,10 @@ __device__ __forceinline__ void task_run(const ApplyCtx<T>& C, const Entry& e, c
     __syncthreads();
     if (e.kind == TK_UPW || e.kind == TK_DNW) {
         taskw_run<T, V>(C, e, idx, vec, wd, out, y, z);
+        return;
+    }
+    if (e.kind == TK_HUP || e.kind == TK_HROOT || e.kind == TK_HDN) {
+        ulv_task<T, V>(C, e, idx, vec, red, out, y, z, us);
         return;
     }
     const int m_i = e.m_i, m_b = e.m_b, i_off = e.i_off;
@@ -574,11 +693,14 @@ __device__ __forceinline__ uint64_t global_ns() {
 
 struct Sched {
     const int32_t* q;          // [QW * nq] entries
-    int32_t nq, ngather, nn, pad;
-    const int32_t* need;       // [NCNT * nn]
-    int32_t* ctl;              // [CTL_WORDS + NCNT * nn], zeroed before the launch
+    int32_t nq, ngather, nn, nrec;
+    const int32_t* need;       // [NCNT * nn + 2 * nrec]
+    int32_t* ctl;              // [CTL_WORDS + NCNT * nn + 2 * nrec], zeroed before the launch
     int32_t* err;              // sticky error word of the factorization
 };
+// counters of the ULV records (up / down), after the per-node counters
+__device__ __forceinline__ int hu_index(const Sched& S, int rec) { return NCNT * S.nn + rec; }
+__device__ __forceinline__ int hd_index(const Sched& S, int rec) { return NCNT * S.nn + S.nrec + rec; }
 
 // Bounded wait until *ctr >= need; false once the wait gave up or another
 // CTA reported a failure.
@@ -636,6 +758,27 @@ __device__ __forceinline__ Deps task_deps(const Sched& S, const int32_t* node, c
         break;
     }
     case TK_DNAXPY: add(s, CN_DDOT); add(s, CN_DIAG); break;
+    case TK_HUP: case TK_HROOT:
+        if (e.b_off & 1) {                          // leaf: the front's y(I^s) is final
+            d.c[0] = S.ctl + 1;
+            d.need[0] = S.ngather;
+            d.n = 1;
+            const int c0 = nf(node, e.a, 2), c1 = nf(node, e.a, 3);
+            if (c0 >= 0) add(c0, CN_UP);
+            if (c1 >= 0) add(c1, CN_UP);
+        } else {                                    // inner: both HSS children went up
+            d.c[0] = cnt + hu_index(S, e.m_i);
+            d.need[0] = S.need[hu_index(S, e.m_i)];
+            d.c[1] = cnt + hu_index(S, e.m_b);
+            d.need[1] = S.need[hu_index(S, e.m_b)];
+            d.n = 2;
+        }
+        break;
+    case TK_HDN:
+        d.c[0] = cnt + hd_index(S, e.i_off);
+        d.need[0] = S.need[hd_index(S, e.i_off)];
+        d.n = 1;
+        break;
     default: break;
     }
     return d;
@@ -711,7 +854,7 @@ template <typename T> constexpr int apply_min_blocks() { return sizeof(T) <= 8 ?
 template <typename T, typename V>
 __global__ void __launch_bounds__(AT, apply_min_blocks<T>()) apply_dataflow_kernel(ApplyCtx<T> C, Sched S, int n, const V* __restrict__ x,
                                                             V* __restrict__ out, T* y, T* z, T* tup, T* tdn, T* dpart,
-                                                            int vlen) {
+                                                            T* us, int vlen) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ T red[AW][APPLY_ROWS];
     __shared__ int s_task, s_ok;
@@ -742,7 +885,7 @@ __global__ void __launch_bounds__(AT, apply_min_blocks<T>()) apply_dataflow_kern
         }
         __syncthreads();
         if (!s_ok) break;
-        task_run<T, V>(C, e, P, idx, vec, red, wd, n, x, out, y, z, tup, tdn, dpart);
+        task_run<T, V>(C, e, P, idx, vec, red, wd, n, x, out, y, z, tup, tdn, dpart, us);
         // publish: the barrier orders every thread's stores before the
         // signalling threads' gpu-scope fences, which order them before the
         // signals
@@ -758,6 +901,13 @@ __global__ void __launch_bounds__(AT, apply_min_blocks<T>()) apply_dataflow_kern
                 } else {
                     atomicAdd(cnt + CN_FIN * S.nn + sj, 1);
                 }
+            }
+        } else if (threadIdx.x == 0 && (e.kind == TK_HUP || e.kind == TK_HROOT || e.kind == TK_HDN)) {
+            __threadfence();
+            atomicAdd(cnt + (e.kind == TK_HUP ? hu_index(S, e.s) : hd_index(S, e.s)), 1);
+            if (e.kind != TK_HUP && (e.b_off & 1)) {        // a leaf wrote its rows of z(I^s)
+                atomicAdd(cnt + CN_DIAG * S.nn + e.a, 1);
+                if (e.fin) atomicAdd(cnt + CN_FIN * S.nn + e.a, 1);
             }
         } else if (threadIdx.x == 0) {
             __threadfence();
@@ -775,7 +925,7 @@ __global__ void __launch_bounds__(AT, apply_min_blocks<T>()) apply_dataflow_kern
 template <typename T, typename V>
 __global__ void __launch_bounds__(AT, apply_min_blocks<T>()) apply_group_kernel(ApplyCtx<T> C, const int32_t* __restrict__ q, int n,
                                                          const V* __restrict__ x, V* __restrict__ out, T* y, T* z, T* tup,
-                                                         T* tdn, T* dpart, int vlen) {
+                                                         T* tdn, T* dpart, T* us, int vlen) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ T red[AW][APPLY_ROWS];
     __shared__ int wd[AW][8];
@@ -784,7 +934,7 @@ __global__ void __launch_bounds__(AT, apply_min_blocks<T>()) apply_group_kernel(
     const Entry e = decode(q, blockIdx.x);
     Pre<T> P;
     task_pre(C, e, P, idx, wd);
-    task_run<T, V>(C, e, P, idx, vec, red, wd, n, x, out, y, z, tup, tdn, dpart);
+    task_run<T, V>(C, e, P, idx, vec, red, wd, n, x, out, y, z, tup, tdn, dpart, us);
 }
 
 bool levels_schedule_requested() {
@@ -794,13 +944,14 @@ bool levels_schedule_requested() {
 
 template <typename T>
 ApplyCtx<T> make_ctx(const FactorData& F) {
-    return ApplyCtx<T>{F.d_node, F.d_blist, F.d_sigma, F.d_perm, static_cast<const T*>(F.d_front), F.d_wdesc};
+    return ApplyCtx<T>{F.d_node, F.d_blist, F.d_sigma, F.d_perm, static_cast<const T*>(F.d_front), F.d_wdesc,
+                       reinterpret_cast<const UlvDev*>(F.d_ulvdev), F.d_ulv_ord};
 }
 
 // work space: y, z (n each), low-rank partials for each sweep, diagonal
 // partials, control words
 struct WorkLayout {
-    size_t y, z, tup, tdn, dpart, ctl, total;
+    size_t y, z, tup, tdn, dpart, us, ctl, total;
 };
 WorkLayout work_layout(const FactorData& F) {
     auto r256 = [](size_t b) { return (b + 255) / 256 * 256; };
@@ -812,8 +963,10 @@ WorkLayout work_layout(const FactorData& F) {
     L.tup = 2 * vec;
     L.tdn = L.tup + tb;
     L.dpart = L.tdn + tb;
-    L.ctl = L.dpart + r256((size_t)std::max<int64_t>(F.dpart_total, 1) * F.esize);
-    L.total = L.ctl + r256(sizeof(int32_t) * (CTL_WORDS + (size_t)NCNT * std::max(F.nnodes, 1)));
+    L.us = L.dpart + r256((size_t)std::max<int64_t>(F.dpart_total, 1) * F.esize);
+    L.ctl = L.us + r256((size_t)std::max<int64_t>(F.ulv_scratch, 1) * F.esize);
+    L.total = L.ctl + r256(sizeof(int32_t) * (CTL_WORDS + (size_t)NCNT * std::max(F.nnodes, 1) +
+                                              2 * (size_t)F.ulv_recs.size()));
     return L;
 }
 
@@ -832,6 +985,7 @@ ndhss_status apply_run(const FactorData& F, int32_t nrhs, const V* x, int64_t ld
     T* tup = reinterpret_cast<T*>(w + WL.tup);
     T* tdn = reinterpret_cast<T*>(w + WL.tdn);
     T* dpart = reinterpret_cast<T*>(w + WL.dpart);
+    T* us = reinterpret_cast<T*>(w + WL.us);
     const size_t smem = smem_bytes(F, sizeof(T));
     const int vlen = F.sched_vlen;
     if (levels_schedule_requested()) {
@@ -840,18 +994,18 @@ ndhss_status apply_run(const FactorData& F, int32_t nrhs, const V* x, int64_t ld
                 const int64_t g0 = F.sched_groups[g], g1 = F.sched_groups[g + 1];
                 if (g1 == g0) continue;
                 apply_group_kernel<T, V><<<(unsigned)(g1 - g0), AT, smem, st>>>(
-                    C, F.d_sched + QW * g0, F.n, x + r * ldx, y + r * ldy, wy, wz, tup, tdn, dpart, vlen);
+                    C, F.d_sched + QW * g0, F.n, x + r * ldx, y + r * ldy, wy, wz, tup, tdn, dpart, us, vlen);
                 NDHSS_LAUNCH_CHECK("apply_group_kernel");
             }
         return NDHSS_OK;
     }
-    Sched S{F.d_sched, (int32_t)F.sched_n, F.sched_ngather, F.nnodes, 0, F.d_need,
+    Sched S{F.d_sched, (int32_t)F.sched_n, F.sched_ngather, F.nnodes, (int32_t)F.ulv_recs.size(), F.d_need,
             reinterpret_cast<int32_t*>(w + WL.ctl), F.d_apply_err};
-    const size_t ctl_bytes = sizeof(int32_t) * (CTL_WORDS + (size_t)NCNT * F.nnodes);
+    const size_t ctl_bytes = sizeof(int32_t) * (CTL_WORDS + (size_t)NCNT * F.nnodes + 2 * F.ulv_recs.size());
     for (int r = 0; r < nrhs; ++r) {
         NDHSS_CUDA_TRY(cudaMemsetAsync(S.ctl, 0, ctl_bytes, st));
         apply_dataflow_kernel<T, V><<<(unsigned)F.sched_grid, AT, smem, st>>>(C, S, F.n, x + r * ldx, y + r * ldy, wy, wz,
-                                                                              tup, tdn, dpart, vlen);
+                                                                              tup, tdn, dpart, us, vlen);
         NDHSS_LAUNCH_CHECK("apply_dataflow_kernel");
     }
     return NDHSS_OK;
@@ -882,7 +1036,8 @@ ndhss_status launch_shape(FactorData& F) {
 ndhss_status build_apply_schedule(FactorData& F, cudaStream_t st) {
     const int nn = F.nnodes;
     if ((int64_t)nn >= (int64_t(1) << TK_SHIFT)) return set_error(NDHSS_ERR_INVALID_ARG, "apply: too many tree nodes");
-    std::vector<int32_t> q, need((size_t)NCNT * std::max(nn, 1), 0);
+    const int nrec = (int)F.ulv_recs.size();
+    std::vector<int32_t> q, need((size_t)NCNT * std::max(nn, 1) + 2 * (size_t)nrec, 0);
     std::vector<int64_t> groups{0};
     std::vector<int64_t> dpoff(std::max(nn, 1), 0);
     auto push = [&](int kind, int s, int a, int b, bool fin) {
@@ -989,10 +1144,11 @@ ndhss_status build_apply_schedule(FactorData& F, cudaStream_t st) {
     // diagonal step of the nodes not fused above, deepest level first (ready
     // early; they fill the GPU while the top levels' up-sweep chain runs):
     // column-chunk partial products, then their sums
+    auto ulv_front = [&](int s) { return !F.ulv_root_of.empty() && F.ulv_root_of[s] >= 0; };
     for (int l = std::min(F.depth, L_w - 1); l >= 0; --l)
         for (int s : F.levels[l]) {
             const int mi = F.m_i(s);
-            if (mi == 0 || fused(s)) continue;
+            if (mi == 0 || fused(s) || ulv_front(s)) continue;
             const int nch = ceil_div(mi, DIAG_COLS);
             dpoff[s] = F.dpart_total;
             F.dpart_total += (int64_t)nch * mi;
@@ -1004,12 +1160,60 @@ ndhss_status build_apply_schedule(FactorData& F, cudaStream_t st) {
     for (int l = std::min(F.depth, L_w - 1); l >= 0; --l)
         for (int s : F.levels[l]) {
             const int mi = F.m_i(s);
-            if (mi == 0 || fused(s)) continue;
+            if (mi == 0 || fused(s) || ulv_front(s)) continue;
             for (int r0 = 0; r0 < mi; r0 += SUM_ROWS) push(TK_DSUM, s, r0, 0, diag_final(s));
             need[CN_DIAG * nn + s] = ceil_div(mi, SUM_ROWS);
             if (diag_final(s)) need[CN_FIN * nn + s] = need[CN_DIAG * nn + s];
         }
     cut();
+    // ULV solves of the HSS fronts: every front's HSS nodes going up (deepest
+    // HSS level first), the roots, then down; the leaves (or a root that is
+    // a leaf) write z(I^s)
+    std::vector<UlvDev> udev(std::max(nrec, 1));
+    F.ulv_scratch = 0;
+    int ulv_maxlev = 0;
+    for (int i = 0; i < nrec; ++i) {
+        const FactorData::UlvRec& r = F.ulv_recs[i];
+        UlvDev& d = udev[i];
+        d.s = r.s; d.lo = r.lo; d.hi = r.hi; d.m = r.m; d.k = r.k; d.ne = r.ne; d.kt = r.kt; d.ka = r.ka; d.kb = r.kb;
+        d.parent = r.parent; d.c1 = r.c1; d.c2 = r.c2; d.leaf = r.leaf; d.root = r.root; d.i_off = F.info(r.s, 4);
+        d.pad = 0;
+        d.ord_off = F.ulv_ord_off[r.s];
+        auto slot = [&](int64_t c) { const int64_t o = F.ulv_scratch; F.ulv_scratch += std::max<int64_t>(c, 1); return o; };
+        d.o_y1 = slot(r.ne);
+        d.o_rh = slot(r.kt);
+        d.o_g = slot(r.k);
+        d.o_x2 = slot(r.kt);
+        d.Mup = r.Mup; d.W = r.W; d.Mm = r.Mm; d.E = r.E; d.Dinv = r.Dinv;
+        ulv_maxlev = std::max(ulv_maxlev, r.level);
+        F.sched_vlen = std::max(F.sched_vlen, r.m + r.ka + r.kb);
+        need[NCNT * nn + i] = 1;
+        need[NCNT * nn + nrec + i] = 1;
+        if (r.leaf) {
+            need[CN_DIAG * nn + r.s] += 1;
+            if (diag_final(r.s)) need[CN_FIN * nn + r.s] += 1;
+        }
+    }
+    auto push_u = [&](int kind, int i) {
+        const FactorData::UlvRec& r = F.ulv_recs[i];
+        const bool writes = r.leaf && kind != TK_HUP;
+        const int32_t w[QW] = {((writes && diag_final(r.s)) ? TK_FINAL : 0) | (kind << TK_SHIFT) | i, r.s, r.level,
+                               r.c1, r.c2, r.parent, (r.leaf ? 1 : 0) | (r.root ? 2 : 0), 0, 0, 0, 0, 0};
+        q.insert(q.end(), w, w + QW);
+    };
+    for (int lv = ulv_maxlev; lv >= 1; --lv) {
+        for (int i = 0; i < nrec; ++i)
+            if (F.ulv_recs[i].level == lv && !F.ulv_recs[i].root) push_u(TK_HUP, i);
+        cut();
+    }
+    for (int i = 0; i < nrec; ++i)
+        if (F.ulv_recs[i].root) push_u(TK_HROOT, i);
+    cut();
+    for (int lv = 1; lv <= ulv_maxlev; ++lv) {
+        for (int i = 0; i < nrec; ++i)
+            if (F.ulv_recs[i].level == lv) push_u(TK_HDN, i);
+        cut();
+    }
     for (int l = 0; l < L_w; ++l) {
         for (int s : F.levels[l]) {
             if (F.m_i(s) == 0 || diag_final(s) || mode(s) != 1) continue;
@@ -1041,7 +1245,7 @@ ndhss_status build_apply_schedule(FactorData& F, cudaStream_t st) {
     F.sched_n = (int64_t)q.size() / QW;
     F.sched_ngather = ng;
     F.sched_groups = groups;
-    F.sched_vlen = std::max(std::max(F.max_mi, F.max_mb), LR_CHUNK);
+    F.sched_vlen = std::max(F.sched_vlen, std::max(std::max(F.max_mi, F.max_mb), LR_CHUNK));
     if (L_w <= F.depth) F.sched_vlen = std::max(F.sched_vlen, AW * WREG);
     F.sched_warp_level = L_w;
     if (F.sched_n >= (int64_t)INT32_MAX / QW) return set_error(NDHSS_ERR_INVALID_ARG, "apply: task queue too long");
@@ -1060,6 +1264,14 @@ ndhss_status build_apply_schedule(FactorData& F, cudaStream_t st) {
     up(&F.d_sched, q);
     up(&F.d_need, need);
     up(&F.d_wdesc, wdesc);
+    if (nrec) {
+        if (pool_malloc_async(&F.d_ulvdev, udev.size() * sizeof(UlvDev), st) != cudaSuccess ||
+            cudaMemcpyAsync(F.d_ulvdev, udev.data(), udev.size() * sizeof(UlvDev), cudaMemcpyHostToDevice, st) !=
+                cudaSuccess) {
+            cudaGetLastError();
+            rc = set_error(NDHSS_ERR_OOM, "apply: ULV records");
+        }
+    }
     if (rc == NDHSS_OK && (pool_malloc_async((void**)&F.d_apply_err, sizeof(int32_t), st) != cudaSuccess ||
                            cudaMemsetAsync(F.d_apply_err, 0, sizeof(int32_t), st) != cudaSuccess)) {
         cudaGetLastError();

@@ -453,6 +453,25 @@ struct LaunchTimer {
     }
 };
 
+// A_ii of a ULV front in its HSS order, copied out of the assembled front
+// before the elimination overwrites it: aii(j, j') = A_ii(ord[j], ord[j']).
+struct AiiJob {
+    int64_t aii_off, foff, ord_off;
+    int32_t m, mi;
+};
+
+template <typename T>
+__global__ void gather_aii_kernel(const AiiJob* __restrict__ jobs, const int32_t* __restrict__ ord,
+                                  const T* __restrict__ front, T* __restrict__ aii) {
+    const AiiJob J = jobs[blockIdx.y];
+    const int32_t* o = ord + J.ord_off;
+    const int64_t tot = (int64_t)J.mi * J.mi;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < tot; q += (int64_t)gridDim.x * blockDim.x) {
+        const int j = (int)(q % J.mi), jj = (int)(q / J.mi);
+        aii[J.aii_off + q] = front[J.foff + (int64_t)o[jj] * J.m + o[j]];
+    }
+}
+
 template <typename T, typename V>
 ndhss_status factor_run(FactorData& F, const Tree& t, const V* d_vals, const int32_t* d_eoff,
                         const int32_t* d_erow, const int32_t* d_ecol, const int32_t* d_eidx,
@@ -488,6 +507,33 @@ ndhss_status factor_run(FactorData& F, const Tree& t, const V* d_vals, const int
         NDHSS_LAUNCH_CHECK("scatter_entries_kernel");
         tm.end(1);
         F.launches += 2;
+        // ULV fronts of this level: their A_ii in HSS order, before the sweep below
+        std::vector<int64_t> aii_off;
+        void* d_aii = nullptr;
+        if (F.ulv && l < F.L_hss) {
+            aii_off.assign(t.nnodes, -1);
+            std::vector<AiiJob> jobs;
+            int64_t tot = 0;
+            for (int s : nodes)
+                if (F.ulv_ord_off[s] >= 0) {
+                    aii_off[s] = tot;
+                    jobs.push_back({tot, F.foff[s], F.ulv_ord_off[s], F.m_i(s) + F.m_b(s), F.m_i(s)});
+                    tot += (int64_t)F.m_i(s) * F.m_i(s);
+                }
+            if (!jobs.empty()) {
+                AiiJob* d_jobs = nullptr;
+                if (pool_malloc_async(&d_aii, (size_t)tot * sizeof(T), st) != cudaSuccess ||
+                    pool_malloc_async((void**)&d_jobs, jobs.size() * sizeof(AiiJob), st) != cudaSuccess) {
+                    cudaGetLastError();
+                    return set_error(NDHSS_ERR_OOM, "ndhss_factor: A_ii copies of level %d", l);
+                }
+                NDHSS_CUDA_TRY(cudaMemcpyAsync(d_jobs, jobs.data(), jobs.size() * sizeof(AiiJob), cudaMemcpyHostToDevice, st));
+                gather_aii_kernel<T><<<dim3(64, (unsigned)jobs.size()), 256, 0, st>>>(d_jobs, F.d_ulv_ord, front,
+                                                                                       static_cast<T*>(d_aii));
+                NDHSS_LAUNCH_CHECK("gather_aii_kernel");
+                cudaFreeAsync(d_jobs, st);
+            }
+        }
         const int gt = (int)((mmax + GT - 1) / GT);
         const int pgx = (int)std::min<int64_t>((mmax + PREP_WARPS - 1) / PREP_WARPS, 1024);
         for (int64_t k0 = 0; k0 < mimax;) {
@@ -540,8 +586,12 @@ ndhss_status factor_run(FactorData& F, const Tree& t, const V* d_vals, const int
             // Alg. 3.4 at and above the switching level: compress S (and R above it)
             tm.begin();
             ndhss_status rc2 = hss_compress_level(F, t, l, o, st);
+            if (rc2 == NDHSS_OK && d_aii) rc2 = hss_ulv_level(F, t, l, d_aii, aii_off, o, st);
+            if (d_aii) cudaFreeAsync(d_aii, st);
             if (rc2 != NDHSS_OK) return rc2;
             tm.end(6);
+        } else if (d_aii) {
+            cudaFreeAsync(d_aii, st);
         }
     }
     return NDHSS_OK;
@@ -585,6 +635,28 @@ static ndhss_status factor_impl(const ndhss_tree* th, int32_t vtype, const int32
     F.L_hss = (o.hss_levels >= 0) ? t.depth - o.hss_levels : -1;
     F.levels.assign(t.depth + 1, {});
     for (int s = 0; s < t.nnodes; ++s) F.levels[t.level(s)].push_back(s);
+    // ULV tier: the HSS order of every A_ii strictly above the switching level,
+    // by the coordinate along the node's cut (ties: position in I^s)
+    F.ulv = o.ulv != 0 && F.L_hss > 0;
+    F.ulv_root_of.assign(t.nnodes, -1);
+    F.ulv_ord_off.assign(t.nnodes, -1);
+    if (F.ulv) {
+        for (int s = 0; s < t.nnodes; ++s) {
+            const int mi = t.m_i(s);
+            if (t.level(s) >= F.L_hss || mi == 0) continue;
+            const int axis = t.info(s, 12);
+            std::vector<int32_t> ord(mi);
+            std::vector<int64_t> along(mi, 0);
+            for (int c = 0; c < mi; ++c) {
+                ord[c] = c;
+                const int d = t.perm[t.i_off(s) + c];
+                if (axis == 0 || axis == 1) along[c] = t.coords[2 * (size_t)d + (1 - axis)];
+            }
+            std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) { return along[a] < along[b]; });
+            F.ulv_ord_off[s] = (int64_t)F.ulv_ord.size();
+            F.ulv_ord.insert(F.ulv_ord.end(), ord.begin(), ord.end());
+        }
+    }
     F.foff.resize(t.nnodes);
     int64_t acc = 0, posacc = 0;
     std::vector<int64_t> poff(t.nnodes);
@@ -649,6 +721,7 @@ static ndhss_status factor_impl(const ndhss_tree* th, int32_t vtype, const int32
     UP(F.d_foff, F.foff);
     UP(F.d_blist, t.blist);
     UP(F.d_perm, t.perm);
+    if (F.ulv) UP(F.d_ulv_ord, F.ulv_ord);
     UPT(d_eoff, t.e_off);
     UPT(d_erow, t.e_row);
     UPT(d_ecol, t.e_col);
@@ -726,6 +799,11 @@ static ndhss_status factor_impl(const ndhss_tree* th, int32_t vtype, const int32
             elems += mi * mi + (F.lr_ptr[s] ? 2 * (mi + mb) * (int64_t)F.lr_k[s] : 2 * mi * mb);
         }
         F.apply_bytes = elems * (int64_t)esize;
+        if (F.ulv) {
+            for (int s = 0; s < t.nnodes; ++s)
+                if (F.ulv_root_of[s] >= 0) F.apply_bytes -= (int64_t)t.m_i(s) * t.m_i(s) * (int64_t)esize;
+            F.apply_bytes += F.ulv_bytes;
+        }
         std::vector<int32_t> lst;
         F.lr_off_l.assign(t.depth + 1, 0);
         F.lr_cnt.assign(t.depth + 1, 0);
@@ -913,6 +991,10 @@ void ndhss_factor_destroy(ndhss_factorization* fh) {
         if (p) cudaFreeAsync(p, 0);
     for (void* b : F.lr_bufs)
         if (b) cudaFreeAsync(b, 0);
+    for (void* b : F.ulv_bufs)
+        if (b) cudaFreeAsync(b, 0);
+    if (F.d_ulv_ord) cudaFreeAsync(F.d_ulv_ord, 0);
+    if (F.d_ulvdev) cudaFreeAsync(F.d_ulvdev, 0);
     cudaStreamSynchronize(0);
     delete fh;
 }

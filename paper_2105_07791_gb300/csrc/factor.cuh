@@ -70,6 +70,29 @@ struct FactorData {
     int64_t lr_t_total = 0;
     int32_t kmax = 0;
     int32_t hss_rounds_max = 0;
+
+    // ULV of HSS(A_ii) strictly above the switching level (opts.ulv): one
+    // record per HSS node of each such front; the apply's diagonal step of
+    // those fronts is the ULV solve (ulv.cu, apply.cu)
+    struct UlvRec {
+        int32_t s;                  // tree node
+        int32_t lo, hi;             // leaf: rows of the front's HSS order; else -1
+        int32_t m, k, ne, kt;       // block, basis width, eliminated, remaining
+        int32_t ka, kb;             // inner: children's basis widths
+        int32_t parent, c1, c2;     // records (-1 = none)
+        int32_t level, leaf, root;
+        uint64_t Mup, W, Mm, E, Dinv;   // device addresses of the solve data
+    };
+    bool ulv = false;
+    std::vector<UlvRec> ulv_recs;
+    std::vector<int32_t> ulv_root_of;       // per tree node: its root record, -1 = dense A_ii^{-1}
+    std::vector<int64_t> ulv_ord_off;       // per tree node: offset of its HSS order in ulv_ord
+    std::vector<int32_t> ulv_ord;           // HSS order of I^s (position -> index in I^s)
+    std::vector<void*> ulv_bufs;
+    int32_t* d_ulv_ord = nullptr;
+    void* d_ulvdev = nullptr;               // device records of the apply (apply.cu)
+    int64_t ulv_scratch = 0;                // apply scratch elements of the ULV vectors
+    int64_t ulv_bytes = 0;                  // solve data streamed per apply
     double hss_ms = 0.0;
 
     double factor_ms = 0.0;
@@ -93,6 +116,11 @@ constexpr int LR_CHUNK = 256;    // input rows per low-rank dot task
 // just been eliminated densely.  Defined in hss.cu.
 ndhss_status hss_compress_level(FactorData& F, const Tree& t, int level, const ndhss_factor_opts& o,
                                 cudaStream_t st);
+// Compress the interior blocks (already gathered in HSS order into aii,
+// node s's block at aii_off[s], ld m_i) of the ULV fronts of tree level
+// `level` and ULV-factor them.  Defined in hss.cu.
+ndhss_status hss_ulv_level(FactorData& F, const Tree& t, int level, void* aii, const std::vector<int64_t>& aii_off,
+                           const ndhss_factor_opts& o, cudaStream_t st);
 
 ndhss_status apply_device(const FactorData& F, int32_t nrhs, const void* d_x, int64_t ldx,
                           void* d_y, int64_t ldy, void* d_work, cudaStream_t st);

@@ -24,6 +24,7 @@
 #include <vector>
 
 #include "factor.cuh"
+#include "ulv.cuh"
 
 namespace ndhss {
 namespace {
@@ -840,6 +841,155 @@ struct Problem {
     uint64_t stream;   // 2*node (S) or 2*node+1 (R), as the oracle
 };
 
+// ULV factorization of HSS fronts whose generators sit in device memory:
+// per HSS node its leaf block (in the front's block), basis / transfer matrix
+// X (ld x_ld), coupling blocks B12 / B21 (inner nodes), rank; jobs run one
+// HSS level per launch, deepest first.  Appends the solve records to F.
+struct UlvIn {
+    int s;              // tree node of the front
+    int lo, hi, level, c1, c2, root;   // c1 / c2: indices into the same input list
+    int k;              // basis width (root: unused)
+    const void* D0;     // leaf block, ld ldd0
+    int64_t ldd0;
+    const void* X;      // leaf basis / inner transfer matrix, ld ldx
+    int64_t ldx;
+    const void* B12;
+    const void* B21;
+};
+
+template <typename T>
+ndhss_status ulv_factor_nodes(const std::vector<UlvIn>& in, FactorData& F, cudaStream_t st) {
+    const int nn = (int)in.size();
+    if (!nn) return NDHSS_OK;
+    std::vector<int> m(nn), ne(nn), kt(nn), kw(nn);
+    int maxlev = 0;
+    for (auto& u : in) maxlev = std::max(maxlev, u.level);
+    std::vector<int> order;
+    for (int l = maxlev; l >= 0; --l)
+        for (int q = 0; q < nn; ++q)
+            if (in[q].level == l) order.push_back(q);
+    std::vector<int> job_of(nn);
+    for (int j = 0; j < nn; ++j) job_of[order[j]] = j;
+    int64_t pers = 0, pass = 0;
+    std::vector<int64_t> o_mup(nn), o_w(nn), o_mm(nn), o_e(nn), o_di(nn), o_dh(nn);
+    for (int q : order) {
+        const UlvIn& u = in[q];
+        m[q] = (u.c1 < 0) ? u.hi - u.lo : kt[u.c1] + kt[u.c2];
+        kw[q] = u.root ? 0 : u.k;
+        ne[q] = u.root ? 0 : std::max(0, m[q] - kw[q]);
+        kt[q] = m[q] - ne[q];
+        const int ka = u.c1 < 0 ? 0 : kw[u.c1], kb = u.c1 < 0 ? 0 : kw[u.c2];
+        auto take = [&](int64_t c) { const int64_t o = pers; pers += (c + 31) / 32 * 32; return o; };
+        o_mup[q] = u.root ? -1 : take((int64_t)(m[q] + kw[q]) * m[q]);
+        o_w[q] = u.root ? -1 : take((int64_t)m[q] * m[q]);
+        o_mm[q] = u.c1 < 0 ? -1 : take((int64_t)m[q] * std::max(ka + kb, 1));
+        o_e[q] = (u.c1 < 0 || u.root) ? -1 : take((int64_t)std::max(ka + kb, 1) * std::max(kw[q], 1));
+        o_di[q] = u.root ? take((int64_t)m[q] * m[q]) : -1;
+        o_dh[q] = pass;
+        pass += ((int64_t)kt[q] * kt[q] + 2 * (int64_t)kt[q] * std::max(kw[q], 1) + 31) / 32 * 32;
+    }
+    void* buf = nullptr;
+    if (pool_malloc_async(&buf, std::max<int64_t>(pers, 1) * sizeof(T), st) != cudaSuccess) {
+        cudaGetLastError();
+        return set_error(NDHSS_ERR_OOM, "ulv: solve data (%lld elements)", (long long)pers);
+    }
+    F.ulv_bufs.push_back(buf);
+    F.dev_bytes += pers * (int64_t)sizeof(T);
+    T* P = static_cast<T*>(buf);
+    // work space: the largest level
+    std::vector<int64_t> lvl_work(maxlev + 1, 0), o_wk(nn);
+    for (int q = 0; q < nn; ++q) {
+        o_wk[q] = lvl_work[in[q].level];
+        lvl_work[in[q].level] += (ulv_work_elems(m[q], kw[q], ne[q]) + 31) / 32 * 32;
+    }
+    int64_t wmax = 1;
+    for (int64_t w : lvl_work) wmax = std::max(wmax, w);
+    DeviceVec<T> work(st), passbuf(st);
+    DeviceVec<int> status(st);
+    HSS_TRY(work.alloc(wmax));
+    HSS_TRY(passbuf.alloc(std::max<int64_t>(pass, 1)));
+    HSS_TRY(status.alloc(1));
+    HSS_TRY(cudaMemsetAsync(status.p, 0, sizeof(int), st));
+    std::vector<UlvJob<T>> jobs(nn);
+    const int rec0 = (int)F.ulv_recs.size();
+    F.ulv_recs.resize(rec0 + nn);
+    for (int j = 0; j < nn; ++j) {
+        const int q = order[j];
+        const UlvIn& u = in[q];
+        UlvJob<T> J{};
+        J.m = m[q];
+        J.k = kw[q];
+        J.ne = ne[q];
+        J.kt = kt[q];
+        J.leaf = u.c1 < 0;
+        J.root = u.root;
+        J.ka = u.c1 < 0 ? 0 : kw[u.c1];
+        J.kb = u.c1 < 0 ? 0 : kw[u.c2];
+        J.c1 = u.c1 < 0 ? -1 : job_of[u.c1];
+        J.c2 = u.c1 < 0 ? -1 : job_of[u.c2];
+        J.D0 = static_cast<const T*>(u.D0);
+        J.ldd0 = u.ldd0;
+        J.X = static_cast<const T*>(u.X);
+        J.ldx = u.ldx;
+        J.B12 = static_cast<const T*>(u.B12);
+        J.B21 = static_cast<const T*>(u.B21);
+        J.Mup = o_mup[q] >= 0 ? P + o_mup[q] : nullptr;
+        J.W = o_w[q] >= 0 ? P + o_w[q] : nullptr;
+        J.Mm = o_mm[q] >= 0 ? P + o_mm[q] : nullptr;
+        J.E = o_e[q] >= 0 ? P + o_e[q] : nullptr;
+        J.Dinv = o_di[q] >= 0 ? P + o_di[q] : nullptr;
+        T* ph = passbuf.p + o_dh[q];
+        J.Dh = ph;
+        J.Uh = ph + (int64_t)kt[q] * kt[q];
+        J.Vh = J.Uh + (int64_t)kt[q] * std::max(kw[q], 1);
+        J.w = work.p + o_wk[q];
+        J.status = status.p;
+        jobs[j] = J;
+        FactorData::UlvRec& r = F.ulv_recs[rec0 + j];
+        r.s = u.s;
+        r.lo = J.leaf ? u.lo : -1;
+        r.hi = J.leaf ? u.hi : -1;
+        r.m = J.m;
+        r.k = J.k;
+        r.ne = J.ne;
+        r.kt = J.kt;
+        r.ka = J.ka;
+        r.kb = J.kb;
+        r.c1 = J.c1 < 0 ? -1 : rec0 + J.c1;
+        r.c2 = J.c2 < 0 ? -1 : rec0 + J.c2;
+        r.parent = -1;
+        r.level = u.level;
+        r.leaf = J.leaf;
+        r.root = J.root;
+        r.Mup = reinterpret_cast<uint64_t>(J.Mup);
+        r.W = reinterpret_cast<uint64_t>(J.W);
+        r.Mm = reinterpret_cast<uint64_t>(J.Mm);
+        r.E = reinterpret_cast<uint64_t>(J.E);
+        r.Dinv = reinterpret_cast<uint64_t>(J.Dinv);
+        if (J.root) F.ulv_root_of[u.s] = rec0 + j;
+    }
+    for (int j = 0; j < nn; ++j) {
+        const FactorData::UlvRec& r = F.ulv_recs[rec0 + j];
+        if (r.c1 >= 0) F.ulv_recs[r.c1].parent = F.ulv_recs[r.c2].parent = rec0 + j;
+    }
+    F.ulv_bytes += pers * (int64_t)sizeof(T);
+    DeviceVec<UlvJob<T>> djobs(st);
+    HSS_TRY(djobs.upload(jobs, st));
+    int j0 = 0;
+    for (int l = maxlev; l >= 0; --l) {
+        int cnt = 0;
+        while (j0 + cnt < nn && in[order[j0 + cnt]].level == l) ++cnt;
+        ndhss_status rc = ulv_launch_level<T>(djobs.p + j0, djobs.p, cnt, st);
+        if (rc != NDHSS_OK) return rc;
+        j0 += cnt;
+    }
+    int hs = 0;
+    HSS_TRY(cudaMemcpyAsync(&hs, status.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+    HSS_TRY(cudaStreamSynchronize(st));
+    if (hs) return set_error(NDHSS_ERR_SINGULAR, "ulv: singular root block of an HSS(A_ii) at level %d", in[0].level);
+    return NDHSS_OK;
+}
+
 // Runs the adaptive rounds of Alg. A.1 (lowrank == false) or of the low-rank
 // range finder (lowrank == true) on all problems; on success S blocks are
 // overwritten by their HSS reconstruction and for R blocks (X, R(J,:)) are
@@ -847,7 +997,7 @@ struct Problem {
 template <typename T>
 ndhss_status compress_problems(std::vector<Problem>& probs, bool lowrank, const ndhss_factor_opts& o,
                                std::vector<int>& kout, std::vector<std::vector<T>>* lr_host, FactorData& F,
-                               cudaStream_t st) {
+                               cudaStream_t st, bool ulv = false) {
     const int r = std::max(o.r, 1), k0 = std::max(o.k0, 1), beta = std::max(o.beta, 1);
     const int rank_cap = std::max(o.rank_cap, 1);
     const double eps = o.eps_hss;
@@ -1097,6 +1247,73 @@ ndhss_status compress_problems(std::vector<Problem>& probs, bool lowrank, const 
                     }
                 }
                 HSS_TRY(cudaStreamSynchronize(st));
+            } else if (ulv) {
+                // HSS generators of the retired blocks into a ULV factorization (the
+                // blocks themselves stay as they are)
+                std::vector<char> keep(nf, 0);
+                for (int i : done) keep[i] = 1;
+                std::vector<int> inner;
+                std::vector<int64_t> ob;
+                int64_t btot = 0;
+                for (size_t q = 0; q < nodes.size(); ++q) {
+                    const HNode& nd = nodes[q];
+                    if (!keep[nd.front] || nd.c1 < 0) continue;
+                    inner.push_back((int)q);
+                    ob.push_back(btot);
+                    btot += 2 * std::max<int64_t>((int64_t)hk[nd.c1] * hk[nd.c2], 1);
+                }
+                DeviceVec<T> bb(st);
+                HSS_TRY(bb.alloc(std::max<int64_t>(btot, 1)));
+                std::vector<T*> p12, p21;
+                for (size_t q = 0; q < inner.size(); ++q) {
+                    const HNode& nd = nodes[inner[q]];
+                    p12.push_back(bb.p + ob[q]);
+                    p21.push_back(bb.p + ob[q] + std::max<int64_t>((int64_t)hk[nd.c1] * hk[nd.c2], 1));
+                }
+                DeviceVec<int> dinner(st);
+                DeviceVec<T*> dp12(st), dp21(st);
+                HSS_TRY(dinner.upload(inner, st));
+                HSS_TRY(dp12.upload(p12, st));
+                HSS_TRY(dp21.upload(p21, st));
+                if (!inner.empty()) {
+                    gather_b_kernel<T><<<(unsigned)inner.size(), HT, 0, st>>>(dinner.p, dnodes.p, dfr.p, iws.p, kk.p, dp12.p,
+                                                                             dp21.p);
+                    NDHSS_LAUNCH_CHECK("gather_b_kernel");
+                }
+                std::vector<int> inner_of(nodes.size(), -1);
+                for (size_t q = 0; q < inner.size(); ++q) inner_of[inner[q]] = (int)q;
+                std::vector<UlvIn> uin;
+                std::vector<int> idx_of(nodes.size(), -1);
+                for (size_t q = 0; q < nodes.size(); ++q)
+                    if (keep[nodes[q].front]) { idx_of[q] = (int)uin.size(); uin.push_back({}); }
+                for (size_t q = 0; q < nodes.size(); ++q) {
+                    if (idx_of[q] < 0) continue;
+                    const HNode& nd = nodes[q];
+                    const HFront& f = fr[nd.front];
+                    UlvIn& u = uin[idx_of[q]];
+                    u.s = probs[active[nd.front]].node;
+                    u.lo = nd.lo;
+                    u.hi = nd.hi;
+                    u.level = nd.level;
+                    u.c1 = nd.c1 < 0 ? -1 : idx_of[nd.c1];
+                    u.c2 = nd.c2 < 0 ? -1 : idx_of[nd.c2];
+                    u.root = (int)q == f.root;
+                    u.k = hk[q];
+                    u.D0 = static_cast<const T*>(f.S) + (int64_t)nd.lo * f.lds + nd.lo;
+                    u.ldd0 = f.lds;
+                    u.X = ws.p + nd.o_x;
+                    u.ldx = nd.rows_cap;
+                    u.B12 = inner_of[q] >= 0 ? p12[inner_of[q]] : nullptr;
+                    u.B21 = inner_of[q] >= 0 ? p21[inner_of[q]] : nullptr;
+                }
+                ndhss_status rc = ulv_factor_nodes<T>(uin, F, st);
+                if (rc != NDHSS_OK) return rc;
+                for (int i : done) {
+                    int km = 0;
+                    for (size_t q = 0; q < nodes.size(); ++q)
+                        if (nodes[q].front == i && (int)q != fr[i].root) km = std::max(km, hk[q]);
+                    kout[active[i]] = km;
+                }
             } else {
                 // S_HSS written over S: leaf diagonal blocks stay; every off-diagonal block
                 // S(I_c1, I_c2) = U~_c1 B12 U~_c2^T with the expanded nested bases
@@ -1280,6 +1497,59 @@ ndhss_status compress_level_impl(FactorData& F, const Tree& t, int level, const 
 }
 
 }  // namespace
+
+namespace {
+
+template <typename T>
+ndhss_status ulv_level_impl(FactorData& F, const Tree& t, int level, T* aii, const std::vector<int64_t>& aii_off,
+                            const ndhss_factor_opts& o, cudaStream_t st) {
+    const int beta = std::max(o.beta, 1);
+    std::vector<Problem> probs;
+    std::vector<UlvIn> small;
+    for (int s : F.levels[level]) {
+        if (aii_off[s] < 0) continue;
+        const int mi = t.m_i(s);
+        T* blk = aii + aii_off[s];
+        if (mi <= beta) {
+            // one HSS block: the ULV is the inverse of A_ii (as the oracle's single-node tree)
+            UlvIn u{};
+            u.s = s;
+            u.lo = 0;
+            u.hi = mi;
+            u.level = 0;
+            u.c1 = u.c2 = -1;
+            u.root = 1;
+            u.D0 = blk;
+            u.ldd0 = mi;
+            small.push_back(u);
+        } else {
+            probs.push_back({s, mi, mi, mi, blk, -1, (uint64_t)2 * t.nnodes + s});
+        }
+    }
+    if (!small.empty()) {
+        // independent single-node fronts: one launch, each its own root
+        ndhss_status rc = ulv_factor_nodes<T>(small, F, st);
+        if (rc != NDHSS_OK) return rc;
+    }
+    if (!probs.empty()) {
+        std::vector<int> ks;
+        ndhss_status rc = compress_problems<T>(probs, false, o, ks, nullptr, F, st, true);
+        if (rc != NDHSS_OK) return rc;
+        for (int k : ks) F.kmax = std::max(F.kmax, k);
+    }
+    return NDHSS_OK;
+}
+
+}  // namespace
+
+ndhss_status hss_ulv_level(FactorData& F, const Tree& t, int level, void* aii, const std::vector<int64_t>& aii_off,
+                           const ndhss_factor_opts& o, cudaStream_t st) {
+    const bool cplx = F.vtype == NDHSS_C128;
+    if (!cplx && F.prec == NDHSS_FP64) return ulv_level_impl<double>(F, t, level, (double*)aii, aii_off, o, st);
+    if (!cplx) return ulv_level_impl<float>(F, t, level, (float*)aii, aii_off, o, st);
+    if (F.prec == NDHSS_FP64) return ulv_level_impl<c128>(F, t, level, (c128*)aii, aii_off, o, st);
+    return ulv_level_impl<c64>(F, t, level, (c64*)aii, aii_off, o, st);
+}
 
 ndhss_status hss_compress_level(FactorData& F, const Tree& t, int level, const ndhss_factor_opts& o, cudaStream_t st) {
     if (F.lr_ptr.size() != (size_t)F.nnodes) {

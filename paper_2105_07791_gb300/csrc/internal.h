@@ -17,6 +17,7 @@ struct Tree {
     int64_t nnz = 0;
     std::vector<int32_t> node_info;   // [nnodes * NODE_NF]
     std::vector<int32_t> perm, iperm, blist, emap, e_off, e_row, e_col, e_idx;
+    std::vector<int32_t> coords;      // [n * 2] lattice coordinates (original numbering)
 
     int32_t info(int s, int f) const { return node_info[(size_t)s * NODE_NF + f]; }
     int32_t level(int s) const { return info(s, 0); }

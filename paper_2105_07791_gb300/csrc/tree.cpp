@@ -92,6 +92,7 @@ ndhss_status build_tree_impl(int32_t n, const int32_t* coords, const int32_t* ro
     for (int64_t k = 0; k < nnz; ++k)
         if (col[k] < 0 || col[k] >= n) return set_error(NDHSS_ERR_INVALID_ARG, "build_tree: column index out of range");
 
+    T->coords.assign(coords, coords + 2 * (size_t)n);
     Builder B;
     B.n = n;
     B.coords = coords;

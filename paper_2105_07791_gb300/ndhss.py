@@ -37,7 +37,7 @@ class NdhssError(RuntimeError):
 class FactorOpts(C.Structure):
     _fields_ = [("prec", C.c_int32), ("hss_levels", C.c_int32), ("eps_hss", C.c_double), ("beta", C.c_int32),
                 ("k0", C.c_int32), ("r", C.c_int32), ("rank_cap", C.c_int32), ("panel", C.c_int32),
-                ("seed", C.c_uint64), ("timing", C.c_int32), ("pad", C.c_int32)]
+                ("seed", C.c_uint64), ("timing", C.c_int32), ("ulv", C.c_int32)]
 
 
 class GmresOpts(C.Structure):
@@ -195,8 +195,8 @@ class Factor:
 
 
 def make_factor_opts(prec=NDHSS_FP64, hss_levels=-1, eps_hss=1e-6, beta=64, k0=32, r=16, rank_cap=512,
-                     panel=0, seed=0, timing=False) -> FactorOpts:
-    return FactorOpts(prec, hss_levels, eps_hss, beta, k0, r, rank_cap, panel, seed, int(bool(timing)), 0)
+                     panel=0, seed=0, timing=False, ulv=False) -> FactorOpts:
+    return FactorOpts(prec, hss_levels, eps_hss, beta, k0, r, rank_cap, panel, seed, int(bool(timing)), int(bool(ulv)))
 
 
 def ndhss_factor(tree: Tree, vtype: int, d_rowptr, d_col, d_vals, opts: FactorOpts | None = None,

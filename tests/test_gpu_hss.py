@@ -136,3 +136,44 @@ def test_compressed_apply_and_gmres(nd, case, prec):
     ro = oracle_gmres(P.A, b, lambda v: apply_compressed(fac, v), tol=1e-8)
     assert st["iters"] <= ro.iters + 2, (st, ro.iters)
     assert _rel(xs, ro.x) <= 1e-6
+
+
+@pytest.fixture(scope="module")
+def ulv_case(case):
+    """The same problem with A_ii in HSS form and its ULV factorization
+    strictly above the switching level (oracle)."""
+    P, T = case["P"], case["T"]
+    facu = factor_compressed(T, P.A, hss_levels=case["hl"], eps=EPS, beta=64, k0=32, r=16, seed=11, ulv=True)
+    return dict(case, facu=facu)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_ulv_apply_matches_oracle_and_schedules_agree(nd, ulv_case, prec, monkeypatch):
+    """The ULV diagonal step (HSS(A_ii) compressed on the device with the same
+    Philox streams, ULV-factored, solved by the up / root / down tasks) gives
+    the oracle's ULV preconditioner; the persistent queue and the level
+    launches agree bit for bit; GMRES still converges."""
+    c = ulv_case
+    P, M, facu = c["P"], c["M"], c["facu"]
+    assert facu.ulv
+    opts = nd.make_factor_opts(prec=prec, hss_levels=c["hl"], eps_hss=EPS, beta=64, k0=32, r=16, seed=11, ulv=True)
+    f = nd.ndhss_factor(c["tree"], M.vtype, M.rowptr, M.col, M.vals, opts)
+    b = P.b if P.b.ndim == 1 else P.b[:, 0]
+    dt = np.complex128 if M.vtype == 1 else np.float64
+    bd = torch.from_numpy(np.ascontiguousarray(b.astype(dt))).cuda()
+    monkeypatch.delenv("NDHSS_APPLY_SCHEDULE", raising=False)
+    y = torch.empty_like(bd)
+    nd.ndhss_apply(f, bd, y)
+    yo = apply_compressed(facu, b)
+    assert _rel(y.cpu().numpy(), yo) <= (1e-4 if prec == 0 else 1e-3)
+    monkeypatch.setenv("NDHSS_APPLY_SCHEDULE", "levels")
+    yl = torch.empty_like(bd)
+    nd.ndhss_apply(f, bd, yl)
+    assert np.array_equal(y.cpu().numpy(), yl.cpu().numpy())
+    monkeypatch.delenv("NDHSS_APPLY_SCHEDULE", raising=False)
+    x = torch.zeros_like(bd)
+    st = nd.ndhss_gmres(f, M.rowptr, M.col, M.vals, bd, x, tol=1e-8)
+    xs = x.cpu().numpy()
+    assert st["converged"] and np.linalg.norm(b - P.A @ xs) / np.linalg.norm(b) <= 1e-8
+    ro = oracle_gmres(P.A, b, lambda v: apply_compressed(facu, v), tol=1e-8)
+    assert st["iters"] <= ro.iters + 2, (st, ro.iters)
