@@ -137,6 +137,20 @@ def _src_sha(name):
         return hashlib.sha256(f.read()).hexdigest()[:16]
 
 
+def _ulv_summary(r, steps):
+    """The mixed path with A_ii in HSS form and its ULV solve above the
+    switching level (Alg. 3.2 / 3.3 tier), measured like the main line."""
+    if not r:
+        return None
+    ap_ms = sum(v[0] for v in r["applies"]) / steps
+    ap_n = sum(v[1] for v in r["applies"]) / steps
+    per = r["fstats"]["apply_bytes"]
+    dur = ap_ms / max(ap_n, 1)
+    return {"solves_per_s": r["solves_per_s"], "factor_ms": r["factor_ms"], "solve_ms": r["solve_ms"],
+            "iters": r["iters"], "true_relres": r["true_relres"], "apply_ms": dur, "apply_bytes": per,
+            "apply_gbs": per / (dur / 1e3) / 1e9 if dur > 0 else None}
+
+
 def _dist():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -171,14 +185,14 @@ def run_gpu(a):
             torch.distributed.barrier()
         torch.cuda.synchronize()
 
-    def fopts(prec, timing=False):
+    def fopts(prec, timing=False, ulv=False):
         return ndhss.make_factor_opts(prec=prec, timing=timing, hss_levels=a.hss_levels, eps_hss=WORKLOAD["eps_hss"],
-                                      beta=WORKLOAD["beta"], seed=WORKLOAD["seed"])
+                                      beta=WORKLOAD["beta"], seed=WORKLOAD["seed"], ulv=ulv)
 
-    def one_step(prec, timing):
+    def one_step(prec, timing, ulv=False):
         e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
         e0.record(stream)
-        f = ndhss.ndhss_factor(tree, M.vtype, M.rowptr, M.col, M.vals, fopts(prec, timing), stream=stream)
+        f = ndhss.ndhss_factor(tree, M.vtype, M.rowptr, M.col, M.vals, fopts(prec, timing, ulv), stream=stream)
         e1.record(stream)
         st = ndhss.ndhss_gmres(f, M.rowptr, M.col, M.vals, b, x, tol=WORKLOAD["tol"], stream=stream, timing=timing)
         e2.record(stream)
@@ -186,12 +200,14 @@ def run_gpu(a):
         return f, st, e0.elapsed_time(e1), e1.elapsed_time(e2)
 
     results = {}
-    modes = [("mixed", ndhss.NDHSS_FP32), ("fp64", ndhss.NDHSS_FP64)]
+    modes = [("mixed", ndhss.NDHSS_FP32, False), ("fp64", ndhss.NDHSS_FP64, False)]
+    if a.hss_levels >= 0 and not a.only:
+        modes.append(("mixed_ulv", ndhss.NDHSS_FP32, True))
     if a.only:
         modes = [m for m in modes if m[0] == a.only]
-    for name, prec in modes:
+    for name, prec, ulv in modes:
         for _ in range(a.warmup):
-            f, st, _, _ = one_step(prec, False)
+            f, st, _, _ = one_step(prec, False, ulv)
             del f
         barrier()
         l0 = ndhss.ndhss_kernel_launches()
@@ -200,7 +216,7 @@ def run_gpu(a):
         with Clocks(local) as clk:
             tw = time.time()
             for k in range(a.steps):
-                f, st, tf, ts = one_step(prec, True)
+                f, st, tf, ts = one_step(prec, True, ulv)
                 fms.append(tf)
                 sms.append(ts)
                 its.append(st["iters"])
@@ -309,6 +325,7 @@ def run_gpu(a):
                  "apply_bytes": fp["fstats"]["apply_bytes"]},
         "mixed_over_fp64": {"solves_per_s": mx["solves_per_s"] / fp["solves_per_s"],
                             "factor_speedup": fp["factor_ms"] / mx["factor_ms"]},
+        "ulv": _ulv_summary(results.get("mixed_ulv"), a.steps),
         "apply_gbs": fs["apply_bytes"] / (ap_ms / max(ap_n, 1) / 1e3) / 1e9,
         "e2e": {"value": world * a.steps / e2e_s, "unit": "solves/s", "h2d_bytes_per_step": int(P.b.nbytes),
                 "d2h_bytes_per_step": int(xn.nbytes), "true_relres": relres_e2e},
