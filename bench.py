@@ -39,7 +39,10 @@ WORKLOAD = dict(N=256, p=2, k=40.0, seed=0, leaf=64, tol=1e-8, hss_levels=4, eps
 
 # ncu DRAM traffic of the dominant kernel class, per launch, keyed by the
 # sha256 of the source file it was measured on (null once the source changes)
-NCU_TRAFFIC = {}
+NCU_TRAFFIC = {
+    # profiles/apply_dataflow_helmholtz_p2_256_mixed.md: dram read 549.5 MB + write 11.1 MB per launch
+    ("apply", "ade3e45fff1ddfca"): 560.6e6,
+}
 
 
 def _args():
