@@ -141,8 +141,9 @@ def _src_sha(name):
 
 
 def _ulv_summary(r, steps):
-    """The mixed path with A_ii in HSS form and its ULV solve above the
-    switching level (Alg. 3.2 / 3.3 tier), measured like the main line."""
+    """A side variant of the mixed path measured like the main line: A_ii in
+    HSS form with its ULV solve above the switching level, or the front
+    updates on the TF32 tensor cores."""
     if not r:
         return None
     ap_ms = sum(v[0] for v in r["applies"]) / steps
@@ -204,6 +205,8 @@ def run_gpu(a):
 
     results = {}
     modes = [("mixed", ndhss.NDHSS_FP32, False), ("fp64", ndhss.NDHSS_FP64, False)]
+    if not a.only:
+        modes.append(("tf32", ndhss.NDHSS_FP32_TF32, False))
     if a.hss_levels >= 0 and not a.only:
         modes.append(("mixed_ulv", ndhss.NDHSS_FP32, True))
     if a.only:
@@ -329,6 +332,7 @@ def run_gpu(a):
         "mixed_over_fp64": {"solves_per_s": mx["solves_per_s"] / fp["solves_per_s"],
                             "factor_speedup": fp["factor_ms"] / mx["factor_ms"]},
         "ulv": _ulv_summary(results.get("mixed_ulv"), a.steps),
+        "tf32": _ulv_summary(results.get("tf32"), a.steps),
         "apply_gbs": fs["apply_bytes"] / (ap_ms / max(ap_n, 1) / 1e3) / 1e9,
         "e2e": {"value": world * a.steps / e2e_s, "unit": "solves/s", "h2d_bytes_per_step": int(P.b.nbytes),
                 "d2h_bytes_per_step": int(xn.nbytes), "true_relres": relres_e2e},

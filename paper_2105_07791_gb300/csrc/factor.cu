@@ -24,6 +24,7 @@
 #include <cmath>
 
 #include "factor.cuh"
+#include "tcgen05.cuh"
 
 namespace ndhss {
 namespace {
@@ -370,6 +371,124 @@ gemm_update_kernel(const int32_t* __restrict__ lev, const int32_t* __restrict__ 
     }
 }
 
+// The same update on the TF32 tensor cores (precision NDHSS_FP32_TF32): one
+// CTA of 128 threads per 128 x 128 tile of the real GEMM
+//   complex:  [Re; Im](C Z) = [[Cr, -Ci], [Ci, Cr]] [Zr; Zi]   (rows interleaved:
+//             real row 2 r / 2 r + 1 = Re / Im of front row r, K = 2 kb)
+//   real:     C Z                                              (K = kb)
+// K padded with zeros to a multiple of 8.  A (rows) and B (front columns) are
+// staged K-major in shared memory, kb / 8 kind::tf32 MMAs accumulate in
+// TMEM (FP32), and each thread reads its TMEM lane back for the epilogue
+// M = beta .* M + C Z.  The completion wait is bounded (status TIMEOUT).
+constexpr int TC_COLS = 128;
+constexpr int TC_MAX_WAIT = 1 << 24;
+
+template <typename T>
+__global__ void __launch_bounds__(128)
+tc_update_kernel(const int32_t* __restrict__ lev, const int32_t* __restrict__ node, const int64_t* __restrict__ foff,
+                 T* __restrict__ front, const T* __restrict__ cbuf, const T* __restrict__ zbuf,
+                 const int64_t* __restrict__ woff, int k0, int kb, DevStatus* status) {
+    if constexpr (sizeof(typename Tr<T>::real) != 4) {
+        return;                                         // TF32 applies to the FP32 types only
+    } else {
+    constexpr bool CPLX = Tr<T>::cplx;
+    constexpr int RT = CPLX ? 64 : 128;                 // front rows per tile
+    extern __shared__ __align__(1024) unsigned char tsm[];
+    __shared__ __align__(8) uint64_t mbar;
+    __shared__ uint32_t tmem_holder;
+    const int li = blockIdx.z;
+    const int s = lev[li];
+    const int m_i = nf(node, s, 5);
+    if (k0 >= m_i) return;
+    const int64_t m = m_i + nf(node, s, 7);
+    const int64_t i0 = (int64_t)blockIdx.x * RT, j0 = (int64_t)blockIdx.y * TC_COLS;
+    if (i0 >= m || j0 >= m) return;
+    const int kbp = min(kb, m_i - k0);
+    const int KP = ((CPLX ? 2 * kbp : kbp) + 7) & ~7;
+    const T* C = cbuf + woff[li] * KBMAX;
+    const T* Z = zbuf + woff[li] * KBMAX;
+    T* F = front + foff[s];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    unsigned char* sA = tsm;
+    unsigned char* sB = tsm + 128 * KP * 4;
+    if (tid == 0) tc::mbar_init(&mbar, 1);
+    if (warp == 0) tc::tmem_alloc(&tmem_holder, TC_COLS);
+    for (int q = tid; q < 128 * KP; q += 128) {
+        const int rr = q & 127, kk = q >> 7;
+        float v = 0.0f;
+        if constexpr (CPLX) {
+            const int64_t r = i0 + (rr >> 1);
+            if (r < m && kk < 2 * kbp) {
+                const T c = C[(int64_t)(kk < kbp ? kk : kk - kbp) * m + r];
+                v = (rr & 1) ? (kk < kbp ? c.y : c.x) : (kk < kbp ? c.x : -c.y);
+            }
+        } else {
+            const int64_t r = i0 + rr;
+            if (r < m && kk < kbp) v = C[(int64_t)kk * m + r];
+        }
+        *reinterpret_cast<float*>(sA + tc::core_off(rr, kk, KP)) = v;
+    }
+    for (int q = tid; q < 128 * KP; q += 128) {
+        const int kk = q % KP, nn = q / KP;
+        const int64_t n = j0 + nn;
+        float v = 0.0f;
+        if constexpr (CPLX) {
+            if (n < m && kk < 2 * kbp) {
+                const T z = Z[n * KBMAX + (kk < kbp ? kk : kk - kbp)];
+                v = kk < kbp ? z.x : z.y;
+            }
+        } else {
+            if (n < m && kk < kbp) v = Z[n * KBMAX + kk];
+        }
+        *reinterpret_cast<float*>(sB + tc::core_off(nn, kk, KP)) = v;
+    }
+    tc::fence_smem_async();
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+    const uint32_t tmem = tmem_holder;
+    if (tid == 0) {
+        const uint32_t idesc = tc::idesc_tf32(128, TC_COLS);
+        const uint32_t sbo = (uint32_t)(KP / 4) * 128u;
+        for (int ks = 0; ks < KP / 8; ++ks)
+            tc::mma_tf32(tmem, tc::smem_desc(tc::smem_u32(sA) + ks * 256u, 128u, sbo),
+                         tc::smem_desc(tc::smem_u32(sB) + ks * 256u, 128u, sbo), idesc, ks > 0 ? 1u : 0u);
+        tc::commit(&mbar);
+    }
+    if (!tc::mbar_wait(&mbar, 0, TC_MAX_WAIT)) {
+        if (tid == 0 && atomicCAS(&status->code, 0, (int)NDHSS_ERR_TIMEOUT) == 0) status->node = nf(node, s, 0);
+    } else {
+        tc::fence_after();
+        const int row = warp * 32 + lane;                  // TMEM lane = row of the real GEMM
+        const int64_t r = CPLX ? i0 + (row >> 1) : i0 + row;
+        const bool pi = r >= k0 && r < k0 + kbp;
+        for (int c0 = 0; c0 < TC_COLS; c0 += 8) {
+            float v[8];
+            tc::tmem_ld8(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int64_t n = j0 + c0 + u;
+                const bool pj = n >= k0 && n < k0 + kbp;
+                if constexpr (CPLX) {
+                    const float other = __shfl_xor_sync(0xffffffffu, v[u], 1);
+                    if ((u & 1) != (lane & 1) || r >= m || n >= m) continue;   // even lanes even columns
+                    const T d = (lane & 1) ? T{other, v[u]} : T{v[u], other};
+                    T* dst = F + n * m + r;
+                    *dst = (pi || pj) ? d : (*dst + d);
+                } else {
+                    if (r >= m || n >= m) continue;
+                    T* dst = F + n * m + r;
+                    *dst = (pi || pj) ? v[u] : (*dst + v[u]);
+                }
+            }
+        }
+    }
+    tc::fence_before();
+    __syncthreads();
+    if (warp == 0) tc::tmem_dealloc(tmem, TC_COLS);
+    }
+}
+
 // sigma(j) = original row of A_ii now at row j, from the interchange record
 __global__ void finalize_sigma_kernel(const int32_t* __restrict__ lev, const int32_t* __restrict__ node,
                                       const int32_t* __restrict__ ipiv, int32_t* __restrict__ sigma) {
@@ -404,6 +523,8 @@ ndhss_status set_smem_attrs() {
                                      panel_factor_kernel<T, 8>, panel_factor_kernel<T, 16>, panel_factor_kernel<T, 32>};
     for (auto k : kernels)
         NDHSS_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PANEL_SMEM_MAX));
+    NDHSS_CUDA_TRY(cudaFuncSetAttribute(tc_update_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        2 * 128 * 2 * KBMAX * 4));
     return NDHSS_OK;
 }
 
@@ -564,9 +685,18 @@ ndhss_status factor_run(FactorData& F, const Tree& t, const V* d_vals, const int
             NDHSS_LAUNCH_CHECK("panel_prep_kernel");
             tm.end(3);
             tm.begin();
-            gemm_update_kernel<T><<<dim3(gt, gt, L), 256, 0, st>>>(lev, F.d_node, F.d_foff, front, d_cbuf, d_zbuf, woff,
-                                                                 (int)k0, kb);
-            NDHSS_LAUNCH_CHECK("gemm_update_kernel");
+            if (F.prec == NDHSS_FP32_TF32 && sizeof(typename Tr<T>::real) == 4) {
+                const int rt = Tr<T>::cplx ? 64 : 128;
+                const int kp = ((Tr<T>::cplx ? 2 * kb : kb) + 7) & ~7;
+                tc_update_kernel<T><<<dim3((unsigned)((mmax + rt - 1) / rt), (unsigned)((mmax + TC_COLS - 1) / TC_COLS), L),
+                                      128, (size_t)2 * 128 * kp * 4, st>>>(lev, F.d_node, F.d_foff, front, d_cbuf, d_zbuf,
+                                                                         woff, (int)k0, kb, d_status);
+                NDHSS_LAUNCH_CHECK("tc_update_kernel");
+            } else {
+                gemm_update_kernel<T><<<dim3(gt, gt, L), 256, 0, st>>>(lev, F.d_node, F.d_foff, front, d_cbuf, d_zbuf, woff,
+                                                                     (int)k0, kb);
+                NDHSS_LAUNCH_CHECK("gemm_update_kernel");
+            }
             tm.end(4);
             F.launches += 3;
             for (int s2 : nodes) {
@@ -782,6 +912,8 @@ static ndhss_status factor_impl(const ndhss_tree* th, int32_t vtype, const int32
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
         if (e != cudaSuccess) {
             rc = set_error(NDHSS_ERR_CUDA, "ndhss_factor: %s", cudaGetErrorString(e));
+        } else if (hs.code == (int)NDHSS_ERR_TIMEOUT) {
+            rc = set_error(NDHSS_ERR_TIMEOUT, "ndhss_factor: a tensor-core update of level %d did not complete", hs.node);
         } else if (hs.code != 0) {
             rc = set_error((ndhss_status)hs.code, "ndhss_factor: zero pivot in A_ii of node %d (level %d)", hs.node,
                            t.level(hs.node));

@@ -62,8 +62,10 @@ def _rel(a, b):
     return np.linalg.norm(a - b) / (nb if nb > 0 else 1.0)
 
 
-@pytest.mark.parametrize("prec,tol", [(0, 1e-9), (1, 2e-3)])
+@pytest.mark.parametrize("prec,tol", [(0, 1e-9), (1, 2e-3), (2, 5e-2)])
 def test_factor_blocks_match_oracle(nd, case, prec, tol):
+    """FP64 to rounding; FP32 and the TF32 tensor-core update (10-bit
+    mantissa products, FP32 accumulation) by their arithmetic's tolerance."""
     f = _gpu_factor(nd, case, prec)
     T, fac = case["T"], case["fac"]
     nodes = list(range(T.nnodes))
@@ -92,7 +94,7 @@ def test_factor_independent_of_pivot_block_width(nd, case, panel):
     assert _rel(nd.ndhss_factor_get_block(f, s, 3, mi, mb), fac.S[s]) <= 1e-9
 
 
-@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("prec", [0, 1, 2])
 def test_apply_matches_oracle_and_direct_solve(nd, case, prec):
     P, fac = case["P"], case["fac"]
     f = _gpu_factor(nd, case, prec)
@@ -104,7 +106,9 @@ def test_apply_matches_oracle_and_direct_solve(nd, case, prec):
     torch.cuda.synchronize()
     yo = apply_inverse(fac, b)
     yd = spla.spsolve(P.A.tocsc(), b)
-    tol = 1e-10 if prec == 0 else 1e-3
+    # TF32 products carry a 10-bit mantissa (unit roundoff 2^-11 ~ 4.9e-4); the
+    # fronts' condition numbers (~1e2 on C1) scale that into the inverse
+    tol = {0: 1e-10, 1: 1e-3, 2: 1e-1}[prec]
     assert _rel(y.cpu().numpy(), yo) <= tol
     assert _rel(y.cpu().numpy(), yd) <= tol
     # host buffers through the same entry point
@@ -127,7 +131,7 @@ def test_spmv_matches_scipy(nd, case):
     assert _rel(yd.cpu().numpy(), ref) <= 1e-14
 
 
-@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("prec", [0, 1, 2])
 def test_gmres_solution_and_iterations(nd, case, prec):
     P, fac = case["P"], case["fac"]
     M = case["M"]
@@ -140,7 +144,13 @@ def test_gmres_solution_and_iterations(nd, case, prec):
     assert st["converged"] and st["true_relres"] <= 1e-8
     assert np.linalg.norm(b - P.A @ x) / np.linalg.norm(b) <= 1e-8
     ro = oracle_gmres(P.A, b, lambda v: apply_inverse(fac, v), tol=1e-8)
-    assert st["iters"] <= ro.iters + 2, (st, ro.iters)
+    if prec <= 1:
+        assert st["iters"] <= ro.iters + 2, (st, ro.iters)
+    else:
+        # TF32 products leave a preconditioner accurate to ~1e-2 (10-bit mantissa):
+        # the float64 restarts refine it, at a few more iterations than the exact
+        # oracle factor needs
+        assert st["iters"] <= ro.iters + 9, (st, ro.iters)
     xdir = spla.spsolve(P.A.tocsc(), b)
     assert _rel(x, ro.x) <= (1e-8 if prec == 0 else 1e-6)
     assert _rel(x, xdir) <= (1e-8 if prec == 0 else 1e-6)
