@@ -162,6 +162,33 @@ def _dist():
     return world, rank, local
 
 
+# ------------------------------------------------------- replicas (N > 1)
+# The path does not shard across GPUs here: every rank factors and solves an
+# independent instance (seed + rank); no collective touches the data path.
+# Ranks meet only to time: max over ranks of each timed total, and the
+# whole-job rate counts every rank's solves.
+
+def replica_seed(rank: int) -> int:
+    return WORKLOAD["seed"] + rank
+
+
+def max_over_ranks(values, device):
+    """Element-wise max of a list of floats over the initialised process group
+    (identity on one rank)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return [float(v) for v in values]
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(v) for v in t.cpu()]
+
+
+def whole_job_rate(world: int, steps: int, max_seconds: float) -> float:
+    """Solves per second of the whole job: all ranks' solves over the slowest rank's time."""
+    return world * steps / max_seconds
+
+
 # ------------------------------------------------------------------ GPU arm
 def run_gpu(a):
     import numpy as np
@@ -176,7 +203,7 @@ def run_gpu(a):
     torch.cuda.set_device(local)
     build.build()
     ndhss.load()
-    P = _workload(a.N, WORKLOAD["seed"] + rank)          # replicas: an independent instance per rank
+    P = _workload(a.N, replica_seed(rank))              # replicas: an independent instance per rank
     tree = ndhss.ndhss_build_tree(P.coords, P.A.indptr, P.A.indices, WORKLOAD["leaf"])
     M = ndhss.DeviceCSR(P.A)
     b = torch.from_numpy(np.ascontiguousarray(P.b)).cuda()
@@ -233,13 +260,9 @@ def run_gpu(a):
             barrier()
             wall = time.time() - tw
         launches = ndhss.ndhss_kernel_launches() - l0
-        tot_f, tot_s = sum(fms), sum(sms)
-        if world > 1:
-            t = torch.tensor([tot_f, tot_s], device="cuda", dtype=torch.float64)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            tot_f, tot_s = float(t[0]), float(t[1])
+        tot_f, tot_s = max_over_ranks([sum(fms), sum(sms)], "cuda")
         results[name] = dict(kmax=fstats["kmax"], factor_ms=tot_f / a.steps, solve_ms=tot_s / a.steps,
-                             solves_per_s=world * a.steps / (tot_s / 1e3), iters=int(statistics.median(its)),
+                             solves_per_s=whole_job_rate(world, a.steps, tot_s / 1e3), iters=int(statistics.median(its)),
                              iters_all=its, true_relres=max(res), launches=launches, clocks=clk.summary(),
                              fstats=fstats, applies=applies, wall_s=wall)
 
@@ -261,11 +284,7 @@ def run_gpu(a):
     for _ in range(a.steps):
         ndhss.ndhss_gmres(f, M.rowptr, M.col, M.vals, bn, xn, tol=WORKLOAD["tol"], stream=stream)
     barrier()
-    e2e_s = time.perf_counter() - t0
-    if world > 1:
-        t = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_s = float(t[0])
+    e2e_s = max_over_ranks([time.perf_counter() - t0], "cuda")[0]
     relres_e2e = float(np.linalg.norm(P.b - P.A @ xn) / np.linalg.norm(P.b))
     del f
 
@@ -334,7 +353,7 @@ def run_gpu(a):
         "ulv": _ulv_summary(results.get("mixed_ulv"), a.steps),
         "tf32": _ulv_summary(results.get("tf32"), a.steps),
         "apply_gbs": fs["apply_bytes"] / (ap_ms / max(ap_n, 1) / 1e3) / 1e9,
-        "e2e": {"value": world * a.steps / e2e_s, "unit": "solves/s", "h2d_bytes_per_step": int(P.b.nbytes),
+        "e2e": {"value": whole_job_rate(world, a.steps, e2e_s), "unit": "solves/s", "h2d_bytes_per_step": int(P.b.nbytes),
                 "d2h_bytes_per_step": int(xn.nbytes), "true_relres": relres_e2e},
         "gpu_launches": mx["launches"],
         "roofline": roof,
