@@ -334,3 +334,50 @@ def helmholtz_impedance(N: int, p: int, k: float, seed: int = 0, *, nsrc: int = 
     return Problem(A=_finish(A), b=np.ascontiguousarray(b), coords=lattice.astype(np.int32),
                    name=f"helmholtz_p{p}_{N}x{N}_k{k:g}",
                    meta=dict(N=N, p=p, k=k, seed=seed, xy=xy, h=1.0 / N, sources=meta_src))
+
+
+def helmholtz_blocks(N: int, k: float, m_blocks, *, p: int = 1, seed: int = 0, nsrc: int = 1,
+                     width: float = 0.02, src_xy=None) -> Problem:
+    """Helmholtz with squared slowness m piecewise constant on an nb x nb grid
+    of blocks (``m_blocks`` [nb, nb], block (i, j) covering cells with
+    i = a * nb // N, j = b * nb // N), impedance on all sides, Gaussian
+    sources (at ``src_xy`` [nsrc, 2] or drawn from ``seed``).
+
+    Besides A(m) and b, meta holds what the derivative of A with respect to
+    one block's m needs:  dA/dm_j = -k^2 sum_{e in j} M_e - i k / (2 sqrt(m_j))
+    sum_{edges in j} E_e, with ``elem`` / ``Me`` the element DOFs and unit
+    mass matrices, ``eblk`` their blocks, ``edges`` / ``Ee`` / ``edge_blk``
+    the boundary edges' DOFs, unit edge mass matrices and blocks.
+    """
+    mb = np.asarray(m_blocks, dtype=np.float64)
+    nb = mb.shape[0]
+    elem, cell, lattice, xy, Lx, Ly = _mesh(N, N, p)
+    eblk = (cell[:, 0] * nb // N) * nb + (cell[:, 1] * nb // N)
+    m_e = mb.ravel()[eblk]
+    if src_xy is None:
+        src_xy = np.random.default_rng(seed).uniform(0.1, 0.9, size=(nsrc, 2))
+    src_xy = np.asarray(src_xy, dtype=np.float64)
+    P = helmholtz_impedance(N, p, k, seed, slowness2=m_e, f=lambda x, y: 0.0 * x)     # b set below
+    _, M, *_ = assemble(N, N, p)
+    F = np.stack([gaussian_source(xy, src_xy[s], width) for s in range(src_xy.shape[0])], axis=1)
+    b = (M @ F).astype(np.complex128)
+    # element data
+    xi, eta, wq = _gauss_triangle(4)
+    val, _ = _basis(p, xi, eta)
+    X = xy[elem]
+    det = (X[:, 1, 0] - X[:, 0, 0]) * (X[:, 2, 1] - X[:, 0, 1]) - (X[:, 2, 0] - X[:, 0, 0]) * (X[:, 1, 1] - X[:, 0, 1])
+    Me = np.einsum("q,qa,qb->ab", wq, val, val)[None, :, :] * np.abs(det)[:, None, None]
+    edges, side = _boundary_edges(N, N, p, Lx)
+    ecell = _edge_cells(N, N)
+    edge_blk = (ecell[:, 0] * nb // N) * nb + (ecell[:, 1] * nb // N)
+    t, w = np.polynomial.legendre.leggauss(4)
+    t = 0.5 * (t + 1.0)
+    w = 0.5 * w
+    eb = _edge_basis(p, t)
+    Em = np.einsum("q,qa,qb->ab", w, eb, eb)
+    Ee = Em[None] * np.full(edges.shape[0], 1.0 / N)[:, None, None]
+    P.b = np.ascontiguousarray(b[:, 0] if b.shape[1] == 1 else b)
+    P.name = f"helmholtz_blocks_p{p}_{N}x{N}_k{k:g}_nb{nb}"
+    P.meta.update(m_blocks=mb, nb=nb, elem=elem, Me=Me, eblk=eblk, edges=edges, Ee=Ee, edge_blk=edge_blk,
+                  sources=src_xy, k=k)
+    return P
