@@ -271,6 +271,29 @@ ndhss_status ndhss_apply(const ndhss_factorization* f, int32_t nrhs, const void*
 ndhss_status ndhss_apply_noalloc(const ndhss_factorization* f, const void* d_x, void* d_y, void* stream);
 
 /*
+ * ndhss_elem_qform -- per group g of elements (elements goff[g] .. goff[g+1]-1):
+ *     q[g] = sum_e sum_{a,b} conj(lam[idx[e][a]]) M_e[a][b] x[idx[e][b]]
+ * the quadratic forms of the adjoint-state gradient of a misfit with respect
+ * to piecewise-constant coefficients (dJ/dm_j = -Re(lam^H dA/dm_j x) with
+ * dA/dm_j assembled from the element matrices of block j; Helmholtz model of
+ * Sec. 4, Eq. 4.2; the paper itself has no adjoint).  No counterpart in the
+ * paper otherwise.
+ *   ngroups    number of groups (output length)
+ *   d_goff     device int32 [ngroups + 1], element offsets of each group
+ *              (elements sorted by group)
+ *   nloc       DOFs per element
+ *   d_idx      device int32 [n_elem x nloc], row-major: the elements' DOFs
+ *   d_mats     device float64 [n_elem x nloc x nloc], row-major real element
+ *              matrices
+ *   d_lam, d_x device complex128 vectors indexed by DOF
+ *   d_q        device complex128 [ngroups], overwritten
+ * Stream-ordered; deterministic (fixed summation order).  INVALID_ARG for
+ * NULL pointers, ngroups < 0 or nloc < 1.
+ */
+ndhss_status ndhss_elem_qform(int32_t ngroups, const int32_t* d_goff, int32_t nloc, const int32_t* d_idx,
+                              const double* d_mats, const void* d_lam, const void* d_x, void* d_q, void* stream);
+
+/*
  * ndhss_testing_stall_apply -- failure-detection hook for tests (no
  * counterpart in the paper).  Raises the completion requirement of the
  * root's diagonal step by one, a count that no task will ever reach, so the

@@ -25,7 +25,7 @@ STATUS = {0: "OK", 1: "INVALID_ARG", 2: "OOM", 3: "SINGULAR", 4: "RANK_CAP", 5: 
 EXPORTED = ("ndhss_version", "ndhss_last_error", "ndhss_kernel_launches", "ndhss_build_tree", "ndhss_tree_sizes", "ndhss_tree_export",
             "ndhss_tree_destroy", "ndhss_factor", "ndhss_factor_stats_get", "ndhss_factor_get_block",
             "ndhss_factor_destroy", "ndhss_apply", "ndhss_apply_noalloc", "ndhss_spmv", "ndhss_gmres",
-            "ndhss_testing_stall_apply")
+            "ndhss_testing_stall_apply", "ndhss_elem_qform")
 
 
 class NdhssError(RuntimeError):
@@ -99,6 +99,7 @@ def load(path: str | None = None):
         "ndhss_apply": (I32, [P, I32, P, I64, P, I64, V]),
         "ndhss_apply_noalloc": (I32, [P, P, P, V]),
         "ndhss_testing_stall_apply": (I32, [P]),
+        "ndhss_elem_qform": (I32, [I32, P, I32, P, P, P, P, P, V]),
         "ndhss_spmv": (I32, [I32, I32, P, P, P, P, P, V]),
         "ndhss_gmres": (I32, [P, P, P, P, I32, P, I64, P, I64, C.POINTER(GmresOpts), C.POINTER(GmresStats), V]),
     }
@@ -252,6 +253,13 @@ def ndhss_apply_noalloc(f: Factor, d_x, d_y, stream=None):
 def ndhss_testing_stall_apply(f: Factor):
     """Failure-detection hook: makes the next apply's bounded waits run out."""
     _check(load().ndhss_testing_stall_apply(f.handle))
+
+
+def ndhss_elem_qform(d_goff, nloc: int, d_idx, d_mats, d_lam, d_x, d_q, stream=None):
+    """q[g] = sum over the elements of group g of conj(lam_e)^T M_e x_e (device tensors)."""
+    _check(load().ndhss_elem_qform(int(d_goff.numel()) - 1, _ptr(d_goff), int(nloc), _ptr(d_idx), _ptr(d_mats),
+                                   _ptr(d_lam), _ptr(d_x), _ptr(d_q), _stream(stream)))
+    return d_q
 
 
 def ndhss_spmv(n: int, vtype: int, d_rowptr, d_col, d_vals, d_x, d_y, stream=None):

@@ -1,0 +1,85 @@
+"""Gradients through the GPU solve (autograd Function with the adjoint
+solve on the same factor) against the oracle's adjoint gradient (sparse
+direct solves), central finite differences of the misfit, and the
+right-hand-side gradient A^{-H} g."""
+import numpy as np
+import pytest
+import scipy.sparse.linalg as spla
+
+from ndhss_inputs.fem import helmholtz_blocks
+from oracle.adjoint import misfit_and_gradient
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def nd():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2105_07791_gb300 import build, ndhss
+    build.build()
+    ndhss.load()
+    return ndhss
+
+
+def _problem(N=24, nb=4, k=10.0, seed=0):
+    rng = np.random.default_rng(seed)
+    m = rng.uniform(0.3, 1.0, (nb, nb))
+    src = np.array([[0.3, 0.2], [0.7, 0.25]])
+    P = helmholtz_blocks(N, k, m, src_xy=src)
+    rec = np.nonzero(np.abs(P.meta["xy"][:, 1] - 0.75) < 1e-12)[0][::2]
+    Pt = helmholtz_blocks(N, k, m + 0.05 * rng.uniform(-1, 1, m.shape), src_xy=src)
+    d = np.stack([spla.spsolve(Pt.A.tocsc(), Pt.b[:, s])[rec] for s in range(2)], axis=1)
+    return P, m, src, rec, d, k, N
+
+
+def _model(nd, P, k, N, src, prec, hss_levels):
+    from paper_2105_07791_gb300.autograd import HelmholtzBlockModel
+    tree = nd.ndhss_build_tree(P.coords, P.A.indptr, P.A.indices, 64)
+    nb = P.meta["nb"]
+    opts = nd.make_factor_opts(prec=prec, hss_levels=hss_levels)
+    return HelmholtzBlockModel(tree, lambda mb: helmholtz_blocks(N, k, mb.reshape(nb, nb), src_xy=src).A, k,
+                               P.meta["elem"], P.meta["Me"], P.meta["eblk"], P.meta["edges"], P.meta["Ee"],
+                               P.meta["edge_blk"], nb * nb, opts=opts, tol=1e-11)
+
+
+def _misfit(nd, model, m_t, B, rec, d):
+    from paper_2105_07791_gb300.autograd import HelmholtzSolve
+    X = HelmholtzSolve.apply(m_t, B, model)
+    r = X[torch.from_numpy(rec).cuda()] - torch.from_numpy(d).cuda()
+    return 0.5 * (r.abs() ** 2).sum(), X
+
+
+@pytest.mark.parametrize("prec,hss_levels", [(0, -1), (1, -1), (1, 2)])
+def test_coefficient_gradient_matches_oracle_and_differences(nd, prec, hss_levels):
+    P, m, src, rec, d, k, N = _problem()
+    model = _model(nd, P, k, N, src, prec, hss_levels)
+    m_t = torch.tensor(m.ravel(), dtype=torch.float64, requires_grad=True)
+    B = torch.from_numpy(np.ascontiguousarray(P.b)).cuda().requires_grad_(True)
+    J, X = _misfit(nd, model, m_t, B, rec, d)
+    J.backward()
+    g = m_t.grad.numpy()
+    Jo, go = misfit_and_gradient(P, rec, d)
+    assert abs(J.item() - Jo) <= 1e-8 * Jo
+    assert np.linalg.norm(g - go) <= 1e-5 * np.linalg.norm(go), np.linalg.norm(g - go) / np.linalg.norm(go)
+    # right-hand-side gradient: A^{-H} R^T (R x - d), column by column
+    Xh = X.detach().cpu().numpy()
+    for s in range(2):
+        gs = np.zeros(P.A.shape[0], dtype=np.complex128)
+        gs[rec] = Xh[rec, s] - d[:, s]
+        lam = np.conj(spla.spsolve(P.A.tocsc(), np.conj(gs)))
+        gb = B.grad[:, s].cpu().numpy()
+        assert np.linalg.norm(gb - lam) <= 1e-6 * np.linalg.norm(lam)
+    # central differences of the GPU misfit on a boundary and an interior block
+    for j in (0, 5):
+        h = 1e-4 * m.ravel()[j]
+        vals = []
+        for sgn in (1, -1):
+            mp = m.ravel().copy()
+            mp[j] += sgn * h
+            with torch.no_grad():
+                Jp, _ = _misfit(nd, model, torch.tensor(mp), B.detach(), rec, d)
+            vals.append(Jp.item())
+        fd = (vals[0] - vals[1]) / (2 * h)
+        assert abs(fd - g[j]) <= 1e-5 * np.abs(go).max(), (j, fd, g[j])
