@@ -83,3 +83,45 @@ def test_coefficient_gradient_matches_oracle_and_differences(nd, prec, hss_level
             vals.append(Jp.item())
         fd = (vals[0] - vals[1]) / (2 * h)
         assert abs(fd - g[j]) <= 1e-5 * np.abs(go).max(), (j, fd, g[j])
+
+
+@pytest.mark.slow
+def test_c5_sized_gradient_matches_oracle():
+    """The adjoint workload's full size: P1 on 512 x 512 cells, k = 80,
+    squared slowness on 32 x 32 blocks ~ U[0.3, 1], 16 sources and receivers
+    on the line y = 0.9, data from a seeded perturbed model; compressed FP32
+    factor with float64 GMRES.  Gradient of all 1024 blocks against the
+    oracle's adjoint gradient (sparse direct) to 1e-5."""
+    import time
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2105_07791_gb300 import build, ndhss
+    build.build()
+    ndhss.load()
+    N, k, nb, ns = 512, 80.0, 32, 16
+    rng = np.random.default_rng(5)
+    m = rng.uniform(0.3, 1.0, (nb, nb))
+    y_line = round(0.9 * N) / N
+    src = np.stack([(np.arange(ns) + 0.5) / ns, np.full(ns, y_line)], axis=1)
+    P = helmholtz_blocks(N, k, m, src_xy=src)
+    xy = P.meta["xy"]
+    rec = np.array([np.argmin((xy[:, 0] - x) ** 2 + (xy[:, 1] - y_line) ** 2) for x in src[:, 0]])
+    Pt = helmholtz_blocks(N, k, m + 0.05 * rng.uniform(-1, 1, m.shape), src_xy=src)
+    lu = spla.splu(Pt.A.tocsc())
+    d = np.stack([lu.solve(Pt.b[:, s])[rec] for s in range(ns)], axis=1)
+    model = _model(ndhss, P, k, N, src, 1, 4)
+    m_t = torch.tensor(m.ravel(), dtype=torch.float64, requires_grad=True)
+    B = torch.from_numpy(np.ascontiguousarray(P.b)).cuda()
+    torch.cuda.synchronize()
+    t0 = time.time()
+    J, X = _misfit(ndhss, model, m_t, B, rec, d)
+    J.backward()
+    torch.cuda.synchronize()
+    t_gpu = time.time() - t0
+    t0 = time.time()
+    Jo, go = misfit_and_gradient(P, rec, d)
+    t_cpu = time.time() - t0
+    g = m_t.grad.numpy()
+    print(f"C5 gradient: GPU {t_gpu:.2f} s (factor + 16 + 16 solves + assembly), oracle {t_cpu:.2f} s")
+    assert abs(J.item() - Jo) <= 1e-7 * Jo
+    assert np.linalg.norm(g - go) <= 1e-5 * np.linalg.norm(go), np.linalg.norm(g - go) / np.linalg.norm(go)
