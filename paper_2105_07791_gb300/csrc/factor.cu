@@ -724,6 +724,12 @@ ndhss_status factor_run(FactorData& F, const Tree& t, const V* d_vals, const int
             cudaFreeAsync(d_aii, st);
         }
     }
+    if (!F.lr_pending.empty()) {
+        tm.begin();
+        ndhss_status rc2 = hss_lowrank_pending(F, o, st);
+        if (rc2 != NDHSS_OK) return rc2;
+        tm.end(6);
+    }
     return NDHSS_OK;
 }
 

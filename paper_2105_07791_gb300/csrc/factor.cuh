@@ -54,10 +54,12 @@ struct FactorData {
     int32_t* d_apply_err = nullptr;
 
     // compressed tier (Alg. 3.4 above the switching level): low-rank R ~ X R(J, :)
-    // per node: X (m_i x k, ld m_i) followed by RJ (k x m_b, ld k), in one
-    // device buffer per tree level
+    // per node: X (m_i x k, ld m_i) followed by R(J, :)^T (m_b x k, ld m_b), in
+    // device buffers of the compression rounds; lr_pending queues the fronts
+    // whose R waits for the batch at the end of the factorization
     int32_t L_hss = -1;                       // levels <= L_hss compress S; < L_hss also R
     std::vector<void*> lr_bufs;
+    std::vector<int32_t> lr_pending;
     std::vector<uint64_t> lr_ptr;             // per node, 0 = dense R
     std::vector<int32_t> lr_k;
     uint64_t* d_lr_ptr = nullptr;
@@ -116,6 +118,9 @@ constexpr int LR_CHUNK = 256;    // input rows per low-rank dot task
 // just been eliminated densely.  Defined in hss.cu.
 ndhss_status hss_compress_level(FactorData& F, const Tree& t, int level, const ndhss_factor_opts& o,
                                 cudaStream_t st);
+// Low-rank compression of the Gauss transforms R queued by hss_compress_level,
+// every level in one batch.  Defined in hss.cu.
+ndhss_status hss_lowrank_pending(FactorData& F, const ndhss_factor_opts& o, cudaStream_t st);
 // Compress the interior blocks (already gathered in HSS order into aii,
 // node s's block at aii_off[s], ld m_i) of the ULV fronts of tree level
 // `level` and ULV-factor them.  Defined in hss.cu.

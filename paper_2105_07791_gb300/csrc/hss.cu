@@ -832,6 +832,27 @@ ndhss_status hss_matvec_run(const std::vector<HNode>& nodes, const std::vector<c
 }
 
 // One compression problem set (all S blocks, or all R blocks, of a level).
+// One retired low-rank problem: X (n x k, ld ldx) and R(J, :) (k x nc, ld ldr)
+// go to dst as X (ld n) followed by R(J, :)^T (nc x k, ld nc).
+struct LrOut {
+    const void* X;
+    const void* RJ;
+    void* dst;
+    int64_t ldx, ldr;
+    int n, nc, k, pad;
+};
+
+template <typename T>
+__global__ void __launch_bounds__(256) lr_out_kernel(const LrOut* __restrict__ jobs) {
+    const LrOut j = jobs[blockIdx.x];
+    const T* X = static_cast<const T*>(j.X);
+    const T* RJ = static_cast<const T*>(j.RJ);
+    T* d = static_cast<T*>(j.dst);
+    const int64_t nx = (int64_t)j.n * j.k, nr = (int64_t)j.nc * j.k;
+    for (int64_t q = threadIdx.x; q < nx; q += blockDim.x) d[q] = X[(q / j.n) * j.ldx + q % j.n];
+    for (int64_t q = threadIdx.x; q < nr; q += blockDim.x) d[nx + q] = RJ[(q % j.nc) * j.ldr + q / j.nc];
+}
+
 struct Problem {
     int node;          // tree node
     int n, ncol;       // rows and columns of the block
@@ -996,13 +1017,13 @@ ndhss_status ulv_factor_nodes(const std::vector<UlvIn>& in, FactorData& F, cudaS
 // written to `lr_out` (per problem: X m_i x k then RJ k x m_b), ranks to kout.
 template <typename T>
 ndhss_status compress_problems(std::vector<Problem>& probs, bool lowrank, const ndhss_factor_opts& o,
-                               std::vector<int>& kout, std::vector<std::vector<T>>* lr_host, FactorData& F,
+                               std::vector<int>& kout, std::vector<uint64_t>* lr_dev, FactorData& F,
                                cudaStream_t st, bool ulv = false) {
     const int r = std::max(o.r, 1), k0 = std::max(o.k0, 1), beta = std::max(o.beta, 1);
     const int rank_cap = std::max(o.rank_cap, 1);
     const double eps = o.eps_hss;
     kout.assign(probs.size(), 0);
-    if (lr_host) lr_host->assign(probs.size(), {});
+    if (lr_dev) lr_dev->assign(probs.size(), 0);
     std::vector<int> active(probs.size());
     for (size_t i = 0; i < probs.size(); ++i) active[i] = (int)i;
     std::vector<double> prev_err(probs.size(), INFINITY);
@@ -1226,27 +1247,39 @@ ndhss_status compress_problems(std::vector<Problem>& probs, bool lowrank, const 
         // finalize the retired problems
         if (!done.empty()) {
             if (lowrank) {
+                // X (n x k, ld n) then R(J, :)^T (ncol x k, ld ncol) of every retired
+                // problem, gathered on the device into one buffer of this round
+                std::vector<LrOut> jobs;
+                std::vector<int64_t> offs;
+                int64_t tot = 0;
                 for (int i : done) {
-                    const int a = active[i];
                     const int k = hk[fr[i].root];
                     const HNode& nd = nodes[fr[i].root];
-                    kout[a] = k;
-                    auto& out = (*lr_host)[a];
-                    const size_t n = fr[i].n, nc = fr[i].ncol;
-                    out.resize(n * k + nc * k);
-                    std::vector<T> rj((size_t)k * nc);
-                    // X (n x k, ld n) then R(J, :)^T (ncol x k, ld ncol)
+                    kout[active[i]] = k;
+                    offs.push_back(tot);
                     if (k > 0) {
-                        HSS_TRY(cudaMemcpy2DAsync(out.data(), n * sizeof(T), ws.p + nd.o_x, (size_t)nd.rows_cap * sizeof(T),
-                                                  n * sizeof(T), k, cudaMemcpyDeviceToHost, st));
-                        HSS_TRY(cudaMemcpy2DAsync(rj.data(), (size_t)k * sizeof(T), fr[i].RJ, (size_t)kcap * sizeof(T),
-                                                  (size_t)k * sizeof(T), nc, cudaMemcpyDeviceToHost, st));
-                        HSS_TRY(cudaStreamSynchronize(st));
-                        for (size_t j = 0; j < nc; ++j)
-                            for (int aa = 0; aa < k; ++aa) out[n * k + j + (size_t)aa * nc] = rj[j * k + aa];
+                        jobs.push_back({ws.p + nd.o_x, fr[i].RJ, nullptr, nd.rows_cap, kcap, (int)fr[i].n,
+                                        (int)fr[i].ncol, k, 0});
+                        jobs.back().dst = reinterpret_cast<void*>(tot);
                     }
+                    tot += ((int64_t)fr[i].n + fr[i].ncol) * k;
                 }
-                HSS_TRY(cudaStreamSynchronize(st));
+                void* buf = nullptr;
+                if (pool_malloc_async(&buf, (size_t)std::max<int64_t>(tot, 1) * sizeof(T), st) != cudaSuccess) {
+                    cudaGetLastError();
+                    return set_error(NDHSS_ERR_OOM, "hss: low-rank storage");
+                }
+                F.lr_bufs.push_back(buf);
+                F.dev_bytes += tot * (int64_t)sizeof(T);
+                for (size_t q = 0; q < done.size(); ++q)
+                    (*lr_dev)[active[done[q]]] = reinterpret_cast<uint64_t>(static_cast<T*>(buf) + offs[q]);
+                for (auto& j : jobs) j.dst = static_cast<T*>(buf) + reinterpret_cast<int64_t>(j.dst);
+                if (!jobs.empty()) {
+                    DeviceVec<LrOut> dj(st);
+                    HSS_TRY(dj.upload(jobs, st));
+                    lr_out_kernel<T><<<(unsigned)jobs.size(), 256, 0, st>>>(dj.p);
+                    NDHSS_LAUNCH_CHECK("lr_out_kernel");
+                }
             } else if (ulv) {
                 // HSS generators of the retired blocks into a ULV factorization (the
                 // blocks themselves stay as they are)
@@ -1449,7 +1482,7 @@ template <typename T>
 ndhss_status compress_level_impl(FactorData& F, const Tree& t, int level, const ndhss_factor_opts& o, cudaStream_t st) {
     T* base = static_cast<T*>(F.d_front);
     const int beta = std::max(o.beta, 1);
-    std::vector<Problem> sp, rp;
+    std::vector<Problem> sp;
     for (int s : F.levels[level]) {
         const int64_t mi = F.m_i(s), mb = F.m_b(s), m = mi + mb;
         T* Fs = base + F.foff[s];
@@ -1459,39 +1492,40 @@ ndhss_status compress_level_impl(FactorData& F, const Tree& t, int level, const 
             for (int q = 0; q < mb; ++q) top += (t.emap[t.b_off(s) + q] < t.m_i(par)) ? 1 : 0;
             sp.push_back({s, (int)mb, (int)mb, m, Fs + mi * m + mi, top, (uint64_t)2 * s});
         }
-        if (level < F.L_hss && mb > 0 && mi > 0) rp.push_back({s, (int)mi, (int)mb, m, Fs + mi * m, 0, (uint64_t)2 * s + 1});
+        // R^sigma is read only by the apply: its compression waits for the end of
+        // the factorization, where the fronts of all levels go in one batch
+        if (level < F.L_hss && mb > 0 && mi > 0) F.lr_pending.push_back(s);
     }
-    std::vector<int> ks, kr;
+    std::vector<int> ks;
     if (!sp.empty()) {
         ndhss_status rc = compress_problems<T>(sp, false, o, ks, nullptr, F, st);
         if (rc != NDHSS_OK) return rc;
         for (int k : ks) F.kmax = std::max(F.kmax, k);
     }
-    if (!rp.empty()) {
-        std::vector<std::vector<T>> lr;
-        ndhss_status rc = compress_problems<T>(rp, true, o, kr, &lr, F, st);
-        if (rc != NDHSS_OK) return rc;
-        size_t tot = 0;
-        for (auto& v : lr) tot += v.size();
-        void* buf = nullptr;
-        if (pool_malloc_async(&buf, std::max<size_t>(tot, 1) * sizeof(T), st) != cudaSuccess) {
-            cudaGetLastError();
-            return set_error(NDHSS_ERR_OOM, "hss: low-rank storage of level %d", level);
-        }
-        F.lr_bufs.push_back(buf);
-        F.dev_bytes += (int64_t)(tot * sizeof(T));
-        size_t off = 0;
-        for (size_t i = 0; i < rp.size(); ++i) {
-            const int s = rp[i].node;
-            T* dst = static_cast<T*>(buf) + off;
-            if (!lr[i].empty())
-                HSS_TRY(cudaMemcpyAsync(dst, lr[i].data(), lr[i].size() * sizeof(T), cudaMemcpyHostToDevice, st));
-            F.lr_ptr[s] = reinterpret_cast<uint64_t>(dst);
-            F.lr_k[s] = kr[i];
-            F.kmax = std::max(F.kmax, kr[i]);
-            off += lr[i].size();
-        }
-        HSS_TRY(cudaStreamSynchronize(st));
+    return NDHSS_OK;
+}
+
+// Low-rank R^sigma ~ X R(J, :) of every front queued by compress_level_impl,
+// all levels in one batch (each front keeps its own Philox stream 2 s + 1, so
+// the result does not depend on the batching).
+template <typename T>
+ndhss_status lowrank_pending_impl(FactorData& F, const ndhss_factor_opts& o, cudaStream_t st) {
+    T* base = static_cast<T*>(F.d_front);
+    std::vector<Problem> rp;
+    for (int s : F.lr_pending) {
+        const int64_t mi = F.m_i(s), mb = F.m_b(s), m = mi + mb;
+        rp.push_back({s, (int)mi, (int)mb, m, base + F.foff[s] + mi * m, 0, (uint64_t)2 * s + 1});
+    }
+    F.lr_pending.clear();
+    if (rp.empty()) return NDHSS_OK;
+    std::vector<int> kr;
+    std::vector<uint64_t> ptr;
+    ndhss_status rc = compress_problems<T>(rp, true, o, kr, &ptr, F, st);
+    if (rc != NDHSS_OK) return rc;
+    for (size_t i = 0; i < rp.size(); ++i) {
+        F.lr_ptr[rp[i].node] = ptr[i];
+        F.lr_k[rp[i].node] = kr[i];
+        F.kmax = std::max(F.kmax, kr[i]);
     }
     return NDHSS_OK;
 }
@@ -1549,6 +1583,14 @@ ndhss_status hss_ulv_level(FactorData& F, const Tree& t, int level, void* aii, c
     if (!cplx) return ulv_level_impl<float>(F, t, level, (float*)aii, aii_off, o, st);
     if (F.prec == NDHSS_FP64) return ulv_level_impl<c128>(F, t, level, (c128*)aii, aii_off, o, st);
     return ulv_level_impl<c64>(F, t, level, (c64*)aii, aii_off, o, st);
+}
+
+ndhss_status hss_lowrank_pending(FactorData& F, const ndhss_factor_opts& o, cudaStream_t st) {
+    const bool cplx = F.vtype == NDHSS_C128;
+    if (!cplx && F.prec == NDHSS_FP64) return lowrank_pending_impl<double>(F, o, st);
+    if (!cplx) return lowrank_pending_impl<float>(F, o, st);
+    if (F.prec == NDHSS_FP64) return lowrank_pending_impl<c128>(F, o, st);
+    return lowrank_pending_impl<c64>(F, o, st);
 }
 
 ndhss_status hss_compress_level(FactorData& F, const Tree& t, int level, const ndhss_factor_opts& o, cudaStream_t st) {

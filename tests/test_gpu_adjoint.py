@@ -110,18 +110,32 @@ def test_c5_sized_gradient_matches_oracle():
     lu = spla.splu(Pt.A.tocsc())
     d = np.stack([lu.solve(Pt.b[:, s])[rec] for s in range(ns)], axis=1)
     model = _model(ndhss, P, k, N, src, 1, 4)
+    t_asm = [0.0]
+    assemble = model.assemble
+
+    def timed_assemble(mb):
+        t = time.time()
+        A = assemble(mb)
+        t_asm[0] += time.time() - t
+        return A
+
+    model.assemble = timed_assemble
     m_t = torch.tensor(m.ravel(), dtype=torch.float64, requires_grad=True)
     B = torch.from_numpy(np.ascontiguousarray(P.b)).cuda()
-    torch.cuda.synchronize()
-    t0 = time.time()
-    J, X = _misfit(ndhss, model, m_t, B, rec, d)
-    J.backward()
-    torch.cuda.synchronize()
-    t_gpu = time.time() - t0
+    for rep in range(2):  # the first pass also pays one-time set-up (memory pool, module load)
+        m_t.grad = None
+        t_asm[0] = 0.0
+        torch.cuda.synchronize()
+        t0 = time.time()
+        J, X = _misfit(ndhss, model, m_t, B, rec, d)
+        J.backward()
+        torch.cuda.synchronize()
+        t_gpu = time.time() - t0
     t0 = time.time()
     Jo, go = misfit_and_gradient(P, rec, d)
     t_cpu = time.time() - t0
     g = m_t.grad.numpy()
-    print(f"C5 gradient: GPU {t_gpu:.2f} s (factor + 16 + 16 solves + assembly), oracle {t_cpu:.2f} s")
+    print(f"C5 gradient: {t_gpu:.2f} s on the GPU path, of which {t_asm[0]:.2f} s host assembly of A(m); "
+          f"oracle (sparse direct, A given) {t_cpu:.2f} s")
     assert abs(J.item() - Jo) <= 1e-7 * Jo
     assert np.linalg.norm(g - go) <= 1e-5 * np.linalg.norm(go), np.linalg.norm(g - go) / np.linalg.norm(go)
