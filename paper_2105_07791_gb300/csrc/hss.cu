@@ -23,6 +23,8 @@
 #include <cmath>
 #include <vector>
 
+#include <cooperative_groups.h>
+
 #include "factor.cuh"
 #include "ulv.cuh"
 
@@ -477,6 +479,222 @@ row_id_kernel(const int* __restrict__ list, const HNode* __restrict__ nodes, T* 
         X[(int64_t)a * nd.rows_cap + piv[i]] = v;
     }
     if (tid == 0) kk[id] = k;
+}
+
+// The same row ID with the columns of W = S_loc^T split over the C CTAs of a
+// thread-block cluster (C = 1: one CTA), every CTA holding its share in shared
+// memory.  A pivot step is one cluster barrier (the CTAs' per-warp candidates
+// of the next pivot become visible and every warp reduces them through
+// distributed shared memory), the copy of the pivot column from its owner, one
+// CTA barrier and the reflection of the remaining local columns, which also
+// yields their new norms and the next candidates.  A column is reflected by a
+// segment of LPC lanes (LPC = 8, 16 or 32 as p <= 64, 128, 256; 8 entries per
+// lane), so a warp works on 32 / LPC columns at once.  Columns never move: a
+// pivot is flagged, the pivot order kept, and R11 = R(0:k, 0:k) gathered at
+// the end.  Ties of the pivot norm go to the lowest row index.
+constexpr int RID_THREADS = 256;
+constexpr int RID_NW = RID_THREADS / 32;
+constexpr int RID_KMAX = 256;                 // ranks stay below the 256-sample limit
+constexpr int RID_MAX_CLUSTER = 8;
+constexpr size_t RID_SMEM = 200 * 1024;       // dynamic shared memory of one CTA's share
+constexpr int RID_SPLIT_COLS = 64;
+
+__host__ __device__ __forceinline__ int rid_lpc(int p) { return p <= 64 ? 8 : p <= 128 ? 16 : 32; }
+
+template <typename T>
+__device__ __forceinline__ T seg_sum(T v, int lpc) {
+    for (int o = lpc >> 1; o; o >>= 1) v = v + shfl_xor_h(v, o);
+    return v;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(RID_THREADS, sizeof(T) > 8 ? 2 : 4)
+row_id_cluster_kernel(const int* __restrict__ list, const HNode* __restrict__ nodes, T* __restrict__ ws,
+                      int* __restrict__ iws, int* __restrict__ kk, const int* __restrict__ rows_in, double eps,
+                      int rank_cap) {
+    using real = typename Tr<T>::real;
+    namespace cg = cooperative_groups;
+    constexpr int CH = 8;                        // column entries per lane in registers
+    cg::cluster_group cl = cg::this_cluster();
+    const int C = (int)cl.num_blocks();
+    const int rk = (int)cl.block_rank();
+    const int id = list[blockIdx.x / C];
+    const HNode nd = nodes[id];
+    const int rows = rows_in[id], p = nd.p;
+    const int chunk = (rows + C - 1) / C;
+    const int c_lo = min(rows, rk * chunk);
+    const int nloc = min(rows, c_lo + chunk) - c_lo;
+    const int lds = p | 1;                       // odd column stride: per-column loops free of bank conflicts
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int lpc = rid_lpc(p), spw = 32 / lpc;  // lanes per column, columns per warp
+    const int seg = lane / lpc, sl = lane % lpc;
+    extern __shared__ __align__(16) unsigned char smem[];
+    T* Ws = reinterpret_cast<T*>(smem);          // nloc columns of W, ld lds
+    T* vsh = Ws + (size_t)lds * chunk;           // pivot column (p)
+    unsigned char* used = reinterpret_cast<unsigned char*>(vsh + p + 1);
+    __shared__ real s_cv[2][RID_NW];
+    __shared__ int s_ci[2][RID_NW];
+    __shared__ T s_beta[RID_KMAX];
+    __shared__ int s_order[RID_KMAX];
+    const T* Wg = ws + nd.o_w;
+    for (int q = tid; q < p * nloc; q += RID_THREADS) {
+        const int c = q / p, j = q % p;
+        Ws[(size_t)c * lds + j] = Wg[(int64_t)(c_lo + c) * p + j];
+    }
+    for (int c = tid; c < nloc; c += RID_THREADS) used[c] = 0;
+    __syncthreads();
+    // the warp's best candidate (squared norm, row) over its segments, to s_cv/s_ci[par]
+    auto publish = [&](real best, int nb, int par) {
+        for (int o = 16; o >= lpc; o >>= 1) {
+            const real ov = __shfl_xor_sync(0xffffffffu, best, o);
+            const int oi = __shfl_xor_sync(0xffffffffu, nb, o);
+            if (ov > best || (ov == best && oi < nb)) { best = ov; nb = oi; }
+        }
+        if (lane == 0) { s_cv[par][warp] = best; s_ci[par][warp] = nb; }
+    };
+    {
+        real best = real(-1);
+        int nb = INT_MAX;
+        for (int c0 = warp * spw; c0 < nloc; c0 += RID_NW * spw) {
+            const int c = c0 + seg;
+            const bool act = c < nloc;
+            const T* col = Ws + (size_t)(act ? c : 0) * lds;
+            real sacc = real(0);
+            for (int j = sl; j < p; j += lpc) sacc += act ? nrm2r(col[j]) : real(0);
+            sacc = seg_sum(sacc, lpc);
+            if (act && sacc > best) { best = sacc; nb = c_lo + c; }
+        }
+        publish(best, nb, 0);
+    }
+    const int kmax = min(min(min(nd.kcap, rank_cap), min(p, rows)), RID_KMAX);
+    // pivot scalars in the working precision, computed by every thread (no
+    // broadcast barrier; double would run on the narrow FP64 pipe)
+    real r11 = real(0);
+    const real reps = (real)eps;
+    int t = 0;
+    for (;; ++t) {
+        if (C > 1) cl.sync(); else __syncthreads();
+        const int par = t & 1;
+        real bv = real(-1);
+        int bi = INT_MAX;
+        for (int q = lane; q < C * RID_NW; q += 32) {
+            const int r = q / RID_NW, w = q % RID_NW;
+            real v;
+            int i;
+            if (C > 1) {
+                v = *cl.map_shared_rank(&s_cv[par][w], r);
+                i = *cl.map_shared_rank(&s_ci[par][w], r);
+            } else {
+                v = s_cv[par][w];
+                i = s_ci[par][w];
+            }
+            if (v > bv || (v == bv && i < bi)) { bv = v; bi = i; }
+        }
+        for (int o = 16; o; o >>= 1) {
+            const real ov = __shfl_xor_sync(0xffffffffu, bv, o);
+            const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+            if (ov > bv || (ov == bv && oi < bi)) { bv = ov; bi = oi; }
+        }
+        const real xn = sqrt(bv > real(0) ? bv : real(0));
+        if (t == 0) r11 = xn;
+        if (t >= kmax || bi == INT_MAX || !(xn > reps * r11)) break;
+        const int cb = bi, owner = cb / chunk;
+        const T* src = (owner == rk) ? Ws + (size_t)(cb - c_lo) * lds
+                                     : cl.map_shared_rank(Ws, owner) + (size_t)(cb - owner * chunk) * lds;
+        for (int j = t + tid; j < p; j += RID_THREADS) vsh[j] = src[j];
+        if (tid == 0) {
+            s_order[t] = cb;
+            if (owner == rk) used[cb - c_lo] = 1;
+        }
+        __syncthreads();
+        // reflector v = x - beta e_t of the pivot column x, beta = -phase(x_t) ||x||
+        const T a0 = vsh[t];
+        const real aa2 = nrm2r(a0), aa = sqrt(aa2);
+        T ph = one<T>();
+        if (aa > real(0)) ph = scale(a0, real(1) / aa);
+        const T beta = scale(ph, -xn);
+        const T v0 = a0 - beta;
+        const real vn2 = xn * xn - aa2 + nrm2r(v0);
+        if (tid == 0) s_beta[t] = beta;
+        const real f = real(2) / vn2;
+        T vl[CH];
+#pragma unroll
+        for (int q = 0; q < CH; ++q) {
+            const int j = t + sl + lpc * q;
+            vl[q] = (j < p) ? (j == t ? v0 : vsh[j]) : zero<T>();
+        }
+        real best = real(-1);
+        int nb = INT_MAX;
+        for (int c0 = warp * spw; c0 < nloc; c0 += RID_NW * spw) {
+            const int c = c0 + seg;
+            const bool act = c < nloc && !used[c];
+            T* col = Ws + (size_t)(act ? c : 0) * lds;
+            T cv[CH];
+            T w = zero<T>();
+#pragma unroll
+            for (int q = 0; q < CH; ++q) {
+                const int j = t + sl + lpc * q;
+                cv[q] = (act && j < p) ? col[j] : zero<T>();
+            }
+#pragma unroll
+            for (int q = 0; q < CH; ++q) w = fmac(conjv(vl[q]), cv[q], w);
+            w = seg_sum(w, lpc);
+            const T g = scale(w, f);
+            real sacc = real(0);
+#pragma unroll
+            for (int q = 0; q < CH; ++q) {
+                const int j = t + sl + lpc * q;
+                if (act && j < p) {
+                    const T u = cv[q] - vl[q] * g;
+                    col[j] = u;
+                    if (j > t) sacc += nrm2r(u);
+                }
+            }
+            sacc = seg_sum(sacc, lpc);
+            if (act && sacc > best) { best = sacc; nb = c_lo + c; }
+        }
+        publish(best, nb, par ^ 1);
+    }
+    const int k = t;
+    // R11 (strictly upper part) from the pivot columns' owners into the global
+    // copy of W, which no CTA reads any more; diagonal = beta
+    T* R11 = ws + nd.o_w;
+    for (int a = 1; a < k; ++a) {
+        const int c = s_order[a] - c_lo;
+        if (c >= 0 && c < nloc)
+            for (int i = tid; i < a; i += RID_THREADS) R11[(int64_t)a * k + i] = Ws[(size_t)c * lds + i];
+    }
+    if (C > 1) cl.sync(); else __syncthreads();
+    // T = R11^{-1} R12 in place of R12 (one column per thread)
+    for (int c = tid; c < nloc; c += RID_THREADS) {
+        if (used[c]) continue;
+        T* col = Ws + (size_t)c * lds;
+        for (int i = k - 1; i >= 0; --i) {
+            T acc = col[i];
+            for (int l = i + 1; l < k; ++l) acc = fmac(-R11[(int64_t)l * k + i], col[l], acc);
+            col[i] = acc * recip(s_beta[i]);
+        }
+    }
+    __syncthreads();
+    T* X = ws + nd.o_x;
+    int* piv = iws + nd.o_piv;
+    for (int q = tid; q < nloc * k; q += RID_THREADS) {
+        const int c = q % nloc, a = q / nloc;
+        T v;
+        if (used[c]) v = (s_order[a] == c_lo + c) ? one<T>() : zero<T>();
+        else v = Ws[(size_t)c * lds + a];
+        X[(int64_t)a * nd.rows_cap + c_lo + c] = v;
+    }
+    // piv: skeleton in pivot order, then the other rows in increasing order
+    if (rk == 0)
+        for (int a = tid; a < k; a += RID_THREADS) piv[a] = s_order[a];
+    for (int c = tid; c < nloc; c += RID_THREADS) {
+        if (used[c]) continue;
+        int below = 0;
+        for (int a = 0; a < k; ++a) below += (s_order[a] < c_lo + c) ? 1 : 0;
+        piv[k + c_lo + c - below] = c_lo + c;
+    }
+    if (rk == 0 && tid == 0) kk[id] = k;
 }
 
 // Omega_i = X^T Omega_loc, S_i = S_loc(J, :), skeleton = iloc(J).
@@ -1159,14 +1377,97 @@ ndhss_status compress_problems(std::vector<Problem>& probs, bool lowrank, const 
         const size_t smem_base = (size_t)(rows_cap_even((int)max_rows)) * sizeof(double) + (size_t)(p + 2) * sizeof(T) + 64;
         const size_t smem_w = smem_base + (size_t)(p | 1) * max_rows * sizeof(T);
         const int w_in_smem = smem_w <= 200 * 1024 ? 1 : 0;
-        const size_t smem_rid = w_in_smem ? smem_w : smem_base;
-        HSS_TRY(cudaFuncSetAttribute(row_id_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)std::max<size_t>(smem_rid, 48 * 1024)));
+        (void)w_in_smem;
+        HSS_TRY(cudaFuncSetAttribute(row_id_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)std::max<size_t>(smem_base, 48 * 1024)));
+        HSS_TRY(cudaFuncSetAttribute(row_id_cluster_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)RID_SMEM));
+        // row IDs of the nodes flat[b, e): the cluster kernel with the smallest
+        // cluster whose share of W fits in shared memory, one launch per cluster
+        // size; a node too large for RID_MAX_CLUSTER CTAs keeps W in global memory
+        auto rid_bytes = [&](int rows_cap, int C) {
+            const size_t chunk = (size_t)(rows_cap + C - 1) / C;
+            return ((size_t)(p | 1) * chunk + (size_t)p + 1) * sizeof(T) + chunk + 16;
+        };
+        int num_sms = 0, dev = 0;
+        HSS_TRY(cudaGetDevice(&dev));
+        HSS_TRY(cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev));
+        auto launch_row_id = [&](size_t b, size_t e) -> ndhss_status {
+            std::vector<int> grp[5], big;
+            // a launch of few nodes also splits a node whose share would exceed
+            // RID_SPLIT_COLS columns per CTA (the pivot steps then run shorter)
+            const bool few = (e - b) * 2 <= (size_t)num_sms;
+            for (size_t q = b; q < e; ++q) {
+                const int rc = nodes[flat[q]].rows_cap;
+                int g = 0;
+                while ((1 << g) <= RID_MAX_CLUSTER && rid_bytes(rc, 1 << g) > RID_SMEM) ++g;
+                while (few && (1 << g) < RID_MAX_CLUSTER && (rc + (1 << g) - 1) / (1 << g) > RID_SPLIT_COLS) ++g;
+                ((1 << g) <= RID_MAX_CLUSTER ? grp[g] : big).push_back(flat[q]);
+            }
+            // a cluster shape the device cannot co-schedule falls back to global memory
+            for (int g = 1; (1 << g) <= RID_MAX_CLUSTER; ++g) {
+                if (grp[g].empty()) continue;
+                cudaLaunchConfig_t cfg{};
+                cfg.gridDim = dim3((unsigned)(1 << g));
+                cfg.blockDim = dim3(RID_THREADS);
+                cfg.dynamicSmemBytes = RID_SMEM;
+                cudaLaunchAttribute at[1];
+                at[0].id = cudaLaunchAttributeClusterDimension;
+                at[0].val.clusterDim.x = (unsigned)(1 << g);
+                at[0].val.clusterDim.y = 1;
+                at[0].val.clusterDim.z = 1;
+                cfg.attrs = at;
+                cfg.numAttrs = 1;
+                int ncl = 0;
+                if (cudaOccupancyMaxActiveClusters(&ncl, row_id_cluster_kernel<T>, &cfg) != cudaSuccess || ncl < 1) {
+                    cudaGetLastError();
+                    big.insert(big.end(), grp[g].begin(), grp[g].end());
+                    grp[g].clear();
+                }
+            }
+            for (int g = 0; (1 << g) <= RID_MAX_CLUSTER; ++g) {
+                if (grp[g].empty()) continue;
+                const int C = 1 << g;
+                int rcmax = 1;
+                for (int id : grp[g]) rcmax = std::max(rcmax, nodes[id].rows_cap);
+                DeviceVec<int> dl(st);
+                HSS_TRY(dl.upload(grp[g], st));
+                const size_t sm = rid_bytes(rcmax, C);
+                if (C == 1) {
+                    row_id_cluster_kernel<T><<<(unsigned)grp[g].size(), RID_THREADS, sm, st>>>(dl.p, dnodes.p, ws.p, iws.p,
+                                                                                              kk.p, rows.p, eps, rank_cap);
+                } else {
+                    cudaLaunchConfig_t cfg{};
+                    cfg.gridDim = dim3((unsigned)(grp[g].size() * C));
+                    cfg.blockDim = dim3(RID_THREADS);
+                    cfg.dynamicSmemBytes = sm;
+                    cfg.stream = st;
+                    cudaLaunchAttribute at[1];
+                    at[0].id = cudaLaunchAttributeClusterDimension;
+                    at[0].val.clusterDim.x = (unsigned)C;
+                    at[0].val.clusterDim.y = 1;
+                    at[0].val.clusterDim.z = 1;
+                    cfg.attrs = at;
+                    cfg.numAttrs = 1;
+                    HSS_TRY(cudaLaunchKernelEx(&cfg, row_id_cluster_kernel<T>, (const int*)dl.p, (const HNode*)dnodes.p,
+                                               ws.p, iws.p, kk.p, (const int*)rows.p, eps, rank_cap));
+                }
+                NDHSS_LAUNCH_CHECK("row_id_cluster_kernel");
+            }
+            if (!big.empty()) {
+                DeviceVec<int> dl(st);
+                HSS_TRY(dl.upload(big, st));
+                row_id_kernel<T><<<(unsigned)big.size(), 512, smem_base, st>>>(dl.p, dnodes.p, ws.p, iws.p, kk.p, rows.p,
+                                                                                eps, rank_cap, 0);
+                NDHSS_LAUNCH_CHECK("row_id_kernel");
+            }
+            return NDHSS_OK;
+        };
         if (lowrank) {
             transpose_samples_kernel<T><<<dim3(64, nf), 256, 0, st>>>(dfr.p, dnodes.p, ws.p, iws.p, rows.p);
             NDHSS_LAUNCH_CHECK("transpose_samples_kernel");
-            row_id_kernel<T><<<(unsigned)bylev[0].size(), 512, smem_rid, st>>>(dflat.p + loff[0], dnodes.p, ws.p, iws.p,
-                                                                              kk.p, rows.p, eps, rank_cap, w_in_smem);
-            NDHSS_LAUNCH_CHECK("row_id_kernel");
+            {
+                const ndhss_status rc = launch_row_id(loff[0], loff[1]);
+                if (rc != NDHSS_OK) return rc;
+            }
             gather_rows_kernel<T><<<dim3(64, nf), 256, 0, st>>>(dfr.p, dnodes.p, ws.p, iws.p, kk.p);
             NDHSS_LAUNCH_CHECK("gather_rows_kernel");
             // Zt = X (R(J,:) Omega~) : needs the ranks on the host for the GEMM shapes
@@ -1193,9 +1494,10 @@ ndhss_status compress_problems(std::vector<Problem>& probs, bool lowrank, const 
                 if (!cnt) continue;
                 form_sloc_kernel<T><<<cnt, HT, 0, st>>>(dflat.p + loff[l], dnodes.p, dfr.p, ws.p, iws.p, kk.p, rows.p);
                 NDHSS_LAUNCH_CHECK("form_sloc_kernel");
-                row_id_kernel<T><<<cnt, HT, smem_rid, st>>>(dflat.p + loff[l], dnodes.p, ws.p, iws.p, kk.p, rows.p, eps,
-                                                           rank_cap, w_in_smem);
-                NDHSS_LAUNCH_CHECK("row_id_kernel");
+                {
+                    const ndhss_status rc = launch_row_id(loff[l], loff[l + 1]);
+                    if (rc != NDHSS_OK) return rc;
+                }
                 finish_kernel<T><<<cnt, HT, 0, st>>>(dflat.p + loff[l], dnodes.p, dfr.p, ws.p, iws.p, kk.p, rows.p);
                 NDHSS_LAUNCH_CHECK("finish_kernel");
             }
