@@ -149,6 +149,26 @@ int64_t ndhss_kernel_launches(void);
 ndhss_status ndhss_build_tree(int32_t n, const int32_t* coords, const int32_t* rowptr,
                               const int32_t* col, int32_t leaf_size, ndhss_tree** out);
 
+/*
+ * ndhss_build_tree_batched -- many independent problems as one forest (the
+ * batched workload: many meshes of uneven size, Sec. 3.1's tree per mesh).
+ * Problem s (0 <= s < nsys) is given exactly as to ndhss_build_tree
+ * (n[s], coords[s], rowptr[s], col[s]; host arrays); its tree is built by the
+ * same rule, and the trees are joined side by side: node ids, DOF positions,
+ * B lists and entry indices shifted, every root on level 0, depth = the
+ * deepest problem's.  The tree describes the block-diagonal matrix
+ * diag(A_0, ..., A_{nsys-1}): problem s's DOFs occupy rows
+ * [sum_{s'<s} n[s'], sum_{s'<=s} n[s']) and its CSR entries follow those of
+ * the problems before it, so ndhss_factor / ndhss_apply / ndhss_gmres_batched
+ * take the problems' CSR arrays concatenated (rowptr shifted by the entry
+ * offset, col by the DOF offset, values in problem order).  One level of the
+ * factorization then eliminates the fronts of all problems together.
+ * Inputs are copied.  INVALID_ARG names the failing problem.
+ */
+ndhss_status ndhss_build_tree_batched(int32_t nsys, const int32_t* n, const int32_t* const* coords,
+                                      const int32_t* const* rowptr, const int32_t* const* col,
+                                      int32_t leaf_size, ndhss_tree** out);
+
 /* Sizes of the arrays ndhss_tree_export fills (any pointer may be NULL). */
 ndhss_status ndhss_tree_sizes(const ndhss_tree* t, int32_t* nnodes, int32_t* depth,
                               int64_t* nnz, int64_t* sum_mb);

@@ -57,6 +57,40 @@ ndhss_status ndhss_build_tree(int32_t n, const int32_t* coords, const int32_t* r
     return NDHSS_OK;
 }
 
+ndhss_status ndhss_build_tree_batched(int32_t nsys, const int32_t* n, const int32_t* const* coords,
+                                      const int32_t* const* rowptr, const int32_t* const* col, int32_t leaf_size,
+                                      ndhss_tree** out) {
+    ndhss::clear_error();
+    if (!out) return ndhss::set_error(NDHSS_ERR_INVALID_ARG, "ndhss_build_tree_batched: out is NULL");
+    *out = nullptr;
+    if (nsys < 1 || !n || !coords || !rowptr || !col)
+        return ndhss::set_error(NDHSS_ERR_INVALID_ARG, "ndhss_build_tree_batched: need nsys >= 1 and the four arrays");
+    auto* t = new (std::nothrow) ndhss_tree();
+    if (!t) return ndhss::set_error(NDHSS_ERR_OOM, "ndhss_build_tree_batched: host allocation failed");
+    ndhss_status rc = NDHSS_OK;
+    try {
+        std::vector<ndhss::Tree> parts(nsys);
+        for (int32_t s = 0; s < nsys && rc == NDHSS_OK; ++s) {
+            rc = ndhss::build_tree_impl(n[s], coords[s], rowptr[s], col[s], leaf_size, &parts[s]);
+            if (rc != NDHSS_OK) {
+                const std::string msg = ndhss_last_error();
+                rc = ndhss::set_error(rc, "ndhss_build_tree_batched: problem %d: %s", s, msg.c_str());
+            }
+        }
+        if (rc == NDHSS_OK) rc = ndhss::join_trees(parts, &t->t);
+    } catch (const std::bad_alloc&) {
+        rc = ndhss::set_error(NDHSS_ERR_OOM, "ndhss_build_tree_batched: host allocation failed");
+    } catch (...) {
+        rc = ndhss::set_error(NDHSS_ERR_INTERNAL, "ndhss_build_tree_batched: unexpected exception");
+    }
+    if (rc != NDHSS_OK) {
+        delete t;
+        return rc;
+    }
+    *out = t;
+    return NDHSS_OK;
+}
+
 ndhss_status ndhss_tree_sizes(const ndhss_tree* t, int32_t* nnodes, int32_t* depth, int64_t* nnz, int64_t* sum_mb) {
     ndhss::clear_error();
     if (!t) return ndhss::set_error(NDHSS_ERR_INVALID_ARG, "ndhss_tree_sizes: NULL tree");

@@ -36,6 +36,8 @@ void note_launches(int64_t k);
 
 ndhss_status build_tree_impl(int32_t n, const int32_t* coords, const int32_t* rowptr,
                              const int32_t* col, int32_t leaf_size, Tree* T);
+// The forest of independent problems' trees (batch_tree.cpp).
+ndhss_status join_trees(const std::vector<Tree>& parts, Tree* T);
 
 }  // namespace ndhss
 

@@ -25,7 +25,7 @@ STATUS = {0: "OK", 1: "INVALID_ARG", 2: "OOM", 3: "SINGULAR", 4: "RANK_CAP", 5: 
 EXPORTED = ("ndhss_version", "ndhss_last_error", "ndhss_kernel_launches", "ndhss_build_tree", "ndhss_tree_sizes", "ndhss_tree_export",
             "ndhss_tree_destroy", "ndhss_factor", "ndhss_factor_stats_get", "ndhss_factor_get_block",
             "ndhss_factor_destroy", "ndhss_apply", "ndhss_apply_noalloc", "ndhss_spmv", "ndhss_gmres",
-            "ndhss_testing_stall_apply", "ndhss_elem_qform")
+            "ndhss_testing_stall_apply", "ndhss_elem_qform", "ndhss_build_tree_batched")
 
 
 class NdhssError(RuntimeError):
@@ -164,6 +164,36 @@ def ndhss_build_tree(coords, rowptr, col, leaf_size: int) -> Tree:
     h = C.c_void_p()
     _check(load().ndhss_build_tree(n, _ptr(coords), _ptr(rowptr), _ptr(col), int(leaf_size), C.byref(h)))
     return Tree(h, n)
+
+
+def ndhss_build_tree_batched(problems, leaf_size: int) -> Tree:
+    """Forest of independent problems; ``problems`` is a sequence of
+    (coords, rowptr, col) host arrays, one per problem.  The tree's DOFs are
+    the problems' DOFs concatenated in order."""
+    keep = []
+    for (coords, rowptr, col) in problems:
+        keep.append((np.ascontiguousarray(coords, dtype=np.int32), np.ascontiguousarray(rowptr, dtype=np.int32),
+                     np.ascontiguousarray(col, dtype=np.int32)))
+    ns = len(keep)
+    n = np.array([k[0].shape[0] for k in keep], dtype=np.int32)
+    P = C.POINTER(C.c_int32)
+    arr = lambda j: (P * ns)(*[k[j].ctypes.data_as(P) for k in keep])
+    h = C.c_void_p()
+    _check(load().ndhss_build_tree_batched(ns, _ptr(n), arr(0), arr(1), arr(2), int(leaf_size), C.byref(h)))
+    return Tree(h, int(n.sum()))
+
+
+def batch_csr(mats):
+    """The block-diagonal CSR of scipy matrices ``mats`` (the layout the
+    batched tree describes) and the DOF offsets [nsys + 1]."""
+    import scipy.sparse as sp
+    A = sp.block_diag([m.tocsr() for m in mats], format="csr")
+    A.sort_indices()
+    A.indptr = A.indptr.astype(np.int32)
+    A.indices = A.indices.astype(np.int32)
+    off = np.zeros(len(mats) + 1, dtype=np.int64)
+    off[1:] = np.cumsum([m.shape[0] for m in mats])
+    return A, off
 
 
 def ndhss_tree_export(tree: Tree) -> dict:

@@ -90,3 +90,51 @@ def test_invalid_arguments_return_error_codes(nd):
     assert ei.value.code == 1 and "out of range" in str(ei.value)
     with pytest.raises(nd.NdhssError):
         nd.ndhss_build_tree(P.coords, P.A.indptr, P.A.indices, 0)
+
+
+def test_batched_tree_is_the_forest_of_the_oracle_trees(nd):
+    """ndhss_build_tree_batched: every problem's oracle tree, node ids, DOF
+    positions, B lists and entry indices shifted by the problems before it,
+    roots on level 0 (the block-diagonal matrix of the batch)."""
+    probs = [poisson_dirichlet(9), helmholtz_impedance(13, 1, 5.0), poisson_dirichlet(20, seed=2),
+             helmholtz_impedance(6, 2, 3.0)]
+    leaf = 16
+    e = nd.ndhss_tree_export(
+        nd.ndhss_build_tree_batched([(P.coords, P.A.indptr, P.A.indices) for P in probs], leaf))
+    want = {k: [] for k in TREE_KEYS}
+    dof = node = boff = eoff = 0
+    want["e_off"] = [np.zeros(1, np.int32)]
+    for P in probs:
+        T = build_tree(P.coords, P.A.indptr, P.A.indices, leaf)
+        ni = T.node_info.copy()
+        for f in (1, 2, 3):
+            ni[:, f] = np.where(ni[:, f] >= 0, ni[:, f] + node, ni[:, f])
+        ni[:, 4] += dof
+        ni[:, 6] += boff
+        want["node_info"].append(ni)
+        want["perm"].append(T.perm + dof)
+        want["blist"].append(T.blist + dof)
+        want["emap"].append(T.emap)
+        want["e_off"].append(T.e_off[1:] + eoff)
+        want["e_row"].append(T.e_row)
+        want["e_col"].append(T.e_col)
+        want["e_idx"].append(T.e_idx + eoff)
+        dof += P.A.shape[0]
+        node += ni.shape[0]
+        boff += T.blist.size
+        eoff += P.A.nnz
+    for k in TREE_KEYS:
+        assert np.array_equal(e[k], np.concatenate(want[k])), k
+    roots = e["node_info"][e["node_info"][:, 1] < 0]
+    assert roots.shape[0] == len(probs) and np.all(roots[:, 0] == 0)
+    # the batch's CSR layout
+    A, off = nd.batch_csr([P.A for P in probs])
+    assert off[-1] == A.shape[0] == dof and A.nnz == eoff
+
+
+def test_batched_tree_rejects_a_bad_problem(nd):
+    P = poisson_dirichlet(8)
+    bad_col = P.A.indices.copy()
+    bad_col[3] = P.A.shape[0] + 5
+    with pytest.raises(nd.NdhssError, match="problem 1"):
+        nd.ndhss_build_tree_batched([(P.coords, P.A.indptr, P.A.indices), (P.coords, P.A.indptr, bad_col)], 16)
