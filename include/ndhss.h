@@ -353,6 +353,51 @@ ndhss_status ndhss_gmres(const ndhss_factorization* f, const int32_t* d_rowptr, 
                          int64_t ldx, const ndhss_gmres_opts* opts, ndhss_gmres_stats* stats,
                          void* stream);
 
+/*
+ * ndhss_apply_multi -- y = P^{-1} x for up to 32 right-hand sides at once
+ * (Alg. 3.1 with one pass over the factor for all of them): per level,
+ * deepest first, z(I^s) = A_ii^{-1} P^T y(I^s) and y(B^s) -= L P^T y(I^s) for
+ * every node of the level as 64-row x 32-column tiles; then per level from
+ * the roots, z(I^s) += R z(B^s).  Dense fronts only: a factorization with
+ * compressed Gauss transforms (hss_levels >= 0 above the switching level) or
+ * a ULV diagonal gives INVALID_ARG (ndhss_apply handles those).
+ *   nrhs       0..32 right-hand sides
+ *   d_x, d_y   device float64 / complex128 (per the factor's vtype) arrays of
+ *              n rows, interleaved: element (row, c) at row * ld + c,
+ *              ldx, ldy >= nrhs; original numbering
+ * Works in the factor's precision (one conversion at entry and exit); uses
+ * 2 n x 32 front-type elements of pooled scratch; synchronises the stream.
+ */
+ndhss_status ndhss_apply_multi(const ndhss_factorization* f, int32_t nrhs, const void* d_x, int64_t ldx,
+                               void* d_y, int64_t ldy, void* stream);
+
+/*
+ * ndhss_gmres_batched -- restarted GMRES (as ndhss_gmres: x0 = 0, classical
+ * Gram-Schmidt twice in float64, complex Givens rotations, true-residual
+ * restarts, the same stopping rules) for nsys independent problems x nrhs
+ * right-hand sides at once, in lockstep: every Arnoldi step is one sparse
+ * product of 32 interleaved columns, one ndhss_apply_multi and segmented
+ * reductions per problem, so a pass over A and over the factor serves all
+ * nsys * nrhs systems.  A system that meets its tolerance stops changing
+ * while the others go on.  f is the factorization of the batch's forest
+ * (ndhss_build_tree_batched), dense fronts only.
+ *   d_rowptr, d_col, d_vals  device CSR of the block-diagonal batch matrix
+ *   nsys       problems; sys_off host int64 [nsys + 1], problem s owns rows
+ *              [sys_off[s], sys_off[s+1]), sys_off[0] = 0, sys_off[nsys] = n
+ *   nrhs       right-hand sides per problem, 0..32
+ *   d_b, d_x   device n x nrhs column-major (ldb, ldx >= n); column c of
+ *              problem s's rows is system (s, c)
+ *   opts       as ndhss_gmres (restart <= 31)
+ *   stats      host array [nsys * nrhs] (system (s, c) at s * nrhs + c), or NULL
+ * Memory: (restart + 5) n x 32 vectors of float64 / complex128 from the
+ * library's pool.  Synchronises once per Arnoldi step.  NOT_CONVERGED if any
+ * system missed tol (x still written).
+ */
+ndhss_status ndhss_gmres_batched(const ndhss_factorization* f, const int32_t* d_rowptr, const int32_t* d_col,
+                                 const void* d_vals, int32_t nsys, const int64_t* sys_off, int32_t nrhs,
+                                 const void* d_b, int64_t ldb, void* d_x, int64_t ldx,
+                                 const ndhss_gmres_opts* opts, ndhss_gmres_stats* stats, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

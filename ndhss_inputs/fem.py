@@ -381,3 +381,49 @@ def helmholtz_blocks(N: int, k: float, m_blocks, *, p: int = 1, seed: int = 0, n
     P.meta.update(m_blocks=mb, nb=nb, elem=elem, Me=Me, eblk=eblk, edges=edges, Ee=Ee, edge_blk=edge_blk,
                   sources=src_xy, k=k)
     return P
+
+
+def helmholtz_macro(Nx: int, Ny: int, c_blocks, *, p: int = 1, ppw: float = 10.0, src_xy=None, nsrc: int = 32,
+                    seed: int = 0, width: float = 0.02) -> Problem:
+    """Helmholtz with impedance on all sides on an Nx x Ny cell grid of
+    [0,1]^2 (cells h_x = 1/Nx by h_y = 1/Ny), wave speed c piecewise constant
+    on the macro blocks of ``c_blocks`` [mb, mb] (cell (a, b) in block
+    (a mb // Nx, b mb // Ny)), angular frequency omega = 2 pi / (ppw max(h_x, h_y))
+    so that the slowest wave (c >= 1) has ``ppw`` points per wavelength, and
+    local wavenumber k = omega / c in the mass and the impedance terms.
+    Right-hand sides: Gaussian sources of the given width at ``src_xy``
+    [nsrc, 2] (default: drawn ~ U[0.1, 0.9]^2 from ``seed``), interpolated
+    and multiplied by the mass matrix.
+    """
+    cb = np.asarray(c_blocks, dtype=np.float64)
+    mb = cb.shape[0]
+    elem, cell, lattice, xy, Lx, Ly = _mesh(Nx, Ny, p)
+    omega = 2.0 * np.pi / (ppw * max(1.0 / Nx, 1.0 / Ny))
+    c_e = cb[cell[:, 0] * mb // Nx, cell[:, 1] * mb // Ny]
+    ecell = _edge_cells(Nx, Ny)
+    c_edge = cb[ecell[:, 0] * mb // Nx, ecell[:, 1] * mb // Ny]
+    A, M, *_ = assemble(Nx, Ny, p, mass_coef=-(omega / c_e) ** 2, impedance_k=omega / c_edge)
+    if src_xy is None:
+        src_xy = np.random.default_rng(seed).uniform(0.1, 0.9, size=(nsrc, 2))
+    src_xy = np.asarray(src_xy, dtype=np.float64)
+    F = np.stack([gaussian_source(xy, src_xy[s], width) for s in range(src_xy.shape[0])], axis=1)
+    b = (M @ F).astype(np.complex128)
+    return Problem(A=_finish(A), b=np.ascontiguousarray(b), coords=lattice.astype(np.int32),
+                   name=f"helmholtz_macro_p{p}_{Nx}x{Ny}",
+                   meta=dict(Nx=Nx, Ny=Ny, p=p, omega=omega, c_blocks=cb, xy=xy, sources=src_xy))
+
+
+def helmholtz_batch(count: int, seed: int = 0, *, nmin: int = 64, nmax: int = 256, nsrc: int = 32,
+                    mb: int = 8, cmin: float = 1.0, cmax: float = 3.0, p: int = 1) -> list:
+    """``count`` independent Helmholtz problems (helmholtz_macro) of the
+    batched workload: problem s draws from seed + s its grid
+    N_x, N_y ~ U{nmin..nmax}, its wave speeds c ~ U[cmin, cmax] on mb x mb
+    macro blocks and its ``nsrc`` source positions ~ U[0.1, 0.9]^2."""
+    out = []
+    for s in range(count):
+        rng = np.random.default_rng([seed, s])
+        Nx, Ny = (int(v) for v in rng.integers(nmin, nmax + 1, size=2))
+        cb = rng.uniform(cmin, cmax, size=(mb, mb))
+        src = rng.uniform(0.1, 0.9, size=(nsrc, 2))
+        out.append(helmholtz_macro(Nx, Ny, cb, p=p, src_xy=src))
+    return out

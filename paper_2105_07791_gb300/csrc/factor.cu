@@ -968,6 +968,7 @@ static ndhss_status factor_impl(const ndhss_tree* th, int32_t vtype, const int32
     }
     cleanup();
     if (rc == NDHSS_OK) rc = build_apply_schedule(F, st);
+    if (rc == NDHSS_OK) rc = build_multi_plan(F, st);
     if (rc != NDHSS_OK) {
         cudaStreamSynchronize(st);
         ndhss_factor_destroy(h);
@@ -1125,7 +1126,7 @@ void ndhss_factor_destroy(ndhss_factorization* fh) {
     cudaDeviceSynchronize();
     for (void* p : {(void*)F.d_node, (void*)F.d_foff, (void*)F.d_blist, (void*)F.d_perm, (void*)F.d_sigma,
                     (void*)F.d_ipiv, F.d_front, (void*)F.d_lr_ptr, (void*)F.d_lr_k, (void*)F.d_lr_list, (void*)F.d_sched,
-                    (void*)F.d_need, (void*)F.d_wdesc, (void*)F.d_apply_err})
+                    (void*)F.d_need, (void*)F.d_wdesc, (void*)F.d_apply_err, (void*)F.d_mjobs})
         if (p) cudaFreeAsync(p, 0);
     for (void* b : F.lr_bufs)
         if (b) cudaFreeAsync(b, 0);

@@ -60,6 +60,12 @@ struct FactorData {
     int32_t L_hss = -1;                       // levels <= L_hss compress S; < L_hss also R
     std::vector<void*> lr_bufs;
     std::vector<int32_t> lr_pending;
+
+    // multi right-hand-side apply (multi.cu): the (node, first row) of every
+    // 64-row tile, up-sweep tiles of all levels then down-sweep tiles, and
+    // each level's range in both
+    int2* d_mjobs = nullptr;
+    std::vector<int64_t> mj_up_off, mj_dn_off;
     std::vector<uint64_t> lr_ptr;             // per node, 0 = dense R
     std::vector<int32_t> lr_k;
     uint64_t* d_lr_ptr = nullptr;
@@ -133,6 +139,8 @@ size_t apply_work_bytes(const FactorData& F);
 // Builds and uploads the dataflow queue once the factor (and its low-rank
 // tier) is complete; defined in apply.cu.
 ndhss_status build_apply_schedule(FactorData& F, cudaStream_t st);
+// The tile lists of the multi right-hand-side apply.  Defined in multi.cu.
+ndhss_status build_multi_plan(FactorData& F, cudaStream_t st);
 // NDHSS_ERR_TIMEOUT if an earlier apply of this factorization gave up a wait.
 ndhss_status apply_check_error(const FactorData& F, const char* who);
 

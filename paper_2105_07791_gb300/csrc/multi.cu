@@ -1,0 +1,701 @@
+// Many right-hand sides at once: Alg. 3.1 applied to 32 interleaved vectors
+// (one pass over the factor serves all of them), and restarted GMRES run in
+// lockstep for many independent problems x 32 right-hand sides (the batched
+// workload: the problems of a forest factorization, ndhss_build_tree_batched).
+//
+// Block vectors are stored interleaved: element (row, c) at row * 32 + c, so a
+// row of 32 right-hand sides is one 512-byte (complex128) or 256-byte
+// (complex64) line and every gather by a row index stays coalesced.
+//
+// Multi apply (dense fronts).  With u = y in elimination order, per level,
+// deepest first, every node s of the level computes from u(I^s) read through
+// its interchanges sigma:
+//     z(I^s) = X11 u(I^s o sigma)          (A_ii^{-1} P^T, the diagonal step)
+//     u(B^s) -= X21 u(I^s o sigma)          (the up-sweep, -L P^T)
+// then per level, root level first:  z(I^s) += X12 z(B^s)  (the down-sweep, R).
+// B^s lies inside the box of s, so the B sets of one level are disjoint and
+// the I rows of a level are never B rows of the same level: a level is one
+// launch of independent 64-row x 32-column tiles with no atomics.
+//
+// Batched GMRES.  System q = (problem s, column c) owns rows [off_s, off_s+1)
+// of column c.  Every reduction is segmented by problem: a CTA covers up to
+// SEG_ROWS rows of one problem and writes its partial sums, a second kernel
+// adds a problem's partials in block order (deterministic).  Hessenberg,
+// Givens rotations and the least-squares residual are per system (one thread
+// each), with the same arithmetic and stopping rules as ndhss_gmres; a system
+// that stops or converges keeps its x while the others go on.
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "factor.cuh"
+
+namespace ndhss {
+namespace {
+
+constexpr int MR = 32;            // interleaved right-hand sides
+constexpr int MT_ROWS = 64;       // rows per apply tile
+constexpr int MT_K = 16;          // K chunk of an apply tile
+constexpr int SEG_ROWS = 2048;    // rows per reduction block
+constexpr int BK = 32;            // restart + 1 <= BK
+
+__device__ __forceinline__ double babs(double a) { return fabs(a); }
+__device__ __forceinline__ double babs(c128 a) { return hypot(a.x, a.y); }
+__device__ __forceinline__ double bre(double a) { return a; }
+__device__ __forceinline__ double bre(c128 a) { return a.x; }
+template <typename V> __device__ __forceinline__ V breal(double v);
+template <> __device__ __forceinline__ double breal<double>(double v) { return v; }
+template <> __device__ __forceinline__ c128 breal<c128>(double v) { return {v, 0.0}; }
+
+// ------------------------------------------------------------ multi apply
+template <typename T, typename V>
+__global__ void mgather_kernel(int64_t n, int nrhs, const int32_t* __restrict__ perm, const V* __restrict__ X,
+                               int64_t ldx, T* __restrict__ U) {
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n * MR; q += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t pos = q / MR;
+        const int c = (int)(q % MR);
+        U[q] = c < nrhs ? from_val<T>(X[(int64_t)perm[pos] * ldx + c]) : zero<T>();
+    }
+}
+
+template <typename T, typename V>
+__global__ void mscatter_kernel(int64_t n, int nrhs, const int32_t* __restrict__ perm, const T* __restrict__ Z,
+                                V* __restrict__ Y, int64_t ldy) {
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n * MR; q += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t pos = q / MR;
+        const int c = (int)(q % MR);
+        if (c < nrhs) Y[(int64_t)perm[pos] * ldy + c] = to_val(Z[q]);
+    }
+}
+
+// One 64-row x 32-column tile of node s: UP = the first m_i columns of the
+// front against u(I^s o sigma) (rows < m_i to z, rows >= m_i subtracted from
+// u(B^s)); !UP = the R block against z(B^s), added to z(I^s).
+template <typename T, bool UP>
+__global__ void __launch_bounds__(256)
+mapply_kernel(const int2* __restrict__ jobs, const int32_t* __restrict__ node, const int64_t* __restrict__ foff,
+              const T* __restrict__ front, const int32_t* __restrict__ sigma, const int32_t* __restrict__ blist,
+              T* __restrict__ U, T* __restrict__ Z) {
+    __shared__ T As[MT_K][MT_ROWS];
+    __shared__ T Bs[MT_K][MR];
+    __shared__ int s_row[MT_K];
+    const int2 J = jobs[blockIdx.x];
+    const int s = J.x, r0 = J.y;
+    const int32_t* nd = node + (size_t)s * 14;
+    const int i_off = nd[4], m_i = nd[5], b_off = nd[6], m_b = nd[7];
+    const int64_t m = (int64_t)m_i + m_b;
+    const T* F = front + foff[s];
+    const int rows = UP ? (int)m : m_i;
+    const int K = UP ? m_i : m_b;
+    const T* A = UP ? F : F + (int64_t)m_i * m;
+    const T* src = UP ? U : Z;
+    const int tid = threadIdx.x, tx = tid & 7, ty = tid >> 3;
+    T acc[2][4];
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = zero<T>();
+    for (int k0 = 0; k0 < K; k0 += MT_K) {
+        const int kc = min(MT_K, K - k0);
+        if (tid < MT_K)
+            s_row[tid] = tid < kc ? (UP ? i_off + sigma[i_off + k0 + tid] : blist[b_off + k0 + tid]) : -1;
+        for (int q = tid; q < MT_ROWS * MT_K; q += 256) {
+            const int r = q % MT_ROWS, kk = q / MT_ROWS;
+            As[kk][r] = (r0 + r < rows && kk < kc) ? A[(int64_t)(k0 + kk) * m + r0 + r] : zero<T>();
+        }
+        __syncthreads();
+        for (int q = tid; q < MT_K * MR; q += 256) {
+            const int kk = q / MR, c = q % MR;
+            Bs[kk][c] = s_row[kk] >= 0 ? src[(int64_t)s_row[kk] * MR + c] : zero<T>();
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < MT_K; ++kk) {
+            const T a0 = As[kk][2 * ty], a1 = As[kk][2 * ty + 1];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const T b = Bs[kk][4 * tx + j];
+                acc[0][j] = fmac(a0, b, acc[0][j]);
+                acc[1][j] = fmac(a1, b, acc[1][j]);
+            }
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        const int r = r0 + 2 * ty + i;
+        if (r >= rows) continue;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int c = 4 * tx + j;
+            if (UP) {
+                if (r < m_i) {
+                    Z[(int64_t)(i_off + r) * MR + c] = acc[i][j];
+                } else {
+                    T* p = U + (int64_t)blist[b_off + r - m_i] * MR + c;
+                    *p = *p - acc[i][j];
+                }
+            } else {
+                T* p = Z + (int64_t)(i_off + r) * MR + c;
+                *p = *p + acc[i][j];
+            }
+        }
+    }
+}
+
+template <typename T, typename V>
+ndhss_status multi_apply_run(const FactorData& F, int nrhs, const V* X, int64_t ldx, V* Y, int64_t ldy, T* U, T* Z,
+                             cudaStream_t st) {
+    const int64_t n = F.n;
+    const int eb = (int)std::min<int64_t>((n * MR + 255) / 256, 8 * 152);
+    mgather_kernel<T, V><<<eb, 256, 0, st>>>(n, nrhs, F.d_perm, X, ldx, U);
+    NDHSS_LAUNCH_CHECK("mgather_kernel");
+    const T* front = static_cast<const T*>(F.d_front);
+    for (int l = F.depth; l >= 0; --l) {
+        const int64_t a = F.mj_up_off[l], b = F.mj_up_off[l + 1];
+        if (b == a) continue;
+        mapply_kernel<T, true><<<(unsigned)(b - a), 256, 0, st>>>(F.d_mjobs + a, F.d_node, F.d_foff, front, F.d_sigma,
+                                                                 F.d_blist, U, Z);
+        NDHSS_LAUNCH_CHECK("mapply_kernel");
+    }
+    for (int l = 0; l <= F.depth; ++l) {
+        const int64_t a = F.mj_dn_off[l], b = F.mj_dn_off[l + 1];
+        if (b == a) continue;
+        mapply_kernel<T, false><<<(unsigned)(b - a), 256, 0, st>>>(F.d_mjobs + a, F.d_node, F.d_foff, front,
+                                                                  F.d_sigma, F.d_blist, U, Z);
+        NDHSS_LAUNCH_CHECK("mapply_kernel");
+    }
+    mscatter_kernel<T, V><<<eb, 256, 0, st>>>(n, nrhs, F.d_perm, Z, Y, ldy);
+    NDHSS_LAUNCH_CHECK("mscatter_kernel");
+    return NDHSS_OK;
+}
+
+// X, Y: n x ld interleaved float64 / complex128 (per the factor's vtype);
+// work: 2 n x 32 front-type elements
+ndhss_status multi_apply_device(const FactorData& F, int nrhs, const void* X, int64_t ldx, void* Y, int64_t ldy,
+                                void* work, cudaStream_t st) {
+    const int64_t nm = (int64_t)F.n * MR;
+    const bool cplx = F.vtype == NDHSS_C128;
+    if (!cplx && F.prec == NDHSS_FP64)
+        return multi_apply_run<double, double>(F, nrhs, (const double*)X, ldx, (double*)Y, ldy, (double*)work,
+                                               (double*)work + nm, st);
+    if (!cplx)
+        return multi_apply_run<float, double>(F, nrhs, (const double*)X, ldx, (double*)Y, ldy, (float*)work,
+                                              (float*)work + nm, st);
+    if (F.prec == NDHSS_FP64)
+        return multi_apply_run<c128, c128>(F, nrhs, (const c128*)X, ldx, (c128*)Y, ldy, (c128*)work, (c128*)work + nm,
+                                           st);
+    return multi_apply_run<c64, c128>(F, nrhs, (const c128*)X, ldx, (c128*)Y, ldy, (c64*)work, (c64*)work + nm, st);
+}
+
+size_t multi_work_bytes(const FactorData& F) { return (size_t)2 * F.n * MR * F.esize + 256; }
+
+ndhss_status multi_supported(const FactorData& F, const char* who) {
+    if (!F.d_mjobs) return set_error(NDHSS_ERR_INVALID_ARG, "%s: the factorization has no multi-apply plan", who);
+    for (uint64_t p : F.lr_ptr)
+        if (p) return set_error(NDHSS_ERR_INVALID_ARG, "%s: compressed Gauss transforms are applied one column at a time (ndhss_apply)", who);
+    if (F.ulv) return set_error(NDHSS_ERR_INVALID_ARG, "%s: ULV factorizations are applied one column at a time (ndhss_apply)", who);
+    return NDHSS_OK;
+}
+
+// ---------------------------------------------------------- batched GMRES
+struct Seg {
+    int32_t s, row0, row1, pad;
+};
+
+enum : int32_t { ST_ACTIVE = 0, ST_STOPPED = 1, ST_CONVERGED = 2, ST_FAILED = 3, ST_PAD = 4 };
+
+struct BState {
+    double bnorm, zb, beta, inv, est, relres;
+    int32_t status, jend, its, cycles;
+};
+
+// Y(:, c) = A X(:, c) for the 32 interleaved columns: one warp per row, lane = column
+template <typename V>
+__global__ void spmm_kernel(int64_t n, const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+                            const V* __restrict__ vals, const V* __restrict__ X, V* __restrict__ Y) {
+    const int lane = threadIdx.x & 31;
+    const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t row = w0; row < n; row += nw) {
+        V acc = zero<V>();
+        for (int k = rowptr[row]; k < rowptr[row + 1]; ++k) acc = fmac(vals[k], X[(int64_t)col[k] * MR + lane], acc);
+        Y[row * MR + lane] = acc;
+    }
+}
+
+// part[blk][i][c] = sum over the block's rows of conj(V_i(row, c)) w(row, c), i < nvec
+template <typename V>
+__global__ void __launch_bounds__(256)
+bdot_kernel(const Seg* __restrict__ segs, const V* __restrict__ Vb, int64_t ldv, int nvec, const V* __restrict__ w,
+            V* __restrict__ part) {
+    __shared__ V red[8][8][MR];
+    const Seg sg = segs[blockIdx.x];
+    const int c = threadIdx.x & 31, rg = threadIdx.x >> 5;
+    for (int i0 = 0; i0 < nvec; i0 += 8) {
+        const int ni = min(8, nvec - i0);
+        V acc[8];
+#pragma unroll
+        for (int ii = 0; ii < 8; ++ii) acc[ii] = zero<V>();
+        for (int row = sg.row0 + rg; row < sg.row1; row += 8) {
+            const V wv = w[(int64_t)row * MR + c];
+#pragma unroll
+            for (int ii = 0; ii < 8; ++ii)
+                if (ii < ni) acc[ii] = fmac(conjv(Vb[(int64_t)(i0 + ii) * ldv + (int64_t)row * MR + c]), wv, acc[ii]);
+        }
+#pragma unroll
+        for (int ii = 0; ii < 8; ++ii) red[ii][rg][c] = acc[ii];
+        __syncthreads();
+        if (rg < ni) {
+            V sum = red[rg][0][c];
+            for (int g = 1; g < 8; ++g) sum = sum + red[rg][g][c];
+            part[((int64_t)blockIdx.x * BK + i0 + rg) * MR + c] = sum;
+        }
+        __syncthreads();
+    }
+}
+
+// out[i][s * 32 + c] = sum of problem s's blocks (block order)
+template <typename V>
+__global__ void breduce_kernel(int nsys, const int32_t* __restrict__ seg_off, int nvec, const V* __restrict__ part,
+                               V* __restrict__ out) {
+    const int Q = nsys * MR;
+    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < Q * nvec; q += gridDim.x * blockDim.x) {
+        const int i = q / Q, sc = q % Q, s = sc / MR, c = sc % MR;
+        V sum = zero<V>();
+        for (int b = seg_off[s]; b < seg_off[s + 1]; ++b) sum = sum + part[((int64_t)b * BK + i) * MR + c];
+        out[(int64_t)i * Q + sc] = sum;
+    }
+}
+
+// w(row, c) += sign * sum_{i < nvec} V_i(row, c) h[i][s * 32 + c]
+template <typename V>
+__global__ void __launch_bounds__(256)
+baxpy_kernel(const Seg* __restrict__ segs, int nsys, const V* __restrict__ Vb, int64_t ldv, int nvec,
+             const V* __restrict__ h, double sign, V* __restrict__ w) {
+    __shared__ V sh[BK][MR];
+    const Seg sg = segs[blockIdx.x];
+    const int Q = nsys * MR;
+    for (int q = threadIdx.x; q < nvec * MR; q += blockDim.x) sh[q / MR][q % MR] = h[(int64_t)(q / MR) * Q + sg.s * MR + q % MR];
+    __syncthreads();
+    const int c = threadIdx.x & 31, rg = threadIdx.x >> 5;
+    for (int row = sg.row0 + rg; row < sg.row1; row += 8) {
+        V acc = zero<V>();
+        for (int i = 0; i < nvec; ++i) acc = fmac(Vb[(int64_t)i * ldv + (int64_t)row * MR + c], sh[i][c], acc);
+        V* p = w + (int64_t)row * MR + c;
+        *p = *p + scale(acc, sign);
+    }
+}
+
+// dst(row, c) = src(row, c) * f[s * 32 + c]
+template <typename V>
+__global__ void bscale_kernel(const Seg* __restrict__ segs, const BState* __restrict__ bs, const V* __restrict__ src,
+                              V* __restrict__ dst) {
+    const Seg sg = segs[blockIdx.x];
+    const int c = threadIdx.x & 31, rg = threadIdx.x >> 5;
+    const double f = bs[sg.s * MR + c].inv;
+    for (int row = sg.row0 + rg; row < sg.row1; row += 8) {
+        const int64_t e = (int64_t)row * MR + c;
+        dst[e] = scale(src[e], f);
+    }
+}
+
+template <typename V>
+__global__ void bsub_kernel(int64_t cnt, const V* __restrict__ a, const V* __restrict__ b, V* __restrict__ out) {
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < cnt; q += (int64_t)gridDim.x * blockDim.x)
+        out[q] = a[q] - b[q];
+}
+
+template <typename V>
+__global__ void binterleave_kernel(int64_t n, int nrhs, const V* __restrict__ b, int64_t ldb, V* __restrict__ Bi) {
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n * MR; q += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t row = q / MR;
+        const int c = (int)(q % MR);
+        Bi[q] = c < nrhs ? b[(int64_t)c * ldb + row] : zero<V>();
+    }
+}
+
+template <typename V>
+__global__ void bdeinterleave_kernel(int64_t n, int nrhs, const V* __restrict__ Xi, V* __restrict__ x, int64_t ldx) {
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n * nrhs; q += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t row = q % n;
+        const int c = (int)(q / n);
+        x[(int64_t)c * ldx + row] = Xi[row * MR + c];
+    }
+}
+
+// ||b_q||, padding columns and zero right-hand sides settle at once
+template <typename V>
+__global__ void binit_kernel(int Q, int nrhs, const V* __restrict__ nb2, BState* __restrict__ bs) {
+    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < Q; q += gridDim.x * blockDim.x) {
+        BState S{};
+        S.bnorm = sqrt(bre(nb2[q]));
+        S.zb = -1.0;
+        S.status = (q % MR) >= nrhs ? ST_PAD : (S.bnorm == 0.0 ? ST_CONVERGED : ST_ACTIVE);
+        bs[q] = S;
+    }
+}
+
+// cycle start: the true residual decides convergence; count the systems that go on
+template <typename V>
+__global__ void bcheck_kernel(int Q, const V* __restrict__ nr2, double tol, int maxit, BState* __restrict__ bs,
+                              int* __restrict__ count) {
+    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < Q; q += gridDim.x * blockDim.x) {
+        BState S = bs[q];
+        if (S.status == ST_ACTIVE || S.status == ST_STOPPED) {
+            S.relres = sqrt(bre(nr2[q])) / S.bnorm;
+            if (S.relres <= tol) S.status = ST_CONVERGED;
+            else if (S.its >= maxit) S.status = ST_FAILED;
+            else {
+                S.status = ST_ACTIVE;
+                S.cycles++;
+                atomicAdd(count, 1);
+            }
+            S.jend = 0;
+        }
+        bs[q] = S;
+    }
+}
+
+// beta = ||P^{-1} r||, g = beta e_1, first cycle: ||P^{-1} b|| = beta
+template <typename V>
+__global__ void bcycle_kernel(int Q, int ldg, const V* __restrict__ nz2, V* __restrict__ g, BState* __restrict__ bs) {
+    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < Q; q += gridDim.x * blockDim.x) {
+        BState S = bs[q];
+        S.inv = 0.0;
+        if (S.status == ST_ACTIVE) {
+            S.beta = sqrt(bre(nz2[q]));
+            if (S.zb < 0) S.zb = S.beta;
+            if (!(S.beta > 0.0) || !(S.zb > 0.0)) {
+                S.status = ST_FAILED;
+            } else {
+                S.inv = 1.0 / S.beta;
+                S.est = S.beta;
+                V* gq = g + (int64_t)q * ldg;
+                gq[0] = breal<V>(S.beta);
+                for (int i = 1; i < ldg; ++i) gq[i] = zero<V>();
+            }
+        }
+        bs[q] = S;
+    }
+}
+
+// Hessenberg column j of every active system, its Givens rotations and the
+// least-squares residual (as arnoldi_step_kernel of the one-system solver)
+template <typename V>
+__global__ void barnoldi_kernel(int Q, int j, int R, const V* __restrict__ h1, const V* __restrict__ h2,
+                                const V* __restrict__ nw2, V* __restrict__ H, V* __restrict__ g, double* __restrict__ cs,
+                                V* __restrict__ sn, BState* __restrict__ bs, double inner_tol, double cycle_rtol,
+                                int maxit, int* __restrict__ count) {
+    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < Q; q += gridDim.x * blockDim.x) {
+        BState S = bs[q];
+        if (S.status != ST_ACTIVE) {
+            S.inv = 0.0;
+            bs[q] = S;
+            continue;
+        }
+        V* Hj = H + ((int64_t)q * R + j) * (R + 1);
+        V* gq = g + (int64_t)q * (R + 1);
+        double* cq = cs + (int64_t)q * R;
+        V* sq = sn + (int64_t)q * R;
+        for (int i = 0; i <= j; ++i) Hj[i] = h1[(int64_t)i * Q + q] + h2[(int64_t)i * Q + q];
+        const double hn = sqrt(bre(nw2[q]));
+        Hj[j + 1] = breal<V>(hn);
+        for (int i = 0; i < j; ++i) {
+            const V t0 = scale(Hj[i], cq[i]) + sq[i] * Hj[i + 1];
+            const V t1 = scale(Hj[i + 1], cq[i]) - conjv(sq[i]) * Hj[i];
+            Hj[i] = t0;
+            Hj[i + 1] = t1;
+        }
+        const V a = Hj[j], b = Hj[j + 1];
+        double c;
+        V s;
+        const double aa = babs(a), ab = babs(b);
+        if (ab == 0.0) {
+            c = 1.0;
+            s = zero<V>();
+        } else if (aa == 0.0) {
+            c = 0.0;
+            s = scale(conjv(b), 1.0 / ab);
+        } else {
+            const double t = hypot(aa, ab);
+            c = aa / t;
+            s = scale(a, 1.0 / aa) * scale(conjv(b), 1.0 / t);
+        }
+        cq[j] = c;
+        sq[j] = s;
+        Hj[j] = scale(a, c) + s * b;
+        Hj[j + 1] = zero<V>();
+        const V gj = gq[j];
+        gq[j + 1] = -(conjv(s) * gj);
+        gq[j] = scale(gj, c);
+        S.est = babs(gq[j + 1]);
+        S.its++;
+        S.jend = j + 1;
+        S.inv = hn > 0 ? 1.0 / hn : 0.0;
+        if (S.est / S.zb <= inner_tol || S.est <= cycle_rtol * S.beta || hn == 0.0 || S.its >= maxit ||
+            j + 1 >= R) {
+            S.status = ST_STOPPED;
+            S.inv = 0.0;
+        } else {
+            atomicAdd(count, 1);
+        }
+        bs[q] = S;
+    }
+}
+
+// y = H(0:jend, 0:jend)^{-1} g(0:jend) per system, zero beyond jend
+template <typename V>
+__global__ void bhsolve_kernel(int Q, int R, const V* __restrict__ H, const V* __restrict__ g, const BState* __restrict__ bs,
+                               V* __restrict__ y) {
+    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < Q; q += gridDim.x * blockDim.x) {
+        const BState S = bs[q];
+        const int k = (S.status == ST_STOPPED || S.status == ST_ACTIVE) ? S.jend : 0;
+        const V* Hq = H + (int64_t)q * R * (R + 1);
+        const V* gq = g + (int64_t)q * (R + 1);
+        for (int i = BK - 1; i >= k; --i) y[(int64_t)i * Q + q] = zero<V>();
+        for (int i = k - 1; i >= 0; --i) {
+            V acc = gq[i];
+            for (int l = i + 1; l < k; ++l) acc = acc - Hq[(int64_t)l * (R + 1) + i] * y[(int64_t)l * Q + q];
+            y[(int64_t)i * Q + q] = acc * recip(Hq[(int64_t)i * (R + 1) + i]);
+        }
+    }
+}
+
+template <typename V>
+ndhss_status gmres_batched_run(const FactorData& F, const int32_t* rowptr, const int32_t* col, const V* vals,
+                               int nsys, const int64_t* sys_off, int nrhs, const V* b, int64_t ldb, V* x, int64_t ldx,
+                               const ndhss_gmres_opts& o, ndhss_gmres_stats* stats, cudaStream_t st) {
+    const int64_t n = F.n;
+    const int R = o.restart;
+    const int Q = nsys * MR;
+    const int64_t nm = n * MR;
+    std::vector<Seg> segs;
+    std::vector<int32_t> seg_off(nsys + 1, 0);
+    for (int s = 0; s < nsys; ++s) {
+        seg_off[s] = (int32_t)segs.size();
+        for (int64_t r0 = sys_off[s]; r0 < sys_off[s + 1]; r0 += SEG_ROWS)
+            segs.push_back({s, (int32_t)r0, (int32_t)std::min<int64_t>(r0 + SEG_ROWS, sys_off[s + 1]), 0});
+    }
+    seg_off[nsys] = (int32_t)segs.size();
+    const int nseg = (int)segs.size();
+    // workspace
+    size_t off = 0;
+    auto take = [&](size_t bytes) { size_t o2 = off; off += (bytes + 255) / 256 * 256; return o2; };
+    const size_t o_seg = take(sizeof(Seg) * std::max(nseg, 1)), o_soff = take(sizeof(int32_t) * (nsys + 1));
+    const size_t o_B = take(sizeof(V) * nm), o_X = take(sizeof(V) * nm), o_w = take(sizeof(V) * nm),
+                 o_t = take(sizeof(V) * nm), o_V = take(sizeof(V) * nm * (R + 1));
+    const size_t o_part = take(sizeof(V) * (size_t)std::max(nseg, 1) * BK * MR);
+    const size_t o_h1 = take(sizeof(V) * (size_t)BK * Q), o_h2 = take(sizeof(V) * (size_t)BK * Q),
+                 o_y = take(sizeof(V) * (size_t)BK * Q), o_n2 = take(sizeof(V) * (size_t)Q);
+    const size_t o_H = take(sizeof(V) * (size_t)Q * R * (R + 1)), o_g = take(sizeof(V) * (size_t)Q * (R + 1)),
+                 o_cs = take(sizeof(double) * (size_t)Q * R), o_sn = take(sizeof(V) * (size_t)Q * R);
+    const size_t o_bs = take(sizeof(BState) * Q), o_cnt = take(sizeof(int) * 4);
+    const size_t o_mw = take(multi_work_bytes(F));
+    void* work = nullptr;
+    NDHSS_CUDA_TRY(pool_malloc_async(&work, off, st));
+    unsigned char* W = static_cast<unsigned char*>(work);
+    Seg* d_seg = (Seg*)(W + o_seg);
+    int32_t* d_soff = (int32_t*)(W + o_soff);
+    V *Bi = (V*)(W + o_B), *Xi = (V*)(W + o_X), *w = (V*)(W + o_w), *t = (V*)(W + o_t), *Vb = (V*)(W + o_V);
+    V *part = (V*)(W + o_part), *h1 = (V*)(W + o_h1), *h2 = (V*)(W + o_h2), *yv = (V*)(W + o_y), *n2 = (V*)(W + o_n2);
+    V *H = (V*)(W + o_H), *g = (V*)(W + o_g), *sn = (V*)(W + o_sn);
+    double* cs = (double*)(W + o_cs);
+    BState* bs = (BState*)(W + o_bs);
+    int* cnt = (int*)(W + o_cnt);
+    void* mw = W + o_mw;
+    ndhss_status rc = NDHSS_OK;
+    auto fail = [&](ndhss_status r) {
+        cudaFreeAsync(work, st);
+        return r;
+    };
+    if (nseg > 0) NDHSS_CUDA_TRY(cudaMemcpyAsync(d_seg, segs.data(), sizeof(Seg) * nseg, cudaMemcpyHostToDevice, st));
+    NDHSS_CUDA_TRY(cudaMemcpyAsync(d_soff, seg_off.data(), sizeof(int32_t) * (nsys + 1), cudaMemcpyHostToDevice, st));
+    NDHSS_CUDA_TRY(cudaMemsetAsync(Xi, 0, sizeof(V) * nm, st));
+    const int eb = (int)std::min<int64_t>((nm + 255) / 256, 8 * 152);
+    const int qb = (Q + 255) / 256;
+    binterleave_kernel<V><<<eb, 256, 0, st>>>(n, nrhs, b, ldb, Bi);
+    NDHSS_LAUNCH_CHECK("binterleave_kernel");
+    auto dots = [&](const V* basis, int nvec, const V* vec, V* out) {
+        bdot_kernel<V><<<nseg, 256, 0, st>>>(d_seg, basis, nm, nvec, vec, part);
+        breduce_kernel<V><<<(Q * nvec + 255) / 256, 256, 0, st>>>(nsys, d_soff, nvec, part, out);
+    };
+    auto read_count = [&](int* h) -> ndhss_status {
+        NDHSS_CUDA_TRY(cudaMemcpyAsync(h, cnt, sizeof(int), cudaMemcpyDeviceToHost, st));
+        NDHSS_CUDA_TRY(cudaStreamSynchronize(st));
+        return NDHSS_OK;
+    };
+    const int sb = (int)std::min<int64_t>((n * 32 + 255) / 256, 16 * 152);
+    dots(Bi, 1, Bi, n2);
+    binit_kernel<V><<<qb, 256, 0, st>>>(Q, nrhs, n2, bs);
+    NDHSS_LAUNCH_CHECK("binit_kernel");
+    int napply = 0, nspmv = 0;
+    while (true) {
+        spmm_kernel<V><<<sb, 256, 0, st>>>(n, rowptr, col, vals, Xi, t);
+        ++nspmv;
+        bsub_kernel<V><<<eb, 256, 0, st>>>(nm, Bi, t, w);
+        dots(w, 1, w, n2);
+        NDHSS_CUDA_TRY(cudaMemsetAsync(cnt, 0, sizeof(int), st));
+        bcheck_kernel<V><<<qb, 256, 0, st>>>(Q, n2, o.tol, o.maxit, bs, cnt);
+        NDHSS_LAUNCH_CHECK("bcheck_kernel");
+        int active = 0;
+        if ((rc = read_count(&active))) return fail(rc);
+        if (active == 0) break;
+        if ((rc = multi_apply_device(F, MR, w, MR, t, MR, mw, st))) return fail(rc);
+        ++napply;
+        dots(t, 1, t, n2);
+        bcycle_kernel<V><<<qb, 256, 0, st>>>(Q, R + 1, n2, g, bs);
+        bscale_kernel<V><<<nseg, 256, 0, st>>>(d_seg, bs, t, Vb);
+        NDHSS_LAUNCH_CHECK("bscale_kernel");
+        int jend = 0;
+        for (int j = 0; j < R; ++j) {
+            spmm_kernel<V><<<sb, 256, 0, st>>>(n, rowptr, col, vals, Vb + (int64_t)j * nm, w);
+            ++nspmv;
+            if ((rc = multi_apply_device(F, MR, w, MR, t, MR, mw, st))) return fail(rc);
+            ++napply;
+            dots(Vb, j + 1, t, h1);
+            baxpy_kernel<V><<<nseg, 256, 0, st>>>(d_seg, nsys, Vb, nm, j + 1, h1, -1.0, t);
+            dots(Vb, j + 1, t, h2);
+            baxpy_kernel<V><<<nseg, 256, 0, st>>>(d_seg, nsys, Vb, nm, j + 1, h2, -1.0, t);
+            dots(t, 1, t, n2);
+            NDHSS_CUDA_TRY(cudaMemsetAsync(cnt, 0, sizeof(int), st));
+            barnoldi_kernel<V><<<qb, 256, 0, st>>>(Q, j, R, h1, h2, n2, H, g, cs, sn, bs, o.inner * o.tol, o.cycle_rtol,
+                                                   o.maxit, cnt);
+            bscale_kernel<V><<<nseg, 256, 0, st>>>(d_seg, bs, t, Vb + (int64_t)(j + 1) * nm);
+            NDHSS_LAUNCH_CHECK("barnoldi_kernel");
+            jend = j + 1;
+            if ((rc = read_count(&active))) return fail(rc);
+            if (active == 0) break;
+        }
+        bhsolve_kernel<V><<<qb, 256, 0, st>>>(Q, R, H, g, bs, yv);
+        baxpy_kernel<V><<<nseg, 256, 0, st>>>(d_seg, nsys, Vb, nm, jend, yv, 1.0, Xi);
+        NDHSS_LAUNCH_CHECK("baxpy_kernel");
+    }
+    bdeinterleave_kernel<V><<<eb, 256, 0, st>>>(n, nrhs, Xi, x, ldx);
+    NDHSS_LAUNCH_CHECK("bdeinterleave_kernel");
+    std::vector<BState> hb(Q);
+    NDHSS_CUDA_TRY(cudaMemcpyAsync(hb.data(), bs, sizeof(BState) * Q, cudaMemcpyDeviceToHost, st));
+    cudaFreeAsync(work, st);
+    NDHSS_CUDA_TRY(cudaStreamSynchronize(st));
+    bool all = true;
+    for (int s = 0; s < nsys; ++s)
+        for (int c = 0; c < nrhs; ++c) {
+            const BState& S = hb[s * MR + c];
+            ndhss_gmres_stats Z{};
+            Z.iters = S.its;
+            Z.cycles = S.cycles;
+            Z.converged = S.status == ST_CONVERGED ? 1 : 0;
+            Z.true_relres = S.relres;
+            Z.precond_relres = S.zb > 0 ? S.est / S.zb : 0.0;
+            Z.napply = napply;
+            Z.nspmv = nspmv;
+            if (stats) stats[(int64_t)s * nrhs + c] = Z;
+            all = all && Z.converged;
+        }
+    if (!all) return set_error(NDHSS_ERR_NOT_CONVERGED, "ndhss_gmres_batched: tolerance not reached within maxit");
+    return NDHSS_OK;
+}
+
+}  // namespace
+
+// The multi-apply plan: per level the (node, first row) of every 64-row tile
+// of the up-sweep (all m rows of the first m_i columns) and of the down-sweep
+// (the m_i rows of R), one device array.
+ndhss_status build_multi_plan(FactorData& F, cudaStream_t st) {
+    std::vector<int32_t> jobs;
+    F.mj_up_off.assign(F.depth + 2, 0);
+    F.mj_dn_off.assign(F.depth + 2, 0);
+    for (int l = 0; l <= F.depth; ++l) {
+        F.mj_up_off[l] = (int64_t)jobs.size() / 2;
+        for (int s : F.levels[l]) {
+            const int mi = F.m_i(s), m = mi + F.m_b(s);
+            if (mi == 0) continue;
+            for (int r0 = 0; r0 < m; r0 += MT_ROWS) { jobs.push_back(s); jobs.push_back(r0); }
+        }
+    }
+    F.mj_up_off[F.depth + 1] = (int64_t)jobs.size() / 2;
+    for (int l = 0; l <= F.depth; ++l) {
+        F.mj_dn_off[l] = (int64_t)jobs.size() / 2;
+        for (int s : F.levels[l]) {
+            const int mi = F.m_i(s);
+            if (mi == 0 || F.m_b(s) == 0) continue;
+            for (int r0 = 0; r0 < mi; r0 += MT_ROWS) { jobs.push_back(s); jobs.push_back(r0); }
+        }
+    }
+    F.mj_dn_off[F.depth + 1] = (int64_t)jobs.size() / 2;
+    if (jobs.empty()) jobs.assign(2, 0);
+    void* p = nullptr;
+    NDHSS_CUDA_TRY(pool_malloc_async(&p, jobs.size() * sizeof(int32_t), st));
+    NDHSS_CUDA_TRY(cudaMemcpyAsync(p, jobs.data(), jobs.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    NDHSS_CUDA_TRY(cudaStreamSynchronize(st));
+    F.d_mjobs = static_cast<int2*>(p);
+    F.dev_bytes += (int64_t)(jobs.size() * sizeof(int32_t));
+    return NDHSS_OK;
+}
+
+}  // namespace ndhss
+
+extern "C" {
+
+ndhss_status ndhss_apply_multi(const ndhss_factorization* fh, int32_t nrhs, const void* d_x, int64_t ldx, void* d_y,
+                               int64_t ldy, void* stream) {
+    using namespace ndhss;
+    clear_error();
+    if (!fh || !d_x || !d_y || nrhs < 0 || nrhs > MR || ldx < nrhs || ldy < nrhs)
+        return set_error(NDHSS_ERR_INVALID_ARG, "ndhss_apply_multi: bad argument (need 0 <= nrhs <= 32 <= ld)");
+    const FactorData& F = fh->f;
+    if (nrhs == 0 || F.n == 0) return NDHSS_OK;
+    if (!is_device_ptr(d_x) || !is_device_ptr(d_y))
+        return set_error(NDHSS_ERR_INVALID_ARG, "ndhss_apply_multi: x and y must be device pointers");
+    ndhss_status rc = multi_supported(F, "ndhss_apply_multi");
+    if (rc != NDHSS_OK) return rc;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    void* work = nullptr;
+    NDHSS_CUDA_TRY(pool_malloc_async(&work, multi_work_bytes(F), st));
+    rc = multi_apply_device(F, nrhs, d_x, ldx, d_y, ldy, work, st);
+    cudaFreeAsync(work, st);
+    if (rc == NDHSS_OK && cudaStreamSynchronize(st) != cudaSuccess)
+        rc = set_error(NDHSS_ERR_CUDA, "ndhss_apply_multi: %s", cudaGetErrorString(cudaGetLastError()));
+    return rc;
+}
+
+ndhss_status ndhss_gmres_batched(const ndhss_factorization* fh, const int32_t* d_rowptr, const int32_t* d_col,
+                                 const void* d_vals, int32_t nsys, const int64_t* sys_off, int32_t nrhs, const void* d_b,
+                                 int64_t ldb, void* d_x, int64_t ldx, const ndhss_gmres_opts* opts,
+                                 ndhss_gmres_stats* stats, void* stream) {
+    using namespace ndhss;
+    clear_error();
+    if (!fh || !d_rowptr || !d_col || !d_vals || !sys_off || !d_b || !d_x || nsys < 1 || nrhs < 0 || nrhs > MR)
+        return set_error(NDHSS_ERR_INVALID_ARG, "ndhss_gmres_batched: bad argument (need nsys >= 1, 0 <= nrhs <= 32)");
+    const FactorData& F = fh->f;
+    if (ldb < F.n || ldx < F.n) return set_error(NDHSS_ERR_INVALID_ARG, "ndhss_gmres_batched: leading dimension < n");
+    if (sys_off[0] != 0 || sys_off[nsys] != F.n)
+        return set_error(NDHSS_ERR_INVALID_ARG, "ndhss_gmres_batched: sys_off must run from 0 to n");
+    for (int s = 0; s < nsys; ++s)
+        if (sys_off[s + 1] < sys_off[s]) return set_error(NDHSS_ERR_INVALID_ARG, "ndhss_gmres_batched: sys_off decreases");
+    if (!is_device_ptr(d_b) || !is_device_ptr(d_x))
+        return set_error(NDHSS_ERR_INVALID_ARG, "ndhss_gmres_batched: b and x must be device pointers");
+    ndhss_gmres_opts o{30, 300, 1e-8, 0, 0, 0.1, -1.0};
+    if (opts) o = *opts;
+    if (o.restart < 1 || o.restart > BK - 1 || o.maxit < 0 || !(o.tol >= 0) || !(o.inner > 0 && o.inner <= 1))
+        return set_error(NDHSS_ERR_INVALID_ARG, "ndhss_gmres_batched: need 1 <= restart <= %d, maxit >= 0, tol >= 0, 0 < inner <= 1",
+                         BK - 1);
+    if (nrhs == 0) return NDHSS_OK;
+    ndhss_status rc = multi_supported(F, "ndhss_gmres_batched");
+    if (rc != NDHSS_OK) return rc;
+    if (o.cycle_rtol < 0) o.cycle_rtol = (F.prec == NDHSS_FP64) ? 0.0 : 1e-4;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (F.vtype == NDHSS_R64)
+        rc = gmres_batched_run<double>(F, d_rowptr, d_col, (const double*)d_vals, nsys, sys_off, nrhs, (const double*)d_b,
+                                       ldb, (double*)d_x, ldx, o, stats, st);
+    else
+        rc = gmres_batched_run<c128>(F, d_rowptr, d_col, (const c128*)d_vals, nsys, sys_off, nrhs, (const c128*)d_b, ldb,
+                                     (c128*)d_x, ldx, o, stats, st);
+    if (rc == NDHSS_OK || rc == NDHSS_ERR_NOT_CONVERGED) {
+        const ndhss_status r2 = apply_check_error(F, "ndhss_gmres_batched");
+        if (r2 != NDHSS_OK) rc = r2;
+    }
+    return rc;
+}
+
+}  // extern "C"

@@ -25,7 +25,8 @@ STATUS = {0: "OK", 1: "INVALID_ARG", 2: "OOM", 3: "SINGULAR", 4: "RANK_CAP", 5: 
 EXPORTED = ("ndhss_version", "ndhss_last_error", "ndhss_kernel_launches", "ndhss_build_tree", "ndhss_tree_sizes", "ndhss_tree_export",
             "ndhss_tree_destroy", "ndhss_factor", "ndhss_factor_stats_get", "ndhss_factor_get_block",
             "ndhss_factor_destroy", "ndhss_apply", "ndhss_apply_noalloc", "ndhss_spmv", "ndhss_gmres",
-            "ndhss_testing_stall_apply", "ndhss_elem_qform", "ndhss_build_tree_batched")
+            "ndhss_testing_stall_apply", "ndhss_elem_qform", "ndhss_build_tree_batched", "ndhss_apply_multi",
+            "ndhss_gmres_batched")
 
 
 class NdhssError(RuntimeError):
@@ -314,6 +315,35 @@ def ndhss_gmres(f: Factor, d_rowptr, d_col, d_vals, b, x, restart=30, maxit=300,
         return st.as_dict()
     _check(code)
     return st.as_dict()
+
+
+def ndhss_apply_multi(f: Factor, X, Y, stream=None):
+    """Y = P^{-1} X for up to 32 right-hand sides stored interleaved: X, Y
+    contiguous (n, nrhs) torch CUDA tensors (row = DOF, column = right-hand side)."""
+    if X.ndim != 2 or X.shape[0] != f.n or tuple(Y.shape) != tuple(X.shape):
+        raise ValueError("X and Y must both have shape (n, nrhs)")
+    nrhs = int(X.shape[1])
+    _check(load().ndhss_apply_multi(f.handle, nrhs, _ptr(X), nrhs, _ptr(Y), nrhs, _stream(stream)))
+    return Y
+
+
+def ndhss_gmres_batched(f: Factor, d_rowptr, d_col, d_vals, sys_off, B, X, restart=30, maxit=300, tol=1e-8,
+                        stream=None, raise_on_nonconvergence=False, inner=0.1, cycle_rtol=-1.0):
+    """Solve the batch's systems in lockstep.  B, X: (nrhs, n) contiguous torch
+    CUDA tensors (column-major n x nrhs); ``sys_off`` the problems' row offsets
+    [nsys + 1].  Returns a list (per problem) of lists (per right-hand side)
+    of stats dicts."""
+    n = f.n
+    off = np.ascontiguousarray(sys_off, dtype=np.int64)
+    nsys = off.size - 1
+    nrhs = int(B.shape[0]) if B.ndim == 2 else 1
+    st = (GmresStats * max(nsys * nrhs, 1))()
+    o = GmresOpts(int(restart), int(maxit), float(tol), 0, 0, float(inner), float(cycle_rtol))
+    code = load().ndhss_gmres_batched(f.handle, _ptr(d_rowptr), _ptr(d_col), _ptr(d_vals), nsys, _ptr(off), nrhs,
+                                      _ptr(B), n, _ptr(X), n, C.byref(o), st, _stream(stream))
+    if not (code == 5 and not raise_on_nonconvergence):
+        _check(code)
+    return [[st[s * nrhs + c].as_dict() for c in range(nrhs)] for s in range(nsys)]
 
 
 class DeviceCSR:
