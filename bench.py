@@ -37,6 +37,11 @@ if ROOT not in sys.path:
 METRIC = "solves/s and factor time at rel. residual 1e-8: mixed vs FP64 GPU path"
 WORKLOAD = dict(N=256, p=2, k=40.0, seed=0, leaf=64, tol=1e-8, hss_levels=4, eps_hss=1e-6, beta=64)
 
+# batched side line: independent Helmholtz problems on uneven grids
+# (N_x, N_y ~ U{64..256}, wave speed on 8 x 8 macro blocks ~ U[1, 3], 10 points
+# per wavelength, impedance), 32 Gaussian sources each, complex64 dense fronts
+BATCH = dict(count=64, seed=0, nmin=64, nmax=256, nrhs=32, leaf=64, tol=1e-8)
+
 # ncu DRAM traffic of the dominant kernel class, per launch, keyed by the
 # sha256 of the source file it was measured on (null once the source changes)
 NCU_TRAFFIC = {
@@ -55,6 +60,8 @@ def _args():
     ap.add_argument("--only", choices=["mixed", "fp64"], help="time one precision only (profiling runs)")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer measurement (profiling runs)")
     ap.add_argument("--N", type=int, default=WORKLOAD["N"], help="cells per side (default: the benchmark workload)")
+    ap.add_argument("--batch-count", type=int, default=BATCH["count"],
+                    help="problems of the batched side line (0 = skip it)")
     ap.add_argument("--hss-levels", type=int, default=WORKLOAD["hss_levels"],
                     help="compress fronts on levels <= depth - this (Alg. 3.4); -1 = exact dense fronts")
     return ap.parse_args()
@@ -362,11 +369,90 @@ def run_gpu(a):
         "factor_kernel_ms": {k: round(v, 3) for k, v in cls_ms.items()},
         "clocks": mx["clocks"],
     }
+    if a.batch_count > 0:
+        line["batched"] = batched_line(a, ndhss, torch, stream)
     if not a.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = cpu_baseline(P)
     print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
+
+
+def batched_line(a, ndhss, torch, stream):
+    """The batched workload: every step factors the forest of all problems
+    (one call, complex64 dense fronts) and solves problems x 32 right-hand
+    sides in lockstep to a true relative residual of 1e-8 each."""
+    import numpy as np
+
+    from ndhss_inputs import helmholtz_batch
+
+    t0 = time.time()
+    probs = helmholtz_batch(a.batch_count, BATCH["seed"], nmin=BATCH["nmin"], nmax=BATCH["nmax"], nsrc=BATCH["nrhs"])
+    tree = ndhss.ndhss_build_tree_batched([(P.coords, P.A.indptr, P.A.indices) for P in probs], BATCH["leaf"])
+    A, off = ndhss.batch_csr([P.A for P in probs])
+    setup_s = time.time() - t0
+    M = ndhss.DeviceCSR(A)
+    n = A.shape[0]
+    Bh = np.zeros((BATCH["nrhs"], n), dtype=np.complex128)
+    for s, P in enumerate(probs):
+        Bh[:, off[s]:off[s + 1]] = P.b.T
+    B = torch.from_numpy(Bh).cuda()
+    X = torch.zeros_like(B)
+    opts = ndhss.make_factor_opts(prec=ndhss.NDHSS_FP32, hss_levels=-1)
+
+    def step():
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        e0.record(stream)
+        f = ndhss.ndhss_factor(tree, M.vtype, M.rowptr, M.col, M.vals, opts, stream=stream)
+        e1.record(stream)
+        st = ndhss.ndhss_gmres_batched(f, M.rowptr, M.col, M.vals, off, B, X, tol=BATCH["tol"], stream=stream)
+        e2.record(stream)
+        torch.cuda.synchronize()
+        return f, st, e0.elapsed_time(e1), e1.elapsed_time(e2)
+
+    for _ in range(max(1, min(a.warmup, 2))):
+        f, st, _, _ = step()
+        del f
+    steps = max(1, min(a.steps, 5))
+    fms, sms = [], []
+    l0 = ndhss.ndhss_kernel_launches()
+    for _ in range(steps):
+        f, st, tf, ts = step()
+        fms.append(tf)
+        sms.append(ts)
+    launches = (ndhss.ndhss_kernel_launches() - l0) // steps
+    flat = [d for row in st for d in row]
+    # the 32-column apply alone (events around ndhss_apply_multi on interleaved vectors)
+    Xi = torch.randn((n, BATCH["nrhs"]), dtype=torch.complex128, device="cuda")
+    Yi = torch.empty_like(Xi)
+    ndhss.ndhss_apply_multi(f, Xi, Yi, stream=stream)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    ev[0].record(stream)
+    for _ in range(5):
+        ndhss.ndhss_apply_multi(f, Xi, Yi, stream=stream)
+    ev[1].record(stream)
+    torch.cuda.synchronize()
+    ap_ms = ev[0].elapsed_time(ev[1]) / 5
+    fs = ndhss.ndhss_factor_stats_get(f)
+    del f
+    # algorithmic work of one 32-column apply: every stored front element of
+    # the first m_i columns and of R read once, 32 complex multiply-adds each
+    ni = ndhss.ndhss_tree_export(tree)["node_info"]
+    mi, mb = ni[:, 5].astype(np.int64), ni[:, 7].astype(np.int64)
+    elems = int(np.sum(mi * (mi + mb) + mi * mb))
+    flops = 8.0 * BATCH["nrhs"] * elems
+    nsolve = len(probs) * BATCH["nrhs"]
+    solve_ms = sum(sms) / steps
+    return {"workload": f"helmholtz_macro_p1 x{len(probs)} (grids {BATCH['nmin']}..{BATCH['nmax']}, "
+                        f"c on 8x8 macro blocks U[1,3], 10 ppw, impedance)",
+            "problems": len(probs), "rhs_per_problem": BATCH["nrhs"], "n_total": int(n), "nnz_total": int(A.nnz),
+            "solves_per_step": nsolve, "steps": steps, "factor_ms": sum(fms) / steps, "solve_ms": solve_ms,
+            "solves_per_s": nsolve / (solve_ms / 1e3), "iters_median": int(statistics.median(d["iters"] for d in flat)),
+            "iters_max": max(d["iters"] for d in flat), "true_relres_max": max(d["true_relres"] for d in flat),
+            "converged": all(d["converged"] for d in flat), "gpu_launches_per_step": int(launches),
+            "factor_bytes": fs["factor_bytes"], "apply_multi_ms": ap_ms,
+            "apply_multi_tflops": flops / (ap_ms / 1e3) / 1e12, "apply_multi_flops": flops,
+            "host_setup_s": setup_s}
 
 
 # ------------------------------------------------------------- CPU oracle

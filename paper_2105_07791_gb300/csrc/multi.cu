@@ -75,12 +75,13 @@ template <typename T, bool UP>
 __global__ void __launch_bounds__(256)
 mapply_kernel(const int2* __restrict__ jobs, const int32_t* __restrict__ node, const int64_t* __restrict__ foff,
               const T* __restrict__ front, const int32_t* __restrict__ sigma, const int32_t* __restrict__ blist,
-              T* __restrict__ U, T* __restrict__ Z) {
+              T* __restrict__ U, T* __restrict__ Z, const int* __restrict__ pact, const int32_t* __restrict__ nprob) {
     __shared__ T As[MT_K][MT_ROWS];
     __shared__ T Bs[MT_K][MR];
     __shared__ int s_row[MT_K];
     const int2 J = jobs[blockIdx.x];
     const int s = J.x, r0 = J.y;
+    if (pact && !pact[nprob[s]]) return;          // a problem whose systems all stopped
     const int32_t* nd = node + (size_t)s * 14;
     const int i_off = nd[4], m_i = nd[5], b_off = nd[6], m_b = nd[7];
     const int64_t m = (int64_t)m_i + m_b;
@@ -145,7 +146,7 @@ mapply_kernel(const int2* __restrict__ jobs, const int32_t* __restrict__ node, c
 
 template <typename T, typename V>
 ndhss_status multi_apply_run(const FactorData& F, int nrhs, const V* X, int64_t ldx, V* Y, int64_t ldy, T* U, T* Z,
-                             cudaStream_t st) {
+                             const int* pact, const int32_t* nprob, cudaStream_t st) {
     const int64_t n = F.n;
     const int eb = (int)std::min<int64_t>((n * MR + 255) / 256, 8 * 152);
     mgather_kernel<T, V><<<eb, 256, 0, st>>>(n, nrhs, F.d_perm, X, ldx, U);
@@ -155,14 +156,14 @@ ndhss_status multi_apply_run(const FactorData& F, int nrhs, const V* X, int64_t 
         const int64_t a = F.mj_up_off[l], b = F.mj_up_off[l + 1];
         if (b == a) continue;
         mapply_kernel<T, true><<<(unsigned)(b - a), 256, 0, st>>>(F.d_mjobs + a, F.d_node, F.d_foff, front, F.d_sigma,
-                                                                 F.d_blist, U, Z);
+                                                                 F.d_blist, U, Z, pact, nprob);
         NDHSS_LAUNCH_CHECK("mapply_kernel");
     }
     for (int l = 0; l <= F.depth; ++l) {
         const int64_t a = F.mj_dn_off[l], b = F.mj_dn_off[l + 1];
         if (b == a) continue;
         mapply_kernel<T, false><<<(unsigned)(b - a), 256, 0, st>>>(F.d_mjobs + a, F.d_node, F.d_foff, front,
-                                                                  F.d_sigma, F.d_blist, U, Z);
+                                                                  F.d_sigma, F.d_blist, U, Z, pact, nprob);
         NDHSS_LAUNCH_CHECK("mapply_kernel");
     }
     mscatter_kernel<T, V><<<eb, 256, 0, st>>>(n, nrhs, F.d_perm, Z, Y, ldy);
@@ -171,21 +172,25 @@ ndhss_status multi_apply_run(const FactorData& F, int nrhs, const V* X, int64_t 
 }
 
 // X, Y: n x ld interleaved float64 / complex128 (per the factor's vtype);
-// work: 2 n x 32 front-type elements
+// work: 2 n x 32 front-type elements; pact / nprob (or null): a node's
+// tiles are skipped when pact[nprob[node]] == 0 (rows of a problem the
+// caller no longer reads)
 ndhss_status multi_apply_device(const FactorData& F, int nrhs, const void* X, int64_t ldx, void* Y, int64_t ldy,
-                                void* work, cudaStream_t st) {
+                                void* work, cudaStream_t st, const int* pact = nullptr,
+                                const int32_t* nprob = nullptr) {
     const int64_t nm = (int64_t)F.n * MR;
     const bool cplx = F.vtype == NDHSS_C128;
     if (!cplx && F.prec == NDHSS_FP64)
         return multi_apply_run<double, double>(F, nrhs, (const double*)X, ldx, (double*)Y, ldy, (double*)work,
-                                               (double*)work + nm, st);
+                                               (double*)work + nm, pact, nprob, st);
     if (!cplx)
         return multi_apply_run<float, double>(F, nrhs, (const double*)X, ldx, (double*)Y, ldy, (float*)work,
-                                              (float*)work + nm, st);
+                                              (float*)work + nm, pact, nprob, st);
     if (F.prec == NDHSS_FP64)
         return multi_apply_run<c128, c128>(F, nrhs, (const c128*)X, ldx, (c128*)Y, ldy, (c128*)work, (c128*)work + nm,
-                                           st);
-    return multi_apply_run<c64, c128>(F, nrhs, (const c128*)X, ldx, (c128*)Y, ldy, (c64*)work, (c64*)work + nm, st);
+                                           pact, nprob, st);
+    return multi_apply_run<c64, c128>(F, nrhs, (const c128*)X, ldx, (c128*)Y, ldy, (c64*)work, (c64*)work + nm, pact,
+                                      nprob, st);
 }
 
 size_t multi_work_bytes(const FactorData& F) { return (size_t)2 * F.n * MR * F.esize + 256; }
@@ -210,27 +215,31 @@ struct BState {
     int32_t status, jend, its, cycles;
 };
 
-// Y(:, c) = A X(:, c) for the 32 interleaved columns: one warp per row, lane = column
+// Y(:, c) = A X(:, c) for the 32 interleaved columns of one block of rows
+// per CTA: one warp per row, lane = column; blocks of a problem with
+// pact[s] == 0 are skipped (pact null: every block)
 template <typename V>
-__global__ void spmm_kernel(int64_t n, const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col,
-                            const V* __restrict__ vals, const V* __restrict__ X, V* __restrict__ Y) {
-    const int lane = threadIdx.x & 31;
-    const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t row = w0; row < n; row += nw) {
+__global__ void __launch_bounds__(256)
+spmm_kernel(const Seg* __restrict__ segs, const int* __restrict__ pact, const int32_t* __restrict__ rowptr,
+            const int32_t* __restrict__ col, const V* __restrict__ vals, const V* __restrict__ X, V* __restrict__ Y) {
+    const Seg sg = segs[blockIdx.x];
+    if (pact && !pact[sg.s]) return;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int row = sg.row0 + warp; row < sg.row1; row += 8) {
         V acc = zero<V>();
         for (int k = rowptr[row]; k < rowptr[row + 1]; ++k) acc = fmac(vals[k], X[(int64_t)col[k] * MR + lane], acc);
-        Y[row * MR + lane] = acc;
+        Y[(int64_t)row * MR + lane] = acc;
     }
 }
 
 // part[blk][i][c] = sum over the block's rows of conj(V_i(row, c)) w(row, c), i < nvec
 template <typename V>
 __global__ void __launch_bounds__(256)
-bdot_kernel(const Seg* __restrict__ segs, const V* __restrict__ Vb, int64_t ldv, int nvec, const V* __restrict__ w,
-            V* __restrict__ part) {
+bdot_kernel(const Seg* __restrict__ segs, const int* __restrict__ pact, const V* __restrict__ Vb, int64_t ldv, int nvec,
+            const V* __restrict__ w, V* __restrict__ part) {
     __shared__ V red[8][8][MR];
     const Seg sg = segs[blockIdx.x];
+    if (pact && !pact[sg.s]) return;
     const int c = threadIdx.x & 31, rg = threadIdx.x >> 5;
     for (int i0 = 0; i0 < nvec; i0 += 8) {
         const int ni = min(8, nvec - i0);
@@ -268,20 +277,29 @@ __global__ void breduce_kernel(int nsys, const int32_t* __restrict__ seg_off, in
     }
 }
 
-// w(row, c) += sign * sum_{i < nvec} V_i(row, c) h[i][s * 32 + c]
+// w(row, c) += sign * sum_{i < nvec} V_i(row, c) h[i][s * 32 + c]; blocks of a
+// problem with pact[s] == 0 are skipped; with bs, column c uses only its own
+// system's jend basis vectors (the others may hold stale rows)
 template <typename V>
 __global__ void __launch_bounds__(256)
-baxpy_kernel(const Seg* __restrict__ segs, int nsys, const V* __restrict__ Vb, int64_t ldv, int nvec,
-             const V* __restrict__ h, double sign, V* __restrict__ w) {
+baxpy_kernel(const Seg* __restrict__ segs, const int* __restrict__ pact, int nsys, const V* __restrict__ Vb,
+             int64_t ldv, int nvec, const V* __restrict__ h, double sign, V* __restrict__ w,
+             const BState* __restrict__ bs) {
     __shared__ V sh[BK][MR];
     const Seg sg = segs[blockIdx.x];
+    if (pact && !pact[sg.s]) return;
     const int Q = nsys * MR;
     for (int q = threadIdx.x; q < nvec * MR; q += blockDim.x) sh[q / MR][q % MR] = h[(int64_t)(q / MR) * Q + sg.s * MR + q % MR];
     __syncthreads();
     const int c = threadIdx.x & 31, rg = threadIdx.x >> 5;
+    int nv = nvec;
+    if (bs) {
+        const BState S = bs[sg.s * MR + c];
+        nv = (S.status == ST_STOPPED || S.status == ST_ACTIVE) ? min(nvec, S.jend) : 0;
+    }
     for (int row = sg.row0 + rg; row < sg.row1; row += 8) {
         V acc = zero<V>();
-        for (int i = 0; i < nvec; ++i) acc = fmac(Vb[(int64_t)i * ldv + (int64_t)row * MR + c], sh[i][c], acc);
+        for (int i = 0; i < nv; ++i) acc = fmac(Vb[(int64_t)i * ldv + (int64_t)row * MR + c], sh[i][c], acc);
         V* p = w + (int64_t)row * MR + c;
         *p = *p + scale(acc, sign);
     }
@@ -289,9 +307,10 @@ baxpy_kernel(const Seg* __restrict__ segs, int nsys, const V* __restrict__ Vb, i
 
 // dst(row, c) = src(row, c) * f[s * 32 + c]
 template <typename V>
-__global__ void bscale_kernel(const Seg* __restrict__ segs, const BState* __restrict__ bs, const V* __restrict__ src,
-                              V* __restrict__ dst) {
+__global__ void bscale_kernel(const Seg* __restrict__ segs, const int* __restrict__ pact, const BState* __restrict__ bs,
+                              const V* __restrict__ src, V* __restrict__ dst) {
     const Seg sg = segs[blockIdx.x];
+    if (pact && !pact[sg.s]) return;
     const int c = threadIdx.x & 31, rg = threadIdx.x >> 5;
     const double f = bs[sg.s * MR + c].inv;
     for (int row = sg.row0 + rg; row < sg.row1; row += 8) {
@@ -462,6 +481,15 @@ __global__ void bhsolve_kernel(int Q, int R, const V* __restrict__ H, const V* _
     }
 }
 
+// pact[s] = 1 when a system of problem s is still iterating in this cycle
+__global__ void bpact_kernel(int nsys, const BState* __restrict__ bs, int* __restrict__ pact) {
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < nsys; s += gridDim.x * blockDim.x) {
+        int a = 0;
+        for (int c = 0; c < MR; ++c) a |= bs[s * MR + c].status == ST_ACTIVE ? 1 : 0;
+        pact[s] = a;
+    }
+}
+
 template <typename V>
 ndhss_status gmres_batched_run(const FactorData& F, const int32_t* rowptr, const int32_t* col, const V* vals,
                                int nsys, const int64_t* sys_off, int nrhs, const V* b, int64_t ldb, V* x, int64_t ldx,
@@ -491,6 +519,7 @@ ndhss_status gmres_batched_run(const FactorData& F, const int32_t* rowptr, const
     const size_t o_H = take(sizeof(V) * (size_t)Q * R * (R + 1)), o_g = take(sizeof(V) * (size_t)Q * (R + 1)),
                  o_cs = take(sizeof(double) * (size_t)Q * R), o_sn = take(sizeof(V) * (size_t)Q * R);
     const size_t o_bs = take(sizeof(BState) * Q), o_cnt = take(sizeof(int) * 4);
+    const size_t o_pact = take(sizeof(int) * nsys), o_nprob = take(sizeof(int32_t) * std::max(F.nnodes, 1));
     const size_t o_mw = take(multi_work_bytes(F));
     void* work = nullptr;
     NDHSS_CUDA_TRY(pool_malloc_async(&work, off, st));
@@ -503,6 +532,8 @@ ndhss_status gmres_batched_run(const FactorData& F, const int32_t* rowptr, const
     double* cs = (double*)(W + o_cs);
     BState* bs = (BState*)(W + o_bs);
     int* cnt = (int*)(W + o_cnt);
+    int* pact = (int*)(W + o_pact);
+    int32_t* nprob = (int32_t*)(W + o_nprob);
     void* mw = W + o_mw;
     ndhss_status rc = NDHSS_OK;
     auto fail = [&](ndhss_status r) {
@@ -511,13 +542,22 @@ ndhss_status gmres_batched_run(const FactorData& F, const int32_t* rowptr, const
     };
     if (nseg > 0) NDHSS_CUDA_TRY(cudaMemcpyAsync(d_seg, segs.data(), sizeof(Seg) * nseg, cudaMemcpyHostToDevice, st));
     NDHSS_CUDA_TRY(cudaMemcpyAsync(d_soff, seg_off.data(), sizeof(int32_t) * (nsys + 1), cudaMemcpyHostToDevice, st));
+    // each node's problem: the one whose rows hold the node's I block
+    std::vector<int32_t> hprob(std::max(F.nnodes, 1), 0);
+    for (int v = 0; v < F.nnodes; ++v) {
+        const int64_t io = F.info(v, 4);
+        hprob[v] = (int32_t)(std::upper_bound(sys_off, sys_off + nsys + 1, io) - sys_off - 1);
+        hprob[v] = std::min(std::max(hprob[v], 0), nsys - 1);
+    }
+    NDHSS_CUDA_TRY(cudaMemcpyAsync(nprob, hprob.data(), sizeof(int32_t) * hprob.size(), cudaMemcpyHostToDevice, st));
+    NDHSS_CUDA_TRY(cudaStreamSynchronize(st));
     NDHSS_CUDA_TRY(cudaMemsetAsync(Xi, 0, sizeof(V) * nm, st));
     const int eb = (int)std::min<int64_t>((nm + 255) / 256, 8 * 152);
     const int qb = (Q + 255) / 256;
     binterleave_kernel<V><<<eb, 256, 0, st>>>(n, nrhs, b, ldb, Bi);
     NDHSS_LAUNCH_CHECK("binterleave_kernel");
-    auto dots = [&](const V* basis, int nvec, const V* vec, V* out) {
-        bdot_kernel<V><<<nseg, 256, 0, st>>>(d_seg, basis, nm, nvec, vec, part);
+    auto dots = [&](const V* basis, int nvec, const V* vec, V* out, const int* mask) {
+        bdot_kernel<V><<<nseg, 256, 0, st>>>(d_seg, mask, basis, nm, nvec, vec, part);
         breduce_kernel<V><<<(Q * nvec + 255) / 256, 256, 0, st>>>(nsys, d_soff, nvec, part, out);
     };
     auto read_count = [&](int* h) -> ndhss_status {
@@ -525,50 +565,52 @@ ndhss_status gmres_batched_run(const FactorData& F, const int32_t* rowptr, const
         NDHSS_CUDA_TRY(cudaStreamSynchronize(st));
         return NDHSS_OK;
     };
-    const int sb = (int)std::min<int64_t>((n * 32 + 255) / 256, 16 * 152);
-    dots(Bi, 1, Bi, n2);
+    const int pb = (nsys + 255) / 256;
+    dots(Bi, 1, Bi, n2, nullptr);
     binit_kernel<V><<<qb, 256, 0, st>>>(Q, nrhs, n2, bs);
     NDHSS_LAUNCH_CHECK("binit_kernel");
     int napply = 0, nspmv = 0;
     while (true) {
-        spmm_kernel<V><<<sb, 256, 0, st>>>(n, rowptr, col, vals, Xi, t);
+        spmm_kernel<V><<<nseg, 256, 0, st>>>(d_seg, nullptr, rowptr, col, vals, Xi, t);
         ++nspmv;
         bsub_kernel<V><<<eb, 256, 0, st>>>(nm, Bi, t, w);
-        dots(w, 1, w, n2);
+        dots(w, 1, w, n2, nullptr);
         NDHSS_CUDA_TRY(cudaMemsetAsync(cnt, 0, sizeof(int), st));
         bcheck_kernel<V><<<qb, 256, 0, st>>>(Q, n2, o.tol, o.maxit, bs, cnt);
         NDHSS_LAUNCH_CHECK("bcheck_kernel");
         int active = 0;
         if ((rc = read_count(&active))) return fail(rc);
         if (active == 0) break;
-        if ((rc = multi_apply_device(F, MR, w, MR, t, MR, mw, st))) return fail(rc);
+        bpact_kernel<<<pb, 256, 0, st>>>(nsys, bs, pact);
+        if ((rc = multi_apply_device(F, MR, w, MR, t, MR, mw, st, pact, nprob))) return fail(rc);
         ++napply;
-        dots(t, 1, t, n2);
+        dots(t, 1, t, n2, pact);
         bcycle_kernel<V><<<qb, 256, 0, st>>>(Q, R + 1, n2, g, bs);
-        bscale_kernel<V><<<nseg, 256, 0, st>>>(d_seg, bs, t, Vb);
+        bscale_kernel<V><<<nseg, 256, 0, st>>>(d_seg, pact, bs, t, Vb);
         NDHSS_LAUNCH_CHECK("bscale_kernel");
         int jend = 0;
         for (int j = 0; j < R; ++j) {
-            spmm_kernel<V><<<sb, 256, 0, st>>>(n, rowptr, col, vals, Vb + (int64_t)j * nm, w);
+            bpact_kernel<<<pb, 256, 0, st>>>(nsys, bs, pact);
+            spmm_kernel<V><<<nseg, 256, 0, st>>>(d_seg, pact, rowptr, col, vals, Vb + (int64_t)j * nm, w);
             ++nspmv;
-            if ((rc = multi_apply_device(F, MR, w, MR, t, MR, mw, st))) return fail(rc);
+            if ((rc = multi_apply_device(F, MR, w, MR, t, MR, mw, st, pact, nprob))) return fail(rc);
             ++napply;
-            dots(Vb, j + 1, t, h1);
-            baxpy_kernel<V><<<nseg, 256, 0, st>>>(d_seg, nsys, Vb, nm, j + 1, h1, -1.0, t);
-            dots(Vb, j + 1, t, h2);
-            baxpy_kernel<V><<<nseg, 256, 0, st>>>(d_seg, nsys, Vb, nm, j + 1, h2, -1.0, t);
-            dots(t, 1, t, n2);
+            dots(Vb, j + 1, t, h1, pact);
+            baxpy_kernel<V><<<nseg, 256, 0, st>>>(d_seg, pact, nsys, Vb, nm, j + 1, h1, -1.0, t, nullptr);
+            dots(Vb, j + 1, t, h2, pact);
+            baxpy_kernel<V><<<nseg, 256, 0, st>>>(d_seg, pact, nsys, Vb, nm, j + 1, h2, -1.0, t, nullptr);
+            dots(t, 1, t, n2, pact);
             NDHSS_CUDA_TRY(cudaMemsetAsync(cnt, 0, sizeof(int), st));
             barnoldi_kernel<V><<<qb, 256, 0, st>>>(Q, j, R, h1, h2, n2, H, g, cs, sn, bs, o.inner * o.tol, o.cycle_rtol,
                                                    o.maxit, cnt);
-            bscale_kernel<V><<<nseg, 256, 0, st>>>(d_seg, bs, t, Vb + (int64_t)(j + 1) * nm);
+            bscale_kernel<V><<<nseg, 256, 0, st>>>(d_seg, pact, bs, t, Vb + (int64_t)(j + 1) * nm);
             NDHSS_LAUNCH_CHECK("barnoldi_kernel");
             jend = j + 1;
             if ((rc = read_count(&active))) return fail(rc);
             if (active == 0) break;
         }
         bhsolve_kernel<V><<<qb, 256, 0, st>>>(Q, R, H, g, bs, yv);
-        baxpy_kernel<V><<<nseg, 256, 0, st>>>(d_seg, nsys, Vb, nm, jend, yv, 1.0, Xi);
+        baxpy_kernel<V><<<nseg, 256, 0, st>>>(d_seg, nullptr, nsys, Vb, nm, jend, yv, 1.0, Xi, bs);
         NDHSS_LAUNCH_CHECK("baxpy_kernel");
     }
     bdeinterleave_kernel<V><<<eb, 256, 0, st>>>(n, nrhs, Xi, x, ldx);

@@ -188,12 +188,17 @@ def batch_csr(mats):
     """The block-diagonal CSR of scipy matrices ``mats`` (the layout the
     batched tree describes) and the DOF offsets [nsys + 1]."""
     import scipy.sparse as sp
-    A = sp.block_diag([m.tocsr() for m in mats], format="csr")
-    A.sort_indices()
-    A.indptr = A.indptr.astype(np.int32)
-    A.indices = A.indices.astype(np.int32)
+    mats = [m.tocsr() for m in mats]
     off = np.zeros(len(mats) + 1, dtype=np.int64)
     off[1:] = np.cumsum([m.shape[0] for m in mats])
+    eoff = np.zeros(len(mats) + 1, dtype=np.int64)
+    eoff[1:] = np.cumsum([m.nnz for m in mats])
+    indptr = np.concatenate([np.zeros(1, np.int64)] + [m.indptr[1:].astype(np.int64) + eoff[s]
+                                                      for s, m in enumerate(mats)])
+    indices = np.concatenate([m.indices.astype(np.int64) + off[s] for s, m in enumerate(mats)])
+    data = np.concatenate([m.data for m in mats])
+    n = int(off[-1])
+    A = sp.csr_matrix((data, indices.astype(np.int32), indptr.astype(np.int32)), shape=(n, n))
     return A, off
 
 
