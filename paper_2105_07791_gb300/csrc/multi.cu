@@ -36,13 +36,20 @@ namespace {
 constexpr int MR = 32;            // interleaved right-hand sides
 constexpr int MT_ROWS = 64;       // rows per apply tile
 constexpr int MT_K = 16;          // K chunk of an apply tile
-constexpr int SEG_ROWS = 2048;    // rows per reduction block
+constexpr int SEG_ROWS = 1024;    // rows per reduction block
 constexpr int BK = 32;            // restart + 1 <= BK
 
 __device__ __forceinline__ double babs(double a) { return fabs(a); }
 __device__ __forceinline__ double babs(c128 a) { return hypot(a.x, a.y); }
 __device__ __forceinline__ double bre(double a) { return a; }
 __device__ __forceinline__ double bre(c128 a) { return a.x; }
+// acc + a b; an entry with zero imaginary part (all but the impedance
+// entries of the Helmholtz matrices) takes two float64 FMAs instead of four
+__device__ __forceinline__ double bmac(double a, double b, double c) { return fma(a, b, c); }
+__device__ __forceinline__ c128 bmac(c128 a, c128 b, c128 c) {
+    if (a.y == 0.0) return {fma(a.x, b.x, c.x), fma(a.x, b.y, c.y)};
+    return fmac(a, b, c);
+}
 template <typename V> __device__ __forceinline__ V breal(double v);
 template <> __device__ __forceinline__ double breal<double>(double v) { return v; }
 template <> __device__ __forceinline__ c128 breal<c128>(double v) { return {v, 0.0}; }
@@ -227,38 +234,63 @@ spmm_kernel(const Seg* __restrict__ segs, const int* __restrict__ pact, const in
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int row = sg.row0 + warp; row < sg.row1; row += 8) {
         V acc = zero<V>();
-        for (int k = rowptr[row]; k < rowptr[row + 1]; ++k) acc = fmac(vals[k], X[(int64_t)col[k] * MR + lane], acc);
+        for (int k = rowptr[row]; k < rowptr[row + 1]; ++k) acc = bmac(vals[k], X[(int64_t)col[k] * MR + lane], acc);
         Y[(int64_t)row * MR + lane] = acc;
     }
 }
 
-// part[blk][i][c] = sum over the block's rows of conj(V_i(row, c)) w(row, c), i < nvec
+// part[blk][i][c] = sum over the block's rows of conj(V_i(row, c)) w(row, c),
+// i < nvec.  Lane = column, warp = a contiguous eighth of the block's rows,
+// four basis vectors per pass and four rows per iteration, so every warp has
+// 4 + 16 independent 512-byte loads in flight (the float64 accumulation
+// chains are too slow to wait on one load at a time).
 template <typename V>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, 4)
 bdot_kernel(const Seg* __restrict__ segs, const int* __restrict__ pact, const V* __restrict__ Vb, int64_t ldv, int nvec,
             const V* __restrict__ w, V* __restrict__ part) {
-    __shared__ V red[8][8][MR];
+    constexpr int NB = 4, UR = 4;
+    __shared__ V red[NB][8][MR];
     const Seg sg = segs[blockIdx.x];
     if (pact && !pact[sg.s]) return;
     const int c = threadIdx.x & 31, rg = threadIdx.x >> 5;
-    for (int i0 = 0; i0 < nvec; i0 += 8) {
-        const int ni = min(8, nvec - i0);
-        V acc[8];
+    const int len = sg.row1 - sg.row0, per = (len + 7) / 8;
+    const int r0 = sg.row0 + rg * per, r1 = min(sg.row1, r0 + per);
+    for (int i0 = 0; i0 < nvec; i0 += NB) {
+        const int ni = min(NB, nvec - i0);
+        V acc[NB];
 #pragma unroll
-        for (int ii = 0; ii < 8; ++ii) acc[ii] = zero<V>();
-        for (int row = sg.row0 + rg; row < sg.row1; row += 8) {
+        for (int ii = 0; ii < NB; ++ii) acc[ii] = zero<V>();
+        int row = r0;
+        for (; row + UR <= r1; row += UR) {
+            V wv[UR];
+#pragma unroll
+            for (int u = 0; u < UR; ++u) wv[u] = w[(int64_t)(row + u) * MR + c];
+#pragma unroll
+            for (int ii = 0; ii < NB; ++ii) {
+                if (ii < ni) {
+                    const V* vp = Vb + (int64_t)(i0 + ii) * ldv + (int64_t)row * MR + c;
+                    V vv[UR];
+#pragma unroll
+                    for (int u = 0; u < UR; ++u) vv[u] = vp[(int64_t)u * MR];
+#pragma unroll
+                    for (int u = 0; u < UR; ++u) acc[ii] = fmac(conjv(vv[u]), wv[u], acc[ii]);
+                }
+            }
+        }
+        for (; row < r1; ++row) {
             const V wv = w[(int64_t)row * MR + c];
 #pragma unroll
-            for (int ii = 0; ii < 8; ++ii)
+            for (int ii = 0; ii < NB; ++ii)
                 if (ii < ni) acc[ii] = fmac(conjv(Vb[(int64_t)(i0 + ii) * ldv + (int64_t)row * MR + c]), wv, acc[ii]);
         }
 #pragma unroll
-        for (int ii = 0; ii < 8; ++ii) red[ii][rg][c] = acc[ii];
+        for (int ii = 0; ii < NB; ++ii) red[ii][rg][c] = acc[ii];
         __syncthreads();
-        if (rg < ni) {
-            V sum = red[rg][0][c];
-            for (int g = 1; g < 8; ++g) sum = sum + red[rg][g][c];
-            part[((int64_t)blockIdx.x * BK + i0 + rg) * MR + c] = sum;
+        for (int q = threadIdx.x; q < ni * MR; q += blockDim.x) {
+            const int ii = q / MR, cc = q % MR;
+            V sum = red[ii][0][cc];
+            for (int g = 1; g < 8; ++g) sum = sum + red[ii][g][cc];
+            part[((int64_t)blockIdx.x * BK + i0 + ii) * MR + cc] = sum;
         }
         __syncthreads();
     }
