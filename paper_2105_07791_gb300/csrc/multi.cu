@@ -43,13 +43,6 @@ __device__ __forceinline__ double babs(double a) { return fabs(a); }
 __device__ __forceinline__ double babs(c128 a) { return hypot(a.x, a.y); }
 __device__ __forceinline__ double bre(double a) { return a; }
 __device__ __forceinline__ double bre(c128 a) { return a.x; }
-// acc + a b; an entry with zero imaginary part (all but the impedance
-// entries of the Helmholtz matrices) takes two float64 FMAs instead of four
-__device__ __forceinline__ double bmac(double a, double b, double c) { return fma(a, b, c); }
-__device__ __forceinline__ c128 bmac(c128 a, c128 b, c128 c) {
-    if (a.y == 0.0) return {fma(a.x, b.x, c.x), fma(a.x, b.y, c.y)};
-    return fmac(a, b, c);
-}
 template <typename V> __device__ __forceinline__ V breal(double v);
 template <> __device__ __forceinline__ double breal<double>(double v) { return v; }
 template <> __device__ __forceinline__ c128 breal<c128>(double v) { return {v, 0.0}; }
@@ -234,7 +227,7 @@ spmm_kernel(const Seg* __restrict__ segs, const int* __restrict__ pact, const in
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int row = sg.row0 + warp; row < sg.row1; row += 8) {
         V acc = zero<V>();
-        for (int k = rowptr[row]; k < rowptr[row + 1]; ++k) acc = bmac(vals[k], X[(int64_t)col[k] * MR + lane], acc);
+        for (int k = rowptr[row]; k < rowptr[row + 1]; ++k) acc = fmac(vals[k], X[(int64_t)col[k] * MR + lane], acc);
         Y[(int64_t)row * MR + lane] = acc;
     }
 }
