@@ -34,7 +34,7 @@ def test_exports_every_declared_symbol(nd):
 TREE_KEYS = ("perm", "node_info", "blist", "emap", "e_off", "e_row", "e_col", "e_idx")
 
 
-@pytest.mark.parametrize("case", ["c1", "p1_odd", "p2_small", "helm_p1", "leaf16", "tiny", "single_leaf"])
+@pytest.mark.parametrize("case", ["c1", "p1_odd", "p2_small", "helm_p1", "leaf16", "tiny", "single_leaf", "elastic_dg"])
 def test_tree_bit_exact_vs_oracle(nd, case):
     leaf = 64
     if case == "c1":
@@ -47,6 +47,9 @@ def test_tree_bit_exact_vs_oracle(nd, case):
         P = helmholtz_impedance(45, 1, 9.0)
     elif case == "leaf16":
         P, leaf = helmholtz_impedance(20, 1, 4.0), 16
+    elif case == "elastic_dg":
+        from ndhss_inputs.elastic import elastic_sipg
+        P, leaf = elastic_sipg(14, seed=1), 60          # 12 DOFs per cell share its coordinate
     elif case == "tiny":
         P, leaf = poisson_dirichlet(4), 2
     else:
