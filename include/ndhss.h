@@ -91,7 +91,11 @@ typedef struct {
     double cycle_rtol;          /* a cycle also ends once its residual estimate fell by
                                    this factor (what one reduced-precision apply can
                                    resolve); < 0 = automatic: 1e-4 for FP32 fronts,
-                                   0 (off) for FP64 fronts                            */
+                                   0 (off) for FP64 fronts.  After a cycle that did
+                                   not halve the true residual, later cycles of that
+                                   solve end only once their estimate fell by the
+                                   reduction the true residual still needs
+                                   (0.1 tol / relres, relative to the cycle start)   */
 } ndhss_gmres_opts;
 
 typedef struct {

@@ -6,7 +6,10 @@
 // reports), when it has fallen by cycle_rtol relative to the cycle's start
 // (with a reduced-precision preconditioner the Krylov estimate cannot be
 // trusted beyond what one apply resolves, so the float64 restart does the
-// refinement), after `restart` steps, on breakdown or at maxit.
+// refinement), after `restart` steps, on breakdown or at maxit.  Once a cycle
+// fails to halve the true residual, the next cycles end only when their
+// estimate fell by the reduction the true residual still needs, relative to
+// their own start.
 //
 // Per Arnoldi step j:  t = A v_j (CSR SpMV);  w = P^{-1} t (Algorithm 3.1);
 // classical Gram-Schmidt twice: h = V^H w, w -= V h (x2); ||w||; a one-thread
@@ -395,6 +398,12 @@ ndhss_status gmres_one(const FactorData& F, const int32_t* rowptr, const int32_t
     double zbnorm = -1.0;
     int its = 0, cycles = 0;
     double last_res = 1.0;
+    // After a cycle that did not halve the true residual (a preconditioner
+    // whose ||P^{-1} r|| / ||P^{-1} b|| no longer tracks ||r|| / ||b||), a cycle
+    // no longer ends on cycle_rtol or on the inner test against ||P^{-1} b||,
+    // but once its residual estimate fell by the factor the true residual
+    // still needs (0.1 tol / relres), relative to the cycle's start.
+    double rtol_eff = o.cycle_rtol, prev_rel = INFINITY, cyc_target = 0.0;
     while (true) {
         if ((rc = timed_spmv(x, t))) return rc;
         residual_kernel<V><<<eb, 256, 0, st>>>(n, b, t, r);
@@ -406,6 +415,13 @@ ndhss_status gmres_one(const FactorData& F, const int32_t* rowptr, const int32_t
         S.true_relres = rel;
         if (rel <= o.tol) { S.converged = 1; break; }
         if (its >= o.maxit) break;
+        if (rel > 0.5 * prev_rel) {
+            rtol_eff = 0.0;
+            cyc_target = 0.1 * o.tol / rel;
+        } else if (cyc_target > 0.0) {
+            cyc_target = 0.1 * o.tol / rel;
+        }
+        prev_rel = rel;
         ++cycles;
         if ((rc = timed_apply(r, w))) return rc;
         nrm2_kernel<V><<<RB, RT, 0, st>>>(n, w, dpart, nrm, counter);
@@ -442,7 +458,8 @@ ndhss_status gmres_one(const FactorData& F, const int32_t* rowptr, const int32_t
             if ((rc = read_scalars(stt, sizeof(GmState), hb))) return rc;
             jend = j + 1;
             last_res = hb[1] / zbnorm;
-            if (last_res <= o.inner * o.tol || hb[1] <= o.cycle_rtol * hb[3] || hb[2] == 0.0 || its >= o.maxit) break;
+            const bool inner_done = cyc_target > 0.0 ? hb[1] <= cyc_target * hb[3] : last_res <= o.inner * o.tol;
+            if (inner_done || hb[1] <= rtol_eff * hb[3] || hb[2] == 0.0 || its >= o.maxit) break;
         }
         hsolve_kernel<V><<<1, 1, 0, st>>>(jend, H, R + 1, g, yv);
         NDHSS_LAUNCH_CHECK("hsolve_kernel");

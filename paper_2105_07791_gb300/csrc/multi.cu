@@ -212,6 +212,8 @@ enum : int32_t { ST_ACTIVE = 0, ST_STOPPED = 1, ST_CONVERGED = 2, ST_FAILED = 3,
 
 struct BState {
     double bnorm, zb, beta, inv, est, relres;
+    double prev_rel, crtol;      // true residual of the previous cycle; this system's cycle_rtol
+    double ctgt;                 // > 0 after a stagnating cycle: the cycle-relative inner target
     int32_t status, jend, its, cycles;
 };
 
@@ -370,11 +372,13 @@ __global__ void bdeinterleave_kernel(int64_t n, int nrhs, const V* __restrict__ 
 
 // ||b_q||, padding columns and zero right-hand sides settle at once
 template <typename V>
-__global__ void binit_kernel(int Q, int nrhs, const V* __restrict__ nb2, BState* __restrict__ bs) {
+__global__ void binit_kernel(int Q, int nrhs, const V* __restrict__ nb2, double cycle_rtol, BState* __restrict__ bs) {
     for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < Q; q += gridDim.x * blockDim.x) {
         BState S{};
         S.bnorm = sqrt(bre(nb2[q]));
         S.zb = -1.0;
+        S.prev_rel = INFINITY;
+        S.crtol = cycle_rtol;
         S.status = (q % MR) >= nrhs ? ST_PAD : (S.bnorm == 0.0 ? ST_CONVERGED : ST_ACTIVE);
         bs[q] = S;
     }
@@ -391,6 +395,15 @@ __global__ void bcheck_kernel(int Q, const V* __restrict__ nr2, double tol, int 
             if (S.relres <= tol) S.status = ST_CONVERGED;
             else if (S.its >= maxit) S.status = ST_FAILED;
             else {
+                // a cycle that did not halve the true residual: from now on a cycle ends
+                // when its estimate fell by what the true residual still needs
+                if (S.relres > 0.5 * S.prev_rel) {
+                    S.crtol = 0.0;
+                    S.ctgt = 0.1 * tol / S.relres;
+                } else if (S.ctgt > 0.0) {
+                    S.ctgt = 0.1 * tol / S.relres;
+                }
+                S.prev_rel = S.relres;
                 S.status = ST_ACTIVE;
                 S.cycles++;
                 atomicAdd(count, 1);
@@ -429,8 +442,8 @@ __global__ void bcycle_kernel(int Q, int ldg, const V* __restrict__ nz2, V* __re
 template <typename V>
 __global__ void barnoldi_kernel(int Q, int j, int R, const V* __restrict__ h1, const V* __restrict__ h2,
                                 const V* __restrict__ nw2, V* __restrict__ H, V* __restrict__ g, double* __restrict__ cs,
-                                V* __restrict__ sn, BState* __restrict__ bs, double inner_tol, double cycle_rtol,
-                                int maxit, int* __restrict__ count) {
+                                V* __restrict__ sn, BState* __restrict__ bs, double inner_tol, int maxit,
+                                int* __restrict__ count) {
     for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < Q; q += gridDim.x * blockDim.x) {
         BState S = bs[q];
         if (S.status != ST_ACTIVE) {
@@ -477,7 +490,8 @@ __global__ void barnoldi_kernel(int Q, int j, int R, const V* __restrict__ h1, c
         S.its++;
         S.jend = j + 1;
         S.inv = hn > 0 ? 1.0 / hn : 0.0;
-        if (S.est / S.zb <= inner_tol || S.est <= cycle_rtol * S.beta || hn == 0.0 || S.its >= maxit ||
+        const bool inner_done = S.ctgt > 0.0 ? S.est <= S.ctgt * S.beta : S.est / S.zb <= inner_tol;
+        if (inner_done || S.est <= S.crtol * S.beta || hn == 0.0 || S.its >= maxit ||
             j + 1 >= R) {
             S.status = ST_STOPPED;
             S.inv = 0.0;
@@ -592,7 +606,7 @@ ndhss_status gmres_batched_run(const FactorData& F, const int32_t* rowptr, const
     };
     const int pb = (nsys + 255) / 256;
     dots(Bi, 1, Bi, n2, nullptr);
-    binit_kernel<V><<<qb, 256, 0, st>>>(Q, nrhs, n2, bs);
+    binit_kernel<V><<<qb, 256, 0, st>>>(Q, nrhs, n2, o.cycle_rtol, bs);
     NDHSS_LAUNCH_CHECK("binit_kernel");
     int napply = 0, nspmv = 0;
     while (true) {
@@ -626,8 +640,7 @@ ndhss_status gmres_batched_run(const FactorData& F, const int32_t* rowptr, const
             baxpy_kernel<V><<<nseg, 256, 0, st>>>(d_seg, pact, nsys, Vb, nm, j + 1, h2, -1.0, t, nullptr);
             dots(t, 1, t, n2, pact);
             NDHSS_CUDA_TRY(cudaMemsetAsync(cnt, 0, sizeof(int), st));
-            barnoldi_kernel<V><<<qb, 256, 0, st>>>(Q, j, R, h1, h2, n2, H, g, cs, sn, bs, o.inner * o.tol, o.cycle_rtol,
-                                                   o.maxit, cnt);
+            barnoldi_kernel<V><<<qb, 256, 0, st>>>(Q, j, R, h1, h2, n2, H, g, cs, sn, bs, o.inner * o.tol, o.maxit, cnt);
             bscale_kernel<V><<<nseg, 256, 0, st>>>(d_seg, pact, bs, t, Vb + (int64_t)(j + 1) * nm);
             NDHSS_LAUNCH_CHECK("barnoldi_kernel");
             jend = j + 1;
