@@ -16,8 +16,11 @@ TEST INFRASTRUCTURE ONLY (see ``oracle/__init__.py``).
   estimator of Eq. 2.7 on r fresh samples decides whether to stop or to
   increase k by r and reuse all samples.  Where the paper is silent (an
   estimate that never reaches eps) the rank stops growing once a round of r
-  more samples fails to halve the estimated error: the estimate then sits at
-  the floor set by the arithmetic, not by the rank.
+  more samples fails to halve an estimated error that is already within
+  STAGNATION_FLOOR (10^3 unit roundoffs) of the block's norm: there the
+  estimate sits at the floor set by the arithmetic; above it a slowly
+  decaying spectrum keeps sampling.  At most MAX_SAMPLES samples per block:
+  no round starts that would exceed it.
 * Gaussian samples come from Philox4x32-10 (Salmon et al., SC'11) with the
   Box-Muller transform, keyed by (seed, stream), so any implementation of
   the same definition draws the same matrices.
@@ -28,6 +31,15 @@ from dataclasses import dataclass, field
 
 import numpy as np
 import scipy.linalg as sla
+
+STAGNATION_FLOOR = 1e3 * np.finfo(np.float64).eps / 2    # relative, float64 arithmetic
+MAX_SAMPLES = 256
+
+
+def _stop(err, ref, eps, prev_err, nsamp, nmax, r):
+    """The adaptive loop's stopping test (shared by both compressions)."""
+    return (err <= eps * ref or nsamp >= nmax or nsamp + r > MAX_SAMPLES
+            or (err > 0.5 * prev_err and err <= STAGNATION_FLOOR * ref))
 
 # ----------------------------------------------------------------------------
 # Philox4x32-10 and Gaussian matrices
@@ -274,10 +286,9 @@ def hss_compress(A: np.ndarray, tree: list, eps: float, k0: int = 32, r: int = 1
         St = A @ Ot
         err = np.linalg.norm(St - hss_matvec(H, Ot))
         ref = np.linalg.norm(St)
-        # stop at eps, when the samples exhaust the matrix, or when r more samples did not
-        # halve the estimated error (the estimate then sits at the arithmetic's floor)
-        if (err <= eps * ref or nsamp >= min(n, rank_cap + oversample_min) or len(tree) == 1
-                or err > 0.5 * prev_err):
+        # stop at eps, when the samples exhaust the matrix or reach MAX_SAMPLES, or when
+        # r more samples did not halve an estimate already at the arithmetic's floor
+        if len(tree) == 1 or _stop(err, ref, eps, prev_err, nsamp, min(n, rank_cap + oversample_min), r):
             return H
         prev_err = err
         Om = np.hstack([Om, Ot])
@@ -469,8 +480,7 @@ def lowrank_rows(R: np.ndarray, eps: float, k0: int = 32, r: int = 16, seed: int
         Ot = gaussian(nb, r, seed, stream * 64 + 33 + rnd)
         Yt = R @ Ot
         err = np.linalg.norm(Yt - lr.matmat(Ot))
-        if (err <= eps * np.linalg.norm(Yt) or Y.shape[1] >= min(m, nb, rank_cap + oversample_min)
-                or err > 0.5 * prev_err):
+        if _stop(err, np.linalg.norm(Yt), eps, prev_err, Y.shape[1], min(m, nb, rank_cap + oversample_min), r):
             return lr
         prev_err = err
         Om = np.hstack([Om, Ot])

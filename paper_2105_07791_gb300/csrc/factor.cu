@@ -33,6 +33,7 @@ constexpr int KBMAX = 32;
 constexpr int PANEL_THREADS = 512;
 constexpr int PREP_WARPS = 8;
 constexpr int GT = 64;          // gemm tile
+constexpr int MAX_GRID_YZ = 65535;   // largest grid y or z dimension
 constexpr int GK = 16;          // gemm k chunk
 constexpr size_t PANEL_SMEM_MAX = 220 * 1024;      // panel values + one int per candidate row
 
@@ -619,8 +620,11 @@ ndhss_status factor_run(FactorData& F, const Tree& t, const V* d_vals, const int
         if (mmax == 0) continue;
         const int agx = (int)std::min<int64_t>(mmax, 256);
         tm.begin();
-        assemble_kernel<T><<<dim3(agx, L), 256, 0, st>>>(lev, F.d_node, F.d_foff, d_fsrc, d_poff, front);
-        NDHSS_LAUNCH_CHECK("assemble_kernel");
+        for (int c0 = 0; c0 < L; c0 += MAX_GRID_YZ) {
+            assemble_kernel<T><<<dim3(agx, std::min(MAX_GRID_YZ, L - c0)), 256, 0, st>>>(lev + c0, F.d_node, F.d_foff,
+                                                                                       d_fsrc, d_poff, front);
+            NDHSS_LAUNCH_CHECK("assemble_kernel");
+        }
         tm.end(0);
         tm.begin();
         scatter_entries_kernel<T, V><<<L, 256, 0, st>>>(lev, F.d_node, F.d_foff, d_eoff, d_erow, d_ecol, d_eidx,
@@ -663,41 +667,50 @@ ndhss_status factor_run(FactorData& F, const Tree& t, const V* d_vals, const int
             if (smem > PANEL_SMEM_MAX)
                 return set_error(NDHSS_ERR_INVALID_ARG, "front with %lld interior unknowns exceeds the panel kernel's shared memory",
                                  (long long)(mimax - k0));
-            tm.begin();
             // one thread per candidate row up to 512: small fronts get small CTAs, so a level of
             // thousands of leaves runs in one wave instead of repeating its pivot chain per wave
             const int pthreads = (int)std::min<int64_t>(PANEL_THREADS, std::max<int64_t>(64, (mimax - k0 + 31) / 32 * 32));
-            switch (kb) {
+            // a level of more than 65535 fronts (the grid's y / z limit) goes in
+            // chunks; the three kernels of a chunk share its per-front scratch
+            for (int c0 = 0; c0 < L; c0 += MAX_GRID_YZ) {
+                const int Lc = std::min(MAX_GRID_YZ, L - c0);
+                const int32_t* levc = lev + c0;
+                const int64_t* woffc = woff + c0;
+                tm.begin();
+                switch (kb) {
 #define NDHSS_PANEL(KBV)                                                                                          \
     case KBV:                                                                                                   \
-        panel_factor_kernel<T, KBV><<<L, pthreads, smem, st>>>(lev, F.d_node, F.d_foff, front, F.d_ipiv, d_ainv, \
-                                                               d_swapmap, (int)k0, kb, d_status);             \
+        panel_factor_kernel<T, KBV><<<Lc, pthreads, smem, st>>>(levc, F.d_node, F.d_foff, front, F.d_ipiv, d_ainv, \
+                                                                d_swapmap, (int)k0, kb, d_status);            \
         break;
-                NDHSS_PANEL(1) NDHSS_PANEL(2) NDHSS_PANEL(4) NDHSS_PANEL(8) NDHSS_PANEL(16) NDHSS_PANEL(32)
+                    NDHSS_PANEL(1) NDHSS_PANEL(2) NDHSS_PANEL(4) NDHSS_PANEL(8) NDHSS_PANEL(16) NDHSS_PANEL(32)
 #undef NDHSS_PANEL
-                default: return set_error(NDHSS_ERR_INTERNAL, "panel width %d is not a power of two <= 32", kb);
+                    default: return set_error(NDHSS_ERR_INTERNAL, "panel width %d is not a power of two <= 32", kb);
+                }
+                NDHSS_LAUNCH_CHECK("panel_factor_kernel");
+                tm.end(2);
+                tm.begin();
+                panel_prep_kernel<T><<<dim3(pgx, Lc), PREP_WARPS * 32, 0, st>>>(levc, F.d_node, F.d_foff, front,
+                                                                               d_swapmap, d_ainv, d_cbuf, d_zbuf, woffc,
+                                                                               (int)k0, kb);
+                NDHSS_LAUNCH_CHECK("panel_prep_kernel");
+                tm.end(3);
+                tm.begin();
+                if (F.prec == NDHSS_FP32_TF32 && sizeof(typename Tr<T>::real) == 4) {
+                    const int rt = Tr<T>::cplx ? 64 : 128;
+                    const int kp = ((Tr<T>::cplx ? 2 * kb : kb) + 7) & ~7;
+                    tc_update_kernel<T><<<dim3((unsigned)((mmax + rt - 1) / rt), (unsigned)((mmax + TC_COLS - 1) / TC_COLS),
+                                               Lc),
+                                          128, (size_t)2 * 128 * kp * 4, st>>>(levc, F.d_node, F.d_foff, front, d_cbuf,
+                                                                             d_zbuf, woffc, (int)k0, kb, d_status);
+                    NDHSS_LAUNCH_CHECK("tc_update_kernel");
+                } else {
+                    gemm_update_kernel<T><<<dim3(gt, gt, Lc), 256, 0, st>>>(levc, F.d_node, F.d_foff, front, d_cbuf,
+                                                                          d_zbuf, woffc, (int)k0, kb);
+                    NDHSS_LAUNCH_CHECK("gemm_update_kernel");
+                }
+                tm.end(4);
             }
-            NDHSS_LAUNCH_CHECK("panel_factor_kernel");
-            tm.end(2);
-            tm.begin();
-            panel_prep_kernel<T><<<dim3(pgx, L), PREP_WARPS * 32, 0, st>>>(lev, F.d_node, F.d_foff, front, d_swapmap,
-                                                                          d_ainv, d_cbuf, d_zbuf, woff, (int)k0, kb);
-            NDHSS_LAUNCH_CHECK("panel_prep_kernel");
-            tm.end(3);
-            tm.begin();
-            if (F.prec == NDHSS_FP32_TF32 && sizeof(typename Tr<T>::real) == 4) {
-                const int rt = Tr<T>::cplx ? 64 : 128;
-                const int kp = ((Tr<T>::cplx ? 2 * kb : kb) + 7) & ~7;
-                tc_update_kernel<T><<<dim3((unsigned)((mmax + rt - 1) / rt), (unsigned)((mmax + TC_COLS - 1) / TC_COLS), L),
-                                      128, (size_t)2 * 128 * kp * 4, st>>>(lev, F.d_node, F.d_foff, front, d_cbuf, d_zbuf,
-                                                                         woff, (int)k0, kb, d_status);
-                NDHSS_LAUNCH_CHECK("tc_update_kernel");
-            } else {
-                gemm_update_kernel<T><<<dim3(gt, gt, L), 256, 0, st>>>(lev, F.d_node, F.d_foff, front, d_cbuf, d_zbuf, woff,
-                                                                     (int)k0, kb);
-                NDHSS_LAUNCH_CHECK("gemm_update_kernel");
-            }
-            tm.end(4);
             F.launches += 3;
             for (int s2 : nodes) {
                 const int64_t mi = F.m_i(s2), m2 = mi + F.m_b(s2);

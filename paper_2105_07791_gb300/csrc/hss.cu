@@ -33,6 +33,12 @@ namespace {
 
 constexpr int HT = 256;
 constexpr int OVERSAMPLE_MIN = 10;   // the rank may use at most (samples - 10) columns
+constexpr int MAX_SAMPLES = 256;     // samples per block (the row ID keeps a column in 8 registers x 32 lanes)
+
+// 10^3 unit roundoffs of the working precision, relative to a block's norm
+template <typename T> constexpr double stagnation_floor() {
+    return sizeof(typename Tr<T>::real) == 4 ? 1e3 * 5.9604644775390625e-8 : 1e3 * 1.1102230246251565e-16;
+}
 
 // ----------------------------------------------------------------- Philox
 __device__ __forceinline__ void philox_round(uint32_t& c0, uint32_t& c1, uint32_t& c2, uint32_t& c3, uint32_t k0,
@@ -1539,10 +1545,13 @@ ndhss_status compress_problems(std::vector<Problem>& probs, bool lowrank, const 
             const Problem& pb = probs[active[i]];
             const int lim = lowrank ? std::min({pb.n, pb.ncol, rank_cap + OVERSAMPLE_MIN})
                                     : std::min(pb.n, rank_cap + OVERSAMPLE_MIN);
-            // stop when eps is met, when the samples exhaust the block, or when a round did
-            // not halve the estimated error (it then sits at the arithmetic's floor)
-            const double err = hn[2 * i];
-            if (err <= eps * hn[2 * i + 1] || p >= lim || err > 0.5 * prev_err[active[i]]) done.push_back(i);
+            // stop when eps is met, when the samples exhaust the block or reach
+            // MAX_SAMPLES, or when a round did not halve an estimate that is already
+            // within 10^3 unit roundoffs of the block's norm (the arithmetic's floor;
+            // above it a slowly decaying spectrum keeps sampling)
+            const double err = hn[2 * i], ref = hn[2 * i + 1];
+            const bool stalled = err > 0.5 * prev_err[active[i]] && err <= stagnation_floor<T>() * ref;
+            if (err <= eps * ref || p >= lim || p + r > MAX_SAMPLES || stalled) done.push_back(i);
             else still.push_back(active[i]);
             prev_err[active[i]] = err;
         }

@@ -196,3 +196,21 @@ def test_gmres_batched_argument_checks(nd, batch):
         nd.ndhss_gmres_batched(f, M.rowptr, M.col, M.vals, bad, B, X)
     with pytest.raises(nd.NdhssError, match="restart"):
         nd.ndhss_gmres_batched(f, M.rowptr, M.col, M.vals, off, B, X, restart=40)
+
+
+def test_level_wider_than_the_grid_limit(nd):
+    """70000 single-front problems: one level holds more fronts than a grid's
+    y / z dimension (65535), so the factorization runs it in chunks."""
+    P = poisson_dirichlet(4)                        # 9 unknowns, one leaf
+    S = 70000
+    tree = nd.ndhss_build_tree_batched([(P.coords, P.A.indptr, P.A.indices)] * S, 64)
+    assert tree.nnodes == S and tree.depth == 0
+    A, off = nd.batch_csr([P.A] * S)
+    M = nd.DeviceCSR(A)
+    f = _factor(nd, tree, M, 0)
+    x = _rand(A.shape[0], 1, 3, cplx=False)[:, 0]
+    xd = torch.from_numpy(np.ascontiguousarray(x)).cuda()
+    yd = torch.empty_like(xd)
+    nd.ndhss_apply(f, xd, yd)
+    want = np.linalg.solve(P.A.toarray()[None], x.reshape(S, 9, 1))[..., 0].ravel()
+    assert _rel(yd.cpu().numpy(), want) <= 1e-12
