@@ -42,6 +42,12 @@ WORKLOAD = dict(N=256, p=2, k=40.0, seed=0, leaf=64, tol=1e-8, hss_levels=4, eps
 # per wavelength, impedance), 32 Gaussian sources each, complex64 dense fronts
 BATCH = dict(count=64, seed=0, nmin=64, nmax=256, nrhs=32, leaf=64, tol=1e-8)
 
+# elastic side line: P1 SIPG time-harmonic elastic waves (2 displacement
+# components, 6 unknowns per triangle), Lame parameters from 16 seeded
+# Fourier modes in [1, 4], rho = 1, 8 points per shear wavelength, absorbing
+# boundary; tolerance 1e-6; leaf 60, beta 60
+ELASTIC = dict(N=512, seed=0, leaf=60, beta=60, tol=1e-6, hss_levels=4)
+
 # ncu DRAM traffic of the dominant kernel class, per launch, keyed by the
 # sha256 of the source file it was measured on (null once the source changes)
 NCU_TRAFFIC = {
@@ -62,6 +68,8 @@ def _args():
     ap.add_argument("--N", type=int, default=WORKLOAD["N"], help="cells per side (default: the benchmark workload)")
     ap.add_argument("--batch-count", type=int, default=BATCH["count"],
                     help="problems of the batched side line (0 = skip it)")
+    ap.add_argument("--elastic-N", type=int, default=ELASTIC["N"],
+                    help="cells per side of the elastic side line (0 = skip it)")
     ap.add_argument("--hss-levels", type=int, default=WORKLOAD["hss_levels"],
                     help="compress fronts on levels <= depth - this (Alg. 3.4); -1 = exact dense fronts")
     return ap.parse_args()
@@ -371,6 +379,8 @@ def run_gpu(a):
     }
     if a.batch_count > 0:
         line["batched"] = batched_line(a, ndhss, torch, stream)
+    if a.elastic_N > 0:
+        line["elastic"] = elastic_line(a, ndhss, torch, stream)
     if not a.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = cpu_baseline(P)
     print(json.dumps(line), flush=True)
@@ -453,6 +463,47 @@ def batched_line(a, ndhss, torch, stream):
             "factor_bytes": fs["factor_bytes"], "apply_multi_ms": ap_ms,
             "apply_multi_tflops": flops / (ap_ms / 1e3) / 1e12, "apply_multi_flops": flops,
             "host_setup_s": setup_s}
+
+
+def elastic_line(a, ndhss, torch, stream):
+    """The elastic workload: per variant (FP32 arithmetic on complex64 fronts,
+    dense and compressed) one warm-up factorization, then one timed
+    factorization and one GMRES solve to a true relative residual of 1e-6."""
+    import numpy as np
+
+    from ndhss_inputs.elastic import elastic_sipg
+
+    t0 = time.time()
+    P = elastic_sipg(a.elastic_N, seed=ELASTIC["seed"])
+    tree = ndhss.ndhss_build_tree(P.coords, P.A.indptr, P.A.indices, ELASTIC["leaf"])
+    setup_s = time.time() - t0
+    M = ndhss.DeviceCSR(P.A)
+    b = torch.from_numpy(np.ascontiguousarray(P.b)).cuda()
+    out = {"workload": f"elastic_sipg_p1_{a.elastic_N}x{a.elastic_N} (n={P.n}, nnz={P.A.nnz}, "
+                       f"omega={P.meta['omega']:.1f}, leaf {ELASTIC['leaf']}, beta {ELASTIC['beta']})",
+           "tol": ELASTIC["tol"], "host_setup_s": setup_s}
+    for name, hl in (("dense", -1), ("compressed", ELASTIC["hss_levels"])):
+        opts = ndhss.make_factor_opts(prec=ndhss.NDHSS_FP32, hss_levels=hl, eps_hss=1e-6, beta=ELASTIC["beta"])
+        f = ndhss.ndhss_factor(tree, M.vtype, M.rowptr, M.col, M.vals, opts, stream=stream)
+        del f
+        torch.cuda.synchronize()
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        x = torch.zeros_like(b)
+        e0.record(stream)
+        f = ndhss.ndhss_factor(tree, M.vtype, M.rowptr, M.col, M.vals, opts, stream=stream)
+        e1.record(stream)
+        st = ndhss.ndhss_gmres(f, M.rowptr, M.col, M.vals, b, x, tol=ELASTIC["tol"], timing=True, stream=stream)
+        e2.record(stream)
+        torch.cuda.synchronize()
+        fs = ndhss.ndhss_factor_stats_get(f)
+        del f
+        out[name] = {"factor_ms": e0.elapsed_time(e1), "solve_ms": e1.elapsed_time(e2),
+                     "solves_per_s": 1e3 / e1.elapsed_time(e2), "iters": st["iters"], "converged": st["converged"],
+                     "true_relres": st["true_relres"], "apply_ms": st["apply_ms"] / max(st["napply"], 1),
+                     "apply_bytes": fs["apply_bytes"], "factor_bytes": fs["factor_bytes"], "kmax": fs["kmax"],
+                     "apply_gbs": fs["apply_bytes"] / (st["apply_ms"] / max(st["napply"], 1) / 1e3) / 1e9
+                     if st["apply_ms"] > 0 else None}
+    return out
 
 
 # ------------------------------------------------------------- CPU oracle
