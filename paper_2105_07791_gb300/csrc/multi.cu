@@ -48,6 +48,21 @@ template <> __device__ __forceinline__ double breal<double>(double v) { return v
 template <> __device__ __forceinline__ c128 breal<c128>(double v) { return {v, 0.0}; }
 
 // ------------------------------------------------------------ multi apply
+// N consecutive elements from 16-byte aligned shared memory in 16-byte loads
+template <int N, typename T>
+__device__ __forceinline__ void lds_vec(const T* p, T (&v)[N]) {
+    static_assert((N * sizeof(T)) % 16 == 0 || N * sizeof(T) < 16, "whole 16-byte words");
+    if constexpr ((N * sizeof(T)) % 16 == 0) {
+        constexpr int W = (int)(N * sizeof(T) / 16);
+        float4 w[W];
+#pragma unroll
+        for (int i = 0; i < W; ++i) w[i] = reinterpret_cast<const float4*>(p)[i];
+        memcpy(v, w, sizeof(v));
+    } else {
+#pragma unroll
+        for (int i = 0; i < N; ++i) v[i] = p[i];
+    }
+}
 template <typename T, typename V>
 __global__ void mgather_kernel(int64_t n, int nrhs, const int32_t* __restrict__ perm, const V* __restrict__ X,
                                int64_t ldx, T* __restrict__ U) {
@@ -76,8 +91,8 @@ __global__ void __launch_bounds__(256)
 mapply_kernel(const int2* __restrict__ jobs, const int32_t* __restrict__ node, const int64_t* __restrict__ foff,
               const T* __restrict__ front, const int32_t* __restrict__ sigma, const int32_t* __restrict__ blist,
               T* __restrict__ U, T* __restrict__ Z, const int* __restrict__ pact, const int32_t* __restrict__ nprob) {
-    __shared__ T As[MT_K][MT_ROWS];
-    __shared__ T Bs[MT_K][MR];
+    __shared__ __align__(16) T As[MT_K][MT_ROWS];
+    __shared__ __align__(16) T Bs[MT_K][MR];
     __shared__ int s_row[MT_K];
     const int2 J = jobs[blockIdx.x];
     const int s = J.x, r0 = J.y;
@@ -112,12 +127,15 @@ mapply_kernel(const int2* __restrict__ jobs, const int32_t* __restrict__ node, c
         __syncthreads();
 #pragma unroll
         for (int kk = 0; kk < MT_K; ++kk) {
-            const T a0 = As[kk][2 * ty], a1 = As[kk][2 * ty + 1];
+            // the thread's two rows of A and four columns of B as 16-byte shared
+            // loads (8-byte loads of B columns 32 bytes apart conflict two-way)
+            T a[2], bv[4];
+            lds_vec<2>(&As[kk][2 * ty], a);
+            lds_vec<4>(&Bs[kk][4 * tx], bv);
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
-                const T b = Bs[kk][4 * tx + j];
-                acc[0][j] = fmac(a0, b, acc[0][j]);
-                acc[1][j] = fmac(a1, b, acc[1][j]);
+                acc[0][j] = fmac(a[0], bv[j], acc[0][j]);
+                acc[1][j] = fmac(a[1], bv[j], acc[1][j]);
             }
         }
         __syncthreads();
