@@ -249,6 +249,7 @@ def run_gpu(a):
     modes = [("mixed", ndhss.NDHSS_FP32, False), ("fp64", ndhss.NDHSS_FP64, False)]
     if not a.only:
         modes.append(("tf32", ndhss.NDHSS_FP32_TF32, False))
+        modes.append(("bf16", ndhss.NDHSS_FP32_BF16, False))
     if a.hss_levels >= 0 and not a.only:
         modes.append(("mixed_ulv", ndhss.NDHSS_FP32, True))
     if a.only:
@@ -367,6 +368,7 @@ def run_gpu(a):
                             "factor_speedup": fp["factor_ms"] / mx["factor_ms"]},
         "ulv": _ulv_summary(results.get("mixed_ulv"), a.steps),
         "tf32": _ulv_summary(results.get("tf32"), a.steps),
+        "bf16": _ulv_summary(results.get("bf16"), a.steps),
         "apply_gbs": fs["apply_bytes"] / (ap_ms / max(ap_n, 1) / 1e3) / 1e9,
         "e2e": {"value": whole_job_rate(world, a.steps, e2e_s), "unit": "solves/s", "h2d_bytes_per_step": int(P.b.nbytes),
                 "d2h_bytes_per_step": int(xn.nbytes), "true_relres": relres_e2e},
@@ -466,9 +468,10 @@ def batched_line(a, ndhss, torch, stream):
 
 
 def elastic_line(a, ndhss, torch, stream):
-    """The elastic workload: per variant (FP32 arithmetic on complex64 fronts,
-    dense and compressed) one warm-up factorization, then one timed
-    factorization and one GMRES solve to a true relative residual of 1e-6."""
+    """The elastic workload: per variant (complex64 fronts: FP32 arithmetic
+    dense and compressed, and the front update with BF16 tensor-core operands)
+    one warm-up factorization, then one timed factorization and one GMRES
+    solve to a true relative residual of 1e-6."""
     import numpy as np
 
     from ndhss_inputs.elastic import elastic_sipg
@@ -482,8 +485,9 @@ def elastic_line(a, ndhss, torch, stream):
     out = {"workload": f"elastic_sipg_p1_{a.elastic_N}x{a.elastic_N} (n={P.n}, nnz={P.A.nnz}, "
                        f"omega={P.meta['omega']:.1f}, leaf {ELASTIC['leaf']}, beta {ELASTIC['beta']})",
            "tol": ELASTIC["tol"], "host_setup_s": setup_s}
-    for name, hl in (("dense", -1), ("compressed", ELASTIC["hss_levels"])):
-        opts = ndhss.make_factor_opts(prec=ndhss.NDHSS_FP32, hss_levels=hl, eps_hss=1e-6, beta=ELASTIC["beta"])
+    for name, hl, prec in (("dense", -1, ndhss.NDHSS_FP32), ("compressed", ELASTIC["hss_levels"], ndhss.NDHSS_FP32),
+                           ("dense_bf16", -1, ndhss.NDHSS_FP32_BF16)):
+        opts = ndhss.make_factor_opts(prec=prec, hss_levels=hl, eps_hss=1e-6, beta=ELASTIC["beta"])
         f = ndhss.ndhss_factor(tree, M.vtype, M.rowptr, M.col, M.vals, opts, stream=stream)
         del f
         torch.cuda.synchronize()

@@ -54,7 +54,9 @@ typedef enum { NDHSS_R64 = 0, NDHSS_C128 = 1 } ndhss_vtype;
 typedef enum {
     NDHSS_FP64 = 0,      /* fronts in float64 / complex128, FP64 arithmetic           */
     NDHSS_FP32 = 1,      /* fronts in float32 / complex64, FP32 arithmetic            */
-    NDHSS_FP32_TF32 = 2  /* as FP32, front updates on TF32 tensor cores, FP32 accum.  */
+    NDHSS_FP32_TF32 = 2, /* as FP32, front updates on TF32 tensor cores, FP32 accum.  */
+    NDHSS_FP32_BF16 = 3  /* as FP32, front updates with BF16 operands on the tensor
+                            cores (tcgen05 kind::f16), FP32 accumulation             */
 } ndhss_prec;
 
 typedef struct ndhss_tree ndhss_tree;

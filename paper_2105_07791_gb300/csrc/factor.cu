@@ -24,6 +24,8 @@
 #include <cmath>
 
 #include "factor.cuh"
+#include <cuda_bf16.h>
+
 #include "tcgen05.cuh"
 
 namespace ndhss {
@@ -381,19 +383,22 @@ gemm_update_kernel(const int32_t* __restrict__ lev, const int32_t* __restrict__ 
 // staged K-major in shared memory, kb / 8 kind::tf32 MMAs accumulate in
 // TMEM (FP32), and each thread reads its TMEM lane back for the epilogue
 // M = beta .* M + C Z.  The completion wait is bounded (status TIMEOUT).
+// BF = true (precision NDHSS_FP32_BF16): the operands rounded to BF16,
+// K padded to a multiple of 16, kind::f16 MMAs with BF16 A and B.
 constexpr int TC_COLS = 128;
 constexpr int TC_MAX_WAIT = 1 << 24;
 
-template <typename T>
+template <typename T, bool BF>
 __global__ void __launch_bounds__(128)
 tc_update_kernel(const int32_t* __restrict__ lev, const int32_t* __restrict__ node, const int64_t* __restrict__ foff,
                  T* __restrict__ front, const T* __restrict__ cbuf, const T* __restrict__ zbuf,
                  const int64_t* __restrict__ woff, int k0, int kb, DevStatus* status) {
     if constexpr (sizeof(typename Tr<T>::real) != 4) {
-        return;                                         // TF32 applies to the FP32 types only
+        return;                                         // TF32 / BF16 apply to the FP32 types only
     } else {
     constexpr bool CPLX = Tr<T>::cplx;
     constexpr int RT = CPLX ? 64 : 128;                 // front rows per tile
+    constexpr int ESZ = BF ? 2 : 4, KAL = BF ? 16 : 8, KMMA = BF ? 16 : 8;
     extern __shared__ __align__(1024) unsigned char tsm[];
     __shared__ __align__(8) uint64_t mbar;
     __shared__ uint32_t tmem_holder;
@@ -405,13 +410,19 @@ tc_update_kernel(const int32_t* __restrict__ lev, const int32_t* __restrict__ no
     const int64_t i0 = (int64_t)blockIdx.x * RT, j0 = (int64_t)blockIdx.y * TC_COLS;
     if (i0 >= m || j0 >= m) return;
     const int kbp = min(kb, m_i - k0);
-    const int KP = ((CPLX ? 2 * kbp : kbp) + 7) & ~7;
+    const int KP = ((CPLX ? 2 * kbp : kbp) + KAL - 1) & ~(KAL - 1);
     const T* C = cbuf + woff[li] * KBMAX;
     const T* Z = zbuf + woff[li] * KBMAX;
     T* F = front + foff[s];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     unsigned char* sA = tsm;
-    unsigned char* sB = tsm + 128 * KP * 4;
+    unsigned char* sB = tsm + 128 * KP * ESZ;
+    // operands rounded to nearest (the tensor core would otherwise drop the
+    // low mantissa bits of an FP32 operand: a biased truncation to TF32)
+    auto put = [&](unsigned char* base, int r, int kk, float v) {
+        if constexpr (BF) *reinterpret_cast<__nv_bfloat16*>(base + tc::core_off16(r, kk, KP)) = __float2bfloat16_rn(v);
+        else *reinterpret_cast<uint32_t*>(base + tc::core_off(r, kk, KP)) = tc::to_tf32_rn(v);
+    };
     if (tid == 0) tc::mbar_init(&mbar, 1);
     if (warp == 0) tc::tmem_alloc(&tmem_holder, TC_COLS);
     for (int q = tid; q < 128 * KP; q += 128) {
@@ -427,7 +438,7 @@ tc_update_kernel(const int32_t* __restrict__ lev, const int32_t* __restrict__ no
             const int64_t r = i0 + rr;
             if (r < m && kk < kbp) v = C[(int64_t)kk * m + r];
         }
-        *reinterpret_cast<float*>(sA + tc::core_off(rr, kk, KP)) = v;
+        put(sA, rr, kk, v);
     }
     for (int q = tid; q < 128 * KP; q += 128) {
         const int kk = q % KP, nn = q / KP;
@@ -441,7 +452,7 @@ tc_update_kernel(const int32_t* __restrict__ lev, const int32_t* __restrict__ no
         } else {
             if (n < m && kk < kbp) v = Z[n * KBMAX + kk];
         }
-        *reinterpret_cast<float*>(sB + tc::core_off(nn, kk, KP)) = v;
+        put(sB, nn, kk, v);
     }
     tc::fence_smem_async();
     tc::fence_before();
@@ -449,11 +460,14 @@ tc_update_kernel(const int32_t* __restrict__ lev, const int32_t* __restrict__ no
     tc::fence_after();
     const uint32_t tmem = tmem_holder;
     if (tid == 0) {
-        const uint32_t idesc = tc::idesc_tf32(128, TC_COLS);
-        const uint32_t sbo = (uint32_t)(KP / 4) * 128u;
-        for (int ks = 0; ks < KP / 8; ++ks)
-            tc::mma_tf32(tmem, tc::smem_desc(tc::smem_u32(sA) + ks * 256u, 128u, sbo),
-                         tc::smem_desc(tc::smem_u32(sB) + ks * 256u, 128u, sbo), idesc, ks > 0 ? 1u : 0u);
+        // 16 bytes of K per core matrix: 4 TF32 or 8 BF16 elements; one MMA takes two
+        const uint32_t sbo = (uint32_t)(KP * ESZ / 16) * 128u;
+        for (int ks = 0; ks < KP / KMMA; ++ks) {
+            const uint64_t ad = tc::smem_desc(tc::smem_u32(sA) + ks * 256u, 128u, sbo);
+            const uint64_t bd = tc::smem_desc(tc::smem_u32(sB) + ks * 256u, 128u, sbo);
+            if constexpr (BF) tc::mma_f16(tmem, ad, bd, tc::idesc_bf16(128, TC_COLS), ks > 0 ? 1u : 0u);
+            else tc::mma_tf32(tmem, ad, bd, tc::idesc_tf32(128, TC_COLS), ks > 0 ? 1u : 0u);
+        }
         tc::commit(&mbar);
     }
     if (!tc::mbar_wait(&mbar, 0, TC_MAX_WAIT)) {
@@ -524,7 +538,9 @@ ndhss_status set_smem_attrs() {
                                      panel_factor_kernel<T, 8>, panel_factor_kernel<T, 16>, panel_factor_kernel<T, 32>};
     for (auto k : kernels)
         NDHSS_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PANEL_SMEM_MAX));
-    NDHSS_CUDA_TRY(cudaFuncSetAttribute(tc_update_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    NDHSS_CUDA_TRY(cudaFuncSetAttribute(tc_update_kernel<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        2 * 128 * 2 * KBMAX * 4));
+    NDHSS_CUDA_TRY(cudaFuncSetAttribute(tc_update_kernel<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                         2 * 128 * 2 * KBMAX * 4));
     return NDHSS_OK;
 }
@@ -696,13 +712,17 @@ ndhss_status factor_run(FactorData& F, const Tree& t, const V* d_vals, const int
                 NDHSS_LAUNCH_CHECK("panel_prep_kernel");
                 tm.end(3);
                 tm.begin();
-                if (F.prec == NDHSS_FP32_TF32 && sizeof(typename Tr<T>::real) == 4) {
+                if ((F.prec == NDHSS_FP32_TF32 || F.prec == NDHSS_FP32_BF16) && sizeof(typename Tr<T>::real) == 4) {
                     const int rt = Tr<T>::cplx ? 64 : 128;
-                    const int kp = ((Tr<T>::cplx ? 2 * kb : kb) + 7) & ~7;
-                    tc_update_kernel<T><<<dim3((unsigned)((mmax + rt - 1) / rt), (unsigned)((mmax + TC_COLS - 1) / TC_COLS),
-                                               Lc),
-                                          128, (size_t)2 * 128 * kp * 4, st>>>(levc, F.d_node, F.d_foff, front, d_cbuf,
-                                                                             d_zbuf, woffc, (int)k0, kb, d_status);
+                    // staged operands sized as for TF32 (BF16 uses half of it)
+                    const int kp = ((Tr<T>::cplx ? 2 * kb : kb) + 15) & ~15;
+                    const dim3 grid((unsigned)((mmax + rt - 1) / rt), (unsigned)((mmax + TC_COLS - 1) / TC_COLS), Lc);
+                    if (F.prec == NDHSS_FP32_BF16)
+                        tc_update_kernel<T, true><<<grid, 128, (size_t)2 * 128 * kp * 4, st>>>(
+                            levc, F.d_node, F.d_foff, front, d_cbuf, d_zbuf, woffc, (int)k0, kb, d_status);
+                    else
+                        tc_update_kernel<T, false><<<grid, 128, (size_t)2 * 128 * kp * 4, st>>>(
+                            levc, F.d_node, F.d_foff, front, d_cbuf, d_zbuf, woffc, (int)k0, kb, d_status);
                     NDHSS_LAUNCH_CHECK("tc_update_kernel");
                 } else {
                     gemm_update_kernel<T><<<dim3(gt, gt, Lc), 256, 0, st>>>(levc, F.d_node, F.d_foff, front, d_cbuf,
@@ -763,7 +783,7 @@ static ndhss_status factor_impl(const ndhss_tree* th, int32_t vtype, const int32
     o.prec = NDHSS_FP64;
     o.hss_levels = -1;
     if (opts) o = *opts;
-    if (o.prec != NDHSS_FP64 && o.prec != NDHSS_FP32 && o.prec != NDHSS_FP32_TF32)
+    if (o.prec != NDHSS_FP64 && o.prec != NDHSS_FP32 && o.prec != NDHSS_FP32_TF32 && o.prec != NDHSS_FP32_BF16)
         return set_error(NDHSS_ERR_INVALID_ARG, "ndhss_factor: bad precision %d", o.prec);
     if (o.hss_levels >= 0 && (!(o.eps_hss > 0) || o.beta < 1 || o.k0 < 1 || o.r < 1 || o.rank_cap < 1))
         return set_error(NDHSS_ERR_INVALID_ARG, "ndhss_factor: compression needs eps_hss > 0 and beta, k0, r, rank_cap >= 1");

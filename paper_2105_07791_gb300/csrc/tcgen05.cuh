@@ -38,6 +38,34 @@ __host__ __device__ constexpr uint32_t idesc_tf32(int m, int n) {
     return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
 }
 
+// FP32 -> TF32 bit pattern, rounded to nearest (ties away from zero)
+__device__ __forceinline__ uint32_t to_tf32_rn(float v) {
+    uint32_t u;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(u) : "f"(v));
+    return u;
+}
+
+// instruction descriptor, kind::f16 with BF16 A and B (both operands of one
+// MMA share the type), FP32 accumulator, both K-major
+__host__ __device__ constexpr uint32_t idesc_bf16(int m, int n) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
+}
+
+// byte offset of element (r, k) in a K-major tile of K 16-bit columns: core
+// matrices of 8 rows x 8 elements (16 bytes), LBO 128 (along K), SBO (K / 8) * 128
+__device__ __forceinline__ uint32_t core_off16(int r, int k, int K) {
+    return ((uint32_t)(r >> 3) * (uint32_t)(K >> 3) + (uint32_t)(k >> 3)) * 128u + (uint32_t)(r & 7) * 16u +
+           (uint32_t)(k & 7) * 2u;
+}
+
+// one kind::f16 MMA (K = 16 for 16-bit operands: the start addresses advance 256 bytes per step)
+__device__ __forceinline__ void mma_f16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc));
+}
+
 __device__ __forceinline__ void mma_tf32(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc, uint32_t acc) {
     asm volatile(
         "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"

@@ -16,7 +16,7 @@ import numpy as np
 from . import build as _build
 
 NDHSS_R64, NDHSS_C128 = 0, 1
-NDHSS_FP64, NDHSS_FP32, NDHSS_FP32_TF32 = 0, 1, 2
+NDHSS_FP64, NDHSS_FP32, NDHSS_FP32_TF32, NDHSS_FP32_BF16 = 0, 1, 2, 3
 NODE_FIELDS = ("level", "parent", "child0", "child1", "i_off", "m_i", "b_off", "m_b",
                "x0", "x1", "y0", "y1", "axis", "cut")
 STATUS = {0: "OK", 1: "INVALID_ARG", 2: "OOM", 3: "SINGULAR", 4: "RANK_CAP", 5: "NOT_CONVERGED",
