@@ -63,7 +63,7 @@ def _args():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ndhss", choices=["ndhss", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--only", choices=["mixed", "fp64"], help="time one precision only (profiling runs)")
+    ap.add_argument("--only", choices=["mixed", "fp64", "tf32", "bf16"], help="time one precision only (profiling runs)")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer measurement (profiling runs)")
     ap.add_argument("--N", type=int, default=WORKLOAD["N"], help="cells per side (default: the benchmark workload)")
     ap.add_argument("--batch-count", type=int, default=BATCH["count"],
@@ -247,7 +247,7 @@ def run_gpu(a):
 
     results = {}
     modes = [("mixed", ndhss.NDHSS_FP32, False), ("fp64", ndhss.NDHSS_FP64, False)]
-    if not a.only:
+    if not a.only or a.only in ("tf32", "bf16"):
         modes.append(("tf32", ndhss.NDHSS_FP32_TF32, False))
         modes.append(("bf16", ndhss.NDHSS_FP32_BF16, False))
     if a.hss_levels >= 0 and not a.only:

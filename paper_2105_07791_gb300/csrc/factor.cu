@@ -425,34 +425,59 @@ tc_update_kernel(const int32_t* __restrict__ lev, const int32_t* __restrict__ no
     };
     if (tid == 0) tc::mbar_init(&mbar, 1);
     if (warp == 0) tc::tmem_alloc(&tmem_holder, TC_COLS);
-    for (int q = tid; q < 128 * KP; q += 128) {
-        const int rr = q & 127, kk = q >> 7;
-        float v = 0.0f;
-        if constexpr (CPLX) {
-            const int64_t r = i0 + (rr >> 1);
-            if (r < m && kk < 2 * kbp) {
-                const T c = C[(int64_t)(kk < kbp ? kk : kk - kbp) * m + r];
-                v = (rr & 1) ? (kk < kbp ? c.y : c.x) : (kk < kbp ? c.x : -c.y);
+    // staging: eight independent loads per thread in flight before the stores
+    // (one load at a time leaves the kernel waiting on global latency)
+    constexpr int SU = 8;
+    for (int q0 = tid; q0 < 128 * KP; q0 += 128 * SU) {
+        float v[SU];
+#pragma unroll
+        for (int u = 0; u < SU; ++u) {
+            const int q = q0 + u * 128;
+            const int rr = q & 127, kk = q >> 7;
+            v[u] = 0.0f;
+            if (q < 128 * KP) {
+                if constexpr (CPLX) {
+                    const int64_t r = i0 + (rr >> 1);
+                    if (r < m && kk < 2 * kbp) {
+                        const T c = C[(int64_t)(kk < kbp ? kk : kk - kbp) * m + r];
+                        v[u] = (rr & 1) ? (kk < kbp ? c.y : c.x) : (kk < kbp ? c.x : -c.y);
+                    }
+                } else {
+                    const int64_t r = i0 + rr;
+                    if (r < m && kk < kbp) v[u] = C[(int64_t)kk * m + r];
+                }
             }
-        } else {
-            const int64_t r = i0 + rr;
-            if (r < m && kk < kbp) v = C[(int64_t)kk * m + r];
         }
-        put(sA, rr, kk, v);
+#pragma unroll
+        for (int u = 0; u < SU; ++u) {
+            const int q = q0 + u * 128;
+            if (q < 128 * KP) put(sA, q & 127, q >> 7, v[u]);
+        }
     }
-    for (int q = tid; q < 128 * KP; q += 128) {
-        const int kk = q % KP, nn = q / KP;
-        const int64_t n = j0 + nn;
-        float v = 0.0f;
-        if constexpr (CPLX) {
-            if (n < m && kk < 2 * kbp) {
-                const T z = Z[n * KBMAX + (kk < kbp ? kk : kk - kbp)];
-                v = kk < kbp ? z.x : z.y;
+    for (int q0 = tid; q0 < 128 * KP; q0 += 128 * SU) {
+        float v[SU];
+#pragma unroll
+        for (int u = 0; u < SU; ++u) {
+            const int q = q0 + u * 128;
+            const int kk = q % KP, nn = q / KP;
+            const int64_t n = j0 + nn;
+            v[u] = 0.0f;
+            if (q < 128 * KP) {
+                if constexpr (CPLX) {
+                    if (n < m && kk < 2 * kbp) {
+                        const T z = Z[n * KBMAX + (kk < kbp ? kk : kk - kbp)];
+                        v[u] = kk < kbp ? z.x : z.y;
+                    }
+                } else {
+                    if (n < m && kk < kbp) v[u] = Z[n * KBMAX + kk];
+                }
             }
-        } else {
-            if (n < m && kk < kbp) v = Z[n * KBMAX + kk];
         }
-        put(sB, nn, kk, v);
+#pragma unroll
+        for (int u = 0; u < SU; ++u) {
+            const int q = q0 + u * 128;
+            if (q < 128 * KP) put(sB, q / KP, q % KP, v[u]);
+        }
     }
     tc::fence_smem_async();
     tc::fence_before();
@@ -477,23 +502,32 @@ tc_update_kernel(const int32_t* __restrict__ lev, const int32_t* __restrict__ no
         const int row = warp * 32 + lane;                  // TMEM lane = row of the real GEMM
         const int64_t r = CPLX ? i0 + (row >> 1) : i0 + row;
         const bool pi = r >= k0 && r < k0 + kbp;
+        // per group of 8 columns: the lane's destination values are loaded
+        // first (independent loads in flight), then its TMEM columns, then
+        // combined and stored (a load after each store would serialise them)
+        constexpr int NW = CPLX ? 4 : 8;                   // columns a lane writes per group
         for (int c0 = 0; c0 < TC_COLS; c0 += 8) {
+            T old[NW];
+#pragma unroll
+            for (int h = 0; h < NW; ++h) {
+                const int u = CPLX ? 2 * h + (lane & 1) : h;          // complex: even lanes even columns
+                const int64_t n = j0 + c0 + u;
+                const bool pj = n >= k0 && n < k0 + kbp;
+                old[h] = (r < m && n < m && !(pi || pj)) ? F[n * m + r] : zero<T>();
+            }
             float v[8];
             tc::tmem_ld8(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
 #pragma unroll
             for (int u = 0; u < 8; ++u) {
                 const int64_t n = j0 + c0 + u;
-                const bool pj = n >= k0 && n < k0 + kbp;
                 if constexpr (CPLX) {
                     const float other = __shfl_xor_sync(0xffffffffu, v[u], 1);
-                    if ((u & 1) != (lane & 1) || r >= m || n >= m) continue;   // even lanes even columns
+                    if ((u & 1) != (lane & 1) || r >= m || n >= m) continue;
                     const T d = (lane & 1) ? T{other, v[u]} : T{v[u], other};
-                    T* dst = F + n * m + r;
-                    *dst = (pi || pj) ? d : (*dst + d);
+                    F[n * m + r] = old[u >> 1] + d;            // old = 0 on pivot rows / columns
                 } else {
                     if (r >= m || n >= m) continue;
-                    T* dst = F + n * m + r;
-                    *dst = (pi || pj) ? v[u] : (*dst + v[u]);
+                    F[n * m + r] = old[u] + v[u];
                 }
             }
         }
