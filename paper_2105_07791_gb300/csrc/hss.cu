@@ -1559,7 +1559,7 @@ ndhss_status compress_problems(std::vector<Problem>& probs, bool lowrank, const 
         if (!done.empty()) {
             if (lowrank) {
                 // X (n x k, ld n) then R(J, :)^T (ncol x k, ld ncol) of every retired
-                // problem, gathered on the device into one buffer of this round
+                // problem, gathered on the device into one buffer per sampling round
                 std::vector<LrOut> jobs;
                 std::vector<int64_t> offs;
                 int64_t tot = 0;
