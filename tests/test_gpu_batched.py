@@ -214,3 +214,27 @@ def test_level_wider_than_the_grid_limit(nd):
     nd.ndhss_apply(f, xd, yd)
     want = np.linalg.solve(P.A.toarray()[None], x.reshape(S, 9, 1))[..., 0].ravel()
     assert _rel(yd.cpu().numpy(), want) <= 1e-12
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_gmres_batched_real_problems(nd, prec):
+    """float64 vectors: a forest of three Poisson problems of different sizes,
+    five random right-hand sides each, against sparse direct solves."""
+    probs = [poisson_dirichlet(N, seed=N) for N in (17, 30, 9)]
+    tree = nd.ndhss_build_tree_batched([(P.coords, P.A.indptr, P.A.indices) for P in probs], 32)
+    A, off = nd.batch_csr([P.A for P in probs])
+    M = nd.DeviceCSR(A)
+    assert M.vtype == 0
+    f = _factor(nd, tree, M, prec)
+    n = A.shape[0]
+    Bh = np.ascontiguousarray(_rand(n, 5, 21, cplx=False).T)
+    B = torch.from_numpy(Bh).cuda()
+    X = torch.zeros_like(B)
+    st = nd.ndhss_gmres_batched(f, M.rowptr, M.col, M.vals, off, B, X, tol=1e-10)
+    Xh = X.cpu().numpy()
+    for s, P in enumerate(probs):
+        lu = spla.splu(P.A.tocsc())
+        for c in range(5):
+            assert st[s][c]["converged"] and st[s][c]["true_relres"] <= 1e-10
+            a, b = off[s], off[s + 1]
+            assert _rel(Xh[c, a:b], lu.solve(Bh[c, a:b])) <= 1e-8
