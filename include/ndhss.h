@@ -92,8 +92,9 @@ typedef struct {
                                    0.1 = one decade below tol, as Sec. 4 stops at 1e-9 */
     double cycle_rtol;          /* a cycle also ends once its residual estimate fell by
                                    this factor (what one reduced-precision apply can
-                                   resolve); < 0 = automatic: 1e-4 for FP32 fronts,
-                                   0 (off) for FP64 fronts.  After a cycle that did
+                                   resolve); < 0 = automatic: 1e-3 for FP32 fronts
+                                   (a cycle then takes about one Arnoldi step and the
+                                   float64 restarts refine), 0 (off) for FP64 fronts.  After a cycle that did
                                    not halve the true residual, later cycles of that
                                    solve end only once their estimate fell by the
                                    reduction the true residual still needs

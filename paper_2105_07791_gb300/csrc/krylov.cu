@@ -521,7 +521,7 @@ ndhss_status ndhss_gmres(const ndhss_factorization* fh, const int32_t* d_rowptr,
         return set_error(NDHSS_ERR_INVALID_ARG,
                          "ndhss_gmres: need 1 <= restart <= %d, maxit >= 0, tol >= 0, 0 < inner <= 1", KMAX - 1);
     if (nrhs == 0) return NDHSS_OK;
-    if (o.cycle_rtol < 0) o.cycle_rtol = (F.prec == NDHSS_FP64) ? 0.0 : 1e-4;
+    if (o.cycle_rtol < 0) o.cycle_rtol = (F.prec == NDHSS_FP64) ? 0.0 : 1e-3;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const size_t vsz = F.vtype == NDHSS_C128 ? 16 : 8;
     const bool bdev = is_device_ptr(b), xdev = is_device_ptr(x);

@@ -781,7 +781,7 @@ ndhss_status ndhss_gmres_batched(const ndhss_factorization* fh, const int32_t* d
     if (nrhs == 0) return NDHSS_OK;
     ndhss_status rc = multi_supported(F, "ndhss_gmres_batched");
     if (rc != NDHSS_OK) return rc;
-    if (o.cycle_rtol < 0) o.cycle_rtol = (F.prec == NDHSS_FP64) ? 0.0 : 1e-4;
+    if (o.cycle_rtol < 0) o.cycle_rtol = (F.prec == NDHSS_FP64) ? 0.0 : 1e-3;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     if (F.vtype == NDHSS_R64)
         rc = gmres_batched_run<double>(F, d_rowptr, d_col, (const double*)d_vals, nsys, sys_off, nrhs, (const double*)d_b,
