@@ -592,11 +592,12 @@ ndhss_status gmres_batched_run(const FactorData& F, const int32_t* rowptr, const
     int* pact = (int*)(W + o_pact);
     int32_t* nprob = (int32_t*)(W + o_nprob);
     void* mw = W + o_mw;
+    int napply = 0, nspmv = 0;
+    std::vector<BState> hb(Q);
+    // everything that uses the workspace; any early return comes back here and
+    // the workspace goes back to the pool below
+    auto body = [&]() -> ndhss_status {
     ndhss_status rc = NDHSS_OK;
-    auto fail = [&](ndhss_status r) {
-        cudaFreeAsync(work, st);
-        return r;
-    };
     if (nseg > 0) NDHSS_CUDA_TRY(cudaMemcpyAsync(d_seg, segs.data(), sizeof(Seg) * nseg, cudaMemcpyHostToDevice, st));
     NDHSS_CUDA_TRY(cudaMemcpyAsync(d_soff, seg_off.data(), sizeof(int32_t) * (nsys + 1), cudaMemcpyHostToDevice, st));
     // each node's problem: the one whose rows hold the node's I block
@@ -626,7 +627,6 @@ ndhss_status gmres_batched_run(const FactorData& F, const int32_t* rowptr, const
     dots(Bi, 1, Bi, n2, nullptr);
     binit_kernel<V><<<qb, 256, 0, st>>>(Q, nrhs, n2, o.cycle_rtol, bs);
     NDHSS_LAUNCH_CHECK("binit_kernel");
-    int napply = 0, nspmv = 0;
     while (true) {
         spmm_kernel<V><<<nseg, 256, 0, st>>>(d_seg, nullptr, rowptr, col, vals, Xi, t);
         ++nspmv;
@@ -636,10 +636,10 @@ ndhss_status gmres_batched_run(const FactorData& F, const int32_t* rowptr, const
         bcheck_kernel<V><<<qb, 256, 0, st>>>(Q, n2, o.tol, o.maxit, bs, cnt);
         NDHSS_LAUNCH_CHECK("bcheck_kernel");
         int active = 0;
-        if ((rc = read_count(&active))) return fail(rc);
+        if ((rc = read_count(&active))) return rc;
         if (active == 0) break;
         bpact_kernel<<<pb, 256, 0, st>>>(nsys, bs, pact);
-        if ((rc = multi_apply_device(F, MR, w, MR, t, MR, mw, st, pact, nprob))) return fail(rc);
+        if ((rc = multi_apply_device(F, MR, w, MR, t, MR, mw, st, pact, nprob))) return rc;
         ++napply;
         dots(t, 1, t, n2, pact);
         bcycle_kernel<V><<<qb, 256, 0, st>>>(Q, R + 1, n2, g, bs);
@@ -650,7 +650,7 @@ ndhss_status gmres_batched_run(const FactorData& F, const int32_t* rowptr, const
             bpact_kernel<<<pb, 256, 0, st>>>(nsys, bs, pact);
             spmm_kernel<V><<<nseg, 256, 0, st>>>(d_seg, pact, rowptr, col, vals, Vb + (int64_t)j * nm, w);
             ++nspmv;
-            if ((rc = multi_apply_device(F, MR, w, MR, t, MR, mw, st, pact, nprob))) return fail(rc);
+            if ((rc = multi_apply_device(F, MR, w, MR, t, MR, mw, st, pact, nprob))) return rc;
             ++napply;
             dots(Vb, j + 1, t, h1, pact);
             baxpy_kernel<V><<<nseg, 256, 0, st>>>(d_seg, pact, nsys, Vb, nm, j + 1, h1, -1.0, t, nullptr);
@@ -662,7 +662,7 @@ ndhss_status gmres_batched_run(const FactorData& F, const int32_t* rowptr, const
             bscale_kernel<V><<<nseg, 256, 0, st>>>(d_seg, pact, bs, t, Vb + (int64_t)(j + 1) * nm);
             NDHSS_LAUNCH_CHECK("barnoldi_kernel");
             jend = j + 1;
-            if ((rc = read_count(&active))) return fail(rc);
+            if ((rc = read_count(&active))) return rc;
             if (active == 0) break;
         }
         bhsolve_kernel<V><<<qb, 256, 0, st>>>(Q, R, H, g, bs, yv);
@@ -671,10 +671,13 @@ ndhss_status gmres_batched_run(const FactorData& F, const int32_t* rowptr, const
     }
     bdeinterleave_kernel<V><<<eb, 256, 0, st>>>(n, nrhs, Xi, x, ldx);
     NDHSS_LAUNCH_CHECK("bdeinterleave_kernel");
-    std::vector<BState> hb(Q);
     NDHSS_CUDA_TRY(cudaMemcpyAsync(hb.data(), bs, sizeof(BState) * Q, cudaMemcpyDeviceToHost, st));
-    cudaFreeAsync(work, st);
     NDHSS_CUDA_TRY(cudaStreamSynchronize(st));
+    return NDHSS_OK;
+    };
+    const ndhss_status rb = body();
+    cudaFreeAsync(work, st);
+    if (rb != NDHSS_OK) return rb;
     bool all = true;
     for (int s = 0; s < nsys; ++s)
         for (int c = 0; c < nrhs; ++c) {
