@@ -15,6 +15,13 @@ separately as ``factor_ms``, as the metric defines); ``ms_per_step`` includes
 both.  Inputs stay resident in HBM; the factor (>= 0.7 GB) exceeds the 129 MB
 L2, so every apply streams it from HBM.
 
+Side lines of the same JSON line: ``fp64`` (the comparator), ``ulv``,
+``tf32`` and ``bf16`` (other factor variants of the same workload),
+``batched`` (64 independent Helmholtz problems x 32 right-hand sides solved
+in lockstep; ``--batch-count 0`` skips it) and ``elastic`` (P1 SIPG elastic
+waves on 512 x 512 cells, dense, compressed and BF16 fronts; ``--elastic-N 0``
+skips it).
+
 ``--impl reference`` times the FP64 CPU oracle (the only other place this
 script runs ``oracle/``) on the host cores.
 """
