@@ -201,7 +201,7 @@ def test_ulv_preconditioner_matches_dense_diagonal_within_tolerance(compressed):
 def test_stopping_rule_keeps_sampling_a_slowly_decaying_spectrum():
     """A spectrum decaying by 0.93 per index: r = 4 more samples never halve the
     estimate, but it is far above the float64 floor, so sampling goes on until
-    eps is met (within the 50 eps that an eps-truncated interpolative
+    eps is met (within the 100 eps that an eps-truncated interpolative
     decomposition of a slowly decaying tail reaches; a rule that stopped at any
     non-halving round returns rank 6 and an error of 0.85 here)."""
     from oracle.hss import MAX_SAMPLES, STAGNATION_FLOOR, _stop
@@ -213,7 +213,7 @@ def test_stopping_rule_keeps_sampling_a_slowly_decaying_spectrum():
     R = (U[:, :nb] * s) @ V.T
     lr = lowrank_rows(R, 1e-6, k0=8, r=4, seed=3)
     err = np.linalg.norm(lr.matmat(np.eye(nb)) - R) / np.linalg.norm(R)
-    assert err <= 50 * 1e-6 * 2, err
+    assert err <= 100 * 1e-6, err
     assert lr.X.shape[1] > 150                      # the rank eps asks for (0.93^k ~ 1e-6 near k ~ 190)
     # the rule itself: stagnation stops only at the floor, the sample cap always
     assert not _stop(1e-3, 1.0, 1e-6, 1.5e-3, 64, 500, 16)
