@@ -345,6 +345,28 @@ def run_gpu(a):
         froof.update(bound="alu", achieved=achf, peak=peak, unit="TFLOP/s", frac=achf / peak)
     else:
         froof.update(bound="latency (many small dependent launches)")
+    # the other hot kernels against the bound that limits them: ALU peaks
+    # derived from unit counts and the maximum SM clock (FP32 SIMT: 152 SMs x
+    # 128 lanes x 2 flops; FP64: GB300's nominal 1.25 TFLOP/s), HBM measured
+    clk = pk.get("sm_max_mhz", 2070.0) * 1e6
+    fp32_peak = 152 * 128 * 2 * clk / 1e12
+    fp64_peak = 1.25
+    n_sp = sum(v[3] for v in mx["applies"]) / a.steps
+    sp_one = sp_ms / max(n_sp, 1)
+    krl = [
+        dict(roof, kernel="apply_dataflow_kernel"),
+        {"kernel": "spmv_kernel (FP64 CSR, complex128)", "bound": "alu", "unit": "TFLOP/s",
+         "achieved": 8.0 * P.A.nnz / (sp_one / 1e3) / 1e12 if sp_one > 0 else None, "peak": fp64_peak,
+         "peak_kind": "nominal FP64", "algorithmic": "8 flops per complex entry (real entries take 4)",
+         "avg_launch_ms": sp_one},
+        {"kernel": "gemm_update_kernel (FP32 SIMT front update)", "bound": "alu", "unit": "TFLOP/s",
+         "achieved": fs["update_flops"] / (cls_ms["update"] / 1e3) / 1e12 if cls_ms.get("update") else None,
+         "peak": fp32_peak, "peak_kind": "derived: 152 SMs x 128 FP32 lanes x 2 x max SM clock",
+         "algorithmic": "8 m^2 kb flops per front and panel"},
+    ]
+    for k in krl:
+        if k.get("achieved") is not None and k.get("peak"):
+            k["frac"] = k["achieved"] / k["peak"]
     line = {
         "metric": METRIC,
         "value": mx["solves_per_s"],
@@ -382,12 +404,18 @@ def run_gpu(a):
         "gpu_launches": mx["launches"],
         "roofline": roof,
         "factor_roofline": froof,
+        "kernel_rooflines": krl,
         "spmv_ms_per_solve": sp_ms,
         "factor_kernel_ms": {k: round(v, 3) for k, v in cls_ms.items()},
         "clocks": mx["clocks"],
     }
     if a.batch_count > 0:
         line["batched"] = batched_line(a, ndhss, torch, stream)
+        b = line["batched"]
+        krl.append({"kernel": "mapply_kernel (batched 32-column apply)", "bound": "alu", "unit": "TFLOP/s",
+                    "achieved": b["apply_multi_tflops"], "peak": fp32_peak,
+                    "peak_kind": "derived: 152 SMs x 128 FP32 lanes x 2 x max SM clock",
+                    "frac": b["apply_multi_tflops"] / fp32_peak, "algorithmic": "8 x 32 flops per stored element"})
     if a.elastic_N > 0:
         line["elastic"] = elastic_line(a, ndhss, torch, stream)
     if not a.no_cpu_baseline and world == 1:
