@@ -58,15 +58,17 @@ __device__ __forceinline__ c128 cdiv(c128 a, c128 b) { return a * recip(b); }
 __device__ __forceinline__ double cdiv(double a, double b) { return a / b; }
 
 // ----------------------------------------------------------------- SpMV
-// acc + a * b.  GB300's FP64 pipe is what bounds the complex product, and
-// most entries of the FEM matrices are real (the impedance term is on the
-// boundary only): the FMAs with a zero imaginary part are skipped.  The
-// rounding of the remaining operations is that of the full product.
+// acc + a * b.  GB300's FP64 pipe is narrow, and most entries of the FEM
+// matrices are real (the impedance term is on the boundary only): the FMAs
+// with a zero imaginary part are skipped.  The test reads the bit pattern
+// (a float64 compare would itself take an FP64-pipe slot; -0.0 just takes
+// the full product).  The rounding of the remaining operations is that of
+// the full product.
 __device__ __forceinline__ double spmv_mac(double a, double b, double c) { return fma(a, b, c); }
 __device__ __forceinline__ c128 spmv_mac(c128 a, c128 b, c128 c) {
     c.x = fma(a.x, b.x, c.x);
     c.y = fma(a.x, b.y, c.y);
-    if (a.y != 0.0) {
+    if (__double_as_longlong(a.y) != 0) {
         c.x = fma(-a.y, b.y, c.x);
         c.y = fma(a.y, b.x, c.y);
     }
