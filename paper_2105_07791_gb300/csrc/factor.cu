@@ -292,10 +292,22 @@ panel_prep_kernel(const int32_t* __restrict__ lev, const int32_t* __restrict__ n
         __syncwarp();
         if (j >= k0 && j < k0 + kbp) {
             const int cidx = (int)(j - k0);
-            for (int64_t i = lane; i < m; i += 32) {
-                T v = Fj[i];
-                if (i >= k0 && i < k0 + kbp) v = (i - k0 == cidx) ? one<T>() : zero<T>();
-                C[(int64_t)cidx * m + i] = v;
+            // the whole pivot column: eight rows per lane loaded before they are
+            // stored (one load-store pair at a time waits out the latency m / 32 times)
+            for (int64_t i0 = lane; i0 < m; i0 += 32 * 8) {
+                T v[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const int64_t i = i0 + 32 * u;
+                    v[u] = i < m ? Fj[i] : zero<T>();
+                }
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const int64_t i = i0 + 32 * u;
+                    if (i >= m) continue;
+                    if (i >= k0 && i < k0 + kbp) v[u] = (i - k0 == cidx) ? one<T>() : zero<T>();
+                    C[(int64_t)cidx * m + i] = v[u];
+                }
             }
             if (lane < kbp) Z[j * KBMAX + lane] = s_ai[cidx * KBMAX + lane];
         } else {
