@@ -176,7 +176,10 @@ ndhss_status ndhss_build_tree_batched(int32_t nsys, const int32_t* n, const int3
                                       const int32_t* const* rowptr, const int32_t* const* col,
                                       int32_t leaf_size, ndhss_tree** out);
 
-/* Sizes of the arrays ndhss_tree_export fills (any pointer may be NULL). */
+/* ndhss_tree_sizes -- sizes of the arrays ndhss_tree_export fills: node
+ * count, tree depth (levels 0 .. depth), number of CSR entries and the summed
+ * length of all B^sigma lists (any output pointer may be NULL).  Host only.
+ * INVALID_ARG when t is NULL. */
 ndhss_status ndhss_tree_sizes(const ndhss_tree* t, int32_t* nnodes, int32_t* depth,
                               int64_t* nnz, int64_t* sum_mb);
 
@@ -224,6 +227,9 @@ ndhss_status ndhss_factor(const ndhss_tree* t, int32_t vtype, const int32_t* d_r
                           const int32_t* d_col, const void* d_vals, const ndhss_factor_opts* opts,
                           void* stream, ndhss_factorization** out);
 
+/* ndhss_factor_stats_get -- copy the factor's sizes, ranks and (with
+ * opts.timing = 1) per-class device times into caller-owned *st.  Host only,
+ * no device work.  INVALID_ARG when f or st is NULL. */
 ndhss_status ndhss_factor_stats_get(const ndhss_factorization* f, ndhss_factor_stats* st);
 
 /*
