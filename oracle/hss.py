@@ -36,6 +36,16 @@ STAGNATION_FLOOR = 1e3 * np.finfo(np.float64).eps / 2    # relative, float64 ari
 MAX_SAMPLES = 256
 
 
+def _matmat(A, X):
+    """A X for a dense array, or an operator's own product (matrix-free form)."""
+    return A @ X if isinstance(A, np.ndarray) else A.matmat(X)
+
+
+def _entries(A, I, J):
+    """The block A(I, J) of a dense array, or entries read from an operator."""
+    return A[np.ix_(I, J)] if isinstance(A, np.ndarray) else A.entries(I, J)
+
+
 def _stop(err, ref, eps, prev_err, nsamp, nmax, r):
     """The adaptive loop's stopping test (shared by both compressions)."""
     return (err <= eps * ref or nsamp >= nmax or nsamp + r > MAX_SAMPLES
@@ -230,9 +240,12 @@ def hss_dense(H: HSS) -> np.ndarray:
 
 def hss_compress(A: np.ndarray, tree: list, eps: float, k0: int = 32, r: int = 16, seed: int = 0,
                  stream: int = 0, rank_cap: int = 512, oversample_min: int = 10) -> HSS:
-    """Algorithm A.1 for a symmetric (or complex symmetric) dense matrix A.
+    """Algorithm A.1 for a symmetric (or complex symmetric) matrix A.
 
-    Matrix-vector products are A @ Omega and entries are read from A.  The
+    A is a dense array, or an operator with ``shape``, ``dtype``,
+    ``matmat(X)`` and ``entries(I, J)``: the two accesses Alg. A.1 makes
+    (products with Gaussian blocks, individual entries), as Sec. 3.5 uses it
+    without forming the matrix.  The
     estimator (Eq. 2.7, relative reading): ||S~ - A_HSS Omega~||_F <= eps ||S~||_F
     with r fresh samples; on failure k <- k + r and Omega, S are extended.
     """
@@ -240,7 +253,7 @@ def hss_compress(A: np.ndarray, tree: list, eps: float, k0: int = 32, r: int = 1
     dtype = np.result_type(A.dtype, np.float64)
     k = k0
     Om = gaussian(n, k + r, seed, stream * 64 + 0)
-    S = A @ Om
+    S = _matmat(A, Om)
     rnd = 0
     prev_err = np.inf
     while True:
@@ -250,7 +263,7 @@ def hss_compress(A: np.ndarray, tree: list, eps: float, k0: int = 32, r: int = 1
         maxr = min(rank_cap, max(1, nsamp - oversample_min))
         levels = max(c.level for c in tree)
         if len(tree) == 1:
-            H.D[0] = A.copy()
+            H.D[0] = A.copy() if isinstance(A, np.ndarray) else A.entries(np.arange(n), np.arange(n))
         for l in range(levels, 0, -1):
             for i, c in enumerate(tree):
                 if c.level != l:
@@ -258,7 +271,7 @@ def hss_compress(A: np.ndarray, tree: list, eps: float, k0: int = 32, r: int = 1
                 if not c.children:
                     Iloc = np.arange(c.lo, c.hi)
                     Oloc = Om[c.lo:c.hi]
-                    Dii = A[np.ix_(Iloc, Iloc)]
+                    Dii = _entries(A, Iloc, Iloc)
                     Sloc = S[c.lo:c.hi] - Dii @ Oloc
                     H.D[i] = Dii
                 else:
@@ -266,8 +279,8 @@ def hss_compress(A: np.ndarray, tree: list, eps: float, k0: int = 32, r: int = 1
                     I1, I2 = H.skel[c1], H.skel[c2]
                     O1, S1 = Hd[c1]
                     O2, S2 = Hd[c2]
-                    A12 = A[np.ix_(I1, I2)]
-                    A21 = A[np.ix_(I2, I1)]
+                    A12 = _entries(A, I1, I2)
+                    A21 = _entries(A, I2, I1)
                     Iloc = np.concatenate([I1, I2])
                     Oloc = np.vstack([O1, O2])
                     Sloc = np.vstack([S1 - A12 @ O2, S2 - A21 @ O1])
@@ -278,12 +291,12 @@ def hss_compress(A: np.ndarray, tree: list, eps: float, k0: int = 32, r: int = 1
                 H.skel[i] = Iloc[J]
         if tree[0].children:
             c1, c2 = tree[0].children
-            H.B12[0] = A[np.ix_(H.skel[c1], H.skel[c2])]
-            H.B21[0] = A[np.ix_(H.skel[c2], H.skel[c1])]
+            H.B12[0] = _entries(A, H.skel[c1], H.skel[c2])
+            H.B21[0] = _entries(A, H.skel[c2], H.skel[c1])
         H.rounds = rnd + 1
         H.samples = nsamp
         Ot = gaussian(n, r, seed, stream * 64 + 1 + rnd)
-        St = A @ Ot
+        St = _matmat(A, Ot)
         err = np.linalg.norm(St - hss_matvec(H, Ot))
         ref = np.linalg.norm(St)
         # stop at eps, when the samples exhaust the matrix or reach MAX_SAMPLES, or when
@@ -466,19 +479,21 @@ class LowRank:
 def lowrank_rows(R: np.ndarray, eps: float, k0: int = 32, r: int = 16, seed: int = 0, stream: int = 0,
                  rank_cap: int = 512, oversample_min: int = 10) -> LowRank:
     """R ~ X R(J, :) by randomized range finding (Sec. 3.4): samples Y = R Omega,
-    a row ID of Y, and the relative estimator on r fresh samples."""
+    a row ID of Y, and the relative estimator on r fresh samples.  R is a
+    dense array, or an operator with ``shape``, ``matmat(X)`` and
+    ``rows(J)`` (the rows R(J, :))."""
     m, nb = R.shape
     k = k0
     Om = gaussian(nb, k + r, seed, stream * 64 + 32)
-    Y = R @ Om
+    Y = _matmat(R, Om)
     rnd = 0
     prev_err = np.inf
     while True:
         maxr = min(rank_cap, max(1, Y.shape[1] - oversample_min), m)
         J, X = row_id(Y, eps, maxr)
-        lr = LowRank(X=X, J=J, RJ=R[J])
+        lr = LowRank(X=X, J=J, RJ=R[J] if isinstance(R, np.ndarray) else R.rows(J))
         Ot = gaussian(nb, r, seed, stream * 64 + 33 + rnd)
-        Yt = R @ Ot
+        Yt = _matmat(R, Ot)
         err = np.linalg.norm(Yt - lr.matmat(Ot))
         if _stop(err, np.linalg.norm(Yt), eps, prev_err, Y.shape[1], min(m, nb, rank_cap + oversample_min), r):
             return lr
