@@ -141,3 +141,48 @@ def test_batched_tree_rejects_a_bad_problem(nd):
     bad_col[3] = P.A.shape[0] + 5
     with pytest.raises(nd.NdhssError, match="problem 1"):
         nd.ndhss_build_tree_batched([(P.coords, P.A.indptr, P.A.indices), (P.coords, P.A.indptr, bad_col)], 16)
+
+
+def test_binding_structs_and_constants_match_the_header(nd, tmp_path):
+    """The ctypes mirrors of the header's structs have the C layout (size and
+    every field's offset, as gcc lays them out), and the binding's status,
+    value-type and precision constants equal the header's enumerators."""
+    import ctypes
+    import shutil
+    import subprocess
+    if shutil.which("gcc") is None:
+        pytest.skip("no C compiler")
+    structs = {"ndhss_factor_opts": nd.FactorOpts, "ndhss_gmres_opts": nd.GmresOpts,
+               "ndhss_gmres_stats": nd.GmresStats, "ndhss_factor_stats": nd.FactorStats}
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "ndhss.h"', "int main(void) {"]
+    for cname, py in structs.items():
+        lines.append(f'printf("{cname} sizeof %zu\\n", sizeof({cname}));')
+        for f, _ in py._fields_:
+            lines.append(f'printf("{cname} {f} %zu\\n", offsetof({cname}, {f}));')
+    enums = ["NDHSS_OK", "NDHSS_ERR_INVALID_ARG", "NDHSS_ERR_OOM", "NDHSS_ERR_SINGULAR", "NDHSS_ERR_RANK_CAP",
+             "NDHSS_ERR_NOT_CONVERGED", "NDHSS_ERR_TIMEOUT", "NDHSS_ERR_CUDA", "NDHSS_ERR_INTERNAL", "NDHSS_R64",
+             "NDHSS_C128", "NDHSS_FP64", "NDHSS_FP32", "NDHSS_FP32_TF32", "NDHSS_FP32_BF16"]
+    for e in enums:
+        lines.append(f'printf("enum {e} %d\\n", (int){e});')
+    lines += ["return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c11", "-Wall", "-Werror", "-I", os.path.join(ROOT, "include"), str(src), "-o",
+                    str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {}
+    for line in out:
+        if line:
+            a, b, v = line.split()
+            got[(a, b)] = int(v)
+    for cname, py in structs.items():
+        assert got[(cname, "sizeof")] == ctypes.sizeof(py), cname
+        for f, _ in py._fields_:
+            assert got[(cname, f)] == getattr(py, f).offset, (cname, f)
+    status = {v: k for k, v in nd.STATUS.items()}
+    for e in enums[:9]:
+        name = e.replace("NDHSS_ERR_", "").replace("NDHSS_", "")
+        assert got[("enum", e)] == status[name], e
+    for e in enums[9:]:
+        assert got[("enum", e)] == getattr(nd, e), e
