@@ -87,7 +87,12 @@ typedef struct {
     int32_t maxit;              /* total Arnoldi steps allowed, e.g. 300               */
     double tol;                 /* relative residual target, e.g. 1e-8                 */
     int32_t timing;             /* 1: time every apply / SpMV with CUDA events         */
-    int32_t pad;
+    int32_t conj_transpose;     /* 1: solve A^H x = b on the same factor (the adjoint
+                                   solve; A complex symmetric, so x = conj(A^{-1}
+                                   conj(b)): b is conjugated into scratch, the solve
+                                   runs as usual and x is conjugated on the device;
+                                   stats describe ||b - A^H x||).  No effect for real
+                                   A.  ndhss_gmres only; 0 otherwise                  */
     double inner;               /* a cycle ends at ||P^{-1} r|| <= inner tol ||P^{-1} b||;
                                    0.1 = one decade below tol, as Sec. 4 stops at 1e-9 */
     double cycle_rtol;          /* a cycle also ends once its residual estimate fell by
@@ -356,7 +361,9 @@ ndhss_status ndhss_spmv(int32_t n, int32_t vtype, const int32_t* d_rowptr, const
  *   d_rowptr, d_col, d_vals  device CSR of A (original numbering, vtype of f)
  *   nrhs      right-hand sides, solved one after another
  *   b, x      n x nrhs column-major (ldb, ldx >= n), device or host pointers
- *   opts      NULL = restart 30, maxit 300, tol 1e-8, inner 0.1, cycle_rtol auto
+ *   opts      NULL = restart 30, maxit 300, tol 1e-8, inner 0.1, cycle_rtol auto,
+ *             conj_transpose 0 (1: the adjoint system A^H x = b, Sec. 4's
+ *             gradient by the adjoint state)
  *   stats     host array of nrhs entries (may be NULL)
  * Returns NOT_CONVERGED if any right-hand side missed tol (x still written).
  * Synchronises the stream once per Arnoldi step (to read the residual).

@@ -5,8 +5,8 @@ Helmholtz model of Sec. 4 (Eq. 4.2) whose squared slowness m is piecewise
 constant on blocks: the forward pass factors A(m) with ``ndhss_factor`` and
 solves every column with ``ndhss_gmres``.  The backward pass needs
 Lambda = A^{-H} G; A is complex symmetric (A^T = A), so
-A^{-H} G = conj(A^{-1} conj(G)) and the adjoint solve reuses the forward
-pass's factor and GMRES.  Then (PyTorch's conjugate-Wirtinger convention,
+A^{-H} G = conj(A^{-1} conj(G)) and the adjoint solve (``ndhss_gmres`` with
+``conj_transpose``) reuses the forward pass's factor and GMRES.  Then (PyTorch's conjugate-Wirtinger convention,
 dJ = Re(G^H dX)):
 
     grad_B   = Lambda
@@ -68,11 +68,11 @@ class HelmholtzBlockModel:
         return -dA.real
 
 
-def _solve_columns(f, M, B, tol):
+def _solve_columns(f, M, B, tol, adjoint=False):
     X = torch.empty_like(B)
     for s in range(B.shape[1]):
         x = torch.zeros(B.shape[0], dtype=B.dtype, device=B.device)
-        st = ndhss.ndhss_gmres(f, M.rowptr, M.col, M.vals, B[:, s].contiguous(), x, tol=tol)
+        st = ndhss.ndhss_gmres(f, M.rowptr, M.col, M.vals, B[:, s].contiguous(), x, tol=tol, conj_transpose=adjoint)
         if not st["converged"]:
             raise RuntimeError(f"ndhss_gmres did not converge: {st}")
         X[:, s] = x
@@ -97,8 +97,8 @@ class HelmholtzSolve(torch.autograd.Function):
         m, X = ctx.saved_tensors
         model = ctx.model
         G2 = (G.unsqueeze(1) if ctx.one else G).resolve_conj().to(torch.complex128)
-        # A^{-H} G = conj(A^{-1} conj(G)) for complex symmetric A
-        Lam = torch.conj_physical(_solve_columns(ctx.f, ctx.M, torch.conj_physical(G2).contiguous(), model.tol))
+        # A^{-H} G by the library's adjoint solve (conj(A^{-1} conj(G)) for complex symmetric A)
+        Lam = _solve_columns(ctx.f, ctx.M, G2.contiguous(), model.tol, adjoint=True)
         md = m.detach().to(device=model.device, dtype=torch.float64)
         gm = torch.zeros(model.nblk, dtype=torch.float64, device=model.device)
         for s in range(X.shape[1]):

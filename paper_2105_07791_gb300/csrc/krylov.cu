@@ -223,6 +223,21 @@ __global__ void residual_kernel(int n, const V* __restrict__ b, const V* __restr
         r[i] = b[i] - ax[i];
 }
 
+// v <- conj(v): the adjoint solve of a complex symmetric A, A^H x = b, is
+// A conj(x) = conj(b).
+__global__ void __launch_bounds__(256) conj_kernel(int64_t n, c128* __restrict__ v) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        v[i].y = -v[i].y;
+}
+
+static ndhss_status conj_inplace(c128* v, int64_t n, cudaStream_t st) {
+    const int64_t blocks = std::min<int64_t>((n + 255) / 256, 152 * 8);
+    if (blocks < 1) return NDHSS_OK;
+    conj_kernel<<<(unsigned)blocks, 256, 0, st>>>(n, v);
+    NDHSS_LAUNCH_CHECK("conj_kernel");
+    return NDHSS_OK;
+}
+
 // scalars: [0] scale for the next basis vector, [1] |g_{j+1}|, [2] h_{j+1,j}, [3] beta
 struct GmState {
     double scal[4];
@@ -519,22 +534,27 @@ ndhss_status ndhss_gmres(const ndhss_factorization* fh, const int32_t* d_rowptr,
     if (ldb < F.n || ldx < F.n) return set_error(NDHSS_ERR_INVALID_ARG, "ndhss_gmres: leading dimension < n");
     ndhss_gmres_opts o{30, 300, 1e-8, 0, 0, 0.1, -1.0};
     if (opts) o = *opts;
-    if (o.restart < 1 || o.restart > KMAX - 1 || o.maxit < 0 || !(o.tol >= 0) || !(o.inner > 0 && o.inner <= 1))
+    if (o.restart < 1 || o.restart > KMAX - 1 || o.maxit < 0 || !(o.tol >= 0) || !(o.inner > 0 && o.inner <= 1) ||
+        o.conj_transpose < 0 || o.conj_transpose > 1)
         return set_error(NDHSS_ERR_INVALID_ARG,
-                         "ndhss_gmres: need 1 <= restart <= %d, maxit >= 0, tol >= 0, 0 < inner <= 1", KMAX - 1);
+                         "ndhss_gmres: need 1 <= restart <= %d, maxit >= 0, tol >= 0, 0 < inner <= 1, conj_transpose 0 or 1",
+                         KMAX - 1);
     if (nrhs == 0) return NDHSS_OK;
     if (o.cycle_rtol < 0) o.cycle_rtol = (F.prec == NDHSS_FP64) ? 0.0 : 1e-3;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const size_t vsz = F.vtype == NDHSS_C128 ? 16 : 8;
     const bool bdev = is_device_ptr(b), xdev = is_device_ptr(x);
+    // A^H = A for real symmetric A: the flag changes nothing there
+    const bool conj = o.conj_transpose != 0 && F.vtype == NDHSS_C128;
+    const bool stage_b = !bdev || conj;          // conj(b) is formed in scratch, never in the caller's b
     const size_t vec = ((size_t)F.n * vsz + 255) / 256 * 256;
-    const size_t wb = gmres_work_bytes(F, o.restart, vsz) + (bdev ? 0 : vec) + (xdev ? 0 : vec);
+    const size_t wb = gmres_work_bytes(F, o.restart, vsz) + (stage_b ? vec : 0) + (xdev ? 0 : vec);
     void* work = nullptr;
     NDHSS_CUDA_TRY(pool_malloc_async(&work, wb, st));
     unsigned char* ws = static_cast<unsigned char*>(work);
     unsigned char* extra = ws + gmres_work_bytes(F, o.restart, vsz);
-    void* db = bdev ? nullptr : extra;
-    void* dx = xdev ? nullptr : extra + (bdev ? 0 : vec);
+    void* db = stage_b ? extra : nullptr;
+    void* dx = xdev ? nullptr : extra + (stage_b ? vec : 0);
     ndhss_status rc = NDHSS_OK;
     bool any_fail = false;
     for (int rhs = 0; rhs < nrhs && rc == NDHSS_OK; ++rhs) {
@@ -542,12 +562,14 @@ ndhss_status ndhss_gmres(const ndhss_factorization* fh, const int32_t* d_rowptr,
         unsigned char* xdst = (unsigned char*)x + (size_t)rhs * ldx * vsz;
         const void* bb = bsrc;
         void* xx = xdst;
-        if (!bdev) {
-            if (cudaMemcpyAsync(db, bsrc, (size_t)F.n * vsz, cudaMemcpyHostToDevice, st) != cudaSuccess) {
-                rc = set_error(NDHSS_ERR_CUDA, "ndhss_gmres: host-to-device copy failed");
+        if (stage_b) {
+            const cudaMemcpyKind kind = bdev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+            if (cudaMemcpyAsync(db, bsrc, (size_t)F.n * vsz, kind, st) != cudaSuccess) {
+                rc = set_error(NDHSS_ERR_CUDA, "ndhss_gmres: copy of b failed");
                 break;
             }
             bb = db;
+            if (conj && (rc = conj_inplace(static_cast<c128*>(db), F.n, st)) != NDHSS_OK) break;
         }
         if (!xdev) xx = dx;
         ndhss_gmres_stats S{};
@@ -555,6 +577,7 @@ ndhss_status ndhss_gmres(const ndhss_factorization* fh, const int32_t* d_rowptr,
             rc = gmres_one<double>(F, d_rowptr, d_col, (const double*)d_vals, (const double*)bb, (double*)xx, o, &S, ws, st);
         else
             rc = gmres_one<c128>(F, d_rowptr, d_col, (const c128*)d_vals, (const c128*)bb, (c128*)xx, o, &S, ws, st);
+        if (rc == NDHSS_OK && conj) rc = conj_inplace(static_cast<c128*>(xx), F.n, st);
         if (rc == NDHSS_OK && !xdev) {
             if (cudaMemcpyAsync(xdst, dx, (size_t)F.n * vsz, cudaMemcpyDeviceToHost, st) != cudaSuccess)
                 rc = set_error(NDHSS_ERR_CUDA, "ndhss_gmres: device-to-host copy failed");

@@ -781,6 +781,8 @@ ndhss_status ndhss_gmres_batched(const ndhss_factorization* fh, const int32_t* d
     if (o.restart < 1 || o.restart > BK - 1 || o.maxit < 0 || !(o.tol >= 0) || !(o.inner > 0 && o.inner <= 1))
         return set_error(NDHSS_ERR_INVALID_ARG, "ndhss_gmres_batched: need 1 <= restart <= %d, maxit >= 0, tol >= 0, 0 < inner <= 1",
                          BK - 1);
+    if (o.conj_transpose != 0)
+        return set_error(NDHSS_ERR_INVALID_ARG, "ndhss_gmres_batched: conj_transpose is not supported (use ndhss_gmres)");
     if (nrhs == 0) return NDHSS_OK;
     ndhss_status rc = multi_supported(F, "ndhss_gmres_batched");
     if (rc != NDHSS_OK) return rc;

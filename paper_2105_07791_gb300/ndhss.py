@@ -43,7 +43,7 @@ class FactorOpts(C.Structure):
 
 class GmresOpts(C.Structure):
     _fields_ = [("restart", C.c_int32), ("maxit", C.c_int32), ("tol", C.c_double), ("timing", C.c_int32),
-                ("pad", C.c_int32), ("inner", C.c_double), ("cycle_rtol", C.c_double)]
+                ("conj_transpose", C.c_int32), ("inner", C.c_double), ("cycle_rtol", C.c_double)]
 
 
 class GmresStats(C.Structure):
@@ -309,11 +309,13 @@ def ndhss_kernel_launches() -> int:
 
 
 def ndhss_gmres(f: Factor, d_rowptr, d_col, d_vals, b, x, restart=30, maxit=300, tol=1e-8, stream=None,
-                raise_on_nonconvergence=False, timing=False, inner=0.1, cycle_rtol=-1.0):
-    """Solve A x = b; b, x are (n,) torch CUDA tensors or numpy arrays.  Returns the stats dict."""
+                raise_on_nonconvergence=False, timing=False, inner=0.1, cycle_rtol=-1.0, conj_transpose=False):
+    """Solve A x = b (A^H x = b with conj_transpose); b, x are (n,) torch CUDA
+    tensors or numpy arrays.  Returns the stats dict."""
     n = f.n
     st = GmresStats()
-    o = GmresOpts(int(restart), int(maxit), float(tol), int(bool(timing)), 0, float(inner), float(cycle_rtol))
+    o = GmresOpts(int(restart), int(maxit), float(tol), int(bool(timing)), int(bool(conj_transpose)), float(inner),
+                  float(cycle_rtol))
     code = load().ndhss_gmres(f.handle, _ptr(d_rowptr), _ptr(d_col), _ptr(d_vals), 1, _ptr(b), n, _ptr(x), n,
                               C.byref(o), C.byref(st), _stream(stream))
     if code == 5 and not raise_on_nonconvergence:

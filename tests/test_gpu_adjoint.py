@@ -139,3 +139,45 @@ def test_c5_sized_gradient_matches_oracle():
           f"oracle (sparse direct, A given) {t_cpu:.2f} s")
     assert abs(J.item() - Jo) <= 1e-7 * Jo
     assert np.linalg.norm(g - go) <= 1e-5 * np.linalg.norm(go), np.linalg.norm(g - go) / np.linalg.norm(go)
+
+
+@pytest.mark.parametrize("host", [False, True])
+def test_conj_transpose_solves_the_adjoint_system(nd, host):
+    """ndhss_gmres with conj_transpose solves A^H x = b on the factor of A
+    (device and host buffers); the caller's b is left as it was."""
+    P = _problem()[0]
+    tree = nd.ndhss_build_tree(P.coords, P.A.indptr, P.A.indices, 64)
+    M = nd.DeviceCSR(P.A)
+    f = nd.ndhss_factor(tree, M.vtype, M.rowptr, M.col, M.vals, nd.make_factor_opts(prec=nd.NDHSS_FP32, hss_levels=2))
+    rng = np.random.default_rng(4)
+    g = rng.standard_normal(P.n) + 1j * rng.standard_normal(P.n)
+    if host:
+        b, x = g.copy(), np.zeros_like(g)
+    else:
+        b = torch.from_numpy(g).cuda()
+        x = torch.zeros_like(b)
+    st = nd.ndhss_gmres(f, M.rowptr, M.col, M.vals, b, x, tol=1e-10, conj_transpose=True)
+    xh = x if host else x.cpu().numpy()
+    bh = b if host else b.cpu().numpy()
+    assert st["converged"] and st["true_relres"] <= 1e-10
+    assert np.array_equal(bh, g)
+    AH = P.A.conj().T.tocsr()
+    assert np.linalg.norm(AH @ xh - g) <= 1e-9 * np.linalg.norm(g)
+    # the plain solve on the same factor is a different system
+    y = np.zeros_like(g)
+    nd.ndhss_gmres(f, M.rowptr, M.col, M.vals, g.copy(), y, tol=1e-10)
+    assert np.linalg.norm(P.A @ y - g) <= 1e-9 * np.linalg.norm(g)
+    assert np.linalg.norm(y - xh) > 1e-3 * np.linalg.norm(y)
+
+
+def test_conj_transpose_changes_nothing_for_a_real_matrix(nd):
+    from ndhss_inputs import poisson_dirichlet
+    P = poisson_dirichlet(40, p=1, seed=0)
+    tree = nd.ndhss_build_tree(P.coords, P.A.indptr, P.A.indices, 64)
+    M = nd.DeviceCSR(P.A)
+    f = nd.ndhss_factor(tree, M.vtype, M.rowptr, M.col, M.vals, nd.make_factor_opts(prec=nd.NDHSS_FP32))
+    b = torch.from_numpy(np.ascontiguousarray(P.b if P.b.ndim == 1 else P.b[:, 0])).cuda()
+    x0, x1 = torch.zeros_like(b), torch.zeros_like(b)
+    nd.ndhss_gmres(f, M.rowptr, M.col, M.vals, b, x0, tol=1e-10)
+    nd.ndhss_gmres(f, M.rowptr, M.col, M.vals, b, x1, tol=1e-10, conj_transpose=True)
+    assert torch.equal(x0, x1)
