@@ -43,16 +43,18 @@ __global__ void elem_qform_kernel(int ngroups, const int32_t* __restrict__ goff,
 extern "C" ndhss_status ndhss_elem_qform(int32_t ngroups, const int32_t* d_goff, int32_t nloc, const int32_t* d_idx,
                                          const double* d_mats, const void* d_lam, const void* d_x, void* d_q,
                                          void* stream) {
-    using namespace ndhss;
-    clear_error();
-    if (ngroups < 0 || nloc < 1 || !d_goff || !d_idx || !d_mats || !d_lam || !d_x || !d_q)
-        return set_error(NDHSS_ERR_INVALID_ARG, "ndhss_elem_qform: bad argument");
-    if (ngroups == 0) return NDHSS_OK;
-    const int threads = 256;
-    const unsigned blocks = (unsigned)(((int64_t)ngroups * 32 + threads - 1) / threads);
-    elem_qform_kernel<<<blocks, threads, 0, static_cast<cudaStream_t>(stream)>>>(
-        ngroups, d_goff, nloc, d_idx, d_mats, static_cast<const c128*>(d_lam), static_cast<const c128*>(d_x),
-        static_cast<c128*>(d_q));
-    NDHSS_LAUNCH_CHECK("elem_qform_kernel");
-    return NDHSS_OK;
+    return ::ndhss::guarded("ndhss_elem_qform", [&]() -> ndhss_status {
+        using namespace ndhss;
+        clear_error();
+        if (ngroups < 0 || nloc < 1 || !d_goff || !d_idx || !d_mats || !d_lam || !d_x || !d_q)
+            return set_error(NDHSS_ERR_INVALID_ARG, "ndhss_elem_qform: bad argument");
+        if (ngroups == 0) return NDHSS_OK;
+        const int threads = 256;
+        const unsigned blocks = (unsigned)(((int64_t)ngroups * 32 + threads - 1) / threads);
+        elem_qform_kernel<<<blocks, threads, 0, static_cast<cudaStream_t>(stream)>>>(
+            ngroups, d_goff, nloc, d_idx, d_mats, static_cast<const c128*>(d_lam), static_cast<const c128*>(d_x),
+            static_cast<c128*>(d_q));
+        NDHSS_LAUNCH_CHECK("elem_qform_kernel");
+        return NDHSS_OK;
+    });
 }

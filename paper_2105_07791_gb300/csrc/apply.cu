@@ -1314,50 +1314,52 @@ ndhss_status apply_device(const FactorData& F, int32_t nrhs, const void* d_x, in
 
 extern "C" ndhss_status ndhss_apply(const ndhss_factorization* fh, int32_t nrhs, const void* x, int64_t ldx, void* y,
                                     int64_t ldy, void* stream) {
-    using namespace ndhss;
-    clear_error();
-    if (!fh || !x || !y || nrhs < 0) return set_error(NDHSS_ERR_INVALID_ARG, "ndhss_apply: bad argument");
-    const FactorData& F = fh->f;
-    if (ldx < F.n || ldy < F.n) return set_error(NDHSS_ERR_INVALID_ARG, "ndhss_apply: leading dimension < n");
-    if (nrhs == 0) return NDHSS_OK;
-    cudaStream_t st = static_cast<cudaStream_t>(stream);
-    const size_t vsz = F.vtype == NDHSS_C128 ? 16 : 8;
-    const bool xdev = is_device_ptr(x), ydev = is_device_ptr(y);
-    const size_t wb = apply_work_bytes(F) + (xdev ? 0 : (size_t)F.n * nrhs * vsz + 256) + (ydev ? 0 : (size_t)F.n * nrhs * vsz + 256);
-    void* work = nullptr;
-    NDHSS_CUDA_TRY(pool_malloc_async(&work, wb, st));
-    unsigned char* p = static_cast<unsigned char*>(work) + (apply_work_bytes(F) + 255) / 256 * 256;
-    const void* dx = x;
-    void* dy = y;
-    int64_t lx = ldx, ly = ldy;
-    ndhss_status rc = NDHSS_OK;
-    if (!xdev) {
-        dx = p;
-        lx = F.n;
-        p += ((size_t)F.n * nrhs * vsz + 255) / 256 * 256;
-        for (int r = 0; r < nrhs && rc == NDHSS_OK; ++r)
-            if (cudaMemcpyAsync((unsigned char*)dx + (size_t)r * F.n * vsz, (const unsigned char*)x + (size_t)r * ldx * vsz,
-                                (size_t)F.n * vsz, cudaMemcpyHostToDevice, st) != cudaSuccess)
-                rc = set_error(NDHSS_ERR_CUDA, "ndhss_apply: host-to-device copy failed");
-    }
-    if (!ydev) {
-        dy = p;
-        ly = F.n;
-    }
-    if (rc == NDHSS_OK) rc = apply_device(F, nrhs, dx, lx, dy, ly, work, st);
-    if (rc == NDHSS_OK && !ydev) {
-        for (int r = 0; r < nrhs && rc == NDHSS_OK; ++r)
-            if (cudaMemcpyAsync((unsigned char*)y + (size_t)r * ldy * vsz, (const unsigned char*)dy + (size_t)r * F.n * vsz,
-                                (size_t)F.n * vsz, cudaMemcpyDeviceToHost, st) != cudaSuccess)
-                rc = set_error(NDHSS_ERR_CUDA, "ndhss_apply: device-to-host copy failed");
-    }
-    cudaFreeAsync(work, st);
-    if (!xdev || !ydev) {
-        if (cudaStreamSynchronize(st) != cudaSuccess && rc == NDHSS_OK)
-            rc = set_error(NDHSS_ERR_CUDA, "ndhss_apply: stream synchronisation failed");
-        if (rc == NDHSS_OK) rc = apply_check_error(F, "ndhss_apply");
-    }
-    return rc;
+    return ::ndhss::guarded("ndhss_apply", [&]() -> ndhss_status {
+        using namespace ndhss;
+        clear_error();
+        if (!fh || !x || !y || nrhs < 0) return set_error(NDHSS_ERR_INVALID_ARG, "ndhss_apply: bad argument");
+        const FactorData& F = fh->f;
+        if (ldx < F.n || ldy < F.n) return set_error(NDHSS_ERR_INVALID_ARG, "ndhss_apply: leading dimension < n");
+        if (nrhs == 0) return NDHSS_OK;
+        cudaStream_t st = static_cast<cudaStream_t>(stream);
+        const size_t vsz = F.vtype == NDHSS_C128 ? 16 : 8;
+        const bool xdev = is_device_ptr(x), ydev = is_device_ptr(y);
+        const size_t wb = apply_work_bytes(F) + (xdev ? 0 : (size_t)F.n * nrhs * vsz + 256) + (ydev ? 0 : (size_t)F.n * nrhs * vsz + 256);
+        void* work = nullptr;
+        NDHSS_CUDA_TRY(pool_malloc_async(&work, wb, st));
+        unsigned char* p = static_cast<unsigned char*>(work) + (apply_work_bytes(F) + 255) / 256 * 256;
+        const void* dx = x;
+        void* dy = y;
+        int64_t lx = ldx, ly = ldy;
+        ndhss_status rc = NDHSS_OK;
+        if (!xdev) {
+            dx = p;
+            lx = F.n;
+            p += ((size_t)F.n * nrhs * vsz + 255) / 256 * 256;
+            for (int r = 0; r < nrhs && rc == NDHSS_OK; ++r)
+                if (cudaMemcpyAsync((unsigned char*)dx + (size_t)r * F.n * vsz, (const unsigned char*)x + (size_t)r * ldx * vsz,
+                                    (size_t)F.n * vsz, cudaMemcpyHostToDevice, st) != cudaSuccess)
+                    rc = set_error(NDHSS_ERR_CUDA, "ndhss_apply: host-to-device copy failed");
+        }
+        if (!ydev) {
+            dy = p;
+            ly = F.n;
+        }
+        if (rc == NDHSS_OK) rc = apply_device(F, nrhs, dx, lx, dy, ly, work, st);
+        if (rc == NDHSS_OK && !ydev) {
+            for (int r = 0; r < nrhs && rc == NDHSS_OK; ++r)
+                if (cudaMemcpyAsync((unsigned char*)y + (size_t)r * ldy * vsz, (const unsigned char*)dy + (size_t)r * F.n * vsz,
+                                    (size_t)F.n * vsz, cudaMemcpyDeviceToHost, st) != cudaSuccess)
+                    rc = set_error(NDHSS_ERR_CUDA, "ndhss_apply: device-to-host copy failed");
+        }
+        cudaFreeAsync(work, st);
+        if (!xdev || !ydev) {
+            if (cudaStreamSynchronize(st) != cudaSuccess && rc == NDHSS_OK)
+                rc = set_error(NDHSS_ERR_CUDA, "ndhss_apply: stream synchronisation failed");
+            if (rc == NDHSS_OK) rc = apply_check_error(F, "ndhss_apply");
+        }
+        return rc;
+    });
 }
 
 // --------------------------------------------------------------------------
@@ -1407,35 +1409,39 @@ ndhss_status scratch_for_current_device(void** out) {
 }  // namespace ndhss
 
 extern "C" ndhss_status ndhss_apply_noalloc(const ndhss_factorization* fh, const void* d_x, void* d_y, void* stream) {
-    using namespace ndhss;
-    clear_error();
-    if (!fh || !d_x || !d_y) return set_error(NDHSS_ERR_INVALID_ARG, "ndhss_apply_noalloc: NULL argument");
-    const FactorData& F = fh->f;
-    const size_t need = apply_work_bytes(F);
-    if (need > NOALLOC_SCRATCH_BYTES)
-        return set_error(NDHSS_ERR_INVALID_ARG,
-                         "ndhss_apply_noalloc: n = %d needs %zu bytes of work space but the static scratch holds %zu; "
-                         "use ndhss_apply", F.n, need, NOALLOC_SCRATCH_BYTES);
-    if (!is_device_ptr(d_x) || !is_device_ptr(d_y))
-        return set_error(NDHSS_ERR_INVALID_ARG, "ndhss_apply_noalloc: x and y must be device pointers");
-    void* scratch = nullptr;
-    const ndhss_status rc = scratch_for_current_device(&scratch);
-    if (rc != NDHSS_OK) return rc;
-    return apply_device(F, 1, d_x, F.n, d_y, F.n, scratch, static_cast<cudaStream_t>(stream));
+    return ::ndhss::guarded("ndhss_apply_noalloc", [&]() -> ndhss_status {
+        using namespace ndhss;
+        clear_error();
+        if (!fh || !d_x || !d_y) return set_error(NDHSS_ERR_INVALID_ARG, "ndhss_apply_noalloc: NULL argument");
+        const FactorData& F = fh->f;
+        const size_t need = apply_work_bytes(F);
+        if (need > NOALLOC_SCRATCH_BYTES)
+            return set_error(NDHSS_ERR_INVALID_ARG,
+                             "ndhss_apply_noalloc: n = %d needs %zu bytes of work space but the static scratch holds %zu; "
+                             "use ndhss_apply", F.n, need, NOALLOC_SCRATCH_BYTES);
+        if (!is_device_ptr(d_x) || !is_device_ptr(d_y))
+            return set_error(NDHSS_ERR_INVALID_ARG, "ndhss_apply_noalloc: x and y must be device pointers");
+        void* scratch = nullptr;
+        const ndhss_status rc = scratch_for_current_device(&scratch);
+        if (rc != NDHSS_OK) return rc;
+        return apply_device(F, 1, d_x, F.n, d_y, F.n, scratch, static_cast<cudaStream_t>(stream));
+    });
 }
 
 // Failure-detection hook: one requirement that no task will ever satisfy.
 extern "C" ndhss_status ndhss_testing_stall_apply(ndhss_factorization* fh) {
-    using namespace ndhss;
-    clear_error();
-    if (!fh || !fh->f.d_need || fh->f.levels.empty() || fh->f.levels[0].empty())
-        return set_error(NDHSS_ERR_INVALID_ARG, "ndhss_testing_stall_apply: no dataflow queue");
-    FactorData& F = fh->f;
-    const int root = F.levels[0][0];
-    int32_t* p = F.d_need + (size_t)CN_FIN * F.nnodes + root;
-    int32_t v = 0;
-    NDHSS_CUDA_TRY(cudaMemcpy(&v, p, sizeof(v), cudaMemcpyDeviceToHost));
-    ++v;
-    NDHSS_CUDA_TRY(cudaMemcpy(p, &v, sizeof(v), cudaMemcpyHostToDevice));
-    return NDHSS_OK;
+    return ::ndhss::guarded("ndhss_testing_stall_apply", [&]() -> ndhss_status {
+        using namespace ndhss;
+        clear_error();
+        if (!fh || !fh->f.d_need || fh->f.levels.empty() || fh->f.levels[0].empty())
+            return set_error(NDHSS_ERR_INVALID_ARG, "ndhss_testing_stall_apply: no dataflow queue");
+        FactorData& F = fh->f;
+        const int root = F.levels[0][0];
+        int32_t* p = F.d_need + (size_t)CN_FIN * F.nnodes + root;
+        int32_t v = 0;
+        NDHSS_CUDA_TRY(cudaMemcpy(&v, p, sizeof(v), cudaMemcpyDeviceToHost));
+        ++v;
+        NDHSS_CUDA_TRY(cudaMemcpy(p, &v, sizeof(v), cudaMemcpyHostToDevice));
+        return NDHSS_OK;
+    });
 }

@@ -1166,13 +1166,17 @@ extern "C" {
 
 ndhss_status ndhss_factor(const ndhss_tree* t, int32_t vtype, const int32_t* d_rowptr, const int32_t* d_col,
                           const void* d_vals, const ndhss_factor_opts* opts, void* stream, ndhss_factorization** out) {
-    ndhss::clear_error();
-    return ndhss::factor_impl(t, vtype, d_rowptr, d_col, d_vals, opts, stream, out);
+    return ::ndhss::guarded("ndhss_factor", [&]() -> ndhss_status {
+        ndhss::clear_error();
+        return ndhss::factor_impl(t, vtype, d_rowptr, d_col, d_vals, opts, stream, out);
+    });
 }
 
 ndhss_status ndhss_factor_get_block(const ndhss_factorization* f, int32_t node, int32_t which, void* host_out, int64_t ld) {
-    ndhss::clear_error();
-    return ndhss::get_block_impl(f, node, which, host_out, ld);
+    return ::ndhss::guarded("ndhss_factor_get_block", [&]() -> ndhss_status {
+        ndhss::clear_error();
+        return ndhss::get_block_impl(f, node, which, host_out, ld);
+    });
 }
 
 ndhss_status ndhss_factor_stats_get(const ndhss_factorization* fh, ndhss_factor_stats* st) {

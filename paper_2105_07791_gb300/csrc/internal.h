@@ -3,6 +3,8 @@
 
 #include <cstdint>
 #include <cstdio>
+#include <exception>
+#include <new>
 #include <string>
 #include <vector>
 
@@ -33,6 +35,23 @@ struct Tree {
 ndhss_status set_error(ndhss_status code, const char* fmt, ...);
 void clear_error();
 void note_launches(int64_t k);
+
+// Runs an entry point's body so that no C++ exception crosses the C ABI: a
+// failed host allocation becomes NDHSS_ERR_OOM, any other exception
+// NDHSS_ERR_INTERNAL (with its message).  Memory that the interrupted call
+// held is not reclaimed on that path.
+template <typename Fn>
+ndhss_status guarded(const char* who, Fn&& fn) noexcept {
+    try {
+        return fn();
+    } catch (const std::bad_alloc&) {
+        return set_error(NDHSS_ERR_OOM, "%s: host allocation failed", who);
+    } catch (const std::exception& e) {
+        return set_error(NDHSS_ERR_INTERNAL, "%s: %s", who, e.what());
+    } catch (...) {
+        return set_error(NDHSS_ERR_INTERNAL, "%s: unexpected exception", who);
+    }
+}
 
 ndhss_status build_tree_impl(int32_t n, const int32_t* coords, const int32_t* rowptr,
                              const int32_t* col, int32_t leaf_size, Tree* T);

@@ -511,87 +511,91 @@ extern "C" {
 
 ndhss_status ndhss_spmv(int32_t n, int32_t vtype, const int32_t* d_rowptr, const int32_t* d_col, const void* d_vals,
                         const void* d_x, void* d_y, void* stream) {
-    using namespace ndhss;
-    clear_error();
-    if (n < 0 || !d_rowptr || !d_col || !d_vals || !d_x || !d_y) return set_error(NDHSS_ERR_INVALID_ARG, "ndhss_spmv: bad argument");
-    if (n == 0) return NDHSS_OK;
-    cudaStream_t st = static_cast<cudaStream_t>(stream);
-    if (vtype == NDHSS_R64)
-        return spmv_launch<double>(n, d_rowptr, d_col, (const double*)d_vals, (const double*)d_x, (double*)d_y, st);
-    if (vtype == NDHSS_C128)
-        return spmv_launch<c128>(n, d_rowptr, d_col, (const c128*)d_vals, (const c128*)d_x, (c128*)d_y, st);
-    return set_error(NDHSS_ERR_INVALID_ARG, "ndhss_spmv: bad vtype %d", vtype);
+    return ::ndhss::guarded("ndhss_spmv", [&]() -> ndhss_status {
+        using namespace ndhss;
+        clear_error();
+        if (n < 0 || !d_rowptr || !d_col || !d_vals || !d_x || !d_y) return set_error(NDHSS_ERR_INVALID_ARG, "ndhss_spmv: bad argument");
+        if (n == 0) return NDHSS_OK;
+        cudaStream_t st = static_cast<cudaStream_t>(stream);
+        if (vtype == NDHSS_R64)
+            return spmv_launch<double>(n, d_rowptr, d_col, (const double*)d_vals, (const double*)d_x, (double*)d_y, st);
+        if (vtype == NDHSS_C128)
+            return spmv_launch<c128>(n, d_rowptr, d_col, (const c128*)d_vals, (const c128*)d_x, (c128*)d_y, st);
+        return set_error(NDHSS_ERR_INVALID_ARG, "ndhss_spmv: bad vtype %d", vtype);
+    });
 }
 
 ndhss_status ndhss_gmres(const ndhss_factorization* fh, const int32_t* d_rowptr, const int32_t* d_col, const void* d_vals,
                          int32_t nrhs, const void* b, int64_t ldb, void* x, int64_t ldx, const ndhss_gmres_opts* opts,
                          ndhss_gmres_stats* stats, void* stream) {
-    using namespace ndhss;
-    clear_error();
-    if (!fh || !d_rowptr || !d_col || !d_vals || !b || !x || nrhs < 0)
-        return set_error(NDHSS_ERR_INVALID_ARG, "ndhss_gmres: bad argument");
-    const FactorData& F = fh->f;
-    if (ldb < F.n || ldx < F.n) return set_error(NDHSS_ERR_INVALID_ARG, "ndhss_gmres: leading dimension < n");
-    ndhss_gmres_opts o{30, 300, 1e-8, 0, 0, 0.1, -1.0};
-    if (opts) o = *opts;
-    if (o.restart < 1 || o.restart > KMAX - 1 || o.maxit < 0 || !(o.tol >= 0) || !(o.inner > 0 && o.inner <= 1) ||
-        o.conj_transpose < 0 || o.conj_transpose > 1)
-        return set_error(NDHSS_ERR_INVALID_ARG,
-                         "ndhss_gmres: need 1 <= restart <= %d, maxit >= 0, tol >= 0, 0 < inner <= 1, conj_transpose 0 or 1",
-                         KMAX - 1);
-    if (nrhs == 0) return NDHSS_OK;
-    if (o.cycle_rtol < 0) o.cycle_rtol = (F.prec == NDHSS_FP64) ? 0.0 : 1e-3;
-    cudaStream_t st = static_cast<cudaStream_t>(stream);
-    const size_t vsz = F.vtype == NDHSS_C128 ? 16 : 8;
-    const bool bdev = is_device_ptr(b), xdev = is_device_ptr(x);
-    // A^H = A for real symmetric A: the flag changes nothing there
-    const bool conj = o.conj_transpose != 0 && F.vtype == NDHSS_C128;
-    const bool stage_b = !bdev || conj;          // conj(b) is formed in scratch, never in the caller's b
-    const size_t vec = ((size_t)F.n * vsz + 255) / 256 * 256;
-    const size_t wb = gmres_work_bytes(F, o.restart, vsz) + (stage_b ? vec : 0) + (xdev ? 0 : vec);
-    void* work = nullptr;
-    NDHSS_CUDA_TRY(pool_malloc_async(&work, wb, st));
-    unsigned char* ws = static_cast<unsigned char*>(work);
-    unsigned char* extra = ws + gmres_work_bytes(F, o.restart, vsz);
-    void* db = stage_b ? extra : nullptr;
-    void* dx = xdev ? nullptr : extra + (stage_b ? vec : 0);
-    ndhss_status rc = NDHSS_OK;
-    bool any_fail = false;
-    for (int rhs = 0; rhs < nrhs && rc == NDHSS_OK; ++rhs) {
-        const unsigned char* bsrc = (const unsigned char*)b + (size_t)rhs * ldb * vsz;
-        unsigned char* xdst = (unsigned char*)x + (size_t)rhs * ldx * vsz;
-        const void* bb = bsrc;
-        void* xx = xdst;
-        if (stage_b) {
-            const cudaMemcpyKind kind = bdev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
-            if (cudaMemcpyAsync(db, bsrc, (size_t)F.n * vsz, kind, st) != cudaSuccess) {
-                rc = set_error(NDHSS_ERR_CUDA, "ndhss_gmres: copy of b failed");
-                break;
+    return ::ndhss::guarded("ndhss_gmres", [&]() -> ndhss_status {
+        using namespace ndhss;
+        clear_error();
+        if (!fh || !d_rowptr || !d_col || !d_vals || !b || !x || nrhs < 0)
+            return set_error(NDHSS_ERR_INVALID_ARG, "ndhss_gmres: bad argument");
+        const FactorData& F = fh->f;
+        if (ldb < F.n || ldx < F.n) return set_error(NDHSS_ERR_INVALID_ARG, "ndhss_gmres: leading dimension < n");
+        ndhss_gmres_opts o{30, 300, 1e-8, 0, 0, 0.1, -1.0};
+        if (opts) o = *opts;
+        if (o.restart < 1 || o.restart > KMAX - 1 || o.maxit < 0 || !(o.tol >= 0) || !(o.inner > 0 && o.inner <= 1) ||
+            o.conj_transpose < 0 || o.conj_transpose > 1)
+            return set_error(NDHSS_ERR_INVALID_ARG,
+                             "ndhss_gmres: need 1 <= restart <= %d, maxit >= 0, tol >= 0, 0 < inner <= 1, conj_transpose 0 or 1",
+                             KMAX - 1);
+        if (nrhs == 0) return NDHSS_OK;
+        if (o.cycle_rtol < 0) o.cycle_rtol = (F.prec == NDHSS_FP64) ? 0.0 : 1e-3;
+        cudaStream_t st = static_cast<cudaStream_t>(stream);
+        const size_t vsz = F.vtype == NDHSS_C128 ? 16 : 8;
+        const bool bdev = is_device_ptr(b), xdev = is_device_ptr(x);
+        // A^H = A for real symmetric A: the flag changes nothing there
+        const bool conj = o.conj_transpose != 0 && F.vtype == NDHSS_C128;
+        const bool stage_b = !bdev || conj;          // conj(b) is formed in scratch, never in the caller's b
+        const size_t vec = ((size_t)F.n * vsz + 255) / 256 * 256;
+        const size_t wb = gmres_work_bytes(F, o.restart, vsz) + (stage_b ? vec : 0) + (xdev ? 0 : vec);
+        void* work = nullptr;
+        NDHSS_CUDA_TRY(pool_malloc_async(&work, wb, st));
+        unsigned char* ws = static_cast<unsigned char*>(work);
+        unsigned char* extra = ws + gmres_work_bytes(F, o.restart, vsz);
+        void* db = stage_b ? extra : nullptr;
+        void* dx = xdev ? nullptr : extra + (stage_b ? vec : 0);
+        ndhss_status rc = NDHSS_OK;
+        bool any_fail = false;
+        for (int rhs = 0; rhs < nrhs && rc == NDHSS_OK; ++rhs) {
+            const unsigned char* bsrc = (const unsigned char*)b + (size_t)rhs * ldb * vsz;
+            unsigned char* xdst = (unsigned char*)x + (size_t)rhs * ldx * vsz;
+            const void* bb = bsrc;
+            void* xx = xdst;
+            if (stage_b) {
+                const cudaMemcpyKind kind = bdev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+                if (cudaMemcpyAsync(db, bsrc, (size_t)F.n * vsz, kind, st) != cudaSuccess) {
+                    rc = set_error(NDHSS_ERR_CUDA, "ndhss_gmres: copy of b failed");
+                    break;
+                }
+                bb = db;
+                if (conj && (rc = conj_inplace(static_cast<c128*>(db), F.n, st)) != NDHSS_OK) break;
             }
-            bb = db;
-            if (conj && (rc = conj_inplace(static_cast<c128*>(db), F.n, st)) != NDHSS_OK) break;
+            if (!xdev) xx = dx;
+            ndhss_gmres_stats S{};
+            if (F.vtype == NDHSS_R64)
+                rc = gmres_one<double>(F, d_rowptr, d_col, (const double*)d_vals, (const double*)bb, (double*)xx, o, &S, ws, st);
+            else
+                rc = gmres_one<c128>(F, d_rowptr, d_col, (const c128*)d_vals, (const c128*)bb, (c128*)xx, o, &S, ws, st);
+            if (rc == NDHSS_OK && conj) rc = conj_inplace(static_cast<c128*>(xx), F.n, st);
+            if (rc == NDHSS_OK && !xdev) {
+                if (cudaMemcpyAsync(xdst, dx, (size_t)F.n * vsz, cudaMemcpyDeviceToHost, st) != cudaSuccess)
+                    rc = set_error(NDHSS_ERR_CUDA, "ndhss_gmres: device-to-host copy failed");
+            }
+            if (stats) stats[rhs] = S;
+            if (!S.converged) any_fail = true;
         }
-        if (!xdev) xx = dx;
-        ndhss_gmres_stats S{};
-        if (F.vtype == NDHSS_R64)
-            rc = gmres_one<double>(F, d_rowptr, d_col, (const double*)d_vals, (const double*)bb, (double*)xx, o, &S, ws, st);
-        else
-            rc = gmres_one<c128>(F, d_rowptr, d_col, (const c128*)d_vals, (const c128*)bb, (c128*)xx, o, &S, ws, st);
-        if (rc == NDHSS_OK && conj) rc = conj_inplace(static_cast<c128*>(xx), F.n, st);
-        if (rc == NDHSS_OK && !xdev) {
-            if (cudaMemcpyAsync(xdst, dx, (size_t)F.n * vsz, cudaMemcpyDeviceToHost, st) != cudaSuccess)
-                rc = set_error(NDHSS_ERR_CUDA, "ndhss_gmres: device-to-host copy failed");
-        }
-        if (stats) stats[rhs] = S;
-        if (!S.converged) any_fail = true;
-    }
-    cudaFreeAsync(work, st);
-    if (cudaStreamSynchronize(st) != cudaSuccess && rc == NDHSS_OK)
-        rc = set_error(NDHSS_ERR_CUDA, "ndhss_gmres: stream synchronisation failed");
-    if (rc == NDHSS_OK) rc = apply_check_error(F, "ndhss_gmres");
-    if (rc == NDHSS_OK && any_fail)
-        rc = set_error(NDHSS_ERR_NOT_CONVERGED, "ndhss_gmres: tolerance not reached within maxit");
-    return rc;
+        cudaFreeAsync(work, st);
+        if (cudaStreamSynchronize(st) != cudaSuccess && rc == NDHSS_OK)
+            rc = set_error(NDHSS_ERR_CUDA, "ndhss_gmres: stream synchronisation failed");
+        if (rc == NDHSS_OK) rc = apply_check_error(F, "ndhss_gmres");
+        if (rc == NDHSS_OK && any_fail)
+            rc = set_error(NDHSS_ERR_NOT_CONVERGED, "ndhss_gmres: tolerance not reached within maxit");
+        return rc;
+    });
 }
 
 }  // extern "C"

@@ -740,65 +740,69 @@ extern "C" {
 
 ndhss_status ndhss_apply_multi(const ndhss_factorization* fh, int32_t nrhs, const void* d_x, int64_t ldx, void* d_y,
                                int64_t ldy, void* stream) {
-    using namespace ndhss;
-    clear_error();
-    if (!fh || !d_x || !d_y || nrhs < 0 || nrhs > MR || ldx < nrhs || ldy < nrhs)
-        return set_error(NDHSS_ERR_INVALID_ARG, "ndhss_apply_multi: bad argument (need 0 <= nrhs <= 32 <= ld)");
-    const FactorData& F = fh->f;
-    if (nrhs == 0 || F.n == 0) return NDHSS_OK;
-    if (!is_device_ptr(d_x) || !is_device_ptr(d_y))
-        return set_error(NDHSS_ERR_INVALID_ARG, "ndhss_apply_multi: x and y must be device pointers");
-    ndhss_status rc = multi_supported(F, "ndhss_apply_multi");
-    if (rc != NDHSS_OK) return rc;
-    cudaStream_t st = static_cast<cudaStream_t>(stream);
-    void* work = nullptr;
-    NDHSS_CUDA_TRY(pool_malloc_async(&work, multi_work_bytes(F), st));
-    rc = multi_apply_device(F, nrhs, d_x, ldx, d_y, ldy, work, st);
-    cudaFreeAsync(work, st);
-    if (rc == NDHSS_OK && cudaStreamSynchronize(st) != cudaSuccess)
-        rc = set_error(NDHSS_ERR_CUDA, "ndhss_apply_multi: %s", cudaGetErrorString(cudaGetLastError()));
-    return rc;
+    return ::ndhss::guarded("ndhss_apply_multi", [&]() -> ndhss_status {
+        using namespace ndhss;
+        clear_error();
+        if (!fh || !d_x || !d_y || nrhs < 0 || nrhs > MR || ldx < nrhs || ldy < nrhs)
+            return set_error(NDHSS_ERR_INVALID_ARG, "ndhss_apply_multi: bad argument (need 0 <= nrhs <= 32 <= ld)");
+        const FactorData& F = fh->f;
+        if (nrhs == 0 || F.n == 0) return NDHSS_OK;
+        if (!is_device_ptr(d_x) || !is_device_ptr(d_y))
+            return set_error(NDHSS_ERR_INVALID_ARG, "ndhss_apply_multi: x and y must be device pointers");
+        ndhss_status rc = multi_supported(F, "ndhss_apply_multi");
+        if (rc != NDHSS_OK) return rc;
+        cudaStream_t st = static_cast<cudaStream_t>(stream);
+        void* work = nullptr;
+        NDHSS_CUDA_TRY(pool_malloc_async(&work, multi_work_bytes(F), st));
+        rc = multi_apply_device(F, nrhs, d_x, ldx, d_y, ldy, work, st);
+        cudaFreeAsync(work, st);
+        if (rc == NDHSS_OK && cudaStreamSynchronize(st) != cudaSuccess)
+            rc = set_error(NDHSS_ERR_CUDA, "ndhss_apply_multi: %s", cudaGetErrorString(cudaGetLastError()));
+        return rc;
+    });
 }
 
 ndhss_status ndhss_gmres_batched(const ndhss_factorization* fh, const int32_t* d_rowptr, const int32_t* d_col,
                                  const void* d_vals, int32_t nsys, const int64_t* sys_off, int32_t nrhs, const void* d_b,
                                  int64_t ldb, void* d_x, int64_t ldx, const ndhss_gmres_opts* opts,
                                  ndhss_gmres_stats* stats, void* stream) {
-    using namespace ndhss;
-    clear_error();
-    if (!fh || !d_rowptr || !d_col || !d_vals || !sys_off || !d_b || !d_x || nsys < 1 || nrhs < 0 || nrhs > MR)
-        return set_error(NDHSS_ERR_INVALID_ARG, "ndhss_gmres_batched: bad argument (need nsys >= 1, 0 <= nrhs <= 32)");
-    const FactorData& F = fh->f;
-    if (ldb < F.n || ldx < F.n) return set_error(NDHSS_ERR_INVALID_ARG, "ndhss_gmres_batched: leading dimension < n");
-    if (sys_off[0] != 0 || sys_off[nsys] != F.n)
-        return set_error(NDHSS_ERR_INVALID_ARG, "ndhss_gmres_batched: sys_off must run from 0 to n");
-    for (int s = 0; s < nsys; ++s)
-        if (sys_off[s + 1] < sys_off[s]) return set_error(NDHSS_ERR_INVALID_ARG, "ndhss_gmres_batched: sys_off decreases");
-    if (!is_device_ptr(d_b) || !is_device_ptr(d_x))
-        return set_error(NDHSS_ERR_INVALID_ARG, "ndhss_gmres_batched: b and x must be device pointers");
-    ndhss_gmres_opts o{30, 300, 1e-8, 0, 0, 0.1, -1.0};
-    if (opts) o = *opts;
-    if (o.restart < 1 || o.restart > BK - 1 || o.maxit < 0 || !(o.tol >= 0) || !(o.inner > 0 && o.inner <= 1))
-        return set_error(NDHSS_ERR_INVALID_ARG, "ndhss_gmres_batched: need 1 <= restart <= %d, maxit >= 0, tol >= 0, 0 < inner <= 1",
-                         BK - 1);
-    if (o.conj_transpose != 0)
-        return set_error(NDHSS_ERR_INVALID_ARG, "ndhss_gmres_batched: conj_transpose is not supported (use ndhss_gmres)");
-    if (nrhs == 0) return NDHSS_OK;
-    ndhss_status rc = multi_supported(F, "ndhss_gmres_batched");
-    if (rc != NDHSS_OK) return rc;
-    if (o.cycle_rtol < 0) o.cycle_rtol = (F.prec == NDHSS_FP64) ? 0.0 : 1e-3;
-    cudaStream_t st = static_cast<cudaStream_t>(stream);
-    if (F.vtype == NDHSS_R64)
-        rc = gmres_batched_run<double>(F, d_rowptr, d_col, (const double*)d_vals, nsys, sys_off, nrhs, (const double*)d_b,
-                                       ldb, (double*)d_x, ldx, o, stats, st);
-    else
-        rc = gmres_batched_run<c128>(F, d_rowptr, d_col, (const c128*)d_vals, nsys, sys_off, nrhs, (const c128*)d_b, ldb,
-                                     (c128*)d_x, ldx, o, stats, st);
-    if (rc == NDHSS_OK || rc == NDHSS_ERR_NOT_CONVERGED) {
-        const ndhss_status r2 = apply_check_error(F, "ndhss_gmres_batched");
-        if (r2 != NDHSS_OK) rc = r2;
-    }
-    return rc;
+    return ::ndhss::guarded("ndhss_gmres_batched", [&]() -> ndhss_status {
+        using namespace ndhss;
+        clear_error();
+        if (!fh || !d_rowptr || !d_col || !d_vals || !sys_off || !d_b || !d_x || nsys < 1 || nrhs < 0 || nrhs > MR)
+            return set_error(NDHSS_ERR_INVALID_ARG, "ndhss_gmres_batched: bad argument (need nsys >= 1, 0 <= nrhs <= 32)");
+        const FactorData& F = fh->f;
+        if (ldb < F.n || ldx < F.n) return set_error(NDHSS_ERR_INVALID_ARG, "ndhss_gmres_batched: leading dimension < n");
+        if (sys_off[0] != 0 || sys_off[nsys] != F.n)
+            return set_error(NDHSS_ERR_INVALID_ARG, "ndhss_gmres_batched: sys_off must run from 0 to n");
+        for (int s = 0; s < nsys; ++s)
+            if (sys_off[s + 1] < sys_off[s]) return set_error(NDHSS_ERR_INVALID_ARG, "ndhss_gmres_batched: sys_off decreases");
+        if (!is_device_ptr(d_b) || !is_device_ptr(d_x))
+            return set_error(NDHSS_ERR_INVALID_ARG, "ndhss_gmres_batched: b and x must be device pointers");
+        ndhss_gmres_opts o{30, 300, 1e-8, 0, 0, 0.1, -1.0};
+        if (opts) o = *opts;
+        if (o.restart < 1 || o.restart > BK - 1 || o.maxit < 0 || !(o.tol >= 0) || !(o.inner > 0 && o.inner <= 1))
+            return set_error(NDHSS_ERR_INVALID_ARG, "ndhss_gmres_batched: need 1 <= restart <= %d, maxit >= 0, tol >= 0, 0 < inner <= 1",
+                             BK - 1);
+        if (o.conj_transpose != 0)
+            return set_error(NDHSS_ERR_INVALID_ARG, "ndhss_gmres_batched: conj_transpose is not supported (use ndhss_gmres)");
+        if (nrhs == 0) return NDHSS_OK;
+        ndhss_status rc = multi_supported(F, "ndhss_gmres_batched");
+        if (rc != NDHSS_OK) return rc;
+        if (o.cycle_rtol < 0) o.cycle_rtol = (F.prec == NDHSS_FP64) ? 0.0 : 1e-3;
+        cudaStream_t st = static_cast<cudaStream_t>(stream);
+        if (F.vtype == NDHSS_R64)
+            rc = gmres_batched_run<double>(F, d_rowptr, d_col, (const double*)d_vals, nsys, sys_off, nrhs, (const double*)d_b,
+                                           ldb, (double*)d_x, ldx, o, stats, st);
+        else
+            rc = gmres_batched_run<c128>(F, d_rowptr, d_col, (const c128*)d_vals, nsys, sys_off, nrhs, (const c128*)d_b, ldb,
+                                         (c128*)d_x, ldx, o, stats, st);
+        if (rc == NDHSS_OK || rc == NDHSS_ERR_NOT_CONVERGED) {
+            const ndhss_status r2 = apply_check_error(F, "ndhss_gmres_batched");
+            if (r2 != NDHSS_OK) rc = r2;
+        }
+        return rc;
+    });
 }
 
 }  // extern "C"
