@@ -249,3 +249,30 @@ def test_sec33_p1_cross_couplings_have_at_most_one_entry_outside_the_facing_clus
             assert np.count_nonzero(At[out_c][:, cl.lo:cl.hi]) <= 1
             checked += 1
     assert checked >= 20
+
+
+def test_sec34_rank_bound_of_R(setup):
+    """Sec. 3.4: rank R = rank A_ib <= rank S_ib^mu + rank S_ib^nu + nnz A~_ib^(mu,nu)
+    + nnz A~_ib^(nu,mu), where the children's couplings S_ib are their HSS
+    root couplings U_1 B_12 U_2^T (rank <= the smaller basis width).  The
+    numerical rank of the dense R of the assembled front respects it."""
+    P, t, fac = setup
+    checked = 0
+    for s in _matfree_nodes(t, fac):
+        mi, mb = int(t.node_info[s, 5]), int(t.node_info[s, 7])
+        if mb == 0:
+            continue
+        F = _dense_front(P, t, fac, s)
+        R = np.linalg.solve(F[:mi, :mi], F[:mi, mi:])
+        sv = np.linalg.svd(R, compute_uv=False)
+        rank = int(np.sum(sv > 1e-10 * sv[0]))
+        front = mf.ImplicitFront(t, s, P.A, fac.hss)
+        bound = front.Sib.nnz
+        for part in front.parts:
+            cp = part.cp
+            if part.ni and part.pb.size:
+                bound += min(cp.D12.shape) if cp.D12 is not None else min(cp.B12.shape)
+        assert rank <= bound, (s, rank, bound)
+        assert rank < min(mi, mb) or bound >= min(mi, mb)
+        checked += 1
+    assert checked
