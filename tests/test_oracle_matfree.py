@@ -276,3 +276,24 @@ def test_sec34_rank_bound_of_R(setup):
         assert rank < min(mi, mb) or bound >= min(mi, mb)
         checked += 1
     assert checked
+
+
+def test_matfree_on_a_lattice_with_holes():
+    """Empty boxes (size-0 leaves), leaves above the switching level and
+    children without a Schur complement: the tier still reproduces the
+    direct solve at a tight tolerance."""
+    P = poisson_dirichlet(32, p=1, seed=0)
+    keep = np.nonzero((P.coords[:, 0] < 10) | (P.coords[:, 0] > 20) | (P.coords[:, 1] < 12))[0]
+    A = P.A[keep][:, keep].tocsr()
+    A.sort_indices()
+    coords = P.coords[keep]
+    b = np.asarray(P.b if P.b.ndim == 1 else P.b[:, 0])[keep]
+    t = build_tree(coords, A.indptr, A.indices, 20)
+    assert np.any(t.f("m_i") + t.f("m_b") == 0)
+    fac = mf.factor_matfree(t, A, hss_levels=1, eps=1e-11, beta=8)
+    lev = t.node_info[:, 0]
+    assert fac.binv
+    assert any(not t.children(s) and lev[s] < fac.L_hss for s in range(t.nnodes))   # a leaf above L_HSS
+    x = spla.spsolve(A.tocsc(), b)
+    y = mf.apply_matfree(fac, b)
+    assert np.linalg.norm(y - x) <= 1e-7 * np.linalg.norm(x)
