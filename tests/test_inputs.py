@@ -62,3 +62,51 @@ def test_helmholtz_c2_shape():
     # the source is a Gaussian of width 0.02 inside [0.1, 0.9]^2
     xs = P.meta["sources"][0]
     assert np.all((xs >= 0.1) & (xs <= 0.9))
+
+
+def test_macro_generator_quadratic_forms_pin_the_coefficients():
+    """helmholtz_macro on rectangular cells with wave speed piecewise constant
+    on macro blocks (the batched workload's generator), pinned by exact
+    quadratic forms: 1^T A 1 = -w^2 int c^-2 - i w int_{boundary} c^-1, and for
+    the interpolant of u = x (exact in P1) u^T A u = int |grad x|^2 -
+    w^2 int x^2 c^-2 - i w int_{boundary} x^2 c^-1, cell by cell."""
+    from ndhss_inputs.fem import helmholtz_macro
+    rng = np.random.default_rng(0)
+    Nx, Ny, mb = 24, 17, 4
+    cb = rng.uniform(1.0, 3.0, (mb, mb))
+    P = helmholtz_macro(Nx, Ny, cb, nsrc=2)
+    w, xy, A = P.meta["omega"], P.meta["xy"], P.A
+    assert abs(w - 2 * np.pi / (10.0 / min(Nx, Ny))) <= 1e-12 * w        # 10 points per wavelength at c = 1
+    hx, hy = 1.0 / Nx, 1.0 / Ny
+    ia = np.arange(Nx)[:, None]
+    ib = np.arange(Ny)[None, :]
+    c = cb[ia * mb // Nx, ib * mb // Ny]                                  # [Nx, Ny] per cell
+    one = np.ones(A.shape[0])
+    mass = (hx * hy / c ** 2).sum()
+    bnd = (hx / c[:, 0]).sum() + (hx / c[:, -1]).sum() + (hy / c[0, :]).sum() + (hy / c[-1, :]).sum()
+    ref = -w * w * mass - 1j * w * bnd
+    assert abs(one @ (A @ one) - ref) <= 1e-10 * abs(ref)
+    u = xy[:, 0].astype(np.complex128)
+    x2 = ((np.arange(Nx) + 1.0) ** 3 - np.arange(Nx) ** 3) * hx ** 3 / 3.0     # int x^2 over each cell column
+    vol = (x2[:, None] * hy / c ** 2).sum()
+    bnd2 = (x2 / c[:, 0]).sum() + (x2 / c[:, -1]).sum() + (hy / c[-1, :]).sum()   # x = 0 on the left side
+    ref2 = 1.0 - w * w * vol - 1j * w * bnd2
+    assert abs(u @ (A @ u) - ref2) <= 1e-9 * abs(ref2)
+    assert abs(A - A.T).max() <= 1e-12 * abs(A).max()
+    assert P.b.shape == (A.shape[0], 2)
+
+
+def test_batch_generator_recipe():
+    from ndhss_inputs.fem import helmholtz_batch
+    probs = helmholtz_batch(6, seed=3, nsrc=4)
+    again = helmholtz_batch(6, seed=3, nsrc=4)
+    for P, Q in zip(probs, again):
+        Nx, Ny = P.meta["Nx"], P.meta["Ny"]
+        assert 64 <= Nx <= 256 and 64 <= Ny <= 256
+        cb = P.meta["c_blocks"]
+        assert cb.shape == (8, 8) and cb.min() >= 1.0 and cb.max() <= 3.0
+        assert P.A.shape[0] == (Nx + 1) * (Ny + 1) and P.b.shape == (P.A.shape[0], 4)
+        src = P.meta["sources"]
+        assert src.min() >= 0.1 and src.max() <= 0.9
+        assert (P.A != Q.A).nnz == 0 and np.array_equal(P.b, Q.b)      # seeded
+    assert len({(P.meta["Nx"], P.meta["Ny"]) for P in probs}) > 1     # uneven sizes
