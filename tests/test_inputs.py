@@ -110,3 +110,22 @@ def test_batch_generator_recipe():
         assert src.min() >= 0.1 and src.max() <= 0.9
         assert (P.A != Q.A).nnz == 0 and np.array_equal(P.b, Q.b)      # seeded
     assert len({(P.meta["Nx"], P.meta["Ny"]) for P in probs}) > 1     # uneven sizes
+
+
+def test_block_slowness_generator_quadratic_form():
+    """helmholtz_blocks (the adjoint workload's generator): squared slowness m
+    piecewise constant on nb x nb blocks enters as -k^2 m in the mass term and
+    -i k sqrt(m) on the boundary: 1^T A 1 = -k^2 int m - i k int_{boundary} sqrt(m)."""
+    from ndhss_inputs.fem import helmholtz_blocks
+    rng = np.random.default_rng(1)
+    N, nb, k = 20, 4, 7.0
+    m = rng.uniform(0.3, 1.0, (nb, nb))
+    P = helmholtz_blocks(N, k, m)
+    A = P.A
+    h = 1.0 / N
+    ia = np.arange(N)
+    mc = m[ia[:, None] * nb // N, ia[None, :] * nb // N]                 # per cell (a, b)
+    one = np.ones(A.shape[0])
+    ref = -k * k * (h * h * mc).sum() - 1j * k * h * (np.sqrt(mc[:, 0]).sum() + np.sqrt(mc[:, -1]).sum()
+                                                       + np.sqrt(mc[0, :]).sum() + np.sqrt(mc[-1, :]).sum())
+    assert abs(one @ (A @ one) - ref) <= 1e-10 * abs(ref)
