@@ -1,5 +1,6 @@
 """Oracle: HSS matrices, randomized adaptive compression (Alg. A.1) and the
-compressed factorization of Alg. 3.4 ("form S densely and compress").
+compressed factorization of Alg. 3.4 in its dense-then-compress variant
+(every Schur complement eliminated densely, then compressed).
 
 TEST INFRASTRUCTURE ONLY (see ``oracle/__init__.py``).
 

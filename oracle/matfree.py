@@ -39,7 +39,7 @@ Readings (where the paper is silent or inconsistent):
   dense-then-compress tier), S~ stream 3 nnodes + s.
 * Nodes on levels >= L_HSS, and leaves on any level, are formed and
   eliminated densely (the lower branch of Alg. 3.4); a node on level L_HSS
-  also compresses its dense S (Alg. 3.4, "form S densely and compress").
+  also compresses its dense S (the switching-level branch of Alg. 3.4).
 """
 from __future__ import annotations
 

@@ -2,7 +2,7 @@
 //
 //   gather/cast   y = x(perm) converted to the factor precision
 //   up-sweep      levels bottom-up:  y(B^s) += L^s y(I^s)          (L = -BL P)
-//   diagonal      all nodes:         z(I^s) = A_ii^{-1} y(I^s)     ("fully in parallel")
+//   diagonal      all nodes:         z(I^s) = A_ii^{-1} y(I^s)     (independent across nodes)
 //   down-sweep    levels top-down:   z(I^s) += R^s z(B^s)
 //   scatter/cast  out(perm) = z converted back to float64, by whichever task
 //                 writes a row's final value
