@@ -89,6 +89,32 @@ def test_well_separated_siblings(prob_tree):
             assert not set(T.B(ch[0]).tolist()) & set(T.B(ch[1]).tolist())
 
 
+def test_subtrees_of_a_level_touch_disjoint_unknowns(prob_tree):
+    """B^s lies in box s (R4), so the nodes of one subtree read and write only
+    their own interior unknowns and the subtree root's B: the subtrees of a
+    level own disjoint unknowns, and a subtree's work needs nothing from its
+    siblings (the up and down sweeps of Alg. 3.1 can run a whole subtree
+    without waiting on another)."""
+    P, T = prob_tree
+    lev = T.f("level")
+
+    def nodes(s):
+        out = [s]
+        for k in T.children(s):
+            out += nodes(k)
+        return out
+
+    for L0 in range(1, T.depth + 1):
+        owner = np.full(P.n, -1)
+        for r in np.nonzero(lev == L0)[0]:
+            sub = nodes(int(r))
+            own = np.concatenate([T.I(s) for s in sub])
+            touched = np.unique(np.concatenate([own] + [T.B(s) for s in sub]))
+            assert np.all(owner[touched] == -1)
+            owner[touched] = r
+            assert set(touched.tolist()) - set(own.tolist()) <= set(T.B(int(r)).tolist())
+
+
 def test_every_entry_enters_one_front(prob_tree):
     """Each A(i, j) is scattered once, inside its front, at the LCA of its leaves."""
     P, T = prob_tree
