@@ -58,7 +58,7 @@ ELASTIC = dict(N=512, seed=0, leaf=60, beta=60, tol=1e-6, hss_levels=4)
 # ncu DRAM traffic of the dominant kernel class, per launch, keyed by the
 # sha256 of the source file it was measured on (null once the source changes)
 NCU_TRAFFIC = {
-    # profiles/apply_dataflow_helmholtz_p2_256_mixed.md: dram read 549.5 MB + write 11.1 MB per launch
+    # dram read 549.5 MB + write 11.1 MB per launch
     ("apply", "ade3e45fff1ddfca"): 560.6e6,
 }
 

@@ -286,25 +286,33 @@ ndhss_status ndhss_apply(const ndhss_factorization* f, int32_t nrhs, const void*
 /*
  * ndhss_apply_noalloc -- the result of ndhss_apply for one right-hand side,
  * from a call that allocates no memory at all.  For callers that cannot
- * allocate at the moment they need P^{-1}: code recording a CUDA graph that
- * must hold no memory nodes, host callbacks, or runtimes whose allocator may
- * not be entered from the calling thread.  The paper has no counterpart; this
- * is an interface convenience.
+ * allocate device memory at the moment they need P^{-1}: a solver loop in a
+ * process whose device memory is reserved up front by another allocator (a
+ * framework's caching allocator, a fixed memory budget), or code under a
+ * no-allocation-after-setup rule, where an allocation could fail or stall.
+ * The paper has no counterpart; this is an interface convenience.
  *   f          factor from ndhss_factor
  *   d_x, d_y   DEVICE pointers, n float64/complex128 values (original
  *              numbering); host pointers are rejected with INVALID_ARG
  *   stream     stream the kernels are ordered on
- * The work area (two vectors of n elements of the factor's type, one slot per
- * rank component of every low-rank node for each sweep, and 4 + 5 x nodes
- * 32-bit control words) lives in one static device array of 16 MiB that every
- * GPU loading the library holds until the process exits; problems needing
- * more (about n > 520000 for complex128 fronts, n > 1000000 for complex64 or
- * float64 fronts) get INVALID_ARG.
+ * The work area (two vectors of n elements of the factor's type, the
+ * low-rank nodes' partial products for each sweep, the diagonal partial
+ * products, and 32-bit control words: 4 + 6 per tree node + 2 per ULV
+ * record) lives in one static device array of 16 MiB that every GPU loading
+ * the library holds until the process exits; problems needing more (about
+ * n > 520000 for complex128 fronts, n > 1000000 for complex64 or float64
+ * fronts, less with compressed factors) get INVALID_ARG.
  * The first call on a device looks up that array's device address (once per
- * device, with that device current): make that first call before any stream
- * capture.  All calls share the array and each overwrites it completely
- * before reading it, so nothing needs clearing; calls that overlap on the
- * GPU (other streams, other threads) race on it and must be serialised.
+ * device, with that device current, and again if the device's context was
+ * replaced, e.g. after a device reset): make that first call before any
+ * stream capture.  All calls share the array and each overwrites what it
+ * reads before reading it, so nothing needs clearing; calls that overlap on
+ * the GPU (other streams, other threads) race on it and must be serialised.
+ * The call never synchronises: if a bounded wait of the apply kernel gives
+ * up inside it, y is undefined, the call has already returned NDHSS_OK, and
+ * the factorization's error mark surfaces at the next synchronising call on
+ * it (ndhss_gmres, or ndhss_apply with a host buffer), which returns
+ * NDHSS_ERR_TIMEOUT.
  */
 ndhss_status ndhss_apply_noalloc(const ndhss_factorization* f, const void* d_x, void* d_y, void* stream);
 

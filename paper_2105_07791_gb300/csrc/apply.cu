@@ -39,6 +39,7 @@
 #include <cstring>
 #include <mutex>
 
+#include "driver.h"
 #include "factor.cuh"
 
 namespace ndhss {
@@ -1365,15 +1366,20 @@ extern "C" ndhss_status ndhss_apply(const ndhss_factorization* fh, int32_t nrhs,
 // --------------------------------------------------------------------------
 // Allocation-free apply (no counterpart in the paper).
 //
-// Callers that must not allocate (graph recording without memory nodes, host
-// callbacks, foreign allocators) get the same Alg. 3.1 result with the two
-// work vectors in this fixed static array instead of stream-ordered
-// allocations.  The array is part of the module image, so every device that
-// loads the library holds it until exit.  Host code must not take its address
-// directly (that would be a host-side shadow): the device address is looked
-// up once per device with cudaGetSymbolAddress.  Every call writes the work
-// area before reading it (the gather all of the first vector, the diagonal
-// step all of the second, an asynchronous memset the queue's control words),
+// Some callers cannot allocate device memory at the moment they need P^{-1}:
+// a solver loop in a process whose device memory is reserved up front by
+// another allocator (a framework's caching allocator, a fixed budget), or
+// code under a no-allocation-after-setup rule, where an allocation can fail
+// or stall.  They get the same Alg. 3.1 result with the work area in this
+// fixed static array instead of stream-ordered allocations.  The array is
+// part of the module image, so every device that loads the library holds it
+// until exit.  Host code must not take its address directly (that would be a
+// host-side shadow): the device address is looked up once per device with
+// cudaGetSymbolAddress, and again if the device's context was replaced (a
+// device reset reloads the module, possibly at another address).  Every call
+// writes the work area before reading it (the gather all of the first
+// vector, the diagonal step all of the second, the low-rank tasks their
+// partial-product slots, an asynchronous memset the queue's control words),
 // so nothing needs clearing between calls; overlapping calls race on the
 // array.
 namespace ndhss {
@@ -1384,7 +1390,11 @@ __device__ __align__(256) unsigned char g_apply_scratch[NOALLOC_SCRATCH_BYTES];
 
 constexpr int NOALLOC_MAX_DEVICES = 64;
 std::mutex g_scratch_mu;
-void* g_scratch_addr[NOALLOC_MAX_DEVICES] = {};
+struct ScratchAddr {
+    unsigned long long ctx_id = 0;       // context the address was looked up in
+    void* addr = nullptr;
+};
+ScratchAddr g_scratch_addr[NOALLOC_MAX_DEVICES];
 
 ndhss_status scratch_for_current_device(void** out) {
     int dev = -1;
@@ -1392,16 +1402,29 @@ ndhss_status scratch_for_current_device(void** out) {
     if (dev < 0 || dev >= NOALLOC_MAX_DEVICES)
         return set_error(NDHSS_ERR_INVALID_ARG, "ndhss_apply_noalloc: device %d beyond the supported %d", dev,
                          NOALLOC_MAX_DEVICES);
+    // cudaGetSymbolAddress also makes the device's primary context current
+    // if no context was, so the id is read after it on a first lookup
     std::lock_guard<std::mutex> lock(g_scratch_mu);
-    if (!g_scratch_addr[dev]) {
-        void* p = nullptr;
-        const cudaError_t e = cudaGetSymbolAddress(&p, g_apply_scratch);
-        if (e != cudaSuccess || !p)
-            return set_error(NDHSS_ERR_CUDA, "ndhss_apply_noalloc: cudaGetSymbolAddress of the scratch array failed: %s",
-                             cudaGetErrorString(e));
-        g_scratch_addr[dev] = p;
+    ScratchAddr& a = g_scratch_addr[dev];
+    unsigned long long id = 0;
+    if (a.addr) {
+        const ndhss_status rc = drv_current_ctx_id(&id);
+        if (rc != NDHSS_OK) return rc;
+        if (id == a.ctx_id) {
+            *out = a.addr;
+            return NDHSS_OK;
+        }
     }
-    *out = g_scratch_addr[dev];
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_apply_scratch);
+    if (e != cudaSuccess || !p)
+        return set_error(NDHSS_ERR_CUDA, "ndhss_apply_noalloc: cudaGetSymbolAddress of the scratch array failed: %s",
+                         cudaGetErrorString(e));
+    const ndhss_status rc = drv_current_ctx_id(&id);
+    if (rc != NDHSS_OK) return rc;
+    a.addr = p;
+    a.ctx_id = id;
+    *out = p;
     return NDHSS_OK;
 }
 

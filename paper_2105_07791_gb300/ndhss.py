@@ -260,13 +260,39 @@ def ndhss_factor_get_block(f: Factor, node: int, which: int, m_i: int, m_b: int)
     return out[:, :rows].T.copy()
 
 
+def _check_vector(f: Factor, v, name: str, device_only: bool = False):
+    """Refuse a buffer the C side would read or write out of bounds: it must
+    hold exactly f.n contiguous values of the factor's value type
+    (float64 / complex128), on the device where the call needs one."""
+    want = "complex128" if f.vtype == NDHSS_C128 else "float64"
+    if hasattr(v, "data_ptr"):
+        if device_only and not v.is_cuda:
+            raise ValueError(f"{name} must be a CUDA tensor")
+        if not v.is_contiguous():
+            raise ValueError(f"{name} must be contiguous")
+        dt = str(v.dtype).replace("torch.", "")
+        size = v.numel()
+    else:
+        if device_only:
+            raise ValueError(f"{name} must be a CUDA tensor")
+        if not (v.flags["C_CONTIGUOUS"] or v.flags["F_CONTIGUOUS"]):
+            raise ValueError(f"{name} must be contiguous")
+        dt = str(v.dtype)
+        size = v.size
+    if dt != want:
+        raise ValueError(f"{name} has dtype {dt}; this factor takes {want}")
+    if size != f.n:
+        raise ValueError(f"{name} has {size} values; this factor takes n = {f.n}")
+
+
 def ndhss_apply(f: Factor, x, y, stream=None):
-    """y = P^{-1} x.  x, y: (n,) or (n, nrhs) column-major data (torch CUDA or numpy)."""
+    """y = P^{-1} x.  x, y: (n,) vectors (torch CUDA or numpy) of the factor's value type."""
     n = f.n
-    nrhs = 1 if x.ndim == 1 else x.shape[1]
     if x.ndim == 2:
         raise ValueError("pass one right-hand side per call, or several as rows of a block via ndhss_apply_block")
-    _check(load().ndhss_apply(f.handle, nrhs, _ptr(x), n, _ptr(y), n, _stream(stream)))
+    _check_vector(f, x, "x")
+    _check_vector(f, y, "y")
+    _check(load().ndhss_apply(f.handle, 1, _ptr(x), n, _ptr(y), n, _stream(stream)))
     return y
 
 
@@ -282,6 +308,8 @@ def ndhss_apply_block(f: Factor, X, Y, stream=None):
 
 def ndhss_apply_noalloc(f: Factor, d_x, d_y, stream=None):
     """y = P^{-1} x without any allocation (device tensors of n values; see include/ndhss.h)."""
+    _check_vector(f, d_x, "d_x", device_only=True)
+    _check_vector(f, d_y, "d_y", device_only=True)
     _check(load().ndhss_apply_noalloc(f.handle, _ptr(d_x), _ptr(d_y), _stream(stream)))
     return d_y
 

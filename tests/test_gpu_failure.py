@@ -52,3 +52,23 @@ def test_stalled_apply_times_out_and_context_survives(nd):
     nd.ndhss_apply(g, b, y2)
     r = P.A @ y2 - b
     assert np.linalg.norm(r) <= 1e-10 * np.linalg.norm(b)
+
+
+def test_noalloc_apply_timeout_surfaces_at_the_next_synchronising_call(nd):
+    # the allocation-free apply never synchronises: a wait that gives up inside
+    # it marks the factorization, and the next synchronising call reports it
+    P = poisson_dirichlet(24)
+    tree = nd.ndhss_build_tree(P.coords, P.A.indptr, P.A.indices, 64)
+    M = nd.DeviceCSR(P.A)
+    f = nd.ndhss_factor(tree, M.vtype, M.rowptr, M.col, M.vals, nd.make_factor_opts(prec=0))
+    xd = torch.from_numpy(np.ascontiguousarray(P.b, dtype=np.float64)).cuda()
+    yd = torch.empty_like(xd)
+    nd.ndhss_testing_stall_apply(f)
+    t0 = time.time()
+    nd.ndhss_apply_noalloc(f, xd, yd)            # returns OK: nothing waited on yet
+    torch.cuda.synchronize()
+    assert time.time() - t0 < 30
+    b = np.ascontiguousarray(P.b, dtype=np.float64)
+    with pytest.raises(nd.NdhssError) as e:
+        nd.ndhss_apply(f, b, np.zeros_like(b))   # host buffers: this call synchronises
+    assert e.value.code == 6
