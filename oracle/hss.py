@@ -540,7 +540,8 @@ def ulv_order(tree, s: int) -> np.ndarray:
 
 
 def factor_compressed(tree, A, hss_levels: int = 4, eps: float = 1e-6, beta: int = 64, k0: int = 32,
-                      r: int = 16, seed: int = 0, rank_cap: int = 512, ulv: bool = False) -> CompressedFactor:
+                      r: int = 16, seed: int = 0, rank_cap: int = 512, ulv: bool = False,
+                      subtree: int | None = None) -> CompressedFactor:
     """Alg. 3.4 with every front formed densely (the matrix-free upper tier of
     Sec. 3.5 is not used): nodes on levels <= L_HSS = depth - hss_levels
     compress their Schur complement by Alg. A.1 with the parent-conforming
@@ -551,13 +552,27 @@ def factor_compressed(tree, A, hss_levels: int = 4, eps: float = 1e-6, beta: int
     A_ii of the nodes strictly above the switching level is compressed too
     (Alg. A.1, top split [F(mu); F(nu)], Philox stream 2 nnodes + s) and its
     ULV factorization replaces the dense LU in the diagonal step of the
-    apply; otherwise A_ii is factored densely everywhere."""
+    apply; otherwise A_ii is factored densely everywhere.  With subtree = s0
+    only the nodes of the subtree rooted at s0 are factored (a front depends
+    on its own subtree only, and post-order numbers a subtree as the
+    contiguous range ending at s0); the entries of the other nodes are None."""
     from .frontal import assemble_front, factor_node
     depth = tree.depth
     Lh = depth - hss_levels
     fac = CompressedFactor(tree=tree, dtype=A.dtype, L_hss=Lh)
     S_keep = {}
-    for s in range(tree.nnodes):
+    first = 0
+    if subtree is not None:
+        first = subtree
+        while True:                                  # lowest post-order number in the subtree
+            ch = tree.children(first)
+            if not ch:
+                break
+            first = min(ch)
+        for lst in (fac.lu, fac.R, fac.L, fac.S, fac.S_exact):
+            lst.extend([None] * first)
+    last = tree.nnodes if subtree is None else subtree + 1
+    for s in range(first, last):
         F = assemble_front(tree, s, A, S_keep)
         m_i, m_b = int(tree.node_info[s, 5]), int(tree.node_info[s, 7])
         lu, L, R, S = factor_node(F, m_i)
@@ -587,6 +602,8 @@ def factor_compressed(tree, A, hss_levels: int = 4, eps: float = 1e-6, beta: int
         fac.R.append(R)
         fac.L.append(L)
         fac.S.append(S)
+    for lst in (fac.lu, fac.R, fac.L, fac.S, fac.S_exact):
+        lst.extend([None] * (tree.nnodes - last))
     return fac
 
 

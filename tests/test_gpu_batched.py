@@ -19,6 +19,7 @@ from ndhss_inputs import helmholtz_batch, poisson_dirichlet
 from oracle.frontal import apply_inverse, factor_dense
 from oracle.gmres import gmres as oracle_gmres
 from oracle.tree import build_tree
+from closeness import rel as _rel
 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
@@ -52,11 +53,6 @@ def _factor(nd, tree, M, prec, hss_levels=-1):
     f = nd.ndhss_factor(tree, M.vtype, M.rowptr, M.col, M.vals, nd.make_factor_opts(prec=prec, hss_levels=hss_levels))
     torch.cuda.synchronize()
     return f
-
-
-def _rel(a, b):
-    nb = np.linalg.norm(b)
-    return np.linalg.norm(a - b) / (nb if nb > 0 else 1.0)
 
 
 def _rand(n, k, seed, cplx=True):

@@ -13,6 +13,7 @@ from oracle.frontal import apply_inverse, factor_dense
 from oracle.gmres import gmres as oracle_gmres
 from oracle.hss import apply_compressed, factor_compressed
 from oracle.tree import build_tree
+from closeness import rel as _rel
 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
@@ -45,10 +46,6 @@ def _factor(nd, el, prec, hl):
     f = nd.ndhss_factor(el["tree"], M.vtype, M.rowptr, M.col, M.vals, opts)
     torch.cuda.synchronize()
     return f
-
-
-def _rel(a, b):
-    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
 
 
 @pytest.mark.parametrize("prec,hl,tol", [(0, -1, 1e-10), (1, -1, 2e-3), (0, HL, 1e-4), (1, HL, 1e-3)])

@@ -20,6 +20,7 @@ from ndhss_inputs import helmholtz_impedance
 from oracle.frontal import assemble_front, factor_node
 from oracle.hss import cluster_tree, hss_compress, hss_dense
 from oracle.tree import build_tree
+from closeness import rel as _rel
 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
@@ -54,10 +55,6 @@ def _factor(nd, c, prec):
     M = c["M"]
     opts = nd.make_factor_opts(prec=prec, hss_levels=HL, eps_hss=EPS, beta=BETA, k0=32, r=16, seed=SEED)
     return nd.ndhss_factor(c["tree"], M.vtype, M.rowptr, M.col, M.vals, opts)
-
-
-def _rel(a, b):
-    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
 
 
 def dense_refs(T, A, s):
@@ -155,3 +152,44 @@ def test_fullsize_fp64_sampled_fronts_switching_level_and_solve(nd, c2):
         exact += e <= 1e-9
     assert exact >= 2
     _solve_and_check(nd, c2, f)
+
+
+def test_fullsize_mixed_compressed_subtree_matches_oracle(nd, c2):
+    """The benchmark's configuration above the switching level: for a seeded
+    level-7 node, the oracle factors that node's subtree alone (Alg. 3.4 with
+    Alg. A.1 on the same Philox streams, low-rank R strictly above the
+    switching level) and every compressed S and low-rank R of the subtree is
+    compared with the GPU's FP32 factor of the whole problem.  Both sides
+    compress to eps = 1e-6 relative, the GPU from FP32 Schur complements and
+    with FP32 sampling (rounding floor ~6e-5 relative on a block's
+    estimator), so they agree to the apply-level tolerance of a compressed
+    FP32 factor, 1e-3 (normwise and entrywise)."""
+    from oracle.hss import factor_compressed
+    P, T = c2["P"], c2["T"]
+    f = _factor(nd, c2, nd.NDHSS_FP32)
+    lev, mi_all, mb_all = T.f("level"), T.f("m_i"), T.f("m_b")
+    Lh = T.depth - HL
+    rng = np.random.default_rng(7)
+    cand = np.nonzero((lev == Lh - 2) & (mi_all > 0) & (mb_all > 0))[0]
+    s0 = int(rng.choice(cand))
+    fac = factor_compressed(T, P.A, hss_levels=HL, eps=EPS, beta=BETA, k0=32, r=16, seed=SEED, subtree=s0)
+    checked_s = checked_r = 0
+    worst = 0.0
+    for s in range(T.nnodes):
+        if fac.S[s] is None or lev[s] > Lh or mb_all[s] == 0:
+            continue
+        mi, mb = int(mi_all[s]), int(mb_all[s])
+        Sg = nd.ndhss_factor_get_block(f, s, 3, mi, mb)
+        e = _rel(Sg, fac.S[s])
+        worst = max(worst, e)
+        assert e <= 1e-3, (s, int(lev[s]), "S", e)
+        checked_s += 1
+        if lev[s] < Lh and mi > 0:
+            Rg = nd.ndhss_factor_get_block(f, s, 1, mi, mb)
+            Ro = fac.R[s].matmat(np.eye(mb))
+            e = _rel(Rg, Ro)
+            worst = max(worst, e)
+            assert e <= 1e-3, (s, int(lev[s]), "R", e)
+            checked_r += 1
+    assert checked_s >= 7 and checked_r >= 3, (checked_s, checked_r)
+    print(f"compressed subtree of node {s0}: {checked_s} S and {checked_r} R blocks, worst difference {worst:.2e}")

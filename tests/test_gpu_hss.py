@@ -15,6 +15,7 @@ from ndhss_inputs import helmholtz_impedance, poisson_dirichlet
 from oracle.gmres import gmres as oracle_gmres
 from oracle.hss import apply_compressed, factor_compressed
 from oracle.tree import build_tree
+from closeness import rel as _rel
 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
@@ -52,10 +53,6 @@ def _factor(nd, c, prec):
     M = c["M"]
     opts = nd.make_factor_opts(prec=prec, hss_levels=c["hl"], eps_hss=EPS, beta=64, k0=32, r=16, seed=11)
     return nd.ndhss_factor(c["tree"], M.vtype, M.rowptr, M.col, M.vals, opts)
-
-
-def _rel(a, b):
-    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
 
 
 def test_compressed_blocks_match_oracle_fp64(nd, case):

@@ -16,6 +16,7 @@ from ndhss_inputs import helmholtz_impedance, poisson_dirichlet
 from oracle.frontal import apply_inverse, factor_dense
 from oracle.gmres import gmres as oracle_gmres
 from oracle.tree import build_tree
+from closeness import rel as _rel
 
 pytestmark = pytest.mark.gpu
 
@@ -55,11 +56,6 @@ def _gpu_factor(nd, c, prec, panel=0):
     f = nd.ndhss_factor(c["tree"], M.vtype, M.rowptr, M.col, M.vals, nd.make_factor_opts(prec=prec, panel=panel))
     torch.cuda.synchronize()
     return f
-
-
-def _rel(a, b):
-    nb = np.linalg.norm(b)
-    return np.linalg.norm(a - b) / (nb if nb > 0 else 1.0)
 
 
 @pytest.mark.parametrize("prec,tol", [(0, 1e-9), (1, 2e-3), (2, 5e-2)])

@@ -220,3 +220,31 @@ def test_stopping_rule_keeps_sampling_a_slowly_decaying_spectrum():
     assert _stop(STAGNATION_FLOOR / 2, 1.0, 1e-20, STAGNATION_FLOOR / 1.5, 64, 500, 16)
     assert _stop(1e-3, 1.0, 1e-6, 1.0, MAX_SAMPLES - 8, 500, 16)
     assert not _stop(1e-3, 1.0, 1e-6, 1.0, MAX_SAMPLES - 16, 500, 16)
+
+
+def test_factor_compressed_subtree_equals_full_factorization_on_that_subtree():
+    """A front depends only on its own subtree: factoring one subtree alone
+    gives bit for bit the blocks the full factorization gives there."""
+    from ndhss_inputs import helmholtz_impedance
+    from oracle.hss import factor_compressed
+    from oracle.tree import build_tree
+    P = helmholtz_impedance(40, 1, 10.0, seed=3)
+    T = build_tree(P.coords, P.A.indptr, P.A.indices, 32)
+    full = factor_compressed(T, P.A, hss_levels=3, eps=1e-6, beta=32, k0=16, r=8, seed=4)
+    lev = T.f("level")
+    s0 = int(np.nonzero(lev == 1)[0][0])
+    sub = factor_compressed(T, P.A, hss_levels=3, eps=1e-6, beta=32, k0=16, r=8, seed=4, subtree=s0)
+    inside = [s for s in range(T.nnodes) if sub.S[s] is not None]
+    def members(s):
+        return [s] + [d for c in T.children(s) for d in members(c)]
+    assert sorted(inside) == sorted(members(s0))
+    assert all(sub.S[s] is None for s in range(T.nnodes) if s not in inside)
+    lowrank = 0
+    for s in inside:
+        assert np.array_equal(sub.S[s], full.S[s])
+        if hasattr(full.R[s], "matmat"):
+            assert np.array_equal(sub.R[s].X, full.R[s].X) and np.array_equal(sub.R[s].RJ, full.R[s].RJ)
+            lowrank += 1
+        else:
+            assert np.array_equal(sub.R[s], full.R[s])
+    assert lowrank > 0
