@@ -1,6 +1,8 @@
 #!/usr/bin/env python
 """Benchmark: solves/s and factor time at relative residual 1e-8, mixed
-(complex64 fronts, FP32 arithmetic) vs FP64 (complex128 fronts) GPU path.
+(complex64 fronts; the large fronts' block exchanges on the TF32 tensor cores
+with two parts per operand, FP32-accurate; the rest FP32) vs FP64
+(complex128 fronts) GPU path.
 
 Workload: 2D Helmholtz -lap u - k^2 u = f on [0,1]^2, P2 continuous Galerkin
 on a 256 x 256 cell grid (n = 263169, nnz = 3018753), k = 40, first-order
@@ -16,10 +18,11 @@ both.  Inputs stay resident in HBM; the factor (>= 0.7 GB) exceeds the 129 MB
 L2, so every apply streams it from HBM.
 
 Side lines of the same JSON line: ``fp64`` (the comparator), ``ulv``,
-``tf32`` and ``bf16`` (other factor variants of the same workload),
+``tf32`` (one TF32 part per operand) and ``bf16`` (three BF16 parts per
+operand) (other factor variants of the same workload),
 ``batched`` (64 independent Helmholtz problems x 32 right-hand sides solved
 in lockstep; ``--batch-count 0`` skips it) and ``elastic`` (P1 SIPG elastic
-waves on 512 x 512 cells, dense, compressed and BF16 fronts; ``--elastic-N 0``
+waves on 512 x 512 cells, dense, compressed and split-BF16 fronts; ``--elastic-N 0``
 skips it).
 
 ``--impl reference`` times the FP64 CPU oracle (the only other place this
@@ -155,6 +158,17 @@ def _peaks():
         return pk, "measured"
     except OSError:
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def _dense_alg_flops(tree):
+    """Algorithmic real flops of the dense elimination of every front (the
+    LU-based count of the hot-path table: LU of A_ii, the two triangular
+    solves for R and L, the Schur product; x4 for complex arithmetic)."""
+    import numpy as np
+    from paper_2105_07791_gb300 import ndhss
+    ni = ndhss.ndhss_tree_export(tree)["node_info"]
+    mi, mb = ni[:, 5].astype(float), ni[:, 7].astype(float)
+    return float(4.0 * np.sum(2.0 / 3.0 * mi ** 3 + 2.0 * mi ** 2 * mb + 2.0 * mi * mb ** 2))
 
 
 def _src_sha(name):
@@ -335,16 +349,23 @@ def run_gpu(a):
             "solve_share": ap_ms / mx["solve_ms"] if mx["solve_ms"] > 0 else None}
     # the factorization's dominant class, for the factor-time half of the metric
     dom = max(cls_ms, key=cls_ms.get)
-    nl = max(fs["class_launches"][dom], 1)
     froof = {"class": dom, "ms_per_factor": cls_ms[dom], "launches": fs["class_launches"][dom],
              "share_of_factor": cls_ms[dom] / mx["factor_ms"] if mx["factor_ms"] > 0 else None}
-    if dom == "update":
-        # FP32 SIMT FMA peak: 152 SMs x 128 lanes x 2 flop x max SM clock
-        peak = 152 * 128 * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
-        achf = fs["update_flops"] / (cls_ms[dom] / 1e3) / 1e12
-        froof.update(bound="alu", achieved=achf, peak=peak, unit="TFLOP/s", frac=achf / peak)
-    else:
-        froof.update(bound="latency (many small dependent launches)")
+    # TF32 dense tensor peak: the measured BF16 burst times the nominal TF32 /
+    # BF16 ratio (1.1 / 2.25 PFLOP/s); a product split into two TF32 parts takes
+    # three MMAs, so FP32-accurate products run at a third of it
+    tf32_peak = pk["bf16_tflops"] * 1.1 / 2.25
+    dense_ms = sum(cls_ms.get(k, 0.0) for k in ("panel", "prep", "update", "finalize", "tensor"))
+    alg = _dense_alg_flops(tree)
+    froof["dense_elimination"] = {
+        "bound": "tensor", "unit": "TFLOP/s", "algorithmic_flops": alg, "ms_per_factor": dense_ms,
+        "achieved": alg / (dense_ms / 1e3) / 1e12 if dense_ms > 0 else None, "peak": tf32_peak / 3,
+        "peak_kind": f"TF32 dense ({pk_kind} bf16 x 1.1/2.25) / 3 (two-part split: three MMAs per product)",
+        "algorithmic": "LU-based count per complex front: 8/3 m_i^3 + 8 m_i^2 m_b + 8 m_i m_b^2"}
+    if froof["dense_elimination"]["achieved"]:
+        froof["dense_elimination"]["frac"] = froof["dense_elimination"]["achieved"] / (tf32_peak / 3)
+    if dom == "compress":
+        froof.update(bound="latency (per-round row-ID pivot chains of the HSS levels, one dependent launch each)")
     # the other hot kernels against the bound that limits them: ALU peaks
     # derived from unit counts and the maximum SM clock (FP32 SIMT: 152 SMs x
     # 128 lanes x 2 flops; FP64: GB300's nominal 1.25 TFLOP/s), HBM measured
@@ -359,10 +380,16 @@ def run_gpu(a):
          "achieved": 8.0 * P.A.nnz / (sp_one / 1e3) / 1e12 if sp_one > 0 else None, "peak": fp64_peak,
          "peak_kind": "nominal FP64", "algorithmic": "8 flops per complex entry (real entries take 4)",
          "avg_launch_ms": sp_one},
-        {"kernel": "gemm_update_kernel (FP32 SIMT front update)", "bound": "alu", "unit": "TFLOP/s",
+        {"kernel": "gemm_update_kernel (FP32 SIMT rank-kb exchange steps: small fronts, slabs of the large ones)",
+         "bound": "alu", "unit": "TFLOP/s",
          "achieved": fs["update_flops"] / (cls_ms["update"] / 1e3) / 1e12 if cls_ms.get("update") else None,
          "peak": fp32_peak, "peak_kind": "derived: 152 SMs x 128 FP32 lanes x 2 x max SM clock",
-         "algorithmic": "8 m^2 kb flops per front and panel"},
+         "algorithmic": "8 m x (columns exchanged) x kb flops per front and panel"},
+        {"kernel": "tc_gemm_kernel (tcgen05 + TMA rank-128 block exchanges, two TF32 parts per operand; class "
+                   "time includes the operand packing)", "bound": "tensor", "unit": "TFLOP/s",
+         "achieved": fs["tc_flops"] / (cls_ms["tensor"] / 1e3) / 1e12 if cls_ms.get("tensor") else None,
+         "peak": tf32_peak / 3, "peak_kind": f"TF32 dense ({pk_kind} bf16 x 1.1/2.25) / 3 MMAs per product",
+         "algorithmic": "8 m (m - w) w flops per front and outer block of w pivots"},
     ]
     for k in krl:
         if k.get("achieved") is not None and k.get("peak"):

@@ -53,10 +53,13 @@ typedef enum { NDHSS_R64 = 0, NDHSS_C128 = 1 } ndhss_vtype;
  * true residual are always float64 (complex128). */
 typedef enum {
     NDHSS_FP64 = 0,      /* fronts in float64 / complex128, FP64 arithmetic           */
-    NDHSS_FP32 = 1,      /* fronts in float32 / complex64, FP32 arithmetic            */
-    NDHSS_FP32_TF32 = 2, /* as FP32, front updates on TF32 tensor cores, FP32 accum.  */
-    NDHSS_FP32_BF16 = 3  /* as FP32, front updates with BF16 operands on the tensor
-                            cores (tcgen05 kind::f16), FP32 accumulation             */
+    NDHSS_FP32 = 1,      /* fronts in float32 / complex64; R, L, S of the larger fronts
+                            on the TF32 tensor cores with each operand split in two
+                            rounded TF32 parts (hi*hi + hi*lo + lo*hi, FP32
+                            accumulation: FP32-accurate products); the rest FP32  */
+    NDHSS_FP32_TF32 = 2, /* as FP32 with one rounded TF32 part per operand          */
+    NDHSS_FP32_BF16 = 3  /* as FP32 with two rounded BF16 parts per operand
+                            (tcgen05 kind::f16, FP32 accumulation, ~16 bits)         */
 } ndhss_prec;
 
 typedef struct ndhss_tree ndhss_tree;
@@ -129,10 +132,14 @@ typedef struct {
     int64_t launches;           /* kernels launched by the last ndhss_factor           */
     /* per kernel class (only when opts.timing = 1): summed device ms and launches;
        classes 0 assemble, 1 scatter, 2 panel, 3 prep, 4 update, 5 finalize,
-       6 compression (S by Alg. A.1, R by a randomized row ID)                          */
+       6 compression (S by Alg. A.1, R by a randomized row ID), 7 tensor-core
+       products R, L, S of the larger fronts (operand packing and tcgen05 GEMMs)     */
     double class_ms[8];
     int64_t class_launches[8];
-    double update_flops;        /* algorithmic real flops of the front updates         */
+    double update_flops;        /* real flops of the Gauss-Jordan rank-kb updates      */
+    double tc_flops;            /* real flops of the tensor-core products R, L, S
+                                   (8 per complex multiply-add), counted once per
+                                   product whatever the operand split              */
 } ndhss_factor_stats;
 
 /* Library version string (static storage). */

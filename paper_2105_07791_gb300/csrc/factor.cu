@@ -24,9 +24,6 @@
 #include <cmath>
 
 #include "factor.cuh"
-#include <cuda_bf16.h>
-
-#include "tcgen05.cuh"
 
 namespace ndhss {
 namespace {
@@ -259,7 +256,7 @@ __global__ void __launch_bounds__(PREP_WARPS * 32)
 panel_prep_kernel(const int32_t* __restrict__ lev, const int32_t* __restrict__ node,
                   const int64_t* __restrict__ foff, T* __restrict__ front, const int32_t* __restrict__ swapmap,
                   const T* __restrict__ ainv_buf, T* __restrict__ cbuf, T* __restrict__ zbuf,
-                  const int64_t* __restrict__ woff, int k0, int kb) {
+                  const int64_t* __restrict__ woff, int k0, int kb, int slab0, int slabw) {
     __shared__ T s_ai[KBMAX * KBMAX];
     __shared__ int s_rows[2 * KBMAX], s_org[2 * KBMAX];
     const int li = blockIdx.y;
@@ -267,6 +264,10 @@ panel_prep_kernel(const int32_t* __restrict__ lev, const int32_t* __restrict__ n
     const int m_i = nf(node, s, 5);
     if (k0 >= m_i) return;
     const int64_t m = m_i + nf(node, s, 7);
+    // columns that take part in this pivot block's exchange: the whole front,
+    // or (two-level blocking) the slab [slab0, slab0 + slabw) of the outer
+    // block; the interchanges go to every column
+    const int64_t zlo = slabw ? slab0 : 0, zhi = slabw ? min((int64_t)slab0 + slabw, (int64_t)m_i) : m;
     const int kbp = min(kb, m_i - k0);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const T* Ai = ainv_buf + (size_t)li * KBMAX * KBMAX;
@@ -290,6 +291,7 @@ panel_prep_kernel(const int32_t* __restrict__ lev, const int32_t* __restrict__ n
         if (lane < na) Fj[s_rows[lane]] = v0;
         if (lane + 32 < na) Fj[s_rows[lane + 32]] = v1;
         __syncwarp();
+        if (j < zlo || j >= zhi) continue;
         if (j >= k0 && j < k0 + kbp) {
             const int cidx = (int)(j - k0);
             // the whole pivot column: eight rows per lane loaded before they are
@@ -324,7 +326,7 @@ template <typename T>
 __global__ void __launch_bounds__(256)
 gemm_update_kernel(const int32_t* __restrict__ lev, const int32_t* __restrict__ node,
                    const int64_t* __restrict__ foff, T* __restrict__ front, const T* __restrict__ cbuf,
-                   const T* __restrict__ zbuf, const int64_t* __restrict__ woff, int k0, int kb) {
+                   const T* __restrict__ zbuf, const int64_t* __restrict__ woff, int k0, int kb, int slab0, int slabw) {
     __shared__ T sC[GK][GT];
     __shared__ T sZ[GK][GT];
     const int li = blockIdx.z;
@@ -332,8 +334,10 @@ gemm_update_kernel(const int32_t* __restrict__ lev, const int32_t* __restrict__ 
     const int m_i = nf(node, s, 5);
     if (k0 >= m_i) return;
     const int64_t m = m_i + nf(node, s, 7);
-    const int64_t i0 = (int64_t)blockIdx.x * GT, j0 = (int64_t)blockIdx.y * GT;
-    if (i0 >= m || j0 >= m) return;
+    // columns [zlo, zhi): the whole front, or the slab of the outer block
+    const int64_t zlo = slabw ? slab0 : 0, zhi = slabw ? min((int64_t)slab0 + slabw, (int64_t)m_i) : m;
+    const int64_t i0 = (int64_t)blockIdx.x * GT, j0 = zlo + (int64_t)blockIdx.y * GT;
+    if (i0 >= m || j0 >= zhi) return;
     const int kbp = min(kb, m_i - k0);
     const T* C = cbuf + woff[li] * KBMAX;
     const T* Z = zbuf + woff[li] * KBMAX;
@@ -353,7 +357,7 @@ gemm_update_kernel(const int32_t* __restrict__ lev, const int32_t* __restrict__ 
         for (int idx = tid; idx < GK * GT; idx += 256) {
             const int l = idx % GK, jj = idx / GK;
             const int64_t j = j0 + jj;
-            sZ[l][jj] = (kc + l < kbp && j < m) ? Z[j * KBMAX + kc + l] : zero<T>();
+            sZ[l][jj] = (kc + l < kbp && j < zhi) ? Z[j * KBMAX + kc + l] : zero<T>();
         }
         __syncthreads();
 #pragma unroll
@@ -373,7 +377,7 @@ gemm_update_kernel(const int32_t* __restrict__ lev, const int32_t* __restrict__ 
 #pragma unroll
     for (int b = 0; b < 4; ++b) {
         const int64_t j = j0 + ty + 16 * b;
-        if (j >= m) continue;
+        if (j >= zhi) continue;
         const bool pj = (j >= k0 && j < k0 + kbp);
 #pragma unroll
         for (int a = 0; a < 4; ++a) {
@@ -383,170 +387,6 @@ gemm_update_kernel(const int32_t* __restrict__ lev, const int32_t* __restrict__ 
             T* dst = F + j * m + i;
             *dst = (pi || pj) ? acc[a][b] : (*dst + acc[a][b]);
         }
-    }
-}
-
-// The same update on the TF32 tensor cores (precision NDHSS_FP32_TF32): one
-// CTA of 128 threads per 128 x 128 tile of the real GEMM
-//   complex:  [Re; Im](C Z) = [[Cr, -Ci], [Ci, Cr]] [Zr; Zi]   (rows interleaved:
-//             real row 2 r / 2 r + 1 = Re / Im of front row r, K = 2 kb)
-//   real:     C Z                                              (K = kb)
-// K padded with zeros to a multiple of 8.  A (rows) and B (front columns) are
-// staged K-major in shared memory, kb / 8 kind::tf32 MMAs accumulate in
-// TMEM (FP32), and each thread reads its TMEM lane back for the epilogue
-// M = beta .* M + C Z.  The completion wait is bounded (status TIMEOUT).
-// BF = true (precision NDHSS_FP32_BF16): the operands rounded to BF16,
-// K padded to a multiple of 16, kind::f16 MMAs with BF16 A and B.
-constexpr int TC_COLS = 128;
-constexpr int TC_MAX_WAIT = 1 << 24;
-
-template <typename T, bool BF>
-__global__ void __launch_bounds__(128)
-tc_update_kernel(const int32_t* __restrict__ lev, const int32_t* __restrict__ node, const int64_t* __restrict__ foff,
-                 T* __restrict__ front, const T* __restrict__ cbuf, const T* __restrict__ zbuf,
-                 const int64_t* __restrict__ woff, int k0, int kb, DevStatus* status) {
-    if constexpr (sizeof(typename Tr<T>::real) != 4) {
-        return;                                         // TF32 / BF16 apply to the FP32 types only
-    } else {
-    constexpr bool CPLX = Tr<T>::cplx;
-    constexpr int RT = CPLX ? 64 : 128;                 // front rows per tile
-    constexpr int ESZ = BF ? 2 : 4, KAL = BF ? 16 : 8, KMMA = BF ? 16 : 8;
-    extern __shared__ __align__(1024) unsigned char tsm[];
-    __shared__ __align__(8) uint64_t mbar;
-    __shared__ uint32_t tmem_holder;
-    const int li = blockIdx.z;
-    const int s = lev[li];
-    const int m_i = nf(node, s, 5);
-    if (k0 >= m_i) return;
-    const int64_t m = m_i + nf(node, s, 7);
-    const int64_t i0 = (int64_t)blockIdx.x * RT, j0 = (int64_t)blockIdx.y * TC_COLS;
-    if (i0 >= m || j0 >= m) return;
-    const int kbp = min(kb, m_i - k0);
-    const int KP = ((CPLX ? 2 * kbp : kbp) + KAL - 1) & ~(KAL - 1);
-    const T* C = cbuf + woff[li] * KBMAX;
-    const T* Z = zbuf + woff[li] * KBMAX;
-    T* F = front + foff[s];
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    unsigned char* sA = tsm;
-    unsigned char* sB = tsm + 128 * KP * ESZ;
-    // operands rounded to nearest (the tensor core would otherwise drop the
-    // low mantissa bits of an FP32 operand: a biased truncation to TF32)
-    auto put = [&](unsigned char* base, int r, int kk, float v) {
-        if constexpr (BF) *reinterpret_cast<__nv_bfloat16*>(base + tc::core_off16(r, kk, KP)) = __float2bfloat16_rn(v);
-        else *reinterpret_cast<uint32_t*>(base + tc::core_off(r, kk, KP)) = tc::to_tf32_rn(v);
-    };
-    if (tid == 0) tc::mbar_init(&mbar, 1);
-    if (warp == 0) tc::tmem_alloc(&tmem_holder, TC_COLS);
-    // staging: eight independent loads per thread in flight before the stores
-    // (one load at a time leaves the kernel waiting on global latency)
-    constexpr int SU = 8;
-    for (int q0 = tid; q0 < 128 * KP; q0 += 128 * SU) {
-        float v[SU];
-#pragma unroll
-        for (int u = 0; u < SU; ++u) {
-            const int q = q0 + u * 128;
-            const int rr = q & 127, kk = q >> 7;
-            v[u] = 0.0f;
-            if (q < 128 * KP) {
-                if constexpr (CPLX) {
-                    const int64_t r = i0 + (rr >> 1);
-                    if (r < m && kk < 2 * kbp) {
-                        const T c = C[(int64_t)(kk < kbp ? kk : kk - kbp) * m + r];
-                        v[u] = (rr & 1) ? (kk < kbp ? c.y : c.x) : (kk < kbp ? c.x : -c.y);
-                    }
-                } else {
-                    const int64_t r = i0 + rr;
-                    if (r < m && kk < kbp) v[u] = C[(int64_t)kk * m + r];
-                }
-            }
-        }
-#pragma unroll
-        for (int u = 0; u < SU; ++u) {
-            const int q = q0 + u * 128;
-            if (q < 128 * KP) put(sA, q & 127, q >> 7, v[u]);
-        }
-    }
-    for (int q0 = tid; q0 < 128 * KP; q0 += 128 * SU) {
-        float v[SU];
-#pragma unroll
-        for (int u = 0; u < SU; ++u) {
-            const int q = q0 + u * 128;
-            const int kk = q % KP, nn = q / KP;
-            const int64_t n = j0 + nn;
-            v[u] = 0.0f;
-            if (q < 128 * KP) {
-                if constexpr (CPLX) {
-                    if (n < m && kk < 2 * kbp) {
-                        const T z = Z[n * KBMAX + (kk < kbp ? kk : kk - kbp)];
-                        v[u] = kk < kbp ? z.x : z.y;
-                    }
-                } else {
-                    if (n < m && kk < kbp) v[u] = Z[n * KBMAX + kk];
-                }
-            }
-        }
-#pragma unroll
-        for (int u = 0; u < SU; ++u) {
-            const int q = q0 + u * 128;
-            if (q < 128 * KP) put(sB, q / KP, q % KP, v[u]);
-        }
-    }
-    tc::fence_smem_async();
-    tc::fence_before();
-    __syncthreads();
-    tc::fence_after();
-    const uint32_t tmem = tmem_holder;
-    if (tid == 0) {
-        // 16 bytes of K per core matrix: 4 TF32 or 8 BF16 elements; one MMA takes two
-        const uint32_t sbo = (uint32_t)(KP * ESZ / 16) * 128u;
-        for (int ks = 0; ks < KP / KMMA; ++ks) {
-            const uint64_t ad = tc::smem_desc(tc::smem_u32(sA) + ks * 256u, 128u, sbo);
-            const uint64_t bd = tc::smem_desc(tc::smem_u32(sB) + ks * 256u, 128u, sbo);
-            if constexpr (BF) tc::mma_f16(tmem, ad, bd, tc::idesc_bf16(128, TC_COLS), ks > 0 ? 1u : 0u);
-            else tc::mma_tf32(tmem, ad, bd, tc::idesc_tf32(128, TC_COLS), ks > 0 ? 1u : 0u);
-        }
-        tc::commit(&mbar);
-    }
-    if (!tc::mbar_wait(&mbar, 0, TC_MAX_WAIT)) {
-        if (tid == 0 && atomicCAS(&status->code, 0, (int)NDHSS_ERR_TIMEOUT) == 0) status->node = nf(node, s, 0);
-    } else {
-        tc::fence_after();
-        const int row = warp * 32 + lane;                  // TMEM lane = row of the real GEMM
-        const int64_t r = CPLX ? i0 + (row >> 1) : i0 + row;
-        const bool pi = r >= k0 && r < k0 + kbp;
-        // per group of 8 columns: the lane's destination values are loaded
-        // first (independent loads in flight), then its TMEM columns, then
-        // combined and stored (a load after each store would serialise them)
-        constexpr int NW = CPLX ? 4 : 8;                   // columns a lane writes per group
-        for (int c0 = 0; c0 < TC_COLS; c0 += 8) {
-            T old[NW];
-#pragma unroll
-            for (int h = 0; h < NW; ++h) {
-                const int u = CPLX ? 2 * h + (lane & 1) : h;          // complex: even lanes even columns
-                const int64_t n = j0 + c0 + u;
-                const bool pj = n >= k0 && n < k0 + kbp;
-                old[h] = (r < m && n < m && !(pi || pj)) ? F[n * m + r] : zero<T>();
-            }
-            float v[8];
-            tc::tmem_ld8(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
-#pragma unroll
-            for (int u = 0; u < 8; ++u) {
-                const int64_t n = j0 + c0 + u;
-                if constexpr (CPLX) {
-                    const float other = __shfl_xor_sync(0xffffffffu, v[u], 1);
-                    if ((u & 1) != (lane & 1) || r >= m || n >= m) continue;
-                    const T d = (lane & 1) ? T{other, v[u]} : T{v[u], other};
-                    F[n * m + r] = old[u >> 1] + d;            // old = 0 on pivot rows / columns
-                } else {
-                    if (r >= m || n >= m) continue;
-                    F[n * m + r] = old[u] + v[u];
-                }
-            }
-        }
-    }
-    tc::fence_before();
-    __syncthreads();
-    if (warp == 0) tc::tmem_dealloc(tmem, TC_COLS);
     }
 }
 
@@ -584,10 +424,6 @@ ndhss_status set_smem_attrs() {
                                      panel_factor_kernel<T, 8>, panel_factor_kernel<T, 16>, panel_factor_kernel<T, 32>};
     for (auto k : kernels)
         NDHSS_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PANEL_SMEM_MAX));
-    NDHSS_CUDA_TRY(cudaFuncSetAttribute(tc_update_kernel<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        2 * 128 * 2 * KBMAX * 4));
-    NDHSS_CUDA_TRY(cudaFuncSetAttribute(tc_update_kernel<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        2 * 128 * 2 * KBMAX * 4));
     return NDHSS_OK;
 }
 
@@ -721,10 +557,22 @@ ndhss_status factor_run(FactorData& F, const Tree& t, const V* d_vals, const int
                 cudaFreeAsync(d_jobs, st);
             }
         }
+        // Two-level blocking on the tensor cores (tcgemm.cu) for levels with
+        // large fronts: the pivots go in outer blocks of TC_KB2 columns; inside
+        // one, the rank-kb steps exchange only the block's own columns (its
+        // slab), then one GEMM with K = TC_KB2 applies the block's exchange to
+        // every other column of the front.  The arithmetic is the sweep's own
+        // (a block of exchanges composed), so S stays the elimination's Schur
+        // complement.  Small fronts keep the rank-kb steps over the whole front.
+        const bool tcl = tc_front_path(F, mimax);
+        const int kb2 = tcl ? TC_KB2 : 0;
         const int gt = (int)((mmax + GT - 1) / GT);
+        const int gty = tcl ? (TC_KB2 + GT - 1) / GT : gt;
         const int pgx = (int)std::min<int64_t>((mmax + PREP_WARPS - 1) / PREP_WARPS, 1024);
         for (int64_t k0 = 0; k0 < mimax;) {
-            const int kb = choose_kb(mimax - k0, sizeof(T), panel_opt);
+            const int64_t s0 = tcl ? k0 / TC_KB2 * TC_KB2 : 0;     // the outer block's first pivot
+            int kb = choose_kb(mimax - k0, sizeof(T), panel_opt);
+            while (tcl && k0 + kb > s0 + TC_KB2) kb >>= 1;
             const size_t smem = (size_t)(mimax - k0) * kb * sizeof(T) + (size_t)(mimax - k0) * sizeof(int);
             if (smem > PANEL_SMEM_MAX)
                 return set_error(NDHSS_ERR_INVALID_ARG, "front with %lld interior unknowns exceeds the panel kernel's shared memory",
@@ -754,35 +602,32 @@ ndhss_status factor_run(FactorData& F, const Tree& t, const V* d_vals, const int
                 tm.begin();
                 panel_prep_kernel<T><<<dim3(pgx, Lc), PREP_WARPS * 32, 0, st>>>(levc, F.d_node, F.d_foff, front,
                                                                                d_swapmap, d_ainv, d_cbuf, d_zbuf, woffc,
-                                                                               (int)k0, kb);
+                                                                               (int)k0, kb, (int)s0, kb2);
                 NDHSS_LAUNCH_CHECK("panel_prep_kernel");
                 tm.end(3);
                 tm.begin();
-                if ((F.prec == NDHSS_FP32_TF32 || F.prec == NDHSS_FP32_BF16) && sizeof(typename Tr<T>::real) == 4) {
-                    const int rt = Tr<T>::cplx ? 64 : 128;
-                    // staged operands sized as for TF32 (BF16 uses half of it)
-                    const int kp = ((Tr<T>::cplx ? 2 * kb : kb) + 15) & ~15;
-                    const dim3 grid((unsigned)((mmax + rt - 1) / rt), (unsigned)((mmax + TC_COLS - 1) / TC_COLS), Lc);
-                    if (F.prec == NDHSS_FP32_BF16)
-                        tc_update_kernel<T, true><<<grid, 128, (size_t)2 * 128 * kp * 4, st>>>(
-                            levc, F.d_node, F.d_foff, front, d_cbuf, d_zbuf, woffc, (int)k0, kb, d_status);
-                    else
-                        tc_update_kernel<T, false><<<grid, 128, (size_t)2 * 128 * kp * 4, st>>>(
-                            levc, F.d_node, F.d_foff, front, d_cbuf, d_zbuf, woffc, (int)k0, kb, d_status);
-                    NDHSS_LAUNCH_CHECK("tc_update_kernel");
-                } else {
-                    gemm_update_kernel<T><<<dim3(gt, gt, Lc), 256, 0, st>>>(levc, F.d_node, F.d_foff, front, d_cbuf,
-                                                                          d_zbuf, woffc, (int)k0, kb);
-                    NDHSS_LAUNCH_CHECK("gemm_update_kernel");
-                }
+                gemm_update_kernel<T><<<dim3(gt, gty, Lc), 256, 0, st>>>(levc, F.d_node, F.d_foff, front, d_cbuf,
+                                                                       d_zbuf, woffc, (int)k0, kb, (int)s0, kb2);
+                NDHSS_LAUNCH_CHECK("gemm_update_kernel");
                 tm.end(4);
             }
             F.launches += 3;
             for (int s2 : nodes) {
                 const int64_t mi = F.m_i(s2), m2 = mi + F.m_b(s2);
-                if (mi > k0) F.update_flops += flops_per_mac * (double)m2 * (double)m2 * (double)std::min<int64_t>(kb, mi - k0);
+                const int64_t cols = tcl ? std::min<int64_t>(TC_KB2, mi - s0) : m2;
+                if (mi > k0) F.update_flops += flops_per_mac * (double)m2 * (double)cols * (double)std::min<int64_t>(kb, mi - k0);
             }
             k0 += kb;
+            if (tcl && (k0 == s0 + TC_KB2 || k0 >= mimax)) {
+                // the outer block's exchange on the columns outside its slab
+                tm.begin();
+                const ndhss_status rc2 = tc_block_exchange(F, nodes, (int)s0, d_status, st);
+                if (rc2 != NDHSS_OK) {
+                    if (d_aii) cudaFreeAsync(d_aii, st);
+                    return rc2;
+                }
+                tm.end(7);
+            }
         }
         if (mimax > 0) {
             tm.begin();
@@ -1198,6 +1043,7 @@ ndhss_status ndhss_factor_stats_get(const ndhss_factorization* fh, ndhss_factor_
         st->class_launches[k] = F.class_launches[k];
     }
     st->update_flops = F.update_flops;
+    st->tc_flops = F.tc_flops;
     return NDHSS_OK;
 }
 

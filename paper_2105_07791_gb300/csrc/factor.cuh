@@ -108,6 +108,7 @@ struct FactorData {
     double class_ms[8] = {0};
     int64_t class_launches[8] = {0};
     double update_flops = 0.0;
+    double tc_flops = 0.0;                    // real flops of the tensor-core front products
     int64_t apply_bytes = 0;
     int64_t dev_bytes = 0;
 
@@ -132,6 +133,18 @@ ndhss_status hss_lowrank_pending(FactorData& F, const ndhss_factor_opts& o, cuda
 // `level` and ULV-factor them.  Defined in hss.cu.
 ndhss_status hss_ulv_level(FactorData& F, const Tree& t, int level, void* aii, const std::vector<int64_t>& aii_off,
                            const ndhss_factor_opts& o, cudaStream_t st);
+
+// Outer pivot block of the two-level Gauss-Jordan sweep on the tensor cores.
+constexpr int TC_KB2 = 128;
+// Whether a level whose largest interior block has mi_max unknowns takes the
+// two-level sweep with tensor-core block exchanges; tcgemm.cu.
+bool tc_front_path(const FactorData& F, int64_t mi_max);
+// The exchange of the outer pivot block starting at pivot k0 (its slab of
+// columns [k0, k0 + TC_KB2) already swept, the row interchanges applied to
+// every column) on every other column of the fronts of `nodes`, as one
+// tcgen05 GEMM with K = the block's width; tcgemm.cu.
+ndhss_status tc_block_exchange(FactorData& F, const std::vector<int>& nodes, int k0, DevStatus* d_status,
+                               cudaStream_t st);
 
 ndhss_status apply_device(const FactorData& F, int32_t nrhs, const void* d_x, int64_t ldx,
                           void* d_y, int64_t ldy, void* d_work, cudaStream_t st);

@@ -61,9 +61,10 @@ class FactorStats(C.Structure):
     _fields_ = [("n", C.c_int64), ("nnodes", C.c_int32), ("depth", C.c_int32), ("front_elems", C.c_int64),
                 ("apply_bytes", C.c_int64), ("factor_bytes", C.c_int64), ("factor_ms", C.c_double),
                 ("kmax", C.c_int32), ("prec", C.c_int32), ("launches", C.c_int64),
-                ("class_ms", C.c_double * 8), ("class_launches", C.c_int64 * 8), ("update_flops", C.c_double)]
+                ("class_ms", C.c_double * 8), ("class_launches", C.c_int64 * 8), ("update_flops", C.c_double),
+                ("tc_flops", C.c_double)]
 
-    CLASSES = ("assemble", "scatter", "panel", "prep", "update", "finalize", "compress")
+    CLASSES = ("assemble", "scatter", "panel", "prep", "update", "finalize", "compress", "tensor")
 
     def as_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_ if k not in ("class_ms", "class_launches")}
