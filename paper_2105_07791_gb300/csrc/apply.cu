@@ -20,6 +20,19 @@
 // entries, the gather indices of its vector), then waits, then stages the
 // vector and finishes: the wait overlaps the matrix traffic.
 //
+// The bottom levels [Ls, depth] (every node dense, small fronts) are not
+// split into per-node tasks: each subtree rooted on level Ls is one up task
+// and one down task.  The subtree's boxes hold its interior rows as one
+// contiguous range of the new numbering and every row its nodes touch lies
+// in that range or in B of the subtree root, so the task keeps that vector
+// segment in shared memory and takes the subtree's levels in turn, separated
+// by CTA barriers instead of cross-SM dependency hops: per level, every row
+// of every node of the level is one dot product (threads over rows, several
+// threads per row with a fixed-order reduction when rows are few).  The up
+// task writes z(I) of its nodes and adds its contributions to y(B^root); the
+// down task, once the root's parent is final, finishes z(I) of the subtree
+// and writes the output rows.
+//
 // Two schedules run the same queue:
 // * dataflow (default): ONE persistent launch.  A CTA takes the next ticket
 //   with one atomic (prefetched while the previous task runs), waits until
@@ -35,9 +48,11 @@
 // * levels: the queue cut into its dependency groups (one tree level and
 //   phase each), one launch per group; selected with
 //   NDHSS_APPLY_SCHEDULE=levels and kept as the bit-exact cross-check.
+#include <algorithm>
 #include <cstdlib>
 #include <cstring>
 #include <mutex>
+#include <unordered_map>
 
 #include "driver.h"
 #include "factor.cuh"
@@ -96,8 +111,15 @@ enum : int {
     TK_DNW,       // the same nodes coming down: z(I) += R z(B), final rows
     TK_HUP,       // ULV solve of HSS(A_ii), one HSS node going up (entry node = ULV record)
     TK_HROOT,     // the root block of a ULV front
-    TK_HDN        // one HSS node coming down (leaves write z(I) rows)
+    TK_HDN,       // one HSS node coming down (leaves write z(I) rows)
+    TK_SUBUP,     // a bottom subtree going up (diagonal steps and y(B) updates of all its nodes)
+    TK_SUBDN      // the same subtree coming down (z(I) += R z(B), output rows)
 };
+// Subtree tasks: limits of a subtree (nodes, levels, nodes per level) and
+// of its shared-memory vector segment (interior rows + B of the root) and
+// per-level staged inputs.
+constexpr int SUB_NODES = 256, SUB_LV = 16, SUB_LVN = 64, SUB_V = 1536, SUB_XIN = 1024;
+constexpr int SUB_MIN_ROOTS = 128;   // fewest subtrees worth the restructuring (GPU fill)
 // Tiny dense nodes (the bottom levels) are handled a warp per node, eight per
 // task: their blocks are a few KB, so one 64-row task per node would be all
 // latency.  Limits of a warp node (rows of the fused pass, interior rows,
@@ -125,6 +147,8 @@ struct ApplyCtx {
     const int32_t* wdesc;     // warp nodes, 8 ints each: node, m_i, m_b, i_off, b_off, front offset (lo, hi), 0
     const struct UlvDev* ulv; // ULV records (HSS nodes of the ULV fronts)
     const int32_t* ulv_ord;   // HSS order of each ULV front's I^s
+    const int64_t* foff;      // front offset of every node
+    const int32_t* sublist;   // per subtree: nl, level offsets [nl + 1], nodes (deepest level first)
 };
 
 // One HSS node of a ULV front on the device: sizes, links, its front, the
@@ -409,6 +433,149 @@ __device__ __forceinline__ void ulv_task(const ApplyCtx<T>& C, const Entry& e, c
     }
 }
 
+// ---- subtree tasks (TK_SUBUP / TK_SUBDN) ----------------------------------
+// Entry: s = subtree root, a = first interior row lo, b = interior rows nI,
+// m_b / b_off = the root's, aux = offset of the subtree's table, k = its
+// length.  The table (built on the host, copied to shared memory at the
+// start of the task, so no level waits on a dependent global load):
+//   header  nl, nodes
+//   level   nl records: count, first node, rows up, rows down, inputs up,
+//           inputs down (deepest level first)
+//   node    records: m_i, m_b, front offset (lo, hi), rows and inputs before
+//           it in its level (up: rows, inputs; down: rows, inputs), interior
+//           slot i_off - lo, B rows before it in its level
+//   slots   the vector slot of every staged input, level by level: up, y(I)
+//           in the order of A_ii^{-1}'s columns; down, z(B) (also the slot
+//           each up-sweep B row adds into)
+// vec holds [z or y rows lo .. lo + nI) | B^root slots | staged inputs | partials].
+constexpr int SUB_HDR = 2, SUB_LREC = 6, SUB_NREC = 10;
+
+template <typename T, typename V>
+__device__ void subtree_task(const ApplyCtx<T>& C, const Entry& e, int* idx, T* vec, const V* __restrict__ x,
+                             V* __restrict__ out, T* y, T* z) {
+    const bool up = e.kind == TK_SUBUP;
+    const int tid = threadIdx.x;
+    const int lo = e.a, nI = e.b, mbr = e.m_b;
+    const int tlen = e.k;
+    {
+        const int32_t* g = C.sublist + e.aux;
+        for (int i = tid; i < tlen; i += AT) idx[i] = g[i];
+    }
+    if (up) {
+        for (int i = tid; i < nI; i += AT) vec[i] = from_val<T>(x[C.perm[lo + i]]);
+        for (int j = tid; j < mbr; j += AT) vec[nI + j] = zero<T>();
+    } else {
+        for (int i = tid; i < nI; i += AT) vec[i] = ldw(z + lo + i);
+        for (int j = tid; j < mbr; j += AT) vec[nI + j] = ldw(z + C.blist[e.b_off + j]);
+    }
+    __syncthreads();
+    const int nl = idx[0], nn = idx[1];
+    const int* lrec = idx + SUB_HDR;
+    const int* nrec = lrec + SUB_LREC * nl;
+    const int* src_up = nrec + SUB_NREC * nn;
+    int n_src_up = 0, n_src_dn = 0;
+    for (int h = 0; h < nl; ++h) {
+        n_src_up += lrec[SUB_LREC * h + 4];
+        n_src_dn += lrec[SUB_LREC * h + 5];
+    }
+    const int* src_dn = src_up + n_src_up;
+    const int* dst_up = src_dn;           // an up-sweep B row adds into the slot its down input reads
+    if (up) {
+        // up inputs: (interior slot << 12 | column c) -> the slot of row sigma(c)
+        int* su = const_cast<int*>(src_up);
+        for (int q = tid; q < n_src_up; q += AT) {
+            const int v = su[q], sl = v >> 12;
+            su[q] = sl + C.sigma[lo + sl + (v & 4095)];
+        }
+        __syncthreads();
+    }
+    T* xin = vec + nI + mbr;
+    T* part = xin + SUB_XIN;
+    // first staged input / first up output of each level
+    int sx_up = 0, sx_dn = 0, so_up = 0;
+    if (!up)
+        for (int h = 0; h < nl; ++h) sx_dn += lrec[SUB_LREC * h + 5];
+    for (int hh = 0; hh < nl; ++hh) {
+        const int h = up ? hh : nl - 1 - hh;              // the table lists the deepest level first
+        const int* L = lrec + SUB_LREC * h;
+        const int cnt = L[0], n0 = L[1];
+        const int R = up ? L[2] : L[3];
+        const int nx = up ? L[4] : L[5];
+        if (!up) sx_dn -= nx;
+        const int* srcs = up ? src_up + sx_up : src_dn + sx_dn;
+        const int* N = nrec + SUB_NREC * n0;
+        // staged inputs (the previous level's results are in vec: barrier above)
+        for (int q = tid; q < nx; q += AT) xin[q] = vec[srcs[q]];
+        __syncthreads();
+        const int qp = R >= AT ? 1 : AT / R;               // threads per row
+        for (int ee = tid; ee < R * qp; ee += AT) {
+            const int row = ee % R, p = ee / R;
+            int j = 0;
+            while (j + 1 < cnt && row >= N[SUB_NREC * (j + 1) + (up ? 4 : 6)]) ++j;
+            const int* nd = N + SUB_NREC * j;
+            const int mi = nd[0], mb = nd[1];
+            const int r = row - nd[up ? 4 : 6];
+            const int64_t m = (int64_t)mi + mb;
+            const int64_t foff = (int64_t)(((uint64_t)(uint32_t)nd[3] << 32) | (uint32_t)nd[2]);
+            // up: row r of [A_ii^{-1} P^T ; -L P^T] (m rows, m_i columns);
+            // down: row r of R (m_i rows, m_b columns, at column m_i)
+            const T* A = C.front + foff + (up ? 0 : (int64_t)mi * m) + r;
+            const int cols = up ? mi : mb;
+            const T* xs = xin + nd[up ? 5 : 7];
+            T acc = zero<T>();
+            int c = p;
+            for (; c + 7 * qp < cols; c += 8 * qp) {
+                T a[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) a[u] = A[(int64_t)(c + u * qp) * m];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) acc = fmac(a[u], xs[c + u * qp], acc);
+            }
+            for (; c < cols; c += qp) acc = fmac(A[(int64_t)c * m], xs[c], acc);
+            if (qp > 1) {
+                part[ee] = acc;
+            } else if (up) {
+                if (r < mi) stw(z + lo + nd[8] + r, acc);
+                else vec[dst_up[so_up + nd[9] + r - mi]] -= acc;
+            } else {
+                vec[nd[8] + r] += acc;
+            }
+        }
+        if (qp > 1) {
+            __syncthreads();
+            for (int row = tid; row < R; row += AT) {
+                T acc = part[row];
+                for (int p = 1; p < qp; ++p) acc += part[p * R + row];
+                int j = 0;
+                while (j + 1 < cnt && row >= N[SUB_NREC * (j + 1) + (up ? 4 : 6)]) ++j;
+                const int* nd = N + SUB_NREC * j;
+                const int r = row - nd[up ? 4 : 6];
+                if (up) {
+                    if (r < nd[0]) stw(z + lo + nd[8] + r, acc);
+                    else vec[dst_up[so_up + nd[9] + r - nd[0]]] -= acc;
+                } else {
+                    vec[nd[8] + r] += acc;
+                }
+            }
+        }
+        if (up) {
+            sx_up += nx;
+            for (int j = 0; j < cnt; ++j) so_up += N[SUB_NREC * j + 1];
+        }
+        __syncthreads();
+    }
+    if (up) {
+        // the subtree's part of y(B^root) (the gather of those rows has finished:
+        // the task waited for it)
+        for (int j = tid; j < mbr; j += AT) {
+            const int g = C.blist[e.b_off + j];
+            stw(y + g, ldw(y + g) + vec[nI + j]);
+        }
+    } else {
+        for (int i = tid; i < nI; i += AT) out[C.perm[lo + i]] = to_val(vec[i]);
+    }
+}
+
 // Loads every task can issue before its dependencies are met: matrix
 // entries (read-only during the apply) and index lists.  idx: shared int
 // array of at least max(m_i, m_b, LR_CHUNK) entries.
@@ -423,6 +590,7 @@ __device__ __forceinline__ void task_pre(const ApplyCtx<T>& C, const Entry& e, P
         taskw_pre(C.wdesc, C.sigma, C.blist, e, idx, wd);
         return;
     }
+    if (e.kind == TK_SUBUP || e.kind == TK_SUBDN) return;
     if (e.kind == TK_HUP || e.kind == TK_HROOT || e.kind == TK_HDN) {
         if (e.b_off & 1) {                       // leaf: the rows of I^s it owns, in HSS order
             const UlvDev& R = C.ulv[e.s];
@@ -536,6 +704,10 @@ __device__ __forceinline__ void task_run(const ApplyCtx<T>& C, const Entry& e, c
     }
     if (e.kind == TK_HUP || e.kind == TK_HROOT || e.kind == TK_HDN) {
         ulv_task<T, V>(C, e, idx, vec, red, out, y, z, us);
+        return;
+    }
+    if (e.kind == TK_SUBUP || e.kind == TK_SUBDN) {
+        subtree_task<T, V>(C, e, const_cast<int*>(idx), vec, x, out, y, z);
         return;
     }
     const int m_i = e.m_i, m_b = e.m_b, i_off = e.i_off;
@@ -780,6 +952,17 @@ __device__ __forceinline__ Deps task_deps(const Sched& S, const int32_t* node, c
         d.need[0] = S.need[hd_index(S, e.i_off)];
         d.n = 1;
         break;
+    case TK_SUBUP:                                  // y(B^root) is added to after the gather
+        d.c[0] = S.ctl + 1;
+        d.need[0] = S.ngather;
+        d.n = 1;
+        break;
+    case TK_SUBDN: {                                // the root's parent final, the subtree's up done
+        const int p = nf(node, s, 1);
+        if (p >= 0) add(p, CN_FIN);
+        add(s, CN_UP);
+        break;
+    }
     default: break;
     }
     return d;
@@ -845,6 +1028,8 @@ __device__ __forceinline__ unsigned task_signals(const Entry& e) {
     case TK_DSUM: return (1u << CN_DIAG) | (e.fin ? (1u << CN_FIN) : 0u);
     case TK_DN: case TK_DNAXPY: case TK_FINNOP: return 1u << CN_FIN;
     case TK_DNDOT: return 1u << CN_DDOT;
+    case TK_SUBUP: return 1u << CN_UP;
+    case TK_SUBDN: return 1u << CN_FIN;
     default: return 0u;
     }
 }
@@ -946,7 +1131,7 @@ bool levels_schedule_requested() {
 template <typename T>
 ApplyCtx<T> make_ctx(const FactorData& F) {
     return ApplyCtx<T>{F.d_node, F.d_blist, F.d_sigma, F.d_perm, static_cast<const T*>(F.d_front), F.d_wdesc,
-                       reinterpret_cast<const UlvDev*>(F.d_ulvdev), F.d_ulv_ord};
+                       reinterpret_cast<const UlvDev*>(F.d_ulvdev), F.d_ulv_ord, F.d_foff, F.d_sublist};
 }
 
 // work space: y, z (n each), low-rank partials for each sweep, diagonal
@@ -1015,13 +1200,13 @@ ndhss_status apply_run(const FactorData& F, int32_t nrhs, const V* x, int64_t ld
 // Grid of the persistent launch: every SM filled to its occupancy limit.
 template <typename T, typename V>
 ndhss_status launch_shape(FactorData& F) {
+    // the opt-in limit also admits dynamic memory that, with the kernels'
+    // static shared memory, passes the default 48 KB
     const size_t smem = smem_bytes(F, sizeof(T));
-    if (smem > 48 * 1024) {
-        NDHSS_CUDA_TRY(cudaFuncSetAttribute(apply_dataflow_kernel<T, V>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                            (int)smem));
-        NDHSS_CUDA_TRY(cudaFuncSetAttribute(apply_group_kernel<T, V>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                            (int)smem));
-    }
+    NDHSS_CUDA_TRY(cudaFuncSetAttribute(apply_dataflow_kernel<T, V>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)smem));
+    NDHSS_CUDA_TRY(cudaFuncSetAttribute(apply_group_kernel<T, V>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)smem));
     int dev = 0, sms = 0, per_sm = 0;
     NDHSS_CUDA_TRY(cudaGetDevice(&dev));
     NDHSS_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
@@ -1073,8 +1258,124 @@ ndhss_status build_apply_schedule(FactorData& F, cudaStream_t st) {
     auto tiny = [&](int s) {
         return mode(s) == 0 && F.m_i(s) <= WN_MI && F.m_i(s) + F.m_b(s) <= WN_M && F.m_b(s) <= WREG;
     };
+    // bottom subtrees: the shallowest level Ls from which every node down to
+    // the leaves is dense with small fronts and every subtree fits one task
+    // (NDHSS_APPLY_SUBTREES=0 keeps per-node tasks everywhere)
+    auto ulv_node = [&](int s) { return !F.ulv_root_of.empty() && F.ulv_root_of[s] >= 0; };
+    std::vector<int32_t> sublist;
+    std::vector<int> sub_off(nn, -1), sub_lo(nn, 0), sub_ni(nn, 0), sub_len(nn, 0);   // per subtree root
+    int Ls = F.depth + 1;
+    {
+        const char* ev = std::getenv("NDHSS_APPLY_SUBTREES");
+        const bool enabled = !(ev && std::strcmp(ev, "0") == 0);
+        std::vector<int> first(nn), cntn(nn, 1), nlev(nn, 1);
+        std::vector<int64_t> ni(nn), mxin(nn, 0);
+        for (int s = 0; s < nn; ++s) {           // post-order: children before parents
+            const int c0 = F.info(s, 2), c1 = F.info(s, 3);
+            first[s] = c0 >= 0 ? first[c0] : s;
+            ni[s] = F.m_i(s) + (c0 >= 0 ? ni[c0] : 0) + (c1 >= 0 ? ni[c1] : 0);
+            cntn[s] = 1 + (c0 >= 0 ? cntn[c0] : 0) + (c1 >= 0 ? cntn[c1] : 0);
+            nlev[s] = 1 + std::max(c0 >= 0 ? nlev[c0] : 0, c1 >= 0 ? nlev[c1] : 0);
+        }
+        auto node_ok = [&](int s) {
+            return mode(s) == 0 && !ulv_node(s) && F.m_i(s) <= 2 * WN_MI && F.m_b(s) <= 4 * WREG;
+        };
+        // a subtree fits: nodes, levels, nodes and staged inputs per level, vector segment
+        auto root_ok = [&](int r) {
+            if (cntn[r] > SUB_NODES || nlev[r] > SUB_LV || ni[r] + F.m_b(r) > SUB_V) return false;
+            std::vector<int> per(nlev[r], 0), xu(nlev[r], 0), xd(nlev[r], 0);
+            const int l0 = F.info(r, 0);
+            for (int s = first[r]; s <= r; ++s) {
+                const int h = F.info(s, 0) - l0;
+                per[h]++;
+                xu[h] += F.m_i(s);
+                xd[h] += F.m_b(s);
+            }
+            for (int h = 0; h < nlev[r]; ++h)
+                if (per[h] > SUB_LVN || xu[h] > SUB_XIN || xd[h] > SUB_XIN) return false;
+            return true;
+        };
+        if (enabled && F.nnodes > 0) {
+            std::vector<char> deep_ok(F.depth + 2, 1);   // every node on levels >= l qualifies
+            for (int l = F.depth; l >= 0; --l) {
+                bool ok = deep_ok[l + 1];
+                for (int s : F.levels[l]) ok = ok && node_ok(s);
+                deep_ok[l] = ok;
+            }
+            for (int l = F.depth; l >= 0; --l) {
+                if (!deep_ok[l]) break;
+                bool ok = true;
+                for (int s : F.levels[l]) ok = ok && root_ok(s);
+                if (!ok) break;
+                Ls = l;
+            }
+            // enough subtrees to fill the GPU (deeper levels have more of them)
+            while (Ls <= F.depth && (int)F.levels[Ls].size() < SUB_MIN_ROOTS) ++Ls;
+        }
+        if (Ls <= F.depth) {
+            for (int r : F.levels[Ls]) {
+                const int lo = F.info(first[r], 4);
+                const int nI = (int)ni[r];
+                sub_lo[r] = lo;
+                sub_ni[r] = nI;
+                // the task's table (see subtree_task): levels deepest first,
+                // ascending ids within a level
+                const int off = (int)sublist.size();
+                const int nl = nlev[r], l0 = F.info(r, 0);
+                std::vector<std::vector<int>> bylev(nl);
+                for (int s = first[r]; s <= r; ++s) bylev[nl - 1 - (F.info(s, 0) - l0)].push_back(s);
+                std::unordered_map<int, int> broot;
+                for (int j = 0; j < F.m_b(r); ++j) broot[F.blist_h[F.info(r, 6) + j]] = nI + j;
+                auto bslot_of = [&](int s, int j) {
+                    const int g = F.blist_h[F.info(s, 6) + j];
+                    if (g >= lo && g < lo + nI) return g - lo;
+                    auto it = broot.find(g);
+                    return it == broot.end() ? -1 : it->second;
+                };
+                std::vector<int32_t> lrec, nrec, src_up, src_dn;
+                int nidx = 0;
+                for (int h = 0; h < nl; ++h) {
+                    int ru = 0, rd = 0, xu = 0, xd = 0, bo = 0;
+                    for (int s : bylev[h]) {
+                        const uint64_t fo = (uint64_t)F.foff[s];
+                        const int32_t nd[SUB_NREC] = {F.m_i(s), F.m_b(s), (int32_t)(uint32_t)fo, (int32_t)(uint32_t)(fo >> 32),
+                                                      ru, xu, rd, xd, F.info(s, 4) - lo, bo};
+                        nrec.insert(nrec.end(), nd, nd + SUB_NREC);
+                        // (interior slot << 12 | column): the task resolves the column
+                        // through sigma when it loads the table
+                        for (int c = 0; c < F.m_i(s); ++c) src_up.push_back(((F.info(s, 4) - lo) << 12) | c);
+                        for (int j = 0; j < F.m_b(s); ++j) {
+                            const int sl = bslot_of(s, j);
+                            if (sl < 0)
+                                return set_error(NDHSS_ERR_INTERNAL, "apply: a B row of node %d lies outside its subtree", s);
+                            src_dn.push_back(sl);
+                        }
+                        ru += F.m_i(s) + F.m_b(s);
+                        rd += F.m_i(s);
+                        xu += F.m_i(s);
+                        xd += F.m_b(s);
+                        bo += F.m_b(s);
+                    }
+                    const int32_t lr[SUB_LREC] = {(int32_t)bylev[h].size(), nidx, ru, rd, xu, xd};
+                    lrec.insert(lrec.end(), lr, lr + SUB_LREC);
+                    nidx += (int)bylev[h].size();
+                }
+                sublist.push_back(nl);
+                sublist.push_back(nidx);
+                sublist.insert(sublist.end(), lrec.begin(), lrec.end());
+                sublist.insert(sublist.end(), nrec.begin(), nrec.end());
+                sublist.insert(sublist.end(), src_up.begin(), src_up.end());
+                sublist.insert(sublist.end(), src_dn.begin(), src_dn.end());
+                sub_off[r] = off;
+                sub_len[r] = (int)sublist.size() - off;
+                F.sched_vlen = std::max(F.sched_vlen, sub_len[r]);
+                F.sched_vlen = std::max(F.sched_vlen, (int)(nI + F.m_b(r) + SUB_XIN + AT));
+            }
+        }
+    }
+    F.sched_sub_level = Ls;
     int L_w = F.depth + 1;
-    for (int l = F.depth; l >= 0; --l) {
+    for (int l = std::min(F.depth, Ls - 1); l >= 0 && Ls > F.depth; --l) {
         bool all = true;
         for (int s : F.levels[l]) all = all && tiny(s);
         if (!all) break;
@@ -1103,14 +1404,27 @@ ndhss_status build_apply_schedule(FactorData& F, cudaStream_t st) {
             q.insert(q.end(), w, w + QW);
         }
     };
+    auto ulv_front = [&](int s) { return !F.ulv_root_of.empty() && F.ulv_root_of[s] >= 0; };
     const int ng = ceil_div(F.n, GATHER_CHUNK);
     for (int i = 0; i < ng; ++i) push(TK_GATHER, 0, i * GATHER_CHUNK, 0, false);
     cut();
+    auto push_sub = [&](int kind, int r) {
+        const int32_t w[QW] = {(kind << TK_SHIFT) | r, sub_lo[r], sub_ni[r], F.m_i(r), F.m_b(r),
+                               F.info(r, 4), F.info(r, 6), sub_len[r], 0, 0, sub_off[r], 0};
+        q.insert(q.end(), w, w + QW);
+    };
+    if (Ls <= F.depth) {
+        for (int r : F.levels[Ls]) {
+            push_sub(TK_SUBUP, r);
+            need[CN_UP * nn + r] = 1;
+        }
+        cut();
+    }
     for (int l = F.depth; l >= L_w; --l) {
         push_w(TK_UPW, l);
         cut();
     }
-    for (int l = std::min(F.depth, L_w - 1); l >= 0; --l) {
+    for (int l = std::min({F.depth, L_w - 1, Ls - 1}); l >= 0; --l) {
         // fused / dense / low-rank-dot tasks of the level, then what completes each node
         for (int s : F.levels[l]) {
             const int mi = F.m_i(s), mb = F.m_b(s);
@@ -1129,6 +1443,21 @@ ndhss_status build_apply_schedule(FactorData& F, cudaStream_t st) {
                 need[CN_DOT * nn + s] = ceil_div(mi, LR_CHUNK) * ceil_div(F.lr_k[s], dgw);
             }
         }
+        // the diagonal step of the level's nodes not fused above (the same
+        // dependencies as their up-sweep: ready together, and queued with it so
+        // the tickets of the up-sweep chain above do not hold it back):
+        // column-chunk partial products, then their sums with the level's
+        // completing tasks
+        for (int s : F.levels[l]) {
+            const int mi = F.m_i(s);
+            if (mi == 0 || fused(s) || ulv_front(s)) continue;
+            const int nch = ceil_div(mi, DIAG_COLS);
+            dpoff[s] = F.dpart_total;
+            F.dpart_total += (int64_t)nch * mi;
+            for (int c0 = 0; c0 < mi; c0 += DIAG_COLS)
+                for (int r0 = 0; r0 < mi; r0 += APPLY_ROWS) push(TK_DPART, s, r0, c0, false);
+            need[CN_DPART * nn + s] = nch * ceil_div(mi, APPLY_ROWS);
+        }
         cut();
         for (int s : F.levels[l]) {
             if (fused(s) || (F.m_i(s) > 0 && F.m_b(s) > 0 && mode(s) == 0)) continue;
@@ -1140,25 +1469,6 @@ ndhss_status build_apply_schedule(FactorData& F, cudaStream_t st) {
                 need[CN_UP * nn + s] = 1;
             }
         }
-        cut();
-    }
-    // diagonal step of the nodes not fused above, deepest level first (ready
-    // early; they fill the GPU while the top levels' up-sweep chain runs):
-    // column-chunk partial products, then their sums
-    auto ulv_front = [&](int s) { return !F.ulv_root_of.empty() && F.ulv_root_of[s] >= 0; };
-    for (int l = std::min(F.depth, L_w - 1); l >= 0; --l)
-        for (int s : F.levels[l]) {
-            const int mi = F.m_i(s);
-            if (mi == 0 || fused(s) || ulv_front(s)) continue;
-            const int nch = ceil_div(mi, DIAG_COLS);
-            dpoff[s] = F.dpart_total;
-            F.dpart_total += (int64_t)nch * mi;
-            for (int c0 = 0; c0 < mi; c0 += DIAG_COLS)
-                for (int r0 = 0; r0 < mi; r0 += APPLY_ROWS) push(TK_DPART, s, r0, c0, false);
-            need[CN_DPART * nn + s] = nch * ceil_div(mi, APPLY_ROWS);
-        }
-    cut();
-    for (int l = std::min(F.depth, L_w - 1); l >= 0; --l)
         for (int s : F.levels[l]) {
             const int mi = F.m_i(s);
             if (mi == 0 || fused(s) || ulv_front(s)) continue;
@@ -1166,7 +1476,8 @@ ndhss_status build_apply_schedule(FactorData& F, cudaStream_t st) {
             need[CN_DIAG * nn + s] = ceil_div(mi, SUM_ROWS);
             if (diag_final(s)) need[CN_FIN * nn + s] = need[CN_DIAG * nn + s];
         }
-    cut();
+        cut();
+    }
     // ULV solves of the HSS fronts: every front's HSS nodes going up (deepest
     // HSS level first), the roots, then down; the leaves (or a root that is
     // a leaf) write z(I^s)
@@ -1215,7 +1526,7 @@ ndhss_status build_apply_schedule(FactorData& F, cudaStream_t st) {
             if (F.ulv_recs[i].level == lv) push_u(TK_HDN, i);
         cut();
     }
-    for (int l = 0; l < L_w; ++l) {
+    for (int l = 0; l < std::min(L_w, Ls); ++l) {
         for (int s : F.levels[l]) {
             if (F.m_i(s) == 0 || diag_final(s) || mode(s) != 1) continue;
             for (int r0 = 0; r0 < F.m_b(s); r0 += LR_CHUNK)
@@ -1243,6 +1554,10 @@ ndhss_status build_apply_schedule(FactorData& F, cudaStream_t st) {
         push_w(TK_DNW, l);
         cut();
     }
+    if (Ls <= F.depth) {
+        for (int r : F.levels[Ls]) push_sub(TK_SUBDN, r);
+        cut();
+    }
     F.sched_n = (int64_t)q.size() / QW;
     F.sched_ngather = ng;
     F.sched_groups = groups;
@@ -1265,6 +1580,7 @@ ndhss_status build_apply_schedule(FactorData& F, cudaStream_t st) {
     up(&F.d_sched, q);
     up(&F.d_need, need);
     up(&F.d_wdesc, wdesc);
+    up(&F.d_sublist, sublist);
     if (nrec) {
         if (pool_malloc_async(&F.d_ulvdev, udev.size() * sizeof(UlvDev), st) != cudaSuccess ||
             cudaMemcpyAsync(F.d_ulvdev, udev.data(), udev.size() * sizeof(UlvDev), cudaMemcpyHostToDevice, st) !=

@@ -692,6 +692,7 @@ static ndhss_status factor_impl(const ndhss_tree* th, int32_t vtype, const int32
     F.depth = t.depth;
     F.esize = esize;
     F.node_info = t.node_info;
+    F.blist_h = t.blist;
     F.L_hss = (o.hss_levels >= 0) ? t.depth - o.hss_levels : -1;
     F.levels.assign(t.depth + 1, {});
     for (int s = 0; s < t.nnodes; ++s) F.levels[t.level(s)].push_back(s);
@@ -1055,7 +1056,7 @@ void ndhss_factor_destroy(ndhss_factorization* fh) {
     cudaDeviceSynchronize();
     for (void* p : {(void*)F.d_node, (void*)F.d_foff, (void*)F.d_blist, (void*)F.d_perm, (void*)F.d_sigma,
                     (void*)F.d_ipiv, F.d_front, (void*)F.d_lr_ptr, (void*)F.d_lr_k, (void*)F.d_lr_list, (void*)F.d_sched,
-                    (void*)F.d_need, (void*)F.d_wdesc, (void*)F.d_apply_err, (void*)F.d_mjobs})
+                    (void*)F.d_need, (void*)F.d_wdesc, (void*)F.d_apply_err, (void*)F.d_mjobs, (void*)F.d_sublist})
         if (p) cudaFreeAsync(p, 0);
     for (void* b : F.lr_bufs)
         if (b) cudaFreeAsync(b, 0);

@@ -23,6 +23,7 @@ struct FactorData {
     int32_t n = 0, nnodes = 0, depth = 0;
     size_t esize = 0;                         // bytes per stored front element
     std::vector<int32_t> node_info;           // copy of the tree's node table
+    std::vector<int32_t> blist_h;             // copy of the tree's B lists (new numbering)
     std::vector<int64_t> foff;                // front offset (elements) per node
     std::vector<std::vector<int32_t>> levels; // levels[l] = node ids on level l
     int64_t front_elems = 0;
@@ -49,6 +50,8 @@ struct FactorData {
     int32_t sched_vlen = 0;
     int32_t* d_need = nullptr;
     int32_t* d_wdesc = nullptr;               // warp-node descriptors (8 ints per node)
+    int32_t* d_sublist = nullptr;             // bottom subtrees: node lists by level
+    int32_t sched_sub_level = 0;              // first level handled by subtree tasks
     int32_t sched_warp_level = 0;             // first level handled a warp per node
     int64_t dpart_total = 0;
     int32_t* d_apply_err = nullptr;
