@@ -1040,7 +1040,13 @@ template <typename T> constexpr int apply_min_blocks() { return sizeof(T) <= 8 ?
 template <typename T, typename V>
 __global__ void __launch_bounds__(AT, apply_min_blocks<T>()) apply_dataflow_kernel(ApplyCtx<T> C, Sched S, int n, const V* __restrict__ x,
                                                             V* __restrict__ out, T* y, T* z, T* tup, T* tdn, T* dpart,
-                                                            T* us, int vlen) {
+                                                            T* us, int vlen, const ApplyInd* ind) {
+    if (ind) {
+        // vectors chosen on the device by the caller's previous kernel
+        if (*(volatile const int32_t*)ind->skip) return;
+        x = static_cast<const V*>(ind->x);
+        out = static_cast<V*>(ind->y);
+    }
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ T red[AW][APPLY_ROWS];
     __shared__ int s_task, s_ok;
@@ -1111,7 +1117,12 @@ __global__ void __launch_bounds__(AT, apply_min_blocks<T>()) apply_dataflow_kern
 template <typename T, typename V>
 __global__ void __launch_bounds__(AT, apply_min_blocks<T>()) apply_group_kernel(ApplyCtx<T> C, const int32_t* __restrict__ q, int n,
                                                          const V* __restrict__ x, V* __restrict__ out, T* y, T* z, T* tup,
-                                                         T* tdn, T* dpart, T* us, int vlen) {
+                                                         T* tdn, T* dpart, T* us, int vlen, const ApplyInd* ind) {
+    if (ind) {
+        if (*(volatile const int32_t*)ind->skip) return;
+        x = static_cast<const V*>(ind->x);
+        out = static_cast<V*>(ind->y);
+    }
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ T red[AW][APPLY_ROWS];
     __shared__ int wd[AW][8];
@@ -1162,7 +1173,7 @@ size_t smem_bytes(const FactorData& F, size_t esize) {
 
 template <typename T, typename V>
 ndhss_status apply_run(const FactorData& F, int32_t nrhs, const V* x, int64_t ldx, V* y, int64_t ldy, unsigned char* w,
-                       cudaStream_t st) {
+                       cudaStream_t st, const ApplyInd* ind) {
     if (!F.d_sched) return set_error(NDHSS_ERR_INTERNAL, "apply: factorization has no task queue");
     const WorkLayout WL = work_layout(F);
     const ApplyCtx<T> C = make_ctx<T>(F);
@@ -1180,7 +1191,7 @@ ndhss_status apply_run(const FactorData& F, int32_t nrhs, const V* x, int64_t ld
                 const int64_t g0 = F.sched_groups[g], g1 = F.sched_groups[g + 1];
                 if (g1 == g0) continue;
                 apply_group_kernel<T, V><<<(unsigned)(g1 - g0), AT, smem, st>>>(
-                    C, F.d_sched + QW * g0, F.n, x + r * ldx, y + r * ldy, wy, wz, tup, tdn, dpart, us, vlen);
+                    C, F.d_sched + QW * g0, F.n, x + r * ldx, y + r * ldy, wy, wz, tup, tdn, dpart, us, vlen, ind);
                 NDHSS_LAUNCH_CHECK("apply_group_kernel");
             }
         return NDHSS_OK;
@@ -1191,7 +1202,7 @@ ndhss_status apply_run(const FactorData& F, int32_t nrhs, const V* x, int64_t ld
     for (int r = 0; r < nrhs; ++r) {
         NDHSS_CUDA_TRY(cudaMemsetAsync(S.ctl, 0, ctl_bytes, st));
         apply_dataflow_kernel<T, V><<<(unsigned)F.sched_grid, AT, smem, st>>>(C, S, F.n, x + r * ldx, y + r * ldy, wy, wz,
-                                                                              tup, tdn, dpart, us, vlen);
+                                                                              tup, tdn, dpart, us, vlen, ind);
         NDHSS_LAUNCH_CHECK("apply_dataflow_kernel");
     }
     return NDHSS_OK;
@@ -1615,16 +1626,16 @@ ndhss_status apply_check_error(const FactorData& F, const char* who) {
 size_t apply_work_bytes(const FactorData& F) { return work_layout(F).total; }
 
 ndhss_status apply_device(const FactorData& F, int32_t nrhs, const void* d_x, int64_t ldx, void* d_y, int64_t ldy,
-                          void* d_work, cudaStream_t st) {
+                          void* d_work, cudaStream_t st, const ApplyInd* ind) {
     const bool cplx = F.vtype == NDHSS_C128;
     unsigned char* w = static_cast<unsigned char*>(d_work);
     if (!cplx && F.prec == NDHSS_FP64)
-        return apply_run<double, double>(F, nrhs, (const double*)d_x, ldx, (double*)d_y, ldy, w, st);
+        return apply_run<double, double>(F, nrhs, (const double*)d_x, ldx, (double*)d_y, ldy, w, st, ind);
     if (!cplx)
-        return apply_run<float, double>(F, nrhs, (const double*)d_x, ldx, (double*)d_y, ldy, w, st);
+        return apply_run<float, double>(F, nrhs, (const double*)d_x, ldx, (double*)d_y, ldy, w, st, ind);
     if (F.prec == NDHSS_FP64)
-        return apply_run<c128, c128>(F, nrhs, (const c128*)d_x, ldx, (c128*)d_y, ldy, w, st);
-    return apply_run<c64, c128>(F, nrhs, (const c128*)d_x, ldx, (c128*)d_y, ldy, w, st);
+        return apply_run<c128, c128>(F, nrhs, (const c128*)d_x, ldx, (c128*)d_y, ldy, w, st, ind);
+    return apply_run<c64, c128>(F, nrhs, (const c128*)d_x, ldx, (c128*)d_y, ldy, w, st, ind);
 }
 
 }  // namespace ndhss

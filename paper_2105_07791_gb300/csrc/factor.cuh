@@ -149,8 +149,17 @@ bool tc_front_path(const FactorData& F, int64_t mi_max);
 ndhss_status tc_block_exchange(FactorData& F, const std::vector<int>& nodes, int k0, DevStatus* d_status,
                                cudaStream_t st);
 
+// Input and output of one apply chosen on the device (by the kernel before
+// it on the stream): the apply kernels read x and y here at their start and
+// return at once while *skip is nonzero.
+struct ApplyInd {
+    const void* x;
+    void* y;
+    const int32_t* skip;
+};
+
 ndhss_status apply_device(const FactorData& F, int32_t nrhs, const void* d_x, int64_t ldx,
-                          void* d_y, int64_t ldy, void* d_work, cudaStream_t st);
+                          void* d_y, int64_t ldy, void* d_work, cudaStream_t st, const ApplyInd* ind = nullptr);
 size_t apply_work_bytes(const FactorData& F);
 // Builds and uploads the dataflow queue once the factor (and its low-rank
 // tier) is complete; defined in apply.cu.

@@ -15,9 +15,9 @@
 // classical Gram-Schmidt twice: h = V^H w, w -= V h (x2); ||w||; a one-thread
 // kernel stores the Hessenberg column, applies the previous complex Givens
 // rotations G = [[c, s], [-conj(s), c]], forms the new one and updates the
-// least-squares residual |g_{j+1}|; v_{j+1} = w / h_{j+1,j}.  The host reads
-// that residual once per step to decide whether the cycle ends.  After each
-// cycle x += V y with H y = g solved on the device, and the float64 true
+// least-squares residual |g_{j+1}|; v_{j+1} = w / h_{j+1,j}.  The device
+// decides whether the cycle ends (see "device-driven GMRES" below).  After
+// each cycle x += V y with H y = g solved on the device, and the float64 true
 // residual ||b - A x|| / ||b|| decides convergence (restarts refine).
 //
 // Reductions are deterministic: each block writes its partial sums and the
@@ -33,7 +33,7 @@ namespace {
 
 constexpr int KMAX = 32;          // restart + 1 <= KMAX
 constexpr int RT = 256;           // reduction block size
-constexpr int RB = 2 * 152;       // reduction grid (two blocks per SM)
+constexpr int RB = 4 * 152;       // reduction grid (four 256-thread blocks per SM)
 
 __device__ __forceinline__ double ldcg(const double* p) { return __ldcg(p); }
 __device__ __forceinline__ c128 ldcg(const c128* p) {
@@ -121,108 +121,6 @@ ndhss_status spmv_launch(int n, const int32_t* rowptr, const int32_t* col, const
     return NDHSS_OK;
 }
 
-// ---------------------------------------------------------- reductions
-// out[i] = sum_rows conj(Vb(row, i)) * w(row), i < k.  Grid (RB, k): block
-// (b, i) sums its grid-stride rows of column i into partial[i * RB + b]; the
-// last block to finish adds each column's partials with one warp in a fixed
-// order.
-template <typename V>
-__global__ void __launch_bounds__(RT)
-mdot_kernel(int n, const V* __restrict__ Vb, int64_t ldv, int k, const V* __restrict__ w, V* __restrict__ partial,
-            V* __restrict__ out, unsigned* __restrict__ counter) {
-    __shared__ V sred[RT / 32];
-    __shared__ bool s_last;
-    const int i = blockIdx.y;
-    const V* v = Vb + (int64_t)i * ldv;
-    V acc0 = zero<V>(), acc1 = zero<V>();
-    const int64_t stride = (int64_t)gridDim.x * RT;
-    int64_t row = (int64_t)blockIdx.x * RT + threadIdx.x;
-    for (; row + stride < n; row += 2 * stride) {
-        acc0 = fmac(conjv(v[row]), w[row], acc0);
-        acc1 = fmac(conjv(v[row + stride]), w[row + stride], acc1);
-    }
-    if (row < n) acc0 = fmac(conjv(v[row]), w[row], acc0);
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const V ws = warp_sum(acc0 + acc1);
-    if (lane == 0) sred[warp] = ws;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        V sum = zero<V>();
-        for (int q = 0; q < RT / 32; ++q) sum += sred[q];
-        partial[(int64_t)i * gridDim.x + blockIdx.x] = sum;
-    }
-    __threadfence();
-    if (threadIdx.x == 0) s_last = (atomicAdd(counter, 1u) == gridDim.x * gridDim.y - 1);
-    __syncthreads();
-    if (s_last) {
-        for (int c = warp; c < k; c += RT / 32) {
-            V sum = zero<V>();
-            for (unsigned b = lane; b < gridDim.x; b += 32) sum += ldcg(partial + (int64_t)c * gridDim.x + b);
-            sum = warp_sum(sum);
-            if (lane == 0) out[c] = sum;
-        }
-        if (threadIdx.x == 0) *counter = 0;
-    }
-}
-
-// out = sum |w|^2
-template <typename V>
-__global__ void __launch_bounds__(RT)
-nrm2_kernel(int n, const V* __restrict__ w, double* __restrict__ partial, double* __restrict__ out,
-            unsigned* __restrict__ counter) {
-    __shared__ double sred[RT / 32];
-    __shared__ bool s_last;
-    double acc = 0.0;
-    for (int64_t row = (int64_t)blockIdx.x * RT + threadIdx.x; row < n; row += (int64_t)gridDim.x * RT) acc += norm2(w[row]);
-    acc = warp_sum(acc);
-    if ((threadIdx.x & 31) == 0) sred[threadIdx.x >> 5] = acc;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double s = 0.0;
-        for (int q = 0; q < RT / 32; ++q) s += sred[q];
-        partial[blockIdx.x] = s;
-    }
-    __threadfence();
-    if (threadIdx.x == 0) s_last = (atomicAdd(counter, 1u) == gridDim.x - 1);
-    __syncthreads();
-    if (s_last && threadIdx.x < 32) {
-        double s = 0.0;
-        for (unsigned b = threadIdx.x; b < gridDim.x; b += 32) s += __ldcg(partial + b);
-        s = warp_sum(s);
-        if (threadIdx.x == 0) {
-            *out = s;
-            *counter = 0;
-        }
-    }
-}
-
-// w += sgn * Vb(:, 0:k) h
-template <typename V>
-__global__ void maxpy_kernel(int n, V* __restrict__ w, const V* __restrict__ Vb, int64_t ldv, int k,
-                             const V* __restrict__ h, double sgn) {
-    __shared__ V sh[KMAX];
-    if (threadIdx.x < k) sh[threadIdx.x] = scale(h[threadIdx.x], sgn);
-    __syncthreads();
-    for (int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; row < n; row += (int64_t)gridDim.x * blockDim.x) {
-        V acc = w[row];
-        for (int i = 0; i < k; ++i) acc = fmac(Vb[row + i * ldv], sh[i], acc);
-        w[row] = acc;
-    }
-}
-
-template <typename V>
-__global__ void scale_kernel(int n, const V* __restrict__ src, V* __restrict__ dst, const double* __restrict__ s) {
-    const double f = *s;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        dst[i] = scale(src[i], f);
-}
-
-template <typename V>
-__global__ void residual_kernel(int n, const V* __restrict__ b, const V* __restrict__ ax, V* __restrict__ r) {
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        r[i] = b[i] - ax[i];
-}
-
 // v <- conj(v): the adjoint solve of a complex symmetric A, A^H x = b, is
 // A conj(x) = conj(b).
 __global__ void __launch_bounds__(256) conj_kernel(int64_t n, c128* __restrict__ v) {
@@ -238,76 +136,519 @@ static ndhss_status conj_inplace(c128* v, int64_t n, cudaStream_t st) {
     return NDHSS_OK;
 }
 
-// scalars: [0] scale for the next basis vector, [1] |g_{j+1}|, [2] h_{j+1,j}, [3] beta
-struct GmState {
-    double scal[4];
+// ------------------------------------------------ device-driven GMRES
+// The host enqueues the same block of launches again and again; the device
+// state decides what each block does, so no launch waits for a decision
+// taken on the host:
+//   begin     (RESTART with a finished cycle: x += V y; chooses the vectors
+//             of the SpMV and the apply below)
+//   SpMV      t = s A v  (RESTART: v = x, s = 1; STEP: v = raw basis vector
+//             j, s its scale)
+//   resid     RESTART: r = b - t, ||r||, the float64 true residual decides
+//             convergence, maxit and the cycle tolerances
+//   apply     RESTART: V_0 = P^{-1} r;  STEP: V_{j+1} = P^{-1} t
+//   dot       RESTART: beta = ||V_0||, g = beta e_1;  STEP: h1 = V^H w
+//   axdot     STEP: w -= V h1, h2 = V^H w   (classical Gram-Schmidt twice)
+//   axnorm    STEP: w -= V h2, ||w||, the Hessenberg column and its Givens
+//             rotation, |g_{j+1}| decides whether the cycle ends (then
+//             y = H^{-1} g for the next block's begin); writes the block's
+//             status word to pinned host memory
+// Basis vectors stay unnormalised (raw w); each carries its scale 1/||w||,
+// applied wherever it is read.  Kernels of a finished solve return at once.
+// The host reads the status word of block b - 1 while block b runs, so the
+// GPU never idles on a host round trip; at most one block of no-op
+// launches follows convergence.
+//
+// Reductions are deterministic: each block writes its partial sums and the
+// last block to finish (ticket counter) adds them in block order.
+enum : int { GM_RESTART = 0, GM_STEP = 1 };
+constexpr int GM_MAX_IT = 1000;               // maxit allowed by ndhss_gmres
+constexpr int GM_MAX_BLOCKS = 2 * GM_MAX_IT + 8;   // a solve takes at most 2 maxit + 2 blocks
+
+struct GmStatus {
+    int32_t done, its, pad0, pad1;
 };
 
-// start of a cycle: beta = ||z||, g = beta e_1
 template <typename V>
-__global__ void cycle_init_kernel(const double* __restrict__ nrm2z, V* __restrict__ g, int restart, GmState* stt) {
-    const double beta = sqrt(*nrm2z);
-    for (int i = 0; i <= restart; ++i) g[i] = zero<V>();
-    V b0 = zero<V>();
-    if constexpr (sizeof(V) == 8) b0 = beta; else b0.x = beta;
-    g[0] = b0;
-    stt->scal[0] = beta > 0 ? 1.0 / beta : 0.0;
-    stt->scal[3] = beta;
-    stt->scal[1] = beta;
+struct alignas(16) GmDev {
+    int32_t mode, bmode, j, jend, its, cycles, done, have_cycle, skip, bnorm_set, maxit, R;
+    double bnorm, zbnorm, beta, relres, last_res, prev_rel, cyc_target, rtol_eff, tol, inner;
+    const V* spmv_in;
+    V* spmv_out;
+    double spmv_scale;
+    ApplyInd ind;
+    unsigned counter[KMAX / 4 + 2];      // reduction tickets (one per dot-product chunk)
+    double scale[KMAX];
+    V g[KMAX], H[KMAX * KMAX], sn[KMAX], h1[KMAX], h2[KMAX], y[KMAX];
+    double cs[KMAX];
+    uint8_t ran[GM_MAX_BLOCKS];          // per block: 1 the SpMV ran, 2 the apply ran
+};
+
+// The last block of a reduction takes its decisions on a shared-memory copy
+// of the state (one parallel load; thread 0's scalar code would otherwise wait
+// out a global-memory round trip per field) and writes it back.
+template <typename V>
+__device__ __forceinline__ void gm_state_load(GmDev<V>& sh, const GmDev<V>* S) {
+    static_assert(sizeof(GmDev<V>) % 16 == 0, "state copied in 16-byte words");
+    const int4* src = reinterpret_cast<const int4*>(S);
+    int4* dst = reinterpret_cast<int4*>(&sh);
+    for (int i = threadIdx.x; i < (int)(sizeof(GmDev<V>) / 16); i += blockDim.x) dst[i] = __ldcg(src + i);
+    __syncthreads();
+}
+template <typename V>
+__device__ __forceinline__ void gm_state_store(GmDev<V>* S, const GmDev<V>& sh) {
+    __syncthreads();
+    const int4* src = reinterpret_cast<const int4*>(&sh);
+    int4* dst = reinterpret_cast<int4*>(S);
+    for (int i = threadIdx.x; i < (int)(sizeof(GmDev<V>) / 16); i += blockDim.x) __stcg(dst + i, src[i]);
 }
 
-// Hessenberg column j, Givens rotations, residual estimate
+template <typename V> __device__ __forceinline__ V from_real(double v);
+template <> __device__ __forceinline__ double from_real<double>(double v) { return v; }
+template <> __device__ __forceinline__ c128 from_real<c128>(double v) { return {v, 0.0}; }
+
+// ticket of the last block of a reduction (resets the counter for the next
+// one).  Only thread 0 wrote the block's partial, so only thread 0 fences
+// before taking its ticket (a fence in every thread of every block costs
+// more than the reduction).
+__device__ __forceinline__ bool last_block(unsigned* counter, unsigned nblocks) {
+    __shared__ bool s_last;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        s_last = atomicAdd(counter, 1u) == nblocks - 1;
+        if (s_last) *counter = 0;
+    }
+    __syncthreads();
+    if (s_last) __threadfence();
+    return s_last;
+}
+
+// block sum of one value per thread, valid in thread 0
+template <typename T>
+__device__ __forceinline__ T block_sum(T v) {
+    __shared__ T sred[RT / 32];
+    v = warp_sum(v);
+    if ((threadIdx.x & 31) == 0) sred[threadIdx.x >> 5] = v;
+    __syncthreads();
+    T s = zero<T>();
+    if (threadIdx.x == 0)
+        for (int q = 0; q < RT / 32; ++q) s += sred[q];
+    __syncthreads();
+    return s;
+}
+
+// sum of the grid's partials by the whole (last) block, four loads in flight
+// per thread, each thread's share in a fixed order, then the block's fixed
+// tree (deterministic); valid in thread 0
+template <typename T>
+__device__ T block_sum_partials(const T* partial, unsigned nb) {
+    T s = zero<T>();
+    unsigned q = threadIdx.x;
+    for (; q + 3 * RT < nb; q += 4 * RT) {
+        const T a0 = ldcg(partial + q), a1 = ldcg(partial + q + RT), a2 = ldcg(partial + q + 2 * RT),
+                a3 = ldcg(partial + q + 3 * RT);
+        s += a0;
+        s += a1;
+        s += a2;
+        s += a3;
+    }
+    for (; q < nb; q += RT) s += ldcg(partial + q);
+    return block_sum(s);
+}
+
 template <typename V>
-__global__ void arnoldi_step_kernel(int j, V* __restrict__ H, int ldh, const V* __restrict__ h1, const V* __restrict__ h2,
-                                    const double* __restrict__ nrm2w, V* __restrict__ g, double* __restrict__ cs,
-                                    V* __restrict__ sn, GmState* stt) {
-    V* Hj = H + (int64_t)j * ldh;
-    for (int i = 0; i <= j; ++i) Hj[i] = h1[i] + h2[i];
-    const double hn = sqrt(*nrm2w);
-    V hv = zero<V>();
-    if constexpr (sizeof(V) == 8) hv = hn; else hv.x = hn;
-    Hj[j + 1] = hv;
+__global__ void gm_init_kernel(GmDev<V>* S, int R, int maxit, double tol, double inner, double rtol) {
+    S->mode = GM_RESTART;
+    S->bmode = GM_RESTART;
+    S->j = S->jend = S->its = S->cycles = S->done = S->have_cycle = S->skip = S->bnorm_set = 0;
+    S->maxit = maxit;
+    S->R = R;
+    S->bnorm = 0.0;
+    S->zbnorm = -1.0;
+    S->beta = S->relres = 0.0;
+    S->last_res = 1.0;
+    S->prev_rel = INFINITY;
+    S->cyc_target = 0.0;
+    S->rtol_eff = rtol;
+    S->tol = tol;
+    S->inner = inner;
+    for (int q = 0; q < KMAX / 4 + 2; ++q) S->counter[q] = 0;
+    S->ind.skip = &S->skip;
+    for (int b = 0; b < GM_MAX_BLOCKS; ++b) S->ran[b] = 0;
+}
+
+template <typename V>
+__global__ void __launch_bounds__(256) gm_begin_kernel(GmDev<V>* S, V* __restrict__ x, const V* __restrict__ Vb, int64_t ldv,
+                                                       V* t, V* r, int n, int blk) {
+    if (S->done) return;
+    const int mode = S->mode;
+    if (mode == GM_RESTART && S->have_cycle) {
+        // x += V y, V_i = scale_i raw_i (y solved when the cycle ended)
+        __shared__ V cy[KMAX];
+        const int k = S->jend;
+        if (threadIdx.x < k) cy[threadIdx.x] = scale(S->y[threadIdx.x], S->scale[threadIdx.x]);
+        __syncthreads();
+        for (int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; row < n; row += (int64_t)gridDim.x * blockDim.x) {
+            V acc = x[row];
+            for (int i = 0; i < k; ++i) acc = fmac(Vb[row + i * ldv], cy[i], acc);
+            x[row] = acc;
+        }
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        S->bmode = mode;
+        S->spmv_out = t;
+        if (mode == GM_RESTART) {
+            S->spmv_in = x;
+            S->spmv_scale = 1.0;
+            S->ind.x = r;
+            S->ind.y = const_cast<V*>(Vb);
+            S->ran[blk] = 1;
+        } else {
+            S->spmv_in = Vb + (int64_t)S->j * ldv;
+            S->spmv_scale = S->scale[S->j];
+            S->ind.x = t;
+            S->ind.y = const_cast<V*>(Vb) + (int64_t)(S->j + 1) * ldv;
+            S->ran[blk] = 3;
+        }
+    }
+}
+
+// t = s A v with v, t, s chosen by gm_begin (see spmv_kernel)
+template <typename V, int TPR, int U>
+__global__ void __launch_bounds__(256) gm_spmv_kernel(int n, const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+                                                      const V* __restrict__ vals, const GmDev<V>* S) {
+    if (S->done) return;
+    const V* __restrict__ x = S->spmv_in;
+    V* __restrict__ y = S->spmv_out;
+    const double sc = S->spmv_scale;
+    const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t row = gt / TPR;
+    const int lane = (int)(gt % TPR);
+    if (row >= n) return;
+    const int k0 = rowptr[row], k1 = rowptr[row + 1];
+    V acc = zero<V>();
+    for (int base = k0; base < k1; base += U * TPR) {
+        int c[U];
+        V a[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int k = base + lane + u * TPR;
+            c[u] = k < k1 ? col[k] : -1;
+            a[u] = k < k1 ? vals[k] : zero<V>();
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+            if (c[u] >= 0) acc = spmv_mac(a[u], x[c[u]], acc);
+    }
+    if constexpr (sizeof(V) == 8) {
+        for (int o = TPR / 2; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o, TPR);
+    } else {
+        for (int o = TPR / 2; o; o >>= 1) {
+            acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o, TPR);
+            acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o, TPR);
+        }
+    }
+    if (lane == 0) y[row] = scale(acc, sc);
+}
+
+template <typename V>
+__device__ void gm_decide(GmDev<V>* S, double rr, int blk);
+
+// RESTART: r = b - t and the true residual's decisions (gm_decide)
+template <typename V>
+__global__ void __launch_bounds__(RT, 4) gm_resid_kernel(GmDev<V>* S, const V* __restrict__ b, const V* __restrict__ t,
+                                                         V* __restrict__ r, int n, double* __restrict__ partial, int blk) {
+    if (S->done || S->bmode != GM_RESTART) return;
+    double acc = 0.0;
+    for (int64_t row = (int64_t)blockIdx.x * RT + threadIdx.x; row < n; row += (int64_t)gridDim.x * RT) {
+        const V v = b[row] - t[row];
+        r[row] = v;
+        acc += norm2(v);
+    }
+    const double bs = block_sum(acc);
+    if (threadIdx.x == 0) partial[blockIdx.x] = bs;
+    if (!last_block(S->counter, gridDim.x)) return;
+    const double tot = block_sum_partials(partial, gridDim.x);
+    __shared__ GmDev<V> sh;
+    gm_state_load(sh, S);
+    if (threadIdx.x == 0) gm_decide(&sh, tot, blk);
+    gm_state_store(S, sh);
+}
+
+// RESTART: the float64 true residual ||r||^2 = rr decides convergence,
+// maxit and the cycle tolerances
+template <typename V>
+__device__ void gm_decide(GmDev<V>* S, double rr, int blk) {
+    const double nr = sqrt(rr);
+    if (!S->bnorm_set) {                  // x0 = 0: the first residual is b
+        S->bnorm = nr;
+        S->bnorm_set = 1;
+    }
+    S->have_cycle = 0;
+    if (S->bnorm == 0.0) {
+        S->relres = 0.0;
+        S->done = 1;
+    } else {
+        const double rel = nr / S->bnorm;
+        S->relres = rel;
+        if (rel <= S->tol) {
+            S->done = 1;
+        } else if (S->its >= S->maxit) {
+            S->done = 2;
+        } else {
+            // a cycle that did not halve the true residual: later cycles end once
+            // their estimate fell by the reduction the true residual still needs
+            if (rel > 0.5 * S->prev_rel) {
+                S->rtol_eff = 0.0;
+                S->cyc_target = 0.1 * S->tol / rel;
+            } else if (S->cyc_target > 0.0) {
+                S->cyc_target = 0.1 * S->tol / rel;
+            }
+            S->prev_rel = rel;
+            S->cycles++;
+            S->ran[blk] |= 2;
+        }
+    }
+    S->skip = S->done != 0;
+}
+
+// acc + conj(v) w, with the conjugation in the FMAs' operand signs (GB300's
+// FP64 pipe is narrow: a separate negation would cost an FP64 slot)
+__device__ __forceinline__ double fmac_conj(double v, double w, double acc) { return fma(v, w, acc); }
+__device__ __forceinline__ c128 fmac_conj(c128 v, c128 w, c128 acc) {
+    acc.x = fma(v.x, w.x, acc.x);
+    acc.x = fma(v.y, w.y, acc.x);
+    acc.y = fma(v.x, w.y, acc.y);
+    acc.y = fma(-v.y, w.x, acc.y);
+    return acc;
+}
+
+// STEP, one chunk of C basis vectors i0 .. i0 + C - 1 (<= j): their dot
+// products with w over this block's rows, reduced over the grid (partials
+// per vector, one ticket counter per chunk; every block reads the same rows
+// in every chunk, so a chunk needs no other block's rows).  FIRST_AXPY:
+// w -= V h1 with all j + 1 vectors first (the first chunk of the second
+// Gram-Schmidt pass).  Exact-count instantiations: a predicated-off FP64
+// instruction still occupies the FP64 pipe.
+template <typename V, int C, bool FIRST_AXPY>
+__device__ void gm_cgs_chunk(GmDev<V>* S, V* __restrict__ Vb, int64_t ldv, int n, V* __restrict__ partial, int j,
+                             int i0, int chunk, const V* ch, V* out) {
+    V* w = Vb + (int64_t)(j + 1) * ldv;
+    V acc[C];
+#pragma unroll
+    for (int u = 0; u < C; ++u) acc[u] = zero<V>();
+    for (int64_t row = (int64_t)blockIdx.x * RT + threadIdx.x; row < n; row += (int64_t)gridDim.x * RT) {
+        V wv = w[row];
+        if (FIRST_AXPY) {
+            for (int i = 0; i <= j; ++i) wv = fmac(Vb[row + i * ldv], ch[i], wv);
+            w[row] = wv;
+        }
+        V v[C];
+#pragma unroll
+        for (int u = 0; u < C; ++u) v[u] = Vb[row + (i0 + u) * ldv];
+#pragma unroll
+        for (int u = 0; u < C; ++u) acc[u] = fmac_conj(v[u], wv, acc[u]);
+    }
+#pragma unroll
+    for (int u = 0; u < C; ++u) {
+        const V bs = block_sum(acc[u]);
+        if (threadIdx.x == 0) partial[(int64_t)(i0 + u) * gridDim.x + blockIdx.x] = bs;
+    }
+    if (last_block(S->counter + 1 + chunk, gridDim.x)) {
+        for (int u = 0; u < C; ++u) {
+            const V sum = block_sum_partials(partial + (int64_t)(i0 + u) * gridDim.x, gridDim.x);
+            if (threadIdx.x == 0) out[i0 + u] = scale(sum, S->scale[i0 + u]);
+        }
+    }
+}
+
+// basis vectors per chunk: eight real or four complex accumulators and
+// loads in flight keep a thread within the 64 registers of four resident
+// 256-thread blocks per SM
+template <typename V> constexpr int cgs_width() { return sizeof(V) == 16 ? 4 : 8; }
+
+template <typename V, bool FIRST_AXPY>
+__device__ void gm_cgs_dispatch(GmDev<V>* S, V* Vb, int64_t ldv, int n, V* partial, int j, int i0, int chunk,
+                                const V* ch, V* out) {
+    constexpr int CW = cgs_width<V>();
+    switch (min(CW, j + 1 - i0)) {
+#define NDHSS_CGS(CC) case CC: if constexpr (CC <= CW) gm_cgs_chunk<V, CC, FIRST_AXPY>(S, Vb, ldv, n, partial, j, i0, chunk, ch, out); break;
+        NDHSS_CGS(1) NDHSS_CGS(2) NDHSS_CGS(3) NDHSS_CGS(4) NDHSS_CGS(5) NDHSS_CGS(6) NDHSS_CGS(7) NDHSS_CGS(8)
+#undef NDHSS_CGS
+        default: break;
+    }
+}
+
+// STEP: h1 = V^H w (AXPY = false), or w -= V h1 then h2 = V^H w (AXPY = true),
+// cgs_width basis vectors at a time
+template <typename V, bool AXPY>
+__device__ void gm_cgs(GmDev<V>* S, V* __restrict__ Vb, int64_t ldv, int n, V* __restrict__ partial) {
+    const int j = S->j;
+    __shared__ V ch[KMAX];
+    if (AXPY && threadIdx.x <= j) ch[threadIdx.x] = -scale(S->h1[threadIdx.x], S->scale[threadIdx.x]);
+    if (AXPY) __syncthreads();
+    V* out = AXPY ? S->h2 : S->h1;
+    for (int i0 = 0, chunk = 0; i0 <= j; i0 += cgs_width<V>(), ++chunk) {
+        if (AXPY && i0 == 0) gm_cgs_dispatch<V, true>(S, Vb, ldv, n, partial, j, i0, chunk, ch, out);
+        else gm_cgs_dispatch<V, false>(S, Vb, ldv, n, partial, j, i0, chunk, ch, out);
+    }
+}
+
+// RESTART: beta = ||V_0||;  STEP: h1 = V^H w
+template <typename V>
+__global__ void __launch_bounds__(RT, 4) gm_dot_kernel(GmDev<V>* S, V* __restrict__ Vb, int64_t ldv, int n,
+                                                    V* __restrict__ partial, double* __restrict__ dpartial) {
+    if (S->done) return;
+    if (S->bmode == GM_RESTART) {
+        double acc = 0.0;
+        for (int64_t row = (int64_t)blockIdx.x * RT + threadIdx.x; row < n; row += (int64_t)gridDim.x * RT)
+            acc += norm2(Vb[row]);
+        const double bs = block_sum(acc);
+        if (threadIdx.x == 0) dpartial[blockIdx.x] = bs;
+        if (!last_block(S->counter, gridDim.x)) return;
+        const double ss = block_sum_partials(dpartial, gridDim.x);
+        __shared__ GmDev<V> sh;
+        gm_state_load(sh, S);
+        if (threadIdx.x == 0) {
+            const double beta = sqrt(ss);
+            bool ok = true;
+            if (sh.zbnorm < 0.0) {
+                sh.zbnorm = beta;
+                if (beta == 0.0) {                   // P^{-1} b vanished
+                    sh.done = 3;
+                    sh.skip = 1;
+                    ok = false;
+                }
+            }
+            if (ok) {
+                sh.beta = beta;
+                for (int i = 0; i < KMAX; ++i) sh.g[i] = zero<V>();
+                sh.g[0] = from_real<V>(beta);
+                sh.scale[0] = beta > 0.0 ? 1.0 / beta : 0.0;
+                sh.j = 0;
+                sh.mode = GM_STEP;
+            }
+        }
+        gm_state_store(S, sh);
+        return;
+    }
+    gm_cgs<V, false>(S, Vb, ldv, n, partial);
+}
+
+// STEP: w -= V h1, h2 = V^H w
+template <typename V>
+__global__ void __launch_bounds__(RT, 4) gm_axdot_kernel(GmDev<V>* S, V* __restrict__ Vb, int64_t ldv, int n,
+                                                      V* __restrict__ partial) {
+    if (S->done || S->bmode != GM_STEP) return;
+    gm_cgs<V, true>(S, Vb, ldv, n, partial);
+}
+
+// STEP: w -= V h2, ||w||, Hessenberg column j, Givens rotation, the cycle's
+// stopping tests; every block writes the status word
+template <typename V>
+__global__ void __launch_bounds__(RT, 4) gm_axnorm_kernel(GmDev<V>* S, V* __restrict__ Vb, int64_t ldv, int n,
+                                                       double* __restrict__ dpartial, GmStatus* hstat) {
+    const bool step = !S->done && S->bmode == GM_STEP;
+    if (!step) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            hstat->done = S->done;
+            hstat->its = S->its;
+            __threadfence_system();
+        }
+        return;
+    }
+    const int j = S->j;
+    __shared__ V ch[KMAX];
+    if (threadIdx.x <= j) ch[threadIdx.x] = -scale(S->h2[threadIdx.x], S->scale[threadIdx.x]);
+    __syncthreads();
+    V* w = Vb + (int64_t)(j + 1) * ldv;
+    double acc = 0.0;
+    for (int64_t row = (int64_t)blockIdx.x * RT + threadIdx.x; row < n; row += (int64_t)gridDim.x * RT) {
+        V wv = w[row];
+        for (int i = 0; i <= j; ++i) wv = fmac(Vb[row + i * ldv], ch[i], wv);
+        w[row] = wv;
+        acc += norm2(wv);
+    }
+    const double bs = block_sum(acc);
+    if (threadIdx.x == 0) dpartial[blockIdx.x] = bs;
+    if (!last_block(S->counter, gridDim.x)) return;
+    const double ss = block_sum_partials(dpartial, gridDim.x);
+    __shared__ GmDev<V> sh;
+    gm_state_load(sh, S);
+    if (threadIdx.x == 0) {
+    GmDev<V>* S = &sh;                          // thread 0 works on the shared copy
+    const double hn = sqrt(ss);
+    V* Hj = S->H + (int64_t)j * KMAX;
+    for (int i = 0; i <= j; ++i) Hj[i] = S->h1[i] + S->h2[i];
+    Hj[j + 1] = from_real<V>(hn);
     for (int i = 0; i < j; ++i) {
-        const V t0 = scale(Hj[i], cs[i]) + sn[i] * Hj[i + 1];
-        const V t1 = scale(Hj[i + 1], cs[i]) - conjv(sn[i]) * Hj[i];
+        const V t0 = scale(Hj[i], S->cs[i]) + S->sn[i] * Hj[i + 1];
+        const V t1 = scale(Hj[i + 1], S->cs[i]) - conjv(S->sn[i]) * Hj[i];
         Hj[i] = t0;
         Hj[i + 1] = t1;
     }
-    const V a = Hj[j], b = Hj[j + 1];
+    const V a = Hj[j], bb = Hj[j + 1];
     double c;
-    V s;
-    const double aa = absv(a), ab = absv(b);
+    V sn;
+    const double aa = absv(a), ab = absv(bb);
     if (ab == 0.0) {
         c = 1.0;
-        s = zero<V>();
+        sn = zero<V>();
     } else if (aa == 0.0) {
         c = 0.0;
-        s = scale(conjv(b), 1.0 / ab);
+        sn = scale(conjv(bb), 1.0 / ab);
     } else {
-        const double t = hypot(aa, ab);
-        c = aa / t;
-        s = scale(a, 1.0 / aa) * scale(conjv(b), 1.0 / t);
+        const double tt = hypot(aa, ab);
+        c = aa / tt;
+        sn = scale(a, 1.0 / aa) * scale(conjv(bb), 1.0 / tt);
     }
-    cs[j] = c;
-    sn[j] = s;
-    Hj[j] = scale(a, c) + s * b;
+    S->cs[j] = c;
+    S->sn[j] = sn;
+    Hj[j] = scale(a, c) + sn * bb;
     Hj[j + 1] = zero<V>();
-    const V gj = g[j];
-    g[j + 1] = -(conjv(s) * gj);
-    g[j] = scale(gj, c);
-    stt->scal[0] = hn > 0 ? 1.0 / hn : 0.0;
-    stt->scal[1] = absv(g[j + 1]);
-    stt->scal[2] = hn;
+    const V gj = S->g[j];
+    S->g[j + 1] = -(conjv(sn) * gj);
+    S->g[j] = scale(gj, c);
+    S->scale[j + 1] = hn > 0.0 ? 1.0 / hn : 0.0;
+    S->its++;
+    const double gres = absv(S->g[j + 1]);
+    S->last_res = gres / S->zbnorm;
+    const bool inner_done = S->cyc_target > 0.0 ? gres <= S->cyc_target * S->beta : S->last_res <= S->inner * S->tol;
+    if (inner_done || gres <= S->rtol_eff * S->beta || hn == 0.0 || S->its >= S->maxit || j + 1 >= S->R) {
+        // the cycle ends: y = H(0:k, 0:k)^{-1} g(0:k) for the next block's x update
+        const int k = j + 1;
+        for (int i = k - 1; i >= 0; --i) {
+            V yv = S->g[i];
+            for (int l = i + 1; l < k; ++l) yv = yv - S->H[(int64_t)l * KMAX + i] * S->y[l];
+            S->y[i] = cdiv(yv, S->H[(int64_t)i * KMAX + i]);
+        }
+        S->jend = k;
+        S->have_cycle = 1;
+        S->mode = GM_RESTART;
+    } else {
+        S->j = j + 1;
+    }
+    hstat->done = S->done;
+    hstat->its = S->its;
+    __threadfence_system();
+    }
+    gm_state_store(S, sh);
 }
 
-// y = H(0:k, 0:k)^{-1} g(0:k) (upper triangular)
-template <typename V>
-__global__ void hsolve_kernel(int k, const V* __restrict__ H, int ldh, const V* __restrict__ g, V* __restrict__ y) {
-    for (int i = k - 1; i >= 0; --i) {
-        V acc = g[i];
-        for (int l = i + 1; l < k; ++l) acc = acc - H[(int64_t)l * ldh + i] * y[l];
-        y[i] = cdiv(acc, H[(int64_t)i * ldh + i]);
+// Pinned status words of this thread's solves (two blocks in flight), mapped
+// into the device address space; kept for the thread's lifetime.
+GmStatus* pinned_status() {
+    thread_local GmStatus* p = nullptr;
+    if (!p) {
+        void* h = nullptr;
+        if (cudaHostAlloc(&h, 2 * sizeof(GmStatus), cudaHostAllocMapped | cudaHostAllocPortable) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        p = static_cast<GmStatus*>(h);
     }
+    return p;
 }
 
 template <typename V>
@@ -323,171 +664,107 @@ ndhss_status gmres_one(const FactorData& F, const int32_t* rowptr, const int32_t
         return p;
     };
     V* Vb = (V*)carve(sizeof(V) * ldv * (R + 1));
-    V* w = (V*)carve(sizeof(V) * n);
     V* t = (V*)carve(sizeof(V) * n);
     V* r = (V*)carve(sizeof(V) * n);
-    V* H = (V*)carve(sizeof(V) * (R + 1) * R);
-    V* g = (V*)carve(sizeof(V) * (R + 1));
-    double* cs = (double*)carve(sizeof(double) * R);
-    V* sn = (V*)carve(sizeof(V) * R);
-    V* h1 = (V*)carve(sizeof(V) * KMAX);
-    V* h2 = (V*)carve(sizeof(V) * KMAX);
-    V* yv = (V*)carve(sizeof(V) * KMAX);
     V* part = (V*)carve(sizeof(V) * RB * KMAX);
     double* dpart = (double*)carve(sizeof(double) * RB);
-    double* nrm = (double*)carve(sizeof(double) * 4);
-    unsigned* counter = (unsigned*)carve(sizeof(unsigned) * 4);
-    GmState* stt = (GmState*)carve(sizeof(GmState));
+    GmDev<V>* S = (GmDev<V>*)carve(sizeof(GmDev<V>));
     void* awork = carve(apply_work_bytes(F));
-    NDHSS_CUDA_TRY(cudaMemsetAsync(counter, 0, sizeof(unsigned) * 4, st));
-    NDHSS_CUDA_TRY(cudaMemsetAsync(x, 0, sizeof(V) * n, st));
+    GmStatus* hst = pinned_status();
+    if (!hst) return set_error(NDHSS_ERR_OOM, "ndhss_gmres: pinned status words");
+    hst[0] = hst[1] = GmStatus{0, 0, 0, 0};
     const int eb = std::min((n + 255) / 256, 4 * 152);
-    ndhss_status rc;
-    double hb[4];
+    const unsigned sblocks = (unsigned)(((int64_t)n * 4 + 255) / 256);
+    gm_init_kernel<V><<<1, 1, 0, st>>>(S, R, o.maxit, o.tol, o.inner, o.cycle_rtol);
+    NDHSS_LAUNCH_CHECK("gm_init_kernel");
+    NDHSS_CUDA_TRY(cudaMemsetAsync(x, 0, sizeof(V) * n, st));
 
-    auto read_scalars = [&](const void* src, size_t bytes, void* dst) -> ndhss_status {
-        NDHSS_CUDA_TRY(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, st));
-        NDHSS_CUDA_TRY(cudaStreamSynchronize(st));
-        return NDHSS_OK;
-    };
-
-    ndhss_gmres_stats S{};
-    // optional CUDA-event timing of every apply and sparse product
-    // events come from a per-thread pool that lives as long as the thread, so
-    // timing adds two records per product and no event creation
+    // optional CUDA-event timing of every apply and sparse product; events
+    // come from a per-thread pool that lives as long as the thread
     thread_local std::vector<cudaEvent_t> pool;
     size_t pool_next = 0;
-    std::vector<cudaEvent_t> ev_apply, ev_spmv;
-    auto event_pair = [&](std::vector<cudaEvent_t>& v) -> ndhss_status {
-        for (int q = 0; q < 2; ++q) {
-            if (pool_next == pool.size()) {
-                cudaEvent_t e;
-                NDHSS_CUDA_TRY(cudaEventCreate(&e));
-                pool.push_back(e);
+    auto ev = [&]() -> cudaEvent_t {
+        if (pool_next == pool.size()) {
+            cudaEvent_t e;
+            if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+            pool.push_back(e);
+        }
+        return pool[pool_next++];
+    };
+    std::vector<cudaEvent_t> evs;             // per block: SpMV start, end, apply start, end
+    cudaEvent_t blk_done[2] = {nullptr, nullptr};
+    if (cudaEventCreateWithFlags(&blk_done[0], cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&blk_done[1], cudaEventDisableTiming) != cudaSuccess)
+        return set_error(NDHSS_ERR_CUDA, "ndhss_gmres: event creation failed");
+    ndhss_status rc = NDHSS_OK;
+    const int max_blocks = std::min(GM_MAX_BLOCKS, 2 * o.maxit + 4);
+    int nblk = 0;
+    for (int blk = 0; blk < max_blocks && rc == NDHSS_OK; ++blk) {
+        gm_begin_kernel<V><<<eb, 256, 0, st>>>(S, x, Vb, ldv, t, r, n, blk);
+        note_launches(1);
+        cudaEvent_t e0 = nullptr, e1 = nullptr, e2 = nullptr, e3 = nullptr;
+        if (o.timing) { e0 = ev(); e1 = ev(); e2 = ev(); e3 = ev(); }
+        if (e0) cudaEventRecord(e0, st);
+        gm_spmv_kernel<V, 4, 4><<<sblocks, 256, 0, st>>>(n, rowptr, col, vals, S);
+        note_launches(1);
+        if (e1) cudaEventRecord(e1, st);
+        gm_resid_kernel<V><<<RB, RT, 0, st>>>(S, b, t, r, n, dpart, blk);
+        note_launches(1);
+        if (e2) cudaEventRecord(e2, st);
+        rc = apply_device(F, 1, nullptr, n, nullptr, n, awork, st, &S->ind);
+        if (rc != NDHSS_OK) break;
+        if (e3) cudaEventRecord(e3, st);
+        gm_dot_kernel<V><<<RB, RT, 0, st>>>(S, Vb, ldv, n, part, dpart);
+        gm_axdot_kernel<V><<<RB, RT, 0, st>>>(S, Vb, ldv, n, part);
+        gm_axnorm_kernel<V><<<RB, RT, 0, st>>>(S, Vb, ldv, n, dpart, hst + (blk & 1));
+        note_launches(3);
+        cudaError_t le = cudaGetLastError();
+        if (le != cudaSuccess) {
+            rc = set_error(NDHSS_ERR_CUDA, "ndhss_gmres: launch failed: %s", cudaGetErrorString(le));
+            break;
+        }
+        if (o.timing) evs.insert(evs.end(), {e0, e1, e2, e3});
+        cudaEventRecord(blk_done[blk & 1], st);
+        nblk = blk + 1;
+        if (blk >= 1) {
+            // the previous block's status while this one runs
+            if (cudaEventSynchronize(blk_done[(blk - 1) & 1]) != cudaSuccess) {
+                rc = set_error(NDHSS_ERR_CUDA, "ndhss_gmres: event synchronisation failed");
+                break;
             }
-            v.push_back(pool[pool_next++]);
+            if (((volatile GmStatus*)hst)[(blk - 1) & 1].done) break;
         }
-        return NDHSS_OK;
-    };
-    auto timed_apply = [&](const V* in, V* outv) -> ndhss_status {
-        ndhss_status r2;
-        if (o.timing) {
-            if ((r2 = event_pair(ev_apply))) return r2;
-            cudaEventRecord(ev_apply[ev_apply.size() - 2], st);
-        }
-        if ((r2 = apply_device(F, 1, in, n, outv, n, awork, st))) return r2;
-        if (o.timing) cudaEventRecord(ev_apply.back(), st);
-        S.napply++;
-        return NDHSS_OK;
-    };
-    auto timed_spmv = [&](const V* in, V* outv) -> ndhss_status {
-        ndhss_status r2;
-        if (o.timing) {
-            if ((r2 = event_pair(ev_spmv))) return r2;
-            cudaEventRecord(ev_spmv[ev_spmv.size() - 2], st);
-        }
-        if ((r2 = spmv_launch<V>(n, rowptr, col, vals, in, outv, st))) return r2;
-        if (o.timing) cudaEventRecord(ev_spmv.back(), st);
-        S.nspmv++;
-        return NDHSS_OK;
-    };
-    auto collect = [&]() {
-        if (!o.timing) return;
-        cudaStreamSynchronize(st);
+    }
+    GmDev<V> hs;
+    if (rc == NDHSS_OK) {
+        if (cudaMemcpyAsync(&hs, S, sizeof(GmDev<V>), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+            cudaStreamSynchronize(st) != cudaSuccess)
+            rc = set_error(NDHSS_ERR_CUDA, "ndhss_gmres: reading the solver state failed");
+    }
+    cudaEventDestroy(blk_done[0]);
+    cudaEventDestroy(blk_done[1]);
+    if (rc != NDHSS_OK) return rc;
+    if (hs.done == 3) return set_error(NDHSS_ERR_INTERNAL, "ndhss_gmres: P^{-1} b vanished");
+    ndhss_gmres_stats Sx{};
+    Sx.converged = hs.done == 1;
+    Sx.iters = hs.its;
+    Sx.cycles = hs.cycles;
+    Sx.true_relres = hs.relres;
+    Sx.precond_relres = hs.last_res;
+    for (int blk = 0; blk < nblk; ++blk) {
+        Sx.nspmv += (hs.ran[blk] & 1) ? 1 : 0;
+        Sx.napply += (hs.ran[blk] & 2) ? 1 : 0;
+    }
+    if (o.timing) {
         float ms;
-        for (size_t i = 0; i + 1 < ev_apply.size(); i += 2)
-            if (cudaEventElapsedTime(&ms, ev_apply[i], ev_apply[i + 1]) == cudaSuccess) S.apply_ms += ms;
-        for (size_t i = 0; i + 1 < ev_spmv.size(); i += 2)
-            if (cudaEventElapsedTime(&ms, ev_spmv[i], ev_spmv[i + 1]) == cudaSuccess) S.spmv_ms += ms;
-        ev_apply.clear();
-        ev_spmv.clear();
-        pool_next = 0;
-    };
-    nrm2_kernel<V><<<RB, RT, 0, st>>>(n, b, dpart, nrm, counter);
-    NDHSS_LAUNCH_CHECK("nrm2_kernel");
-    if ((rc = read_scalars(nrm, sizeof(double), hb))) return rc;
-    const double bnorm = sqrt(hb[0]);
-    if (bnorm == 0.0) {
-        S.converged = 1;
-        if (stats) *stats = S;
-        return NDHSS_OK;
+        for (int blk = 0; blk < nblk && 4 * blk + 3 < (int)evs.size(); ++blk) {
+            if ((hs.ran[blk] & 1) && cudaEventElapsedTime(&ms, evs[4 * blk], evs[4 * blk + 1]) == cudaSuccess)
+                Sx.spmv_ms += ms;
+            if ((hs.ran[blk] & 2) && cudaEventElapsedTime(&ms, evs[4 * blk + 2], evs[4 * blk + 3]) == cudaSuccess)
+                Sx.apply_ms += ms;
+        }
     }
-    double zbnorm = -1.0;
-    int its = 0, cycles = 0;
-    double last_res = 1.0;
-    // After a cycle that did not halve the true residual (a preconditioner
-    // whose ||P^{-1} r|| / ||P^{-1} b|| no longer tracks ||r|| / ||b||), a cycle
-    // no longer ends on cycle_rtol or on the inner test against ||P^{-1} b||,
-    // but once its residual estimate fell by the factor the true residual
-    // still needs (0.1 tol / relres), relative to the cycle's start.
-    double rtol_eff = o.cycle_rtol, prev_rel = INFINITY, cyc_target = 0.0;
-    while (true) {
-        if ((rc = timed_spmv(x, t))) return rc;
-        residual_kernel<V><<<eb, 256, 0, st>>>(n, b, t, r);
-        NDHSS_LAUNCH_CHECK("residual_kernel");
-        nrm2_kernel<V><<<RB, RT, 0, st>>>(n, r, dpart, nrm, counter);
-        NDHSS_LAUNCH_CHECK("nrm2_kernel");
-        if ((rc = read_scalars(nrm, sizeof(double), hb))) return rc;
-        const double rel = sqrt(hb[0]) / bnorm;
-        S.true_relres = rel;
-        if (rel <= o.tol) { S.converged = 1; break; }
-        if (its >= o.maxit) break;
-        if (rel > 0.5 * prev_rel) {
-            rtol_eff = 0.0;
-            cyc_target = 0.1 * o.tol / rel;
-        } else if (cyc_target > 0.0) {
-            cyc_target = 0.1 * o.tol / rel;
-        }
-        prev_rel = rel;
-        ++cycles;
-        if ((rc = timed_apply(r, w))) return rc;
-        nrm2_kernel<V><<<RB, RT, 0, st>>>(n, w, dpart, nrm, counter);
-        NDHSS_LAUNCH_CHECK("nrm2_kernel");
-        cycle_init_kernel<V><<<1, 1, 0, st>>>(nrm, g, R, stt);
-        NDHSS_LAUNCH_CHECK("cycle_init_kernel");
-        scale_kernel<V><<<eb, 256, 0, st>>>(n, w, Vb, &stt->scal[0]);
-        NDHSS_LAUNCH_CHECK("scale_kernel");
-        if (zbnorm < 0) {
-            if ((rc = read_scalars(stt, sizeof(GmState), hb))) return rc;
-            zbnorm = hb[3];
-            if (zbnorm == 0.0) return set_error(NDHSS_ERR_INTERNAL, "ndhss_gmres: P^{-1} b vanished");
-        }
-        int jend = 0;
-        for (int j = 0; j < R; ++j) {
-            V* vj = Vb + (int64_t)j * ldv;
-            if ((rc = timed_spmv(vj, t))) return rc;
-            if ((rc = timed_apply(t, w))) return rc;
-            ++its;
-            mdot_kernel<V><<<dim3(RB, j + 1), RT, 0, st>>>(n, Vb, ldv, j + 1, w, part, h1, counter);
-            NDHSS_LAUNCH_CHECK("mdot_kernel");
-            maxpy_kernel<V><<<eb, 256, 0, st>>>(n, w, Vb, ldv, j + 1, h1, -1.0);
-            NDHSS_LAUNCH_CHECK("maxpy_kernel");
-            mdot_kernel<V><<<dim3(RB, j + 1), RT, 0, st>>>(n, Vb, ldv, j + 1, w, part, h2, counter);
-            NDHSS_LAUNCH_CHECK("mdot_kernel");
-            maxpy_kernel<V><<<eb, 256, 0, st>>>(n, w, Vb, ldv, j + 1, h2, -1.0);
-            NDHSS_LAUNCH_CHECK("maxpy_kernel");
-            nrm2_kernel<V><<<RB, RT, 0, st>>>(n, w, dpart, nrm, counter);
-            NDHSS_LAUNCH_CHECK("nrm2_kernel");
-            arnoldi_step_kernel<V><<<1, 1, 0, st>>>(j, H, R + 1, h1, h2, nrm, g, cs, sn, stt);
-            NDHSS_LAUNCH_CHECK("arnoldi_step_kernel");
-            scale_kernel<V><<<eb, 256, 0, st>>>(n, w, Vb + (int64_t)(j + 1) * ldv, &stt->scal[0]);
-            NDHSS_LAUNCH_CHECK("scale_kernel");
-            if ((rc = read_scalars(stt, sizeof(GmState), hb))) return rc;
-            jend = j + 1;
-            last_res = hb[1] / zbnorm;
-            const bool inner_done = cyc_target > 0.0 ? hb[1] <= cyc_target * hb[3] : last_res <= o.inner * o.tol;
-            if (inner_done || hb[1] <= rtol_eff * hb[3] || hb[2] == 0.0 || its >= o.maxit) break;
-        }
-        hsolve_kernel<V><<<1, 1, 0, st>>>(jend, H, R + 1, g, yv);
-        NDHSS_LAUNCH_CHECK("hsolve_kernel");
-        maxpy_kernel<V><<<eb, 256, 0, st>>>(n, x, Vb, ldv, jend, yv, 1.0);
-        NDHSS_LAUNCH_CHECK("maxpy_kernel");
-    }
-    collect();
-    S.iters = its;
-    S.cycles = cycles;
-    S.precond_relres = last_res;
-    if (stats) *stats = S;
+    if (stats) *stats = Sx;
     return NDHSS_OK;
 }
 
@@ -496,10 +773,11 @@ size_t gmres_work_bytes(const FactorData& F, int R, size_t vsz) {
     size_t b = 0;
     auto add = [&](size_t x) { b += (x + 255) / 256 * 256; };
     add(vsz * ldv * (R + 1));
-    add(vsz * F.n); add(vsz * F.n); add(vsz * F.n);
-    add(vsz * (R + 1) * R); add(vsz * (R + 1)); add(8 * R); add(vsz * R);
-    add(vsz * KMAX); add(vsz * KMAX); add(vsz * KMAX);
-    add(vsz * RB * KMAX); add(8 * RB); add(32); add(16); add(sizeof(GmState));
+    add(vsz * F.n);
+    add(vsz * F.n);
+    add(vsz * RB * KMAX);
+    add(8 * RB);
+    add(std::max(sizeof(GmDev<double>), sizeof(GmDev<c128>)));
     add(apply_work_bytes(F));
     return b;
 }
@@ -537,11 +815,12 @@ ndhss_status ndhss_gmres(const ndhss_factorization* fh, const int32_t* d_rowptr,
         if (ldb < F.n || ldx < F.n) return set_error(NDHSS_ERR_INVALID_ARG, "ndhss_gmres: leading dimension < n");
         ndhss_gmres_opts o{30, 300, 1e-8, 0, 0, 0.1, -1.0};
         if (opts) o = *opts;
-        if (o.restart < 1 || o.restart > KMAX - 1 || o.maxit < 0 || !(o.tol >= 0) || !(o.inner > 0 && o.inner <= 1) ||
+        if (o.restart < 1 || o.restart > KMAX - 1 || o.maxit < 0 || o.maxit > GM_MAX_IT || !(o.tol >= 0) ||
+            !(o.inner > 0 && o.inner <= 1) ||
             o.conj_transpose < 0 || o.conj_transpose > 1)
             return set_error(NDHSS_ERR_INVALID_ARG,
-                             "ndhss_gmres: need 1 <= restart <= %d, maxit >= 0, tol >= 0, 0 < inner <= 1, conj_transpose 0 or 1",
-                             KMAX - 1);
+                             "ndhss_gmres: need 1 <= restart <= %d, 0 <= maxit <= %d, tol >= 0, 0 < inner <= 1, "
+                             "conj_transpose 0 or 1", KMAX - 1, GM_MAX_IT);
         if (nrhs == 0) return NDHSS_OK;
         if (o.cycle_rtol < 0) o.cycle_rtol = (F.prec == NDHSS_FP64) ? 0.0 : 1e-3;
         cudaStream_t st = static_cast<cudaStream_t>(stream);
