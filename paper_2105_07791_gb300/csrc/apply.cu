@@ -167,6 +167,23 @@ struct Pre {
     int gi, pi;
 };
 
+// ---- L2 prefetch of read-only factor data ---------------------------------
+// One prefetch request per 128-byte line of [p, p + bytes); each request
+// names an address inside the range (the first byte, then line starts), so
+// none leaves the buffer.  Requests q0, q0 + step, ... of the range's lines.
+__device__ __forceinline__ void prefetch_l2(const void* p) {
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+__device__ __forceinline__ int range_lines(const void* p, int64_t bytes) {
+    if (bytes <= 0) return 0;
+    const uintptr_t a = reinterpret_cast<uintptr_t>(p);
+    return (int)(((a + bytes - 1) >> 7) - (a >> 7) + 1);
+}
+__device__ __forceinline__ void prefetch_line(const void* p, int l) {
+    const uintptr_t a = reinterpret_cast<uintptr_t>(p);
+    prefetch_l2(l == 0 ? p : reinterpret_cast<const void*>(((a >> 7) + l) << 7));
+}
+
 // ---- 64-row GEMV ----------------------------------------------------------
 // Rows [r0, r0 + 64) of (block A, column-major, leading dimension lda) times
 // the vector xs (shared memory): 8 warps take every 8th column, each lane
@@ -186,6 +203,17 @@ __device__ __forceinline__ void gemv_pre(const T* __restrict__ A, int64_t lda, i
         const T* col = A + (int64_t)c * lda;
         pre[u] = (c < cols && ra < rows) ? col[ra] : zero<T>();
         pre[4 + u] = (c < cols && rb < rows) ? col[rb] : zero<T>();
+    }
+    // the rest of the 64-row segment into L2 while the task waits
+    const int nr = min(APPLY_ROWS, rows - r0);
+    if (nr > 0 && cols > 4 * AW) {
+        constexpr int LPC = (APPLY_ROWS * (int)sizeof(T) + 127) / 128 + 1;   // lines a segment can touch
+        const int tot = (cols - 4 * AW) * LPC;
+        for (int q = threadIdx.x; q < tot; q += AT) {
+            const T* seg = A + (int64_t)(4 * AW + q / LPC) * lda + r0;
+            const int l = q % LPC;
+            if (l < range_lines(seg, (int64_t)nr * sizeof(T))) prefetch_line(seg, l);
+        }
     }
 }
 
@@ -450,24 +478,56 @@ __device__ __forceinline__ void ulv_task(const ApplyCtx<T>& C, const Entry& e, c
 // vec holds [z or y rows lo .. lo + nI) | B^root slots | staged inputs | partials].
 constexpr int SUB_HDR = 2, SUB_LREC = 6, SUB_NREC = 10;
 
+struct Sched;
+// bounded wait of one thread for every gather task (defined with the queue)
+__device__ bool wait_gather(const Sched* S);
+
 template <typename T, typename V>
 __device__ void subtree_task(const ApplyCtx<T>& C, const Entry& e, int* idx, T* vec, const V* __restrict__ x,
-                             V* __restrict__ out, T* y, T* z) {
+                             V* __restrict__ out, T* y, T* z, const Sched* Sp) {
     const bool up = e.kind == TK_SUBUP;
     const int tid = threadIdx.x;
     const int lo = e.a, nI = e.b, mbr = e.m_b;
     const int tlen = e.k;
+    // the set-up loads go out in batches of four, so a thread waits for
+    // memory once per batch
     {
-        const int32_t* g = C.sublist + e.aux;
-        for (int i = tid; i < tlen; i += AT) idx[i] = g[i];
+        const int32_t* __restrict__ g = C.sublist + e.aux;
+        for (int i0 = 0; i0 < tlen; i0 += 4 * AT) {
+            int v[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int i = i0 + tid + u * AT;
+                v[u] = i < tlen ? g[i] : 0;
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                if (i0 + tid + u * AT < tlen) idx[i0 + tid + u * AT] = v[u];
+        }
     }
-    if (up) {
-        for (int i = tid; i < nI; i += AT) vec[i] = from_val<T>(x[C.perm[lo + i]]);
-        for (int j = tid; j < mbr; j += AT) vec[nI + j] = zero<T>();
-    } else {
-        for (int i = tid; i < nI; i += AT) vec[i] = ldw(z + lo + i);
-        for (int j = tid; j < mbr; j += AT) vec[nI + j] = ldw(z + C.blist[e.b_off + j]);
+    for (int i0 = 0; i0 < nI; i0 += 4 * AT) {
+        int pi[4];
+        T v[4];
+        if (up) {
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int i = i0 + tid + u * AT;
+                pi[u] = i < nI ? C.perm[lo + i] : -1;
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) v[u] = pi[u] >= 0 ? from_val<T>(x[pi[u]]) : zero<T>();
+        } else {
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int i = i0 + tid + u * AT;
+                v[u] = i < nI ? ldw(z + lo + i) : zero<T>();
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+            if (i0 + tid + u * AT < nI) vec[i0 + tid + u * AT] = v[u];
     }
+    for (int j = tid; j < mbr; j += AT) vec[nI + j] = up ? zero<T>() : ldw(z + C.blist[e.b_off + j]);
     __syncthreads();
     const int nl = idx[0], nn = idx[1];
     const int* lrec = idx + SUB_HDR;
@@ -480,15 +540,29 @@ __device__ void subtree_task(const ApplyCtx<T>& C, const Entry& e, int* idx, T* 
     }
     const int* src_dn = src_up + n_src_up;
     const int* dst_up = src_dn;           // an up-sweep B row adds into the slot its down input reads
-    if (up) {
-        // up inputs: (interior slot << 12 | column c) -> the slot of row sigma(c)
-        int* su = const_cast<int*>(src_up);
-        for (int q = tid; q < n_src_up; q += AT) {
-            const int v = su[q], sl = v >> 12;
-            su[q] = sl + C.sigma[lo + sl + (v & 4095)];
+    // the matrix data of level hh (in sweep order) into L2: up, [A_ii^{-1}; -L]
+    // of each node (m x m_i, contiguous); down, the m_i rows of each column of R
+    auto prefetch_level = [&](int hh) {
+        if (hh >= nl) return;
+        const int* L = lrec + SUB_LREC * (up ? hh : nl - 1 - hh);
+        for (int j = 0; j < L[0]; ++j) {
+            const int* nd = nrec + SUB_NREC * (L[1] + j);
+            const int mi = nd[0], mb = nd[1];
+            const int64_t m = (int64_t)mi + mb;
+            const T* F = C.front + (int64_t)(((uint64_t)(uint32_t)nd[3] << 32) | (uint32_t)nd[2]);
+            if (up) {
+                const int nlines = range_lines(F, m * mi * (int64_t)sizeof(T));
+                for (int l = tid; l < nlines; l += AT) prefetch_line(F, l);
+            } else if (mi > 0) {
+                const int lpc = (int)((mi * (int64_t)sizeof(T) + 127) / 128) + 1;
+                for (int q = tid; q < mb * lpc; q += AT) {
+                    const T* seg = F + (int64_t)(mi + q / lpc) * m;
+                    if (q % lpc < range_lines(seg, mi * (int64_t)sizeof(T))) prefetch_line(seg, q % lpc);
+                }
+            }
         }
-        __syncthreads();
-    }
+    };
+    prefetch_level(0);
     T* xin = vec + nI + mbr;
     T* part = xin + SUB_XIN;
     // first staged input / first up output of each level
@@ -496,6 +570,7 @@ __device__ void subtree_task(const ApplyCtx<T>& C, const Entry& e, int* idx, T* 
     if (!up)
         for (int h = 0; h < nl; ++h) sx_dn += lrec[SUB_LREC * h + 5];
     for (int hh = 0; hh < nl; ++hh) {
+        prefetch_level(hh + 1);
         const int h = up ? hh : nl - 1 - hh;              // the table lists the deepest level first
         const int* L = lrec + SUB_LREC * h;
         const int cnt = L[0], n0 = L[1];
@@ -522,6 +597,8 @@ __device__ void subtree_task(const ApplyCtx<T>& C, const Entry& e, int* idx, T* 
             const T* A = C.front + foff + (up ? 0 : (int64_t)mi * m) + r;
             const int cols = up ? mi : mb;
             const T* xs = xin + nd[up ? 5 : 7];
+            // rounds of eight loads, the ragged last one predicated: it costs one
+            // memory wait, not one per column
             T acc = zero<T>();
             int c = p;
             for (; c + 7 * qp < cols; c += 8 * qp) {
@@ -531,7 +608,13 @@ __device__ void subtree_task(const ApplyCtx<T>& C, const Entry& e, int* idx, T* 
 #pragma unroll
                 for (int u = 0; u < 8; ++u) acc = fmac(a[u], xs[c + u * qp], acc);
             }
-            for (; c < cols; c += qp) acc = fmac(A[(int64_t)c * m], xs[c], acc);
+            if (c < cols) {
+                T a[7];
+#pragma unroll
+                for (int u = 0; u < 7; ++u) a[u] = c + u * qp < cols ? A[(int64_t)(c + u * qp) * m] : zero<T>();
+#pragma unroll
+                for (int u = 0; u < 7; ++u) acc = fmac(a[u], c + u * qp < cols ? xs[c + u * qp] : zero<T>(), acc);
+            }
             if (qp > 1) {
                 part[ee] = acc;
             } else if (up) {
@@ -565,14 +648,31 @@ __device__ void subtree_task(const ApplyCtx<T>& C, const Entry& e, int* idx, T* 
         __syncthreads();
     }
     if (up) {
-        // the subtree's part of y(B^root) (the gather of those rows has finished:
-        // the task waited for it)
+        // the subtree's part of y(B^root), once the gather has written those
+        // rows (the task reads x itself, so only this step waits for it;
+        // one launch per level has run the gather before)
+        if (Sp) {
+            __shared__ int s_gok;
+            if (tid == 0) s_gok = wait_gather(Sp) ? 1 : 0;
+            __syncthreads();
+            if (!s_gok) return;
+        }
         for (int j = tid; j < mbr; j += AT) {
             const int g = C.blist[e.b_off + j];
             stw(y + g, ldw(y + g) + vec[nI + j]);
         }
     } else {
-        for (int i = tid; i < nI; i += AT) out[C.perm[lo + i]] = to_val(vec[i]);
+        for (int i0 = 0; i0 < nI; i0 += 4 * AT) {
+            int pi[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int i = i0 + tid + u * AT;
+                pi[u] = i < nI ? C.perm[lo + i] : -1;
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                if (pi[u] >= 0) out[pi[u]] = to_val(vec[i0 + tid + u * AT]);
+        }
     }
 }
 
@@ -647,6 +747,14 @@ __device__ __forceinline__ void task_pre(const ApplyCtx<T>& C, const Entry& e, P
             const int i = lane + 32 * u;
             P.v[u] = (a < k && i < rn) ? M[(int64_t)a * len + i] : zero<T>();
         }
+        if (sizeof(T) <= 8) {                 // the column the warp loads after the wait, into L2
+            const int a1 = a + AW;
+            if (a1 < k) {
+                const T* seg = M + (int64_t)a1 * len;
+                const int nl = range_lines(seg, (int64_t)rn * sizeof(T));
+                for (int l = lane; l < nl; l += 32) prefetch_line(seg, l);
+            }
+        }
         if (!up)
             for (int i = tid; i < rn; i += AT) idx[i] = C.blist[b_off + e.a + i];
         break;
@@ -676,7 +784,8 @@ __device__ __forceinline__ void task_pre(const ApplyCtx<T>& C, const Entry& e, P
 template <typename T, typename V>
 __device__ __forceinline__ void task_run(const ApplyCtx<T>& C, const Entry& e, const Pre<T>& P, const int* idx, T* vec,
                                          T (*red)[APPLY_ROWS], const int (*wd)[8], int n, const V* __restrict__ x,
-                                         V* __restrict__ out, T* y, T* z, T* tup, T* tdn, T* dpart, T* us) {
+                                         V* __restrict__ out, T* y, T* z, T* tup, T* tdn, T* dpart, T* us,
+                                         const Sched* Sp) {
     const int s = e.s;
     const int tid = threadIdx.x;
     if (e.kind == TK_GATHER) {
@@ -707,7 +816,7 @@ __device__ __forceinline__ void task_run(const ApplyCtx<T>& C, const Entry& e, c
         return;
     }
     if (e.kind == TK_SUBUP || e.kind == TK_SUBDN) {
-        subtree_task<T, V>(C, e, const_cast<int*>(idx), vec, x, out, y, z);
+        subtree_task<T, V>(C, e, const_cast<int*>(idx), vec, x, out, y, z, Sp);
         return;
     }
     const int m_i = e.m_i, m_b = e.m_b, i_off = e.i_off;
@@ -879,19 +988,22 @@ __device__ __forceinline__ int hd_index(const Sched& S, int rec) { return NCNT *
 // CTA reported a failure.
 __device__ bool wait_geq(const Sched& S, const int32_t* ctr, int need, uint64_t& t0) {
     if (need <= 0 || ld_acquire(ctr) >= need) return true;
-    unsigned sleep = 32;
-    for (;;) {
+    // short sleeps while the wait is young (a dependency in the low-rank
+    // chain is usually a few microseconds away), the abort flag and the clock
+    // every 16th poll
+    for (unsigned it = 0;; ++it) {
         if (ld_acquire(ctr) >= need) return true;
-        if (ld_acquire(S.ctl + 2)) return false;
-        __nanosleep(sleep);
-        if (sleep < 256) sleep *= 2;
-        const uint64_t now = global_ns();
-        if (t0 == 0) t0 = now;
-        else if (now - t0 > APPLY_WAIT_NS) {
-            atomicExch(S.ctl + 2, 1);
-            atomicExch(S.err, 1);
-            return false;
+        if ((it & 15) == 15) {
+            if (ld_relaxed(S.ctl + 2)) return false;
+            const uint64_t now = global_ns();
+            if (t0 == 0) t0 = now;
+            else if (now - t0 > APPLY_WAIT_NS) {
+                atomicExch(S.ctl + 2, 1);
+                atomicExch(S.err, 1);
+                return false;
+            }
         }
+        __nanosleep(it < 64 ? 20 : 200);
     }
 }
 
@@ -952,10 +1064,7 @@ __device__ __forceinline__ Deps task_deps(const Sched& S, const int32_t* node, c
         d.need[0] = S.need[hd_index(S, e.i_off)];
         d.n = 1;
         break;
-    case TK_SUBUP:                                  // y(B^root) is added to after the gather
-        d.c[0] = S.ctl + 1;
-        d.need[0] = S.ngather;
-        d.n = 1;
+    case TK_SUBUP:                                  // waits for the gather only before adding to y(B^root)
         break;
     case TK_SUBDN: {                                // the root's parent final, the subtree's up done
         const int p = nf(node, s, 1);
@@ -968,14 +1077,16 @@ __device__ __forceinline__ Deps task_deps(const Sched& S, const int32_t* node, c
     return d;
 }
 
-// All requirements read at once with relaxed loads (the common case: already
-// met), then a fence for acquire ordering; otherwise bounded spins.
+// All requirements read at once with acquire loads (the common case: already
+// met), otherwise bounded spins with acquire loads.  The waiting thread's
+// acquire and the CTA barrier after it order the task's reads after the
+// producers' release fences.
 __device__ bool wait_deps(const Sched& S, const int32_t* node, const Entry& e) {
     if (ld_relaxed(S.ctl + 2) || ld_relaxed(S.err)) return false;
     const Deps d = task_deps(S, node, e);
     int v[3];
 #pragma unroll
-    for (int i = 0; i < 3; ++i) v[i] = (i < d.n) ? ld_relaxed(d.c[i]) : 0;
+    for (int i = 0; i < 3; ++i) v[i] = (i < d.n) ? ld_acquire(d.c[i]) : 0;
     bool met = true;
 #pragma unroll
     for (int i = 0; i < 3; ++i) met = met && (i >= d.n || v[i] >= d.need[i]);
@@ -985,8 +1096,12 @@ __device__ bool wait_deps(const Sched& S, const int32_t* node, const Entry& e) {
         for (int i = 0; i < 3; ++i)
             if (i < d.n && !wait_geq(S, d.c[i], d.need[i], t0)) return false;
     }
-    __threadfence();
     return true;
+}
+
+__device__ bool wait_gather(const Sched* S) {
+    uint64_t t0 = 0;
+    return wait_geq(*S, S->ctl + 1, S->ngather, t0);
 }
 
 // Dependencies of a warp-node task, checked by warp 0: lane j < e.a waits for
@@ -1077,7 +1192,7 @@ __global__ void __launch_bounds__(AT, apply_min_blocks<T>()) apply_dataflow_kern
         }
         __syncthreads();
         if (!s_ok) break;
-        task_run<T, V>(C, e, P, idx, vec, red, wd, n, x, out, y, z, tup, tdn, dpart, us);
+        task_run<T, V>(C, e, P, idx, vec, red, wd, n, x, out, y, z, tup, tdn, dpart, us, &S);
         // publish: the barrier orders every thread's stores before the
         // signalling threads' gpu-scope fences, which order them before the
         // signals
@@ -1131,7 +1246,7 @@ __global__ void __launch_bounds__(AT, apply_min_blocks<T>()) apply_group_kernel(
     const Entry e = decode(q, blockIdx.x);
     Pre<T> P;
     task_pre(C, e, P, idx, wd);
-    task_run<T, V>(C, e, P, idx, vec, red, wd, n, x, out, y, z, tup, tdn, dpart, us);
+    task_run<T, V>(C, e, P, idx, vec, red, wd, n, x, out, y, z, tup, tdn, dpart, us, nullptr);
 }
 
 bool levels_schedule_requested() {
@@ -1324,6 +1439,13 @@ ndhss_status build_apply_schedule(FactorData& F, cudaStream_t st) {
             while (Ls <= F.depth && (int)F.levels[Ls].size() < SUB_MIN_ROOTS) ++Ls;
         }
         if (Ls <= F.depth) {
+            // the pivot order of every interior block (final: the factorization
+            // has synchronised) resolves the staged inputs of the up sweep here
+            std::vector<int32_t> sig_h(std::max(F.n, 1));
+            cudaError_t ce = cudaMemcpyAsync(sig_h.data(), F.d_sigma, sizeof(int32_t) * (size_t)F.n,
+                                             cudaMemcpyDeviceToHost, st);
+            if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
+            if (ce != cudaSuccess) return set_error(NDHSS_ERR_CUDA, "apply: %s", cudaGetErrorString(ce));
             for (int r : F.levels[Ls]) {
                 const int lo = F.info(first[r], 4);
                 const int nI = (int)ni[r];
@@ -1352,9 +1474,9 @@ ndhss_status build_apply_schedule(FactorData& F, cudaStream_t st) {
                         const int32_t nd[SUB_NREC] = {F.m_i(s), F.m_b(s), (int32_t)(uint32_t)fo, (int32_t)(uint32_t)(fo >> 32),
                                                       ru, xu, rd, xd, F.info(s, 4) - lo, bo};
                         nrec.insert(nrec.end(), nd, nd + SUB_NREC);
-                        // (interior slot << 12 | column): the task resolves the column
-                        // through sigma when it loads the table
-                        for (int c = 0; c < F.m_i(s); ++c) src_up.push_back(((F.info(s, 4) - lo) << 12) | c);
+                        // column c of A_ii^{-1} multiplies interior row sigma(c)
+                        for (int c = 0; c < F.m_i(s); ++c)
+                            src_up.push_back(F.info(s, 4) - lo + sig_h[F.info(s, 4) + c]);
                         for (int j = 0; j < F.m_b(s); ++j) {
                             const int sl = bslot_of(s, j);
                             if (sl < 0)
