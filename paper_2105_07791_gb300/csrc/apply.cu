@@ -65,6 +65,7 @@ constexpr int AW = AT / 32;
 constexpr int GATHER_CHUNK = 8 * AT;
 constexpr int DIAG_COLS = 256;    // column chunk of A_ii^{-1} per task (and fused-pass limit)
 constexpr int SUM_ROWS = AT;      // rows per partial-sum task
+constexpr int DIAG_LAG = 2;       // levels a node's diagonal tasks are queued behind its up-sweep
 constexpr uint64_t APPLY_WAIT_NS = 2000000000ull;   // 2 s
 
 __device__ __forceinline__ int nf(const int32_t* node, int s, int f) { return node[s * NODE_NF + f]; }
@@ -887,15 +888,13 @@ __device__ __forceinline__ void task_run(const ApplyCtx<T>& C, const Entry& e, c
         const int k = e.k;
         const int len = up ? m_i : m_b;
         const int rn = min(LR_CHUNK, len - e.a);
-        for (int i = tid; i < rn; i += AT) vec[i] = up ? ldw(y + i_off + e.a + i) : ldw(z + idx[i]);
-        __syncthreads();
         const int lane = tid & 31, warp = tid >> 5;
         const T* X = reinterpret_cast<const T*>(e.base);
         const T* M = (up ? X : X + (int64_t)m_i * k) + e.a;
         T* dst = (up ? tup : tdn) + e.aux + (int64_t)(e.a / LR_CHUNK) * k;
         // the task's column group: columns b + warp + v * AW, v < CPS (two per
         // warp for 8-byte types, one for 16-byte types); v = 0 was loaded in
-        // the pre-phase
+        // the pre-phase, v >= 1 goes out together with the input rows
         constexpr int CPS = sizeof(T) <= 8 ? 2 : 1;
         T p[CPS][8];
 #pragma unroll
@@ -905,6 +904,8 @@ __device__ __forceinline__ void task_run(const ApplyCtx<T>& C, const Entry& e, c
                 const int i = lane + 32 * u, av = e.b + warp + v * AW;
                 p[v][u] = (v == 0) ? P.v[u] : ((av < k && i < rn) ? M[(int64_t)av * len + i] : zero<T>());
             }
+        for (int i = tid; i < rn; i += AT) vec[i] = up ? ldw(y + i_off + e.a + i) : ldw(z + idx[i]);
+        __syncthreads();
         T sp[CPS];
 #pragma unroll
         for (int v = 0; v < CPS; ++v) sp[v] = zero<T>();
@@ -931,20 +932,31 @@ __device__ __forceinline__ void task_run(const ApplyCtx<T>& C, const Entry& e, c
         const int len_in = up ? m_i : m_b, len = up ? m_b : m_i;
         const int nch = (len_in + LR_CHUNK - 1) / LR_CHUNK;
         const T* tp = (up ? tup : tdn) + e.aux;
+        const int r = e.a + tid;
+        // the row this thread updates is final once the task's dependencies
+        // are (siblings' B sets are disjoint): its load goes out with the
+        // chunk partials of t, eight chunks at a time
+        T old = zero<T>();
+        if (tid < APPLY_ROWS && r < len) old = up ? ldw(y + P.gi) : ldw(z + i_off + r);
         for (int a = tid; a < k; a += AT) {
-            T acc = ldw(tp + a);
-            for (int c = 1; c < nch; ++c) acc = acc + ldw(tp + (int64_t)c * k + a);
+            T acc = zero<T>();
+            for (int c0 = 0; c0 < nch; c0 += 8) {
+                T pv[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) pv[u] = c0 + u < nch ? ldw(tp + (int64_t)(c0 + u) * k + a) : zero<T>();
+#pragma unroll
+                for (int u = 0; u < 8; ++u) acc = acc + pv[u];
+            }
             vec[a] = acc;
         }
         __syncthreads();
         const T* X = reinterpret_cast<const T*>(e.base);
         const T sum = gemv_rows64(up ? X + (int64_t)m_i * k : X, len, len, k, e.a, vec, red, P.v);
-        const int r = e.a + tid;
         if (tid < APPLY_ROWS && r < len) {
             if (up) {
-                stw(y + P.gi, ldw(y + P.gi) + sum);
+                stw(y + P.gi, old + sum);
             } else {
-                const T v = ldw(z + i_off + r) + sum;
+                const T v = old + sum;
                 stw(z + i_off + r, v);
                 out[P.pi] = to_val(v);
             }
@@ -975,6 +987,7 @@ __device__ __forceinline__ uint64_t global_ns() {
 
 struct Sched {
     const int32_t* q;          // [QW * nq] entries
+    const int4* dep;           // [2 * nq] dependency records (sched_deps_kernel)
     int32_t nq, ngather, nn, nrec;
     const int32_t* need;       // [NCNT * nn + 2 * nrec]
     int32_t* ctl;              // [CTL_WORDS + NCNT * nn + 2 * nrec], zeroed before the launch
@@ -1077,24 +1090,45 @@ __device__ __forceinline__ Deps task_deps(const Sched& S, const int32_t* node, c
     return d;
 }
 
-// All requirements read at once with acquire loads (the common case: already
-// met), otherwise bounded spins with acquire loads.  The waiting thread's
-// acquire and the CTA barrier after it order the task's reads after the
-// producers' release fences.
-__device__ bool wait_deps(const Sched& S, const int32_t* node, const Entry& e) {
-    if (ld_relaxed(S.ctl + 2) || ld_relaxed(S.err)) return false;
-    const Deps d = task_deps(S, node, e);
+// The dependency record of every queue entry, written once per schedule
+// (and again when a requirement changes): counter words relative to ctl and
+// their count, then the requirements.  A task's wait then reads its counters
+// in one round of loads instead of walking the node table first.
+__global__ void sched_deps_kernel(Sched S, const int32_t* __restrict__ node, int4* __restrict__ dep) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= S.nq) return;
+    const Entry e = decode(S.q, t);
+    Deps d;
+    d.n = 0;
+    if (e.kind != TK_UPW && e.kind != TK_DNW) d = task_deps(S, node, e);
+    int c[3] = {0, 0, 0}, need[3] = {0, 0, 0};
+    for (int i = 0; i < d.n; ++i) {
+        c[i] = (int)(d.c[i] - S.ctl);
+        need[i] = d.need[i];
+    }
+    dep[2 * t] = make_int4(c[0], c[1], c[2], d.n);
+    dep[2 * t + 1] = make_int4(need[0], need[1], need[2], 0);
+}
+
+// All requirements read at once with acquire loads, together with the abort
+// flags (the common case: already met), otherwise bounded spins with acquire
+// loads.  The waiting thread's acquire and the CTA barrier after it order the
+// task's reads after the producers' release fences.
+__device__ bool wait_deps(const Sched& S, int4 d0, int4 d1) {
+    const int n = d0.w;
+    const int c[3] = {d0.x, d0.y, d0.z}, need[3] = {d1.x, d1.y, d1.z};
     int v[3];
 #pragma unroll
-    for (int i = 0; i < 3; ++i) v[i] = (i < d.n) ? ld_acquire(d.c[i]) : 0;
+    for (int i = 0; i < 3; ++i) v[i] = (i < n) ? ld_acquire(S.ctl + c[i]) : 0;
+    if (ld_relaxed(S.ctl + 2) || ld_relaxed(S.err)) return false;
     bool met = true;
 #pragma unroll
-    for (int i = 0; i < 3; ++i) met = met && (i >= d.n || v[i] >= d.need[i]);
+    for (int i = 0; i < 3; ++i) met = met && (i >= n || v[i] >= need[i]);
     if (!met) {
         uint64_t t0 = 0;
 #pragma unroll
         for (int i = 0; i < 3; ++i)
-            if (i < d.n && !wait_geq(S, d.c[i], d.need[i], t0)) return false;
+            if (i < n && !wait_geq(S, S.ctl + c[i], need[i], t0)) return false;
     }
     return true;
 }
@@ -1172,22 +1206,30 @@ __global__ void __launch_bounds__(AT, apply_min_blocks<T>()) apply_dataflow_kern
     // thread 0 holds the next ticket while the CTA works on the current task:
     // the ticket's atomic overlaps the work (deadlock-free: a held ticket is
     // only waited on by higher tickets, and its holder starts it as soon as
-    // its current task ends)
+    // its current task ends); subtree tasks take theirs at the end
     int next = (threadIdx.x == 0) ? atomicAdd(S.ctl, 1) : 0;
     for (;;) {
         if (threadIdx.x == 0) s_task = next;
         __syncthreads();
         const int t = s_task;
         if (t >= S.nq) break;
+        int4 d0 = make_int4(0, 0, 0, 0), d1 = d0;
+        if (threadIdx.x == 0) {
+            d0 = __ldg(S.dep + 2 * (int64_t)t);
+            d1 = __ldg(S.dep + 2 * (int64_t)t + 1);
+        }
         const Entry e = decode(S.q, t);
         Pre<T> P;
         task_pre(C, e, P, idx, wd);
         const bool warp_nodes = e.kind == TK_UPW || e.kind == TK_DNW;
+        // a subtree task runs for tens of microseconds: the CTA takes its next
+        // ticket when it ends, so no ready task waits behind it
+        const bool long_task = e.kind == TK_SUBUP || e.kind == TK_SUBDN;
         if (warp_nodes ? threadIdx.x < 32 : threadIdx.x == 0) {
-            const bool ok = warp_nodes ? wait_deps_w(S, C.node, C.wdesc, e) : wait_deps(S, C.node, e);
+            const bool ok = warp_nodes ? wait_deps_w(S, C.node, C.wdesc, e) : wait_deps(S, d0, d1);
             if (threadIdx.x == 0) {
                 s_ok = ok ? 1 : 0;
-                if (ok) next = atomicAdd(S.ctl, 1);
+                if (ok && !long_task) next = atomicAdd(S.ctl, 1);
             }
         }
         __syncthreads();
@@ -1197,6 +1239,7 @@ __global__ void __launch_bounds__(AT, apply_min_blocks<T>()) apply_dataflow_kern
         // signalling threads' gpu-scope fences, which order them before the
         // signals
         __syncthreads();
+        if (long_task && threadIdx.x == 0) next = atomicAdd(S.ctl, 1);
         if (warp_nodes) {
             const int lane = threadIdx.x;
             if (lane < e.a) {
@@ -1311,8 +1354,8 @@ ndhss_status apply_run(const FactorData& F, int32_t nrhs, const V* x, int64_t ld
             }
         return NDHSS_OK;
     }
-    Sched S{F.d_sched, (int32_t)F.sched_n, F.sched_ngather, F.nnodes, (int32_t)F.ulv_recs.size(), F.d_need,
-            reinterpret_cast<int32_t*>(w + WL.ctl), F.d_apply_err};
+    Sched S{F.d_sched, reinterpret_cast<const int4*>(F.d_sched_dep), (int32_t)F.sched_n, F.sched_ngather, F.nnodes,
+            (int32_t)F.ulv_recs.size(), F.d_need, reinterpret_cast<int32_t*>(w + WL.ctl), F.d_apply_err};
     const size_t ctl_bytes = sizeof(int32_t) * (CTL_WORDS + (size_t)NCNT * F.nnodes + 2 * F.ulv_recs.size());
     for (int r = 0; r < nrhs; ++r) {
         NDHSS_CUDA_TRY(cudaMemsetAsync(S.ctl, 0, ctl_bytes, st));
@@ -1345,6 +1388,15 @@ ndhss_status launch_shape(FactorData& F) {
 }  // namespace
 
 // Host-built task queue of the apply (see the top of this file).
+ndhss_status fill_sched_deps(const FactorData& F, cudaStream_t st) {
+    const Sched S{F.d_sched, nullptr, (int32_t)F.sched_n, F.sched_ngather, F.nnodes, (int32_t)F.ulv_recs.size(),
+                  F.d_need, nullptr, nullptr};
+    const unsigned blocks = (unsigned)((F.sched_n + 255) / 256);
+    sched_deps_kernel<<<blocks, 256, 0, st>>>(S, F.d_node, reinterpret_cast<int4*>(F.d_sched_dep));
+    NDHSS_LAUNCH_CHECK("sched_deps_kernel");
+    return NDHSS_OK;
+}
+
 ndhss_status build_apply_schedule(FactorData& F, cudaStream_t st) {
     const int nn = F.nnodes;
     if ((int64_t)nn >= (int64_t(1) << TK_SHIFT)) return set_error(NDHSS_ERR_INVALID_ARG, "apply: too many tree nodes");
@@ -1557,7 +1609,47 @@ ndhss_status build_apply_schedule(FactorData& F, cudaStream_t st) {
         push_w(TK_UPW, l);
         cut();
     }
-    for (int l = std::min({F.depth, L_w - 1, Ls - 1}); l >= 0; --l) {
+    // The diagonal step of the nodes not fused into their up-sweep tasks:
+    // column-chunk partial products, then their sums.  Ready with the node's
+    // up-sweep but needed only when the down sweep returns to the node, so a
+    // level's diagonal tasks are queued DIAG_LAG levels further up (the root's
+    // with the root): the low-rank chain's tickets go first while the lower
+    // levels are wide, and the diagonal work fills CTAs the narrow upper
+    // levels leave idle.  Each precedes, in the queue, every task waiting for it.
+    const int l_top = std::min({F.depth, L_w - 1, Ls - 1});
+    int diag_lag = DIAG_LAG;
+    if (const char* ev = std::getenv("NDHSS_APPLY_DIAG_LAG")) diag_lag = std::max(0, std::atoi(ev));
+    auto diag_levels = [&](int l) {
+        std::vector<int> v;
+        if (l == 0) {
+            for (int ld = 0; ld <= std::min(diag_lag, l_top); ++ld) v.push_back(ld);
+        } else if (l + diag_lag <= l_top) {
+            v.push_back(l + diag_lag);
+        }
+        return v;
+    };
+    auto push_dpart = [&](int l) {
+        for (int s : F.levels[l]) {
+            const int mi = F.m_i(s);
+            if (mi == 0 || fused(s) || ulv_front(s)) continue;
+            const int nch = ceil_div(mi, DIAG_COLS);
+            dpoff[s] = F.dpart_total;
+            F.dpart_total += (int64_t)nch * mi;
+            for (int c0 = 0; c0 < mi; c0 += DIAG_COLS)
+                for (int r0 = 0; r0 < mi; r0 += APPLY_ROWS) push(TK_DPART, s, r0, c0, false);
+            need[CN_DPART * nn + s] = nch * ceil_div(mi, APPLY_ROWS);
+        }
+    };
+    auto push_dsum = [&](int l) {
+        for (int s : F.levels[l]) {
+            const int mi = F.m_i(s);
+            if (mi == 0 || fused(s) || ulv_front(s)) continue;
+            for (int r0 = 0; r0 < mi; r0 += SUM_ROWS) push(TK_DSUM, s, r0, 0, diag_final(s));
+            need[CN_DIAG * nn + s] = ceil_div(mi, SUM_ROWS);
+            if (diag_final(s)) need[CN_FIN * nn + s] = need[CN_DIAG * nn + s];
+        }
+    };
+    for (int l = l_top; l >= 0; --l) {
         // fused / dense / low-rank-dot tasks of the level, then what completes each node
         for (int s : F.levels[l]) {
             const int mi = F.m_i(s), mb = F.m_b(s);
@@ -1576,21 +1668,7 @@ ndhss_status build_apply_schedule(FactorData& F, cudaStream_t st) {
                 need[CN_DOT * nn + s] = ceil_div(mi, LR_CHUNK) * ceil_div(F.lr_k[s], dgw);
             }
         }
-        // the diagonal step of the level's nodes not fused above (the same
-        // dependencies as their up-sweep: ready together, and queued with it so
-        // the tickets of the up-sweep chain above do not hold it back):
-        // column-chunk partial products, then their sums with the level's
-        // completing tasks
-        for (int s : F.levels[l]) {
-            const int mi = F.m_i(s);
-            if (mi == 0 || fused(s) || ulv_front(s)) continue;
-            const int nch = ceil_div(mi, DIAG_COLS);
-            dpoff[s] = F.dpart_total;
-            F.dpart_total += (int64_t)nch * mi;
-            for (int c0 = 0; c0 < mi; c0 += DIAG_COLS)
-                for (int r0 = 0; r0 < mi; r0 += APPLY_ROWS) push(TK_DPART, s, r0, c0, false);
-            need[CN_DPART * nn + s] = nch * ceil_div(mi, APPLY_ROWS);
-        }
+        for (int ld : diag_levels(l)) push_dpart(ld);
         cut();
         for (int s : F.levels[l]) {
             if (fused(s) || (F.m_i(s) > 0 && F.m_b(s) > 0 && mode(s) == 0)) continue;
@@ -1602,13 +1680,7 @@ ndhss_status build_apply_schedule(FactorData& F, cudaStream_t st) {
                 need[CN_UP * nn + s] = 1;
             }
         }
-        for (int s : F.levels[l]) {
-            const int mi = F.m_i(s);
-            if (mi == 0 || fused(s) || ulv_front(s)) continue;
-            for (int r0 = 0; r0 < mi; r0 += SUM_ROWS) push(TK_DSUM, s, r0, 0, diag_final(s));
-            need[CN_DIAG * nn + s] = ceil_div(mi, SUM_ROWS);
-            if (diag_final(s)) need[CN_FIN * nn + s] = need[CN_DIAG * nn + s];
-        }
+        for (int ld : diag_levels(l)) push_dsum(ld);
         cut();
     }
     // ULV solves of the HSS fronts: every front's HSS nodes going up (deepest
@@ -1726,6 +1798,15 @@ ndhss_status build_apply_schedule(FactorData& F, cudaStream_t st) {
                            cudaMemsetAsync(F.d_apply_err, 0, sizeof(int32_t), st) != cudaSuccess)) {
         cudaGetLastError();
         rc = set_error(NDHSS_ERR_OOM, "apply: error word");
+    }
+    if (rc == NDHSS_OK && F.sched_n > 0) {
+        if (pool_malloc_async((void**)&F.d_sched_dep, sizeof(int4) * 2 * (size_t)F.sched_n, st) != cudaSuccess) {
+            cudaGetLastError();
+            rc = set_error(NDHSS_ERR_OOM, "apply: dependency records");
+        } else {
+            F.dev_bytes += (int64_t)(sizeof(int4) * 2 * F.sched_n);
+            rc = fill_sched_deps(F, st);
+        }
     }
     if (rc != NDHSS_OK) return rc;
     const bool cplx = F.vtype == NDHSS_C128;
@@ -1914,6 +1995,9 @@ extern "C" ndhss_status ndhss_testing_stall_apply(ndhss_factorization* fh) {
         NDHSS_CUDA_TRY(cudaMemcpy(&v, p, sizeof(v), cudaMemcpyDeviceToHost));
         ++v;
         NDHSS_CUDA_TRY(cudaMemcpy(p, &v, sizeof(v), cudaMemcpyHostToDevice));
+        const ndhss_status rc = fill_sched_deps(F, 0);
+        if (rc != NDHSS_OK) return rc;
+        NDHSS_CUDA_TRY(cudaDeviceSynchronize());
         return NDHSS_OK;
     });
 }

@@ -51,6 +51,7 @@ struct FactorData {
     int32_t* d_need = nullptr;
     int32_t* d_wdesc = nullptr;               // warp-node descriptors (8 ints per node)
     int32_t* d_sublist = nullptr;             // bottom subtrees: node lists by level
+    int32_t* d_sched_dep = nullptr;           // per task: counter words, count | requirements (2 x int4)
     int32_t sched_sub_level = 0;              // first level handled by subtree tasks
     int32_t sched_warp_level = 0;             // first level handled a warp per node
     int64_t dpart_total = 0;
