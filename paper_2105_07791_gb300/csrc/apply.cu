@@ -62,10 +62,10 @@ namespace {
 
 constexpr int AT = 256;
 constexpr int AW = AT / 32;
-constexpr int GATHER_CHUNK = 8 * AT;
+constexpr int GATHER_CHUNK = 8 * AT;     // rows per gather task
 constexpr int DIAG_COLS = 256;    // column chunk of A_ii^{-1} per task (and fused-pass limit)
 constexpr int SUM_ROWS = AT;      // rows per partial-sum task
-constexpr int DIAG_LAG = 2;       // levels a node's diagonal tasks are queued behind its up-sweep
+constexpr int ROOT_DIAG_COLS = 128; // the same for the top level's nodes
 constexpr uint64_t APPLY_WAIT_NS = 2000000000ull;   // 2 s
 
 __device__ __forceinline__ int nf(const int32_t* node, int s, int f) { return node[s * NODE_NF + f]; }
@@ -250,11 +250,22 @@ __device__ __forceinline__ T gemv_rows64(const T* __restrict__ A, int64_t lda, i
             acc1 = fmac(b[u], x[u], acc1);
         }
     }
-    for (; c < cols; c += AW) {
-        const T* col = A + (int64_t)c * lda;
-        const T xv = xs[c];
-        if (va) acc0 = fmac(col[ra], xv, acc0);
-        if (vb) acc1 = fmac(col[rb], xv, acc1);
+    if (c < cols) {                  // the ragged last columns: one round of predicated loads
+        T a[3], b[3], x[3];
+#pragma unroll
+        for (int u = 0; u < 3; ++u) {
+            const int cu = c + u * AW;
+            const bool ok = cu < cols;
+            const T* col = A + (int64_t)(ok ? cu : c) * lda;
+            a[u] = (ok && va) ? col[ra] : zero<T>();
+            b[u] = (ok && vb) ? col[rb] : zero<T>();
+            x[u] = ok ? xs[cu] : zero<T>();
+        }
+#pragma unroll
+        for (int u = 0; u < 3; ++u) {
+            acc0 = fmac(a[u], x[u], acc0);
+            acc1 = fmac(b[u], x[u], acc1);
+        }
     }
     red[warp][lane] = acc0;
     red[warp][lane + 32] = acc1;
@@ -720,7 +731,7 @@ __device__ __forceinline__ void task_pre(const ApplyCtx<T>& C, const Entry& e, P
         break;
     }
     case TK_DPART: {
-        const int nc = min(DIAG_COLS, m_i - e.b);
+        const int nc = min(e.k, m_i - e.b);
         gemv_pre(F + (int64_t)e.b * m, m, m_i, nc, e.a, P.v);
         for (int c = tid; c < nc; c += AT) idx[c] = C.sigma[i_off + e.b + c];
         break;
@@ -791,7 +802,7 @@ __device__ __forceinline__ void task_run(const ApplyCtx<T>& C, const Entry& e, c
     const int tid = threadIdx.x;
     if (e.kind == TK_GATHER) {
         // index loads, then gathers, four at a time (register budget)
-        for (int h = 0; h < GATHER_CHUNK / AT; h += 4) {
+        for (int h = 0; h < e.b / AT; h += 4) {             // e.b rows, a multiple of 4 AT
             int pi[4];
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
@@ -847,21 +858,28 @@ __device__ __forceinline__ void task_run(const ApplyCtx<T>& C, const Entry& e, c
         break;
     }
     case TK_DPART: {
-        const int nc = min(DIAG_COLS, m_i - e.b);
+        const int nc = min(e.k, m_i - e.b);
         for (int c = tid; c < nc; c += AT) vec[c] = ldw(y + i_off + idx[c]);
         __syncthreads();
         const T sum = gemv_rows64(F + (int64_t)e.b * m, m, m_i, nc, e.a, vec, red, P.v);
         const int r = e.a + tid;
-        if (tid < APPLY_ROWS && r < m_i) stw(dpart + e.aux + (int64_t)(e.b / DIAG_COLS) * m_i + r, sum);
+        if (tid < APPLY_ROWS && r < m_i) stw(dpart + e.aux + (int64_t)(e.b / e.k) * m_i + r, sum);
         break;
     }
     case TK_DSUM: {
         const int r = e.a + tid;
         if (r < m_i) {
-            const int nch = (m_i + DIAG_COLS - 1) / DIAG_COLS;
+            // the column-chunk partials (chunk width e.k), eight loads in flight
+            const int nch = (m_i + e.k - 1) / e.k;
             const T* p = dpart + e.aux + r;
-            T acc = ldw(p);
-            for (int c = 1; c < nch; ++c) acc = acc + ldw(p + (int64_t)c * m_i);
+            T acc = zero<T>();
+            for (int c0 = 0; c0 < nch; c0 += 8) {
+                T pv[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) pv[u] = c0 + u < nch ? ldw(p + (int64_t)(c0 + u) * m_i) : zero<T>();
+#pragma unroll
+                for (int u = 0; u < 8; ++u) acc = acc + pv[u];
+            }
             stw(z + i_off + r, acc);
             if (e.fin) out[P.pi] = to_val(acc);
         }
@@ -1404,6 +1422,7 @@ ndhss_status build_apply_schedule(FactorData& F, cudaStream_t st) {
     std::vector<int32_t> q, need((size_t)NCNT * std::max(nn, 1) + 2 * (size_t)nrec, 0);
     std::vector<int64_t> groups{0};
     std::vector<int64_t> dpoff(std::max(nn, 1), 0);
+    std::vector<int32_t> dcols(std::max(nn, 1), DIAG_COLS);   // column chunk of each node's diagonal tasks
     auto push = [&](int kind, int s, int a, int b, bool fin) {
         const bool lr = kind == TK_UPDOT || kind == TK_UPAXPY || kind == TK_DNDOT || kind == TK_DNAXPY;
         const int64_t base = kind == TK_GATHER ? 0 : lr ? (int64_t)F.lr_ptr[s] : F.foff[s];
@@ -1411,7 +1430,7 @@ ndhss_status build_apply_schedule(FactorData& F, cudaStream_t st) {
         const bool g = kind == TK_GATHER;
         const int32_t w[QW] = {(fin ? TK_FINAL : 0) | (kind << TK_SHIFT) | s, a, b,
                                g ? 0 : F.m_i(s), g ? 0 : F.m_b(s), g ? 0 : F.info(s, 4), g ? 0 : F.info(s, 6),
-                               lr ? F.lr_k[s] : 0,
+                               lr ? F.lr_k[s] : (kind == TK_DPART || kind == TK_DSUM) ? dcols[s] : 0,
                                (int32_t)(uint32_t)(uint64_t)base, (int32_t)(uint32_t)((uint64_t)base >> 32),
                                (int32_t)(uint32_t)(uint64_t)aux, (int32_t)(uint32_t)((uint64_t)aux >> 32)};
         q.insert(q.end(), w, w + QW);
@@ -1591,7 +1610,7 @@ ndhss_status build_apply_schedule(FactorData& F, cudaStream_t st) {
     };
     auto ulv_front = [&](int s) { return !F.ulv_root_of.empty() && F.ulv_root_of[s] >= 0; };
     const int ng = ceil_div(F.n, GATHER_CHUNK);
-    for (int i = 0; i < ng; ++i) push(TK_GATHER, 0, i * GATHER_CHUNK, 0, false);
+    for (int i = 0; i < ng; ++i) push(TK_GATHER, 0, i * GATHER_CHUNK, GATHER_CHUNK, false);
     cut();
     auto push_sub = [&](int kind, int r) {
         const int32_t w[QW] = {(kind << TK_SHIFT) | r, sub_lo[r], sub_ni[r], F.m_i(r), F.m_b(r),
@@ -1610,32 +1629,21 @@ ndhss_status build_apply_schedule(FactorData& F, cudaStream_t st) {
         cut();
     }
     // The diagonal step of the nodes not fused into their up-sweep tasks:
-    // column-chunk partial products, then their sums.  Ready with the node's
-    // up-sweep but needed only when the down sweep returns to the node, so a
-    // level's diagonal tasks are queued DIAG_LAG levels further up (the root's
-    // with the root): the low-rank chain's tickets go first while the lower
-    // levels are wide, and the diagonal work fills CTAs the narrow upper
-    // levels leave idle.  Each precedes, in the queue, every task waiting for it.
+    // column-chunk partial products, then their sums.  Same dependencies as
+    // the node's up-sweep, so they are queued with it: ready together, and the
+    // tickets of the up-sweep chain above do not hold them back.
     const int l_top = std::min({F.depth, L_w - 1, Ls - 1});
-    int diag_lag = DIAG_LAG;
-    if (const char* ev = std::getenv("NDHSS_APPLY_DIAG_LAG")) diag_lag = std::max(0, std::atoi(ev));
-    auto diag_levels = [&](int l) {
-        std::vector<int> v;
-        if (l == 0) {
-            for (int ld = 0; ld <= std::min(diag_lag, l_top); ++ld) v.push_back(ld);
-        } else if (l + diag_lag <= l_top) {
-            v.push_back(l + diag_lag);
-        }
-        return v;
-    };
     auto push_dpart = [&](int l) {
         for (int s : F.levels[l]) {
             const int mi = F.m_i(s);
             if (mi == 0 || fused(s) || ulv_front(s)) continue;
-            const int nch = ceil_div(mi, DIAG_COLS);
+            // the top level's diagonal step lies on the critical path (the down
+            // sweep starts from it): narrower chunks, more tasks in parallel
+            dcols[s] = l == 0 ? ROOT_DIAG_COLS : DIAG_COLS;
+            const int nch = ceil_div(mi, dcols[s]);
             dpoff[s] = F.dpart_total;
             F.dpart_total += (int64_t)nch * mi;
-            for (int c0 = 0; c0 < mi; c0 += DIAG_COLS)
+            for (int c0 = 0; c0 < mi; c0 += dcols[s])
                 for (int r0 = 0; r0 < mi; r0 += APPLY_ROWS) push(TK_DPART, s, r0, c0, false);
             need[CN_DPART * nn + s] = nch * ceil_div(mi, APPLY_ROWS);
         }
@@ -1668,7 +1676,7 @@ ndhss_status build_apply_schedule(FactorData& F, cudaStream_t st) {
                 need[CN_DOT * nn + s] = ceil_div(mi, LR_CHUNK) * ceil_div(F.lr_k[s], dgw);
             }
         }
-        for (int ld : diag_levels(l)) push_dpart(ld);
+        push_dpart(l);
         cut();
         for (int s : F.levels[l]) {
             if (fused(s) || (F.m_i(s) > 0 && F.m_b(s) > 0 && mode(s) == 0)) continue;
@@ -1680,7 +1688,7 @@ ndhss_status build_apply_schedule(FactorData& F, cudaStream_t st) {
                 need[CN_UP * nn + s] = 1;
             }
         }
-        for (int ld : diag_levels(l)) push_dsum(ld);
+        push_dsum(l);
         cut();
     }
     // ULV solves of the HSS fronts: every front's HSS nodes going up (deepest
