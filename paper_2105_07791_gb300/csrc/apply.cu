@@ -49,10 +49,11 @@
 //   phase each), one launch per group; selected with
 //   NDHSS_APPLY_SCHEDULE=levels and kept as the bit-exact cross-check.
 #include <algorithm>
+#include <atomic>
+#include <thread>
 #include <cstdlib>
 #include <cstring>
 #include <mutex>
-#include <unordered_map>
 
 #include "driver.h"
 #include "factor.cuh"
@@ -693,7 +694,6 @@ __device__ void subtree_task(const ApplyCtx<T>& C, const Entry& e, int* idx, T* 
 // array of at least max(m_i, m_b, LR_CHUNK) entries.
 template <typename T>
 __device__ __forceinline__ void task_pre(const ApplyCtx<T>& C, const Entry& e, Pre<T>& P, int* idx, int (*wd)[8]) {
-    const int s = e.s;
     const int tid = threadIdx.x;
     P.gi = -1;
     P.pi = -1;
@@ -798,7 +798,6 @@ __device__ __forceinline__ void task_run(const ApplyCtx<T>& C, const Entry& e, c
                                          T (*red)[APPLY_ROWS], const int (*wd)[8], int n, const V* __restrict__ x,
                                          V* __restrict__ out, T* y, T* z, T* tup, T* tdn, T* dpart, T* us,
                                          const Sched* Sp) {
-    const int s = e.s;
     const int tid = threadIdx.x;
     if (e.kind == TK_GATHER) {
         // index loads, then gathers, four at a time (register budget)
@@ -1517,63 +1516,94 @@ ndhss_status build_apply_schedule(FactorData& F, cudaStream_t st) {
                                              cudaMemcpyDeviceToHost, st);
             if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
             if (ce != cudaSuccess) return set_error(NDHSS_ERR_CUDA, "apply: %s", cudaGetErrorString(ce));
-            for (int r : F.levels[Ls]) {
+            // the tables of all subtrees, built in parallel: sizes and offsets
+            // first, then every subtree fills its own range
+            const std::vector<int>& roots = F.levels[Ls];
+            const int nsub = (int)roots.size();
+            std::vector<int64_t> soff(nsub + 1, 0);
+            for (int i = 0; i < nsub; ++i) {
+                const int r = roots[i];
+                int64_t mbs = 0;
+                for (int q = first[r]; q <= r; ++q) mbs += F.m_b(q);
+                soff[i + 1] = soff[i] + SUB_HDR + (int64_t)SUB_LREC * nlev[r] + (int64_t)SUB_NREC * cntn[r] + ni[r] + mbs;
+            }
+            if (soff[nsub] >= (int64_t)INT32_MAX) return set_error(NDHSS_ERR_INVALID_ARG, "apply: subtree tables too long");
+            sublist.assign((size_t)soff[nsub], 0);
+            std::atomic<int> bad{-1};
+            auto fill = [&](int i) {
+                const int r = roots[i];
                 const int lo = F.info(first[r], 4);
                 const int nI = (int)ni[r];
-                sub_lo[r] = lo;
-                sub_ni[r] = nI;
+                int32_t* out = sublist.data() + soff[i];
                 // the task's table (see subtree_task): levels deepest first,
                 // ascending ids within a level
-                const int off = (int)sublist.size();
                 const int nl = nlev[r], l0 = F.info(r, 0);
                 std::vector<std::vector<int>> bylev(nl);
-                for (int s = first[r]; s <= r; ++s) bylev[nl - 1 - (F.info(s, 0) - l0)].push_back(s);
-                std::unordered_map<int, int> broot;
-                for (int j = 0; j < F.m_b(r); ++j) broot[F.blist_h[F.info(r, 6) + j]] = nI + j;
-                auto bslot_of = [&](int s, int j) {
-                    const int g = F.blist_h[F.info(s, 6) + j];
+                for (int q = first[r]; q <= r; ++q) bylev[nl - 1 - (F.info(q, 0) - l0)].push_back(q);
+                // the vector slot of every B^root row (sorted by row for the lookups)
+                std::vector<std::pair<int, int>> broot((size_t)F.m_b(r));
+                for (int j = 0; j < F.m_b(r); ++j) broot[j] = {F.blist_h[F.info(r, 6) + j], nI + j};
+                std::sort(broot.begin(), broot.end());
+                auto bslot_of = [&](int q, int j) {
+                    const int g = F.blist_h[F.info(q, 6) + j];
                     if (g >= lo && g < lo + nI) return g - lo;
-                    auto it = broot.find(g);
-                    return it == broot.end() ? -1 : it->second;
+                    auto it = std::lower_bound(broot.begin(), broot.end(), std::make_pair(g, INT32_MIN));
+                    return (it != broot.end() && it->first == g) ? it->second : -1;
                 };
-                std::vector<int32_t> lrec, nrec, src_up, src_dn;
+                int32_t* lrec = out + SUB_HDR;
+                int32_t* nrec = lrec + SUB_LREC * nl;
+                int32_t* src_up = nrec + SUB_NREC * cntn[r];
+                int32_t* src_dn = src_up + nI;
                 int nidx = 0;
                 for (int h = 0; h < nl; ++h) {
                     int ru = 0, rd = 0, xu = 0, xd = 0, bo = 0;
-                    for (int s : bylev[h]) {
-                        const uint64_t fo = (uint64_t)F.foff[s];
-                        const int32_t nd[SUB_NREC] = {F.m_i(s), F.m_b(s), (int32_t)(uint32_t)fo, (int32_t)(uint32_t)(fo >> 32),
-                                                      ru, xu, rd, xd, F.info(s, 4) - lo, bo};
-                        nrec.insert(nrec.end(), nd, nd + SUB_NREC);
+                    for (int q : bylev[h]) {
+                        const uint64_t fo = (uint64_t)F.foff[q];
+                        const int32_t nd[SUB_NREC] = {F.m_i(q), F.m_b(q), (int32_t)(uint32_t)fo, (int32_t)(uint32_t)(fo >> 32),
+                                                      ru, xu, rd, xd, F.info(q, 4) - lo, bo};
+                        std::copy(nd, nd + SUB_NREC, nrec);
+                        nrec += SUB_NREC;
                         // column c of A_ii^{-1} multiplies interior row sigma(c)
-                        for (int c = 0; c < F.m_i(s); ++c)
-                            src_up.push_back(F.info(s, 4) - lo + sig_h[F.info(s, 4) + c]);
-                        for (int j = 0; j < F.m_b(s); ++j) {
-                            const int sl = bslot_of(s, j);
-                            if (sl < 0)
-                                return set_error(NDHSS_ERR_INTERNAL, "apply: a B row of node %d lies outside its subtree", s);
-                            src_dn.push_back(sl);
+                        for (int c = 0; c < F.m_i(q); ++c) *src_up++ = F.info(q, 4) - lo + sig_h[F.info(q, 4) + c];
+                        for (int j = 0; j < F.m_b(q); ++j) {
+                            const int sl = bslot_of(q, j);
+                            if (sl < 0) bad.store(q);
+                            *src_dn++ = sl;
                         }
-                        ru += F.m_i(s) + F.m_b(s);
-                        rd += F.m_i(s);
-                        xu += F.m_i(s);
-                        xd += F.m_b(s);
-                        bo += F.m_b(s);
+                        ru += F.m_i(q) + F.m_b(q);
+                        rd += F.m_i(q);
+                        xu += F.m_i(q);
+                        xd += F.m_b(q);
+                        bo += F.m_b(q);
                     }
                     const int32_t lr[SUB_LREC] = {(int32_t)bylev[h].size(), nidx, ru, rd, xu, xd};
-                    lrec.insert(lrec.end(), lr, lr + SUB_LREC);
+                    std::copy(lr, lr + SUB_LREC, lrec + SUB_LREC * h);
                     nidx += (int)bylev[h].size();
                 }
-                sublist.push_back(nl);
-                sublist.push_back(nidx);
-                sublist.insert(sublist.end(), lrec.begin(), lrec.end());
-                sublist.insert(sublist.end(), nrec.begin(), nrec.end());
-                sublist.insert(sublist.end(), src_up.begin(), src_up.end());
-                sublist.insert(sublist.end(), src_dn.begin(), src_dn.end());
-                sub_off[r] = off;
-                sub_len[r] = (int)sublist.size() - off;
+                out[0] = nl;
+                out[1] = nidx;
+            };
+            const int nth = (int)std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
+            if (nth == 1 || nsub < 64) {
+                for (int i = 0; i < nsub; ++i) fill(i);
+            } else {
+                std::vector<std::thread> pool;
+                for (int w = 0; w < nth; ++w)
+                    pool.emplace_back([&, w]() {
+                        for (int i = w; i < nsub; i += nth) fill(i);
+                    });
+                for (auto& th : pool) th.join();
+            }
+            if (bad.load() >= 0)
+                return set_error(NDHSS_ERR_INTERNAL, "apply: a B row of node %d lies outside its subtree", bad.load());
+            for (int i = 0; i < nsub; ++i) {
+                const int r = roots[i];
+                sub_lo[r] = F.info(first[r], 4);
+                sub_ni[r] = (int)ni[r];
+                sub_off[r] = (int)soff[i];
+                sub_len[r] = (int)(soff[i + 1] - soff[i]);
                 F.sched_vlen = std::max(F.sched_vlen, sub_len[r]);
-                F.sched_vlen = std::max(F.sched_vlen, (int)(nI + F.m_b(r) + SUB_XIN + AT));
+                F.sched_vlen = std::max(F.sched_vlen, (int)(ni[r] + F.m_b(r) + SUB_XIN + AT));
             }
         }
     }
