@@ -58,6 +58,12 @@ BATCH = dict(count=64, seed=0, nmin=64, nmax=256, nrhs=32, leaf=64, tol=1e-8)
 # boundary; tolerance 1e-6; leaf 60, beta 60
 ELASTIC = dict(N=512, seed=0, leaf=60, beta=60, tol=1e-6, hss_levels=4)
 
+# C1 side line: 2D Poisson, P1 CG on 64 x 64 cells, homogeneous Dirichlet,
+# f ~ U[-1, 1] per node (seed 0), FP64 fronts, leaf 64, HSS eps 1e-6 on the
+# levels <= depth - 4, GMRES(30) to 1e-8; also the oracle's compressed factor
+# of the same configuration (the like-for-like CPU baseline)
+C1 = dict(N=64, seed=0, leaf=64, tol=1e-8, hss_levels=4, eps_hss=1e-6, beta=64, solves=50)
+
 # ncu DRAM traffic of the dominant kernel class, per launch, keyed by the
 # sha256 of the source file it was measured on (null once the source changes)
 NCU_TRAFFIC = {
@@ -76,6 +82,7 @@ def _args():
     ap.add_argument("--only", choices=["mixed", "fp64", "tf32", "bf16"], help="time one precision only (profiling runs)")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer measurement (profiling runs)")
     ap.add_argument("--N", type=int, default=WORKLOAD["N"], help="cells per side (default: the benchmark workload)")
+    ap.add_argument("--no-c1", action="store_true", help="skip the C1 Poisson side line")
     ap.add_argument("--batch-count", type=int, default=BATCH["count"],
                     help="problems of the batched side line (0 = skip it)")
     ap.add_argument("--elastic-N", type=int, default=ELASTIC["N"],
@@ -245,6 +252,8 @@ def run_gpu(a):
     b = torch.from_numpy(np.ascontiguousarray(P.b)).cuda()
     x = torch.zeros_like(b)
     stream = torch.cuda.current_stream()
+    # FMA rates of this GPU's CUDA cores (the ALU rooflines), before anything is timed
+    alu_peaks = {"fp64": ndhss.ndhss_measure_fma_peak(0, stream), "fp32": ndhss.ndhss_measure_fma_peak(1, stream)}
 
     def barrier():
         torch.cuda.synchronize()
@@ -366,24 +375,22 @@ def run_gpu(a):
         froof["dense_elimination"]["frac"] = froof["dense_elimination"]["achieved"] / (tf32_peak / 3)
     if dom == "compress":
         froof.update(bound="latency (per-round row-ID pivot chains of the HSS levels, one dependent launch each)")
-    # the other hot kernels against the bound that limits them: ALU peaks
-    # derived from unit counts and the maximum SM clock (FP32 SIMT: 152 SMs x
-    # 128 lanes x 2 flops; FP64: GB300's nominal 1.25 TFLOP/s), HBM measured
-    clk = pk.get("sm_max_mhz", 2070.0) * 1e6
-    fp32_peak = 152 * 128 * 2 * clk / 1e12
-    fp64_peak = 1.25
+    # the other hot kernels against the bound that limits them: the FP64 and
+    # FP32 FMA rates measured on this GPU in this run (the library's
+    # independent-FMA-chain kernel), HBM from the measured peaks
+    fp64_peak, fp32_peak = alu_peaks["fp64"], alu_peaks["fp32"]
     n_sp = sum(v[3] for v in mx["applies"]) / a.steps
     sp_one = sp_ms / max(n_sp, 1)
     krl = [
         dict(roof, kernel="apply_dataflow_kernel"),
         {"kernel": "spmv_kernel (FP64 CSR, complex128)", "bound": "alu", "unit": "TFLOP/s",
          "achieved": 8.0 * P.A.nnz / (sp_one / 1e3) / 1e12 if sp_one > 0 else None, "peak": fp64_peak,
-         "peak_kind": "nominal FP64", "algorithmic": "8 flops per complex entry (real entries take 4)",
+         "peak_kind": "FP64 FMA rate measured in this run", "algorithmic": "8 flops per complex entry (real entries take 4)",
          "avg_launch_ms": sp_one},
         {"kernel": "gemm_update_kernel (FP32 SIMT rank-kb exchange steps: small fronts, slabs of the large ones)",
          "bound": "alu", "unit": "TFLOP/s",
          "achieved": fs["update_flops"] / (cls_ms["update"] / 1e3) / 1e12 if cls_ms.get("update") else None,
-         "peak": fp32_peak, "peak_kind": "derived: 152 SMs x 128 FP32 lanes x 2 x max SM clock",
+         "peak": fp32_peak, "peak_kind": "FP32 FMA rate measured in this run",
          "algorithmic": "8 m x (columns exchanged) x kb flops per front and panel"},
         {"kernel": "tc_gemm_kernel (tcgen05 + TMA rank-128 block exchanges, two TF32 parts per operand; class "
                    "time includes the operand packing)", "bound": "tensor", "unit": "TFLOP/s",
@@ -432,6 +439,7 @@ def run_gpu(a):
         "roofline": roof,
         "factor_roofline": froof,
         "kernel_rooflines": krl,
+        "alu_peaks_tflops": alu_peaks,
         "spmv_ms_per_solve": sp_ms,
         "factor_kernel_ms": {k: round(v, 3) for k, v in cls_ms.items()},
         "clocks": mx["clocks"],
@@ -441,12 +449,17 @@ def run_gpu(a):
         b = line["batched"]
         krl.append({"kernel": "mapply_kernel (batched 32-column apply)", "bound": "alu", "unit": "TFLOP/s",
                     "achieved": b["apply_multi_tflops"], "peak": fp32_peak,
-                    "peak_kind": "derived: 152 SMs x 128 FP32 lanes x 2 x max SM clock",
+                    "peak_kind": "FP32 FMA rate measured in this run",
                     "frac": b["apply_multi_tflops"] / fp32_peak, "algorithmic": "8 x 32 flops per stored element"})
     if a.elastic_N > 0:
         line["elastic"] = elastic_line(a, ndhss, torch, stream)
+    if not a.no_c1:
+        line["c1"] = c1_line(a, ndhss, torch, stream)
     if not a.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = cpu_baseline(P)
+        if "c1" in line:
+            line["cpu_baseline"]["like_for_like_c1"] = c1_oracle()
+            line["c1"]["gpu_over_oracle"] = line["c1"]["solves_per_s"] / line["cpu_baseline"]["like_for_like_c1"]["solves_per_s"]
     print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
@@ -570,6 +583,94 @@ def elastic_line(a, ndhss, torch, stream):
                      "apply_gbs": fs["apply_bytes"] / (st["apply_ms"] / max(st["napply"], 1) / 1e3) / 1e9
                      if st["apply_ms"] > 0 else None}
     return out
+
+
+def _c1_problem():
+    from ndhss_inputs import poisson_dirichlet
+    return poisson_dirichlet(C1["N"], seed=C1["seed"])
+
+
+def c1_line(a, ndhss, torch, stream):
+    """C1: the Poisson configuration, FP64 fronts with HSS compression;
+    factor time (three factorizations after a warm-up, mean), then C1["solves"]
+    GMRES solves to 1e-8 timed together (solves/s), and one solve with the
+    apply timed for its GB/s."""
+    import numpy as np
+
+    P = _c1_problem()
+    tree = ndhss.ndhss_build_tree(P.coords, P.A.indptr, P.A.indices, C1["leaf"])
+    M = ndhss.DeviceCSR(P.A)
+    b = torch.from_numpy(np.ascontiguousarray(P.b)).cuda()
+    opts = ndhss.make_factor_opts(prec=ndhss.NDHSS_FP64, hss_levels=C1["hss_levels"], eps_hss=C1["eps_hss"],
+                                  beta=C1["beta"], seed=0)
+    f = ndhss.ndhss_factor(tree, M.vtype, M.rowptr, M.col, M.vals, opts, stream=stream)
+    del f
+    torch.cuda.synchronize()
+    fms = []
+    for _ in range(3):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        f = ndhss.ndhss_factor(tree, M.vtype, M.rowptr, M.col, M.vals, opts, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        fms.append(e0.elapsed_time(e1))
+        if len(fms) < 3:
+            del f
+    x = torch.zeros_like(b)
+    for _ in range(3):
+        x.zero_()
+        ndhss.ndhss_gmres(f, M.rowptr, M.col, M.vals, b, x, tol=C1["tol"], stream=stream)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(C1["solves"]):
+        x.zero_()
+        st = ndhss.ndhss_gmres(f, M.rowptr, M.col, M.vals, b, x, tol=C1["tol"], stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    solve_ms = e0.elapsed_time(e1) / C1["solves"]
+    x.zero_()
+    stt = ndhss.ndhss_gmres(f, M.rowptr, M.col, M.vals, b, x, tol=C1["tol"], timing=True, stream=stream)
+    fs = ndhss.ndhss_factor_stats_get(f)
+    xs = x.cpu().numpy()
+    relres = float(np.linalg.norm(P.b - P.A @ xs) / np.linalg.norm(P.b))
+    ap_ms = stt["apply_ms"] / max(stt["napply"], 1)
+    return {"workload": f"poisson_p1_cg_{C1['N']}x{C1['N']}_dirichlet (n={P.n}, nnz={P.A.nnz}, leaf {C1['leaf']})",
+            "dtype": "f64 fronts, f64 Krylov",
+            "compression": f"HSS on levels <= depth - {C1['hss_levels']}, eps {C1['eps_hss']:g}, beta {C1['beta']}",
+            "factor_ms": statistics.mean(fms), "solve_ms": solve_ms, "solves_per_s": 1e3 / solve_ms,
+            "iters": st["iters"], "true_relres": relres, "kmax": fs["kmax"], "apply_ms": ap_ms,
+            "apply_bytes": fs["apply_bytes"],
+            "apply_gbs": fs["apply_bytes"] / (ap_ms / 1e3) / 1e9 if ap_ms > 0 else None,
+            "note": "a 4k-unknown problem: every kernel is launch- and latency-bound, not bandwidth-bound"}
+
+
+def c1_oracle():
+    """The oracle's compressed factor of C1 (the same preconditioner as the
+    GPU's C1 line: FP64, same tree, eps, beta, Philox streams), timed on the
+    host cores: tree + factor once, then GMRES solves for about 2 s."""
+    from oracle.gmres import gmres
+    from oracle.hss import apply_compressed, factor_compressed
+    from oracle.tree import build_tree
+    P = _c1_problem()
+    t0 = time.perf_counter()
+    T = build_tree(P.coords, P.A.indptr, P.A.indices, C1["leaf"])
+    t1 = time.perf_counter()
+    fac = factor_compressed(T, P.A, hss_levels=C1["hss_levels"], eps=C1["eps_hss"], beta=C1["beta"], k0=32, r=16,
+                            seed=0)
+    t2 = time.perf_counter()
+    n = 0
+    t3 = time.perf_counter()
+    while True:
+        r = gmres(P.A, P.b, lambda v: apply_compressed(fac, v), tol=C1["tol"])
+        n += 1
+        if time.perf_counter() - t3 > 2.0:
+            break
+    ts = (time.perf_counter() - t3) / n
+    return {"value": 1.0 / ts, "solves_per_s": 1.0 / ts, "unit": "solves/s", "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"C1 with the oracle's compressed FP64 factor (the GPU C1 line's preconditioner): {n} GMRES solves "
+                      f"(tol 1e-8, {r.iters} it) after one factorization",
+            "factor_s": t2 - t1, "tree_s": t1 - t0, "iters": r.iters, "kmax": fac.kmax}
 
 
 # ------------------------------------------------------------- CPU oracle

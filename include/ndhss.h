@@ -152,6 +152,16 @@ const char* ndhss_last_error(void);
  * (monotonic; for accounting of device work, e.g. per timed region). */
 int64_t ndhss_kernel_launches(void);
 
+/* Measurement aid, no counterpart in the paper: the sustained FMA rate of the
+ * current device's CUDA cores in TFLOP/s (two flops per FMA), which = 0 for
+ * FP64, 1 for FP32: a kernel of eight independent FMA chains per thread, eight
+ * 256-thread CTAs per SM, timed with CUDA events on `stream` (0 = default),
+ * best of three launches after a warm-up (tens of ms).  It is the denominator
+ * of the rooflines of the kernels bound by plain arithmetic.  *tflops is
+ * written on success.  Errors: NDHSS_ERR_INVALID_ARG (another `which`, null
+ * pointer), NDHSS_ERR_CUDA (allocation or launch failure). */
+ndhss_status ndhss_measure_fma_peak(int32_t which, void* stream, double* tflops);
+
 /*
  * ndhss_build_tree -- box nested dissection and elimination tree
  * (Def. 3.1; boxes of Fig. 3; Sec. 3.1 for I^sigma and B^sigma; Sec. 3.3 and

@@ -26,7 +26,7 @@ EXPORTED = ("ndhss_version", "ndhss_last_error", "ndhss_kernel_launches", "ndhss
             "ndhss_tree_destroy", "ndhss_factor", "ndhss_factor_stats_get", "ndhss_factor_get_block",
             "ndhss_factor_destroy", "ndhss_apply", "ndhss_apply_noalloc", "ndhss_spmv", "ndhss_gmres",
             "ndhss_testing_stall_apply", "ndhss_elem_qform", "ndhss_build_tree_batched", "ndhss_apply_multi",
-            "ndhss_gmres_batched")
+            "ndhss_gmres_batched", "ndhss_measure_fma_peak")
 
 
 class NdhssError(RuntimeError):
@@ -90,6 +90,7 @@ def load(path: str | None = None):
         "ndhss_version": (C.c_char_p, []),
         "ndhss_last_error": (C.c_char_p, []),
         "ndhss_kernel_launches": (C.c_int64, []),
+        "ndhss_measure_fma_peak": (I32, [I32, V, C.POINTER(C.c_double)]),
         "ndhss_build_tree": (I32, [I32, P, P, P, I32, C.POINTER(C.c_void_p)]),
         "ndhss_tree_sizes": (I32, [P, C.POINTER(I32), C.POINTER(I32), C.POINTER(I64), C.POINTER(I64)]),
         "ndhss_tree_export": (I32, [P] + [P] * 8),
@@ -335,6 +336,16 @@ def ndhss_spmv(n: int, vtype: int, d_rowptr, d_col, d_vals, d_x, d_y, stream=Non
 
 def ndhss_kernel_launches() -> int:
     return int(load().ndhss_kernel_launches())
+
+
+def ndhss_measure_fma_peak(which: int, stream=None) -> float:
+    """Sustained FMA rate of the device's CUDA cores in TFLOP/s: which = 0
+    FP64, 1 FP32 (measurement aid, no counterpart in the paper)."""
+    if which not in (0, 1):
+        raise ValueError("which must be 0 (FP64) or 1 (FP32)")
+    out = C.c_double(0.0)
+    _check(load().ndhss_measure_fma_peak(int(which), _stream(stream), C.byref(out)))
+    return float(out.value)
 
 
 def ndhss_gmres(f: Factor, d_rowptr, d_col, d_vals, b, x, restart=30, maxit=300, tol=1e-8, stream=None,

@@ -223,3 +223,16 @@ def test_singular_front_is_reported(nd):
     # the context is still usable afterwards
     x = torch.ones(4, device="cuda")
     assert float(x.sum()) == 4.0
+
+
+def test_fma_peak_measurement(nd):
+    """The ALU roofline denominators: FP32 well above FP64 on GB300's CUDA
+    cores, both within physical bounds (152 SMs x 128 FP32 lanes x 2 flops
+    x 2.1 GHz = 82 TFLOP/s at most)."""
+    f64 = nd.ndhss_measure_fma_peak(0)
+    f32 = nd.ndhss_measure_fma_peak(1)
+    assert 0.1 < f64 < 10.0, f64
+    assert 10.0 < f32 < 85.0, f32
+    assert f32 > 8 * f64
+    with pytest.raises(ValueError):
+        nd.ndhss_measure_fma_peak(2)
