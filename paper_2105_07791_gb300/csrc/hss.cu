@@ -255,7 +255,80 @@ struct HNode {
     int64_t o_skel, o_iloc, o_piv;                      // int offsets
 };
 
+// ---------------------------------------------- per-node small products
+// One 64 x 64 tile (rows i0.., columns j0..) of C = A B, K in chunks of 16
+// staged in shared memory; the next chunk's loads are in registers while the
+// current chunk is multiplied, so a tile waits for memory about once, not
+// once per product term.  A(i, l) and B(l, j) come from the caller's
+// accessors (gathers allowed); A_KMAJ: consecutive threads load consecutive l
+// of A (A stored along K), else consecutive i; B is always loaded along K.
+// out(i, j, c) receives every valid entry of the tile.  All 256 threads call it.
+constexpr int NT_TILE = 64, NT_K = 16;
+
+__host__ __device__ __forceinline__ int tiles64(int n) { return (n + NT_TILE - 1) / NT_TILE; }
+
+template <typename T, bool A_KMAJ, typename FA, typename FB, typename FO>
+__device__ __forceinline__ void tile_gemm64(int M, int N, int K, int i0, int j0, FA fa, FB fb, FO out) {
+    __shared__ T sA[NT_K][NT_TILE];
+    __shared__ T sB[NT_K][NT_TILE];
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    T acc[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b] = zero<T>();
+    T ra[4], rb[4];
+    auto load = [&](int kc) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int q = tid + 256 * u;
+            const int ia = A_KMAJ ? q / NT_K : q % NT_TILE, la = A_KMAJ ? q % NT_K : q / NT_TILE;
+            ra[u] = (kc + la < K && i0 + ia < M) ? fa(i0 + ia, kc + la) : zero<T>();
+            const int jb = q / NT_K, lb = q % NT_K;
+            rb[u] = (kc + lb < K && j0 + jb < N) ? fb(kc + lb, j0 + jb) : zero<T>();
+        }
+    };
+    load(0);
+    for (int kc = 0; kc < K; kc += NT_K) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int q = tid + 256 * u;
+            const int ia = A_KMAJ ? q / NT_K : q % NT_TILE, la = A_KMAJ ? q % NT_K : q / NT_TILE;
+            sA[la][ia] = ra[u];
+            sB[q % NT_K][q / NT_K] = rb[u];
+        }
+        __syncthreads();
+        if (kc + NT_K < K) load(kc + NT_K);
+#pragma unroll
+        for (int l = 0; l < NT_K; ++l) {
+            T av[4], bv[4];
+#pragma unroll
+            for (int a = 0; a < 4; ++a) av[a] = sA[l][tx + 16 * a];
+#pragma unroll
+            for (int b = 0; b < 4; ++b) bv[b] = sB[l][ty + 16 * b];
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int b = 0; b < 4; ++b) acc[a][b] = fmac(av[a], bv[b], acc[a][b]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+        const int j = j0 + ty + 16 * b;
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+            const int i = i0 + tx + 16 * a;
+            if (i < M && j < N) out(i, j, acc[a][b]);
+        }
+    }
+}
+
 // S_loc^T into W (p x rows, ld p) and S_loc into SL (rows x p, ld rows_cap); iloc = global rows.
+// Leaf: S_loc = Y(I, :) - S(I, I) Om(I, :).  Inner node: the children's
+// skeleton rows, S_loc = [S_c1(J1, :) - S(J1, J2) Om_c2; S_c2(J2, :) - S(J2, J1) Om_c1].
+// Grid: (nodes, tiles): a leaf's tiles cover rows x p; an inner node's two
+// parts (rows of c1, rows of c2) ceil(kcap / 64) row tiles each.
 template <typename T>
 __global__ void __launch_bounds__(HT)
 form_sloc_kernel(const int* __restrict__ list, const HNode* __restrict__ nodes, const HFront* __restrict__ fronts,
@@ -270,47 +343,53 @@ form_sloc_kernel(const int* __restrict__ list, const HNode* __restrict__ nodes, 
     T* W = ws + nd.o_w;
     T* SL = ws + nd.o_sl;
     int* iloc = iws + nd.o_iloc;
-    int rows;
+    const int tn = tiles64(p);
+    const int t = blockIdx.y;
     if (nd.c1 < 0) {
-        rows = nd.hi - nd.lo;
-        for (int q = threadIdx.x; q < rows * p; q += HT) {
-            const int r = q % rows, j = q / rows;
-            T acc = Y[j * n + nd.lo + r];
-            for (int c = 0; c < rows; ++c)
-                acc = fmac(-S[(int64_t)(nd.lo + c) * lds + nd.lo + r], Om[j * n + nd.lo + c], acc);
-            W[(int64_t)r * p + j] = acc;
-            SL[(int64_t)j * nd.rows_cap + r] = acc;
+        const int rows = nd.hi - nd.lo;
+        const int i0 = (t / tn) * NT_TILE, j0 = (t % tn) * NT_TILE;
+        if (t == 0) {
+            for (int r = threadIdx.x; r < rows; r += HT) iloc[r] = nd.lo + r;
+            if (threadIdx.x == 0) rows_out[list[blockIdx.x]] = rows;
         }
-        for (int r = threadIdx.x; r < rows; r += HT) iloc[r] = nd.lo + r;
+        if (i0 >= rows) return;
+        tile_gemm64<T, false>(
+            rows, p, rows, i0, j0, [&](int r, int c) { return -S[(int64_t)(nd.lo + c) * lds + nd.lo + r]; },
+            [&](int c, int j) { return Om[(int64_t)j * n + nd.lo + c]; },
+            [&](int r, int j, T acc) {
+                acc = acc + Y[(int64_t)j * n + nd.lo + r];
+                W[(int64_t)r * p + j] = acc;
+                SL[(int64_t)j * nd.rows_cap + r] = acc;
+            });
     } else {
         const HNode a = nodes[nd.c1], b = nodes[nd.c2];
         const int k1 = kk[nd.c1], k2 = kk[nd.c2];
-        rows = k1 + k2;
         const int* sk1 = iws + a.o_skel;
         const int* sk2 = iws + b.o_skel;
-        const T* S1 = ws + a.o_si;
-        const T* S2 = ws + b.o_si;
-        const T* O1 = ws + a.o_om;
-        const T* O2 = ws + b.o_om;
-        for (int q = threadIdx.x; q < rows * p; q += HT) {
-            const int r = q % rows, j = q / rows;
-            T acc;
-            if (r < k1) {
-                acc = S1[(int64_t)j * a.kcap + r];
-                const int gr = sk1[r];
-                for (int c = 0; c < k2; ++c) acc = fmac(-S[(int64_t)sk2[c] * lds + gr], O2[(int64_t)j * b.kcap + c], acc);
-            } else {
-                const int rr = r - k1;
-                acc = S2[(int64_t)j * b.kcap + rr];
-                const int gr = sk2[rr];
-                for (int c = 0; c < k1; ++c) acc = fmac(-S[(int64_t)sk1[c] * lds + gr], O1[(int64_t)j * a.kcap + c], acc);
-            }
-            W[(int64_t)r * p + j] = acc;
-            SL[(int64_t)j * nd.rows_cap + r] = acc;
+        if (t == 0) {
+            for (int r = threadIdx.x; r < k1 + k2; r += HT) iloc[r] = (r < k1) ? sk1[r] : sk2[r - k1];
+            if (threadIdx.x == 0) rows_out[list[blockIdx.x]] = k1 + k2;
         }
-        for (int r = threadIdx.x; r < rows; r += HT) iloc[r] = (r < k1) ? sk1[r] : sk2[r - k1];
+        const int tm = tiles64(nd.kcap);
+        const int part = t / (tm * tn), tt = t % (tm * tn);
+        const int i0 = (tt / tn) * NT_TILE, j0 = (tt % tn) * NT_TILE;
+        // part 0: rows of c1 (coupled to c2's skeleton), part 1: rows of c2
+        const int M = part == 0 ? k1 : k2, K = part == 0 ? k2 : k1, roff = part == 0 ? 0 : k1;
+        if (part > 1 || i0 >= M) return;
+        const int* own = part == 0 ? sk1 : sk2;
+        const int* oth = part == 0 ? sk2 : sk1;
+        const T* Sown = ws + (part == 0 ? a.o_si : b.o_si);
+        const T* Ooth = ws + (part == 0 ? b.o_om : a.o_om);
+        const int kcown = part == 0 ? a.kcap : b.kcap, kcoth = part == 0 ? b.kcap : a.kcap;
+        tile_gemm64<T, false>(
+            M, p, K, i0, j0, [&](int r, int c) { return -S[(int64_t)oth[c] * lds + own[r]]; },
+            [&](int c, int j) { return Ooth[(int64_t)j * kcoth + c]; },
+            [&](int r, int j, T acc) {
+                acc = acc + Sown[(int64_t)j * kcown + r];
+                W[(int64_t)(roff + r) * p + j] = acc;
+                SL[(int64_t)j * nd.rows_cap + roff + r] = acc;
+            });
     }
-    if (threadIdx.x == 0) rows_out[list[blockIdx.x]] = rows;
 }
 
 // Row interpolative decomposition of S_loc from a Householder QR with column
@@ -730,23 +809,26 @@ finish_kernel(const int* __restrict__ list, const HNode* __restrict__ nodes, con
         ld1 = nodes[nd.c1].kcap;
         ld2 = nodes[nd.c2].kcap;
     }
-    for (int q = threadIdx.x; q < k * p; q += HT) {
-        const int a = q % k, j = q / k;
-        T acc = zero<T>();
-        for (int r = 0; r < rows; ++r) {
-            T o;
-            if (nd.c1 < 0) o = Om[(int64_t)j * fr.n + nd.lo + r];
-            else o = (r < k1) ? O1[(int64_t)j * ld1 + r] : O2[(int64_t)j * ld2 + (r - k1)];
-            acc = fmac(X[(int64_t)a * nd.rows_cap + r], o, acc);
-        }
-        OM[(int64_t)j * nd.kcap + a] = acc;
-        SI[(int64_t)j * nd.kcap + a] = SL[(int64_t)j * nd.rows_cap + piv[a]];
-    }
-    for (int a = threadIdx.x; a < k; a += HT) skel[a] = iloc[piv[a]];
+    const int tn = tiles64(p), t = blockIdx.y;
+    if (t == 0)
+        for (int a = threadIdx.x; a < k; a += HT) skel[a] = iloc[piv[a]];
+    const int i0 = (t / tn) * NT_TILE, j0 = (t % tn) * NT_TILE;
+    if (i0 >= k) return;
+    // Om_i = X^T Om_loc (k x p), S_i = S_loc(J, :)
+    tile_gemm64<T, true>(
+        k, p, rows, i0, j0, [&](int a, int r) { return X[(int64_t)a * nd.rows_cap + r]; },
+        [&](int r, int j) {
+            if (nd.c1 < 0) return Om[(int64_t)j * fr.n + nd.lo + r];
+            return (r < k1) ? O1[(int64_t)j * ld1 + r] : O2[(int64_t)j * ld2 + (r - k1)];
+        },
+        [&](int a, int j, T acc) {
+            OM[(int64_t)j * nd.kcap + a] = acc;
+            SI[(int64_t)j * nd.kcap + a] = SL[(int64_t)j * nd.rows_cap + piv[a]];
+        });
 }
 
 // ---------------------------------------------- HSS matvec (nc columns)
-// up: xh_i = X_i^T (x(lo:hi) or [xh_c1; xh_c2])
+// up: xh_i = X_i^T (x(lo:hi) or [xh_c1; xh_c2]); grid (nodes, k x nc tiles)
 template <typename T>
 __global__ void __launch_bounds__(HT)
 hss_up_kernel(const int* __restrict__ list, const HNode* __restrict__ nodes, const T* __restrict__ ws, T* __restrict__ hb,
@@ -766,20 +848,20 @@ hss_up_kernel(const int* __restrict__ list, const HNode* __restrict__ nodes, con
         h1 = hb + nodes[nd.c1].o_xh;
         h2 = hb + nodes[nd.c2].o_xh;
     }
-    for (int q = threadIdx.x; q < k * nc; q += HT) {
-        const int a = q % k, j = q / k;
-        T acc = zero<T>();
-        for (int r = 0; r < rows; ++r) {
-            T v;
-            if (nd.c1 < 0) v = x[(int64_t)j * lx + nd.lo + r];
-            else v = (r < k1) ? h1[(int64_t)j * xh_ld + r] : h2[(int64_t)j * xh_ld + (r - k1)];
-            acc = fmac(X[(int64_t)a * nd.rows_cap + r], v, acc);
-        }
-        xh[(int64_t)j * xh_ld + a] = acc;
-    }
+    const int tn = tiles64(nc), t = blockIdx.y;
+    const int i0 = (t / tn) * NT_TILE, j0 = (t % tn) * NT_TILE;
+    if (i0 >= k) return;
+    tile_gemm64<T, true>(
+        k, nc, rows, i0, j0, [&](int a, int r) { return X[(int64_t)a * nd.rows_cap + r]; },
+        [&](int r, int j) {
+            if (nd.c1 < 0) return x[(int64_t)j * lx + nd.lo + r];
+            return (r < k1) ? h1[(int64_t)j * xh_ld + r] : h2[(int64_t)j * xh_ld + (r - k1)];
+        },
+        [&](int a, int j, T acc) { xh[(int64_t)j * xh_ld + a] = acc; });
 }
 
-// down at inner node i: yh_c1 = S(sk1, sk2) xh_c2 + (X_i yh_i)(0:k1), yh_c2 = S(sk2, sk1) xh_c1 + (X_i yh_i)(k1:)
+// down at inner node i: yh_c1 = S(sk1, sk2) xh_c2 + (X_i yh_i)(0:k1), yh_c2 = S(sk2, sk1) xh_c1 + (X_i yh_i)(k1:);
+// grid (nodes, 2 parts x row tiles x nc tiles), K = [X_i's columns | the sibling's skeleton]
 template <typename T>
 __global__ void __launch_bounds__(HT)
 hss_down_kernel(const int* __restrict__ list, const HNode* __restrict__ nodes, const HFront* __restrict__ fronts,
@@ -793,33 +875,29 @@ hss_down_kernel(const int* __restrict__ list, const HNode* __restrict__ nodes, c
     const int64_t lds = fr.lds;
     const HNode a = nodes[nd.c1], b = nodes[nd.c2];
     const int k1 = kk[nd.c1], k2 = kk[nd.c2];
-    const int* sk1 = iws + a.o_skel;
-    const int* sk2 = iws + b.o_skel;
-    const T* xh1 = hb + a.o_xh;
-    const T* xh2 = hb + b.o_xh;
-    T* yh1 = hb + a.o_yh;
-    T* yh2 = hb + b.o_yh;
     const bool root = (id == fr.root);
     const int k = root ? 0 : kk[id];
     const T* X = ws + nd.o_x;
     const T* yh = hb + nd.o_yh;
-    for (int q = threadIdx.x; q < (k1 + k2) * nc; q += HT) {
-        const int r = q % (k1 + k2), j = q / (k1 + k2);
-        T acc = zero<T>();
-        for (int c = 0; c < k; ++c) acc = fmac(X[(int64_t)c * nd.rows_cap + r], yh[(int64_t)j * xh_ld + c], acc);
-        if (r < k1) {
-            const int gr = sk1[r];
-            for (int c = 0; c < k2; ++c) acc = fmac(S[(int64_t)sk2[c] * lds + gr], xh2[(int64_t)j * xh_ld + c], acc);
-            yh1[(int64_t)j * xh_ld + r] = acc;
-        } else {
-            const int rr = r - k1, gr = sk2[rr];
-            for (int c = 0; c < k1; ++c) acc = fmac(S[(int64_t)sk1[c] * lds + gr], xh1[(int64_t)j * xh_ld + c], acc);
-            yh2[(int64_t)j * xh_ld + rr] = acc;
-        }
-    }
+    const int tn = tiles64(nc), tm = tiles64(nd.kcap), t = blockIdx.y;
+    const int part = t / (tm * tn), tt = t % (tm * tn);
+    const int i0 = (tt / tn) * NT_TILE, j0 = (tt % tn) * NT_TILE;
+    const int M = part == 0 ? k1 : k2, Ko = part == 0 ? k2 : k1, roff = part == 0 ? 0 : k1;
+    if (part > 1 || i0 >= M) return;
+    const int* own = iws + (part == 0 ? a.o_skel : b.o_skel);
+    const int* oth = iws + (part == 0 ? b.o_skel : a.o_skel);
+    const T* xo = hb + (part == 0 ? b.o_xh : a.o_xh);
+    T* yo = hb + (part == 0 ? a.o_yh : b.o_yh);
+    tile_gemm64<T, false>(
+        M, nc, k + Ko, i0, j0,
+        [&](int r, int l) {
+            return l < k ? X[(int64_t)l * nd.rows_cap + roff + r] : S[(int64_t)oth[l - k] * lds + own[r]];
+        },
+        [&](int l, int j) { return l < k ? yh[(int64_t)j * xh_ld + l] : xo[(int64_t)j * xh_ld + (l - k)]; },
+        [&](int r, int j, T acc) { yo[(int64_t)j * xh_ld + r] = acc; });
 }
 
-// leaves: y(lo:hi) = D x(lo:hi) + X yh
+// leaves: y(lo:hi) = D x(lo:hi) + X yh; grid (nodes, rows x nc tiles), K = [D's columns | X's columns]
 template <typename T>
 __global__ void __launch_bounds__(HT)
 hss_leaf_kernel(const int* __restrict__ list, const HNode* __restrict__ nodes, const HFront* __restrict__ fronts,
@@ -840,14 +918,16 @@ hss_leaf_kernel(const int* __restrict__ list, const HNode* __restrict__ nodes, c
     const T* x = xin[nd.front];
     T* y = yout[nd.front];
     const int64_t lx = ldx[nd.front], ly = ldy[nd.front];
-    for (int q = threadIdx.x; q < rows * nc; q += HT) {
-        const int r = q % rows, j = q / rows;
-        T acc = zero<T>();
-        for (int c = 0; c < rows; ++c)
-            acc = fmac(S[(int64_t)(nd.lo + c) * lds + nd.lo + r], x[(int64_t)j * lx + nd.lo + c], acc);
-        for (int c = 0; c < k; ++c) acc = fmac(X[(int64_t)c * nd.rows_cap + r], yh[(int64_t)j * xh_ld + c], acc);
-        y[(int64_t)j * ly + nd.lo + r] = acc;
-    }
+    const int tn = tiles64(nc), t = blockIdx.y;
+    const int i0 = (t / tn) * NT_TILE, j0 = (t % tn) * NT_TILE;
+    if (i0 >= rows) return;
+    tile_gemm64<T, false>(
+        rows, nc, rows + k, i0, j0,
+        [&](int r, int l) {
+            return l < rows ? S[(int64_t)(nd.lo + l) * lds + nd.lo + r] : X[(int64_t)(l - rows) * nd.rows_cap + r];
+        },
+        [&](int l, int j) { return l < rows ? x[(int64_t)j * lx + nd.lo + l] : yh[(int64_t)j * xh_ld + (l - rows)]; },
+        [&](int r, int j, T acc) { y[(int64_t)j * ly + nd.lo + r] = acc; });
 }
 
 // coupling blocks of inner node i: B12 = S(skel_c1, skel_c2) (k1 x k2), B21 = S(skel_c2, skel_c1)
@@ -1014,7 +1094,7 @@ template <typename T>
 ndhss_status hss_matvec_run(const std::vector<HNode>& nodes, const std::vector<char>& keep, int maxlev,
                             const HNode* dnodes, const HFront* dfr, const T* ws, T* hb, const int* iws, const int* kk,
                             const int* rows, const T* const* dx, const int64_t* dlx, T* const* dy, const int64_t* dly,
-                            const int* dncs, int64_t xh_ld, cudaStream_t st) {
+                            const int* dncs, int nc_max, int64_t xh_ld, cudaStream_t st) {
     std::vector<int> flat;
     std::vector<size_t> up_off(maxlev + 2, 0), dn_off(maxlev + 2, 0);
     for (int l = 0; l <= maxlev; ++l) {            // up lists (non-root)
@@ -1035,21 +1115,31 @@ ndhss_status hss_matvec_run(const std::vector<HNode>& nodes, const std::vector<c
     const size_t leaf_cnt = flat.size() - leaf_off;
     DeviceVec<int> dflat(st);
     HSS_TRY(dflat.upload(flat, st));
+    // tile grids: k x nc (up), 2 parts x kcap x nc (down), leaf rows x nc (leaves)
+    int kcap = 1, leaf_rows = 1;
+    for (size_t i = 0; i < nodes.size(); ++i) {
+        if (!keep[nodes[i].front]) continue;
+        kcap = std::max(kcap, nodes[i].kcap);
+        if (nodes[i].c1 < 0) leaf_rows = std::max(leaf_rows, nodes[i].hi - nodes[i].lo);
+    }
+    const unsigned tnc = (unsigned)tiles64(nc_max);
     for (int l = maxlev; l >= 1; --l) {
         const unsigned cnt = (unsigned)(up_off[l + 1] - up_off[l]);
         if (!cnt) continue;
-        hss_up_kernel<T><<<cnt, HT, 0, st>>>(dflat.p + up_off[l], dnodes, ws, hb, kk, rows, dx, dlx, dncs, xh_ld);
+        hss_up_kernel<T><<<dim3(cnt, tiles64(kcap) * tnc), HT, 0, st>>>(dflat.p + up_off[l], dnodes, ws, hb, kk, rows, dx,
+                                                                         dlx, dncs, xh_ld);
         NDHSS_LAUNCH_CHECK("hss_up_kernel");
     }
     for (int l = 0; l <= maxlev; ++l) {
         const unsigned cnt = (unsigned)(dn_off[l + 1] - dn_off[l]);
         if (!cnt) continue;
-        hss_down_kernel<T><<<cnt, HT, 0, st>>>(dflat.p + dn_off[l], dnodes, dfr, ws, hb, iws, kk, dncs, xh_ld);
+        hss_down_kernel<T><<<dim3(cnt, 2 * tiles64(kcap) * tnc), HT, 0, st>>>(dflat.p + dn_off[l], dnodes, dfr, ws, hb,
+                                                                               iws, kk, dncs, xh_ld);
         NDHSS_LAUNCH_CHECK("hss_down_kernel");
     }
     if (leaf_cnt) {
-        hss_leaf_kernel<T><<<(unsigned)leaf_cnt, HT, 0, st>>>(dflat.p + leaf_off, dnodes, dfr, ws, hb, kk, dx, dlx, dy,
-                                                              dly, dncs, xh_ld);
+        hss_leaf_kernel<T><<<dim3((unsigned)leaf_cnt, tiles64(leaf_rows) * tnc), HT, 0, st>>>(
+            dflat.p + leaf_off, dnodes, dfr, ws, hb, kk, dx, dlx, dy, dly, dncs, xh_ld);
         NDHSS_LAUNCH_CHECK("hss_leaf_kernel");
     }
     return NDHSS_OK;
@@ -1498,13 +1588,19 @@ ndhss_status compress_problems(std::vector<Problem>& probs, bool lowrank, const 
             for (int l = maxlev; l >= 1; --l) {
                 const unsigned cnt = (unsigned)(loff[l + 1] - loff[l]);
                 if (!cnt) continue;
-                form_sloc_kernel<T><<<cnt, HT, 0, st>>>(dflat.p + loff[l], dnodes.p, dfr.p, ws.p, iws.p, kk.p, rows.p);
+                int leaf_rows = 1;
+                for (size_t q = loff[l]; q < loff[l + 1]; ++q)
+                    if (nodes[flat[q]].c1 < 0) leaf_rows = std::max(leaf_rows, nodes[flat[q]].hi - nodes[flat[q]].lo);
+                const unsigned tf = (unsigned)(std::max(tiles64(leaf_rows), 2 * tiles64(kcap)) * tiles64(p));
+                form_sloc_kernel<T><<<dim3(cnt, tf), HT, 0, st>>>(dflat.p + loff[l], dnodes.p, dfr.p, ws.p, iws.p, kk.p,
+                                                                 rows.p);
                 NDHSS_LAUNCH_CHECK("form_sloc_kernel");
                 {
                     const ndhss_status rc = launch_row_id(loff[l], loff[l + 1]);
                     if (rc != NDHSS_OK) return rc;
                 }
-                finish_kernel<T><<<cnt, HT, 0, st>>>(dflat.p + loff[l], dnodes.p, dfr.p, ws.p, iws.p, kk.p, rows.p);
+                finish_kernel<T><<<dim3(cnt, tiles64(kcap) * tiles64(p)), HT, 0, st>>>(dflat.p + loff[l], dnodes.p, dfr.p,
+                                                                                      ws.p, iws.p, kk.p, rows.p);
                 NDHSS_LAUNCH_CHECK("finish_kernel");
             }
             // estimator: Zt = HSS(S) Omega~
@@ -1528,7 +1624,7 @@ ndhss_status compress_problems(std::vector<Problem>& probs, bool lowrank, const 
             HSS_TRY(dncs.upload(ncs, st));
             std::vector<char> all(nf, 1);
             ndhss_status rc = hss_matvec_run<T>(nodes, all, maxlev, dnodes.p, dfr.p, ws.p, ws.p, iws.p, kk.p, rows.p, dx.p,
-                                               dlx.p, dy.p, dly.p, dncs.p, (int64_t)kcap, st);
+                                               dlx.p, dy.p, dly.p, dncs.p, r, (int64_t)kcap, st);
             if (rc != NDHSS_OK) return rc;
         }
         DeviceVec<double> dn(st);
