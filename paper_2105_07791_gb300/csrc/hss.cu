@@ -163,47 +163,64 @@ struct GemmJob {
     int transA = 0, transB = 0;   // operand stored transposed (plain transpose, no conjugation)
 };
 
+// 64 x 64 tiles of every job; blockIdx.z = job * ksplit + split.  The K
+// chunks are staged in shared memory, the next chunk's loads in registers
+// while the current chunk is multiplied.  ksplit > 1: the CTA of split q
+// takes K chunks q, q + ksplit, ... and writes its raw partial tile to
+// part[(z * tiles + tile) * 4096]; bgemm_reduce_kernel adds the partials in
+// split order (deterministic) and applies alpha / beta.
 template <typename T>
-__global__ void __launch_bounds__(256) bgemm_kernel(const GemmJob* __restrict__ jobs) {
+__global__ void __launch_bounds__(256) bgemm_kernel(const GemmJob* __restrict__ jobs, int ksplit, T* __restrict__ part) {
     constexpr int TT = 64, TK = 16;
     __shared__ T sA[TK][TT];
     __shared__ T sB[TK][TT];
-    const GemmJob jb = jobs[blockIdx.z];
+    const int job = blockIdx.z / ksplit, split = blockIdx.z % ksplit;
+    const GemmJob jb = jobs[job];
     const int64_t i0 = (int64_t)blockIdx.x * TT, j0 = (int64_t)blockIdx.y * TT;
     if (i0 >= jb.M || j0 >= jb.N) return;
     const T* A = static_cast<const T*>(jb.A);
     const T* B = static_cast<const T*>(jb.B);
-    T* Cm = static_cast<T*>(jb.C);
     const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
     T acc[4][4];
 #pragma unroll
     for (int a = 0; a < 4; ++a)
 #pragma unroll
         for (int b = 0; b < 4; ++b) acc[a][b] = zero<T>();
-    for (int kc = 0; kc < jb.K; kc += TK) {
-        if (!jb.transA) {
-            for (int q = tid; q < TK * TT; q += 256) {
-                const int ii = q % TT, l = q / TT;
-                sA[l][ii] = (kc + l < jb.K && i0 + ii < jb.M) ? A[(int64_t)(kc + l) * jb.lda + i0 + ii] : zero<T>();
-            }
-        } else {
-            for (int q = tid; q < TK * TT; q += 256) {
-                const int l = q % TK, ii = q / TK;
-                sA[l][ii] = (kc + l < jb.K && i0 + ii < jb.M) ? A[(i0 + ii) * jb.lda + kc + l] : zero<T>();
-            }
+    // element u of this thread's share of the A and B chunks at K offset kc
+    auto a_idx = [&](int u, int& ii, int& l) {
+        const int q = tid + 256 * u;
+        if (!jb.transA) { ii = q % TT; l = q / TT; } else { l = q % TK; ii = q / TK; }
+    };
+    auto b_idx = [&](int u, int& jj, int& l) {
+        const int q = tid + 256 * u;
+        if (!jb.transB) { l = q % TK; jj = q / TK; } else { jj = q % TT; l = q / TT; }
+    };
+    T ra[4], rb[4];
+    auto load = [&](int kc) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            int ii, l, jj, lb;
+            a_idx(u, ii, l);
+            b_idx(u, jj, lb);
+            const bool va = kc + l < jb.K && i0 + ii < jb.M, vb = kc + lb < jb.K && j0 + jj < jb.N;
+            ra[u] = va ? (!jb.transA ? A[(int64_t)(kc + l) * jb.lda + i0 + ii] : A[(i0 + ii) * jb.lda + kc + l]) : zero<T>();
+            rb[u] = vb ? (!jb.transB ? B[(j0 + jj) * jb.ldb + kc + lb] : B[(int64_t)(kc + lb) * jb.ldb + j0 + jj]) : zero<T>();
         }
-        if (!jb.transB) {
-            for (int q = tid; q < TK * TT; q += 256) {
-                const int l = q % TK, jj = q / TK;
-                sB[l][jj] = (kc + l < jb.K && j0 + jj < jb.N) ? B[(j0 + jj) * jb.ldb + kc + l] : zero<T>();
-            }
-        } else {
-            for (int q = tid; q < TK * TT; q += 256) {
-                const int jj = q % TT, l = q / TT;
-                sB[l][jj] = (kc + l < jb.K && j0 + jj < jb.N) ? B[(int64_t)(kc + l) * jb.ldb + j0 + jj] : zero<T>();
-            }
+    };
+    const int step = TK * ksplit;
+    int kc = split * TK;
+    if (kc < jb.K) load(kc);
+    for (; kc < jb.K; kc += step) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            int ii, l, jj, lb;
+            a_idx(u, ii, l);
+            b_idx(u, jj, lb);
+            sA[l][ii] = ra[u];
+            sB[lb][jj] = rb[u];
         }
         __syncthreads();
+        if (kc + step < jb.K) load(kc + step);
 #pragma unroll
         for (int l = 0; l < TK; ++l) {
             T av[4], bv[4];
@@ -218,7 +235,16 @@ __global__ void __launch_bounds__(256) bgemm_kernel(const GemmJob* __restrict__ 
         }
         __syncthreads();
     }
+    if (ksplit > 1) {
+        T* P = part + ((int64_t)blockIdx.z * gridDim.x * gridDim.y + (int64_t)blockIdx.y * gridDim.x + blockIdx.x) * (TT * TT);
+#pragma unroll
+        for (int b = 0; b < 4; ++b)
+#pragma unroll
+            for (int a = 0; a < 4; ++a) P[(ty + 16 * b) * TT + tx + 16 * a] = acc[a][b];
+        return;
+    }
     using real = typename Tr<T>::real;
+    T* Cm = static_cast<T*>(jb.C);
     for (int b = 0; b < 4; ++b) {
         const int64_t j = j0 + ty + 16 * b;
         if (j >= jb.N) continue;
@@ -229,6 +255,28 @@ __global__ void __launch_bounds__(256) bgemm_kernel(const GemmJob* __restrict__ 
             const T v = scale(acc[a][b], (real)jb.alpha);
             *dst = jb.beta ? (*dst + v) : v;
         }
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) bgemm_reduce_kernel(const GemmJob* __restrict__ jobs, int ksplit,
+                                                           const T* __restrict__ part) {
+    constexpr int TT = 64;
+    const GemmJob jb = jobs[blockIdx.z];
+    const int64_t i0 = (int64_t)blockIdx.x * TT, j0 = (int64_t)blockIdx.y * TT;
+    if (i0 >= jb.M || j0 >= jb.N) return;
+    using real = typename Tr<T>::real;
+    T* Cm = static_cast<T*>(jb.C);
+    const int64_t tiles = (int64_t)gridDim.x * gridDim.y, tile = (int64_t)blockIdx.y * gridDim.x + blockIdx.x;
+    for (int e = threadIdx.x; e < TT * TT; e += 256) {
+        const int il = e % TT, jl = e / TT;
+        const int64_t i = i0 + il, j = j0 + jl;
+        if (i >= jb.M || j >= jb.N) continue;
+        T acc = zero<T>();
+        for (int q = 0; q < ksplit; ++q) acc = acc + part[(((int64_t)blockIdx.z * ksplit + q) * tiles + tile) * (TT * TT) + e];
+        T* dst = Cm + j * jb.ldc + i;
+        const T v = scale(acc, (real)jb.alpha);
+        *dst = jb.beta ? (*dst + v) : v;
     }
 }
 
@@ -1087,6 +1135,44 @@ struct DeviceVec {
             return set_error(NDHSS_ERR_CUDA, "hss: %s failed: %s", #expr, cudaGetErrorString(e_));           \
     } while (0)
 
+// The batched GEMM of a job list: one launch of 64 x 64 tiles, or, when the
+// tiles of all jobs leave the GPU mostly idle and K is long, K split over
+// ksplit CTAs per tile plus an ordered reduction of their partials.
+template <typename T>
+ndhss_status run_bgemm(const std::vector<GemmJob>& jobs, cudaStream_t st) {
+    if (jobs.empty()) return NDHSS_OK;
+    int maxM = 1, maxN = 1, maxK = 1;
+    for (const GemmJob& g : jobs) {
+        maxM = std::max(maxM, g.M);
+        maxN = std::max(maxN, g.N);
+        maxK = std::max(maxK, g.K);
+    }
+    const int tm = (maxM + 63) / 64, tn = (maxN + 63) / 64;
+    int dev = 0, sms = 1;
+    HSS_TRY(cudaGetDevice(&dev));
+    HSS_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const int64_t base = (int64_t)tm * tn * (int64_t)jobs.size();
+    int ks = 1;
+    if (base < 2 * sms && maxK >= 256)
+        ks = (int)std::min<int64_t>({(2 * sms + base - 1) / base, maxK / 128, 16});
+    ks = std::max(ks, 1);
+    DeviceVec<GemmJob> dj(st);
+    HSS_TRY(dj.upload(jobs, st));
+    const size_t per = (size_t)std::max(1, 65535 / ks);     // jobs per launch (grid z limit)
+    DeviceVec<T> part(st);
+    if (ks > 1) HSS_TRY(part.alloc((size_t)std::min(per, jobs.size()) * ks * tm * tn * 4096));
+    for (size_t j0 = 0; j0 < jobs.size(); j0 += per) {
+        const unsigned nj = (unsigned)std::min(per, jobs.size() - j0);
+        bgemm_kernel<T><<<dim3(tm, tn, nj * ks), 256, 0, st>>>(dj.p + j0, ks, part.p);
+        NDHSS_LAUNCH_CHECK("bgemm_kernel");
+        if (ks > 1) {
+            bgemm_reduce_kernel<T><<<dim3(tm, tn, nj), 256, 0, st>>>(dj.p + j0, ks, part.p);
+            NDHSS_LAUNCH_CHECK("bgemm_reduce_kernel");
+        }
+    }
+    return NDHSS_OK;
+}
+
 
 // y = A_HSS x for the fronts listed in the node table: up-sweep deepest level
 // first, coupling + down-sweep root first, then the leaf blocks.
@@ -1452,10 +1538,10 @@ ndhss_status compress_problems(std::vector<Problem>& probs, bool lowrank, const 
             maxM = std::max(maxM, pb.n);
             maxN = std::max(maxN, p);
         }
-        DeviceVec<GemmJob> dgm(st);
-        HSS_TRY(dgm.upload(gm, st));
-        bgemm_kernel<T><<<dim3((maxM + 63) / 64, (maxN + 63) / 64, (unsigned)gm.size()), 256, 0, st>>>(dgm.p);
-        NDHSS_LAUNCH_CHECK("bgemm_kernel");
+        {
+            const ndhss_status rc = run_bgemm<T>(gm, st);
+            if (rc != NDHSS_OK) return rc;
+        }
         // node lists per HSS level
         std::vector<std::vector<int>> bylev(maxlev + 1);
         for (size_t i = 0; i < nodes.size(); ++i) bylev[nodes[i].level].push_back((int)i);
@@ -1577,13 +1663,11 @@ ndhss_status compress_problems(std::vector<Problem>& probs, bool lowrank, const 
                 g2.push_back({fr[i].RJ, fr[i].Ot, fr[i].T1, kcap, fr[i].ncol, kcap, k, r, fr[i].ncol, 0, 1.0});
                 g3.push_back({ws.p + nd.o_x, fr[i].T1, fr[i].Zt, nd.rows_cap, kcap, fr[i].n, fr[i].n, r, k, 0, 1.0});
             }
-            DeviceVec<GemmJob> dg2(st), dg3(st);
-            HSS_TRY(dg2.upload(g2, st));
-            HSS_TRY(dg3.upload(g3, st));
-            bgemm_kernel<T><<<dim3((kcap + 63) / 64, (r + 63) / 64, nf), 256, 0, st>>>(dg2.p);
-            NDHSS_LAUNCH_CHECK("bgemm_kernel");
-            bgemm_kernel<T><<<dim3((maxM + 63) / 64, (r + 63) / 64, nf), 256, 0, st>>>(dg3.p);
-            NDHSS_LAUNCH_CHECK("bgemm_kernel");
+            {
+                ndhss_status rc = run_bgemm<T>(g2, st);
+                if (rc == NDHSS_OK) rc = run_bgemm<T>(g3, st);
+                if (rc != NDHSS_OK) return rc;
+            }
         } else {
             for (int l = maxlev; l >= 1; --l) {
                 const unsigned cnt = (unsigned)(loff[l + 1] - loff[l]);
@@ -1808,12 +1892,8 @@ ndhss_status compress_problems(std::vector<Problem>& probs, bool lowrank, const 
                         gj2.push_back({up[nd.c2], X + k1, U + s1, uld[nd.c2], nd.rows_cap, uld[q], s2, k, k2, 0, 1.0});
                     }
                     if (gj2.empty()) continue;
-                    int mM = 1, mN = 1;
-                    for (auto& g : gj2) { mM = std::max(mM, g.M); mN = std::max(mN, g.N); }
-                    DeviceVec<GemmJob> dg(st);
-                    HSS_TRY(dg.upload(gj2, st));
-                    bgemm_kernel<T><<<dim3((mM + 63) / 64, (mN + 63) / 64, (unsigned)gj2.size()), 256, 0, st>>>(dg.p);
-                    NDHSS_LAUNCH_CHECK("bgemm_kernel");
+                    const ndhss_status rc = run_bgemm<T>(gj2, st);
+                    if (rc != NDHSS_OK) return rc;
                 }
                 // coupling blocks (all gathered before any block of S is overwritten)
                 std::vector<T*> p12, p21;
@@ -1860,13 +1940,9 @@ ndhss_status compress_problems(std::vector<Problem>& probs, bool lowrank, const 
                     n2 = std::max({n2, s1, s2});
                 }
                 if (!g1.empty()) {
-                    DeviceVec<GemmJob> dg1(st), dg2(st);
-                    HSS_TRY(dg1.upload(g1, st));
-                    HSS_TRY(dg2.upload(g2, st));
-                    bgemm_kernel<T><<<dim3((m1 + 63) / 64, (n1 + 63) / 64, (unsigned)g1.size()), 256, 0, st>>>(dg1.p);
-                    NDHSS_LAUNCH_CHECK("bgemm_kernel");
-                    bgemm_kernel<T><<<dim3((m2 + 63) / 64, (n2 + 63) / 64, (unsigned)g2.size()), 256, 0, st>>>(dg2.p);
-                    NDHSS_LAUNCH_CHECK("bgemm_kernel");
+                    ndhss_status rc = run_bgemm<T>(g1, st);
+                    if (rc == NDHSS_OK) rc = run_bgemm<T>(g2, st);
+                    if (rc != NDHSS_OK) return rc;
                 }
                 HSS_TRY(cudaStreamSynchronize(st));
                 for (int i : done) {
