@@ -20,6 +20,7 @@
 // S_i = S_loc(J_i, :) upward.
 #include <algorithm>
 #include <climits>
+#include <cstdlib>
 #include <cmath>
 #include <vector>
 
@@ -630,7 +631,7 @@ constexpr int RID_NW = RID_THREADS / 32;
 constexpr int RID_KMAX = 256;                 // ranks stay below the 256-sample limit
 constexpr int RID_MAX_CLUSTER = 8;
 constexpr size_t RID_SMEM = 200 * 1024;       // dynamic shared memory of one CTA's share
-constexpr int RID_SPLIT_COLS = 64;
+constexpr int RID_SPLIT_COLS = 128;
 
 __host__ __device__ __forceinline__ int rid_lpc(int p) { return p <= 64 ? 8 : p <= 128 ? 16 : 32; }
 
@@ -789,13 +790,14 @@ row_id_cluster_kernel(const int* __restrict__ list, const HNode* __restrict__ no
         publish(best, nb, par ^ 1);
     }
     const int k = t;
-    // R11 (strictly upper part) from the pivot columns' owners into the global
-    // copy of W, which no CTA reads any more; diagonal = beta
-    T* R11 = ws + nd.o_w;
-    for (int a = 1; a < k; ++a) {
-        const int c = s_order[a] - c_lo;
-        if (c >= 0 && c < nloc)
-            for (int i = tid; i < a; i += RID_THREADS) R11[(int64_t)a * k + i] = Ws[(size_t)c * lds + i];
+    // R11 stays in the pivot columns, in the shared memory of their owners
+    // (the pivot columns are not written below): one pointer per column,
+    // local or through distributed shared memory
+    __shared__ const T* s_pcol[RID_KMAX];
+    for (int a = tid; a < k; a += RID_THREADS) {
+        const int cb = s_order[a], owner = cb / chunk;
+        s_pcol[a] = (owner == rk) ? Ws + (size_t)(cb - c_lo) * lds
+                                  : cl.map_shared_rank(Ws, owner) + (size_t)(cb - owner * chunk) * lds;
     }
     if (C > 1) cl.sync(); else __syncthreads();
     // T = R11^{-1} R12 in place of R12 (one column per thread)
@@ -804,11 +806,12 @@ row_id_cluster_kernel(const int* __restrict__ list, const HNode* __restrict__ no
         T* col = Ws + (size_t)c * lds;
         for (int i = k - 1; i >= 0; --i) {
             T acc = col[i];
-            for (int l = i + 1; l < k; ++l) acc = fmac(-R11[(int64_t)l * k + i], col[l], acc);
+            for (int l = i + 1; l < k; ++l) acc = fmac(-s_pcol[l][i], col[l], acc);
             col[i] = acc * recip(s_beta[i]);
         }
     }
-    __syncthreads();
+    // no CTA leaves while another may still read its pivot columns
+    if (C > 1) cl.sync(); else __syncthreads();
     T* X = ws + nd.o_x;
     int* piv = iws + nd.o_piv;
     for (int q = tid; q < nloc * k; q += RID_THREADS) {
@@ -1009,9 +1012,20 @@ __global__ void est_norm_kernel(const HFront* __restrict__ fronts, int r, double
     const T* Zt = static_cast<const T*>(fr.Zt);
     const int64_t n = (int64_t)fr.n * r;
     double e = 0.0, f = 0.0;
-    for (int64_t q = threadIdx.x; q < n; q += blockDim.x) {
-        e += nrm2v(Yt[q] - Zt[q]);
-        f += nrm2v(Yt[q]);
+    // eight elements of each operand in flight per thread
+    for (int64_t q0 = threadIdx.x; q0 < n; q0 += 8 * (int64_t)blockDim.x) {
+        T y[8], z[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int64_t q = q0 + (int64_t)u * blockDim.x;
+            y[u] = q < n ? Yt[q] : zero<T>();
+            z[u] = q < n ? Zt[q] : zero<T>();
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            e += nrm2v(y[u] - z[u]);
+            f += nrm2v(y[u]);
+        }
     }
     __shared__ double se[HT], sf[HT];
     se[threadIdx.x] = e;
