@@ -58,47 +58,76 @@ __device__ __forceinline__ c128 cdiv(c128 a, c128 b) { return a * recip(b); }
 __device__ __forceinline__ double cdiv(double a, double b) { return a / b; }
 
 // ----------------------------------------------------------------- SpMV
-// acc + a * b.  GB300's FP64 pipe is narrow, and most entries of the FEM
-// matrices are real (the impedance term is on the boundary only): the FMAs
-// with a zero imaginary part are skipped.  The test reads the bit pattern
-// (a float64 compare would itself take an FP64-pipe slot; -0.0 just takes
-// the full product).  The rounding of the remaining operations is that of
-// the full product.
-__device__ __forceinline__ double spmv_mac(double a, double b, double c) { return fma(a, b, c); }
-__device__ __forceinline__ c128 spmv_mac(c128 a, c128 b, c128 c) {
-    c.x = fma(a.x, b.x, c.x);
-    c.y = fma(a.x, b.y, c.y);
-    if (__double_as_longlong(a.y) != 0) {
-        c.x = fma(-a.y, b.y, c.x);
-        c.y = fma(a.y, b.x, c.y);
+// GB300's FP64 pipe retires 2 DFMA per clock per SM, and a predicated-off
+// FP64 instruction still takes its slot, so the row product issues exactly
+// the FMAs it needs: TPR threads per row load all their entries of the row
+// at once (up to SP_U each; then the x gathers), the FMA loops run over a
+// warp-uniform count (the longest row of the warp, dispatched to an
+// exact-count instance), and the imaginary parts of the matrix entries
+// (zero inside the domain: the impedance term sits on the boundary) are
+// multiplied only when some lane of the warp holds one, after the products
+// of the real parts of the same batch of entries.
+constexpr int SP_TPR = 2, SP_U = 6;   // best measured on the 256 x 256 P2 Helmholtz matrix (cold L2: 31 us; 4 x 8: 54 us)
+static_assert(SP_U <= 8, "spmv_row dispatches up to eight passes per batch");
+
+__device__ __forceinline__ bool spmv_cplx(double) { return false; }
+__device__ __forceinline__ bool spmv_cplx(c128 a) { return __double_as_longlong(a.y) != 0; }
+
+template <int NP>
+__device__ __forceinline__ void spmv_fmas(const double* a, const double* xv, double& acc, bool) {
+#pragma unroll
+    for (int u = 0; u < NP; ++u) acc = fma(a[u], xv[u], acc);
+}
+template <int NP>
+__device__ __forceinline__ void spmv_fmas(const c128* a, const c128* xv, c128& acc, bool any_cplx) {
+#pragma unroll
+    for (int u = 0; u < NP; ++u) {
+        acc.x = fma(a[u].x, xv[u].x, acc.x);
+        acc.y = fma(a[u].x, xv[u].y, acc.y);
     }
-    return c;
+    if (any_cplx) {
+#pragma unroll
+        for (int u = 0; u < NP; ++u) {
+            acc.x = fma(-a[u].y, xv[u].y, acc.x);
+            acc.y = fma(a[u].y, xv[u].x, acc.y);
+        }
+    }
 }
 
-// TPR threads per row; each issues all U of its column indices and values
-// at once, then the U gathers of x, so a row costs three dependent memory
-// round trips (row pointers, entries, x) instead of two per entry.
+// this thread's share of row `row` (lane = its index among the row's TPR
+// threads; U <= 8 entries per batch); `valid` false for threads past the
+// last row (they still take part in the warp's votes)
 template <typename V, int TPR, int U>
-__global__ void __launch_bounds__(256) spmv_kernel(int n, const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col,
-                                                   const V* __restrict__ vals, const V* __restrict__ x, V* __restrict__ y) {
-    const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int64_t row = gt / TPR;
-    const int lane = (int)(gt % TPR);
-    if (row >= n) return;               // whole TPR groups leave together
-    const int k0 = rowptr[row], k1 = rowptr[row + 1];
+__device__ __forceinline__ V spmv_row(bool valid, int64_t row, int lane, const int32_t* __restrict__ rowptr,
+                                      const int32_t* __restrict__ col, const V* __restrict__ vals,
+                                      const V* __restrict__ x) {
+    const int k0 = valid ? rowptr[row] : 0, k1 = valid ? rowptr[row + 1] : 0;
+    int np = (k1 - k0 + TPR - 1) / TPR;          // passes this row needs
+    for (int o = 16; o; o >>= 1) np = max(np, __shfl_xor_sync(0xffffffffu, np, o));
     V acc = zero<V>();
-    for (int base = k0; base < k1; base += U * TPR) {
+    for (int p0 = 0; p0 < np; p0 += U) {
         int c[U];
-        V a[U];
+        V a[U], xv[U];
 #pragma unroll
         for (int u = 0; u < U; ++u) {
-            const int k = base + lane + u * TPR;
-            c[u] = k < k1 ? col[k] : -1;
-            a[u] = k < k1 ? vals[k] : zero<V>();
+            const int k = k0 + lane + (p0 + u) * TPR;
+            const bool ok = p0 + u < np && k < k1;
+            c[u] = ok ? col[k] : -1;
+            a[u] = ok ? vals[k] : zero<V>();
         }
+        bool cx = false;
 #pragma unroll
-        for (int u = 0; u < U; ++u)
-            if (c[u] >= 0) acc = spmv_mac(a[u], x[c[u]], acc);
+        for (int u = 0; u < U; ++u) {
+            xv[u] = c[u] >= 0 ? x[c[u]] : zero<V>();
+            cx = cx || spmv_cplx(a[u]);
+        }
+        const bool any_cplx = __any_sync(0xffffffffu, cx);
+        switch (min(U, np - p0)) {
+#define NDHSS_SPF(NN) case NN: if constexpr (NN <= U) spmv_fmas<NN>(a, xv, acc, any_cplx); break;
+            NDHSS_SPF(1) NDHSS_SPF(2) NDHSS_SPF(3) NDHSS_SPF(4) NDHSS_SPF(5) NDHSS_SPF(6) NDHSS_SPF(7) NDHSS_SPF(8)
+#undef NDHSS_SPF
+            default: break;
+        }
     }
     if constexpr (sizeof(V) == 8) {
         for (int o = TPR / 2; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o, TPR);
@@ -108,15 +137,24 @@ __global__ void __launch_bounds__(256) spmv_kernel(int n, const int32_t* __restr
             acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o, TPR);
         }
     }
-    if (lane == 0) y[row] = acc;
+    return acc;
+}
+
+template <typename V, int TPR, int U>
+__global__ void __launch_bounds__(256) spmv_kernel(int n, const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+                                                   const V* __restrict__ vals, const V* __restrict__ x, V* __restrict__ y) {
+    const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t row = gt / TPR;
+    const int lane = (int)(gt % TPR);
+    const V acc = spmv_row<V, TPR, U>(row < n, row, lane, rowptr, col, vals, x);
+    if (row < n && lane == 0) y[row] = acc;
 }
 
 template <typename V>
 ndhss_status spmv_launch(int n, const int32_t* rowptr, const int32_t* col, const V* vals, const V* x, V* y,
                          cudaStream_t st) {
-    const int64_t threads = (int64_t)n * 4;
-    const unsigned blocks = (unsigned)((threads + 255) / 256);
-    spmv_kernel<V, 4, 4><<<blocks, 256, 0, st>>>(n, rowptr, col, vals, x, y);
+    const int64_t threads = (int64_t)n * SP_TPR;
+    spmv_kernel<V, SP_TPR, SP_U><<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(n, rowptr, col, vals, x, y);
     NDHSS_LAUNCH_CHECK("spmv_kernel");
     return NDHSS_OK;
 }
@@ -315,7 +353,7 @@ __global__ void __launch_bounds__(256) gm_begin_kernel(GmDev<V>* S, V* __restric
 }
 
 // t = s A v with v, t, s chosen by gm_begin (see spmv_kernel)
-template <typename V, int TPR, int U>
+template <typename V>
 __global__ void __launch_bounds__(256) gm_spmv_kernel(int n, const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col,
                                                       const V* __restrict__ vals, const GmDev<V>* S) {
     if (S->done) return;
@@ -323,33 +361,10 @@ __global__ void __launch_bounds__(256) gm_spmv_kernel(int n, const int32_t* __re
     V* __restrict__ y = S->spmv_out;
     const double sc = S->spmv_scale;
     const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int64_t row = gt / TPR;
-    const int lane = (int)(gt % TPR);
-    if (row >= n) return;
-    const int k0 = rowptr[row], k1 = rowptr[row + 1];
-    V acc = zero<V>();
-    for (int base = k0; base < k1; base += U * TPR) {
-        int c[U];
-        V a[U];
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-            const int k = base + lane + u * TPR;
-            c[u] = k < k1 ? col[k] : -1;
-            a[u] = k < k1 ? vals[k] : zero<V>();
-        }
-#pragma unroll
-        for (int u = 0; u < U; ++u)
-            if (c[u] >= 0) acc = spmv_mac(a[u], x[c[u]], acc);
-    }
-    if constexpr (sizeof(V) == 8) {
-        for (int o = TPR / 2; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o, TPR);
-    } else {
-        for (int o = TPR / 2; o; o >>= 1) {
-            acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o, TPR);
-            acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o, TPR);
-        }
-    }
-    if (lane == 0) y[row] = scale(acc, sc);
+    const int64_t row = gt / SP_TPR;
+    const int lane = (int)(gt % SP_TPR);
+    const V acc = spmv_row<V, SP_TPR, SP_U>(row < n, row, lane, rowptr, col, vals, x);
+    if (row < n && lane == 0) y[row] = scale(acc, sc);
 }
 
 template <typename V>
@@ -674,7 +689,7 @@ ndhss_status gmres_one(const FactorData& F, const int32_t* rowptr, const int32_t
     if (!hst) return set_error(NDHSS_ERR_OOM, "ndhss_gmres: pinned status words");
     hst[0] = hst[1] = GmStatus{0, 0, 0, 0};
     const int eb = std::min((n + 255) / 256, 4 * 152);
-    const unsigned sblocks = (unsigned)(((int64_t)n * 4 + 255) / 256);
+    const unsigned sblocks = (unsigned)(((int64_t)n * SP_TPR + 255) / 256);
     gm_init_kernel<V><<<1, 1, 0, st>>>(S, R, o.maxit, o.tol, o.inner, o.cycle_rtol);
     NDHSS_LAUNCH_CHECK("gm_init_kernel");
     NDHSS_CUDA_TRY(cudaMemsetAsync(x, 0, sizeof(V) * n, st));
@@ -705,7 +720,7 @@ ndhss_status gmres_one(const FactorData& F, const int32_t* rowptr, const int32_t
         cudaEvent_t e0 = nullptr, e1 = nullptr, e2 = nullptr, e3 = nullptr;
         if (o.timing) { e0 = ev(); e1 = ev(); e2 = ev(); e3 = ev(); }
         if (e0) cudaEventRecord(e0, st);
-        gm_spmv_kernel<V, 4, 4><<<sblocks, 256, 0, st>>>(n, rowptr, col, vals, S);
+        gm_spmv_kernel<V><<<sblocks, 256, 0, st>>>(n, rowptr, col, vals, S);
         note_launches(1);
         if (e1) cudaEventRecord(e1, st);
         gm_resid_kernel<V><<<RB, RT, 0, st>>>(S, b, t, r, n, dpart, blk);
