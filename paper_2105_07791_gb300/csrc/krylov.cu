@@ -210,6 +210,7 @@ struct GmStatus {
 template <typename V>
 struct alignas(16) GmDev {
     int32_t mode, bmode, j, jend, its, cycles, done, have_cycle, skip, bnorm_set, maxit, R;
+    int32_t spmv_zero, pad_[3];        // 1: this block's SpMV input is x = 0 (the first restart)
     double bnorm, zbnorm, beta, relres, last_res, prev_rel, cyc_target, rtol_eff, tol, inner;
     const V* spmv_in;
     V* spmv_out;
@@ -300,6 +301,7 @@ __global__ void gm_init_kernel(GmDev<V>* S, int R, int maxit, double tol, double
     S->mode = GM_RESTART;
     S->bmode = GM_RESTART;
     S->j = S->jend = S->its = S->cycles = S->done = S->have_cycle = S->skip = S->bnorm_set = 0;
+    S->spmv_zero = 0;
     S->maxit = maxit;
     S->R = R;
     S->bnorm = 0.0;
@@ -337,12 +339,15 @@ __global__ void __launch_bounds__(256) gm_begin_kernel(GmDev<V>* S, V* __restric
         S->bmode = mode;
         S->spmv_out = t;
         if (mode == GM_RESTART) {
+            // x = 0 before the first cycle (the solver zeroes it): A x = 0, no product
+            S->spmv_zero = (!S->have_cycle && S->its == 0) ? 1 : 0;
             S->spmv_in = x;
             S->spmv_scale = 1.0;
             S->ind.x = r;
             S->ind.y = const_cast<V*>(Vb);
-            S->ran[blk] = 1;
+            S->ran[blk] = S->spmv_zero ? 0 : 1;
         } else {
+            S->spmv_zero = 0;
             S->spmv_in = Vb + (int64_t)S->j * ldv;
             S->spmv_scale = S->scale[S->j];
             S->ind.x = t;
@@ -356,7 +361,7 @@ __global__ void __launch_bounds__(256) gm_begin_kernel(GmDev<V>* S, V* __restric
 template <typename V>
 __global__ void __launch_bounds__(256) gm_spmv_kernel(int n, const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col,
                                                       const V* __restrict__ vals, const GmDev<V>* S) {
-    if (S->done) return;
+    if (S->done || S->spmv_zero) return;
     const V* __restrict__ x = S->spmv_in;
     V* __restrict__ y = S->spmv_out;
     const double sc = S->spmv_scale;
@@ -375,9 +380,10 @@ template <typename V>
 __global__ void __launch_bounds__(RT, 4) gm_resid_kernel(GmDev<V>* S, const V* __restrict__ b, const V* __restrict__ t,
                                                          V* __restrict__ r, int n, double* __restrict__ partial, int blk) {
     if (S->done || S->bmode != GM_RESTART) return;
+    const bool tz = S->spmv_zero != 0;                 // t = A 0 was not formed
     double acc = 0.0;
     for (int64_t row = (int64_t)blockIdx.x * RT + threadIdx.x; row < n; row += (int64_t)gridDim.x * RT) {
-        const V v = b[row] - t[row];
+        const V v = tz ? b[row] : b[row] - t[row];
         r[row] = v;
         acc += norm2(v);
     }
@@ -510,69 +516,13 @@ __device__ void gm_cgs(GmDev<V>* S, V* __restrict__ Vb, int64_t ldv, int n, V* _
     }
 }
 
-// RESTART: beta = ||V_0||;  STEP: h1 = V^H w
+// STEP, last part: w -= V h2, ||w||; the last block forms the Hessenberg
+// column j, the Givens rotation and the cycle's stopping tests and writes
+// the status word.  barrier_word: the grid barrier's counter, cleared here
+// (every block has passed the barriers by then).
 template <typename V>
-__global__ void __launch_bounds__(RT, 4) gm_dot_kernel(GmDev<V>* S, V* __restrict__ Vb, int64_t ldv, int n,
-                                                    V* __restrict__ partial, double* __restrict__ dpartial) {
-    if (S->done) return;
-    if (S->bmode == GM_RESTART) {
-        double acc = 0.0;
-        for (int64_t row = (int64_t)blockIdx.x * RT + threadIdx.x; row < n; row += (int64_t)gridDim.x * RT)
-            acc += norm2(Vb[row]);
-        const double bs = block_sum(acc);
-        if (threadIdx.x == 0) dpartial[blockIdx.x] = bs;
-        if (!last_block(S->counter, gridDim.x)) return;
-        const double ss = block_sum_partials(dpartial, gridDim.x);
-        __shared__ GmDev<V> sh;
-        gm_state_load(sh, S);
-        if (threadIdx.x == 0) {
-            const double beta = sqrt(ss);
-            bool ok = true;
-            if (sh.zbnorm < 0.0) {
-                sh.zbnorm = beta;
-                if (beta == 0.0) {                   // P^{-1} b vanished
-                    sh.done = 3;
-                    sh.skip = 1;
-                    ok = false;
-                }
-            }
-            if (ok) {
-                sh.beta = beta;
-                for (int i = 0; i < KMAX; ++i) sh.g[i] = zero<V>();
-                sh.g[0] = from_real<V>(beta);
-                sh.scale[0] = beta > 0.0 ? 1.0 / beta : 0.0;
-                sh.j = 0;
-                sh.mode = GM_STEP;
-            }
-        }
-        gm_state_store(S, sh);
-        return;
-    }
-    gm_cgs<V, false>(S, Vb, ldv, n, partial);
-}
-
-// STEP: w -= V h1, h2 = V^H w
-template <typename V>
-__global__ void __launch_bounds__(RT, 4) gm_axdot_kernel(GmDev<V>* S, V* __restrict__ Vb, int64_t ldv, int n,
-                                                      V* __restrict__ partial) {
-    if (S->done || S->bmode != GM_STEP) return;
-    gm_cgs<V, true>(S, Vb, ldv, n, partial);
-}
-
-// STEP: w -= V h2, ||w||, Hessenberg column j, Givens rotation, the cycle's
-// stopping tests; every block writes the status word
-template <typename V>
-__global__ void __launch_bounds__(RT, 4) gm_axnorm_kernel(GmDev<V>* S, V* __restrict__ Vb, int64_t ldv, int n,
-                                                       double* __restrict__ dpartial, GmStatus* hstat) {
-    const bool step = !S->done && S->bmode == GM_STEP;
-    if (!step) {
-        if (blockIdx.x == 0 && threadIdx.x == 0) {
-            hstat->done = S->done;
-            hstat->its = S->its;
-            __threadfence_system();
-        }
-        return;
-    }
+__device__ void gm_axnorm_step(GmDev<V>* S, V* __restrict__ Vb, int64_t ldv, int n, double* __restrict__ dpartial,
+                               GmStatus* hstat, GmDev<V>& sh, int barrier_word) {
     const int j = S->j;
     __shared__ V ch[KMAX];
     if (threadIdx.x <= j) ch[threadIdx.x] = -scale(S->h2[threadIdx.x], S->scale[threadIdx.x]);
@@ -589,10 +539,10 @@ __global__ void __launch_bounds__(RT, 4) gm_axnorm_kernel(GmDev<V>* S, V* __rest
     if (threadIdx.x == 0) dpartial[blockIdx.x] = bs;
     if (!last_block(S->counter, gridDim.x)) return;
     const double ss = block_sum_partials(dpartial, gridDim.x);
-    __shared__ GmDev<V> sh;
     gm_state_load(sh, S);
     if (threadIdx.x == 0) {
     GmDev<V>* S = &sh;                          // thread 0 works on the shared copy
+    if (barrier_word >= 0) S->counter[barrier_word] = 0;
     const double hn = sqrt(ss);
     V* Hj = S->H + (int64_t)j * KMAX;
     for (int i = 0; i <= j; ++i) Hj[i] = S->h1[i] + S->h2[i];
@@ -651,6 +601,111 @@ __global__ void __launch_bounds__(RT, 4) gm_axnorm_kernel(GmDev<V>* S, V* __rest
     gm_state_store(S, sh);
 }
 
+// Grid barrier of a cooperative launch (every block resident): thread 0
+// publishes the block's writes and counts in, then waits, bounded, until
+// `target` blocks have; false if the wait gave up.
+__device__ bool gm_grid_sync(unsigned* ctr, unsigned target) {
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        atomicAdd(ctr, 1u);
+        int ok = 1;
+        uint64_t t0;
+        asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
+        for (;;) {
+            unsigned v;
+            asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(ctr) : "memory");
+            if (v >= target) break;
+            __nanosleep(64);
+            uint64_t t1;
+            asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t1));
+            if (t1 - t0 > 2000000000ull) {
+                ok = 0;
+                break;
+            }
+        }
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+constexpr int GM_BARRIER = KMAX / 4 + 1;    // counter word of the Arnoldi kernel's grid barrier
+
+// One cooperative launch per GMRES block for what follows the apply.
+// RESTART: beta = ||V_0||, g = beta e_1.  STEP: h1 = V^H w (grid barrier),
+// w -= V h1 and h2 = V^H w (grid barrier), w -= V h2, ||w||, the Hessenberg
+// column and the cycle's tests.  Every path leaves the status word for the
+// host.  All blocks read the solver state's mode words before any block can
+// change them (the last block of each reduction is the only writer).
+template <typename V>
+__global__ void __launch_bounds__(RT, 4) gm_arnoldi_kernel(GmDev<V>* S, V* __restrict__ Vb, int64_t ldv, int n,
+                                                        V* __restrict__ partial, double* __restrict__ dpartial,
+                                                        GmStatus* hstat) {
+    __shared__ GmDev<V> sh;
+    const int done = S->done, bmode = S->bmode;
+    if (done) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            hstat->done = done;
+            hstat->its = S->its;
+            __threadfence_system();
+        }
+        return;
+    }
+    if (bmode == GM_RESTART) {
+        double acc = 0.0;
+        for (int64_t row = (int64_t)blockIdx.x * RT + threadIdx.x; row < n; row += (int64_t)gridDim.x * RT)
+            acc += norm2(Vb[row]);
+        const double bs = block_sum(acc);
+        if (threadIdx.x == 0) dpartial[blockIdx.x] = bs;
+        if (!last_block(S->counter, gridDim.x)) return;
+        const double ss = block_sum_partials(dpartial, gridDim.x);
+        gm_state_load(sh, S);
+        if (threadIdx.x == 0) {
+            const double beta = sqrt(ss);
+            bool ok = true;
+            if (sh.zbnorm < 0.0) {
+                sh.zbnorm = beta;
+                if (beta == 0.0) {                   // P^{-1} b vanished
+                    sh.done = 3;
+                    sh.skip = 1;
+                    ok = false;
+                }
+            }
+            if (ok) {
+                sh.beta = beta;
+                for (int i = 0; i < KMAX; ++i) sh.g[i] = zero<V>();
+                sh.g[0] = from_real<V>(beta);
+                sh.scale[0] = beta > 0.0 ? 1.0 / beta : 0.0;
+                sh.j = 0;
+                sh.mode = GM_STEP;
+            }
+            hstat->done = sh.done;
+            hstat->its = sh.its;
+            __threadfence_system();
+        }
+        gm_state_store(S, sh);
+        return;
+    }
+    unsigned* bar = S->counter + GM_BARRIER;
+    gm_cgs<V, false>(S, Vb, ldv, n, partial);
+    bool ok = gm_grid_sync(bar, gridDim.x);
+    if (ok) {
+        gm_cgs<V, true>(S, Vb, ldv, n, partial);
+        ok = gm_grid_sync(bar, 2 * gridDim.x);
+    }
+    if (!ok) {
+        if (threadIdx.x == 0) {
+            S->done = 4;
+            hstat->done = 4;
+            __threadfence_system();
+        }
+        return;
+    }
+    gm_axnorm_step<V>(S, Vb, ldv, n, dpartial, hstat, sh, GM_BARRIER);
+}
+
 // Pinned status words of this thread's solves (two blocks in flight), mapped
 // into the device address space; kept for the thread's lifetime.
 GmStatus* pinned_status() {
@@ -690,6 +745,16 @@ ndhss_status gmres_one(const FactorData& F, const int32_t* rowptr, const int32_t
     hst[0] = hst[1] = GmStatus{0, 0, 0, 0};
     const int eb = std::min((n + 255) / 256, 4 * 152);
     const unsigned sblocks = (unsigned)(((int64_t)n * SP_TPR + 255) / 256);
+    // the Arnoldi kernel's grid: every block resident at once (its grid barriers)
+    int agrid = 0;
+    {
+        int dev = 0, sms = 0, per_sm = 0;
+        NDHSS_CUDA_TRY(cudaGetDevice(&dev));
+        NDHSS_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        NDHSS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gm_arnoldi_kernel<V>, RT, 0));
+        agrid = std::min(RB, per_sm * sms);
+        if (agrid < 1) return set_error(NDHSS_ERR_CUDA, "ndhss_gmres: the Arnoldi kernel cannot be resident");
+    }
     gm_init_kernel<V><<<1, 1, 0, st>>>(S, R, o.maxit, o.tol, o.inner, o.cycle_rtol);
     NDHSS_LAUNCH_CHECK("gm_init_kernel");
     NDHSS_CUDA_TRY(cudaMemsetAsync(x, 0, sizeof(V) * n, st));
@@ -729,10 +794,17 @@ ndhss_status gmres_one(const FactorData& F, const int32_t* rowptr, const int32_t
         rc = apply_device(F, 1, nullptr, n, nullptr, n, awork, st, &S->ind);
         if (rc != NDHSS_OK) break;
         if (e3) cudaEventRecord(e3, st);
-        gm_dot_kernel<V><<<RB, RT, 0, st>>>(S, Vb, ldv, n, part, dpart);
-        gm_axdot_kernel<V><<<RB, RT, 0, st>>>(S, Vb, ldv, n, part);
-        gm_axnorm_kernel<V><<<RB, RT, 0, st>>>(S, Vb, ldv, n, dpart, hst + (blk & 1));
-        note_launches(3);
+        {
+            GmStatus* hs_blk = hst + (blk & 1);
+            void* args[] = {(void*)&S, (void*)&Vb, (void*)&ldv, (void*)&n, (void*)&part, (void*)&dpart, (void*)&hs_blk};
+            cudaError_t ce = cudaLaunchCooperativeKernel((const void*)gm_arnoldi_kernel<V>, dim3(agrid), dim3(RT), args, 0, st);
+            if (ce != cudaSuccess) {
+                cudaGetLastError();
+                rc = set_error(NDHSS_ERR_CUDA, "ndhss_gmres: cooperative launch failed: %s", cudaGetErrorString(ce));
+                break;
+            }
+        }
+        note_launches(1);
         cudaError_t le = cudaGetLastError();
         if (le != cudaSuccess) {
             rc = set_error(NDHSS_ERR_CUDA, "ndhss_gmres: launch failed: %s", cudaGetErrorString(le));
@@ -760,6 +832,7 @@ ndhss_status gmres_one(const FactorData& F, const int32_t* rowptr, const int32_t
     cudaEventDestroy(blk_done[1]);
     if (rc != NDHSS_OK) return rc;
     if (hs.done == 3) return set_error(NDHSS_ERR_INTERNAL, "ndhss_gmres: P^{-1} b vanished");
+    if (hs.done == 4) return set_error(NDHSS_ERR_TIMEOUT, "ndhss_gmres: a grid barrier of the Arnoldi step gave up");
     ndhss_gmres_stats Sx{};
     Sx.converged = hs.done == 1;
     Sx.iters = hs.its;
