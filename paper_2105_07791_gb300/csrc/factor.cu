@@ -1056,7 +1056,7 @@ void ndhss_factor_destroy(ndhss_factorization* fh) {
     cudaDeviceSynchronize();
     for (void* p : {(void*)F.d_node, (void*)F.d_foff, (void*)F.d_blist, (void*)F.d_perm, (void*)F.d_sigma,
                     (void*)F.d_ipiv, F.d_front, (void*)F.d_lr_ptr, (void*)F.d_lr_k, (void*)F.d_lr_list, (void*)F.d_sched,
-                    (void*)F.d_need, (void*)F.d_wdesc, (void*)F.d_apply_err, (void*)F.d_mjobs, (void*)F.d_sublist,
+                    (void*)F.d_need, (void*)F.d_wdesc, (void*)F.d_apply_err, (void*)F.d_mjobs, (void*)F.d_mlr, (void*)F.d_sublist,
                     (void*)F.d_sched_dep})
         if (p) cudaFreeAsync(p, 0);
     for (void* b : F.lr_bufs)

@@ -70,6 +70,12 @@ struct FactorData {
     // each level's range in both
     int2* d_mjobs = nullptr;
     std::vector<int64_t> mj_up_off, mj_dn_off;
+    // low-rank nodes of the multi apply: (node, first row, T offset) tiles
+    // per level of the four products t = X^T u(I), u(B) += RJt t,
+    // t = RJt^T z(B), z(I) += X t; T scratch elements (k x 32 per node)
+    int4* d_mlr = nullptr;
+    std::vector<int64_t> ml_off[4];
+    int64_t ml_t_total = 0;
     std::vector<uint64_t> lr_ptr;             // per node, 0 = dense R
     std::vector<int32_t> lr_k;
     uint64_t* d_lr_ptr = nullptr;

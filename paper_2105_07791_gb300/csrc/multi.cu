@@ -90,7 +90,8 @@ template <typename T, bool UP>
 __global__ void __launch_bounds__(256)
 mapply_kernel(const int2* __restrict__ jobs, const int32_t* __restrict__ node, const int64_t* __restrict__ foff,
               const T* __restrict__ front, const int32_t* __restrict__ sigma, const int32_t* __restrict__ blist,
-              T* __restrict__ U, T* __restrict__ Z, const int* __restrict__ pact, const int32_t* __restrict__ nprob) {
+              T* __restrict__ U, T* __restrict__ Z, const int* __restrict__ pact, const int32_t* __restrict__ nprob,
+              const uint64_t* __restrict__ lr_ptr) {
     __shared__ __align__(16) T As[MT_K][MT_ROWS];
     __shared__ __align__(16) T Bs[MT_K][MR];
     __shared__ int s_row[MT_K];
@@ -101,7 +102,9 @@ mapply_kernel(const int2* __restrict__ jobs, const int32_t* __restrict__ node, c
     const int i_off = nd[4], m_i = nd[5], b_off = nd[6], m_b = nd[7];
     const int64_t m = (int64_t)m_i + m_b;
     const T* F = front + foff[s];
-    const int rows = UP ? (int)m : m_i;
+    // a low-rank node's B rows go through mlr_kernel (its up tiles cover I only)
+    const bool lowrank = lr_ptr && lr_ptr[s];
+    const int rows = (UP && !lowrank) ? (int)m : m_i;
     const int K = UP ? m_i : m_b;
     const T* A = UP ? F : F + (int64_t)m_i * m;
     const T* src = UP ? U : Z;
@@ -162,6 +165,105 @@ mapply_kernel(const int2* __restrict__ jobs, const int32_t* __restrict__ node, c
     }
 }
 
+// Low-rank nodes (R ~ X R(J, :), stored as X (m_i x k) then RJt = R(J, :)^T
+// (m_b x k), column-major; L = R^T): one 64-row x 32-column tile of
+//   MODE 0: T = X^T u(I)          (rows: k, K: m_i)
+//   MODE 1: u(B) += RJt T         (rows: m_b, K: k)
+//   MODE 2: T = RJt^T z(B)        (rows: k, K: m_b)
+//   MODE 3: z(I) += X T           (rows: m_i, K: k)
+// the same products as the one-vector apply's low-rank dot and axpy tasks;
+// T: k x 32 per node (row a at a * 32) in the job's slot.  Job: node, first
+// row, T offset (lo, hi).
+template <typename T, int MODE>
+__global__ void __launch_bounds__(256)
+mlr_kernel(const int4* __restrict__ jobs, const int32_t* __restrict__ node, const uint64_t* __restrict__ lr_ptr,
+           const int32_t* __restrict__ lr_k, const int32_t* __restrict__ blist, T* __restrict__ U, T* __restrict__ Z,
+           T* __restrict__ Tb, const int* __restrict__ pact, const int32_t* __restrict__ nprob) {
+    __shared__ __align__(16) T As[MT_K][MT_ROWS];
+    __shared__ __align__(16) T Bs[MT_K][MR];
+    __shared__ int s_row[MT_K];
+    const int4 J = jobs[blockIdx.x];
+    const int s = J.x, r0 = J.y;
+    const int64_t toff = (int64_t)(((uint64_t)(uint32_t)J.w << 32) | (uint32_t)J.z);
+    if (pact && !pact[nprob[s]]) return;
+    const int32_t* nd = node + (size_t)s * 14;
+    const int i_off = nd[4], m_i = nd[5], b_off = nd[6], m_b = nd[7];
+    const int k = lr_k[s];
+    const T* X = reinterpret_cast<const T*>(lr_ptr[s]);
+    const T* RJt = X + (int64_t)m_i * k;
+    T* Ts = Tb + toff;
+    const int rows = (MODE == 0 || MODE == 2) ? k : (MODE == 1 ? m_b : m_i);
+    const int K = MODE == 0 ? m_i : (MODE == 2 ? m_b : k);
+    const int tid = threadIdx.x, tx = tid & 7, ty = tid >> 3;
+    T acc[2][4];
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = zero<T>();
+    for (int k0 = 0; k0 < K; k0 += MT_K) {
+        const int kc = min(MT_K, K - k0);
+        if (tid < MT_K) {
+            int sr = -1;
+            if (tid < kc) {
+                const int q = k0 + tid;
+                sr = MODE == 0 ? i_off + q : (MODE == 2 ? blist[b_off + q] : q);
+            }
+            s_row[tid] = sr;
+        }
+        for (int q = tid; q < MT_ROWS * MT_K; q += 256) {
+            // transposed operands (MODE 0, 2) load along K, the others along rows
+            const bool kfast = MODE == 0 || MODE == 2;
+            const int r = kfast ? q / MT_K : q % MT_ROWS, kk = kfast ? q % MT_K : q / MT_ROWS;
+            T a = zero<T>();
+            if (r0 + r < rows && kk < kc) {
+                const int rr = r0 + r, ki = k0 + kk;
+                a = MODE == 0 ? X[(int64_t)rr * m_i + ki]
+                  : MODE == 1 ? RJt[(int64_t)ki * m_b + rr]
+                  : MODE == 2 ? RJt[(int64_t)rr * m_b + ki]
+                              : X[(int64_t)ki * m_i + rr];
+            }
+            As[kk][r] = a;
+        }
+        __syncthreads();
+        for (int q = tid; q < MT_K * MR; q += 256) {
+            const int kk = q / MR, c = q % MR;
+            const T* src = (MODE == 0) ? U : (MODE == 2 ? Z : Ts);
+            Bs[kk][c] = s_row[kk] >= 0 ? src[(int64_t)s_row[kk] * MR + c] : zero<T>();
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < MT_K; ++kk) {
+            T a[2], bv[4];
+            lds_vec<2>(&As[kk][2 * ty], a);
+            lds_vec<4>(&Bs[kk][4 * tx], bv);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                acc[0][j] = fmac(a[0], bv[j], acc[0][j]);
+                acc[1][j] = fmac(a[1], bv[j], acc[1][j]);
+            }
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        const int r = r0 + 2 * ty + i;
+        if (r >= rows) continue;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int c = 4 * tx + j;
+            if (MODE == 0 || MODE == 2) {
+                Ts[(int64_t)r * MR + c] = acc[i][j];
+            } else if (MODE == 1) {
+                T* p = U + (int64_t)blist[b_off + r] * MR + c;
+                *p = *p + acc[i][j];
+            } else {
+                T* p = Z + (int64_t)(i_off + r) * MR + c;
+                *p = *p + acc[i][j];
+            }
+        }
+    }
+}
+
 template <typename T, typename V>
 ndhss_status multi_apply_run(const FactorData& F, int nrhs, const V* X, int64_t ldx, V* Y, int64_t ldy, T* U, T* Z,
                              const int* pact, const int32_t* nprob, cudaStream_t st) {
@@ -170,19 +272,43 @@ ndhss_status multi_apply_run(const FactorData& F, int nrhs, const V* X, int64_t 
     mgather_kernel<T, V><<<eb, 256, 0, st>>>(n, nrhs, F.d_perm, X, ldx, U);
     NDHSS_LAUNCH_CHECK("mgather_kernel");
     const T* front = static_cast<const T*>(F.d_front);
+    T* Tb = Z + (int64_t)F.n * MR;                  // the low-rank nodes' k x 32 blocks
+    const uint64_t* lrp = F.d_mlr ? F.d_lr_ptr : nullptr;
+    auto lr_launch = [&](int mode, int l) -> ndhss_status {
+        if (!F.d_mlr) return NDHSS_OK;
+        const int64_t a = F.ml_off[mode][l], b = F.ml_off[mode][l + 1];
+        if (b == a) return NDHSS_OK;
+        const int4* jb = F.d_mlr + a;
+        switch (mode) {
+            case 0: mlr_kernel<T, 0><<<(unsigned)(b - a), 256, 0, st>>>(jb, F.d_node, F.d_lr_ptr, F.d_lr_k, F.d_blist, U, Z, Tb, pact, nprob); break;
+            case 1: mlr_kernel<T, 1><<<(unsigned)(b - a), 256, 0, st>>>(jb, F.d_node, F.d_lr_ptr, F.d_lr_k, F.d_blist, U, Z, Tb, pact, nprob); break;
+            case 2: mlr_kernel<T, 2><<<(unsigned)(b - a), 256, 0, st>>>(jb, F.d_node, F.d_lr_ptr, F.d_lr_k, F.d_blist, U, Z, Tb, pact, nprob); break;
+            default: mlr_kernel<T, 3><<<(unsigned)(b - a), 256, 0, st>>>(jb, F.d_node, F.d_lr_ptr, F.d_lr_k, F.d_blist, U, Z, Tb, pact, nprob); break;
+        }
+        NDHSS_LAUNCH_CHECK("mlr_kernel");
+        return NDHSS_OK;
+    };
     for (int l = F.depth; l >= 0; --l) {
         const int64_t a = F.mj_up_off[l], b = F.mj_up_off[l + 1];
-        if (b == a) continue;
-        mapply_kernel<T, true><<<(unsigned)(b - a), 256, 0, st>>>(F.d_mjobs + a, F.d_node, F.d_foff, front, F.d_sigma,
-                                                                 F.d_blist, U, Z, pact, nprob);
-        NDHSS_LAUNCH_CHECK("mapply_kernel");
+        if (b > a) {
+            mapply_kernel<T, true><<<(unsigned)(b - a), 256, 0, st>>>(F.d_mjobs + a, F.d_node, F.d_foff, front, F.d_sigma,
+                                                                     F.d_blist, U, Z, pact, nprob, lrp);
+            NDHSS_LAUNCH_CHECK("mapply_kernel");
+        }
+        ndhss_status rc = lr_launch(0, l);
+        if (rc == NDHSS_OK) rc = lr_launch(1, l);
+        if (rc != NDHSS_OK) return rc;
     }
     for (int l = 0; l <= F.depth; ++l) {
         const int64_t a = F.mj_dn_off[l], b = F.mj_dn_off[l + 1];
-        if (b == a) continue;
-        mapply_kernel<T, false><<<(unsigned)(b - a), 256, 0, st>>>(F.d_mjobs + a, F.d_node, F.d_foff, front,
-                                                                  F.d_sigma, F.d_blist, U, Z, pact, nprob);
-        NDHSS_LAUNCH_CHECK("mapply_kernel");
+        if (b > a) {
+            mapply_kernel<T, false><<<(unsigned)(b - a), 256, 0, st>>>(F.d_mjobs + a, F.d_node, F.d_foff, front,
+                                                                      F.d_sigma, F.d_blist, U, Z, pact, nprob, lrp);
+            NDHSS_LAUNCH_CHECK("mapply_kernel");
+        }
+        ndhss_status rc = lr_launch(2, l);
+        if (rc == NDHSS_OK) rc = lr_launch(3, l);
+        if (rc != NDHSS_OK) return rc;
     }
     mscatter_kernel<T, V><<<eb, 256, 0, st>>>(n, nrhs, F.d_perm, Z, Y, ldy);
     NDHSS_LAUNCH_CHECK("mscatter_kernel");
@@ -211,12 +337,10 @@ ndhss_status multi_apply_device(const FactorData& F, int nrhs, const void* X, in
                                       nprob, st);
 }
 
-size_t multi_work_bytes(const FactorData& F) { return (size_t)2 * F.n * MR * F.esize + 256; }
+size_t multi_work_bytes(const FactorData& F) { return ((size_t)2 * F.n * MR + (size_t)F.ml_t_total) * F.esize + 256; }
 
 ndhss_status multi_supported(const FactorData& F, const char* who) {
     if (!F.d_mjobs) return set_error(NDHSS_ERR_INVALID_ARG, "%s: the factorization has no multi-apply plan", who);
-    for (uint64_t p : F.lr_ptr)
-        if (p) return set_error(NDHSS_ERR_INVALID_ARG, "%s: compressed Gauss transforms are applied one column at a time (ndhss_apply)", who);
     if (F.ulv) return set_error(NDHSS_ERR_INVALID_ARG, "%s: ULV factorizations are applied one column at a time (ndhss_apply)", who);
     return NDHSS_OK;
 }
@@ -706,10 +830,11 @@ ndhss_status build_multi_plan(FactorData& F, cudaStream_t st) {
     std::vector<int32_t> jobs;
     F.mj_up_off.assign(F.depth + 2, 0);
     F.mj_dn_off.assign(F.depth + 2, 0);
+    auto lowrank = [&](int s) { return !F.lr_ptr.empty() && F.lr_ptr[s] != 0; };
     for (int l = 0; l <= F.depth; ++l) {
         F.mj_up_off[l] = (int64_t)jobs.size() / 2;
         for (int s : F.levels[l]) {
-            const int mi = F.m_i(s), m = mi + F.m_b(s);
+            const int mi = F.m_i(s), m = lowrank(s) ? mi : mi + F.m_b(s);
             if (mi == 0) continue;
             for (int r0 = 0; r0 < m; r0 += MT_ROWS) { jobs.push_back(s); jobs.push_back(r0); }
         }
@@ -719,11 +844,44 @@ ndhss_status build_multi_plan(FactorData& F, cudaStream_t st) {
         F.mj_dn_off[l] = (int64_t)jobs.size() / 2;
         for (int s : F.levels[l]) {
             const int mi = F.m_i(s);
-            if (mi == 0 || F.m_b(s) == 0) continue;
+            if (mi == 0 || F.m_b(s) == 0 || lowrank(s)) continue;
             for (int r0 = 0; r0 < mi; r0 += MT_ROWS) { jobs.push_back(s); jobs.push_back(r0); }
         }
     }
     F.mj_dn_off[F.depth + 1] = (int64_t)jobs.size() / 2;
+    // low-rank tiles: T = X^T u(I), u(B) += RJt T, T = RJt^T z(B), z(I) += X T
+    std::vector<int32_t> lj;
+    std::vector<int64_t> toff(std::max(F.nnodes, 1), 0);
+    F.ml_t_total = 0;
+    for (int s = 0; s < F.nnodes; ++s)
+        if (lowrank(s) && F.lr_k[s] > 0) {
+            toff[s] = F.ml_t_total;
+            F.ml_t_total += (int64_t)F.lr_k[s] * MR;
+        }
+    for (int mode = 0; mode < 4; ++mode) {
+        F.ml_off[mode].assign(F.depth + 2, 0);
+        for (int l = 0; l <= F.depth; ++l) {
+            F.ml_off[mode][l] = (int64_t)lj.size() / 4;
+            for (int s : F.levels[l]) {
+                if (!lowrank(s) || F.lr_k[s] == 0 || F.m_i(s) == 0 || F.m_b(s) == 0) continue;
+                const int rows = (mode == 0 || mode == 2) ? F.lr_k[s] : (mode == 1 ? F.m_b(s) : F.m_i(s));
+                for (int r0 = 0; r0 < rows; r0 += MT_ROWS) {
+                    lj.push_back(s);
+                    lj.push_back(r0);
+                    lj.push_back((int32_t)(uint32_t)(uint64_t)toff[s]);
+                    lj.push_back((int32_t)(uint32_t)((uint64_t)toff[s] >> 32));
+                }
+            }
+        }
+        F.ml_off[mode][F.depth + 1] = (int64_t)lj.size() / 4;
+    }
+    if (!lj.empty()) {
+        void* q = nullptr;
+        NDHSS_CUDA_TRY(pool_malloc_async(&q, lj.size() * sizeof(int32_t), st));
+        NDHSS_CUDA_TRY(cudaMemcpyAsync(q, lj.data(), lj.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+        F.d_mlr = static_cast<int4*>(q);
+        F.dev_bytes += (int64_t)(lj.size() * sizeof(int32_t));
+    }
     if (jobs.empty()) jobs.assign(2, 0);
     void* p = nullptr;
     NDHSS_CUDA_TRY(pool_malloc_async(&p, jobs.size() * sizeof(int32_t), st));

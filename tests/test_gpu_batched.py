@@ -112,14 +112,44 @@ def test_multi_apply_argument_checks(nd, batch):
     X = torch.zeros((n, 33), dtype=torch.complex128, device="cuda")
     with pytest.raises(nd.NdhssError, match="INVALID_ARG"):
         nd.ndhss_apply_multi(f, X, torch.empty_like(X))
-    # compressed Gauss transforms are applied column by column only
+    # ULV factorizations are applied column by column only
     P = helmholtz_batch(1, seed=9, nmin=64, nmax=64, nsrc=1)[0]
     tree = nd.ndhss_build_tree(P.coords, P.A.indptr, P.A.indices, 32)
     M = nd.DeviceCSR(P.A)
-    fc = _factor(nd, tree, M, 1, hss_levels=2)
+    fu = nd.ndhss_factor(tree, M.vtype, M.rowptr, M.col, M.vals,
+                         nd.make_factor_opts(prec=1, hss_levels=2, ulv=True))
     X = torch.zeros((P.n, 4), dtype=torch.complex128, device="cuda")
     with pytest.raises(nd.NdhssError, match="column"):
-        nd.ndhss_apply_multi(fc, X, torch.empty_like(X))
+        nd.ndhss_apply_multi(fu, X, torch.empty_like(X))
+
+
+@pytest.mark.parametrize("prec,tol_o,tol_1", [(0, 1e-4, 1e-12), (1, 1e-3, 1e-4)])
+def test_multi_apply_compressed_factor(nd, prec, tol_o, tol_1):
+    """Compressed fronts (low-rank R and L above the switching level): the
+    32-column apply against the oracle's compressed preconditioner
+    (apply_compressed, same Philox streams; the tolerance of the one-vector
+    compressed apply) and column by column against ndhss_apply."""
+    from oracle.hss import apply_compressed, factor_compressed
+    P = helmholtz_batch(1, seed=9, nmin=96, nmax=96, nsrc=1)[0]
+    T = build_tree(P.coords, P.A.indptr, P.A.indices, 32)
+    fac = factor_compressed(T, P.A, hss_levels=3, eps=1e-6, beta=64, k0=32, r=16, seed=11)
+    tree = nd.ndhss_build_tree(P.coords, P.A.indptr, P.A.indices, 32)
+    M = nd.DeviceCSR(P.A)
+    f = nd.ndhss_factor(tree, M.vtype, M.rowptr, M.col, M.vals,
+                        nd.make_factor_opts(prec=prec, hss_levels=3, eps_hss=1e-6, beta=64, k0=32, r=16, seed=11))
+    assert nd.ndhss_factor_stats_get(f)["kmax"] > 0
+    for k in (32, 5):
+        X = _rand(P.n, k, 20 + k)
+        Xd = torch.from_numpy(X).cuda().contiguous()
+        Yd = torch.empty_like(Xd)
+        nd.ndhss_apply_multi(f, Xd, Yd)
+        Y = Yd.cpu().numpy()
+        assert _rel(Y, apply_compressed(fac, X)) <= tol_o, _rel(Y, apply_compressed(fac, X))
+        for c in range(min(k, 3)):
+            x1 = torch.from_numpy(np.ascontiguousarray(X[:, c])).cuda()
+            y1 = torch.empty_like(x1)
+            nd.ndhss_apply(f, x1, y1)
+            assert _rel(Y[:, c], y1.cpu().numpy()) <= tol_1, (c, _rel(Y[:, c], y1.cpu().numpy()))
 
 
 @pytest.mark.parametrize("prec", [0, 1])
@@ -234,3 +264,29 @@ def test_gmres_batched_real_problems(nd, prec):
             assert st[s][c]["converged"] and st[s][c]["true_relres"] <= 1e-10
             a, b = off[s], off[s + 1]
             assert _rel(Xh[c, a:b], lu.solve(Bh[c, a:b])) <= 1e-8
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_gmres_batched_compressed_forest(nd, batch, prec):
+    """The lockstep GMRES on a compressed forest factor (the 32-column apply
+    with low-rank tiles): every system to a float64 true residual of 1e-8,
+    solutions within 1e-5 of a direct solve."""
+    tree, M, probs, off = batch["tree"], batch["M"], batch["probs"], batch["off"]
+    f = _factor(nd, tree, M, prec, hss_levels=2)
+    assert nd.ndhss_factor_stats_get(f)["kmax"] > 0          # low-rank tiles are exercised
+    n = batch["A"].shape[0]
+    nrhs = 4
+    Bh = np.zeros((nrhs, n), dtype=np.complex128)
+    for s, P in enumerate(probs):
+        Bh[:, off[s]:off[s + 1]] = P.b[:, :nrhs].T
+    B = torch.from_numpy(Bh).cuda()
+    X = torch.zeros_like(B)
+    st = nd.ndhss_gmres_batched(f, M.rowptr, M.col, M.vals, off, B, X, tol=1e-8)
+    Xh = X.cpu().numpy()
+    for s, P in enumerate(probs):
+        lu = spla.splu(P.A.tocsc())
+        for c in range(nrhs):
+            S = st[s][c]
+            assert S["converged"] and S["true_relres"] <= 1e-8, (s, c, S)
+            xs, bs = Xh[c, off[s]:off[s + 1]], Bh[c, off[s]:off[s + 1]]
+            assert _rel(xs, lu.solve(bs)) <= 1e-5, (s, c)
