@@ -403,15 +403,18 @@ ndhss_status ndhss_gmres(const ndhss_factorization* f, const int32_t* d_rowptr, 
  * (Alg. 3.1 with one pass over the factor for all of them): per level,
  * deepest first, z(I^s) = A_ii^{-1} P^T y(I^s) and y(B^s) -= L P^T y(I^s) for
  * every node of the level as 64-row x 32-column tiles; then per level from
- * the roots, z(I^s) += R z(B^s).  Dense fronts only: a factorization with
- * compressed Gauss transforms (hss_levels >= 0 above the switching level) or
- * a ULV diagonal gives INVALID_ARG (ndhss_apply handles those).
+ * the roots, z(I^s) += R z(B^s).  Nodes with compressed Gauss transforms
+ * (R ~ X R(J,:), L = R^T above the switching level) take the low-rank
+ * products t = X^T y(I^s), y(B^s) += R(J,:)^T t on the way up and
+ * t = R(J,:) z(B^s), z(I^s) += X t on the way down, 32 columns at a time.  A
+ * factorization with a ULV diagonal gives INVALID_ARG (ndhss_apply handles it).
  *   nrhs       0..32 right-hand sides
  *   d_x, d_y   device float64 / complex128 (per the factor's vtype) arrays of
  *              n rows, interleaved: element (row, c) at row * ld + c,
  *              ldx, ldy >= nrhs; original numbering
  * Works in the factor's precision (one conversion at entry and exit); uses
- * 2 n x 32 front-type elements of pooled scratch; synchronises the stream.
+ * 2 n x 32 front-type elements of pooled scratch plus k x 32 per low-rank
+ * node; synchronises the stream.
  */
 ndhss_status ndhss_apply_multi(const ndhss_factorization* f, int32_t nrhs, const void* d_x, int64_t ldx,
                                void* d_y, int64_t ldy, void* stream);
