@@ -428,7 +428,7 @@ ndhss_status ndhss_apply_multi(const ndhss_factorization* f, int32_t nrhs, const
  * reductions per problem, so a pass over A and over the factor serves all
  * nsys * nrhs systems.  A system that meets its tolerance stops changing
  * while the others go on.  f is the factorization of the batch's forest
- * (ndhss_build_tree_batched), dense fronts only.
+ * (ndhss_build_tree_batched), dense or compressed fronts (no ULV diagonal).
  *   d_rowptr, d_col, d_vals  device CSR of the block-diagonal batch matrix
  *   nsys       problems; sys_off host int64 [nsys + 1], problem s owns rows
  *              [sys_off[s], sys_off[s+1]), sys_off[0] = 0, sys_off[nsys] = n
