@@ -36,6 +36,7 @@ namespace {
 constexpr int MR = 32;            // interleaved right-hand sides
 constexpr int MT_ROWS = 64;       // rows per apply tile
 constexpr int MT_K = 16;          // K chunk of an apply tile
+constexpr int MT_THREADS = 128;   // threads of a dense apply tile (4 x 4 products each)
 constexpr int SEG_ROWS = 1024;    // rows per reduction block
 constexpr int BK = 32;            // restart + 1 <= BK
 
@@ -87,14 +88,13 @@ __global__ void mscatter_kernel(int64_t n, int nrhs, const int32_t* __restrict__
 // front against u(I^s o sigma) (rows < m_i to z, rows >= m_i subtracted from
 // u(B^s)); !UP = the R block against z(B^s), added to z(I^s).
 template <typename T, bool UP>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(MT_THREADS)
 mapply_kernel(const int2* __restrict__ jobs, const int32_t* __restrict__ node, const int64_t* __restrict__ foff,
               const T* __restrict__ front, const int32_t* __restrict__ sigma, const int32_t* __restrict__ blist,
               T* __restrict__ U, T* __restrict__ Z, const int* __restrict__ pact, const int32_t* __restrict__ nprob,
               const uint64_t* __restrict__ lr_ptr) {
     __shared__ __align__(16) T As[MT_K][MT_ROWS];
     __shared__ __align__(16) T Bs[MT_K][MR];
-    __shared__ int s_row[MT_K];
     const int2 J = jobs[blockIdx.x];
     const int s = J.x, r0 = J.y;
     if (pact && !pact[nprob[s]]) return;          // a problem whose systems all stopped
@@ -108,44 +108,74 @@ mapply_kernel(const int2* __restrict__ jobs, const int32_t* __restrict__ node, c
     const int K = UP ? m_i : m_b;
     const T* A = UP ? F : F + (int64_t)m_i * m;
     const T* src = UP ? U : Z;
+    // 128 threads: thread (ty, tx) owns rows 4 ty .. 4 ty + 3 and columns
+    // 4 tx .. 4 tx + 3 of the 64 x 32 tile (16 products per 64 bytes read
+    // from shared memory)
     const int tid = threadIdx.x, tx = tid & 7, ty = tid >> 3;
-    T acc[2][4];
+    T acc[4][4];
 #pragma unroll
-    for (int i = 0; i < 2; ++i)
+    for (int i = 0; i < 4; ++i)
 #pragma unroll
         for (int j = 0; j < 4; ++j) acc[i][j] = zero<T>();
-    for (int k0 = 0; k0 < K; k0 += MT_K) {
+    // the next K chunk's A entries, its row indices and then its B rows are
+    // loaded into registers while the current chunk is multiplied
+    T ra[MT_ROWS * MT_K / MT_THREADS], rb[MT_K * MR / MT_THREADS];
+    auto load_a = [&](int k0) {
         const int kc = min(MT_K, K - k0);
-        if (tid < MT_K)
-            s_row[tid] = tid < kc ? (UP ? i_off + sigma[i_off + k0 + tid] : blist[b_off + k0 + tid]) : -1;
-        for (int q = tid; q < MT_ROWS * MT_K; q += 256) {
-            const int r = q % MT_ROWS, kk = q / MT_ROWS;
-            As[kk][r] = (r0 + r < rows && kk < kc) ? A[(int64_t)(k0 + kk) * m + r0 + r] : zero<T>();
+#pragma unroll
+        for (int u = 0; u < MT_ROWS * MT_K / MT_THREADS; ++u) {
+            const int q = tid + MT_THREADS * u, r = q % MT_ROWS, kk = q / MT_ROWS;
+            ra[u] = (r0 + r < rows && kk < kc) ? A[(int64_t)(k0 + kk) * m + r0 + r] : zero<T>();
+        }
+    };
+    auto src_row = [&](int k0, int kk) {
+        return k0 + kk < K ? (UP ? i_off + sigma[i_off + k0 + kk] : blist[b_off + k0 + kk]) : -1;
+    };
+    auto load_b = [&](int k0) {
+#pragma unroll
+        for (int u = 0; u < MT_K * MR / MT_THREADS; ++u) {
+            const int q = tid + MT_THREADS * u, kk = q / MR, c = q % MR;
+            const int sr = src_row(k0, kk);
+            rb[u] = sr >= 0 ? src[(int64_t)sr * MR + c] : zero<T>();
+        }
+    };
+    if (K > 0) {
+        load_a(0);
+        load_b(0);
+    }
+    for (int k0 = 0; k0 < K; k0 += MT_K) {
+#pragma unroll
+        for (int u = 0; u < MT_ROWS * MT_K / MT_THREADS; ++u) {
+            const int q = tid + MT_THREADS * u;
+            As[q / MT_ROWS][q % MT_ROWS] = ra[u];
+        }
+#pragma unroll
+        for (int u = 0; u < MT_K * MR / MT_THREADS; ++u) {
+            const int q = tid + MT_THREADS * u;
+            Bs[q / MR][q % MR] = rb[u];
         }
         __syncthreads();
-        for (int q = tid; q < MT_K * MR; q += 256) {
-            const int kk = q / MR, c = q % MR;
-            Bs[kk][c] = s_row[kk] >= 0 ? src[(int64_t)s_row[kk] * MR + c] : zero<T>();
+        if (k0 + MT_K < K) {
+            load_a(k0 + MT_K);
+            load_b(k0 + MT_K);
         }
-        __syncthreads();
 #pragma unroll
         for (int kk = 0; kk < MT_K; ++kk) {
-            // the thread's two rows of A and four columns of B as 16-byte shared
-            // loads (8-byte loads of B columns 32 bytes apart conflict two-way)
-            T a[2], bv[4];
-            lds_vec<2>(&As[kk][2 * ty], a);
+            // the thread's four rows of A and four columns of B as 16-byte
+            // shared loads
+            T a[4], bv[4];
+            lds_vec<4>(&As[kk][4 * ty], a);
             lds_vec<4>(&Bs[kk][4 * tx], bv);
 #pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                acc[0][j] = fmac(a[0], bv[j], acc[0][j]);
-                acc[1][j] = fmac(a[1], bv[j], acc[1][j]);
-            }
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] = fmac(a[i], bv[j], acc[i][j]);
         }
         __syncthreads();
     }
 #pragma unroll
-    for (int i = 0; i < 2; ++i) {
-        const int r = r0 + 2 * ty + i;
+    for (int i = 0; i < 4; ++i) {
+        const int r = r0 + 4 * ty + i;
         if (r >= rows) continue;
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
@@ -291,7 +321,7 @@ ndhss_status multi_apply_run(const FactorData& F, int nrhs, const V* X, int64_t 
     for (int l = F.depth; l >= 0; --l) {
         const int64_t a = F.mj_up_off[l], b = F.mj_up_off[l + 1];
         if (b > a) {
-            mapply_kernel<T, true><<<(unsigned)(b - a), 256, 0, st>>>(F.d_mjobs + a, F.d_node, F.d_foff, front, F.d_sigma,
+            mapply_kernel<T, true><<<(unsigned)(b - a), MT_THREADS, 0, st>>>(F.d_mjobs + a, F.d_node, F.d_foff, front, F.d_sigma,
                                                                      F.d_blist, U, Z, pact, nprob, lrp);
             NDHSS_LAUNCH_CHECK("mapply_kernel");
         }
@@ -302,7 +332,7 @@ ndhss_status multi_apply_run(const FactorData& F, int nrhs, const V* X, int64_t 
     for (int l = 0; l <= F.depth; ++l) {
         const int64_t a = F.mj_dn_off[l], b = F.mj_dn_off[l + 1];
         if (b > a) {
-            mapply_kernel<T, false><<<(unsigned)(b - a), 256, 0, st>>>(F.d_mjobs + a, F.d_node, F.d_foff, front,
+            mapply_kernel<T, false><<<(unsigned)(b - a), MT_THREADS, 0, st>>>(F.d_mjobs + a, F.d_node, F.d_foff, front,
                                                                       F.d_sigma, F.d_blist, U, Z, pact, nprob, lrp);
             NDHSS_LAUNCH_CHECK("mapply_kernel");
         }
