@@ -205,13 +205,12 @@ mapply_kernel(const int2* __restrict__ jobs, const int32_t* __restrict__ node, c
 // T: k x 32 per node (row a at a * 32) in the job's slot.  Job: node, first
 // row, T offset (lo, hi).
 template <typename T, int MODE>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(MT_THREADS)
 mlr_kernel(const int4* __restrict__ jobs, const int32_t* __restrict__ node, const uint64_t* __restrict__ lr_ptr,
            const int32_t* __restrict__ lr_k, const int32_t* __restrict__ blist, T* __restrict__ U, T* __restrict__ Z,
            T* __restrict__ Tb, const int* __restrict__ pact, const int32_t* __restrict__ nprob) {
     __shared__ __align__(16) T As[MT_K][MT_ROWS];
     __shared__ __align__(16) T Bs[MT_K][MR];
-    __shared__ int s_row[MT_K];
     const int4 J = jobs[blockIdx.x];
     const int s = J.x, r0 = J.y;
     const int64_t toff = (int64_t)(((uint64_t)(uint32_t)J.w << 32) | (uint32_t)J.z);
@@ -224,59 +223,73 @@ mlr_kernel(const int4* __restrict__ jobs, const int32_t* __restrict__ node, cons
     T* Ts = Tb + toff;
     const int rows = (MODE == 0 || MODE == 2) ? k : (MODE == 1 ? m_b : m_i);
     const int K = MODE == 0 ? m_i : (MODE == 2 ? m_b : k);
+    const T* src = (MODE == 0) ? U : (MODE == 2 ? Z : Ts);
     const int tid = threadIdx.x, tx = tid & 7, ty = tid >> 3;
-    T acc[2][4];
+    T acc[4][4];
 #pragma unroll
-    for (int i = 0; i < 2; ++i)
+    for (int i = 0; i < 4; ++i)
 #pragma unroll
         for (int j = 0; j < 4; ++j) acc[i][j] = zero<T>();
-    for (int k0 = 0; k0 < K; k0 += MT_K) {
-        const int kc = min(MT_K, K - k0);
-        if (tid < MT_K) {
-            int sr = -1;
-            if (tid < kc) {
-                const int q = k0 + tid;
-                sr = MODE == 0 ? i_off + q : (MODE == 2 ? blist[b_off + q] : q);
-            }
-            s_row[tid] = sr;
-        }
-        for (int q = tid; q < MT_ROWS * MT_K; q += 256) {
-            // transposed operands (MODE 0, 2) load along K, the others along rows
-            const bool kfast = MODE == 0 || MODE == 2;
-            const int r = kfast ? q / MT_K : q % MT_ROWS, kk = kfast ? q % MT_K : q / MT_ROWS;
+    // transposed operands (MODE 0, 2) are loaded along K, the others along rows
+    constexpr bool kfast = MODE == 0 || MODE == 2;
+    auto a_pos = [&](int q, int& r, int& kk) {
+        r = kfast ? q / MT_K : q % MT_ROWS;
+        kk = kfast ? q % MT_K : q / MT_ROWS;
+    };
+    T ra[MT_ROWS * MT_K / MT_THREADS], rb[MT_K * MR / MT_THREADS];
+    auto load = [&](int k0) {
+#pragma unroll
+        for (int u = 0; u < MT_ROWS * MT_K / MT_THREADS; ++u) {
+            int r, kk;
+            a_pos(tid + MT_THREADS * u, r, kk);
             T a = zero<T>();
-            if (r0 + r < rows && kk < kc) {
+            if (r0 + r < rows && k0 + kk < K) {
                 const int rr = r0 + r, ki = k0 + kk;
                 a = MODE == 0 ? X[(int64_t)rr * m_i + ki]
                   : MODE == 1 ? RJt[(int64_t)ki * m_b + rr]
                   : MODE == 2 ? RJt[(int64_t)rr * m_b + ki]
                               : X[(int64_t)ki * m_i + rr];
             }
-            As[kk][r] = a;
+            ra[u] = a;
+        }
+#pragma unroll
+        for (int u = 0; u < MT_K * MR / MT_THREADS; ++u) {
+            const int q = tid + MT_THREADS * u, kk = q / MR, c = q % MR, ki = k0 + kk;
+            int sr = -1;
+            if (ki < K) sr = MODE == 0 ? i_off + ki : (MODE == 2 ? blist[b_off + ki] : ki);
+            rb[u] = sr >= 0 ? src[(int64_t)sr * MR + c] : zero<T>();
+        }
+    };
+    if (K > 0) load(0);
+    for (int k0 = 0; k0 < K; k0 += MT_K) {
+#pragma unroll
+        for (int u = 0; u < MT_ROWS * MT_K / MT_THREADS; ++u) {
+            int r, kk;
+            a_pos(tid + MT_THREADS * u, r, kk);
+            As[kk][r] = ra[u];
+        }
+#pragma unroll
+        for (int u = 0; u < MT_K * MR / MT_THREADS; ++u) {
+            const int q = tid + MT_THREADS * u;
+            Bs[q / MR][q % MR] = rb[u];
         }
         __syncthreads();
-        for (int q = tid; q < MT_K * MR; q += 256) {
-            const int kk = q / MR, c = q % MR;
-            const T* src = (MODE == 0) ? U : (MODE == 2 ? Z : Ts);
-            Bs[kk][c] = s_row[kk] >= 0 ? src[(int64_t)s_row[kk] * MR + c] : zero<T>();
-        }
-        __syncthreads();
+        if (k0 + MT_K < K) load(k0 + MT_K);
 #pragma unroll
         for (int kk = 0; kk < MT_K; ++kk) {
-            T a[2], bv[4];
-            lds_vec<2>(&As[kk][2 * ty], a);
+            T a[4], bv[4];
+            lds_vec<4>(&As[kk][4 * ty], a);
             lds_vec<4>(&Bs[kk][4 * tx], bv);
 #pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                acc[0][j] = fmac(a[0], bv[j], acc[0][j]);
-                acc[1][j] = fmac(a[1], bv[j], acc[1][j]);
-            }
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] = fmac(a[i], bv[j], acc[i][j]);
         }
         __syncthreads();
     }
 #pragma unroll
-    for (int i = 0; i < 2; ++i) {
-        const int r = r0 + 2 * ty + i;
+    for (int i = 0; i < 4; ++i) {
+        const int r = r0 + 4 * ty + i;
         if (r >= rows) continue;
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
@@ -310,10 +323,10 @@ ndhss_status multi_apply_run(const FactorData& F, int nrhs, const V* X, int64_t 
         if (b == a) return NDHSS_OK;
         const int4* jb = F.d_mlr + a;
         switch (mode) {
-            case 0: mlr_kernel<T, 0><<<(unsigned)(b - a), 256, 0, st>>>(jb, F.d_node, F.d_lr_ptr, F.d_lr_k, F.d_blist, U, Z, Tb, pact, nprob); break;
-            case 1: mlr_kernel<T, 1><<<(unsigned)(b - a), 256, 0, st>>>(jb, F.d_node, F.d_lr_ptr, F.d_lr_k, F.d_blist, U, Z, Tb, pact, nprob); break;
-            case 2: mlr_kernel<T, 2><<<(unsigned)(b - a), 256, 0, st>>>(jb, F.d_node, F.d_lr_ptr, F.d_lr_k, F.d_blist, U, Z, Tb, pact, nprob); break;
-            default: mlr_kernel<T, 3><<<(unsigned)(b - a), 256, 0, st>>>(jb, F.d_node, F.d_lr_ptr, F.d_lr_k, F.d_blist, U, Z, Tb, pact, nprob); break;
+            case 0: mlr_kernel<T, 0><<<(unsigned)(b - a), MT_THREADS, 0, st>>>(jb, F.d_node, F.d_lr_ptr, F.d_lr_k, F.d_blist, U, Z, Tb, pact, nprob); break;
+            case 1: mlr_kernel<T, 1><<<(unsigned)(b - a), MT_THREADS, 0, st>>>(jb, F.d_node, F.d_lr_ptr, F.d_lr_k, F.d_blist, U, Z, Tb, pact, nprob); break;
+            case 2: mlr_kernel<T, 2><<<(unsigned)(b - a), MT_THREADS, 0, st>>>(jb, F.d_node, F.d_lr_ptr, F.d_lr_k, F.d_blist, U, Z, Tb, pact, nprob); break;
+            default: mlr_kernel<T, 3><<<(unsigned)(b - a), MT_THREADS, 0, st>>>(jb, F.d_node, F.d_lr_ptr, F.d_lr_k, F.d_blist, U, Z, Tb, pact, nprob); break;
         }
         NDHSS_LAUNCH_CHECK("mlr_kernel");
         return NDHSS_OK;
