@@ -34,6 +34,7 @@ namespace {
 constexpr int KMAX = 32;          // restart + 1 <= KMAX
 constexpr int RT = 256;           // reduction block size
 constexpr int RB = 4 * 152;       // reduction grid (four 256-thread blocks per SM)
+constexpr int GM_BARRIER = KMAX / 4 + 1;   // counter word of the Arnoldi kernel's grid barrier
 
 __device__ __forceinline__ double ldcg(const double* p) { return __ldcg(p); }
 __device__ __forceinline__ c128 ldcg(const c128* p) {
@@ -445,24 +446,23 @@ __device__ __forceinline__ c128 fmac_conj(c128 v, c128 w, c128 acc) {
     return acc;
 }
 
-// STEP, one chunk of C basis vectors i0 .. i0 + C - 1 (<= j): their dot
-// products with w over this block's rows, reduced over the grid (partials
-// per vector, one ticket counter per chunk; every block reads the same rows
-// in every chunk, so a chunk needs no other block's rows).  FIRST_AXPY:
-// w -= V h1 with all j + 1 vectors first (the first chunk of the second
+// STEP, one chunk of C basis vectors i0 .. i0 + C - 1 (<= j): this block's
+// partial dot products with w over its rows (every block takes the same rows
+// in every pass), one partial per vector and block.  AXPY: w += sum_i
+// raw_i cw[i] with all j + 1 vectors first (the first chunk of the second
 // Gram-Schmidt pass).  Exact-count instantiations: a predicated-off FP64
 // instruction still occupies the FP64 pipe.
-template <typename V, int C, bool FIRST_AXPY>
-__device__ void gm_cgs_chunk(GmDev<V>* S, V* __restrict__ Vb, int64_t ldv, int n, V* __restrict__ partial, int j,
-                             int i0, int chunk, const V* ch, V* out) {
+template <typename V, int C, bool AXPY>
+__device__ void gm_pass_chunk(V* __restrict__ Vb, int64_t ldv, int n, int j, int i0, const V* cw,
+                              V* __restrict__ partial) {
     V* w = Vb + (int64_t)(j + 1) * ldv;
     V acc[C];
 #pragma unroll
     for (int u = 0; u < C; ++u) acc[u] = zero<V>();
     for (int64_t row = (int64_t)blockIdx.x * RT + threadIdx.x; row < n; row += (int64_t)gridDim.x * RT) {
         V wv = w[row];
-        if (FIRST_AXPY) {
-            for (int i = 0; i <= j; ++i) wv = fmac(Vb[row + i * ldv], ch[i], wv);
+        if (AXPY) {
+            for (int i = 0; i <= j; ++i) wv = fmac(Vb[row + i * ldv], cw[i], wv);
             w[row] = wv;
         }
         V v[C];
@@ -476,12 +476,6 @@ __device__ void gm_cgs_chunk(GmDev<V>* S, V* __restrict__ Vb, int64_t ldv, int n
         const V bs = block_sum(acc[u]);
         if (threadIdx.x == 0) partial[(int64_t)(i0 + u) * gridDim.x + blockIdx.x] = bs;
     }
-    if (last_block(S->counter + 1 + chunk, gridDim.x)) {
-        for (int u = 0; u < C; ++u) {
-            const V sum = block_sum_partials(partial + (int64_t)(i0 + u) * gridDim.x, gridDim.x);
-            if (threadIdx.x == 0) out[i0 + u] = scale(sum, S->scale[i0 + u]);
-        }
-    }
 }
 
 // basis vectors per chunk: eight real or four complex accumulators and
@@ -489,43 +483,53 @@ __device__ void gm_cgs_chunk(GmDev<V>* S, V* __restrict__ Vb, int64_t ldv, int n
 // 256-thread blocks per SM
 template <typename V> constexpr int cgs_width() { return sizeof(V) == 16 ? 4 : 8; }
 
-template <typename V, bool FIRST_AXPY>
-__device__ void gm_cgs_dispatch(GmDev<V>* S, V* Vb, int64_t ldv, int n, V* partial, int j, int i0, int chunk,
-                                const V* ch, V* out) {
+// one Gram-Schmidt pass's partials: V^H w (AXPY: after w += V cw)
+template <typename V, bool AXPY>
+__device__ void gm_pass(V* Vb, int64_t ldv, int n, int j, const V* cw, V* partial) {
     constexpr int CW = cgs_width<V>();
-    switch (min(CW, j + 1 - i0)) {
-#define NDHSS_CGS(CC) case CC: if constexpr (CC <= CW) gm_cgs_chunk<V, CC, FIRST_AXPY>(S, Vb, ldv, n, partial, j, i0, chunk, ch, out); break;
-        NDHSS_CGS(1) NDHSS_CGS(2) NDHSS_CGS(3) NDHSS_CGS(4) NDHSS_CGS(5) NDHSS_CGS(6) NDHSS_CGS(7) NDHSS_CGS(8)
+    for (int i0 = 0; i0 <= j; i0 += CW) {
+        const bool ax = AXPY && i0 == 0;
+        switch (min(CW, j + 1 - i0)) {
+#define NDHSS_CGS(CC)                                                                               \
+    case CC:                                                                                        \
+        if constexpr (CC <= CW) {                                                                   \
+            if (ax) gm_pass_chunk<V, CC, true>(Vb, ldv, n, j, i0, cw, partial);                     \
+            else gm_pass_chunk<V, CC, false>(Vb, ldv, n, j, i0, cw, partial);                       \
+        }                                                                                           \
+        break;
+            NDHSS_CGS(1) NDHSS_CGS(2) NDHSS_CGS(3) NDHSS_CGS(4) NDHSS_CGS(5) NDHSS_CGS(6) NDHSS_CGS(7) NDHSS_CGS(8)
 #undef NDHSS_CGS
-        default: break;
+            default: break;
+        }
     }
 }
 
-// STEP: h1 = V^H w (AXPY = false), or w -= V h1 then h2 = V^H w (AXPY = true),
-// cgs_width basis vectors at a time
-template <typename V, bool AXPY>
-__device__ void gm_cgs(GmDev<V>* S, V* __restrict__ Vb, int64_t ldv, int n, V* __restrict__ partial) {
-    const int j = S->j;
-    __shared__ V ch[KMAX];
-    if (AXPY && threadIdx.x <= j) ch[threadIdx.x] = -scale(S->h1[threadIdx.x], S->scale[threadIdx.x]);
-    if (AXPY) __syncthreads();
-    V* out = AXPY ? S->h2 : S->h1;
-    for (int i0 = 0, chunk = 0; i0 <= j; i0 += cgs_width<V>(), ++chunk) {
-        if (AXPY && i0 == 0) gm_cgs_dispatch<V, true>(S, Vb, ldv, n, partial, j, i0, chunk, ch, out);
-        else gm_cgs_dispatch<V, false>(S, Vb, ldv, n, partial, j, i0, chunk, ch, out);
+// after a grid barrier: h[i] = scale_i * (sum over blocks of the partials of
+// vector i), i <= j, into shared memory; warp w adds vectors w, w + 8, ...
+// (lane-strided in block order, then the warp's fixed tree: every block gets
+// the same values)
+template <typename V>
+__device__ void gm_sum_partials(const V* __restrict__ partial, int j, const double* scl, V* h) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int i = warp; i <= j; i += RT / 32) {
+        V acc = zero<V>();
+        for (unsigned q = lane; q < gridDim.x; q += 32) acc += ldcg(partial + (int64_t)i * gridDim.x + q);
+        acc = warp_sum(acc);
+        if (lane == 0) h[i] = scale(acc, scl[i]);
     }
+    __syncthreads();
 }
 
 // STEP, last part: w -= V h2, ||w||; the last block forms the Hessenberg
-// column j, the Givens rotation and the cycle's stopping tests and writes
-// the status word.  barrier_word: the grid barrier's counter, cleared here
-// (every block has passed the barriers by then).
+// column j from h1 + h2 and ||w||, applies the previous Givens rotations,
+// forms the new one, runs the cycle's stopping tests (and, when the cycle
+// ends, solves H y = g), clears the barrier word and writes the status word.
+// Only the fields it needs are staged in shared memory.
 template <typename V>
 __device__ void gm_axnorm_step(GmDev<V>* S, V* __restrict__ Vb, int64_t ldv, int n, double* __restrict__ dpartial,
-                               GmStatus* hstat, GmDev<V>& sh, int barrier_word) {
-    const int j = S->j;
+                               GmStatus* hstat, const V* h1, const V* h2, const double* scl, int j) {
     __shared__ V ch[KMAX];
-    if (threadIdx.x <= j) ch[threadIdx.x] = -scale(S->h2[threadIdx.x], S->scale[threadIdx.x]);
+    if (threadIdx.x <= j) ch[threadIdx.x] = -scale(h2[threadIdx.x], scl[threadIdx.x]);
     __syncthreads();
     V* w = Vb + (int64_t)(j + 1) * ldv;
     double acc = 0.0;
@@ -539,66 +543,95 @@ __device__ void gm_axnorm_step(GmDev<V>* S, V* __restrict__ Vb, int64_t ldv, int
     if (threadIdx.x == 0) dpartial[blockIdx.x] = bs;
     if (!last_block(S->counter, gridDim.x)) return;
     const double ss = block_sum_partials(dpartial, gridDim.x);
-    gm_state_load(sh, S);
+    __shared__ V sHj[KMAX + 1], ssn[KMAX], sy[KMAX], sg[KMAX + 1];
+    __shared__ double scs[KMAX];
+    __shared__ int s_end, s_k;
+    for (int i = threadIdx.x; i < j; i += RT) {
+        ssn[i] = S->sn[i];
+        scs[i] = S->cs[i];
+    }
+    __syncthreads();
     if (threadIdx.x == 0) {
-    GmDev<V>* S = &sh;                          // thread 0 works on the shared copy
-    if (barrier_word >= 0) S->counter[barrier_word] = 0;
-    const double hn = sqrt(ss);
-    V* Hj = S->H + (int64_t)j * KMAX;
-    for (int i = 0; i <= j; ++i) Hj[i] = S->h1[i] + S->h2[i];
-    Hj[j + 1] = from_real<V>(hn);
-    for (int i = 0; i < j; ++i) {
-        const V t0 = scale(Hj[i], S->cs[i]) + S->sn[i] * Hj[i + 1];
-        const V t1 = scale(Hj[i + 1], S->cs[i]) - conjv(S->sn[i]) * Hj[i];
-        Hj[i] = t0;
-        Hj[i + 1] = t1;
-    }
-    const V a = Hj[j], bb = Hj[j + 1];
-    double c;
-    V sn;
-    const double aa = absv(a), ab = absv(bb);
-    if (ab == 0.0) {
-        c = 1.0;
-        sn = zero<V>();
-    } else if (aa == 0.0) {
-        c = 0.0;
-        sn = scale(conjv(bb), 1.0 / ab);
-    } else {
-        const double tt = hypot(aa, ab);
-        c = aa / tt;
-        sn = scale(a, 1.0 / aa) * scale(conjv(bb), 1.0 / tt);
-    }
-    S->cs[j] = c;
-    S->sn[j] = sn;
-    Hj[j] = scale(a, c) + sn * bb;
-    Hj[j + 1] = zero<V>();
-    const V gj = S->g[j];
-    S->g[j + 1] = -(conjv(sn) * gj);
-    S->g[j] = scale(gj, c);
-    S->scale[j + 1] = hn > 0.0 ? 1.0 / hn : 0.0;
-    S->its++;
-    const double gres = absv(S->g[j + 1]);
-    S->last_res = gres / S->zbnorm;
-    const bool inner_done = S->cyc_target > 0.0 ? gres <= S->cyc_target * S->beta : S->last_res <= S->inner * S->tol;
-    if (inner_done || gres <= S->rtol_eff * S->beta || hn == 0.0 || S->its >= S->maxit || j + 1 >= S->R) {
-        // the cycle ends: y = H(0:k, 0:k)^{-1} g(0:k) for the next block's x update
-        const int k = j + 1;
-        for (int i = k - 1; i >= 0; --i) {
-            V yv = S->g[i];
-            for (int l = i + 1; l < k; ++l) yv = yv - S->H[(int64_t)l * KMAX + i] * S->y[l];
-            S->y[i] = cdiv(yv, S->H[(int64_t)i * KMAX + i]);
+        S->counter[GM_BARRIER] = 0;
+        const double hn = sqrt(ss);
+        V* Hj = sHj;
+        for (int i = 0; i <= j; ++i) Hj[i] = h1[i] + h2[i];
+        Hj[j + 1] = from_real<V>(hn);
+        for (int i = 0; i < j; ++i) {
+            const V t0 = scale(Hj[i], scs[i]) + ssn[i] * Hj[i + 1];
+            const V t1 = scale(Hj[i + 1], scs[i]) - conjv(ssn[i]) * Hj[i];
+            Hj[i] = t0;
+            Hj[i + 1] = t1;
         }
-        S->jend = k;
-        S->have_cycle = 1;
-        S->mode = GM_RESTART;
-    } else {
+        const V a = Hj[j], bb = Hj[j + 1];
+        double c;
+        V sn;
+        const double aa = absv(a), ab = absv(bb);
+        if (ab == 0.0) {
+            c = 1.0;
+            sn = zero<V>();
+        } else if (aa == 0.0) {
+            c = 0.0;
+            sn = scale(conjv(bb), 1.0 / ab);
+        } else {
+            const double tt = hypot(aa, ab);
+            c = aa / tt;
+            sn = scale(a, 1.0 / aa) * scale(conjv(bb), 1.0 / tt);
+        }
+        S->cs[j] = c;
+        S->sn[j] = sn;
+        Hj[j] = scale(a, c) + sn * bb;
+        Hj[j + 1] = zero<V>();
+        const V gj = S->g[j];
+        const V gj1 = -(conjv(sn) * gj);
+        S->g[j + 1] = gj1;
+        S->g[j] = scale(gj, c);
+        S->scale[j + 1] = hn > 0.0 ? 1.0 / hn : 0.0;
+        const int its = S->its + 1;
+        S->its = its;
+        const double gres = absv(gj1), beta = S->beta, cyc_target = S->cyc_target;
+        const double last_res = gres / S->zbnorm;
+        S->last_res = last_res;
+        const bool inner_done = cyc_target > 0.0 ? gres <= cyc_target * beta : last_res <= S->inner * S->tol;
+        const bool end = inner_done || gres <= S->rtol_eff * beta || hn == 0.0 || its >= S->maxit || j + 1 >= S->R;
+        s_end = end ? 1 : 0;
+        s_k = j + 1;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i <= j + 1; i += RT) S->H[(int64_t)j * KMAX + i] = sHj[i];
+    if (s_end) {
+        // the cycle ends: y = H(0:k, 0:k)^{-1} g(0:k) for the next block's x update
+        const int k = s_k;
+        __shared__ V sH[KMAX * KMAX];
+        for (int q = threadIdx.x; q < k * k; q += RT) {
+            const int col = q / k, row = q % k;
+            sH[col * KMAX + row] = col == j ? sHj[row] : S->H[(int64_t)col * KMAX + row];
+        }
+        for (int i = threadIdx.x; i < k; i += RT) sg[i] = S->g[i];
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            for (int i = k - 1; i >= 0; --i) {
+                V yv = sg[i];
+                for (int l = i + 1; l < k; ++l) yv = yv - sH[l * KMAX + i] * sy[l];
+                sy[i] = cdiv(yv, sH[i * KMAX + i]);
+            }
+        }
+        __syncthreads();
+        for (int i = threadIdx.x; i < k; i += RT) S->y[i] = sy[i];
+        if (threadIdx.x == 0) {
+            S->jend = k;
+            S->have_cycle = 1;
+            S->mode = GM_RESTART;
+        }
+    } else if (threadIdx.x == 0) {
         S->j = j + 1;
     }
-    hstat->done = S->done;
-    hstat->its = S->its;
-    __threadfence_system();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        hstat->done = S->done;
+        hstat->its = S->its;
+        __threadfence_system();
     }
-    gm_state_store(S, sh);
 }
 
 // Grid barrier of a cooperative launch (every block resident): thread 0
@@ -631,7 +664,6 @@ __device__ bool gm_grid_sync(unsigned* ctr, unsigned target) {
     return s_ok != 0;
 }
 
-constexpr int GM_BARRIER = KMAX / 4 + 1;    // counter word of the Arnoldi kernel's grid barrier
 
 // One cooperative launch per GMRES block for what follows the apply.
 // RESTART: beta = ||V_0||, g = beta e_1.  STEP: h1 = V^H w (grid barrier),
@@ -689,10 +721,21 @@ __global__ void __launch_bounds__(RT, 4) gm_arnoldi_kernel(GmDev<V>* S, V* __res
         return;
     }
     unsigned* bar = S->counter + GM_BARRIER;
-    gm_cgs<V, false>(S, Vb, ldv, n, partial);
+    const int j = S->j;
+    __shared__ double scl[KMAX];
+    __shared__ V h1[KMAX], h2[KMAX], cw[KMAX];
+    if (threadIdx.x <= j) scl[threadIdx.x] = S->scale[threadIdx.x];
+    __syncthreads();
+    // h1 = V^H w: partials, grid barrier, every block adds them
+    gm_pass<V, false>(Vb, ldv, n, j, nullptr, partial);
     bool ok = gm_grid_sync(bar, gridDim.x);
     if (ok) {
-        gm_cgs<V, true>(S, Vb, ldv, n, partial);
+        gm_sum_partials(partial, j, scl, h1);
+        if (threadIdx.x <= j) cw[threadIdx.x] = -scale(h1[threadIdx.x], scl[threadIdx.x]);
+        __syncthreads();
+        // w -= V h1, h2 = V^H w (the second pass's partials in their own buffer:
+        // other blocks may still be adding the first pass's)
+        gm_pass<V, true>(Vb, ldv, n, j, cw, partial + (int64_t)RB * KMAX);
         ok = gm_grid_sync(bar, 2 * gridDim.x);
     }
     if (!ok) {
@@ -703,7 +746,8 @@ __global__ void __launch_bounds__(RT, 4) gm_arnoldi_kernel(GmDev<V>* S, V* __res
         }
         return;
     }
-    gm_axnorm_step<V>(S, Vb, ldv, n, dpartial, hstat, sh, GM_BARRIER);
+    gm_sum_partials(partial + (int64_t)RB * KMAX, j, scl, h2);
+    gm_axnorm_step<V>(S, Vb, ldv, n, dpartial, hstat, h1, h2, scl, j);
 }
 
 // Pinned status words of this thread's solves (two blocks in flight), mapped
@@ -736,7 +780,7 @@ ndhss_status gmres_one(const FactorData& F, const int32_t* rowptr, const int32_t
     V* Vb = (V*)carve(sizeof(V) * ldv * (R + 1));
     V* t = (V*)carve(sizeof(V) * n);
     V* r = (V*)carve(sizeof(V) * n);
-    V* part = (V*)carve(sizeof(V) * RB * KMAX);
+    V* part = (V*)carve(sizeof(V) * 2 * RB * KMAX);   // the two Gram-Schmidt passes' partials
     double* dpart = (double*)carve(sizeof(double) * RB);
     GmDev<V>* S = (GmDev<V>*)carve(sizeof(GmDev<V>));
     void* awork = carve(apply_work_bytes(F));
@@ -863,7 +907,7 @@ size_t gmres_work_bytes(const FactorData& F, int R, size_t vsz) {
     add(vsz * ldv * (R + 1));
     add(vsz * F.n);
     add(vsz * F.n);
-    add(vsz * RB * KMAX);
+    add(vsz * 2 * RB * KMAX);
     add(8 * RB);
     add(std::max(sizeof(GmDev<double>), sizeof(GmDev<c128>)));
     add(apply_work_bytes(F));
