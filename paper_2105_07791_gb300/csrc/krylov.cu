@@ -227,22 +227,6 @@ struct alignas(16) GmDev {
 // The last block of a reduction takes its decisions on a shared-memory copy
 // of the state (one parallel load; thread 0's scalar code would otherwise wait
 // out a global-memory round trip per field) and writes it back.
-template <typename V>
-__device__ __forceinline__ void gm_state_load(GmDev<V>& sh, const GmDev<V>* S) {
-    static_assert(sizeof(GmDev<V>) % 16 == 0, "state copied in 16-byte words");
-    const int4* src = reinterpret_cast<const int4*>(S);
-    int4* dst = reinterpret_cast<int4*>(&sh);
-    for (int i = threadIdx.x; i < (int)(sizeof(GmDev<V>) / 16); i += blockDim.x) dst[i] = __ldcg(src + i);
-    __syncthreads();
-}
-template <typename V>
-__device__ __forceinline__ void gm_state_store(GmDev<V>* S, const GmDev<V>& sh) {
-    __syncthreads();
-    const int4* src = reinterpret_cast<const int4*>(&sh);
-    int4* dst = reinterpret_cast<int4*>(S);
-    for (int i = threadIdx.x; i < (int)(sizeof(GmDev<V>) / 16); i += blockDim.x) __stcg(dst + i, src[i]);
-}
-
 template <typename V> __device__ __forceinline__ V from_real(double v);
 template <> __device__ __forceinline__ double from_real<double>(double v) { return v; }
 template <> __device__ __forceinline__ c128 from_real<c128>(double v) { return {v, 0.0}; }
@@ -392,10 +376,8 @@ __global__ void __launch_bounds__(RT, 4) gm_resid_kernel(GmDev<V>* S, const V* _
     if (threadIdx.x == 0) partial[blockIdx.x] = bs;
     if (!last_block(S->counter, gridDim.x)) return;
     const double tot = block_sum_partials(partial, gridDim.x);
-    __shared__ GmDev<V> sh;
-    gm_state_load(sh, S);
-    if (threadIdx.x == 0) gm_decide(&sh, tot, blk);
-    gm_state_store(S, sh);
+    // a handful of scalar fields: thread 0 works on the state in place
+    if (threadIdx.x == 0) gm_decide(S, tot, blk);
 }
 
 // RESTART: the float64 true residual ||r||^2 = rr decides convergence,
@@ -675,7 +657,6 @@ template <typename V>
 __global__ void __launch_bounds__(RT, 4) gm_arnoldi_kernel(GmDev<V>* S, V* __restrict__ Vb, int64_t ldv, int n,
                                                         V* __restrict__ partial, double* __restrict__ dpartial,
                                                         GmStatus* hstat) {
-    __shared__ GmDev<V> sh;
     const int done = S->done, bmode = S->bmode;
     if (done) {
         if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -693,31 +674,29 @@ __global__ void __launch_bounds__(RT, 4) gm_arnoldi_kernel(GmDev<V>* S, V* __res
         if (threadIdx.x == 0) dpartial[blockIdx.x] = bs;
         if (!last_block(S->counter, gridDim.x)) return;
         const double ss = block_sum_partials(dpartial, gridDim.x);
-        gm_state_load(sh, S);
+        const double beta = sqrt(ss);
+        for (int i = threadIdx.x; i < KMAX; i += RT) S->g[i] = i == 0 ? from_real<V>(beta) : zero<V>();
         if (threadIdx.x == 0) {
-            const double beta = sqrt(ss);
             bool ok = true;
-            if (sh.zbnorm < 0.0) {
-                sh.zbnorm = beta;
+            if (S->zbnorm < 0.0) {
+                S->zbnorm = beta;
                 if (beta == 0.0) {                   // P^{-1} b vanished
-                    sh.done = 3;
-                    sh.skip = 1;
+                    S->done = 3;
+                    S->skip = 1;
                     ok = false;
                 }
             }
             if (ok) {
-                sh.beta = beta;
-                for (int i = 0; i < KMAX; ++i) sh.g[i] = zero<V>();
-                sh.g[0] = from_real<V>(beta);
-                sh.scale[0] = beta > 0.0 ? 1.0 / beta : 0.0;
-                sh.j = 0;
-                sh.mode = GM_STEP;
+                S->beta = beta;
+                S->scale[0] = beta > 0.0 ? 1.0 / beta : 0.0;
+                S->j = 0;
+                S->mode = GM_STEP;
             }
-            hstat->done = sh.done;
-            hstat->its = sh.its;
+            __threadfence();
+            hstat->done = S->done;
+            hstat->its = S->its;
             __threadfence_system();
         }
-        gm_state_store(S, sh);
         return;
     }
     unsigned* bar = S->counter + GM_BARRIER;
