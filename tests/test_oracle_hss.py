@@ -248,3 +248,26 @@ def test_factor_compressed_subtree_equals_full_factorization_on_that_subtree():
         else:
             assert np.array_equal(sub.R[s], full.R[s])
     assert lowrank > 0
+
+
+@pytest.mark.parametrize("case", ["poisson", "helmholtz"])
+def test_compressed_apply_converges_to_the_exact_apply_as_eps_shrinks(case):
+    """With compression active on every level at and above the switching level
+    (HSS S, low-rank R and L = R^T above it) and eps = 1e-12, Alg. 3.1 on the
+    compressed factor agrees with the exact dense factor's apply to ~1e-9;
+    at eps = 1e-6 the difference is orders of magnitude larger.  A transposed
+    or dropped low-rank block, or a sign error in the up or down sweep, fails
+    the tight bound."""
+    P = poisson_dirichlet(48) if case == "poisson" else helmholtz_impedance(40, 2, 10.0, seed=5)
+    T = build_tree(P.coords, P.A.indptr, P.A.indices, 32)
+    exact = apply_inverse(factor_dense(T, P.A), P.b)
+    tight = factor_compressed(T, P.A, hss_levels=3, eps=1e-12)
+    loose = factor_compressed(T, P.A, hss_levels=3, eps=1e-6)
+    assert tight.hss and tight.kmax > 0
+    lr_nodes = [s for s, R in tight.R.items() if hasattr(R, "matmat")] if isinstance(tight.R, dict) else \
+               [s for s in range(T.nnodes) if tight.R[s] is not None and hasattr(tight.R[s], "matmat")]
+    assert lr_nodes, "no low-rank Gauss transform was exercised"
+    e_tight = np.linalg.norm(apply_compressed(tight, P.b) - exact) / np.linalg.norm(exact)
+    e_loose = np.linalg.norm(apply_compressed(loose, P.b) - exact) / np.linalg.norm(exact)
+    assert e_tight <= 1e-9, e_tight
+    assert e_loose >= 100 * e_tight, (e_loose, e_tight)
