@@ -471,6 +471,12 @@ def run_gpu(a):
         torch.distributed.destroy_process_group()
 
 
+def _mapply_tiles():
+    """The committed tile-shape table of the 32-column apply (autotune.py)."""
+    from paper_2105_07791_gb300 import autotune
+    return autotune.current_table()
+
+
 def batched_line(a, ndhss, torch, stream):
     """The batched workload: every step factors the forest of all problems
     (one call, complex64 dense fronts) and solves problems x 32 right-hand
@@ -566,7 +572,7 @@ def batched_line(a, ndhss, torch, stream):
             "converged": all(d["converged"] for d in flat), "gpu_launches_per_step": int(launches),
             "factor_bytes": fs["factor_bytes"], "apply_multi_ms": ap_ms,
             "apply_multi_tflops": flops / (ap_ms / 1e3) / 1e12, "apply_multi_flops": flops,
-            "host_setup_s": setup_s, "compressed": compressed}
+            "host_setup_s": setup_s, "compressed": compressed, "mapply_tiles": _mapply_tiles()}
 
 
 def elastic_line(a, ndhss, torch, stream):

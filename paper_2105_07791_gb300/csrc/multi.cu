@@ -26,9 +26,11 @@
 // that stops or converges keeps its x while the others go on.
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <vector>
 
 #include "factor.cuh"
+#include "mapply_tune.h"
 
 namespace ndhss {
 namespace {
@@ -84,16 +86,18 @@ __global__ void mscatter_kernel(int64_t n, int nrhs, const int32_t* __restrict__
     }
 }
 
-// One 64-row x 32-column tile of node s: UP = the first m_i columns of the
-// front against u(I^s o sigma) (rows < m_i to z, rows >= m_i subtracted from
-// u(B^s)); !UP = the R block against z(B^s), added to z(I^s).
-template <typename T, bool UP>
-__global__ void __launch_bounds__(MT_THREADS)
+// One ROWS-row x 32-column tile of node s (ROWS 32 or 64, 2 ROWS threads):
+// UP = the first m_i columns of the front against u(I^s o sigma) (rows < m_i
+// to z, rows >= m_i subtracted from u(B^s)); !UP = the R block against
+// z(B^s), added to z(I^s).
+template <typename T, bool UP, int ROWS>
+__global__ void __launch_bounds__(2 * ROWS)
 mapply_kernel(const int2* __restrict__ jobs, const int32_t* __restrict__ node, const int64_t* __restrict__ foff,
               const T* __restrict__ front, const int32_t* __restrict__ sigma, const int32_t* __restrict__ blist,
               T* __restrict__ U, T* __restrict__ Z, const int* __restrict__ pact, const int32_t* __restrict__ nprob,
               const uint64_t* __restrict__ lr_ptr) {
-    __shared__ __align__(16) T As[MT_K][MT_ROWS];
+    constexpr int NTH = 2 * ROWS;
+    __shared__ __align__(16) T As[MT_K][ROWS];
     __shared__ __align__(16) T Bs[MT_K][MR];
     const int2 J = jobs[blockIdx.x];
     const int s = J.x, r0 = J.y;
@@ -108,9 +112,8 @@ mapply_kernel(const int2* __restrict__ jobs, const int32_t* __restrict__ node, c
     const int K = UP ? m_i : m_b;
     const T* A = UP ? F : F + (int64_t)m_i * m;
     const T* src = UP ? U : Z;
-    // 128 threads: thread (ty, tx) owns rows 4 ty .. 4 ty + 3 and columns
-    // 4 tx .. 4 tx + 3 of the 64 x 32 tile (16 products per 64 bytes read
-    // from shared memory)
+    // thread (ty, tx) owns rows 4 ty .. 4 ty + 3 and columns 4 tx .. 4 tx + 3
+    // of the tile (16 products per 64 bytes read from shared memory)
     const int tid = threadIdx.x, tx = tid & 7, ty = tid >> 3;
     T acc[4][4];
 #pragma unroll
@@ -119,12 +122,12 @@ mapply_kernel(const int2* __restrict__ jobs, const int32_t* __restrict__ node, c
         for (int j = 0; j < 4; ++j) acc[i][j] = zero<T>();
     // the next K chunk's A entries, its row indices and then its B rows are
     // loaded into registers while the current chunk is multiplied
-    T ra[MT_ROWS * MT_K / MT_THREADS], rb[MT_K * MR / MT_THREADS];
+    T ra[ROWS * MT_K / NTH], rb[MT_K * MR / NTH];
     auto load_a = [&](int k0) {
         const int kc = min(MT_K, K - k0);
 #pragma unroll
-        for (int u = 0; u < MT_ROWS * MT_K / MT_THREADS; ++u) {
-            const int q = tid + MT_THREADS * u, r = q % MT_ROWS, kk = q / MT_ROWS;
+        for (int u = 0; u < ROWS * MT_K / NTH; ++u) {
+            const int q = tid + NTH * u, r = q % ROWS, kk = q / ROWS;
             ra[u] = (r0 + r < rows && kk < kc) ? A[(int64_t)(k0 + kk) * m + r0 + r] : zero<T>();
         }
     };
@@ -133,8 +136,8 @@ mapply_kernel(const int2* __restrict__ jobs, const int32_t* __restrict__ node, c
     };
     auto load_b = [&](int k0) {
 #pragma unroll
-        for (int u = 0; u < MT_K * MR / MT_THREADS; ++u) {
-            const int q = tid + MT_THREADS * u, kk = q / MR, c = q % MR;
+        for (int u = 0; u < MT_K * MR / NTH; ++u) {
+            const int q = tid + NTH * u, kk = q / MR, c = q % MR;
             const int sr = src_row(k0, kk);
             rb[u] = sr >= 0 ? src[(int64_t)sr * MR + c] : zero<T>();
         }
@@ -145,13 +148,13 @@ mapply_kernel(const int2* __restrict__ jobs, const int32_t* __restrict__ node, c
     }
     for (int k0 = 0; k0 < K; k0 += MT_K) {
 #pragma unroll
-        for (int u = 0; u < MT_ROWS * MT_K / MT_THREADS; ++u) {
-            const int q = tid + MT_THREADS * u;
-            As[q / MT_ROWS][q % MT_ROWS] = ra[u];
+        for (int u = 0; u < ROWS * MT_K / NTH; ++u) {
+            const int q = tid + NTH * u;
+            As[q / ROWS][q % ROWS] = ra[u];
         }
 #pragma unroll
-        for (int u = 0; u < MT_K * MR / MT_THREADS; ++u) {
-            const int q = tid + MT_THREADS * u;
+        for (int u = 0; u < MT_K * MR / NTH; ++u) {
+            const int q = tid + NTH * u;
             Bs[q / MR][q % MR] = rb[u];
         }
         __syncthreads();
@@ -331,23 +334,38 @@ ndhss_status multi_apply_run(const FactorData& F, int nrhs, const V* X, int64_t 
         NDHSS_LAUNCH_CHECK("mlr_kernel");
         return NDHSS_OK;
     };
-    for (int l = F.depth; l >= 0; --l) {
-        const int64_t a = F.mj_up_off[l], b = F.mj_up_off[l + 1];
-        if (b > a) {
-            mapply_kernel<T, true><<<(unsigned)(b - a), MT_THREADS, 0, st>>>(F.d_mjobs + a, F.d_node, F.d_foff, front, F.d_sigma,
-                                                                     F.d_blist, U, Z, pact, nprob, lrp);
+    // the dense tiles of level l in its two tile shapes (plan: variant-major per level)
+    auto dense_launch = [&](bool up, int l) -> ndhss_status {
+        const std::vector<int64_t>& off = up ? F.mj_up_off : F.mj_dn_off;
+        for (int v = 0; v < 2; ++v) {
+            const int64_t a = off[2 * l + v], b = off[2 * l + v + 1];
+            if (b == a) continue;
+            const int2* jb = F.d_mjobs + a;
+            if (up && v == 0)
+                mapply_kernel<T, true, 32><<<(unsigned)(b - a), 64, 0, st>>>(jb, F.d_node, F.d_foff, front, F.d_sigma, F.d_blist, U, Z, pact, nprob, lrp);
+            else if (up)
+                mapply_kernel<T, true, 64><<<(unsigned)(b - a), 128, 0, st>>>(jb, F.d_node, F.d_foff, front, F.d_sigma, F.d_blist, U, Z, pact, nprob, lrp);
+            else if (v == 0)
+                mapply_kernel<T, false, 32><<<(unsigned)(b - a), 64, 0, st>>>(jb, F.d_node, F.d_foff, front, F.d_sigma, F.d_blist, U, Z, pact, nprob, lrp);
+            else
+                mapply_kernel<T, false, 64><<<(unsigned)(b - a), 128, 0, st>>>(jb, F.d_node, F.d_foff, front, F.d_sigma, F.d_blist, U, Z, pact, nprob, lrp);
             NDHSS_LAUNCH_CHECK("mapply_kernel");
+        }
+        return NDHSS_OK;
+    };
+    for (int l = F.depth; l >= 0; --l) {
+        {
+            const ndhss_status rc = dense_launch(true, l);
+            if (rc != NDHSS_OK) return rc;
         }
         ndhss_status rc = lr_launch(0, l);
         if (rc == NDHSS_OK) rc = lr_launch(1, l);
         if (rc != NDHSS_OK) return rc;
     }
     for (int l = 0; l <= F.depth; ++l) {
-        const int64_t a = F.mj_dn_off[l], b = F.mj_dn_off[l + 1];
-        if (b > a) {
-            mapply_kernel<T, false><<<(unsigned)(b - a), MT_THREADS, 0, st>>>(F.d_mjobs + a, F.d_node, F.d_foff, front,
-                                                                      F.d_sigma, F.d_blist, U, Z, pact, nprob, lrp);
-            NDHSS_LAUNCH_CHECK("mapply_kernel");
+        {
+            const ndhss_status rc = dense_launch(false, l);
+            if (rc != NDHSS_OK) return rc;
         }
         ndhss_status rc = lr_launch(2, l);
         if (rc == NDHSS_OK) rc = lr_launch(3, l);
@@ -866,32 +884,61 @@ ndhss_status gmres_batched_run(const FactorData& F, const int32_t* rowptr, const
 
 }  // namespace
 
-// The multi-apply plan: per level the (node, first row) of every 64-row tile
-// of the up-sweep (all m rows of the first m_i columns) and of the down-sweep
-// (the m_i rows of R), one device array.
+// The tile-rows table (32 or 64 per front-size bucket): the autotuned one,
+// or NDHSS_MAPPLY_TILES ("r0,r1,r2,r3"), read at every plan
+static void mapply_tile_table(int (&table)[MAPPLY_NBUCKET]) {
+    for (int q = 0; q < MAPPLY_NBUCKET; ++q) table[q] = MAPPLY_TILE_ROWS[q];
+    if (const char* e = std::getenv("NDHSS_MAPPLY_TILES")) {
+        int q = 0;
+        for (const char* c = e; *c && q < MAPPLY_NBUCKET; ++q) {
+            const int v = std::atoi(c);
+            if (v == 32 || v == 64) table[q] = v;
+            while (*c && *c != ',') ++c;
+            if (*c == ',') ++c;
+        }
+    }
+}
+
+// The multi-apply plan: per level and tile shape the (node, first row) of
+// every tile of the up-sweep (all m rows of the first m_i columns; a
+// low-rank node's m_i) and of the down-sweep (the m_i rows of R), one device
+// array; offsets at [2 level + shape], shape 0: 32 rows, 1: 64 rows.
 ndhss_status build_multi_plan(FactorData& F, cudaStream_t st) {
     std::vector<int32_t> jobs;
-    F.mj_up_off.assign(F.depth + 2, 0);
-    F.mj_dn_off.assign(F.depth + 2, 0);
+    int table[MAPPLY_NBUCKET];
+    mapply_tile_table(table);
+    auto mapply_tile_rows = [&](int rows) {
+        int q = 0;
+        while (q < MAPPLY_NBUCKET - 1 && rows >= MAPPLY_BUCKET_EDGES[q]) ++q;
+        return table[q];
+    };
+    F.mj_up_off.assign(2 * (F.depth + 1) + 1, 0);
+    F.mj_dn_off.assign(2 * (F.depth + 1) + 1, 0);
     auto lowrank = [&](int s) { return !F.lr_ptr.empty() && F.lr_ptr[s] != 0; };
-    for (int l = 0; l <= F.depth; ++l) {
-        F.mj_up_off[l] = (int64_t)jobs.size() / 2;
-        for (int s : F.levels[l]) {
-            const int mi = F.m_i(s), m = lowrank(s) ? mi : mi + F.m_b(s);
-            if (mi == 0) continue;
-            for (int r0 = 0; r0 < m; r0 += MT_ROWS) { jobs.push_back(s); jobs.push_back(r0); }
+    for (int l = 0; l <= F.depth; ++l)
+        for (int v = 0; v < 2; ++v) {
+            F.mj_up_off[2 * l + v] = (int64_t)jobs.size() / 2;
+            for (int s : F.levels[l]) {
+                const int mi = F.m_i(s), m = lowrank(s) ? mi : mi + F.m_b(s);
+                if (mi == 0) continue;
+                const int tr = mapply_tile_rows(m);
+                if ((tr == 32) != (v == 0)) continue;
+                for (int r0 = 0; r0 < m; r0 += tr) { jobs.push_back(s); jobs.push_back(r0); }
+            }
         }
-    }
-    F.mj_up_off[F.depth + 1] = (int64_t)jobs.size() / 2;
-    for (int l = 0; l <= F.depth; ++l) {
-        F.mj_dn_off[l] = (int64_t)jobs.size() / 2;
-        for (int s : F.levels[l]) {
-            const int mi = F.m_i(s);
-            if (mi == 0 || F.m_b(s) == 0 || lowrank(s)) continue;
-            for (int r0 = 0; r0 < mi; r0 += MT_ROWS) { jobs.push_back(s); jobs.push_back(r0); }
+    F.mj_up_off[2 * (F.depth + 1)] = (int64_t)jobs.size() / 2;
+    for (int l = 0; l <= F.depth; ++l)
+        for (int v = 0; v < 2; ++v) {
+            F.mj_dn_off[2 * l + v] = (int64_t)jobs.size() / 2;
+            for (int s : F.levels[l]) {
+                const int mi = F.m_i(s);
+                if (mi == 0 || F.m_b(s) == 0 || lowrank(s)) continue;
+                const int tr = mapply_tile_rows(mi);
+                if ((tr == 32) != (v == 0)) continue;
+                for (int r0 = 0; r0 < mi; r0 += tr) { jobs.push_back(s); jobs.push_back(r0); }
+            }
         }
-    }
-    F.mj_dn_off[F.depth + 1] = (int64_t)jobs.size() / 2;
+    F.mj_dn_off[2 * (F.depth + 1)] = (int64_t)jobs.size() / 2;
     // low-rank tiles: T = X^T u(I), u(B) += RJt T, T = RJt^T z(B), z(I) += X T
     std::vector<int32_t> lj;
     std::vector<int64_t> toff(std::max(F.nnodes, 1), 0);

@@ -290,3 +290,21 @@ def test_gmres_batched_compressed_forest(nd, batch, prec):
             assert S["converged"] and S["true_relres"] <= 1e-8, (s, c, S)
             xs, bs = Xh[c, off[s]:off[s + 1]], Bh[c, off[s]:off[s + 1]]
             assert _rel(xs, lu.solve(bs)) <= 1e-5, (s, c)
+
+
+@pytest.mark.parametrize("tiles", ["32,32,32,32", "32,64,32,64"])
+def test_multi_apply_tile_shapes_agree(nd, batch, tiles, monkeypatch):
+    """Both tile shapes of the 32-column apply (chosen per front-size bucket
+    by the autotuned table, overridden here) give the same result up to the
+    summation order of their K chunks (the same chunks: bit-identical)."""
+    f64 = _factor(nd, batch["tree"], batch["M"], 1)
+    n = batch["A"].shape[0]
+    X = _rand(n, 32, 77)
+    Xd = torch.from_numpy(X).cuda().contiguous()
+    Ya = torch.empty_like(Xd)
+    nd.ndhss_apply_multi(f64, Xd, Ya)
+    monkeypatch.setenv("NDHSS_MAPPLY_TILES", tiles)
+    f32 = _factor(nd, batch["tree"], batch["M"], 1)
+    Yb = torch.empty_like(Xd)
+    nd.ndhss_apply_multi(f32, Xd, Yb)
+    assert torch.equal(Ya, Yb)
