@@ -292,7 +292,7 @@ def test_gmres_batched_compressed_forest(nd, batch, prec):
             assert _rel(xs, lu.solve(bs)) <= 1e-5, (s, c)
 
 
-@pytest.mark.parametrize("tiles", ["32,32,32,32", "32,64,32,64"])
+@pytest.mark.parametrize("tiles", ["64,64,64,64", "32,64,32,64"])
 def test_multi_apply_tile_shapes_agree(nd, batch, tiles, monkeypatch):
     """Both tile shapes of the 32-column apply (chosen per front-size bucket
     by the autotuned table, overridden here) give the same result up to the
