@@ -103,6 +103,48 @@ __device__ __forceinline__ double to_val(float v) { return (double)v; }
 __device__ __forceinline__ c128 to_val(c128 v) { return v; }
 __device__ __forceinline__ c128 to_val(c64 v) { return {(double)v.x, (double)v.y}; }
 
+// Warp-wide maximum of a pivot candidate's key.  The bits of a non-negative
+// float (double) order like its value; key 0 marks "no candidate" (a NaN, or
+// a lane without one), so a NaN never wins, as with a strict comparison
+// against a negative start value.  FP32 keys take one redux.sync; FP64 keys
+// shuffles.
+template <typename R> struct PivKey;
+template <> struct PivKey<float> {
+    using K = unsigned;
+    static __device__ __forceinline__ K of(float v) { return v >= 0.0f ? __float_as_uint(v) + 1u : 0u; }
+    static __device__ __forceinline__ K wmax(K k) { return __reduce_max_sync(0xffffffffu, k); }
+    static __device__ __forceinline__ float val(K k) { return __uint_as_float(k - 1u); }
+};
+template <> struct PivKey<double> {
+    using K = unsigned long long;
+    static __device__ __forceinline__ K of(double v) {
+        return v >= 0.0 ? (unsigned long long)__double_as_longlong(v) + 1ull : 0ull;
+    }
+    static __device__ __forceinline__ K wmax(K k) {
+        for (int o = 16; o; o >>= 1) {
+            const K x = __shfl_xor_sync(0xffffffffu, k, o);
+            k = x > k ? x : k;
+        }
+        return k;
+    }
+    static __device__ __forceinline__ double val(K k) { return __longlong_as_double((long long)(k - 1ull)); }
+};
+
+// The warp's argmax over (value, index) pairs: the largest value, then the
+// lowest index among equal values (the i?amax convention); invalid or NaN
+// entries never win.  Returns the index (INT_MAX when no lane has a
+// candidate) and its value in *best (-1 when none).
+template <typename R>
+__device__ __forceinline__ int warp_argmax(R val, int idx, bool valid, R* best) {
+    using PK = PivKey<R>;
+    using K = typename PK::K;
+    const K key = valid ? PK::of(val) : K(0);
+    const K kmax = PK::wmax(key);
+    const unsigned imin = __reduce_min_sync(0xffffffffu, (kmax != K(0) && key == kmax) ? (unsigned)idx : 0xffffffffu);
+    *best = kmax != K(0) ? PK::val(kmax) : R(-1);
+    return kmax != K(0) ? (int)imin : 0x7fffffff;
+}
+
 // Device status word written by kernels that detect a numerical failure.
 struct DevStatus {
     int32_t code;

@@ -22,6 +22,8 @@
 #include <algorithm>
 #include <climits>
 #include <cmath>
+#include <cstdlib>
+#include <cstring>
 
 #include "factor.cuh"
 
@@ -103,6 +105,26 @@ __global__ void scatter_entries_kernel(const int32_t* __restrict__ lev, const in
         F[(int64_t)e_col[e] * m + e_row[e]] += from_val<T>(vals[e_idx[e]]);
 }
 
+// -0 in every component: the exact additive identity (x + -0 = x, also for x = +0)
+template <typename T> __device__ __forceinline__ T neg_zero();
+template <> __device__ __forceinline__ float neg_zero<float>() { return -0.0f; }
+template <> __device__ __forceinline__ double neg_zero<double>() { return -0.0; }
+template <> __device__ __forceinline__ c64 neg_zero<c64>() { return {-0.0f, -0.0f}; }
+
+// r = v when i == j, by a predicated move: a plain select on a runtime
+// column index lets the compiler turn the row's registers into a
+// local-memory array with an indexed load
+__device__ __forceinline__ void take_if(int j, int i, float v, float& r) {
+    asm("{\n\t.reg .pred q;\n\tsetp.eq.s32 q, %1, %2;\n\t@q mov.f32 %0, %3;\n\t}" : "+f"(r) : "r"(i), "r"(j), "f"(v));
+}
+__device__ __forceinline__ void take_if(int j, int i, double v, double& r) {
+    asm("{\n\t.reg .pred q;\n\tsetp.eq.s32 q, %1, %2;\n\t@q mov.f64 %0, %3;\n\t}" : "+d"(r) : "r"(i), "r"(j), "d"(v));
+}
+__device__ __forceinline__ void take_if(int j, int i, c64 v, c64& r) {
+    asm("{\n\t.reg .pred q;\n\tsetp.eq.s32 q, %2, %3;\n\t@q mov.f32 %0, %4;\n\t@q mov.f32 %1, %5;\n\t}"
+        : "+f"(r.x), "+f"(r.y) : "r"(i), "r"(j), "f"(v.x), "f"(v.y));
+}
+
 // ---------------------------------------------------------------- panel
 // One CTA per front.  The candidate rows [k0, m_i) of the kb panel columns
 // are swept in shared memory with the in-place Gauss-Jordan exchange step
@@ -135,9 +157,24 @@ panel_factor_kernel(const int32_t* __restrict__ lev, const int32_t* __restrict__
     T* P = reinterpret_cast<T*>(smem_raw);                       // mc x kbp, ld mc
     int* idx = reinterpret_cast<int*>(P + (size_t)mc * kbp);     // row arrangement, mc
     const T* F = front + foff[s];
-    for (int q = tid; q < mc * kbp; q += blockDim.x) {
-        const int r = q % mc, c = q / mc;
-        P[q] = F[(int64_t)(k0 + c) * m + k0 + r];
+    {
+        // eight loads in flight per thread (a panel of the root front is ~200 KB:
+        // one load-store pair at a time waits out the memory latency ~50 times)
+        constexpr int LB = 8;
+        const int tot = mc * kbp;
+        for (int q0 = tid; q0 < tot; q0 += LB * blockDim.x) {
+            T tmp[LB];
+#pragma unroll
+            for (int u = 0; u < LB; ++u) {
+                const int q = q0 + u * blockDim.x;
+                if (q < tot) tmp[u] = F[(int64_t)(k0 + q / mc) * m + k0 + q % mc];
+            }
+#pragma unroll
+            for (int u = 0; u < LB; ++u) {
+                const int q = q0 + u * blockDim.x;
+                if (q < tot) P[q] = tmp[u];
+            }
+        }
     }
     for (int r = tid; r < mc; r += blockDim.x) idx[r] = r;
     if (tid == 0) s_na = 0;
@@ -246,6 +283,130 @@ panel_factor_kernel(const int32_t* __restrict__ lev, const int32_t* __restrict__
             sm[1 + a] = k0 + r;
             sm[1 + 2 * KBMAX + a] = k0 + idx[r];
         }
+    }
+    __syncthreads();
+    if (tid == 0) sm[0] = s_na;
+}
+
+// The warp's best pivot candidate (largest key, then lowest position): its
+// key and position to key / pos (lane 0), its row to cand (the winning lane).
+template <typename T, int KB>
+__device__ __forceinline__ void panel_publish(const T (&v)[KB], typename Tr<T>::real val, bool cand, int pos, T* cand_row,
+                                              typename PivKey<typename Tr<T>::real>::K* key_out, int* pos_out, int lane) {
+    using PK = PivKey<typename Tr<T>::real>;
+    using K = typename PK::K;
+    const K key = cand ? PK::of(val) : K(0);
+    const K kmax = PK::wmax(key);
+    const unsigned pmin = __reduce_min_sync(0xffffffffu, (kmax != K(0) && key == kmax) ? (unsigned)pos : 0xffffffffu);
+    if (kmax != K(0) && (unsigned)pos == pmin) {
+#pragma unroll
+        for (int j = 0; j < KB; ++j) cand_row[j] = v[j];
+    }
+    if (lane == 0) {
+        *key_out = kmax;
+        *pos_out = (int)pmin;
+    }
+}
+
+// The panel of panel_factor_kernel with every candidate row in the
+// registers of one thread (fronts with at most PANEL_THREADS candidate rows,
+// elements of at most 8 bytes).  Rows are never moved: each thread tracks
+// the position its row would hold after the interchanges, so pivots, ties
+// (lowest position first) and the exchange arithmetic are those of the
+// shared-memory kernel, and so are the outputs.  A pivot costs one barrier:
+// at the end of a step every warp publishes its best candidate for the next
+// column together with that row's values (double-buffered by step parity);
+// after the barrier every warp picks the winner and forms the pivot row
+// itself (lane j: entry j), then each thread updates its own row.
+template <typename T, int KB>
+__global__ void __launch_bounds__(PANEL_THREADS)
+panel_reg_kernel(const int32_t* __restrict__ lev, const int32_t* __restrict__ node,
+                 const int64_t* __restrict__ foff, const T* __restrict__ front, int32_t* __restrict__ ipiv,
+                 T* __restrict__ ainv_buf, int32_t* __restrict__ swapmap, int k0, int kb, DevStatus* status) {
+    using real = typename Tr<T>::real;
+    using PK = PivKey<real>;
+    using K = typename PK::K;
+    constexpr int NW = PANEL_THREADS / 32;
+    static_assert(KB <= 32, "one lane per pivot-row entry");
+    __shared__ T s_cand[2][NW][KB];          // each warp's best candidate row
+    __shared__ K s_key[2][NW];
+    __shared__ int s_pos[2][NW];
+    __shared__ T s_pr[NW][KB];               // the pivot row, formed by each warp for itself
+    __shared__ int s_na;
+    const int s = lev[blockIdx.x];
+    const int m_i = nf(node, s, 5);
+    if (k0 >= m_i) return;
+    const int64_t m = m_i + nf(node, s, 7);
+    const int kbp = min(kb, m_i - k0);
+    const int mc = m_i - k0;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
+    const bool has = tid < mc;
+    const T* F = front + foff[s];
+    T v[KB];
+#pragma unroll
+    for (int j = 0; j < KB; ++j) v[j] = (has && j < kbp) ? F[(int64_t)(k0 + j) * m + k0 + tid] : zero<T>();
+    int pos = tid;                           // this row's position after the interchanges so far
+    if (tid == 0) s_na = 0;
+    panel_publish<T, KB>(v, abs1(v[0]), has, pos, s_cand[0][warp], &s_key[0][warp], &s_pos[0][warp], lane);
+    __syncthreads();
+    int32_t* ip = ipiv + nf(node, s, 4) + k0;
+    T a = v[0];                              // this row's entry in the pivot column
+    for (int c = 0; c < kbp; ++c) {
+        const int par = c & 1;
+        const K kw = lane < nwarps ? s_key[par][lane] : K(0);
+        const K kmax = PK::wmax(kw);
+        const unsigned pw = __reduce_min_sync(
+            0xffffffffu, (lane < nwarps && kmax != K(0) && kw == kmax) ? ((unsigned)s_pos[par][lane] << 5) | (unsigned)lane
+                                                                        : 0xffffffffu);
+        // all candidates NaN: keep the diagonal (its pivot is then flagged below)
+        const int p = kmax != K(0) ? (int)(pw >> 5) : c;
+        const int w = kmax != K(0) ? (int)(pw & 31u) : -1;
+        if (lane < KB) {
+            T piv = w >= 0 ? s_cand[par][w][c] : zero<T>();
+            if (!(abs1(piv) > real(0))) {                         // exact zero (or NaN) pivot
+                piv = one<T>();
+                if (tid == 0 && atomicCAS(&status->code, 0, (int)NDHSS_ERR_SINGULAR) == 0) status->node = s;
+            }
+            const T pinv = recip(piv);
+            const T b = w >= 0 ? s_cand[par][w][lane] : zero<T>();
+            s_pr[warp][lane] = lane >= kbp ? zero<T>() : (lane == c) ? pinv : -(b * pinv);
+        }
+        if (tid == 0) ip[c] = k0 + p;
+        __syncwarp();
+        const bool is_piv = has && pos == p;
+        // one FMA form for every entry: the pivot column's entry becomes
+        // a * pr(c) and the pivot row becomes pr; both are fmac with the
+        // addend -0 (x + -0 = x exactly), the pivot row with multiplier one
+        const T am = is_piv ? one<T>() : a;
+        T an = a;                            // this row's updated entry in the next column
+#pragma unroll
+        for (int j = 0; j < KB; ++j) {
+            const T prj = s_pr[warp][j];
+            const T vin = (is_piv || j == c) ? neg_zero<T>() : v[j];
+            v[j] = fmac(am, prj, vin);
+            take_if(j, c + 1, v[j], an);
+        }
+        a = an;
+        if (pos == c) pos = p;
+        else if (pos == p) pos = c;
+        if (c + 1 < kbp)
+            panel_publish<T, KB>(v, abs1(a), has && pos > c, pos, s_cand[par ^ 1][warp], &s_key[par ^ 1][warp],
+                                 &s_pos[par ^ 1][warp], lane);
+        __syncthreads();
+    }
+    // rows at positions < kbp hold (A_PP)^{-1} of the interchanged pivot block
+    T* Ai = ainv_buf + (size_t)blockIdx.x * KBMAX * KBMAX;
+    if (has && pos < kbp) {
+#pragma unroll
+        for (int j = 0; j < KB; ++j)
+            if (j < kbp) Ai[j * KBMAX + pos] = v[j];
+    }
+    // net row map of the interchanges: position k0 + pos receives the old row k0 + tid
+    int32_t* sm = swapmap + (size_t)blockIdx.x * (4 * KBMAX + 1);
+    if (has && pos != tid) {
+        const int a = atomicAdd(&s_na, 1);
+        sm[1 + a] = k0 + pos;
+        sm[1 + 2 * KBMAX + a] = k0 + tid;
     }
     __syncthreads();
     if (tid == 0) sm[0] = s_na;
@@ -409,6 +570,21 @@ __global__ void finalize_sigma_kernel(const int32_t* __restrict__ lev, const int
     for (int j = threadIdx.x; j < m_i; j += blockDim.x) sigma[i_off + j] = a[j];
 }
 
+// One panel launch: the register-resident kernel when asked and the element
+// fits (8 bytes at most), else the shared-memory kernel.
+template <typename T, int KB>
+void launch_panel(bool reg, int grid, int threads, size_t smem, cudaStream_t st, const int32_t* lev,
+                  const int32_t* node, const int64_t* foff, const T* front, int32_t* ipiv, T* ainv, int32_t* swapmap,
+                  int k0, int kb, DevStatus* status) {
+    if constexpr (sizeof(T) <= 8) {
+        if (reg) {
+            panel_reg_kernel<T, KB><<<grid, threads, 0, st>>>(lev, node, foff, front, ipiv, ainv, swapmap, k0, kb, status);
+            return;
+        }
+    }
+    panel_factor_kernel<T, KB><<<grid, threads, smem, st>>>(lev, node, foff, front, ipiv, ainv, swapmap, k0, kb, status);
+}
+
 int choose_kb(int64_t mc, size_t esize, int panel_opt) {
     int kb = KBMAX;
     while (kb > 1 && (size_t)mc * (kb * esize + sizeof(int)) > PANEL_SMEM_MAX) kb >>= 1;
@@ -500,6 +676,10 @@ ndhss_status factor_run(FactorData& F, const Tree& t, const V* d_vals, const int
                         T* d_ainv, int32_t* d_swapmap, DevStatus* d_status, const ndhss_factor_opts& o,
                         LaunchTimer& tm, cudaStream_t st) {
     const int panel_opt = o.panel;
+    // NDHSS_PANEL=smem keeps every panel in shared memory (panel_factor_kernel;
+    // a cross-check of the register-resident panel, which gives the same outputs)
+    const char* pe = std::getenv("NDHSS_PANEL");
+    const bool reg_panel_ok = sizeof(T) <= 8 && !(pe && std::strcmp(pe, "smem") == 0);
     ndhss_status rc = set_smem_attrs<T>();
     if (rc != NDHSS_OK) return rc;
     T* front = static_cast<T*>(F.d_front);
@@ -580,6 +760,8 @@ ndhss_status factor_run(FactorData& F, const Tree& t, const V* d_vals, const int
             // one thread per candidate row up to 512: small fronts get small CTAs, so a level of
             // thousands of leaves runs in one wave instead of repeating its pivot chain per wave
             const int pthreads = (int)std::min<int64_t>(PANEL_THREADS, std::max<int64_t>(64, (mimax - k0 + 31) / 32 * 32));
+            // every candidate row in one thread's registers when the rows fit one CTA
+            const bool reg_panel = reg_panel_ok && mimax - k0 <= PANEL_THREADS;
             // a level of more than 65535 fronts (the grid's y / z limit) goes in
             // chunks; the three kernels of a chunk share its per-front scratch
             for (int c0 = 0; c0 < L; c0 += MAX_GRID_YZ) {
@@ -590,8 +772,8 @@ ndhss_status factor_run(FactorData& F, const Tree& t, const V* d_vals, const int
                 switch (kb) {
 #define NDHSS_PANEL(KBV)                                                                                          \
     case KBV:                                                                                                   \
-        panel_factor_kernel<T, KBV><<<Lc, pthreads, smem, st>>>(levc, F.d_node, F.d_foff, front, F.d_ipiv, d_ainv, \
-                                                                d_swapmap, (int)k0, kb, d_status);            \
+        launch_panel<T, KBV>(reg_panel, Lc, pthreads, smem, st, levc, F.d_node, F.d_foff, front, F.d_ipiv, d_ainv, \
+                             d_swapmap, (int)k0, kb, d_status);                                                 \
         break;
                     NDHSS_PANEL(1) NDHSS_PANEL(2) NDHSS_PANEL(4) NDHSS_PANEL(8) NDHSS_PANEL(16) NDHSS_PANEL(32)
 #undef NDHSS_PANEL

@@ -664,8 +664,7 @@ row_id_cluster_kernel(const int* __restrict__ list, const HNode* __restrict__ no
     const int seg = lane / lpc, sl = lane % lpc;
     extern __shared__ __align__(16) unsigned char smem[];
     T* Ws = reinterpret_cast<T*>(smem);          // nloc columns of W, ld lds
-    T* vsh = Ws + (size_t)lds * chunk;           // pivot column (p)
-    unsigned char* used = reinterpret_cast<unsigned char*>(vsh + p + 1);
+    unsigned char* used = reinterpret_cast<unsigned char*>(Ws + (size_t)lds * chunk + p + 1);
     __shared__ real s_cv[2][RID_NW];
     __shared__ int s_ci[2][RID_NW];
     __shared__ T s_beta[RID_KMAX];
@@ -679,12 +678,9 @@ row_id_cluster_kernel(const int* __restrict__ list, const HNode* __restrict__ no
     __syncthreads();
     // the warp's best candidate (squared norm, row) over its segments, to s_cv/s_ci[par]
     auto publish = [&](real best, int nb, int par) {
-        for (int o = 16; o >= lpc; o >>= 1) {
-            const real ov = __shfl_xor_sync(0xffffffffu, best, o);
-            const int oi = __shfl_xor_sync(0xffffffffu, nb, o);
-            if (ov > best || (ov == best && oi < nb)) { best = ov; nb = oi; }
-        }
-        if (lane == 0) { s_cv[par][warp] = best; s_ci[par][warp] = nb; }
+        real wv;
+        const int wi = warp_argmax(best, nb, nb != INT_MAX, &wv);
+        if (lane == 0) { s_cv[par][warp] = wv; s_ci[par][warp] = wi; }
     };
     {
         real best = real(-1);
@@ -724,25 +720,25 @@ row_id_cluster_kernel(const int* __restrict__ list, const HNode* __restrict__ no
             }
             if (v > bv || (v == bv && i < bi)) { bv = v; bi = i; }
         }
-        for (int o = 16; o; o >>= 1) {
-            const real ov = __shfl_xor_sync(0xffffffffu, bv, o);
-            const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-            if (ov > bv || (ov == bv && oi < bi)) { bv = ov; bi = oi; }
+        {
+            real gv;
+            bi = warp_argmax(bv, bi, bi != INT_MAX, &gv);
+            bv = gv;
         }
         const real xn = sqrt(bv > real(0) ? bv : real(0));
         if (t == 0) r11 = xn;
         if (t >= kmax || bi == INT_MAX || !(xn > reps * r11)) break;
         const int cb = bi, owner = cb / chunk;
+        // the pivot column, read in place by every thread (local or through
+        // distributed shared memory): no step writes it from here on
         const T* src = (owner == rk) ? Ws + (size_t)(cb - c_lo) * lds
                                      : cl.map_shared_rank(Ws, owner) + (size_t)(cb - owner * chunk) * lds;
-        for (int j = t + tid; j < p; j += RID_THREADS) vsh[j] = src[j];
         if (tid == 0) {
             s_order[t] = cb;
-            if (owner == rk) used[cb - c_lo] = 1;
+            if (owner == rk) used[cb - c_lo] = 1;    // read from the next step on (after its barrier)
         }
-        __syncthreads();
         // reflector v = x - beta e_t of the pivot column x, beta = -phase(x_t) ||x||
-        const T a0 = vsh[t];
+        const T a0 = src[t];
         const real aa2 = nrm2r(a0), aa = sqrt(aa2);
         T ph = one<T>();
         if (aa > real(0)) ph = scale(a0, real(1) / aa);
@@ -755,13 +751,13 @@ row_id_cluster_kernel(const int* __restrict__ list, const HNode* __restrict__ no
 #pragma unroll
         for (int q = 0; q < CH; ++q) {
             const int j = t + sl + lpc * q;
-            vl[q] = (j < p) ? (j == t ? v0 : vsh[j]) : zero<T>();
+            vl[q] = (j < p) ? (j == t ? v0 : src[j]) : zero<T>();
         }
         real best = real(-1);
         int nb = INT_MAX;
         for (int c0 = warp * spw; c0 < nloc; c0 += RID_NW * spw) {
             const int c = c0 + seg;
-            const bool act = c < nloc && !used[c];
+            const bool act = c < nloc && !used[c] && c_lo + c != cb;
             T* col = Ws + (size_t)(act ? c : 0) * lds;
             T cv[CH];
             T w = zero<T>();

@@ -158,6 +158,34 @@ def test_tensor_core_sweep_matches_rank_kb_sweep(nd, case, prec, monkeypatch):
             assert _rel(a, b) <= (1e-3 if w == 0 else 1e-4), (s, w, _rel(a, b))
 
 
+@pytest.mark.parametrize("prec", [0, 1])
+def test_register_panel_matches_shared_memory_panel(nd, case, prec, monkeypatch):
+    """Panels of at most 512 candidate rows with elements of at most 8 bytes
+    run with each row in one thread's registers, tracking positions instead
+    of moving rows.  Pivots, ties and the exchange arithmetic are those of
+    the shared-memory panel (NDHSS_PANEL=smem): real factors agree bit for
+    bit.  Complex products may be contracted into FMAs differently in the
+    two kernels (measured: one FP32 ulp, 7.7e-8 relative), checked at 1e-6;
+    complex FP64 takes the shared-memory panel both times."""
+    fa = _gpu_factor(nd, case, prec)
+    monkeypatch.setenv("NDHSS_PANEL", "smem")
+    fb = _gpu_factor(nd, case, prec)
+    T = case["T"]
+    mi_all, mb_all = T.f("m_i"), T.f("m_b")
+    nodes = [s for s in range(T.nnodes) if mi_all[s] > 0]
+    if len(nodes) > 80:
+        nodes = nodes[:: len(nodes) // 80] + [T.nnodes - 1]
+    for s in nodes:
+        mi, mb = int(mi_all[s]), int(mb_all[s])
+        for w in range(4 if mb else 1):
+            a = nd.ndhss_factor_get_block(fa, s, w, mi, mb)
+            b = nd.ndhss_factor_get_block(fb, s, w, mi, mb)
+            if np.iscomplexobj(a):
+                assert _rel(a, b) <= 1e-6, (s, w, _rel(a, b))
+            else:
+                assert np.array_equal(a, b), (s, w, _rel(a, b))
+
+
 def test_spmv_matches_scipy(nd, case):
     P, M = case["P"], case["M"]
     rng = np.random.default_rng(7)
