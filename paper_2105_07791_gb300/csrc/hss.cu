@@ -152,6 +152,16 @@ __global__ void gauss_kernel(const GaussJob* __restrict__ jobs, uint64_t seed) {
     }
 }
 
+// c + a * b for a complex a and a real b (the products of a complex block
+// with a real Gaussian sample matrix): the values of fmac with b's imaginary
+// part zero, in two FMAs instead of four
+template <typename R>
+__device__ __forceinline__ Cx<R> fmar(Cx<R> a, R b, Cx<R> c) {
+    c.x = fma(a.x, b, c.x);
+    c.y = fma(a.y, b, c.y);
+    return c;
+}
+
 // ------------------------------------------------------- batched GEMM
 // C = (beta ? C : 0) + alpha * A * B, column-major, A M x K, B K x N.
 struct GemmJob {
@@ -162,6 +172,7 @@ struct GemmJob {
     int M, N, K, beta;
     double alpha;
     int transA = 0, transB = 0;   // operand stored transposed (plain transpose, no conjugation)
+    int realB = 0;                // complex T: B holds real values (zero imaginary parts); 2 FMAs per product
 };
 
 // 64 x 64 tiles of every job; blockIdx.z = job * ksplit + split.  The K
@@ -170,7 +181,7 @@ struct GemmJob {
 // takes K chunks q, q + ksplit, ... and writes its raw partial tile to
 // part[(z * tiles + tile) * 4096]; bgemm_reduce_kernel adds the partials in
 // split order (deterministic) and applies alpha / beta.
-template <typename T>
+template <typename T, bool RB>
 __global__ void __launch_bounds__(256) bgemm_kernel(const GemmJob* __restrict__ jobs, int ksplit, T* __restrict__ part) {
     constexpr int TT = 64, TK = 16;
     __shared__ T sA[TK][TT];
@@ -232,7 +243,10 @@ __global__ void __launch_bounds__(256) bgemm_kernel(const GemmJob* __restrict__ 
 #pragma unroll
             for (int a = 0; a < 4; ++a)
 #pragma unroll
-                for (int b = 0; b < 4; ++b) acc[a][b] = fmac(av[a], bv[b], acc[a][b]);
+                for (int b = 0; b < 4; ++b) {
+                    if constexpr (RB && Tr<T>::cplx) acc[a][b] = fmar(av[a], bv[b].x, acc[a][b]);
+                    else acc[a][b] = fmac(av[a], bv[b], acc[a][b]);
+                }
         }
         __syncthreads();
     }
@@ -1148,8 +1162,8 @@ struct DeviceVec {
 // The batched GEMM of a job list: one launch of 64 x 64 tiles, or, when the
 // tiles of all jobs leave the GPU mostly idle and K is long, K split over
 // ksplit CTAs per tile plus an ordered reduction of their partials.
-template <typename T>
-ndhss_status run_bgemm(const std::vector<GemmJob>& jobs, cudaStream_t st) {
+template <typename T, bool RB>
+ndhss_status run_bgemm_group(const std::vector<GemmJob>& jobs, cudaStream_t st) {
     if (jobs.empty()) return NDHSS_OK;
     int maxM = 1, maxN = 1, maxK = 1;
     for (const GemmJob& g : jobs) {
@@ -1173,7 +1187,7 @@ ndhss_status run_bgemm(const std::vector<GemmJob>& jobs, cudaStream_t st) {
     if (ks > 1) HSS_TRY(part.alloc((size_t)std::min(per, jobs.size()) * ks * tm * tn * 4096));
     for (size_t j0 = 0; j0 < jobs.size(); j0 += per) {
         const unsigned nj = (unsigned)std::min(per, jobs.size() - j0);
-        bgemm_kernel<T><<<dim3(tm, tn, nj * ks), 256, 0, st>>>(dj.p + j0, ks, part.p);
+        bgemm_kernel<T, RB><<<dim3(tm, tn, nj * ks), 256, 0, st>>>(dj.p + j0, ks, part.p);
         NDHSS_LAUNCH_CHECK("bgemm_kernel");
         if (ks > 1) {
             bgemm_reduce_kernel<T><<<dim3(tm, tn, nj), 256, 0, st>>>(dj.p + j0, ks, part.p);
@@ -1181,6 +1195,17 @@ ndhss_status run_bgemm(const std::vector<GemmJob>& jobs, cudaStream_t st) {
         }
     }
     return NDHSS_OK;
+}
+
+// Jobs with a real B (complex T) take the two-FMA products; the rest the
+// full complex ones.
+template <typename T>
+ndhss_status run_bgemm(const std::vector<GemmJob>& jobs, cudaStream_t st) {
+    std::vector<GemmJob> gr, gc;
+    for (const GemmJob& g : jobs) ((Tr<T>::cplx && g.realB) ? gr : gc).push_back(g);
+    ndhss_status rc = run_bgemm_group<T, true>(gr, st);
+    if (rc == NDHSS_OK) rc = run_bgemm_group<T, false>(gc, st);
+    return rc;
 }
 
 
@@ -1490,10 +1515,13 @@ ndhss_status compress_problems(std::vector<Problem>& probs, bool lowrank, const 
         std::vector<int64_t> o_om(nf), o_y(nf), o_ot(nf), o_yt(nf), o_zt(nf), o_t1(nf), o_rj(nf);
         for (int i = 0; i < nf; ++i) {
             const int64_t n = fr[i].n, nc = fr[i].ncol;
-            o_om[i] = take((lowrank ? nc : n) * p);
-            o_y[i] = take(n * p);
-            o_ot[i] = take((lowrank ? nc : n) * r);
-            o_yt[i] = take(n * r);
+            // [Omega | Omega~] and [Y | Y~] side by side (same leading dimension):
+            // one product per block gives both
+            const int64_t ro = lowrank ? nc : n;
+            o_om[i] = take(ro * (p + r));
+            o_ot[i] = o_om[i] + ro * p;
+            o_y[i] = take(n * (p + r));
+            o_yt[i] = o_y[i] + n * p;
             o_zt[i] = take(n * r);
             o_t1[i] = take((int64_t)kcap * r);
             o_rj[i] = take((int64_t)kcap * nc);
@@ -1543,8 +1571,9 @@ ndhss_status compress_problems(std::vector<Problem>& probs, bool lowrank, const 
         for (int i = 0; i < nf; ++i) {
             const Problem& pb = probs[active[i]];
             const int K = lowrank ? pb.ncol : pb.n;
-            gm.push_back({pb.ptr, fr[i].Om, fr[i].Y, pb.lds, K, pb.n, pb.n, p, K, 0, 1.0});
-            gm.push_back({pb.ptr, fr[i].Ot, fr[i].Yt, pb.lds, K, pb.n, pb.n, r, K, 0, 1.0});
+            GemmJob g{pb.ptr, fr[i].Om, fr[i].Y, pb.lds, K, pb.n, pb.n, p + r, K, 0, 1.0};
+            g.realB = 1;
+            gm.push_back(g);
             maxM = std::max(maxM, pb.n);
             maxN = std::max(maxN, p);
         }
@@ -1671,6 +1700,7 @@ ndhss_status compress_problems(std::vector<Problem>& probs, bool lowrank, const 
                 const int k = hk[fr[i].root];
                 const HNode& nd = nodes[fr[i].root];
                 g2.push_back({fr[i].RJ, fr[i].Ot, fr[i].T1, kcap, fr[i].ncol, kcap, k, r, fr[i].ncol, 0, 1.0});
+                g2.back().realB = 1;
                 g3.push_back({ws.p + nd.o_x, fr[i].T1, fr[i].Zt, nd.rows_cap, kcap, fr[i].n, fr[i].n, r, k, 0, 1.0});
             }
             {
