@@ -22,6 +22,8 @@
 #include <climits>
 #include <cstdlib>
 #include <cmath>
+#include <memory>
+#include <mutex>
 #include <vector>
 
 #include <cooperative_groups.h>
@@ -1152,6 +1154,70 @@ struct DeviceVec {
     }
 };
 
+// Independent launches of one step on side streams: forked from the
+// caller's stream st by an event, each joined back to st by its own event,
+// so everything after the join stays ordered on st.  Without side launches
+// (n == 0) every stream() is st itself.  The side streams are created once
+// per device and kept (four, shared by all callers: sharing only orders
+// their launches more strictly).
+struct SideFork {
+    static constexpr int NS = 4;
+    cudaStream_t st;
+    int n;
+    cudaError_t status = cudaSuccess;
+    cudaEvent_t fork_ev = nullptr;
+    std::vector<cudaEvent_t> done;
+    cudaStream_t side[NS] = {};
+    SideFork(cudaStream_t s, int count) : st(s), n(std::min(count, NS)) {
+        if (n <= 1) { n = 0; return; }
+        static std::mutex mu;
+        static cudaStream_t pool[64][NS];
+        static bool made[64] = {};
+        int dev = 0;
+        if ((status = cudaGetDevice(&dev)) != cudaSuccess) { n = 0; return; }
+        {
+            std::lock_guard<std::mutex> lk(mu);
+            if (!made[dev & 63]) {
+                for (int i = 0; i < NS && status == cudaSuccess; ++i)
+                    status = cudaStreamCreateWithFlags(&pool[dev & 63][i], cudaStreamNonBlocking);
+                if (status != cudaSuccess) { n = 0; return; }
+                made[dev & 63] = true;
+            }
+            for (int i = 0; i < NS; ++i) side[i] = pool[dev & 63][i];
+        }
+        if ((status = cudaEventCreateWithFlags(&fork_ev, cudaEventDisableTiming)) != cudaSuccess) { n = 0; return; }
+        status = cudaEventRecord(fork_ev, st);
+        done.assign(n, nullptr);
+    }
+    // launch i goes to stream(i); call start(i) after its inputs are enqueued on st
+    cudaStream_t stream(int i) const { return n ? side[i % NS] : st; }
+    cudaError_t start(int i) {
+        if (!n) return cudaSuccess;
+        // the fork event was recorded before this launch's inputs: re-record it
+        cudaError_t e = cudaEventRecord(fork_ev, st);
+        return e == cudaSuccess ? cudaStreamWaitEvent(stream(i), fork_ev, 0) : e;
+    }
+    cudaError_t finish(int i) {
+        if (!n) return cudaSuccess;
+        cudaError_t e = cudaSuccess;
+        if (!done[i % n]) e = cudaEventCreateWithFlags(&done[i % n], cudaEventDisableTiming);
+        return e == cudaSuccess ? cudaEventRecord(done[i % n], stream(i)) : e;
+    }
+    cudaError_t join() {
+        for (cudaEvent_t ev : done) {
+            if (!ev) continue;
+            cudaError_t e = cudaStreamWaitEvent(st, ev, 0);
+            if (e != cudaSuccess) return e;
+        }
+        return cudaSuccess;
+    }
+    ~SideFork() {
+        if (fork_ev) cudaEventDestroy(fork_ev);
+        for (cudaEvent_t ev : done)
+            if (ev) cudaEventDestroy(ev);
+    }
+};
+
 #define HSS_TRY(expr)                                                                                      \
     do {                                                                                                   \
         cudaError_t e_ = (expr);                                                                           \
@@ -1613,14 +1679,29 @@ ndhss_status compress_problems(std::vector<Problem>& probs, bool lowrank, const 
         HSS_TRY(cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev));
         auto launch_row_id = [&](size_t b, size_t e) -> ndhss_status {
             std::vector<int> grp[5], big;
-            // a launch of few nodes also splits a node whose share would exceed
-            // RID_SPLIT_COLS columns per CTA (the pivot steps then run shorter)
-            const bool few = (e - b) * 2 <= (size_t)num_sms;
-            for (size_t q = b; q < e; ++q) {
-                const int rc = nodes[flat[q]].rows_cap;
+            // a node whose share would exceed RID_SPLIT_COLS columns per CTA is
+            // split further (its pivot steps run shorter) when all such nodes
+            // together take at most two CTAs per SM: the launch lasts as long
+            // as its longest pivot chain
+            auto g_fit = [&](int rc) {
                 int g = 0;
                 while ((1 << g) <= RID_MAX_CLUSTER && rid_bytes(rc, 1 << g) > RID_SMEM) ++g;
-                while (few && (1 << g) < RID_MAX_CLUSTER && (rc + (1 << g) - 1) / (1 << g) > RID_SPLIT_COLS) ++g;
+                return g;
+            };
+            auto g_split = [&](int rc, int g) {
+                while ((1 << g) < RID_MAX_CLUSTER && (rc + (1 << g) - 1) / (1 << g) > RID_SPLIT_COLS) ++g;
+                return g;
+            };
+            int64_t split_ctas = 0;
+            for (size_t q = b; q < e; ++q) {
+                const int rc = nodes[flat[q]].rows_cap, g0 = g_fit(rc);
+                if (g0 > 0 || g_split(rc, g0) > g0) split_ctas += (int64_t)1 << g_split(rc, g0);
+            }
+            const bool split = split_ctas <= 2 * (int64_t)num_sms;
+            for (size_t q = b; q < e; ++q) {
+                const int rc = nodes[flat[q]].rows_cap;
+                int g = g_fit(rc);
+                if (split && (1 << g) <= RID_MAX_CLUSTER) g = g_split(rc, g);
                 ((1 << g) <= RID_MAX_CLUSTER ? grp[g] : big).push_back(flat[q]);
             }
             // a cluster shape the device cannot co-schedule falls back to global memory
@@ -1644,23 +1725,34 @@ ndhss_status compress_problems(std::vector<Problem>& probs, bool lowrank, const 
                     grp[g].clear();
                 }
             }
+            // the launches of different cluster shapes are independent: with more
+            // than one, each runs on a side stream forked from st and joined back
+            int nlaunch = big.empty() ? 0 : 1;
+            for (int g = 0; (1 << g) <= RID_MAX_CLUSTER; ++g) nlaunch += grp[g].empty() ? 0 : 1;
+            SideFork fork(st, nlaunch > 1 ? nlaunch : 0);
+            HSS_TRY(fork.status);
+            std::vector<std::unique_ptr<DeviceVec<int>>> lists;
+            int li = 0;
             for (int g = 0; (1 << g) <= RID_MAX_CLUSTER; ++g) {
                 if (grp[g].empty()) continue;
                 const int C = 1 << g;
+                cudaStream_t ls = fork.stream(li++);
                 int rcmax = 1;
                 for (int id : grp[g]) rcmax = std::max(rcmax, nodes[id].rows_cap);
-                DeviceVec<int> dl(st);
+                lists.emplace_back(new DeviceVec<int>(st));
+                DeviceVec<int>& dl = *lists.back();
                 HSS_TRY(dl.upload(grp[g], st));
+                HSS_TRY(fork.start(li - 1));
                 const size_t sm = rid_bytes(rcmax, C);
                 if (C == 1) {
-                    row_id_cluster_kernel<T><<<(unsigned)grp[g].size(), RID_THREADS, sm, st>>>(dl.p, dnodes.p, ws.p, iws.p,
+                    row_id_cluster_kernel<T><<<(unsigned)grp[g].size(), RID_THREADS, sm, ls>>>(dl.p, dnodes.p, ws.p, iws.p,
                                                                                               kk.p, rows.p, eps, rank_cap);
                 } else {
                     cudaLaunchConfig_t cfg{};
                     cfg.gridDim = dim3((unsigned)(grp[g].size() * C));
                     cfg.blockDim = dim3(RID_THREADS);
                     cfg.dynamicSmemBytes = sm;
-                    cfg.stream = st;
+                    cfg.stream = ls;
                     cudaLaunchAttribute at[1];
                     at[0].id = cudaLaunchAttributeClusterDimension;
                     at[0].val.clusterDim.x = (unsigned)C;
@@ -1672,14 +1764,21 @@ ndhss_status compress_problems(std::vector<Problem>& probs, bool lowrank, const 
                                                ws.p, iws.p, kk.p, (const int*)rows.p, eps, rank_cap));
                 }
                 NDHSS_LAUNCH_CHECK("row_id_cluster_kernel");
+                HSS_TRY(fork.finish(li - 1));
             }
             if (!big.empty()) {
-                DeviceVec<int> dl(st);
+                cudaStream_t ls = fork.stream(li++);
+                lists.emplace_back(new DeviceVec<int>(st));
+                DeviceVec<int>& dl = *lists.back();
                 HSS_TRY(dl.upload(big, st));
-                row_id_kernel<T><<<(unsigned)big.size(), 512, smem_base, st>>>(dl.p, dnodes.p, ws.p, iws.p, kk.p, rows.p,
+                HSS_TRY(fork.start(li - 1));
+                row_id_kernel<T><<<(unsigned)big.size(), 512, smem_base, ls>>>(dl.p, dnodes.p, ws.p, iws.p, kk.p, rows.p,
                                                                                 eps, rank_cap, 0);
                 NDHSS_LAUNCH_CHECK("row_id_kernel");
+                HSS_TRY(fork.finish(li - 1));
             }
+            // st waits for every side launch before the node lists are freed on it
+            HSS_TRY(fork.join());
             return NDHSS_OK;
         };
         if (lowrank) {
