@@ -318,16 +318,16 @@ __device__ __forceinline__ void panel_publish(const T (&v)[KB], typename Tr<T>::
 // column together with that row's values (double-buffered by step parity);
 // after the barrier every warp picks the winner and forms the pivot row
 // itself (lane j: entry j), then each thread updates its own row.
-template <typename T, int KB>
-__global__ void __launch_bounds__(PANEL_THREADS)
+template <typename T, int KB, int MAXT>
+__global__ void __launch_bounds__(MAXT)
 panel_reg_kernel(const int32_t* __restrict__ lev, const int32_t* __restrict__ node,
                  const int64_t* __restrict__ foff, const T* __restrict__ front, int32_t* __restrict__ ipiv,
                  T* __restrict__ ainv_buf, int32_t* __restrict__ swapmap, int k0, int kb, DevStatus* status) {
     using real = typename Tr<T>::real;
     using PK = PivKey<real>;
     using K = typename PK::K;
-    constexpr int NW = PANEL_THREADS / 32;
-    static_assert(KB <= 32, "one lane per pivot-row entry");
+    constexpr int NW = MAXT / 32;
+    static_assert(KB <= 32 && NW <= 32, "one lane per pivot-row entry and per warp");
     __shared__ T s_cand[2][NW][KB];          // each warp's best candidate row
     __shared__ K s_key[2][NW];
     __shared__ int s_pos[2][NW];
@@ -571,15 +571,25 @@ __global__ void finalize_sigma_kernel(const int32_t* __restrict__ lev, const int
 }
 
 // One panel launch: the register-resident kernel when asked and the element
-// fits (8 bytes at most), else the shared-memory kernel.
+// fits (8 bytes at most), else the shared-memory kernel.  More than
+// PANEL_THREADS rows take the 2 * PANEL_THREADS instance (64 registers a
+// thread: KB <= 16).
 template <typename T, int KB>
 void launch_panel(bool reg, int grid, int threads, size_t smem, cudaStream_t st, const int32_t* lev,
                   const int32_t* node, const int64_t* foff, const T* front, int32_t* ipiv, T* ainv, int32_t* swapmap,
                   int k0, int kb, DevStatus* status) {
     if constexpr (sizeof(T) <= 8) {
-        if (reg) {
-            panel_reg_kernel<T, KB><<<grid, threads, 0, st>>>(lev, node, foff, front, ipiv, ainv, swapmap, k0, kb, status);
+        if (reg && threads <= PANEL_THREADS) {
+            panel_reg_kernel<T, KB, PANEL_THREADS><<<grid, threads, 0, st>>>(lev, node, foff, front, ipiv, ainv, swapmap,
+                                                                             k0, kb, status);
             return;
+        }
+        if constexpr (KB <= 16) {
+            if (reg) {
+                panel_reg_kernel<T, KB, 2 * PANEL_THREADS><<<grid, threads, 0, st>>>(lev, node, foff, front, ipiv, ainv,
+                                                                                     swapmap, k0, kb, status);
+                return;
+            }
         }
     }
     panel_factor_kernel<T, KB><<<grid, threads, smem, st>>>(lev, node, foff, front, ipiv, ainv, swapmap, k0, kb, status);
@@ -753,15 +763,18 @@ ndhss_status factor_run(FactorData& F, const Tree& t, const V* d_vals, const int
             const int64_t s0 = tcl ? k0 / TC_KB2 * TC_KB2 : 0;     // the outer block's first pivot
             int kb = choose_kb(mimax - k0, sizeof(T), panel_opt);
             while (tcl && k0 + kb > s0 + TC_KB2) kb >>= 1;
+            // every candidate row in one thread's registers when the rows fit one
+            // CTA (up to 2 * PANEL_THREADS rows, at most 16 columns beyond PANEL_THREADS)
+            const bool reg_panel = reg_panel_ok && mimax - k0 <= 2 * PANEL_THREADS;
+            if (reg_panel && mimax - k0 > PANEL_THREADS) kb = std::min(kb, 16);
             const size_t smem = (size_t)(mimax - k0) * kb * sizeof(T) + (size_t)(mimax - k0) * sizeof(int);
             if (smem > PANEL_SMEM_MAX)
                 return set_error(NDHSS_ERR_INVALID_ARG, "front with %lld interior unknowns exceeds the panel kernel's shared memory",
                                  (long long)(mimax - k0));
             // one thread per candidate row up to 512: small fronts get small CTAs, so a level of
             // thousands of leaves runs in one wave instead of repeating its pivot chain per wave
-            const int pthreads = (int)std::min<int64_t>(PANEL_THREADS, std::max<int64_t>(64, (mimax - k0 + 31) / 32 * 32));
-            // every candidate row in one thread's registers when the rows fit one CTA
-            const bool reg_panel = reg_panel_ok && mimax - k0 <= PANEL_THREADS;
+            const int pthreads = (int)std::min<int64_t>(reg_panel ? 2 * PANEL_THREADS : PANEL_THREADS,
+                                                        std::max<int64_t>(64, (mimax - k0 + 31) / 32 * 32));
             // a level of more than 65535 fronts (the grid's y / z limit) goes in
             // chunks; the three kernels of a chunk share its per-front scratch
             for (int c0 = 0; c0 < L; c0 += MAX_GRID_YZ) {
