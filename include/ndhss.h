@@ -140,6 +140,10 @@ typedef struct {
     double tc_flops;            /* real flops of the tensor-core products R, L, S
                                    (8 per complex multiply-add), counted once per
                                    product whatever the operand split              */
+    double host_setup_ms;       /* host time from the call's entry to its first launch
+                                   (table uploads, allocations)                     */
+    double host_tail_ms;        /* host time from the last factor kernel's completion
+                                   to the return (apply schedule and multi-apply plan) */
 } ndhss_factor_stats;
 
 /* Library version string (static storage). */

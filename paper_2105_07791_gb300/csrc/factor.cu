@@ -20,6 +20,7 @@
 //   gemm_update   M = beta .* M + C * Z, beta = 0 on pivot rows / columns,
 //                 i.e. the rank-kb Gauss-Jordan update of the whole front.
 #include <algorithm>
+#include <chrono>
 #include <climits>
 #include <cmath>
 #include <cstdlib>
@@ -862,6 +863,7 @@ static ndhss_status factor_impl(const ndhss_tree* th, int32_t vtype, const int32
                                 const void* d_vals, const ndhss_factor_opts* opts, void* stream, ndhss_factorization** out) {
     (void)d_rowptr;
     (void)d_col;
+    const auto t_entry = std::chrono::steady_clock::now();
     if (!th || !d_vals || !out) return set_error(NDHSS_ERR_INVALID_ARG, "ndhss_factor: NULL argument");
     if (vtype != NDHSS_R64 && vtype != NDHSS_C128) return set_error(NDHSS_ERR_INVALID_ARG, "ndhss_factor: bad vtype %d", vtype);
     const Tree& t = th->t;
@@ -964,6 +966,7 @@ static ndhss_status factor_impl(const ndhss_tree* th, int32_t vtype, const int32
     DevStatus* d_status = nullptr;
     int64_t tmp_bytes = 0;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
+    auto t_done = std::chrono::steady_clock::now();
     auto cleanup = [&]() {
         for (void* q : {(void*)d_eoff, (void*)d_erow, (void*)d_ecol, (void*)d_eidx, (void*)d_fsrc, (void*)d_lev,
                         (void*)d_poff, (void*)d_woff, d_cbuf, d_zbuf, d_ainv, (void*)d_swapmap, (void*)d_status})
@@ -1017,6 +1020,7 @@ static ndhss_status factor_impl(const ndhss_tree* th, int32_t vtype, const int32
     tm.on = o.timing != 0;
     tm.st = st;
     NDHSS_CUDA_TRY(cudaEventRecord(e0, st));
+    F.host_setup_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_entry).count();
     if (!cplx && fp64)
         rc = factor_run<double, double>(F, t, (const double*)d_vals, d_eoff, d_erow, d_ecol, d_eidx, d_fsrc, d_poff, d_lev,
                                         lev_off, d_woff, (double*)d_cbuf, (double*)d_zbuf, (double*)d_ainv, d_swapmap, d_status,
@@ -1036,6 +1040,7 @@ static ndhss_status factor_impl(const ndhss_tree* th, int32_t vtype, const int32
         DevStatus hs{};
         cudaError_t e = cudaMemcpyAsync(&hs, d_status, sizeof(hs), cudaMemcpyDeviceToHost, st);
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        t_done = std::chrono::steady_clock::now();
         if (e != cudaSuccess) {
             rc = set_error(NDHSS_ERR_CUDA, "ndhss_factor: %s", cudaGetErrorString(e));
         } else if (hs.code == (int)NDHSS_ERR_TIMEOUT) {
@@ -1094,6 +1099,7 @@ static ndhss_status factor_impl(const ndhss_tree* th, int32_t vtype, const int32
         ndhss_factor_destroy(h);
         return rc;
     }
+    F.host_tail_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_done).count();
     *out = h;
     return NDHSS_OK;
 }
@@ -1240,6 +1246,8 @@ ndhss_status ndhss_factor_stats_get(const ndhss_factorization* fh, ndhss_factor_
     }
     st->update_flops = F.update_flops;
     st->tc_flops = F.tc_flops;
+    st->host_setup_ms = F.host_setup_ms;
+    st->host_tail_ms = F.host_tail_ms;
     return NDHSS_OK;
 }
 

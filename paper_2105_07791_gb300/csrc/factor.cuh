@@ -119,6 +119,8 @@ struct FactorData {
     int64_t class_launches[8] = {0};
     double update_flops = 0.0;
     double tc_flops = 0.0;                    // real flops of the tensor-core front products
+    double host_setup_ms = 0.0;               // host time from the call's entry to the first launch
+    double host_tail_ms = 0.0;                // host time from the last kernel's completion to the return
     int64_t apply_bytes = 0;
     int64_t dev_bytes = 0;
 

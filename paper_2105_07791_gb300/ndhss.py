@@ -62,7 +62,7 @@ class FactorStats(C.Structure):
                 ("apply_bytes", C.c_int64), ("factor_bytes", C.c_int64), ("factor_ms", C.c_double),
                 ("kmax", C.c_int32), ("prec", C.c_int32), ("launches", C.c_int64),
                 ("class_ms", C.c_double * 8), ("class_launches", C.c_int64 * 8), ("update_flops", C.c_double),
-                ("tc_flops", C.c_double)]
+                ("tc_flops", C.c_double), ("host_setup_ms", C.c_double), ("host_tail_ms", C.c_double)]
 
     CLASSES = ("assemble", "scatter", "panel", "prep", "update", "finalize", "compress", "tensor")
 
