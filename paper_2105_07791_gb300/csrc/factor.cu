@@ -22,9 +22,14 @@
 #include <algorithm>
 #include <chrono>
 #include <climits>
+#include <condition_variable>
+#include <deque>
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
+#include <string>
+#include <thread>
 
 #include "factor.cuh"
 
@@ -679,6 +684,126 @@ __global__ void gather_aii_kernel(const AiiJob* __restrict__ jobs, const int32_t
     }
 }
 
+// Compresses the low-rank R of finished levels on a stream and host thread
+// of its own while the main stream factors the levels above (R is read only
+// by the apply; the compression's adaptive rounds synchronise only the
+// worker's stream).  Levels are handed over in the order they finish, each
+// with an event recorded on the main stream after it; finish() waits for
+// all of them, merges the storage and counters, and makes the main stream
+// wait for the worker's.
+class LowRankWorker {
+public:
+    LowRankWorker(FactorData& F, const ndhss_factor_opts& o) : F_(F), o_(o) {}
+    LowRankWorker(const LowRankWorker&) = delete;
+    LowRankWorker& operator=(const LowRankWorker&) = delete;
+    ~LowRankWorker() {
+        stop();
+        // storage of a factorization that failed before finish(): freed after
+        // the worker's stream has drained
+        for (void* b : acc_.lr_bufs) cudaFreeAsync(b, st_);
+        for (cudaStream_t& x : acc_.side_streams)
+            if (x) cudaStreamDestroy(x);
+        if (st_) cudaStreamDestroy(st_);
+    }
+    ndhss_status start() {
+        NDHSS_CUDA_TRY(cudaGetDevice(&dev_));
+        NDHSS_CUDA_TRY(cudaStreamCreateWithFlags(&st_, cudaStreamNonBlocking));
+        for (cudaStream_t& x : acc_.side_streams) NDHSS_CUDA_TRY(cudaStreamCreateWithFlags(&x, cudaStreamNonBlocking));
+        th_ = std::thread([this] { run(); });
+        return NDHSS_OK;
+    }
+    // the fronts' R blocks are final once the main stream reaches this point
+    ndhss_status submit(std::vector<int32_t>&& fronts, cudaStream_t main) {
+        cudaEvent_t ev = nullptr;
+        NDHSS_CUDA_TRY(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+        const cudaError_t e = cudaEventRecord(ev, main);
+        if (e != cudaSuccess) {
+            cudaEventDestroy(ev);
+            return set_error(NDHSS_ERR_CUDA, "ndhss_factor: low-rank hand-over: %s", cudaGetErrorString(e));
+        }
+        {
+            std::lock_guard<std::mutex> lk(mu_);
+            q_.push_back({std::move(fronts), ev});
+        }
+        cv_.notify_one();
+        return NDHSS_OK;
+    }
+    ndhss_status finish(cudaStream_t main) {
+        stop();
+        if (status_ != NDHSS_OK) return set_error(status_, "%s", msg_.c_str());
+        F_.dev_bytes += acc_.dev_bytes;
+        F_.lr_bufs.insert(F_.lr_bufs.end(), acc_.lr_bufs.begin(), acc_.lr_bufs.end());
+        acc_.lr_bufs.clear();
+        F_.hss_rounds_max = std::max(F_.hss_rounds_max, acc_.hss_rounds_max);
+        F_.kmax = std::max(F_.kmax, kmax_);
+        cudaEvent_t ev = nullptr;
+        NDHSS_CUDA_TRY(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+        cudaError_t e = cudaEventRecord(ev, st_);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(main, ev, 0);
+        cudaEventDestroy(ev);
+        if (e != cudaSuccess) return set_error(NDHSS_ERR_CUDA, "ndhss_factor: low-rank join: %s", cudaGetErrorString(e));
+        return NDHSS_OK;
+    }
+
+private:
+    struct Job {
+        std::vector<int32_t> fronts;
+        cudaEvent_t ev;
+    };
+    void stop() {
+        if (!th_.joinable()) return;
+        {
+            std::lock_guard<std::mutex> lk(mu_);
+            done_ = true;
+        }
+        cv_.notify_one();
+        th_.join();
+    }
+    void run() {
+        cudaSetDevice(dev_);
+        for (;;) {
+            Job j;
+            {
+                std::unique_lock<std::mutex> lk(mu_);
+                cv_.wait(lk, [this] { return done_ || !q_.empty(); });
+                if (q_.empty()) return;
+                j = std::move(q_.front());
+                q_.pop_front();
+            }
+            if (status_ == NDHSS_OK) {
+                ndhss_status rc = NDHSS_OK;
+                try {
+                    const cudaError_t e = cudaStreamWaitEvent(st_, j.ev, 0);
+                    rc = e == cudaSuccess ? hss_lowrank_fronts(F_, j.fronts, acc_, &kmax_, o_, st_)
+                                          : set_error(NDHSS_ERR_CUDA, "ndhss_factor: %s", cudaGetErrorString(e));
+                } catch (const std::bad_alloc&) {
+                    rc = set_error(NDHSS_ERR_OOM, "ndhss_factor: host allocation failed in the low-rank worker");
+                } catch (...) {
+                    rc = set_error(NDHSS_ERR_INTERNAL, "ndhss_factor: exception in the low-rank worker");
+                }
+                if (rc != NDHSS_OK) {
+                    status_ = rc;
+                    msg_ = ndhss_last_error();
+                }
+            }
+            cudaEventDestroy(j.ev);
+        }
+    }
+    FactorData& F_;
+    const ndhss_factor_opts& o_;
+    FactorData acc_;
+    int kmax_ = 0;
+    int dev_ = 0;
+    cudaStream_t st_ = nullptr;
+    std::thread th_;
+    std::mutex mu_;
+    std::condition_variable cv_;
+    std::deque<Job> q_;
+    bool done_ = false;
+    ndhss_status status_ = NDHSS_OK;     // written by the worker only, read after the join
+    std::string msg_;
+};
+
 template <typename T, typename V>
 ndhss_status factor_run(FactorData& F, const Tree& t, const V* d_vals, const int32_t* d_eoff,
                         const int32_t* d_erow, const int32_t* d_ecol, const int32_t* d_eidx,
@@ -687,6 +812,14 @@ ndhss_status factor_run(FactorData& F, const Tree& t, const V* d_vals, const int
                         T* d_ainv, int32_t* d_swapmap, DevStatus* d_status, const ndhss_factor_opts& o,
                         LaunchTimer& tm, cudaStream_t st) {
     const int panel_opt = o.panel;
+    // the low-rank R of the levels below the switching level compresses on a
+    // second stream while the main stream factors the root level
+    LowRankWorker lrw(F, o);
+    const bool lr_async = F.L_hss > 1;
+    if (lr_async) {
+        const ndhss_status rcw = lrw.start();
+        if (rcw != NDHSS_OK) return rcw;
+    }
     // NDHSS_PANEL=smem keeps every panel in shared memory (panel_factor_kernel;
     // a cross-check of the register-resident panel, which gives the same outputs)
     const char* pe = std::getenv("NDHSS_PANEL");
@@ -838,11 +971,27 @@ ndhss_status factor_run(FactorData& F, const Tree& t, const V* d_vals, const int
             ndhss_status rc2 = hss_compress_level(F, t, l, o, st);
             if (rc2 == NDHSS_OK && d_aii) rc2 = hss_ulv_level(F, t, l, d_aii, aii_off, o, st);
             if (d_aii) cudaFreeAsync(d_aii, st);
+            // all levels' R in one batch (as few adaptive rounds as at the end),
+            // handed over before the root level, whose elimination runs one CTA
+            // at a time and leaves the SMs to the worker (handing over level
+            // by level slowed the main stream's latency-bound kernels more than
+            // it saved)
+            if (rc2 == NDHSS_OK && lr_async && l == 1 && !F.lr_pending.empty()) {
+                std::vector<int32_t> fronts;
+                fronts.swap(F.lr_pending);
+                rc2 = lrw.submit(std::move(fronts), st);
+            }
             if (rc2 != NDHSS_OK) return rc2;
             tm.end(6);
         } else if (d_aii) {
             cudaFreeAsync(d_aii, st);
         }
+    }
+    if (lr_async) {
+        tm.begin();
+        const ndhss_status rc2 = lrw.finish(st);
+        if (rc2 != NDHSS_OK) return rc2;
+        tm.end(6);
     }
     if (!F.lr_pending.empty()) {
         tm.begin();

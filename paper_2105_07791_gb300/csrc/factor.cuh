@@ -63,6 +63,9 @@ struct FactorData {
     // whose R waits for the batch at the end of the factorization
     int32_t L_hss = -1;                       // levels <= L_hss compress S; < L_hss also R
     std::vector<void*> lr_bufs;
+    // side streams of the row-ID launches for a caller that owns its own (a
+    // second host thread); null: the library's per-device pool
+    cudaStream_t side_streams[4] = {};
     std::vector<int32_t> lr_pending;
 
     // multi right-hand-side apply (multi.cu): the (node, first row) of every
@@ -173,6 +176,11 @@ size_t apply_work_bytes(const FactorData& F);
 // Builds and uploads the dataflow queue once the factor (and its low-rank
 // tier) is complete; defined in apply.cu.
 ndhss_status build_apply_schedule(FactorData& F, cudaStream_t st);
+// Low-rank R of the given (final) fronts on stream st: results to F.lr_ptr /
+// F.lr_k (one element per front), device storage and counters to acc, the
+// largest rank to *kmax.  Defined in hss.cu.
+ndhss_status hss_lowrank_fronts(FactorData& F, const std::vector<int32_t>& fronts, FactorData& acc, int* kmax,
+                                const ndhss_factor_opts& o, cudaStream_t st);
 // The tile lists of the multi right-hand-side apply.  Defined in multi.cu.
 ndhss_status build_multi_plan(FactorData& F, cudaStream_t st);
 // NDHSS_ERR_TIMEOUT if an earlier apply of this factorization gave up a wait.

@@ -1168,8 +1168,15 @@ struct SideFork {
     cudaEvent_t fork_ev = nullptr;
     std::vector<cudaEvent_t> done;
     cudaStream_t side[NS] = {};
-    SideFork(cudaStream_t s, int count) : st(s), n(std::min(count, NS)) {
+    SideFork(cudaStream_t s, int count, const cudaStream_t* own = nullptr) : st(s), n(std::min(count, NS)) {
         if (n <= 1) { n = 0; return; }
+        if (own && own[0]) {
+            for (int i = 0; i < NS; ++i) side[i] = own[i];
+            if ((status = cudaEventCreateWithFlags(&fork_ev, cudaEventDisableTiming)) != cudaSuccess) { n = 0; return; }
+            status = cudaEventRecord(fork_ev, st);
+            done.assign(n, nullptr);
+            return;
+        }
         static std::mutex mu;
         static cudaStream_t pool[64][NS];
         static bool made[64] = {};
@@ -1729,7 +1736,7 @@ ndhss_status compress_problems(std::vector<Problem>& probs, bool lowrank, const 
             // than one, each runs on a side stream forked from st and joined back
             int nlaunch = big.empty() ? 0 : 1;
             for (int g = 0; (1 << g) <= RID_MAX_CLUSTER; ++g) nlaunch += grp[g].empty() ? 0 : 1;
-            SideFork fork(st, nlaunch > 1 ? nlaunch : 0);
+            SideFork fork(st, nlaunch > 1 ? nlaunch : 0, F.side_streams);
             HSS_TRY(fork.status);
             std::vector<std::unique_ptr<DeviceVec<int>>> lists;
             int li = 0;
@@ -2114,8 +2121,8 @@ ndhss_status compress_level_impl(FactorData& F, const Tree& t, int level, const 
             for (int q = 0; q < mb; ++q) top += (t.emap[t.b_off(s) + q] < t.m_i(par)) ? 1 : 0;
             sp.push_back({s, (int)mb, (int)mb, m, Fs + mi * m + mi, top, (uint64_t)2 * s});
         }
-        // R^sigma is read only by the apply: its compression waits for the end of
-        // the factorization, where the fronts of all levels go in one batch
+        // R^sigma is read only by the apply: queued here, compressed while the
+        // levels above are factored (or at the end, all levels in one batch)
         if (level < F.L_hss && mb > 0 && mi > 0) F.lr_pending.push_back(s);
     }
     std::vector<int> ks;
@@ -2127,29 +2134,42 @@ ndhss_status compress_level_impl(FactorData& F, const Tree& t, int level, const 
     return NDHSS_OK;
 }
 
-// Low-rank R^sigma ~ X R(J, :) of every front queued by compress_level_impl,
-// all levels in one batch (each front keeps its own Philox stream 2 s + 1, so
-// the result does not depend on the batching).
+// Low-rank R^sigma ~ X R(J, :) of the given fronts (each keeps its own
+// Philox stream 2 s + 1, so the result does not depend on the batching).
+// F is only read here, apart from the fronts' own lr_ptr / lr_k elements;
+// the storage and counters go to acc: the factorization runs this on a
+// second host thread while the main stream factors the levels above.
 template <typename T>
-ndhss_status lowrank_pending_impl(FactorData& F, const ndhss_factor_opts& o, cudaStream_t st) {
+ndhss_status lowrank_fronts_impl(FactorData& F, const std::vector<int32_t>& fronts, FactorData& acc, int* kmax,
+                                 const ndhss_factor_opts& o, cudaStream_t st) {
     T* base = static_cast<T*>(F.d_front);
     std::vector<Problem> rp;
-    for (int s : F.lr_pending) {
+    for (int s : fronts) {
         const int64_t mi = F.m_i(s), mb = F.m_b(s), m = mi + mb;
         rp.push_back({s, (int)mi, (int)mb, m, base + F.foff[s] + mi * m, 0, (uint64_t)2 * s + 1});
     }
-    F.lr_pending.clear();
     if (rp.empty()) return NDHSS_OK;
     std::vector<int> kr;
     std::vector<uint64_t> ptr;
-    ndhss_status rc = compress_problems<T>(rp, true, o, kr, &ptr, F, st);
+    ndhss_status rc = compress_problems<T>(rp, true, o, kr, &ptr, acc, st);
     if (rc != NDHSS_OK) return rc;
     for (size_t i = 0; i < rp.size(); ++i) {
         F.lr_ptr[rp[i].node] = ptr[i];
         F.lr_k[rp[i].node] = kr[i];
-        F.kmax = std::max(F.kmax, kr[i]);
+        *kmax = std::max(*kmax, kr[i]);
     }
     return NDHSS_OK;
+}
+
+// The fronts queued by compress_level_impl, all levels in one batch.
+template <typename T>
+ndhss_status lowrank_pending_impl(FactorData& F, const ndhss_factor_opts& o, cudaStream_t st) {
+    std::vector<int32_t> pending;
+    pending.swap(F.lr_pending);
+    int kmax = F.kmax;
+    const ndhss_status rc = lowrank_fronts_impl<T>(F, pending, F, &kmax, o, st);
+    F.kmax = kmax;
+    return rc;
 }
 
 }  // namespace
@@ -2213,6 +2233,15 @@ ndhss_status hss_lowrank_pending(FactorData& F, const ndhss_factor_opts& o, cuda
     if (!cplx) return lowrank_pending_impl<float>(F, o, st);
     if (F.prec == NDHSS_FP64) return lowrank_pending_impl<c128>(F, o, st);
     return lowrank_pending_impl<c64>(F, o, st);
+}
+
+ndhss_status hss_lowrank_fronts(FactorData& F, const std::vector<int32_t>& fronts, FactorData& acc, int* kmax,
+                                const ndhss_factor_opts& o, cudaStream_t st) {
+    const bool cplx = F.vtype == NDHSS_C128;
+    if (!cplx && F.prec == NDHSS_FP64) return lowrank_fronts_impl<double>(F, fronts, acc, kmax, o, st);
+    if (!cplx) return lowrank_fronts_impl<float>(F, fronts, acc, kmax, o, st);
+    if (F.prec == NDHSS_FP64) return lowrank_fronts_impl<c128>(F, fronts, acc, kmax, o, st);
+    return lowrank_fronts_impl<c64>(F, fronts, acc, kmax, o, st);
 }
 
 ndhss_status hss_compress_level(FactorData& F, const Tree& t, int level, const ndhss_factor_opts& o, cudaStream_t st) {
