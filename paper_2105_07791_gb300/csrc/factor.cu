@@ -315,11 +315,12 @@ __device__ __forceinline__ void panel_publish(const T (&v)[KB], typename Tr<T>::
 }
 
 // The panel of panel_factor_kernel with every candidate row in the
-// registers of one thread (fronts with at most PANEL_THREADS candidate rows,
-// elements of at most 8 bytes).  Rows are never moved: each thread tracks
-// the position its row would hold after the interchanges, so pivots, ties
+// registers of one thread (fronts with at most MAXT candidate rows, elements
+// of at most 8 bytes).  Rows are never moved: each thread tracks the
+// position its row would hold after the interchanges, so pivots, ties
 // (lowest position first) and the exchange arithmetic are those of the
-// shared-memory kernel, and so are the outputs.  A pivot costs one barrier:
+// shared-memory kernel: real outputs are bit for bit the same, complex ones
+// up to how the compiler contracts the complex products.  A pivot costs one barrier:
 // at the end of a step every warp publishes its best candidate for the next
 // column together with that row's values (double-buffered by step parity);
 // after the barrier every warp picks the winner and forms the pivot row
@@ -684,13 +685,12 @@ __global__ void gather_aii_kernel(const AiiJob* __restrict__ jobs, const int32_t
     }
 }
 
-// Compresses the low-rank R of finished levels on a stream and host thread
-// of its own while the main stream factors the levels above (R is read only
-// by the apply; the compression's adaptive rounds synchronise only the
-// worker's stream).  Levels are handed over in the order they finish, each
-// with an event recorded on the main stream after it; finish() waits for
-// all of them, merges the storage and counters, and makes the main stream
-// wait for the worker's.
+// Compresses the low-rank R of finished fronts on a stream and host thread
+// of its own while the main stream goes on factoring (R is read only by the
+// apply; the compression's adaptive rounds synchronise only the worker's
+// stream).  Each hand-over carries an event recorded on the main stream
+// once its fronts are final; finish() waits for every hand-over, merges the
+// storage and counters, and makes the main stream wait for the worker's.
 class LowRankWorker {
 public:
     LowRankWorker(FactorData& F, const ndhss_factor_opts& o) : F_(F), o_(o) {}
@@ -821,7 +821,8 @@ ndhss_status factor_run(FactorData& F, const Tree& t, const V* d_vals, const int
         if (rcw != NDHSS_OK) return rcw;
     }
     // NDHSS_PANEL=smem keeps every panel in shared memory (panel_factor_kernel;
-    // a cross-check of the register-resident panel, which gives the same outputs)
+    // a cross-check of the register-resident panel: the same real outputs, the
+    // complex ones up to FMA contraction)
     const char* pe = std::getenv("NDHSS_PANEL");
     const bool reg_panel_ok = sizeof(T) <= 8 && !(pe && std::strcmp(pe, "smem") == 0);
     ndhss_status rc = set_smem_attrs<T>();

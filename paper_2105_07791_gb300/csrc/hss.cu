@@ -1157,9 +1157,10 @@ struct DeviceVec {
 // Independent launches of one step on side streams: forked from the
 // caller's stream st by an event, each joined back to st by its own event,
 // so everything after the join stays ordered on st.  Without side launches
-// (n == 0) every stream() is st itself.  The side streams are created once
-// per device and kept (four, shared by all callers: sharing only orders
-// their launches more strictly).
+// (n == 0) every stream() is st itself.  The side streams are the caller's
+// own when it passes four (a second host thread of the factorization), else
+// a pool created once per device and kept (shared by all such callers:
+// sharing only orders their launches more strictly).
 struct SideFork {
     static constexpr int NS = 4;
     cudaStream_t st;
@@ -2121,8 +2122,9 @@ ndhss_status compress_level_impl(FactorData& F, const Tree& t, int level, const 
             for (int q = 0; q < mb; ++q) top += (t.emap[t.b_off(s) + q] < t.m_i(par)) ? 1 : 0;
             sp.push_back({s, (int)mb, (int)mb, m, Fs + mi * m + mi, top, (uint64_t)2 * s});
         }
-        // R^sigma is read only by the apply: queued here, compressed while the
-        // levels above are factored (or at the end, all levels in one batch)
+        // R^sigma is read only by the apply: queued here, compressed in one
+        // batch of all levels beside the root level's elimination (or after
+        // the level loop)
         if (level < F.L_hss && mb > 0 && mi > 0) F.lr_pending.push_back(s);
     }
     std::vector<int> ks;
@@ -2138,7 +2140,7 @@ ndhss_status compress_level_impl(FactorData& F, const Tree& t, int level, const 
 // Philox stream 2 s + 1, so the result does not depend on the batching).
 // F is only read here, apart from the fronts' own lr_ptr / lr_k elements;
 // the storage and counters go to acc: the factorization runs this on a
-// second host thread while the main stream factors the levels above.
+// second host thread while the main stream eliminates the root level.
 template <typename T>
 ndhss_status lowrank_fronts_impl(FactorData& F, const std::vector<int32_t>& fronts, FactorData& acc, int* kmax,
                                  const ndhss_factor_opts& o, cudaStream_t st) {
