@@ -246,6 +246,10 @@ void ndhss_tree_destroy(ndhss_tree* t);
  *              read during the call
  *   opts       factor options (NULL = FP64, no compression)
  *   stream     stream for all device work; synchronised before returning
+ *              (with compression, the low-rank R is compressed on a stream
+ *              and host thread of the library's own, beside the root level's
+ *              elimination; both are joined back to `stream` and ended
+ *              before the call returns)
  *   out        receives a new factor handle holding device memory
  * Errors: SINGULAR (node reported), OOM, CUDA, INVALID_ARG.
  */
